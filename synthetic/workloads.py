@@ -1,0 +1,234 @@
+"""Synthetic borehole logging workloads (models, shots, wavelet), seeded.
+
+The paper inverts synthetic data only (Numerical Examples) and prints no
+model values, so the workloads below stand in for its layered and
+flushed-zone models: a fluid-filled borehole of radius 0.10 m (water,
+Vp 1500 m/s, rho 1000 kg/m^3) in an axially layered formation with a radial
+damage annulus, a monopole source and pressure receivers on the axis
+(Numerical Examples; Fig. 2, Fig. 3).
+
+Every array is float32 (the precision the CUDA path steps in); the oracle
+upcasts the same values to float64.  Indices are window coordinates: cell
+(i, j) sits at r = (i + 1/2) dr, z = j dz.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FLUID_VP = 1500.0
+FLUID_RHO = 1000.0
+BOREHOLE_RADIUS = 0.10
+
+
+@dataclass
+class Workload:
+    name: str
+    nr: int
+    nz: int                # global model length in cells
+    nt: int
+    npml_r: int
+    npml_z: int
+    dr: float
+    dz: float
+    dt: float
+    f0: float
+    vp: np.ndarray         # [nr, nz] float32, start model
+    vs: np.ndarray
+    rho: np.ndarray
+    vp_true: np.ndarray    # [nr, nz] float32, model that makes the "measured" data
+    vs_true: np.ndarray
+    rho_true: np.ndarray
+    shots: list = field(default_factory=list)  # dicts: z_offset, nz, src, rec_iz
+    wavelet: np.ndarray | None = None          # [nt] float32, s(t_{n+1/2})
+    pml_R: float = 1e-3
+
+    @property
+    def nshots(self):
+        return len(self.shots)
+
+    @property
+    def nrec(self):
+        return max(len(s["rec_iz"]) for s in self.shots)
+
+    def cell_steps(self):
+        """Cell updates of one forward pass over all shots."""
+        return sum(self.nr * s["nz"] * self.nt for s in self.shots)
+
+
+def ricker(nt: int, dt: float, f0: float, t0: float | None = None) -> np.ndarray:
+    """Ricker wavelet of unit amplitude sampled at t = (n + 1/2) dt, with
+    delay t0 = 1.5 / f0 (the paper names no wavelet; this is the reading)."""
+    t0 = 1.5 / f0 if t0 is None else t0
+    t = (np.arange(nt) + 0.5) * dt - t0
+    a = (np.pi * f0 * t) ** 2
+    return ((1.0 - 2.0 * a) * np.exp(-a)).astype(np.float32)
+
+
+def _borehole(nr, nz, dr, fluid_radius=BOREHOLE_RADIUS):
+    """Boolean [nr] of radial cells inside the borehole fluid."""
+    r = (np.arange(nr) + 0.5) * dr
+    return r < fluid_radius
+
+
+def _fill_fluid(vp, vs, rho, fluid_rows):
+    vp[fluid_rows, :] = FLUID_VP
+    vs[fluid_rows, :] = 0.0
+    rho[fluid_rows, :] = FLUID_RHO
+
+
+def _f32(*arrs):
+    return [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
+
+
+def homogeneous(nr, nz, nt, npml_r, npml_z, h, dt, f0, vp, vs, rho, src, rec_iz,
+                name="homogeneous"):
+    """A homogeneous whole space (vs = 0 gives a fluid), single shot."""
+    a = np.full((nr, nz), vp)
+    b = np.full((nr, nz), vs)
+    c = np.full((nr, nz), rho)
+    a, b, c = _f32(a, b, c)
+    return Workload(name, nr, nz, nt, npml_r, npml_z, h, h, dt, f0, a, b, c, a.copy(),
+                    b.copy(), c.copy(),
+                    [dict(z_offset=0, nz=nz, src=tuple(src), rec_iz=list(rec_iz))],
+                    ricker(nt, dt, f0))
+
+
+def config0():
+    """Single-shot correctness case: nr 80 (20-cell C-PML), nz 400 (20-cell
+    C-PML top and bottom), 1 cm cells, dt 1 us, 2500 steps, 5 kHz Ricker on
+    the axis at z = 0.4 m, 8 receivers on the axis at 2.00 ... 3.05 m.
+    Formation Vp 4000, Vs 2300, rho 2500; the true model adds a damaged
+    annulus at r = 0.10 ... 0.20 m with Vp and Vs lowered by 10 %."""
+    nr, nz, h, dt, nt = 80, 400, 0.01, 1e-6, 2500
+    vp = np.full((nr, nz), 4000.0)
+    vs = np.full((nr, nz), 2300.0)
+    rho = np.full((nr, nz), 2500.0)
+    fl = _borehole(nr, nz, h)
+    _fill_fluid(vp, vs, rho, fl)
+    vpt, vst = vp.copy(), vs.copy()
+    r = (np.arange(nr) + 0.5) * h
+    ann = (r >= 0.10) & (r < 0.20)
+    vpt[ann, :] *= 0.9
+    vst[ann, :] *= 0.9
+    vp, vs, rho, vpt, vst = _f32(vp, vs, rho, vpt, vst)
+    rec = [int(round(z / h)) for z in np.arange(8) * 0.15 + 2.00]
+    shot = dict(z_offset=0, nz=nz, src=(0, int(round(0.4 / h))), rec_iz=rec)
+    return Workload("c0", nr, nz, nt, 20, 20, h, h, dt, 5e3, vp, vs, rho, vpt, vst,
+                    rho.copy(), [shot], ricker(nt, dt, 5e3))
+
+
+def _layered(rng, nr, nz, h, fluid_rows):
+    """Axially layered formation: beds 0.3-1.0 m thick, Vp U(3000, 5000),
+    Vs = Vp / U(1.7, 1.9), rho U(2200, 2600); plus one radial damage zone of
+    depth U(0.05, 0.25) m beyond the borehole wall with Vp and Vs lowered by
+    U(5, 15) %.  Returns start (undamaged) and true (damaged) models."""
+    vp = np.empty((nr, nz))
+    vs = np.empty((nr, nz))
+    rho = np.empty((nr, nz))
+    z = 0
+    while z < nz:
+        thick = max(1, int(round(rng.uniform(0.3, 1.0) / h)))
+        bvp = rng.uniform(3000.0, 5000.0)
+        vp[:, z: z + thick] = bvp
+        vs[:, z: z + thick] = bvp / rng.uniform(1.7, 1.9)
+        rho[:, z: z + thick] = rng.uniform(2200.0, 2600.0)
+        z += thick
+    _fill_fluid(vp, vs, rho, fluid_rows)
+    depth = rng.uniform(0.05, 0.25)
+    drop = rng.uniform(0.05, 0.15)
+    r = (np.arange(nr) + 0.5) * h
+    dmg = (r >= BOREHOLE_RADIUS) & (r < BOREHOLE_RADIUS + depth)
+    vpt, vst = vp.copy(), vs.copy()
+    vpt[dmg, :] *= 1.0 - drop
+    vst[dmg, :] *= 1.0 - drop
+    return vp, vs, rho, vpt, vst
+
+
+def _shot(z_offset, nz, npml_z, h):
+    """Source on the axis 80 cells below the window's top C-PML; 13
+    receivers on the axis at offsets 3.00 ... 4.80 m (0.15 m apart)."""
+    src_iz = npml_z + 80
+    rec = [src_iz + int(round(o / h)) for o in 3.0 + 0.15 * np.arange(13)]
+    assert rec[-1] < nz - npml_z, "receivers must sit above the bottom C-PML"
+    return dict(z_offset=int(z_offset), nz=int(nz), src=(0, src_iz), rec_iz=rec)
+
+
+def config1(seed=0):
+    """Production single shot: nr 240 (40-cell C-PML), nz 1600 (40-cell
+    C-PML), 5 mm cells, dt 0.5 us, 8000 steps, 10 kHz Ricker."""
+    rng = np.random.default_rng(seed)
+    nr, nz, h, dt, nt, npml = 240, 1600, 0.005, 0.5e-6, 8000, 40
+    vp, vs, rho, vpt, vst = _layered(rng, nr, nz, h, _borehole(nr, nz, h))
+    vp, vs, rho, vpt, vst = _f32(vp, vs, rho, vpt, vst)
+    return Workload("c1", nr, nz, nt, npml, npml, h, h, dt, 1e4, vp, vs, rho, vpt, vst,
+                    rho.copy(), [_shot(0, nz, npml, h)], ricker(nt, dt, 1e4))
+
+
+def _batched(name, rng, nshots, nz_lo, nz_hi, model_len_cells, nt=8000):
+    nr, h, dt, npml = 240, 0.005, 0.5e-6, 40
+    vp, vs, rho, vpt, vst = _layered(rng, nr, model_len_cells, h, _borehole(nr, 0, h))
+    vp, vs, rho, vpt, vst = _f32(vp, vs, rho, vpt, vst)
+    step = int(round(0.15 / h))
+    shots = []
+    for s in range(nshots):
+        nzs = int(rng.integers(nz_lo, nz_hi + 1))
+        z0 = s * step
+        assert z0 + nzs <= model_len_cells
+        shots.append(_shot(z0, nzs, npml, h))
+    return Workload(name, nr, model_len_cells, nt, npml, npml, h, h, dt, 1e4, vp, vs, rho,
+                    vpt, vst, rho.copy(), shots, ricker(nt, dt, 1e4))
+
+
+def config2(seed=0, nt=8000):
+    """Batched logging run: 64 shots, source stepped 0.15 m, windows
+    nz ~ U{1400..2000} cells over a 20 m layered model."""
+    return _batched("c2", np.random.default_rng(seed), 64, 1400, 2000, 4000, nt)
+
+
+def config3(seed=0, nt=12000):
+    """Large single shot: nr 400, nz 4000, 5 mm cells, 12000 steps."""
+    rng = np.random.default_rng(seed)
+    nr, nz, h, dt, npml = 400, 4000, 0.005, 0.5e-6, 40
+    vp, vs, rho, vpt, vst = _layered(rng, nr, nz, h, _borehole(nr, nz, h))
+    vp, vs, rho, vpt, vst = _f32(vp, vs, rho, vpt, vst)
+    return Workload("c3", nr, nz, nt, npml, npml, h, h, dt, 1e4, vp, vs, rho, vpt, vst,
+                    rho.copy(), [_shot(0, nz, npml, h)], ricker(nt, dt, 1e4))
+
+
+def config4(seed=0, nt=8000):
+    """256 shots with windows nz ~ U{1200..2400} over a layered model
+    extended to 256 * 0.15 m + 2400 cells + 1 m (about 51.4 m)."""
+    length = 256 * 30 + 2400 + 200
+    return _batched("c4", np.random.default_rng(seed), 256, 1200, 2400, length, nt)
+
+
+def tiny_borehole(seed=0, nr=24, nz=48, npml=6, nt=300, h=0.01, dt=1e-6, f0=15e3,
+                  fluid_rows=4, nrec=3, heterogeneous=True):
+    """A small borehole model for finite-difference gradient and dot-product
+    tests: fluid in the first `fluid_rows` radial cells, a formation with
+    random per-cell perturbations (so that every cell matters)."""
+    rng = np.random.default_rng(seed)
+    vp = np.full((nr, nz), 3500.0)
+    vs = np.full((nr, nz), 2000.0)
+    rho = np.full((nr, nz), 2400.0)
+    if heterogeneous:
+        vp *= 1.0 + 0.05 * rng.standard_normal((nr, nz))
+        vs *= 1.0 + 0.05 * rng.standard_normal((nr, nz))
+        rho *= 1.0 + 0.05 * rng.standard_normal((nr, nz))
+    vp[:fluid_rows] = FLUID_VP
+    vs[:fluid_rows] = 0.0
+    rho[:fluid_rows] = FLUID_RHO
+    vpt = vp * (1.0 + 0.03 * rng.standard_normal((nr, nz)))
+    vst = vs * (1.0 + 0.03 * rng.standard_normal((nr, nz)))
+    vpt[:fluid_rows], vst[:fluid_rows] = vp[:fluid_rows], vs[:fluid_rows]
+    vp, vs, rho, vpt, vst = _f32(vp, vs, rho, vpt, vst)
+    src = (0, npml + 3)
+    rec = list(np.linspace(npml + 10, nz - npml - 2, nrec).round().astype(int))
+    shot = dict(z_offset=0, nz=nz, src=src, rec_iz=[int(x) for x in rec])
+    return Workload("tiny", nr, nz, nt, npml, npml, h, h, dt, f0, vp, vs, rho, vpt, vst,
+                    rho.copy(), [shot], ricker(nt, dt, f0))
+
+
+PRESETS = {"c0": config0, "c1": config1, "c2": config2, "c3": config3, "c4": config4}
