@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the borehole FWI hot path on GB300.
+
+One step = one full inversion iteration of the production single-shot
+workload (nr 240 x nz 1600 cells, 8000 steps, 10 kHz): forward modelling,
+residual and misfit, adjoint modelling with the fused gradient correlation,
+per-cell gradients, preconditioner, and model update, all through the C ABI
+of libbh.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (launched by torchrun) every rank
+inverts its own independent shot (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s and gradient evals/s (fwd+adj+grad) at 1 GB300; % of HBM roofline"
+UNIT = "Gcell-updates/s"
+PROFILE_EVERY = 64
+CPU_SAMPLE_STEPS = 100
+REF_SAMPLE_STEPS = 100
+
+# Algorithmic bytes per cell and launch of each stepping kernel: every array
+# the kernel must touch, streamed once (FP32 fields, FP32 model/coefficients,
+# Kahan pairs, FP32 history), C-PML memories weighted by the fraction of
+# cells inside the layers (s = npml_r / nr + 2 npml_z / nz).
+def kernel_bytes_per_cell(kernel: str, s: float) -> float:
+    return {
+        # 4 stresses read, v_r v_z read+write, 2 buoyancies, 4 memories r+w
+        "fwd_vel": 16 + 16 + 8 + 16 * s,
+        # v_r v_z read, 4 stresses read+write, lambda mu mu_h, history write, 4 memories
+        "fwd_stress": 8 + 32 + 12 + 8 + 16 * s,
+        # 4 adjoint stresses read, 2 adjoint velocities r+w, lambda mu mu_h,
+        # history v^{n+1/2} and v^{n-1/2}, 5 Kahan pairs r+w, 3 Hessian r+w,
+        # 4 adjoint memories (read one bank, write the other)
+        "adj_stress": 16 + 16 + 12 + 16 + 80 + 24 + 16 * s,
+        # 2 adjoint velocities read, 4 adjoint stresses r+w, 2 buoyancies, 4 memories
+        "adj_vel": 8 + 32 + 8 + 16 * s,
+    }[kernel]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2005_00281_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_sha") != source_sha():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_config(w, nt=None):
+    return {"workload": f"{w.name}: single-shot borehole FWI iteration, nr {w.nr} x nz {w.nz} "
+                        f"cells (C-PML {w.npml_r}/{w.npml_z}), {nt or w.nt} steps, "
+                        f"h {w.dr} m, dt {w.dt} s, f0 {w.f0:g} Hz, {w.nrec} receivers",
+            "nr": w.nr, "nz": w.nz, "nt": nt or w.nt, "nshots": w.nshots,
+            "l2": "inputs larger than L2: the forward history streamed every step is "
+                  f"{2 * 8 * w.nr * w.nz * (nt or w.nt) / 1e9:.1f} GB (write + read)"}
+
+
+# ---------------------------------------------------------------- oracle
+
+def oracle_sample(w, nt_sample):
+    """The FP64 oracle as it stands, one forward + adjoint + gradient of the
+    workload's first shot truncated to nt_sample steps.  Returns
+    (Gcell-updates/s, seconds, threads)."""
+    import numpy as np
+    from oracle import oracle as O
+
+    sh = w.shots[0]
+    g = O.Grid(w.nr, sh["nz"], nt_sample, w.npml_r, w.npml_z, w.dr, w.dz, w.dt, w.f0, w.pml_R)
+    z0 = sh["z_offset"]
+    sl = np.s_[:, z0: z0 + sh["nz"]]
+    vp, vs, rho = (np.ascontiguousarray(a[sl]) for a in (w.vp, w.vs, w.rho))
+    wav = w.wavelet[:nt_sample]
+    t0 = time.perf_counter()
+    seis, vh = O.forward(g, vp, vs, rho, wav, sh["src"], sh["rec_iz"])
+    resid, J = O.residual_misfit(seis, np.zeros_like(seis))
+    acc, _, _ = O.adjoint(g, vp, vs, rho, resid, sh["src"], sh["rec_iz"], vh)
+    O.finalize(g, vp, vs, rho, acc)
+    dt = time.perf_counter() - t0
+    cells = 2.0 * w.nr * sh["nz"] * nt_sample
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return cells / dt / 1e9, dt, threads
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, sec, threads = oracle_sample(w, REF_SAMPLE_STEPS)
+        if k >= args.warmup:
+            vals.append((v, sec))
+    value = statistics.mean(v for v, _ in vals)
+    sample = (f"first shot of {w.name}, nt truncated to {REF_SAMPLE_STEPS} of {w.nt} steps "
+              f"(forward + adjoint + gradient); forward loops OpenMP, adjoint serial")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(s for _, s in vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, REF_SAMPLE_STEPS),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args, w):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_00281_gb300.build import build_library
+    from paper_2005_00281_gb300.bh import model_from_workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    build_library()
+
+    if world > 1 and rank > 0:
+        # every rank inverts its own independent shot: same sizes, other seed
+        from synthetic import PRESETS
+        w = PRESETS[args.config](seed=rank)
+
+    stream = torch.cuda.current_stream(dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    # observed data: forward modelling in the true model (outside the timing)
+    true = model_from_workload(w, device=dev)
+    true.set_model(t(w.vp_true), t(w.vs_true), t(w.rho_true))
+    wav = t(w.wavelet)
+    obs = true.forward(wav).clone()
+    torch.cuda.synchronize()
+    true.close()
+    del true
+
+    m = model_from_workload(w, device=dev)
+    start_model = (t(w.vp), t(w.vs), t(w.rho))
+    seis = m.empty_seis()
+    resid = torch.empty_like(seis)
+    shape = (w.nr, w.nz)
+    g = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(3)]
+    vp_out = torch.empty(shape, dtype=torch.float32, device=dev)
+    vs_out = torch.empty_like(vp_out)
+    lib = m.lib
+    import ctypes
+    P = lambda x: ctypes.c_void_p(x.data_ptr())
+    Jc = ctypes.c_double()
+    alpha = (ctypes.c_double * 2)()
+
+    def step(wav_d, obs_d):
+        """One inversion iteration through the C ABI."""
+        m._rc(lib.bh_forward(m.h, P(wav_d), P(seis)))
+        m._rc(lib.bh_residual_misfit(m.h, P(seis), P(obs_d), P(resid), ctypes.byref(Jc)))
+        m._rc(lib.bh_adjoint_gradient(m.h, P(resid), P(g[0]), P(g[1]), P(g[2])))
+        m._rc(lib.bh_precondition(m.h, P(g[0]), P(g[1]), ctypes.c_double(1e-3)))
+        m._rc(lib.bh_update(m.h, P(g[0]), P(g[1]), ctypes.c_double(0.02), None, P(vp_out),
+                            P(vs_out)))
+        return Jc.value
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        tt = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    # ---- device-resident inputs
+    for _ in range(args.warmup):
+        step(wav, obs)
+    m.set_model(*start_model)
+    torch.cuda.synchronize()
+    m.profile(PROFILE_EVERY)
+    m.profile_reset()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Js = []
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            Js.append(step(wav, obs))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    prof = m.profile_read()
+    m.profile(0)
+
+    # ---- end to end: host inputs copied in, result copied out, every step
+    wav_h = torch.from_numpy(w.wavelet).pin_memory()
+    obs_h = obs.cpu().pin_memory()
+    vp_h = torch.empty(shape, dtype=torch.float32).pin_memory()
+    vs_h = torch.empty_like(vp_h)
+    wav_d = torch.empty_like(wav)
+    obs_d = torch.empty_like(obs)
+    m.set_model(*start_model)
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        wav_d.copy_(wav_h, non_blocking=True)
+        obs_d.copy_(obs_h, non_blocking=True)
+        step(wav_d, obs_d)
+        vp_h.copy_(vp_out, non_blocking=True)
+        vs_h.copy_(vs_out, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1))
+    h2d = wav_h.numel() * 4 + obs_h.numel() * 4
+    d2h = 8 + vp_h.numel() * 4 * 2
+
+    cells_per_step = 2.0 * w.cell_steps()          # forward + adjoint cell updates
+    value = world * cells_per_step * args.steps / (ms / 1e3) / 1e9
+    grads_per_s = world * w.nshots * args.steps / (ms / 1e3)
+    value_e2e = world * cells_per_step * args.steps / (ms_e2e / 1e3) / 1e9
+
+    # ---- roofline of the dominant kernel (largest sampled time)
+    peak, peak_kind = measured_peaks()
+    s = w.npml_r / w.nr + 2.0 * w.npml_z / w.nz
+    dom = max(prof, key=lambda k: prof[k][0])
+    tot_ms, nlaunch = prof[dom]
+    cells_per_launch = w.nr * w.nz
+    alg_bytes = kernel_bytes_per_cell(dom, s) * cells_per_launch
+    achieved = alg_bytes / (tot_ms / nlaunch / 1e3) / 1e9 if nlaunch else None
+    kernels = {k: {"avg_us": 1e3 * v[0] / v[1] if v[1] else None, "sampled_launches": v[1],
+                   "alg_bytes_per_launch": kernel_bytes_per_cell(k, s) * cells_per_launch,
+                   "alg_GBps": (kernel_bytes_per_cell(k, s) * cells_per_launch /
+                                (v[0] / v[1] / 1e3) / 1e9) if v[1] else None}
+               for k, v in prof.items()}
+    step_bytes = sum(kernel_bytes_per_cell(k, s) for k in prof) * cells_per_launch * w.nt
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                "traffic": ncu_traffic(dom, w.name), "peak_source": f"{peak_kind} (hbm_gbs)",
+                "note": "state of one 240 x 1600 window (~9 MB) stays in the 129 MB L2; "
+                        "algorithmic bytes count every array once per launch"}
+    launches_per_step = w.nshots * (4 * w.nt + 2) + 1 + 2 + 4
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(w),
+            "gradient_evals_per_s": grads_per_s,
+            "step_alg_GBps": world * step_bytes * args.steps / (ms / 1e3) / 1e9,
+            "roofline": roofline, "kernels": kernels,
+            "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / args.steps},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(), "J_first_last": [Js[0], Js[-1]],
+            "source_sha": source_sha()}
+    if rank == 0 and not args.no_cpu_baseline:
+        v, sec, threads = oracle_sample(w, CPU_SAMPLE_STEPS)
+        line["cpu_baseline"] = {
+            "value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first shot of {w.name}, nt truncated to {CPU_SAMPLE_STEPS} of {w.nt} "
+                      f"steps (forward + adjoint + gradient, {sec:.1f} s); forward loops "
+                      f"OpenMP on {threads} threads, adjoint serial"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", default="c1", choices=["c0", "c1"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    from synthetic import PRESETS
+    w = PRESETS[args.config](seed=0)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

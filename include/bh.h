@@ -1,0 +1,221 @@
+/*
+ * bh.h - C ABI of libbh, the GB300 (sm_103a) hot path of borehole acoustic
+ * full-waveform inversion (Tang, Cheng, Li, Fang, "Borehole acoustic
+ * full-waveform inversion").
+ *
+ * The calls follow the five steps of one inversion iteration (Method
+ * section, Fig. 1): forward modelling, data residual, adjoint modelling,
+ * gradient, model update.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Grid.  Cell (i, j), 0 <= i < nr, 0 <= j < nz, sits at r = (i + 1/2) dr,
+ *   z = j dz and carries the normal stresses and lambda, mu, rho.  v_r sits
+ *   at (i dr, j dz), v_z at ((i + 1/2) dr, (j + 1/2) dz), tau_rz at
+ *   (i dr, (j + 1/2) dz).  v_r and tau_rz vanish on the axis (i = 0).
+ *   Space is 4th order (staggered), time 2nd order (leapfrog).  A C-PML
+ *   absorbs at the outer radial edge and at the top and bottom of every
+ *   shot window; the axis is a symmetry line.
+ * - Model arrays are row-major [nr][nz_global] float32, z contiguous.
+ * - Every pointer argument is owned by the caller.  Pointers are DEVICE
+ *   pointers unless a comment says "host".  libbh owns everything it
+ *   allocates (wavefields, C-PML memories, forward history, accumulators)
+ *   and frees it in bh_model_destroy.
+ * - All device work is enqueued on the CUDA stream given to
+ *   bh_model_create, in call order.  A call returns once its work is
+ *   enqueued, except where it writes a host scalar (J, alpha): those calls
+ *   synchronise the stream before returning.
+ * - Every call returns a bh_status; nothing aborts or exits.  On error the
+ *   model keeps its previous state where possible and bh_last_error()
+ *   describes the failure.
+ * - One model must not be used from two host threads at once.
+ */
+#ifndef BH_H
+#define BH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BH_OK = 0,
+    BH_ERR_INVALID_ARG = 1, /* NULL pointer, bad size, index out of range   */
+    BH_ERR_CFL = 2,         /* dt violates the 4th-order staggered limit    */
+    BH_ERR_OOM = 3,         /* device allocation failed or exceeds the cap  */
+    BH_ERR_CUDA = 4,        /* a CUDA runtime call failed                   */
+    BH_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired           */
+    BH_ERR_STATE = 6,       /* calls made in the wrong order                */
+    BH_ERR_UNSUPPORTED = 7  /* option not available in this build           */
+} bh_status;
+
+typedef struct bh_model bh_model; /* opaque, owned by libbh */
+
+typedef struct {
+    int nr;              /* radial cells, outer C-PML included                 */
+    int nz;              /* axial cells of the global model (== nz_global)     */
+    int nt;              /* time steps per shot                                */
+    int npml_r;          /* C-PML cells at the outer radial edge               */
+    int npml_z;          /* C-PML cells at the top and at the bottom of a window */
+    double dr, dz, dt;   /* m, m, s                                            */
+    double f0;           /* Hz; sets the C-PML frequency shift pi f0           */
+    double pml_R;        /* target C-PML reflection; <= 0 means 1e-3           */
+    int snapshot_precision;      /* forward history: 0 fp32 (1 bf16, 2 fp16: reserved) */
+    size_t checkpoint_cap_bytes; /* 0: store every step's v_r, v_z; else cap   */
+} bh_grid_desc;
+
+typedef struct {
+    int z_offset;        /* first global row of the shot's window              */
+    int nz;              /* window length in cells (its own top/bottom C-PML)  */
+    int src_ir, src_iz;  /* source cell, window coordinates                    */
+    int nrec;            /* receivers of this shot                             */
+    const int* rec_iz;   /* host [nrec]: receiver cells (i = 0, on the axis)   */
+} bh_shot_desc;
+
+/*
+ * Build a model: Lame parameters from velocities (Eq. 3, Eq. 4), buoyancy
+ * at the velocity nodes, harmonic-mean mu at the shear-stress nodes,
+ * C-PML profiles, shot descriptors, and the forward-history store.
+ *   grid      host; grid->nz must equal nz_global
+ *   vp, vs, rho  device [nr][nz_global] float32 (vs = 0 marks fluid)
+ *   shots     host [nshots]; every window must lie inside the model, every
+ *             source and receiver inside the window's interior
+ *   stream    cudaStream_t (NULL = legacy default stream)
+ *   out       host; receives the new model
+ * Errors: BH_ERR_INVALID_ARG (bad sizes or indices), BH_ERR_CFL when
+ *   dt Vmax sqrt(1/dr^2 + 1/dz^2) (9/8 + 1/24) >= 1, BH_ERR_OOM, BH_ERR_CUDA.
+ * Citation: Method section, Eq. 2-4; C-PML and axis conditions as cited
+ *   there (finite differences, PML on top, bottom and radial boundaries).
+ */
+bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* vp,
+                          const float* vs, const float* rho, const bh_shot_desc* shots,
+                          int nshots, void* stream, bh_model** out);
+
+/* Free every device buffer of the model.  NULL is accepted. */
+void bh_model_destroy(bh_model* model);
+
+/*
+ * Replace the model (velocities and density) without rebuilding the shot
+ * plan; invalidates any stored forward history.
+ *   vp, vs, rho  device [nr][nz_global] float32
+ * Errors: BH_ERR_INVALID_ARG, BH_ERR_CFL.
+ */
+bh_status bh_set_model(bh_model* model, const float* vp, const float* vs, const float* rho);
+
+/*
+ * Forward modelling (Eq. 2) of every shot: leapfrog steps of the velocity
+ * and stress equations; the source rate wavelet[n] (sampled at
+ * t = (n + 1/2) dt) is injected as dt * wavelet[n] / V into the three
+ * normal stresses of the source cell (V the cell volume); the pressure is
+ * recorded as the mean normal stress at the receivers ("normal stress ...
+ * at the receiver positions", Method section).  Keeps the forward history
+ * needed by bh_adjoint_gradient.
+ *   wavelet  device [nt] float32
+ *   seis     device [nshots][nrec_max][nt] float32, row n = after step n;
+ *            entries of receivers a shot does not have are set to 0
+ * Errors: BH_ERR_INVALID_ARG, BH_ERR_CUDA.
+ */
+bh_status bh_forward(bh_model* model, const float* wavelet, float* seis);
+
+/*
+ * Data residual Delta p = p_mod - p_mes (Eq. 5) and misfit
+ * J = 1/2 ||Delta p||^2 (Eq. 1), summed in FP64 in a fixed order.
+ *   seis_mod, seis_obs  device [nshots][nrec_max][nt] float32
+ *   resid    device, same shape, float32 (may alias seis_mod)
+ *   J        host double; the call synchronises the stream
+ * Errors: BH_ERR_INVALID_ARG, BH_ERR_CUDA.
+ */
+bh_status bh_residual_misfit(bh_model* model, const float* seis_mod, const float* seis_obs,
+                             float* resid, double* J);
+
+/*
+ * Adjoint modelling driven by the residual (Eq. 6, as the exact transpose
+ * of the discrete forward step) and the zero-lag correlations of Eq. 7
+ * (lambda) and Eq. 8 (mu), plus the density term through the buoyancy.
+ * The gradients of every shot are added, in FP64, into the global model
+ * arrays; cells inside the C-PML (radial, and the top/bottom layers of
+ * every window that covers them) receive nothing.  Also accumulates the
+ * diagonal pseudo-Hessian used by bh_precondition.
+ *   resid    device [nshots][nrec_max][nt] float32 (the adjoint source)
+ *   g_lam, g_mu  device [nr][nz_global] double, OVERWRITTEN
+ *   g_rho    device [nr][nz_global] double or NULL
+ * Errors: BH_ERR_STATE without a preceding bh_forward on the same model,
+ *   BH_ERR_INVALID_ARG, BH_ERR_CUDA.
+ */
+bh_status bh_adjoint_gradient(bh_model* model, const float* resid, double* g_lam,
+                              double* g_mu, double* g_rho);
+
+/*
+ * Copy the pseudo-Hessian diagonals accumulated by the last
+ * bh_adjoint_gradient:  H_lam = sum dt (div v)^2,
+ * H_mu = sum dt [ (2 e_rr)^2 + (2 e_tt)^2 + (2 e_zz)^2 ] plus a quarter of
+ * sum dt (dv_r/dz + dv_z/dr)^2 from each of the cell's four shear nodes.
+ *   H_lam, H_mu  device [nr][nz_global] double
+ * Errors: BH_ERR_STATE, BH_ERR_INVALID_ARG.
+ */
+bh_status bh_get_hessian(bh_model* model, double* H_lam, double* H_mu);
+
+/*
+ * Diagonal preconditioner (Numerical Examples, Fig. 6: weights the
+ * gradient to suppress the borehole guided-wave imprint near the wall; the
+ * paper prints no formula): g <- g / (H + eps_rel * max H), with H the
+ * pseudo-Hessian of the same parameter and max over the inversion mask;
+ * g <- 0 outside the mask (fluid cells and C-PML cells).
+ *   g_lam, g_mu  device [nr][nz_global] double, in place
+ * Errors: BH_ERR_STATE without a preceding bh_adjoint_gradient,
+ *   BH_ERR_INVALID_ARG (eps_rel < 0), BH_ERR_CUDA.
+ */
+bh_status bh_precondition(bh_model* model, double* g_lam, double* g_mu, double eps_rel);
+
+/*
+ * Gradient-descent update (Eq. 9, Eq. 10) with alpha chosen per parameter
+ * so that no cell changes by more than kappa times the largest modulus
+ * ("alpha ... controlling the greatest change", Method section):
+ * alpha_m = kappa max|m| / max|g_m| over the inversion mask; then mu >= 0,
+ * lambda + 2 mu >= rho (1 m/s)^2, and Vp, Vs from Eq. 11, Eq. 12.  The
+ * model's own coefficients are rebuilt; any stored history is invalidated.
+ *   g_lam, g_mu  device [nr][nz_global] double
+ *   alpha_out    host double[2] (alpha_lambda, alpha_mu) or NULL; when
+ *                given, the call synchronises the stream
+ *   vp_out, vs_out  device [nr][nz_global] float32 or NULL
+ * Errors: BH_ERR_INVALID_ARG (kappa < 0), BH_ERR_CUDA.
+ */
+bh_status bh_update(bh_model* model, const double* g_lam, const double* g_mu, double kappa,
+                    double* alpha_out, float* vp_out, float* vs_out);
+
+/* Current model velocities (Eq. 11, Eq. 12).  vp, vs: device [nr][nz_global]. */
+bh_status bh_get_model(bh_model* model, float* vp, float* vs);
+
+/*
+ * Sampled kernel timing (tracing aid; the paper has no counterpart).  With
+ * every > 0, CUDA events bracket the launches of every every-th time step
+ * of the stepping kernels on the model's stream; every = 0 turns it off.
+ * bh_profile_read synchronises the stream and returns, for one kernel, the
+ * summed event time in ms and the number of sampled launches since the last
+ * bh_profile_reset.  Kernel ids: BH_KERNEL_*.
+ * Errors: BH_ERR_INVALID_ARG, BH_ERR_CUDA.
+ */
+enum {
+    BH_KERNEL_FWD_VEL = 0,     /* velocity half-step, Eq. 2 lines 1-2          */
+    BH_KERNEL_FWD_STRESS = 1,  /* stress half-step, Eq. 2 lines 3-6            */
+    BH_KERNEL_ADJ_STRESS = 2,  /* transposed stress step + Eq. 7 / Eq. 8        */
+    BH_KERNEL_ADJ_VEL = 3,     /* transposed velocity step                     */
+    BH_KERNEL_COUNT = 4
+};
+bh_status bh_profile_enable(bh_model* model, int every);
+bh_status bh_profile_read(bh_model* model, int kernel, double* total_ms, long* launches);
+bh_status bh_profile_reset(bh_model* model);
+
+/* Static description of a status code. */
+const char* bh_status_string(bh_status status);
+
+/* Text of the last error on this model ("" if none); NULL model: the last
+ * error of bh_model_create on this thread. */
+const char* bh_last_error(const bh_model* model);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BH_H */

@@ -1,0 +1,261 @@
+"""Thin ctypes binding of libbh (include/bh.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+Tensors are PyTorch CUDA tensors (device memory and streams); the library
+enqueues on the stream that was current when the model was created.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+from .build import LIB
+
+BH_OK = 0
+STATUS_NAMES = {0: "BH_OK", 1: "BH_ERR_INVALID_ARG", 2: "BH_ERR_CFL", 3: "BH_ERR_OOM",
+                4: "BH_ERR_CUDA", 5: "BH_ERR_TIMEOUT", 6: "BH_ERR_STATE",
+                7: "BH_ERR_UNSUPPORTED"}
+
+# every entry point declared in include/bh.h
+EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
+           "bh_residual_misfit", "bh_adjoint_gradient", "bh_get_hessian", "bh_precondition",
+           "bh_update", "bh_get_model", "bh_status_string", "bh_last_error",
+           "bh_profile_enable", "bh_profile_read", "bh_profile_reset")
+KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel")
+
+
+class BhError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("nr", ctypes.c_int), ("nz", ctypes.c_int), ("nt", ctypes.c_int),
+        ("npml_r", ctypes.c_int), ("npml_z", ctypes.c_int),
+        ("dr", ctypes.c_double), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
+        ("f0", ctypes.c_double), ("pml_R", ctypes.c_double),
+        ("snapshot_precision", ctypes.c_int), ("checkpoint_cap_bytes", ctypes.c_size_t),
+    ]
+
+
+class ShotDesc(ctypes.Structure):
+    _fields_ = [
+        ("z_offset", ctypes.c_int), ("nz", ctypes.c_int),
+        ("src_ir", ctypes.c_int), ("src_iz", ctypes.c_int),
+        ("nrec", ctypes.c_int), ("rec_iz", ctypes.POINTER(ctypes.c_int)),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libbh.so; raises if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbh.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    st = ctypes.c_int
+    lib.bh_model_create.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int, vp, vp, vp,
+                                    ctypes.POINTER(ShotDesc), ctypes.c_int, vp,
+                                    ctypes.POINTER(vp)]
+    lib.bh_model_create.restype = st
+    lib.bh_model_destroy.argtypes = [vp]
+    lib.bh_model_destroy.restype = None
+    lib.bh_set_model.argtypes = [vp, vp, vp, vp]
+    lib.bh_set_model.restype = st
+    lib.bh_forward.argtypes = [vp, vp, vp]
+    lib.bh_forward.restype = st
+    lib.bh_residual_misfit.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.bh_residual_misfit.restype = st
+    lib.bh_adjoint_gradient.argtypes = [vp, vp, vp, vp, vp]
+    lib.bh_adjoint_gradient.restype = st
+    lib.bh_get_hessian.argtypes = [vp, vp, vp]
+    lib.bh_get_hessian.restype = st
+    lib.bh_precondition.argtypes = [vp, vp, vp, ctypes.c_double]
+    lib.bh_precondition.restype = st
+    lib.bh_update.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                              vp, vp]
+    lib.bh_update.restype = st
+    lib.bh_get_model.argtypes = [vp, vp, vp]
+    lib.bh_get_model.restype = st
+    lib.bh_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.bh_profile_enable.restype = st
+    lib.bh_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_long)]
+    lib.bh_profile_read.restype = st
+    lib.bh_profile_reset.argtypes = [vp]
+    lib.bh_profile_reset.restype = st
+    lib.bh_status_string.argtypes = [st]
+    lib.bh_status_string.restype = ctypes.c_char_p
+    lib.bh_last_error.argtypes = [vp]
+    lib.bh_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libbh takes CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(x, dtype, shape, name):
+    if x.dtype != dtype or tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected {dtype} {tuple(shape)}, got {x.dtype} {tuple(x.shape)}")
+
+
+@dataclass
+class Shot:
+    z_offset: int
+    nz: int
+    src: tuple
+    rec_iz: list = field(default_factory=list)
+
+
+class Model:
+    """A libbh model: grid, shots, model parameters and the working state."""
+
+    def __init__(self, nr, nz, nt, npml_r, npml_z, dr, dz, dt, f0, vp, vs, rho, shots,
+                 pml_R=1e-3, stream=None, checkpoint_cap_bytes=0, snapshot_precision=0):
+        self.lib = load_library()
+        self.nr, self.nz, self.nt = nr, nz, nt
+        self.shots = [s if isinstance(s, Shot) else Shot(s["z_offset"], s["nz"], tuple(s["src"]),
+                                                         list(s["rec_iz"])) for s in shots]
+        self.nshots = len(self.shots)
+        self.nrec_max = max(len(s.rec_iz) for s in self.shots)
+        self.device = vp.device
+        for name, t in (("vp", vp), ("vs", vs), ("rho", rho)):
+            _check(t, torch.float32, (nr, nz), name)
+        g = GridDesc(nr, nz, nt, npml_r, npml_z, dr, dz, dt, f0, pml_R, snapshot_precision,
+                     checkpoint_cap_bytes)
+        self._rec = [(ctypes.c_int * max(1, len(s.rec_iz)))(*s.rec_iz) for s in self.shots]
+        arr = (ShotDesc * self.nshots)()
+        for k, s in enumerate(self.shots):
+            arr[k] = ShotDesc(s.z_offset, s.nz, s.src[0], s.src[1], len(s.rec_iz),
+                              ctypes.cast(self._rec[k], ctypes.POINTER(ctypes.c_int)))
+        self.stream = stream if stream is not None else torch.cuda.current_stream(vp.device)
+        h = ctypes.c_void_p()
+        rc = self.lib.bh_model_create(ctypes.byref(g), nz, _ptr(vp), _ptr(vs), _ptr(rho), arr,
+                                      self.nshots, ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.byref(h))
+        if rc != BH_OK:
+            raise BhError(rc, self.lib.bh_last_error(None).decode())
+        self.h = h
+
+    # -- helpers
+    def _rc(self, rc):
+        if rc != BH_OK:
+            raise BhError(rc, self.lib.bh_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bh_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def seis_shape(self):
+        return (self.nshots, self.nrec_max, self.nt)
+
+    def empty_seis(self):
+        return torch.empty(self.seis_shape(), dtype=torch.float32, device=self.device)
+
+    # -- the C ABI, one method per entry point
+    def set_model(self, vp, vs, rho):
+        for name, t in (("vp", vp), ("vs", vs), ("rho", rho)):
+            _check(t, torch.float32, (self.nr, self.nz), name)
+        self._rc(self.lib.bh_set_model(self.h, _ptr(vp), _ptr(vs), _ptr(rho)))
+
+    def forward(self, wavelet, seis=None):
+        _check(wavelet, torch.float32, (self.nt,), "wavelet")
+        seis = self.empty_seis() if seis is None else seis
+        _check(seis, torch.float32, self.seis_shape(), "seis")
+        self._rc(self.lib.bh_forward(self.h, _ptr(wavelet), _ptr(seis)))
+        return seis
+
+    def residual_misfit(self, seis_mod, seis_obs, resid=None):
+        resid = torch.empty_like(seis_mod) if resid is None else resid
+        for name, t in (("seis_mod", seis_mod), ("seis_obs", seis_obs), ("resid", resid)):
+            _check(t, torch.float32, self.seis_shape(), name)
+        J = ctypes.c_double()
+        self._rc(self.lib.bh_residual_misfit(self.h, _ptr(seis_mod), _ptr(seis_obs), _ptr(resid),
+                                             ctypes.byref(J)))
+        return resid, J.value
+
+    def adjoint_gradient(self, resid, with_rho=True, out=None):
+        _check(resid, torch.float32, self.seis_shape(), "resid")
+        shape = (self.nr, self.nz)
+        if out is None:
+            out = [torch.empty(shape, dtype=torch.float64, device=self.device)
+                   for _ in range(3 if with_rho else 2)]
+        g_rho = out[2] if with_rho else None
+        self._rc(self.lib.bh_adjoint_gradient(self.h, _ptr(resid), _ptr(out[0]), _ptr(out[1]),
+                                              _ptr(g_rho)))
+        return tuple(out) if with_rho else (out[0], out[1], None)
+
+    def hessian(self):
+        H = [torch.empty((self.nr, self.nz), dtype=torch.float64, device=self.device)
+             for _ in range(2)]
+        self._rc(self.lib.bh_get_hessian(self.h, _ptr(H[0]), _ptr(H[1])))
+        return H[0], H[1]
+
+    def precondition(self, g_lam, g_mu, eps_rel=1e-3):
+        self._rc(self.lib.bh_precondition(self.h, _ptr(g_lam), _ptr(g_mu), float(eps_rel)))
+        return g_lam, g_mu
+
+    def update(self, g_lam, g_mu, kappa=0.02, want_velocities=True):
+        alpha = (ctypes.c_double * 2)()
+        vp = vs = None
+        if want_velocities:
+            vp = torch.empty((self.nr, self.nz), dtype=torch.float32, device=self.device)
+            vs = torch.empty_like(vp)
+        self._rc(self.lib.bh_update(self.h, _ptr(g_lam), _ptr(g_mu), float(kappa), alpha,
+                                    _ptr(vp), _ptr(vs)))
+        return (alpha[0], alpha[1]), vp, vs
+
+    def profile(self, every):
+        """Sample kernel timing on every every-th step (0 = off)."""
+        self._rc(self.lib.bh_profile_enable(self.h, int(every)))
+
+    def profile_read(self):
+        """{kernel name: (total ms, sampled launches)} since the last reset."""
+        out = {}
+        for k, name in enumerate(KERNELS):
+            t, n = ctypes.c_double(), ctypes.c_long()
+            self._rc(self.lib.bh_profile_read(self.h, k, ctypes.byref(t), ctypes.byref(n)))
+            out[name] = (t.value, n.value)
+        return out
+
+    def profile_reset(self):
+        self._rc(self.lib.bh_profile_reset(self.h))
+
+    def velocities(self):
+        vp = torch.empty((self.nr, self.nz), dtype=torch.float32, device=self.device)
+        vs = torch.empty_like(vp)
+        self._rc(self.lib.bh_get_model(self.h, _ptr(vp), _ptr(vs)))
+        return vp, vs
+
+
+def model_from_workload(w, device="cuda", **kw):
+    """Build a Model from a synthetic.Workload (start model)."""
+    t = lambda a: torch.from_numpy(a).to(device)
+    return Model(w.nr, w.nz, w.nt, w.npml_r, w.npml_z, w.dr, w.dz, w.dt, w.f0, t(w.vp), t(w.vs),
+                 t(w.rho), w.shots, pml_R=w.pml_R, **kw)

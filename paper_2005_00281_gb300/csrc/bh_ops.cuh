@@ -1,0 +1,200 @@
+// Small kernels of libbh: model setup (Eq. 3, Eq. 4 and the material
+// averages), misfit (Eq. 1, Eq. 5), diagonal preconditioner, and the
+// gradient-descent update (Eq. 9-12).  Reductions run in one block with a
+// fixed traversal order so that their results do not depend on scheduling.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bh {
+
+constexpr int kRedThreads = 1024;
+
+// lambda, mu (Eq. 3, Eq. 4) and rho per cell, plus the fluid flag source
+__global__ void k_setup_cells(int n, const float* __restrict__ vp, const float* __restrict__ vs,
+                              const float* __restrict__ rho, float* lam, float* mu,
+                              float* rho_out)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float r = rho[k], a = vp[k], b = vs[k];
+    rho_out[k] = r;
+    mu[k] = r * b * b;
+    lam[k] = r * a * a - 2.f * r * b * b;
+}
+
+// buoyancy at v_r / v_z nodes and harmonic mu at trz nodes of the global
+// model; at the global axial edge the last node row sees its own cells only
+__global__ void k_setup_nodes(int nr, int nzg, const float* __restrict__ mu,
+                              const float* __restrict__ rho, float* bvr, float* bvz, float* muh)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nr || j >= nzg) return;
+    size_t c = (size_t)i * nzg + j;
+    int jp = (j + 1 < nzg) ? j + 1 : nzg - 1;
+    size_t cp = (size_t)i * nzg + jp;
+    bvz[c] = 0.5f * (1.f / rho[c] + 1.f / rho[cp]);
+    if (i >= 1) {
+        bvr[c] = 0.5f * (1.f / rho[c - nzg] + 1.f / rho[c]);
+        float q0 = mu[c - nzg], q1 = mu[c], q2 = mu[cp - nzg], q3 = mu[cp];
+        if (q0 <= 0.f || q1 <= 0.f || q2 <= 0.f || q3 <= 0.f) muh[c] = 0.f;
+        else muh[c] = 4.f / (1.f / q0 + 1.f / q1 + 1.f / q2 + 1.f / q3);
+    } else {
+        bvr[c] = 0.f;
+        muh[c] = 0.f;
+    }
+}
+
+// inversion mask: formation cell (vs > 0), outside the radial C-PML, and
+// inside the axial interior of at least one shot window (colcov[j] != 0)
+__global__ void k_setup_mask(int nr, int nzg, int npml_r, const float* __restrict__ vs,
+                             const uint8_t* __restrict__ colcov, uint8_t* mask)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nr || j >= nzg) return;
+    size_t c = (size_t)i * nzg + j;
+    mask[c] = (vs[c] > 0.f && i < nr - npml_r && colcov[j]) ? 1 : 0;
+}
+
+__device__ __forceinline__ void block_reduce_max(double* sh, double v)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+}
+
+// max over all entries of a float array (for the CFL check and C-PML d0)
+__global__ void __launch_bounds__(kRedThreads) k_max_f32(size_t n, const float* __restrict__ a,
+                                                         double* out)
+{
+    __shared__ double sh[kRedThreads];
+    double m = -1e300;
+    for (size_t k = threadIdx.x; k < n; k += blockDim.x) m = fmax(m, (double)a[k]);
+    block_reduce_max(sh, m);
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// Eq. 5 residual and Eq. 1 misfit, J summed in FP64 in a fixed order:
+// thread t adds elements t, t + T, t + 2T, ... then a fixed binary tree.
+__global__ void __launch_bounds__(kRedThreads) k_misfit(size_t n, const float* __restrict__ mod,
+                                                        const float* __restrict__ obs,
+                                                        float* resid, double* J)
+{
+    __shared__ double sh[kRedThreads];
+    double s = 0.0;
+    for (size_t k = threadIdx.x; k < n; k += blockDim.x) {
+        float d = mod[k] - obs[k];
+        resid[k] = d;
+        s += (double)d * (double)d;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *J = 0.5 * sh[0];
+}
+
+// masked maxima: out[0] = max H_lam, out[1] = max H_mu
+__global__ void __launch_bounds__(kRedThreads) k_masked_max2(size_t n, const uint8_t* __restrict__ mask,
+                                                             const double* __restrict__ a,
+                                                             const double* __restrict__ b,
+                                                             double* out)
+{
+    __shared__ double sh[kRedThreads];
+    double ma = 0.0, mb = 0.0;
+    for (size_t k = threadIdx.x; k < n; k += blockDim.x)
+        if (mask[k]) {
+            ma = fmax(ma, fabs(a[k]));
+            mb = fmax(mb, fabs(b[k]));
+        }
+    block_reduce_max(sh, ma);
+    if (threadIdx.x == 0) out[0] = sh[0];
+    __syncthreads();
+    block_reduce_max(sh, mb);
+    if (threadIdx.x == 0) out[1] = sh[0];
+}
+
+// g <- g / (H + eps max H) inside the mask, 0 outside
+__global__ void k_precondition(size_t n, const uint8_t* __restrict__ mask,
+                               const double* __restrict__ H_lam, const double* __restrict__ H_mu,
+                               const double* __restrict__ hmax, double eps, double* g_lam,
+                               double* g_mu)
+{
+    size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (!mask[k]) {
+        g_lam[k] = 0.0;
+        g_mu[k] = 0.0;
+        return;
+    }
+    double dl = H_lam[k] + eps * hmax[0];
+    double dm = H_mu[k] + eps * hmax[1];
+    g_lam[k] = dl > 0.0 ? g_lam[k] / dl : 0.0;
+    g_mu[k] = dm > 0.0 ? g_mu[k] / dm : 0.0;
+}
+
+// step lengths: alpha_m = kappa max|m| / max|g_m| over the mask
+__global__ void __launch_bounds__(kRedThreads) k_update_alpha(size_t n, const uint8_t* __restrict__ mask,
+                                                              const float* __restrict__ lam,
+                                                              const float* __restrict__ mu,
+                                                              const double* __restrict__ g_lam,
+                                                              const double* __restrict__ g_mu,
+                                                              double kappa, double* alpha)
+{
+    __shared__ double sh[kRedThreads];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (size_t k = threadIdx.x; k < n; k += blockDim.x)
+        if (mask[k]) {
+            v[0] = fmax(v[0], fabs((double)lam[k]));
+            v[1] = fmax(v[1], fabs((double)mu[k]));
+            v[2] = fmax(v[2], fabs(g_lam[k]));
+            v[3] = fmax(v[3], fabs(g_mu[k]));
+        }
+    double r[4];
+    for (int q = 0; q < 4; ++q) {
+        block_reduce_max(sh, v[q]);
+        r[q] = sh[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        alpha[0] = r[2] > 0.0 ? kappa * r[0] / r[2] : 0.0;
+        alpha[1] = r[3] > 0.0 ? kappa * r[1] / r[3] : 0.0;
+    }
+}
+
+// Eq. 9, Eq. 10 inside the mask, then mu >= 0, lambda + 2 mu >= rho (1 m/s)^2
+__global__ void k_update_apply(size_t n, const uint8_t* __restrict__ mask,
+                               const double* __restrict__ g_lam, const double* __restrict__ g_mu,
+                               const double* __restrict__ alpha, const float* __restrict__ rho,
+                               float* lam, float* mu)
+{
+    size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || !mask[k]) return;
+    double l = (double)lam[k] - alpha[0] * g_lam[k];
+    double m = (double)mu[k] - alpha[1] * g_mu[k];
+    if (m < 0.0) m = 0.0;
+    double floor = (double)rho[k] - 2.0 * m;
+    if (l < floor) l = floor;
+    lam[k] = (float)l;
+    mu[k] = (float)m;
+}
+
+// Eq. 11, Eq. 12
+__global__ void k_velocities(size_t n, const float* __restrict__ lam, const float* __restrict__ mu,
+                             const float* __restrict__ rho, float* vp, float* vs)
+{
+    size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double l = lam[k], m = mu[k], r = rho[k];
+    if (vp) vp[k] = (float)sqrt((l + 2.0 * m) / r);
+    if (vs) vs[k] = (float)sqrt(m / r);
+}
+
+}  // namespace bh

@@ -1,0 +1,61 @@
+"""Shared helpers of the GPU tests: run the CUDA path through the C ABI and
+the oracle on the same seeded inputs, and compare."""
+import numpy as np
+import torch
+
+from oracle import oracle as O
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a))
+
+
+def oracle_grid(w):
+    return O.Grid(w.nr, w.nz, w.nt, w.npml_r, w.npml_z, w.dr, w.dz, w.dt, w.f0, w.pml_R)
+
+
+def oracle_observed(w):
+    """'Measured' data: oracle forward modelling in the true model."""
+    obs = []
+    vpmax = float(w.vp.max())
+    for sh in w.shots:
+        z0, nzs = sh["z_offset"], sh["nz"]
+        sl = np.s_[:, z0: z0 + nzs]
+        g = O.Grid(w.nr, nzs, w.nt, w.npml_r, w.npml_z, w.dr, w.dz, w.dt, w.f0, w.pml_R)
+        s, _ = O.forward(g, *(np.ascontiguousarray(a[sl]) for a in (w.vp_true, w.vs_true,
+                                                                      w.rho_true)),
+                         w.wavelet, sh["src"], sh["rec_iz"], store_v=False, vpmax=vpmax)
+        obs.append(s)
+    nrec = max(len(sh["rec_iz"]) for sh in w.shots)
+    out = np.zeros((len(w.shots), nrec, w.nt))
+    for k, s in enumerate(obs):
+        out[k, : s.shape[0]] = s
+    return out
+
+
+def gpu_gradient(w, obs, device="cuda"):
+    """Forward, residual, adjoint through libbh.  Returns a dict of numpy arrays."""
+    from paper_2005_00281_gb300.bh import model_from_workload
+
+    m = model_from_workload(w, device=device)
+    wav = torch.from_numpy(w.wavelet).to(device)
+    seis = m.forward(wav)
+    obs_t = torch.from_numpy(obs.astype(np.float32)).to(device)
+    resid, J = m.residual_misfit(seis, obs_t)
+    g_lam, g_mu, g_rho = m.adjoint_gradient(resid)
+    H_lam, H_mu = m.hessian()
+    torch.cuda.synchronize()
+    out = dict(seis=seis.cpu().numpy(), resid=resid.cpu().numpy(), J=J, g_lam=g_lam.cpu().numpy(),
+               g_mu=g_mu.cpu().numpy(), g_rho=g_rho.cpu().numpy(), H_lam=H_lam.cpu().numpy(),
+               H_mu=H_mu.cpu().numpy())
+    return m, out
+
+
+def oracle_gradient(w, obs):
+    """The oracle on the same inputs (obs is what the GPU path was given,
+    rounded to float32 like the GPU copy)."""
+    obs32 = obs.astype(np.float32).astype(np.float64)
+    return O.shot_gradient(oracle_grid(w), w.vp, w.vs, w.rho, w.wavelet, w.shots, obs32)

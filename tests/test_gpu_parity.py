@@ -1,0 +1,106 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Tolerances: seismogram relative L2 <= 1e-5, gradient relative L2
+<= 1e-4 (FP32 stepping against FP64)."""
+import numpy as np
+import pytest
+
+from synthetic import config0, tiny_borehole
+from tests.gpu_common import (oracle_gradient, oracle_observed, gpu_gradient, rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+SEIS_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_00281_gb300.bh import load_library
+    load_library()
+    return torch
+
+
+def _compare(gpu, ref, nshots):
+    for s in range(nshots):
+        n = ref["seis"][s].shape[0]
+        assert rel_l2(gpu["seis"][s, :n], ref["seis"][s]) <= SEIS_TOL, s
+    assert abs(gpu["J"] - ref["J"]) <= 1e-5 * ref["J"]
+    for k in ("g_lam", "g_mu", "g_rho"):
+        e = rel_l2(gpu[k], ref[k])
+        assert e <= GRAD_TOL, (k, e)
+    for k in ("H_lam", "H_mu"):
+        e = rel_l2(gpu[k], ref[k])
+        assert e <= GRAD_TOL, (k, e)
+
+
+@pytest.mark.parametrize("seed,nz,nt", [(1, 48, 300), (2, 61, 257)])
+def test_tiny_parity(cuda, orc, seed, nz, nt):
+    """Several tiles and a ragged tail in z (61 is not a multiple of 32)."""
+    w = tiny_borehole(seed=seed, nz=nz, nt=nt)
+    obs = oracle_observed(w)
+    _, gpu = gpu_gradient(w, obs)
+    ref = oracle_gradient(w, obs)
+    _compare(gpu, ref, 1)
+
+
+def test_config0_parity(cuda, orc):
+    """The single-shot correctness workload in full: 80 x 400 cells, 2500 steps."""
+    w = config0()
+    obs = oracle_observed(w)
+    _, gpu = gpu_gradient(w, obs)
+    ref = oracle_gradient(w, obs)
+    _compare(gpu, ref, 1)
+
+
+def test_multishot_windows(cuda, orc):
+    """Three shots with uneven axial windows of one global model; the
+    gradients of all shots are summed into the global arrays."""
+    w = tiny_borehole(seed=3, nz=90, nt=240)
+    shots = []
+    for z0, nzs in ((0, 60), (17, 73), (30, 55)):
+        shots.append(dict(z_offset=z0, nz=nzs, src=(0, 9), rec_iz=[20, 35, nzs - 12]))
+    w.shots = shots
+    obs = oracle_observed(w)
+    _, gpu = gpu_gradient(w, obs)
+    ref = oracle_gradient(w, obs)
+    _compare(gpu, ref, 3)
+
+
+def test_precondition_update_parity(cuda, orc):
+    from oracle import oracle as O
+
+    w = tiny_borehole(seed=4, nt=260)
+    obs = oracle_observed(w)
+    m, gpu = gpu_gradient(w, obs)
+    ref = oracle_gradient(w, obs)
+    torch = cuda
+    mask = O.inversion_mask(w.nr, w.nz, w.npml_r, w.npml_z, w.vs)
+    gl = torch.from_numpy(gpu["g_lam"]).cuda()
+    gm = torch.from_numpy(gpu["g_mu"]).cuda()
+    m.precondition(gl, gm, 1e-3)
+    pl = O.precondition(ref["g_lam"], ref["H_lam"], mask, 1e-3)
+    pm = O.precondition(ref["g_mu"], ref["H_mu"], mask, 1e-3)
+    assert rel_l2(gl.cpu().numpy(), pl) <= GRAD_TOL
+    assert rel_l2(gm.cpu().numpy(), pm) <= GRAD_TOL
+    (al, am), vp, vs = m.update(gl, gm, kappa=0.02)
+    lam, mu = O.lame(w.vp, w.vs, w.rho)
+    lam2, mu2, vp_o, vs_o, (al_o, am_o) = O.update(lam, mu, w.rho, pl, pm, mask, 0.02)
+    assert al == pytest.approx(al_o, rel=1e-3) and am == pytest.approx(am_o, rel=1e-3)
+    np.testing.assert_allclose(vp.cpu().numpy(), vp_o, rtol=1e-5)
+    np.testing.assert_allclose(vs.cpu().numpy(), vs_o, rtol=1e-5, atol=1e-3)
+    # the update changes only formation cells outside the C-PML
+    assert np.all(vs.cpu().numpy()[~mask] == w.vs[~mask])
+
+
+def test_deterministic(cuda):
+    """Two runs of the same inputs give bit-identical results (no atomics)."""
+    w = tiny_borehole(seed=5, nt=200)
+    obs = np.zeros((1, len(w.shots[0]["rec_iz"]), w.nt))
+    _, a = gpu_gradient(w, obs)
+    _, b = gpu_gradient(w, obs)
+    for k in ("seis", "g_lam", "g_mu", "g_rho", "H_lam"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["J"] == b["J"]
