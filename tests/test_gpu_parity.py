@@ -91,8 +91,10 @@ def test_precondition_update_parity(cuda, orc):
     assert al == pytest.approx(al_o, rel=1e-3) and am == pytest.approx(am_o, rel=1e-3)
     np.testing.assert_allclose(vp.cpu().numpy(), vp_o, rtol=1e-5)
     np.testing.assert_allclose(vs.cpu().numpy(), vs_o, rtol=1e-5, atol=1e-3)
-    # the update changes only formation cells outside the C-PML
-    assert np.all(vs.cpu().numpy()[~mask] == w.vs[~mask])
+    # the update changes only formation cells outside the C-PML (there Vs is
+    # rebuilt from the FP32 mu and rho, so it matches the input to rounding)
+    np.testing.assert_allclose(vs.cpu().numpy()[~mask], w.vs[~mask], rtol=2e-7)
+    np.testing.assert_allclose(vp.cpu().numpy()[~mask], w.vp[~mask], rtol=2e-7)
 
 
 def test_deterministic(cuda):
