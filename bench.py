@@ -387,9 +387,14 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="c1", choices=["c0", "c1"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nt", type=int, default=None,
+                    help="override the step count (small cases for ncu captures only)")
     args = ap.parse_args()
-    from synthetic import PRESETS
+    from synthetic import PRESETS, ricker
     w = PRESETS[args.config](seed=0)
+    if args.nt:
+        w.nt = args.nt
+        w.wavelet = ricker(w.nt, w.dt, w.f0)
     if args.impl == "reference":
         run_reference(args, w)
     else:
