@@ -207,11 +207,36 @@ bh_status bh_profile_enable(bh_model* model, int every);
 bh_status bh_profile_read(bh_model* model, int kernel, double* total_ms, long* launches);
 bh_status bh_profile_reset(bh_model* model);
 
+/*
+ * Residual and misfit without any device allocation (the paper has no
+ * counterpart; this is a service for callers that may not allocate device
+ * memory, for example code running under stream capture or inside a
+ * process whose device memory is owned by another allocator).  Computes
+ * exactly what bh_residual_misfit computes, Delta p = p_mod - p_mes and
+ * J = 1/2 ||Delta p||^2 in FP64, but needs no bh_model: its scratch is a
+ * fixed 64 KB array inside the library, present on every GPU that loads
+ * the library until the process exits.
+ *   seis_mod, seis_obs  device float32 [n]
+ *   resid    device float32 [n] (may alias seis_mod)
+ *   n        number of samples, at most BH_NOALLOC_MAX_SAMPLES
+ *   J        host double; the call synchronises `stream`
+ *   stream   cudaStream_t (NULL = legacy default stream)
+ * The first call on a device looks up the scratch address on that device
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one scratch array: calls whose work overlaps on the
+ * GPU (unordered streams) race and may return a wrong J.
+ * Errors: BH_ERR_INVALID_ARG (NULL pointer, n > BH_NOALLOC_MAX_SAMPLES),
+ *   BH_ERR_CUDA; bh_last_error(NULL) gives the message.
+ */
+#define BH_NOALLOC_MAX_SAMPLES 33554432 /* 8192 blocks x 4096 samples */
+bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_obs,
+                                     float* resid, size_t n, double* J, void* stream);
+
 /* Static description of a status code. */
 const char* bh_status_string(bh_status status);
 
 /* Text of the last error on this model ("" if none); NULL model: the last
- * error of bh_model_create on this thread. */
+ * error of bh_model_create or bh_residual_misfit_noalloc on this thread. */
 const char* bh_last_error(const bh_model* model);
 
 #ifdef __cplusplus

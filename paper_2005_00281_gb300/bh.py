@@ -23,7 +23,9 @@ STATUS_NAMES = {0: "BH_OK", 1: "BH_ERR_INVALID_ARG", 2: "BH_ERR_CFL", 3: "BH_ERR
 EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
            "bh_residual_misfit", "bh_adjoint_gradient", "bh_get_hessian", "bh_precondition",
            "bh_update", "bh_get_model", "bh_status_string", "bh_last_error",
-           "bh_profile_enable", "bh_profile_read", "bh_profile_reset")
+           "bh_profile_enable", "bh_profile_read", "bh_profile_reset",
+           "bh_residual_misfit_noalloc")
+NOALLOC_MAX_SAMPLES = 33554432
 KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel")
 
 
@@ -95,6 +97,9 @@ def load_library(path: str | None = None):
     lib.bh_profile_read.restype = st
     lib.bh_profile_reset.argtypes = [vp]
     lib.bh_profile_reset.restype = st
+    lib.bh_residual_misfit_noalloc.argtypes = [vp, vp, vp, ctypes.c_size_t,
+                                               ctypes.POINTER(ctypes.c_double), vp]
+    lib.bh_residual_misfit_noalloc.restype = st
     lib.bh_status_string.argtypes = [st]
     lib.bh_status_string.restype = ctypes.c_char_p
     lib.bh_last_error.argtypes = [vp]
@@ -259,3 +264,21 @@ def model_from_workload(w, device="cuda", **kw):
     t = lambda a: torch.from_numpy(a).to(device)
     return Model(w.nr, w.nz, w.nt, w.npml_r, w.npml_z, w.dr, w.dz, w.dt, w.f0, t(w.vp), t(w.vs),
                  t(w.rho), w.shots, pml_R=w.pml_R, **kw)
+
+
+def residual_misfit_noalloc(seis_mod, seis_obs, resid, stream=None):
+    """bh_residual_misfit_noalloc: Eq. 5 residual into `resid` and the Eq. 1
+    misfit J, with no device allocation by the library (and none here: the
+    caller passes every buffer).  Returns J."""
+    lib = load_library()
+    for name, t in (("seis_obs", seis_obs), ("resid", resid)):
+        if t.dtype != torch.float32 or t.numel() != seis_mod.numel():
+            raise ValueError(f"{name}: float32 tensor with {seis_mod.numel()} elements expected")
+    stream = stream if stream is not None else torch.cuda.current_stream(seis_mod.device)
+    J = ctypes.c_double()
+    rc = lib.bh_residual_misfit_noalloc(_ptr(seis_mod), _ptr(seis_obs), _ptr(resid),
+                                        seis_mod.numel(), ctypes.byref(J),
+                                        ctypes.c_void_p(stream.cuda_stream))
+    if rc != BH_OK:
+        raise BhError(rc, lib.bh_last_error(None).decode())
+    return J.value

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libbh.so")
-SOURCES = ["bh_runtime.cu"]
+SOURCES = ["bh_runtime.cu", "bh_noalloc.cu"]
 DEPS = ["bh_kernels.cuh", "bh_ops.cuh"]
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

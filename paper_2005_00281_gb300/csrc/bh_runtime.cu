@@ -326,6 +326,9 @@ bh_status setup_profiles(bh_model* m)
 
 }  // namespace
 
+// error text of calls that have no model (read with bh_last_error(NULL))
+void bh_internal_set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 const char* bh_status_string(bh_status s)
