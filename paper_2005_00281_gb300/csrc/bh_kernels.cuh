@@ -97,55 +97,98 @@ __device__ __forceinline__ void kahan_add(float2* __restrict__ acc, size_t k, fl
     acc[k] = s;
 }
 
+// ------------------------------------------------------------- tiling
+//
+// Every stepping kernel works on a tile of TR x TZ nodes (16 rows of r by 32
+// columns of z; 256 threads, each thread two rows 8 apart so that a warp
+// always covers 32 consecutive z) and first stages what its stencils read
+// from the tile plus a 2-node halo into shared memory, with the axis mirror
+// and the zero edges already applied.  The adjoint kernels then build the
+// transposed-stencil coefficients once per staged node.
+constexpr int kTZ = 32, kTR = 16, kH = 2;
+constexpr int kSZ = kTZ + 2 * kH, kSR = kTR + 2 * kH, kNS = kSZ * kSR;
+constexpr int kThreads = 256;
+
+// Programmatic dependent launch: a kernel may be scheduled while its
+// predecessor drains; it must wait here before touching the predecessor's
+// outputs.  No-op when launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// model value at window cell (i, j), i and j in range
+__device__ __forceinline__ float ldm(const float* __restrict__ f, int i, int j, const WinK& g)
+{
+    return f[(size_t)i * g.nzg + g.z0 + j];
+}
+
 // ------------------------------------------------------- forward: Eq. 2
 
 // Velocity half-step: Eq. 2 lines 1-2 with the C-PML memories 0..3.
-__global__ void __launch_bounds__(256) k_fwd_vel(WinK g, CoefK C, StateK S)
+__global__ void __launch_bounds__(kThreads) k_fwd_vel(WinK g, CoefK C, StateK S)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nr || j >= g.nz) return;
-    const size_t c = (size_t)i * g.P + j;
-    const size_t cg = (size_t)i * g.nzg + g.z0 + j;
-    if (i >= 1) {
-        float d_trr = d4(ld_h(S.trr, i, j, g), ld_h(S.trr, i - 1, j, g), ld_h(S.trr, i + 1, j, g),
-                         ld_h(S.trr, i - 2, j, g)) * g.inv_dr;
-        float d_trz = d4(ld_i(S.trz, i, j, g), ld_i(S.trz, i, j - 1, g), ld_i(S.trz, i, j + 1, g),
-                         ld_i(S.trz, i, j - 2, g)) * g.inv_dz;
-        float hoop = 0.5f * ((S.trr[c - g.P] - S.ttt[c - g.P]) + (S.trr[c] - S.ttt[c])) *
-                     C.inv_r_int[i];
-        float a = C.ar_int[i];
-        if (a != 0.f) {
-            float p = C.br_int[i] * S.psi[0][c] + a * d_trr;
-            S.psi_w[0][c] = p;
-            d_trr += p;
+    __shared__ float s_rr[kSR][kSZ], s_tt[kSR][kSZ], s_rz[kSR][kSZ], s_zz[kSR][kSZ];
+    pdl_wait();
+    const int j0 = blockIdx.x * kTZ, i0 = blockIdx.y * kTR;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int k = tid; k < kNS; k += kThreads) {
+        const int rr = k / kSZ, zz = k - rr * kSZ;
+        const int i = i0 - kH + rr, j = j0 - kH + zz;
+        s_rr[rr][zz] = ld_h(S.trr, i, j, g);
+        s_tt[rr][zz] = ld_h(S.ttt, i, j, g);
+        s_rz[rr][zz] = ld_i(S.trz, i, j, g);
+        s_zz[rr][zz] = ld_h(S.tzz, i, j, g);
+    }
+    __syncthreads();
+    pdl_launch_dependents();
+    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
+    if (j >= g.nz) return;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
+        if (i >= g.nr) break;
+        const size_t c = (size_t)i * g.P + j;
+        const size_t cg = (size_t)i * g.nzg + g.z0 + j;
+        if (i >= 1) {
+            float d_trr = d4(s_rr[rr][zz], s_rr[rr - 1][zz], s_rr[rr + 1][zz], s_rr[rr - 2][zz]) *
+                          g.inv_dr;
+            float d_trz = d4(s_rz[rr][zz], s_rz[rr][zz - 1], s_rz[rr][zz + 1], s_rz[rr][zz - 2]) *
+                          g.inv_dz;
+            float hoop = 0.5f * ((s_rr[rr - 1][zz] - s_tt[rr - 1][zz]) + (s_rr[rr][zz] - s_tt[rr][zz])) *
+                         C.inv_r_int[i];
+            float a = C.ar_int[i];
+            if (a != 0.f) {
+                float q = C.br_int[i] * S.psi[0][c] + a * d_trr;
+                S.psi_w[0][c] = q;
+                d_trr += q;
+            }
+            a = C.az_int[j];
+            if (a != 0.f) {
+                float q = C.bz_int[j] * S.psi[1][c] + a * d_trz;
+                S.psi_w[1][c] = q;
+                d_trz += q;
+            }
+            S.vr[c] += g.dt * C.bvr[cg] * (d_trr + d_trz + hoop);
         }
-        a = C.az_int[j];
+        float d_trz = d4(s_rz[rr + 1][zz], s_rz[rr][zz], s_rz[rr + 2][zz], s_rz[rr - 1][zz]) * g.inv_dr;
+        float d_tzz = d4(s_zz[rr][zz + 1], s_zz[rr][zz], s_zz[rr][zz + 2], s_zz[rr][zz - 1]) * g.inv_dz;
+        float hoop = 0.5f * (s_rz[rr][zz] + s_rz[rr + 1][zz]) * C.inv_r_half[i];
+        float a = C.ar_half[i];
         if (a != 0.f) {
-            float p = C.bz_int[j] * S.psi[1][c] + a * d_trz;
-            S.psi_w[1][c] = p;
-            d_trz += p;
+            float q = C.br_half[i] * S.psi[2][c] + a * d_trz;
+            S.psi_w[2][c] = q;
+            d_trz += q;
         }
-        S.vr[c] += g.dt * C.bvr[cg] * (d_trr + d_trz + hoop);
+        a = C.az_half[j];
+        if (a != 0.f) {
+            float q = C.bz_half[j] * S.psi[3][c] + a * d_tzz;
+            S.psi_w[3][c] = q;
+            d_tzz += q;
+        }
+        S.vz[c] += g.dt * bvz_at(C, g, i, j) * (d_trz + d_tzz + hoop);
     }
-    float d_trz = d4(ld_i(S.trz, i + 1, j, g), ld_i(S.trz, i, j, g), ld_i(S.trz, i + 2, j, g),
-                     ld_i(S.trz, i - 1, j, g)) * g.inv_dr;
-    float d_tzz = d4(ld_h(S.tzz, i, j + 1, g), ld_h(S.tzz, i, j, g), ld_h(S.tzz, i, j + 2, g),
-                     ld_h(S.tzz, i, j - 1, g)) * g.inv_dz;
-    float hoop = 0.5f * (ld_i(S.trz, i, j, g) + ld_i(S.trz, i + 1, j, g)) * C.inv_r_half[i];
-    float a = C.ar_half[i];
-    if (a != 0.f) {
-        float p = C.br_half[i] * S.psi[2][c] + a * d_trz;
-        S.psi_w[2][c] = p;
-        d_trz += p;
-    }
-    a = C.az_half[j];
-    if (a != 0.f) {
-        float p = C.bz_half[j] * S.psi[3][c] + a * d_tzz;
-        S.psi_w[3][c] = p;
-        d_tzz += p;
-    }
-    S.vz[c] += g.dt * bvz_at(C, g, i, j) * (d_trz + d_tzz + hoop);
 }
 
 struct SrcRecK {
@@ -161,76 +204,97 @@ struct SrcRecK {
 // Stress half-step: Eq. 2 lines 3-6 with the C-PML memories 4..7, source
 // injection into the three normal stresses, pressure recording, and the
 // store of v^{n+1/2} for the adjoint.
-__global__ void __launch_bounds__(256) k_fwd_stress(WinK g, CoefK C, StateK S, SrcRecK q)
+__global__ void __launch_bounds__(kThreads) k_fwd_stress(WinK g, CoefK C, StateK S, SrcRecK q)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nr || j >= g.nz) return;
-    const size_t c = (size_t)i * g.P + j;
-    const size_t cg = (size_t)i * g.nzg + g.z0 + j;
-
-    float d_vr = d4(ld_i(S.vr, i + 1, j, g), ld_i(S.vr, i, j, g), ld_i(S.vr, i + 2, j, g),
-                    ld_i(S.vr, i - 1, j, g)) * g.inv_dr;
-    float vr_r = 0.5f * (ld_i(S.vr, i, j, g) + ld_i(S.vr, i + 1, j, g)) * C.inv_r_half[i];
-    float d_vz = d4(ld_h(S.vz, i, j, g), ld_h(S.vz, i, j - 1, g), ld_h(S.vz, i, j + 1, g),
-                    ld_h(S.vz, i, j - 2, g)) * g.inv_dz;
-    float a = C.ar_half[i];
-    if (a != 0.f) {
-        float p = C.br_half[i] * S.psi[4][c] + a * d_vr;
-        S.psi_w[4][c] = p;
-        d_vr += p;
+    __shared__ float s_vr[kSR][kSZ], s_vz[kSR][kSZ];
+    pdl_wait();
+    const int j0 = blockIdx.x * kTZ, i0 = blockIdx.y * kTR;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int k = tid; k < kNS; k += kThreads) {
+        const int rr = k / kSZ, zz = k - rr * kSZ;
+        const int i = i0 - kH + rr, j = j0 - kH + zz;
+        s_vr[rr][zz] = ld_i(S.vr, i, j, g);
+        s_vz[rr][zz] = ld_h(S.vz, i, j, g);
     }
-    a = C.az_int[j];
-    if (a != 0.f) {
-        float p = C.bz_int[j] * S.psi[5][c] + a * d_vz;
-        S.psi_w[5][c] = p;
-        d_vz += p;
-    }
-    const float lam = C.lam[cg];
-    const float l2m = lam + 2.f * C.mu[cg];
-    float trr = S.trr[c] + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
-    float ttt = S.ttt[c] + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
-    float tzz = S.tzz[c] + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
-    if ((int)c == q.src_c) {
-        float inj = q.src_scale * q.wavelet[q.n];
-        trr += inj;
-        ttt += inj;
-        tzz += inj;
-    }
-    S.trr[c] = trr;
-    S.ttt[c] = ttt;
-    S.tzz[c] = tzz;
-    if (i == 0) {
-        int k = q.recmap[j];
-        if (k >= 0) q.seis[(size_t)k * q.nt + q.n] = (trr + ttt + tzz) * (1.f / 3.f);
-    }
-    if (i >= 1) {
-        float d_vrz = d4(ld_i(S.vr, i, j + 1, g), ld_i(S.vr, i, j, g), ld_i(S.vr, i, j + 2, g),
-                         ld_i(S.vr, i, j - 1, g)) * g.inv_dz;
-        float d_vzr = d4(ld_h(S.vz, i, j, g), ld_h(S.vz, i - 1, j, g), ld_h(S.vz, i + 1, j, g),
-                         ld_h(S.vz, i - 2, j, g)) * g.inv_dr;
-        a = C.az_half[j];
+    __syncthreads();
+    pdl_launch_dependents();
+    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
+    if (j >= g.nz) return;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
+        if (i >= g.nr) break;
+        const size_t c = (size_t)i * g.P + j;
+        const size_t cg = (size_t)i * g.nzg + g.z0 + j;
+        float d_vr = d4(s_vr[rr + 1][zz], s_vr[rr][zz], s_vr[rr + 2][zz], s_vr[rr - 1][zz]) * g.inv_dr;
+        float vr_r = 0.5f * (s_vr[rr][zz] + s_vr[rr + 1][zz]) * C.inv_r_half[i];
+        float d_vz = d4(s_vz[rr][zz], s_vz[rr][zz - 1], s_vz[rr][zz + 1], s_vz[rr][zz - 2]) * g.inv_dz;
+        float a = C.ar_half[i];
         if (a != 0.f) {
-            float p = C.bz_half[j] * S.psi[6][c] + a * d_vrz;
-            S.psi_w[6][c] = p;
-            d_vrz += p;
+            float w = C.br_half[i] * S.psi[4][c] + a * d_vr;
+            S.psi_w[4][c] = w;
+            d_vr += w;
         }
-        a = C.ar_int[i];
+        a = C.az_int[j];
         if (a != 0.f) {
-            float p = C.br_int[i] * S.psi[7][c] + a * d_vzr;
-            S.psi_w[7][c] = p;
-            d_vzr += p;
+            float w = C.bz_int[j] * S.psi[5][c] + a * d_vz;
+            S.psi_w[5][c] = w;
+            d_vz += w;
         }
-        S.trz[c] += g.dt * muh_at(C, g, i, j) * (d_vrz + d_vzr);
-    }
-    if (q.hist) {
-        float* h = q.hist + (size_t)q.n * 2 * g.nr * g.P;
-        h[c] = S.vr[c];
-        h[(size_t)g.nr * g.P + c] = S.vz[c];
+        const float lam = C.lam[cg];
+        const float l2m = lam + 2.f * C.mu[cg];
+        float trr = S.trr[c] + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
+        float ttt = S.ttt[c] + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
+        float tzz = S.tzz[c] + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
+        if ((int)c == q.src_c) {
+            float inj = q.src_scale * q.wavelet[q.n];
+            trr += inj;
+            ttt += inj;
+            tzz += inj;
+        }
+        S.trr[c] = trr;
+        S.ttt[c] = ttt;
+        S.tzz[c] = tzz;
+        if (i == 0) {
+            int k = q.recmap[j];
+            if (k >= 0) q.seis[(size_t)k * q.nt + q.n] = (trr + ttt + tzz) * (1.f / 3.f);
+        }
+        if (i >= 1) {
+            float d_vrz = d4(s_vr[rr][zz + 1], s_vr[rr][zz], s_vr[rr][zz + 2], s_vr[rr][zz - 1]) *
+                          g.inv_dz;
+            float d_vzr = d4(s_vz[rr][zz], s_vz[rr - 1][zz], s_vz[rr + 1][zz], s_vz[rr - 2][zz]) *
+                          g.inv_dr;
+            a = C.az_half[j];
+            if (a != 0.f) {
+                float w = C.bz_half[j] * S.psi[6][c] + a * d_vrz;
+                S.psi_w[6][c] = w;
+                d_vrz += w;
+            }
+            a = C.ar_int[i];
+            if (a != 0.f) {
+                float w = C.br_int[i] * S.psi[7][c] + a * d_vzr;
+                S.psi_w[7][c] = w;
+                d_vzr += w;
+            }
+            S.trz[c] += g.dt * muh_at(C, g, i, j) * (d_vrz + d_vzr);
+        }
+        if (q.hist) {
+            float* h = q.hist + (size_t)q.n * 2 * g.nr * g.P;
+            h[c] = s_vr[rr][zz];
+            h[(size_t)g.nr * g.P + c] = s_vz[rr][zz];
+        }
     }
 }
 
 // ------------------------------------------ adjoint: transpose of Eq. 2
+//
+// Gather form of the transpose.  The forward step reads ghost values through
+// the axis mirror and the zero edges; the transpose of "mirror, then
+// stencil" is "stencil of the coefficients extended with the same parity,
+// then fold", which here means: the transposed stencil reads the adjoint
+// coefficients of cells and v_z nodes with the even extension
+// (X[-1-k] = X[k]), those of v_r and trz nodes with the odd extension
+// (X[-k] = -X[k], X[0] = 0), and zero beyond the edges.
 
 struct AdjK {
     const float* resid;   // [nrec_max][nt] of this shot
@@ -241,273 +305,247 @@ struct AdjK {
     float *H_lam, *H_munn, *H_murz;                 // [nr*P]
 };
 
-// Adjoint of the stress-step quantities at a cell: the coefficient that the
-// transposed stencil applies to D_r v_r (x_rr), to v_r/r (y_tt) and to
-// D_z v_z (x_zz).  Cells outside the window give zero.
-__device__ __forceinline__ float adj_x_rr(const WinK& g, const CoefK& C, const StateK& S,
-                                          int i, int j)
-{
-    if (j < 0 || j >= g.nz || i >= g.nr) return 0.f;
-    if (i < 0) i = -1 - i;  // even extension about the axis
-    const size_t c = (size_t)i * g.P + j;
-    const size_t cg = (size_t)i * g.nzg + g.z0 + j;
-    const float lam = C.lam[cg], l2m = lam + 2.f * C.mu[cg];
-    float y = g.dt * (l2m * S.trr[c] + lam * (S.ttt[c] + S.tzz[c]));
-    float a = C.ar_half[i];
-    if (a != 0.f) y = y + a * (y + C.br_half[i] * S.psi[4][c]);
-    return y;
-}
-
-__device__ __forceinline__ float adj_y_tt(const WinK& g, const CoefK& C, const StateK& S,
-                                          int i, int j)
-{
-    const size_t c = (size_t)i * g.P + j;
-    const size_t cg = (size_t)i * g.nzg + g.z0 + j;
-    const float lam = C.lam[cg], l2m = lam + 2.f * C.mu[cg];
-    return g.dt * (l2m * S.ttt[c] + lam * (S.trr[c] + S.tzz[c]));
-}
-
-__device__ __forceinline__ float adj_x_zz(const WinK& g, const CoefK& C, const StateK& S,
-                                          int i, int j)
-{
-    if (j < 0 || j >= g.nz) return 0.f;
-    const size_t c = (size_t)i * g.P + j;
-    const size_t cg = (size_t)i * g.nzg + g.z0 + j;
-    const float lam = C.lam[cg], l2m = lam + 2.f * C.mu[cg];
-    float y = g.dt * (l2m * S.tzz[c] + lam * (S.trr[c] + S.ttt[c]));
-    float a = C.az_int[j];
-    if (a != 0.f) y = y + a * (y + C.bz_int[j] * S.psi[5][c]);
-    return y;
-}
-
-// shear node: coefficient on D_z v_r (x6, axial layer) and on D_r v_z (x7,
-// radial layer); odd extension about the axis, zero outside
-__device__ __forceinline__ float adj_x_rz_z(const WinK& g, const CoefK& C, const StateK& S,
-                                            int i, int j)
-{
-    if (j < 0 || j >= g.nz) return 0.f;
-    const size_t c = (size_t)i * g.P + j;
-    float y = g.dt * muh_at(C, g, i, j) * S.trz[c];
-    float a = C.az_half[j];
-    if (a != 0.f) y = y + a * (y + C.bz_half[j] * S.psi[6][c]);
-    return y;
-}
-
-__device__ __forceinline__ float adj_x_rz_r(const WinK& g, const CoefK& C, const StateK& S,
-                                            int i, int j)
-{
-    float s = 1.f;
-    if (i < 0) { i = -i; s = -1.f; }
-    if (i == 0 || i >= g.nr) return 0.f;
-    const size_t c = (size_t)i * g.P + j;
-    float y = g.dt * muh_at(C, g, i, j) * S.trz[c];
-    float a = C.ar_int[i];
-    if (a != 0.f) y = y + a * (y + C.br_int[i] * S.psi[7][c]);
-    return s * y;
-}
-
 // Transpose of the stress step at reverse step n, fused with the gradient
 // correlations (Eq. 7, Eq. 8, and the density term).  S.{trr..trz} hold
 // dJ/dtau^{n+1}; S.{vr,vz} accumulate to dJ/dv^{n+1/2}; psi[4..7] are the
 // adjoint memories read side, psi_w[4..7] the write side.
-__global__ void __launch_bounds__(256) k_adj_stress(WinK g, CoefK C, StateK S, AdjK q)
+__global__ void __launch_bounds__(kThreads) k_adj_stress(WinK g, CoefK C, StateK S, AdjK q)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nr || j >= g.nz) return;
-    const size_t c = (size_t)i * g.P + j;
-    const float dt = g.dt;
-
-    // ---- gradient correlation with the forward strains of v^{n+1/2}
+    // staged inputs: adjoint stresses, lambda, mu, mu_h, forward v^{n+1/2}
+    __shared__ float s_arr[kSR][kSZ], s_att[kSR][kSZ], s_azz[kSR][kSZ], s_arz[kSR][kSZ];
+    __shared__ float s_lam[kSR][kSZ], s_mu[kSR][kSZ], s_muh[kSR][kSZ];
+    __shared__ float s_fvr[kSR][kSZ], s_fvz[kSR][kSZ];
+    // transposed-stencil coefficients: on D_r v_r (x4), v_r/r (ytt), D_z v_z
+    // (x5) at cells; on D_z v_r (x6) and D_r v_z (x7) at trz nodes
+    __shared__ float s_x4[kSR][kSZ], s_ytt[kSR][kSZ], s_x5[kSR][kSZ], s_x6[kSR][kSZ],
+        s_x7[kSR][kSZ];
+    pdl_wait();
+    const int j0 = blockIdx.x * kTZ, i0 = blockIdx.y * kTR;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     const float* fvr = q.hist + (size_t)q.n * 2 * g.nr * g.P;
     const float* fvz = fvr + (size_t)g.nr * g.P;
-    {
-        float err = d4(ld_i(fvr, i + 1, j, g), ld_i(fvr, i, j, g), ld_i(fvr, i + 2, j, g),
-                       ld_i(fvr, i - 1, j, g)) * g.inv_dr;
-        float ett = 0.5f * (ld_i(fvr, i, j, g) + ld_i(fvr, i + 1, j, g)) * C.inv_r_half[i];
-        float ezz = d4(ld_h(fvz, i, j, g), ld_h(fvz, i, j - 1, g), ld_h(fvz, i, j + 1, g),
-                       ld_h(fvz, i, j - 2, g)) * g.inv_dz;
-        float arr = S.trr[c], att = S.ttt[c], azz = S.tzz[c];
-        float div = err + ett + ezz;
-        kahan_add(q.G_lam, c, dt * div * (arr + att + azz));
-        kahan_add(q.G_munn, c, 2.f * dt * (err * arr + ett * att + ezz * azz));
-        q.H_lam[c] += dt * div * div;
-        q.H_munn[c] += 4.f * dt * (err * err + ett * ett + ezz * ezz);
+    const float dt = g.dt;
+
+    for (int k = tid; k < kNS; k += kThreads) {
+        const int rr = k / kSZ, zz = k - rr * kSZ;
+        const int i = i0 - kH + rr, j = j0 - kH + zz;
+        s_arr[rr][zz] = ld_h(S.trr, i, j, g);
+        s_att[rr][zz] = ld_h(S.ttt, i, j, g);
+        s_azz[rr][zz] = ld_h(S.tzz, i, j, g);
+        s_arz[rr][zz] = ld_i(S.trz, i, j, g);
+        s_fvr[rr][zz] = ld_i(fvr, i, j, g);
+        s_fvz[rr][zz] = ld_h(fvz, i, j, g);
+        float lam = 0.f, mu = 0.f, mh = 0.f;
+        if (j >= 0 && j < g.nz) {
+            const int ic = i < 0 ? -1 - i : i;  // cells: even about the axis
+            const int it = i < 0 ? -i : i;      // trz nodes: mirror row of an integer node
+            if (ic < g.nr) {
+                lam = ldm(C.lam, ic, j, g);
+                mu = ldm(C.mu, ic, j, g);
+            }
+            if (it >= 1 && it < g.nr) mh = muh_at(C, g, it, j);
+        }
+        s_lam[rr][zz] = lam;
+        s_mu[rr][zz] = mu;
+        s_muh[rr][zz] = mh;
+    }
+    __syncthreads();
+    for (int k = tid; k < kNS; k += kThreads) {
+        const int rr = k / kSZ, zz = k - rr * kSZ;
+        const int i = i0 - kH + rr, j = j0 - kH + zz;
+        float x4 = 0.f, ytt = 0.f, x5 = 0.f, x6 = 0.f, x7 = 0.f;
+        if (j >= 0 && j < g.nz && i < g.nr) {
+            const int ic = i < 0 ? -1 - i : i;
+            const float lam = s_lam[rr][zz], l2m = lam + 2.f * s_mu[rr][zz];
+            const float arr = s_arr[rr][zz], att = s_att[rr][zz], azz = s_azz[rr][zz];
+            x4 = dt * (l2m * arr + lam * (att + azz));
+            ytt = dt * (l2m * att + lam * (arr + azz));
+            x5 = dt * (l2m * azz + lam * (arr + att));
+            float a = C.ar_half[ic];
+            if (a != 0.f) x4 = x4 + a * (x4 + C.br_half[ic] * S.psi[4][(size_t)ic * g.P + j]);
+            a = C.az_int[j];
+            if (a != 0.f) x5 = x5 + a * (x5 + C.bz_int[j] * S.psi[5][(size_t)ic * g.P + j]);
+            // trz node: the staged values are already odd about the axis
+            const float y = dt * s_muh[rr][zz] * s_arz[rr][zz];
+            x6 = y;
+            x7 = y;
+            if (i >= 1) {
+                a = C.az_half[j];
+                if (a != 0.f) x6 = y + a * (y + C.bz_half[j] * S.psi[6][(size_t)i * g.P + j]);
+                a = C.ar_int[i];
+                if (a != 0.f) x7 = y + a * (y + C.br_int[i] * S.psi[7][(size_t)i * g.P + j]);
+            }
+        }
+        s_x4[rr][zz] = x4;
+        s_ytt[rr][zz] = ytt;
+        s_x5[rr][zz] = x5;
+        s_x6[rr][zz] = x6;
+        s_x7[rr][zz] = x7;
+    }
+    __syncthreads();
+    pdl_launch_dependents();
+
+    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
+    if (j >= g.nz) return;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
+        if (i >= g.nr) break;
+        const size_t c = (size_t)i * g.P + j;
+
+        // ---- gradient correlation with the forward strains of v^{n+1/2}
+        const float arr = s_arr[rr][zz], att = s_att[rr][zz], azz = s_azz[rr][zz];
+        {
+            float err = d4(s_fvr[rr + 1][zz], s_fvr[rr][zz], s_fvr[rr + 2][zz], s_fvr[rr - 1][zz]) *
+                        g.inv_dr;
+            float ett = 0.5f * (s_fvr[rr][zz] + s_fvr[rr + 1][zz]) * C.inv_r_half[i];
+            float ezz = d4(s_fvz[rr][zz], s_fvz[rr][zz - 1], s_fvz[rr][zz + 1], s_fvz[rr][zz - 2]) *
+                        g.inv_dz;
+            float div = err + ett + ezz;
+            kahan_add(q.G_lam, c, dt * div * (arr + att + azz));
+            kahan_add(q.G_munn, c, 2.f * dt * (err * arr + ett * att + ezz * azz));
+            q.H_lam[c] += dt * div * div;
+            q.H_munn[c] += 4.f * dt * (err * err + ett * ett + ezz * ezz);
+            if (i >= 1) {
+                float gam = d4(s_fvr[rr][zz + 1], s_fvr[rr][zz], s_fvr[rr][zz + 2], s_fvr[rr][zz - 1]) *
+                                g.inv_dz +
+                            d4(s_fvz[rr][zz], s_fvz[rr - 1][zz], s_fvz[rr + 1][zz], s_fvz[rr - 2][zz]) *
+                                g.inv_dr;
+                kahan_add(q.G_murz, c, dt * gam * s_arz[rr][zz]);
+                q.H_murz[c] += dt * gam * gam;
+            }
+        }
+
+        // ---- transpose of the stress step into Av, and the density term
         if (i >= 1) {
-            float gam = d4(ld_i(fvr, i, j + 1, g), ld_i(fvr, i, j, g), ld_i(fvr, i, j + 2, g),
-                           ld_i(fvr, i, j - 1, g)) * g.inv_dz +
-                        d4(ld_h(fvz, i, j, g), ld_h(fvz, i - 1, j, g), ld_h(fvz, i + 1, j, g),
-                           ld_h(fvz, i - 2, j, g)) * g.inv_dr;
-            kahan_add(q.G_murz, c, dt * gam * S.trz[c]);
-            q.H_murz[c] += dt * gam * gam;
+            float s = d4(s_x4[rr - 1][zz], s_x4[rr][zz], s_x4[rr - 2][zz], s_x4[rr + 1][zz]) * g.inv_dr;
+            s += 0.5f * (s_ytt[rr - 1][zz] * C.inv_r_half[i - 1] + s_ytt[rr][zz] * C.inv_r_half[i]);
+            s += d4(s_x6[rr][zz - 1], s_x6[rr][zz], s_x6[rr][zz - 2], s_x6[rr][zz + 1]) * g.inv_dz;
+            float av = S.vr[c] + s;
+            S.vr[c] = av;
+            float dv = s_fvr[rr][zz] - (q.n > 0 ? fvr[c - (size_t)2 * g.nr * g.P] : 0.f);
+            kahan_add(q.G_br, c, dv * av);
+        }
+        {
+            float s = d4(s_x5[rr][zz], s_x5[rr][zz + 1], s_x5[rr][zz - 1], s_x5[rr][zz + 2]) * g.inv_dz;
+            s += d4(s_x7[rr][zz], s_x7[rr + 1][zz], s_x7[rr - 1][zz], s_x7[rr + 2][zz]) * g.inv_dr;
+            float av = S.vz[c] + s;
+            S.vz[c] = av;
+            float dv = s_fvz[rr][zz] - (q.n > 0 ? fvz[c - (size_t)2 * g.nr * g.P] : 0.f);
+            kahan_add(q.G_bz, c, dv * av);
+        }
+
+        // ---- adjoint memories of the stress step (own cell / own shear node)
+        {
+            const float lam = s_lam[rr][zz], l2m = lam + 2.f * s_mu[rr][zz];
+            if (C.ar_half[i] != 0.f)
+                S.psi_w[4][c] = dt * (l2m * arr + lam * (att + azz)) + C.br_half[i] * S.psi[4][c];
+            if (C.az_int[j] != 0.f)
+                S.psi_w[5][c] = dt * (l2m * azz + lam * (arr + att)) + C.bz_int[j] * S.psi[5][c];
+            if (i >= 1) {
+                const float y = dt * s_muh[rr][zz] * s_arz[rr][zz];
+                if (C.az_half[j] != 0.f) S.psi_w[6][c] = y + C.bz_half[j] * S.psi[6][c];
+                if (C.ar_int[i] != 0.f) S.psi_w[7][c] = y + C.br_int[i] * S.psi[7][c];
+            }
         }
     }
-
-    // ---- transpose of the stress step into Av
-    if (i >= 1) {
-        float s = d4(adj_x_rr(g, C, S, i - 1, j), adj_x_rr(g, C, S, i, j),
-                     adj_x_rr(g, C, S, i - 2, j), adj_x_rr(g, C, S, i + 1, j)) * g.inv_dr;
-        s += 0.5f * (adj_y_tt(g, C, S, i - 1, j) * C.inv_r_half[i - 1] +
-                     adj_y_tt(g, C, S, i, j) * C.inv_r_half[i]);
-        s += d4(adj_x_rz_z(g, C, S, i, j - 1), adj_x_rz_z(g, C, S, i, j),
-                adj_x_rz_z(g, C, S, i, j - 2), adj_x_rz_z(g, C, S, i, j + 1)) * g.inv_dz;
-        float av = S.vr[c] + s;
-        S.vr[c] = av;
-        float dv = fvr[c] - (q.n > 0 ? fvr[c - (size_t)2 * g.nr * g.P] : 0.f);
-        kahan_add(q.G_br, c, dv * av);
-    }
-    {
-        float s = d4(adj_x_zz(g, C, S, i, j), adj_x_zz(g, C, S, i, j + 1),
-                     adj_x_zz(g, C, S, i, j - 1), adj_x_zz(g, C, S, i, j + 2)) * g.inv_dz;
-        s += d4(adj_x_rz_r(g, C, S, i, j), adj_x_rz_r(g, C, S, i + 1, j),
-                adj_x_rz_r(g, C, S, i - 1, j), adj_x_rz_r(g, C, S, i + 2, j)) * g.inv_dr;
-        float av = S.vz[c] + s;
-        S.vz[c] = av;
-        float dv = fvz[c] - (q.n > 0 ? fvz[c - (size_t)2 * g.nr * g.P] : 0.f);
-        kahan_add(q.G_bz, c, dv * av);
-    }
-
-    // ---- adjoint memories of the stress step (own cell / own shear node)
-    {
-        const size_t cg = (size_t)i * g.nzg + g.z0 + j;
-        const float lam = C.lam[cg], l2m = lam + 2.f * C.mu[cg];
-        float a = C.ar_half[i];
-        if (a != 0.f)
-            S.psi_w[4][c] = dt * (l2m * S.trr[c] + lam * (S.ttt[c] + S.tzz[c])) +
-                            C.br_half[i] * S.psi[4][c];
-        a = C.az_int[j];
-        if (a != 0.f)
-            S.psi_w[5][c] = dt * (l2m * S.tzz[c] + lam * (S.trr[c] + S.ttt[c])) +
-                            C.bz_int[j] * S.psi[5][c];
-        if (i >= 1) {
-            float y = dt * muh_at(C, g, i, j) * S.trz[c];
-            a = C.az_half[j];
-            if (a != 0.f) S.psi_w[6][c] = y + C.bz_half[j] * S.psi[6][c];
-            a = C.ar_int[i];
-            if (a != 0.f) S.psi_w[7][c] = y + C.br_int[i] * S.psi[7][c];
-        }
-    }
-}
-
-// velocity-node adjoint weights W = dt b Av, and the coefficients applied
-// to the four stretched derivatives of the velocity step
-__device__ __forceinline__ float adj_w_r(const WinK& g, const CoefK& C, const StateK& S,
-                                         int i, int j)
-{
-    if (i <= 0 || i >= g.nr || j < 0 || j >= g.nz) return 0.f;
-    const size_t c = (size_t)i * g.P + j;
-    return g.dt * C.bvr[(size_t)i * g.nzg + g.z0 + j] * S.vr[c];
-}
-
-__device__ __forceinline__ float adj_w_z(const WinK& g, const CoefK& C, const StateK& S,
-                                         int i, int j)
-{
-    if (i < 0 || i >= g.nr || j < 0 || j >= g.nz) return 0.f;
-    const size_t c = (size_t)i * g.P + j;
-    return g.dt * bvz_at(C, g, i, j) * S.vz[c];
-}
-
-// on d trr/dr at v_r (i,j): odd extension about the axis
-__device__ __forceinline__ float adj_x0(const WinK& g, const CoefK& C, const StateK& S,
-                                        int i, int j)
-{
-    float s = 1.f;
-    if (i < 0) { i = -i; s = -1.f; }
-    if (i == 0 || i >= g.nr) return 0.f;
-    float w = adj_w_r(g, C, S, i, j);
-    float a = C.ar_int[i];
-    if (a != 0.f) w = w + a * (w + C.br_int[i] * S.psi[0][(size_t)i * g.P + j]);
-    return s * w;
-}
-
-// on d trz/dz at v_r (i,j), i >= 1
-__device__ __forceinline__ float adj_x1(const WinK& g, const CoefK& C, const StateK& S,
-                                        int i, int j)
-{
-    if (j < 0 || j >= g.nz) return 0.f;
-    float w = adj_w_r(g, C, S, i, j);
-    float a = C.az_int[j];
-    if (a != 0.f) w = w + a * (w + C.bz_int[j] * S.psi[1][(size_t)i * g.P + j]);
-    return w;
-}
-
-// on d trz/dr at v_z (i,j): even extension about the axis
-__device__ __forceinline__ float adj_x2(const WinK& g, const CoefK& C, const StateK& S,
-                                        int i, int j)
-{
-    if (i < 0) i = -1 - i;
-    if (i >= g.nr) return 0.f;
-    float w = adj_w_z(g, C, S, i, j);
-    float a = C.ar_half[i];
-    if (a != 0.f) w = w + a * (w + C.br_half[i] * S.psi[2][(size_t)i * g.P + j]);
-    return w;
-}
-
-// on d tzz/dz at v_z (i,j)
-__device__ __forceinline__ float adj_x3(const WinK& g, const CoefK& C, const StateK& S,
-                                        int i, int j)
-{
-    if (j < 0 || j >= g.nz) return 0.f;
-    float w = adj_w_z(g, C, S, i, j);
-    float a = C.az_half[j];
-    if (a != 0.f) w = w + a * (w + C.bz_half[j] * S.psi[3][(size_t)i * g.P + j]);
-    return w;
 }
 
 // Transpose of the velocity step at reverse step n: S.{vr,vz} hold
 // dJ/dv^{n+1/2}; S.{trr..trz} accumulate to dJ/dtau^n.  Then the residual
 // of step n-1 is injected at the receivers (transpose of the recording).
-__global__ void __launch_bounds__(256) k_adj_vel(WinK g, CoefK C, StateK S, AdjK q)
+__global__ void __launch_bounds__(kThreads) k_adj_vel(WinK g, CoefK C, StateK S, AdjK q)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nr || j >= g.nz) return;
-    const size_t c = (size_t)i * g.P + j;
-
-    // cell (i,j)
-    float hoop = 0.5f * (adj_w_r(g, C, S, i, j) * (i >= 1 ? C.inv_r_int[i] : 0.f) +
-                         adj_w_r(g, C, S, i + 1, j) * (i + 1 < g.nr ? C.inv_r_int[i + 1] : 0.f));
-    float arr = d4(adj_x0(g, C, S, i, j), adj_x0(g, C, S, i + 1, j), adj_x0(g, C, S, i - 1, j),
-                   adj_x0(g, C, S, i + 2, j)) * g.inv_dr;
-    float azz = d4(adj_x3(g, C, S, i, j - 1), adj_x3(g, C, S, i, j), adj_x3(g, C, S, i, j - 2),
-                   adj_x3(g, C, S, i, j + 1)) * g.inv_dz;
-    float trr = S.trr[c] + arr + hoop;
-    float ttt = S.ttt[c] - hoop;
-    float tzz = S.tzz[c] + azz;
-    if (i == 0 && q.n > 0) {
-        int k = q.recmap[j];
-        if (k >= 0) {
-            float r3 = q.resid[(size_t)k * q.nt + (q.n - 1)] * (1.f / 3.f);
-            trr += r3;
-            ttt += r3;
-            tzz += r3;
+    // W = dt b Av at the velocity nodes (odd about the axis for v_r, even
+    // for v_z), and the coefficients on the four stretched derivatives
+    __shared__ float s_wr[kSR][kSZ], s_wz[kSR][kSZ];
+    __shared__ float s_x0[kSR][kSZ], s_x1[kSR][kSZ], s_x2[kSR][kSZ], s_x3[kSR][kSZ];
+    pdl_wait();
+    const int j0 = blockIdx.x * kTZ, i0 = blockIdx.y * kTR;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int k = tid; k < kNS; k += kThreads) {
+        const int rr = k / kSZ, zz = k - rr * kSZ;
+        const int i = i0 - kH + rr, j = j0 - kH + zz;
+        float wr = 0.f, wz = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
+        if (j >= 0 && j < g.nz) {
+            // v_r node: odd extension, zero on the axis and beyond nr
+            const int ir = i < 0 ? -i : i;
+            if (ir >= 1 && ir < g.nr) {
+                const float sg = i < 0 ? -1.f : 1.f;
+                const size_t c = (size_t)ir * g.P + j;
+                const float w = g.dt * ldm(C.bvr, ir, j, g) * S.vr[c];
+                float a = C.ar_int[ir];
+                x0 = (a != 0.f) ? w + a * (w + C.br_int[ir] * S.psi[0][c]) : w;
+                a = C.az_int[j];
+                x1 = (a != 0.f) ? w + a * (w + C.bz_int[j] * S.psi[1][c]) : w;
+                wr = sg * w;
+                x0 *= sg;
+                x1 *= sg;
+            }
+            // v_z node: even extension, zero beyond nr
+            const int iz = i < 0 ? -1 - i : i;
+            if (iz < g.nr) {
+                const size_t c = (size_t)iz * g.P + j;
+                const float w = g.dt * bvz_at(C, g, iz, j) * S.vz[c];
+                float a = C.ar_half[iz];
+                x2 = (a != 0.f) ? w + a * (w + C.br_half[iz] * S.psi[2][c]) : w;
+                a = C.az_half[j];
+                x3 = (a != 0.f) ? w + a * (w + C.bz_half[j] * S.psi[3][c]) : w;
+                wz = w;
+            }
         }
+        s_wr[rr][zz] = wr;
+        s_wz[rr][zz] = wz;
+        s_x0[rr][zz] = x0;
+        s_x1[rr][zz] = x1;
+        s_x2[rr][zz] = x2;
+        s_x3[rr][zz] = x3;
     }
-    S.trr[c] = trr;
-    S.ttt[c] = ttt;
-    S.tzz[c] = tzz;
+    __syncthreads();
+    pdl_launch_dependents();
 
-    // shear node (i,j)
-    if (i >= 1) {
-        float s = d4(adj_x1(g, C, S, i, j), adj_x1(g, C, S, i, j + 1), adj_x1(g, C, S, i, j - 1),
-                     adj_x1(g, C, S, i, j + 2)) * g.inv_dz;
-        s += d4(adj_x2(g, C, S, i - 1, j), adj_x2(g, C, S, i, j), adj_x2(g, C, S, i - 2, j),
-                adj_x2(g, C, S, i + 1, j)) * g.inv_dr;
-        s += 0.5f * (adj_w_z(g, C, S, i - 1, j) * C.inv_r_half[i - 1] +
-                     adj_w_z(g, C, S, i, j) * C.inv_r_half[i]);
-        S.trz[c] += s;
-    }
+    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
+    if (j >= g.nz) return;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
+        if (i >= g.nr) break;
+        const size_t c = (size_t)i * g.P + j;
+        // cell (i,j); inv_r_int[0] is 0 and W_r vanishes on the axis
+        float hoop = 0.5f * (s_wr[rr][zz] * C.inv_r_int[i] +
+                             s_wr[rr + 1][zz] * (i + 1 < g.nr ? C.inv_r_int[i + 1] : 0.f));
+        float arr = d4(s_x0[rr][zz], s_x0[rr + 1][zz], s_x0[rr - 1][zz], s_x0[rr + 2][zz]) * g.inv_dr;
+        float azz = d4(s_x3[rr][zz - 1], s_x3[rr][zz], s_x3[rr][zz - 2], s_x3[rr][zz + 1]) * g.inv_dz;
+        float trr = S.trr[c] + arr + hoop;
+        float ttt = S.ttt[c] - hoop;
+        float tzz = S.tzz[c] + azz;
+        if (i == 0 && q.n > 0) {
+            int k = q.recmap[j];
+            if (k >= 0) {
+                float r3 = q.resid[(size_t)k * q.nt + (q.n - 1)] * (1.f / 3.f);
+                trr += r3;
+                ttt += r3;
+                tzz += r3;
+            }
+        }
+        S.trr[c] = trr;
+        S.ttt[c] = ttt;
+        S.tzz[c] = tzz;
 
-    // adjoint memories of the velocity step at the own velocity nodes
-    if (i >= 1) {
-        float w = adj_w_r(g, C, S, i, j);
-        if (C.ar_int[i] != 0.f) S.psi_w[0][c] = w + C.br_int[i] * S.psi[0][c];
-        if (C.az_int[j] != 0.f) S.psi_w[1][c] = w + C.bz_int[j] * S.psi[1][c];
-    }
-    {
-        float w = adj_w_z(g, C, S, i, j);
-        if (C.ar_half[i] != 0.f) S.psi_w[2][c] = w + C.br_half[i] * S.psi[2][c];
-        if (C.az_half[j] != 0.f) S.psi_w[3][c] = w + C.bz_half[j] * S.psi[3][c];
+        if (i >= 1) {
+            float s = d4(s_x1[rr][zz], s_x1[rr][zz + 1], s_x1[rr][zz - 1], s_x1[rr][zz + 2]) * g.inv_dz;
+            s += d4(s_x2[rr - 1][zz], s_x2[rr][zz], s_x2[rr - 2][zz], s_x2[rr + 1][zz]) * g.inv_dr;
+            s += 0.5f * (s_wz[rr - 1][zz] * C.inv_r_half[i - 1] + s_wz[rr][zz] * C.inv_r_half[i]);
+            S.trz[c] += s;
+            const float w = s_wr[rr][zz];
+            if (C.ar_int[i] != 0.f) S.psi_w[0][c] = w + C.br_int[i] * S.psi[0][c];
+            if (C.az_int[j] != 0.f) S.psi_w[1][c] = w + C.bz_int[j] * S.psi[1][c];
+        }
+        {
+            const float w = s_wz[rr][zz];
+            if (C.ar_half[i] != 0.f) S.psi_w[2][c] = w + C.br_half[i] * S.psi[2][c];
+            if (C.az_half[j] != 0.f) S.psi_w[3][c] = w + C.bz_half[j] * S.psi[3][c];
+        }
     }
 }
 

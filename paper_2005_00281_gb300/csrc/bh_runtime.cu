@@ -218,6 +218,28 @@ void prof_end(bh_model* m, size_t i)
 
 dim3 block2d() { return dim3(32, 8); }
 dim3 grid2d(int nr, int nz) { return dim3((nz + 31) / 32, (nr + 7) / 8); }
+// grid of the tiled stepping kernels: kTR x kTZ nodes per block
+dim3 grid_tiles(int nr, int nz) { return dim3((nz + kTZ - 1) / kTZ, (nr + kTR - 1) / kTR); }
+
+// Launch a stepping kernel with programmatic stream serialization: its
+// blocks may be scheduled while the previous kernel drains and wait in
+// griddepcontrol.wait for its results.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream,
+                       Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 bh_status rebuild_coefficients(bh_model* m)
 {
@@ -362,7 +384,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         return fail(nullptr, BH_ERR_INVALID_ARG, "NULL argument or nshots <= 0");
     const bh_grid_desc& g = *grid;
     if (g.nr < 4 || nz_global < 4 || g.nt < 1 || g.npml_r < 0 || g.npml_z < 0 ||
-        g.npml_r >= g.nr || !(g.dr > 0) || !(g.dz > 0) || !(g.dt > 0) || g.f0 < 0 ||
+        g.nr - g.npml_r < 4 || !(g.dr > 0) || !(g.dz > 0) || !(g.dt > 0) || g.f0 < 0 ||
         g.nz != nz_global)
         return fail(nullptr, BH_ERR_INVALID_ARG, "bad grid description");
     if (g.snapshot_precision != 0)
@@ -492,17 +514,16 @@ bh_status bh_forward(bh_model* m, const float* wavelet, float* seis)
         q.seis = seis + seis_per_shot * s;
         q.nt = gd.nt;
         q.hist = sd.d_hist;
-        const dim3 grd = grid2d(gd.nr, sd.nz), blk = block2d();
+        const dim3 grd = grid_tiles(gd.nr, sd.nz), blk = block2d();
         for (int n = 0; n < gd.nt; ++n) {
             q.n = n;
             size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
-            k_fwd_vel<<<grd, blk, 0, m->stream>>>(g, C, S);
+            BH_CUDA(m, launch_pdl(k_fwd_vel, grd, blk, m->stream, g, C, S));
             prof_end(m, e);
             e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
-            k_fwd_stress<<<grd, blk, 0, m->stream>>>(g, C, S, q);
+            BH_CUDA(m, launch_pdl(k_fwd_stress, grd, blk, m->stream, g, C, S, q));
             prof_end(m, e);
         }
-        BH_LAUNCH(m);
     }
     m->have_forward = true;
     m->have_gradient = false;
@@ -563,6 +584,7 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
         q.H_munn = m->d_H + nw;
         q.H_murz = m->d_H + 2 * nw;
         const dim3 grd = grid2d(gd.nr, sd.nz), blk = block2d();
+        const dim3 grt = grid_tiles(gd.nr, sd.nz);
         q.n = gd.nt - 1;
         k_adj_inject<<<(sd.nz + 127) / 128, 128, 0, m->stream>>>(g, make_state(m, 0), q,
                                                                  sd.nrec);
@@ -571,14 +593,13 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
             q.n = n;
             StateK S = make_state(m, parity);
             size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
-            k_adj_stress<<<grd, blk, 0, m->stream>>>(g, C, S, q);
+            BH_CUDA(m, launch_pdl(k_adj_stress, grt, blk, m->stream, g, C, S, q));
             prof_end(m, e);
             e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
-            k_adj_vel<<<grd, blk, 0, m->stream>>>(g, C, S, q);
+            BH_CUDA(m, launch_pdl(k_adj_vel, grt, blk, m->stream, g, C, S, q));
             prof_end(m, e);
             parity ^= 1;
         }
-        BH_LAUNCH(m);
         k_finalize<<<grd, blk, 0, m->stream>>>(g, C, q, f);
         BH_LAUNCH(m);
     }
