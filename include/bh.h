@@ -201,7 +201,9 @@ enum {
     BH_KERNEL_FWD_STRESS = 1,  /* stress half-step, Eq. 2 lines 3-6            */
     BH_KERNEL_ADJ_STRESS = 2,  /* transposed stress step + Eq. 7 / Eq. 8        */
     BH_KERNEL_ADJ_VEL = 3,     /* transposed velocity step                     */
-    BH_KERNEL_COUNT = 4
+    BH_KERNEL_FWD_PERSIST = 4, /* persistent forward: all steps of one shot     */
+    BH_KERNEL_ADJ_PERSIST = 5, /* persistent adjoint + correlation, one shot     */
+    BH_KERNEL_COUNT = 6
 };
 bh_status bh_profile_enable(bh_model* model, int every);
 bh_status bh_profile_read(bh_model* model, int kernel, double* total_ms, long* launches);
@@ -231,6 +233,28 @@ bh_status bh_profile_reset(bh_model* model);
 #define BH_NOALLOC_MAX_SAMPLES 33554432 /* 8192 blocks x 4096 samples */
 bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_obs,
                                      float* resid, size_t n, double* J, void* stream);
+
+/*
+ * Execution options (the paper has no counterpart).
+ *   "persistent"      1 (default where the device supports cooperative
+ *                     launch): one cooperative launch runs every time step
+ *                     of a shot, with a bounded grid barrier between half
+ *                     steps; 0: one kernel launch per half-step.  Both give
+ *                     bit-identical results.
+ *   "barrier_timeout_ms"  wall-clock limit of one barrier wait (default
+ *                     2000).  A wait that runs out sets a device error flag,
+ *                     every block returns, and bh_forward /
+ *                     bh_adjoint_gradient return BH_ERR_TIMEOUT; the CUDA
+ *                     context stays usable.
+ *   "barrier_extra_arrivals"  test knob: the barrier waits for this many
+ *                     arrivals beyond the blocks launched, so every wait
+ *                     runs out (default 0).
+ * In persistent mode bh_forward and bh_adjoint_gradient synchronise the
+ * stream once per shot to read the barrier status.
+ * Errors: BH_ERR_INVALID_ARG (unknown key, value out of range),
+ *   BH_ERR_UNSUPPORTED (persistent mode without cooperative launch).
+ */
+bh_status bh_set_option(bh_model* model, const char* key, double value);
 
 /* Static description of a status code. */
 const char* bh_status_string(bh_status status);

@@ -24,9 +24,9 @@ EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
            "bh_residual_misfit", "bh_adjoint_gradient", "bh_get_hessian", "bh_precondition",
            "bh_update", "bh_get_model", "bh_status_string", "bh_last_error",
            "bh_profile_enable", "bh_profile_read", "bh_profile_reset",
-           "bh_residual_misfit_noalloc")
+           "bh_residual_misfit_noalloc", "bh_set_option")
 NOALLOC_MAX_SAMPLES = 33554432
-KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel")
+KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel", "fwd_persist", "adj_persist")
 
 
 class BhError(RuntimeError):
@@ -97,6 +97,8 @@ def load_library(path: str | None = None):
     lib.bh_profile_read.restype = st
     lib.bh_profile_reset.argtypes = [vp]
     lib.bh_profile_reset.restype = st
+    lib.bh_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_double]
+    lib.bh_set_option.restype = st
     lib.bh_residual_misfit_noalloc.argtypes = [vp, vp, vp, ctypes.c_size_t,
                                                ctypes.POINTER(ctypes.c_double), vp]
     lib.bh_residual_misfit_noalloc.restype = st
@@ -235,6 +237,10 @@ class Model:
         self._rc(self.lib.bh_update(self.h, _ptr(g_lam), _ptr(g_mu), float(kappa), alpha,
                                     _ptr(vp), _ptr(vs)))
         return (alpha[0], alpha[1]), vp, vs
+
+    def set_option(self, key, value):
+        """bh_set_option: "persistent", "barrier_timeout_ms", "barrier_extra_arrivals"."""
+        self._rc(self.lib.bh_set_option(self.h, key.encode(), float(value)))
 
     def profile(self, every):
         """Sample kernel timing on every every-th step (0 = off)."""

@@ -99,15 +99,24 @@ __device__ __forceinline__ void kahan_add(float2* __restrict__ acc, size_t k, fl
 
 // ------------------------------------------------------------- tiling
 //
-// Every stepping kernel works on a tile of TR x TZ nodes (16 rows of r by 32
-// columns of z; 256 threads, each thread two rows 8 apart so that a warp
-// always covers 32 consecutive z) and first stages what its stencils read
-// from the tile plus a 2-node halo into shared memory, with the axis mirror
-// and the zero edges already applied.  The adjoint kernels then build the
-// transposed-stencil coefficients once per staged node.
+// Every stepping kernel works on tiles of kTR x kTZ nodes (16 rows of r by
+// 32 columns of z).  A block of 256 threads (8 warps) first stages what the
+// tile's stencils read, tile plus a 2-node halo, into shared memory (warp w
+// stages rows w, w+8, w+16, one row per pass so that row-level decisions --
+// axis mirror, outer edge -- are warp-uniform), with the mirror and the zero
+// edges applied; then warp w computes rows w and w+8 of the tile, one column
+// per lane.  The adjoint tiles also build the transposed-stencil
+// coefficients once per staged node.
+//
+// The same tile functions serve two launch forms: one kernel per half-step
+// (one tile per block), and one persistent cooperative kernel per shot that
+// runs every time step, with a bounded grid barrier between half-steps.
+// State written inside a launch is read with ld.global.cg (L2, not the
+// SM-private L1, which other SMs' writes do not update).
 constexpr int kTZ = 32, kTR = 16, kH = 2;
-constexpr int kSZ = kTZ + 2 * kH, kSR = kTR + 2 * kH, kNS = kSZ * kSR;
+constexpr int kSZ = kTZ + 2 * kH, kSR = kTR + 2 * kH;
 constexpr int kThreads = 256;
+typedef float Tile[kSR][kSZ];
 
 // Programmatic dependent launch: a kernel may be scheduled while its
 // predecessor drains; it must wait here before touching the predecessor's
@@ -118,78 +127,39 @@ __device__ __forceinline__ void pdl_launch_dependents()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// model value at window cell (i, j), i and j in range
-__device__ __forceinline__ float ldm(const float* __restrict__ f, int i, int j, const WinK& g)
+__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+
+// Stage the tile's rows [i0-2, i0+18) x columns [j0-2, j0+34) of a window
+// field.  EVEN: half-r field (cells, v_z), mirror f[-1-k] = f[k].  ODD:
+// integer-r field (v_r, trz), f[-k] = -f[k], f[0] = 0.  Zero beyond nr and
+// outside 0 <= z < nz.
+enum { EVEN = 0, ODD = 1 };
+template <int KIND>
+__device__ __forceinline__ void stage(Tile& s, const float* __restrict__ f, int i0, int j0,
+                                      const WinK& g)
 {
-    return f[(size_t)i * g.nzg + g.z0 + j];
+    const int lane = threadIdx.x;
+    for (int rr = threadIdx.y; rr < kSR; rr += 8) {
+        int i = i0 - kH + rr;
+        float sg = 1.f;
+        if (KIND == EVEN) {
+            if (i < 0) i = -1 - i;
+        } else {
+            if (i < 0) { i = -i; sg = -1.f; }
+            if (i == 0) sg = 0.f;
+        }
+        const bool live = i < g.nr && sg != 0.f;
+        const float* row = f + (live ? i * g.P : 0);
+        int j = j0 - kH + lane;
+        s[rr][lane] = (live && j >= 0 && j < g.nz) ? sg * ldcg(row + j) : 0.f;
+        if (lane < kSZ - 32) {
+            j += 32;
+            s[rr][lane + 32] = (live && j < g.nz) ? sg * ldcg(row + j) : 0.f;
+        }
+    }
 }
 
 // ------------------------------------------------------- forward: Eq. 2
-
-// Velocity half-step: Eq. 2 lines 1-2 with the C-PML memories 0..3.
-__global__ void __launch_bounds__(kThreads) k_fwd_vel(WinK g, CoefK C, StateK S)
-{
-    __shared__ float s_rr[kSR][kSZ], s_tt[kSR][kSZ], s_rz[kSR][kSZ], s_zz[kSR][kSZ];
-    pdl_wait();
-    const int j0 = blockIdx.x * kTZ, i0 = blockIdx.y * kTR;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int k = tid; k < kNS; k += kThreads) {
-        const int rr = k / kSZ, zz = k - rr * kSZ;
-        const int i = i0 - kH + rr, j = j0 - kH + zz;
-        s_rr[rr][zz] = ld_h(S.trr, i, j, g);
-        s_tt[rr][zz] = ld_h(S.ttt, i, j, g);
-        s_rz[rr][zz] = ld_i(S.trz, i, j, g);
-        s_zz[rr][zz] = ld_h(S.tzz, i, j, g);
-    }
-    __syncthreads();
-    pdl_launch_dependents();
-    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
-    if (j >= g.nz) return;
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
-        if (i >= g.nr) break;
-        const size_t c = (size_t)i * g.P + j;
-        const size_t cg = (size_t)i * g.nzg + g.z0 + j;
-        if (i >= 1) {
-            float d_trr = d4(s_rr[rr][zz], s_rr[rr - 1][zz], s_rr[rr + 1][zz], s_rr[rr - 2][zz]) *
-                          g.inv_dr;
-            float d_trz = d4(s_rz[rr][zz], s_rz[rr][zz - 1], s_rz[rr][zz + 1], s_rz[rr][zz - 2]) *
-                          g.inv_dz;
-            float hoop = 0.5f * ((s_rr[rr - 1][zz] - s_tt[rr - 1][zz]) + (s_rr[rr][zz] - s_tt[rr][zz])) *
-                         C.inv_r_int[i];
-            float a = C.ar_int[i];
-            if (a != 0.f) {
-                float q = C.br_int[i] * S.psi[0][c] + a * d_trr;
-                S.psi_w[0][c] = q;
-                d_trr += q;
-            }
-            a = C.az_int[j];
-            if (a != 0.f) {
-                float q = C.bz_int[j] * S.psi[1][c] + a * d_trz;
-                S.psi_w[1][c] = q;
-                d_trz += q;
-            }
-            S.vr[c] += g.dt * C.bvr[cg] * (d_trr + d_trz + hoop);
-        }
-        float d_trz = d4(s_rz[rr + 1][zz], s_rz[rr][zz], s_rz[rr + 2][zz], s_rz[rr - 1][zz]) * g.inv_dr;
-        float d_tzz = d4(s_zz[rr][zz + 1], s_zz[rr][zz], s_zz[rr][zz + 2], s_zz[rr][zz - 1]) * g.inv_dz;
-        float hoop = 0.5f * (s_rz[rr][zz] + s_rz[rr + 1][zz]) * C.inv_r_half[i];
-        float a = C.ar_half[i];
-        if (a != 0.f) {
-            float q = C.br_half[i] * S.psi[2][c] + a * d_trz;
-            S.psi_w[2][c] = q;
-            d_trz += q;
-        }
-        a = C.az_half[j];
-        if (a != 0.f) {
-            float q = C.bz_half[j] * S.psi[3][c] + a * d_tzz;
-            S.psi_w[3][c] = q;
-            d_tzz += q;
-        }
-        S.vz[c] += g.dt * bvz_at(C, g, i, j) * (d_trz + d_tzz + hoop);
-    }
-}
 
 struct SrcRecK {
     int src_c;            // window state index of the source cell
@@ -201,52 +171,109 @@ struct SrcRecK {
     float* hist;          // [nt][2][nr*P] or nullptr
 };
 
-// Stress half-step: Eq. 2 lines 3-6 with the C-PML memories 4..7, source
-// injection into the three normal stresses, pressure recording, and the
-// store of v^{n+1/2} for the adjoint.
-__global__ void __launch_bounds__(kThreads) k_fwd_stress(WinK g, CoefK C, StateK S, SrcRecK q)
+struct FwdSmem {
+    Tile a, b, c, d;
+};
+
+// Velocity half-step of one tile: Eq. 2 lines 1-2 with the C-PML memories 0..3.
+__device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
+                                             int i0, int j0, FwdSmem& sm)
 {
-    __shared__ float s_vr[kSR][kSZ], s_vz[kSR][kSZ];
-    pdl_wait();
-    const int j0 = blockIdx.x * kTZ, i0 = blockIdx.y * kTR;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int k = tid; k < kNS; k += kThreads) {
-        const int rr = k / kSZ, zz = k - rr * kSZ;
-        const int i = i0 - kH + rr, j = j0 - kH + zz;
-        s_vr[rr][zz] = ld_i(S.vr, i, j, g);
-        s_vz[rr][zz] = ld_h(S.vz, i, j, g);
-    }
+    Tile &s_rr = sm.a, &s_tt = sm.b, &s_rz = sm.c, &s_zz = sm.d;
     __syncthreads();
-    pdl_launch_dependents();
+    stage<EVEN>(s_rr, S.trr, i0, j0, g);
+    stage<EVEN>(s_tt, S.ttt, i0, j0, g);
+    stage<ODD>(s_rz, S.trz, i0, j0, g);
+    stage<EVEN>(s_zz, S.tzz, i0, j0, g);
+    __syncthreads();
     const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
     if (j >= g.nz) return;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
         if (i >= g.nr) break;
-        const size_t c = (size_t)i * g.P + j;
+        const int c = i * g.P + j;
+        const size_t cg = (size_t)i * g.nzg + g.z0 + j;
+        if (i >= 1) {
+            float d_trr = d4(s_rr[rr][zz], s_rr[rr - 1][zz], s_rr[rr + 1][zz], s_rr[rr - 2][zz]) *
+                          g.inv_dr;
+            float d_trz = d4(s_rz[rr][zz], s_rz[rr][zz - 1], s_rz[rr][zz + 1], s_rz[rr][zz - 2]) *
+                          g.inv_dz;
+            float hoop = 0.5f * ((s_rr[rr - 1][zz] - s_tt[rr - 1][zz]) + (s_rr[rr][zz] - s_tt[rr][zz])) *
+                         C.inv_r_int[i];
+            float a = C.ar_int[i];
+            if (a != 0.f) {
+                float q = C.br_int[i] * ldcg(S.psi[0] + c) + a * d_trr;
+                S.psi_w[0][c] = q;
+                d_trr += q;
+            }
+            a = C.az_int[j];
+            if (a != 0.f) {
+                float q = C.bz_int[j] * ldcg(S.psi[1] + c) + a * d_trz;
+                S.psi_w[1][c] = q;
+                d_trz += q;
+            }
+            S.vr[c] = ldcg(S.vr + c) + g.dt * __ldg(C.bvr + cg) * (d_trr + d_trz + hoop);
+        }
+        float d_trz = d4(s_rz[rr + 1][zz], s_rz[rr][zz], s_rz[rr + 2][zz], s_rz[rr - 1][zz]) * g.inv_dr;
+        float d_tzz = d4(s_zz[rr][zz + 1], s_zz[rr][zz], s_zz[rr][zz + 2], s_zz[rr][zz - 1]) * g.inv_dz;
+        float hoop = 0.5f * (s_rz[rr][zz] + s_rz[rr + 1][zz]) * C.inv_r_half[i];
+        float a = C.ar_half[i];
+        if (a != 0.f) {
+            float q = C.br_half[i] * ldcg(S.psi[2] + c) + a * d_trz;
+            S.psi_w[2][c] = q;
+            d_trz += q;
+        }
+        a = C.az_half[j];
+        if (a != 0.f) {
+            float q = C.bz_half[j] * ldcg(S.psi[3] + c) + a * d_tzz;
+            S.psi_w[3][c] = q;
+            d_tzz += q;
+        }
+        S.vz[c] = ldcg(S.vz + c) + g.dt * bvz_at(C, g, i, j) * (d_trz + d_tzz + hoop);
+    }
+}
+
+// Stress half-step of one tile: Eq. 2 lines 3-6 with the C-PML memories
+// 4..7, source injection into the three normal stresses, pressure
+// recording, and the store of v^{n+1/2} for the adjoint.
+__device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
+                                                const SrcRecK& q, int i0, int j0, FwdSmem& sm)
+{
+    Tile &s_vr = sm.a, &s_vz = sm.b;
+    __syncthreads();
+    stage<ODD>(s_vr, S.vr, i0, j0, g);
+    stage<EVEN>(s_vz, S.vz, i0, j0, g);
+    __syncthreads();
+    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
+    if (j >= g.nz) return;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
+        if (i >= g.nr) break;
+        const int c = i * g.P + j;
         const size_t cg = (size_t)i * g.nzg + g.z0 + j;
         float d_vr = d4(s_vr[rr + 1][zz], s_vr[rr][zz], s_vr[rr + 2][zz], s_vr[rr - 1][zz]) * g.inv_dr;
         float vr_r = 0.5f * (s_vr[rr][zz] + s_vr[rr + 1][zz]) * C.inv_r_half[i];
         float d_vz = d4(s_vz[rr][zz], s_vz[rr][zz - 1], s_vz[rr][zz + 1], s_vz[rr][zz - 2]) * g.inv_dz;
         float a = C.ar_half[i];
         if (a != 0.f) {
-            float w = C.br_half[i] * S.psi[4][c] + a * d_vr;
+            float w = C.br_half[i] * ldcg(S.psi[4] + c) + a * d_vr;
             S.psi_w[4][c] = w;
             d_vr += w;
         }
         a = C.az_int[j];
         if (a != 0.f) {
-            float w = C.bz_int[j] * S.psi[5][c] + a * d_vz;
+            float w = C.bz_int[j] * ldcg(S.psi[5] + c) + a * d_vz;
             S.psi_w[5][c] = w;
             d_vz += w;
         }
-        const float lam = C.lam[cg];
-        const float l2m = lam + 2.f * C.mu[cg];
-        float trr = S.trr[c] + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
-        float ttt = S.ttt[c] + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
-        float tzz = S.tzz[c] + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
-        if ((int)c == q.src_c) {
+        const float lam = __ldg(C.lam + cg);
+        const float l2m = lam + 2.f * __ldg(C.mu + cg);
+        float trr = ldcg(S.trr + c) + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
+        float ttt = ldcg(S.ttt + c) + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
+        float tzz = ldcg(S.tzz + c) + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
+        if (c == q.src_c) {
             float inj = q.src_scale * q.wavelet[q.n];
             trr += inj;
             ttt += inj;
@@ -266,23 +293,139 @@ __global__ void __launch_bounds__(kThreads) k_fwd_stress(WinK g, CoefK C, StateK
                           g.inv_dr;
             a = C.az_half[j];
             if (a != 0.f) {
-                float w = C.bz_half[j] * S.psi[6][c] + a * d_vrz;
+                float w = C.bz_half[j] * ldcg(S.psi[6] + c) + a * d_vrz;
                 S.psi_w[6][c] = w;
                 d_vrz += w;
             }
             a = C.ar_int[i];
             if (a != 0.f) {
-                float w = C.br_int[i] * S.psi[7][c] + a * d_vzr;
+                float w = C.br_int[i] * ldcg(S.psi[7] + c) + a * d_vzr;
                 S.psi_w[7][c] = w;
                 d_vzr += w;
             }
-            S.trz[c] += g.dt * muh_at(C, g, i, j) * (d_vrz + d_vzr);
+            S.trz[c] = ldcg(S.trz + c) + g.dt * muh_at(C, g, i, j) * (d_vrz + d_vzr);
         }
         if (q.hist) {
             float* h = q.hist + (size_t)q.n * 2 * g.nr * g.P;
             h[c] = s_vr[rr][zz];
-            h[(size_t)g.nr * g.P + c] = s_vz[rr][zz];
+            h[g.nr * g.P + c] = s_vz[rr][zz];
         }
+    }
+}
+
+__device__ __forceinline__ void tile_origin(const WinK& g, int t, int* i0, int* j0)
+{
+    const int ntz = (g.nz + kTZ - 1) / kTZ;
+    *i0 = (t / ntz) * kTR;
+    *j0 = (t % ntz) * kTZ;
+}
+
+__device__ __forceinline__ int tile_count(const WinK& g)
+{
+    return ((g.nz + kTZ - 1) / kTZ) * ((g.nr + kTR - 1) / kTR);
+}
+
+__global__ void __launch_bounds__(kThreads) k_fwd_vel(WinK g, CoefK C, StateK S)
+{
+    __shared__ FwdSmem sm;
+    pdl_wait();
+    int i0, j0;
+    tile_origin(g, blockIdx.x, &i0, &j0);
+    fwd_vel_tile(g, C, S, i0, j0, sm);
+    pdl_launch_dependents();
+}
+
+__global__ void __launch_bounds__(kThreads) k_fwd_stress(WinK g, CoefK C, StateK S, SrcRecK q)
+{
+    __shared__ FwdSmem sm;
+    pdl_wait();
+    int i0, j0;
+    tile_origin(g, blockIdx.x, &i0, &j0);
+    fwd_stress_tile(g, C, S, q, i0, j0, sm);
+    pdl_launch_dependents();
+}
+
+// ------------------------------------------------- bounded grid barrier
+
+struct BarK {
+    unsigned* count;               // arrivals in the current generation
+    unsigned* gen;                 // generation number
+    int* err;                      // 1 once any wait gave up
+    unsigned expected;             // arrivals that complete a generation
+    unsigned long long timeout_ns; // give up after this long
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All blocks of a cooperative launch meet here.  Returns false, in every
+// thread of the block, when the wait ran past timeout_ns or another block
+// reported that it did; the caller then returns from the kernel, and the
+// host reads the error flag.  Writes before the barrier are visible to
+// ld.global.cg loads after it.
+__device__ bool grid_barrier(const BarK& b)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned* vgen = b.gen;
+        volatile int* verr = b.err;
+        int ok = 1;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(b.count, 1u) + 1u;
+        if (arrived == b.expected) {
+            atomicExch(b.count, 0u);
+            __threadfence();
+            atomicAdd(b.gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            // second bound, independent of the timer: every pass costs at
+            // least one L2 round trip (hundreds of ns)
+            const unsigned long long max_spins = b.timeout_ns / 64ull + 1024ull;
+            unsigned long long spins = 0;
+            while (*vgen == g0) {
+                if (*verr) { ok = 0; break; }
+                if (global_ns() - t0 > b.timeout_ns || ++spins > max_spins) {
+                    atomicExch(b.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*verr) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Every time step of one shot's forward modelling in one launch.
+__global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(WinK g, CoefK C, StateK S,
+                                                             SrcRecK q, BarK b)
+{
+    __shared__ FwdSmem sm;
+    const int nt_tiles = tile_count(g);
+    for (int n = 0; n < q.nt; ++n) {
+        for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
+            int i0, j0;
+            tile_origin(g, t, &i0, &j0);
+            fwd_vel_tile(g, C, S, i0, j0, sm);
+        }
+        if (!grid_barrier(b)) return;
+        q.n = n;
+        for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
+            int i0, j0;
+            tile_origin(g, t, &i0, &j0);
+            fwd_stress_tile(g, C, S, q, i0, j0, sm);
+        }
+        if (!grid_barrier(b)) return;
     }
 }
 
@@ -305,85 +448,108 @@ struct AdjK {
     float *H_lam, *H_munn, *H_murz;                 // [nr*P]
 };
 
-// Transpose of the stress step at reverse step n, fused with the gradient
-// correlations (Eq. 7, Eq. 8, and the density term).  S.{trr..trz} hold
-// dJ/dtau^{n+1}; S.{vr,vz} accumulate to dJ/dv^{n+1/2}; psi[4..7] are the
-// adjoint memories read side, psi_w[4..7] the write side.
-__global__ void __launch_bounds__(kThreads) k_adj_stress(WinK g, CoefK C, StateK S, AdjK q)
-{
-    // staged inputs: adjoint stresses, lambda, mu, mu_h, forward v^{n+1/2}
-    __shared__ float s_arr[kSR][kSZ], s_att[kSR][kSZ], s_azz[kSR][kSZ], s_arz[kSR][kSZ];
-    __shared__ float s_lam[kSR][kSZ], s_mu[kSR][kSZ], s_muh[kSR][kSZ];
-    __shared__ float s_fvr[kSR][kSZ], s_fvz[kSR][kSZ];
+struct AdjSmem {
+    // staged: adjoint stresses, lambda, mu, mu_h, forward v^{n+1/2}
+    Tile arr, att, azz, arz, lam, mu, muh, fvr, fvz;
     // transposed-stencil coefficients: on D_r v_r (x4), v_r/r (ytt), D_z v_z
-    // (x5) at cells; on D_z v_r (x6) and D_r v_z (x7) at trz nodes
-    __shared__ float s_x4[kSR][kSZ], s_ytt[kSR][kSZ], s_x5[kSR][kSZ], s_x6[kSR][kSZ],
-        s_x7[kSR][kSZ];
-    pdl_wait();
-    const int j0 = blockIdx.x * kTZ, i0 = blockIdx.y * kTR;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    const float* fvr = q.hist + (size_t)q.n * 2 * g.nr * g.P;
-    const float* fvz = fvr + (size_t)g.nr * g.P;
-    const float dt = g.dt;
+    // (x5) at cells; on D_z v_r (x6) and D_r v_z (x7) at trz nodes.  The
+    // velocity-step tile reuses x4..x7, ytt, arr as W_r, W_z, X0..X3.
+    Tile x4, ytt, x5, x6, x7;
+};
 
-    for (int k = tid; k < kNS; k += kThreads) {
-        const int rr = k / kSZ, zz = k - rr * kSZ;
-        const int i = i0 - kH + rr, j = j0 - kH + zz;
-        s_arr[rr][zz] = ld_h(S.trr, i, j, g);
-        s_att[rr][zz] = ld_h(S.ttt, i, j, g);
-        s_azz[rr][zz] = ld_h(S.tzz, i, j, g);
-        s_arz[rr][zz] = ld_i(S.trz, i, j, g);
-        s_fvr[rr][zz] = ld_i(fvr, i, j, g);
-        s_fvz[rr][zz] = ld_h(fvz, i, j, g);
-        float lam = 0.f, mu = 0.f, mh = 0.f;
-        if (j >= 0 && j < g.nz) {
-            const int ic = i < 0 ? -1 - i : i;  // cells: even about the axis
-            const int it = i < 0 ? -i : i;      // trz nodes: mirror row of an integer node
-            if (ic < g.nr) {
-                lam = ldm(C.lam, ic, j, g);
-                mu = ldm(C.mu, ic, j, g);
-            }
-            if (it >= 1 && it < g.nr) mh = muh_at(C, g, it, j);
+// stage a model field over the tile: cells (CELL) mirror evenly; trz nodes
+// (harmonic mu) mirror about the axis row to row |i| with the window's own
+// last-row rule
+enum { CELL = 0, SHEAR = 1 };
+template <int KIND>
+__device__ __forceinline__ void stage_model(Tile& s, const float* __restrict__ f, const CoefK& C,
+                                            int i0, int j0, const WinK& g)
+{
+    const int lane = threadIdx.x;
+    for (int rr = threadIdx.y; rr < kSR; rr += 8) {
+        int i = i0 - kH + rr;
+        if (KIND == CELL) {
+            if (i < 0) i = -1 - i;
+        } else {
+            if (i < 0) i = -i;
         }
-        s_lam[rr][zz] = lam;
-        s_mu[rr][zz] = mu;
-        s_muh[rr][zz] = mh;
+        const bool live = i < g.nr && (KIND == CELL || i >= 1);
+        for (int h = 0; h < 2; ++h) {
+            const int zz = lane + 32 * h;
+            if (zz >= kSZ) break;
+            const int j = j0 - kH + zz;
+            float v = 0.f;
+            if (live && j >= 0 && j < g.nz)
+                v = (KIND == CELL) ? __ldg(f + (size_t)i * g.nzg + g.z0 + j) : muh_at(C, g, i, j);
+            s[rr][zz] = v;
+        }
     }
+}
+
+// Transpose of the stress step of one tile at reverse step n, fused with
+// the gradient correlations (Eq. 7, Eq. 8, and the density term).
+// S.{trr..trz} hold dJ/dtau^{n+1}; S.{vr,vz} accumulate to dJ/dv^{n+1/2};
+// psi[4..7] are the adjoint memories read side, psi_w[4..7] the write side.
+__device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
+                                                const AdjK& q, int i0, int j0, AdjSmem& sm)
+{
+    const float* fvr = q.hist + (size_t)q.n * 2 * g.nr * g.P;
+    const float* fvz = fvr + g.nr * g.P;
+    const float dt = g.dt;
     __syncthreads();
-    for (int k = tid; k < kNS; k += kThreads) {
-        const int rr = k / kSZ, zz = k - rr * kSZ;
-        const int i = i0 - kH + rr, j = j0 - kH + zz;
-        float x4 = 0.f, ytt = 0.f, x5 = 0.f, x6 = 0.f, x7 = 0.f;
-        if (j >= 0 && j < g.nz && i < g.nr) {
+    stage<EVEN>(sm.arr, S.trr, i0, j0, g);
+    stage<EVEN>(sm.att, S.ttt, i0, j0, g);
+    stage<EVEN>(sm.azz, S.tzz, i0, j0, g);
+    stage<ODD>(sm.arz, S.trz, i0, j0, g);
+    stage<ODD>(sm.fvr, fvr, i0, j0, g);
+    stage<EVEN>(sm.fvz, fvz, i0, j0, g);
+    stage_model<CELL>(sm.lam, C.lam, C, i0, j0, g);
+    stage_model<CELL>(sm.mu, C.mu, C, i0, j0, g);
+    stage_model<SHEAR>(sm.muh, nullptr, C, i0, j0, g);
+    __syncthreads();
+    {
+        const int lane = threadIdx.x;
+        for (int rr = threadIdx.y; rr < kSR; rr += 8) {
+            const int i = i0 - kH + rr;
             const int ic = i < 0 ? -1 - i : i;
-            const float lam = s_lam[rr][zz], l2m = lam + 2.f * s_mu[rr][zz];
-            const float arr = s_arr[rr][zz], att = s_att[rr][zz], azz = s_azz[rr][zz];
-            x4 = dt * (l2m * arr + lam * (att + azz));
-            ytt = dt * (l2m * att + lam * (arr + azz));
-            x5 = dt * (l2m * azz + lam * (arr + att));
-            float a = C.ar_half[ic];
-            if (a != 0.f) x4 = x4 + a * (x4 + C.br_half[ic] * S.psi[4][(size_t)ic * g.P + j]);
-            a = C.az_int[j];
-            if (a != 0.f) x5 = x5 + a * (x5 + C.bz_int[j] * S.psi[5][(size_t)ic * g.P + j]);
-            // trz node: the staged values are already odd about the axis
-            const float y = dt * s_muh[rr][zz] * s_arz[rr][zz];
-            x6 = y;
-            x7 = y;
-            if (i >= 1) {
-                a = C.az_half[j];
-                if (a != 0.f) x6 = y + a * (y + C.bz_half[j] * S.psi[6][(size_t)i * g.P + j]);
-                a = C.ar_int[i];
-                if (a != 0.f) x7 = y + a * (y + C.br_int[i] * S.psi[7][(size_t)i * g.P + j]);
+            const bool row_cell = i < g.nr;
+            const float arh = row_cell ? C.ar_half[ic] : 0.f;
+            const float brh = row_cell ? C.br_half[ic] : 0.f;
+            const float ari = (i >= 1 && i < g.nr) ? C.ar_int[i] : 0.f;
+            const float bri = (i >= 1 && i < g.nr) ? C.br_int[i] : 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int zz = lane + 32 * h;
+                if (zz >= kSZ) break;
+                const int j = j0 - kH + zz;
+                float x4 = 0.f, ytt = 0.f, x5 = 0.f, x6 = 0.f, x7 = 0.f;
+                if (j >= 0 && j < g.nz && row_cell) {
+                    const float lam = sm.lam[rr][zz], l2m = lam + 2.f * sm.mu[rr][zz];
+                    const float arr = sm.arr[rr][zz], att = sm.att[rr][zz], azz = sm.azz[rr][zz];
+                    x4 = dt * (l2m * arr + lam * (att + azz));
+                    ytt = dt * (l2m * att + lam * (arr + azz));
+                    x5 = dt * (l2m * azz + lam * (arr + att));
+                    if (arh != 0.f) x4 = x4 + arh * (x4 + brh * ldcg(S.psi[4] + ic * g.P + j));
+                    const float azi = C.az_int[j];
+                    if (azi != 0.f) x5 = x5 + azi * (x5 + C.bz_int[j] * ldcg(S.psi[5] + ic * g.P + j));
+                    // trz node: the staged values are already odd about the axis
+                    const float y = dt * sm.muh[rr][zz] * sm.arz[rr][zz];
+                    x6 = y;
+                    x7 = y;
+                    if (i >= 1) {
+                        const float azh = C.az_half[j];
+                        if (azh != 0.f) x6 = y + azh * (y + C.bz_half[j] * ldcg(S.psi[6] + i * g.P + j));
+                        if (ari != 0.f) x7 = y + ari * (y + bri * ldcg(S.psi[7] + i * g.P + j));
+                    }
+                }
+                sm.x4[rr][zz] = x4;
+                sm.ytt[rr][zz] = ytt;
+                sm.x5[rr][zz] = x5;
+                sm.x6[rr][zz] = x6;
+                sm.x7[rr][zz] = x7;
             }
         }
-        s_x4[rr][zz] = x4;
-        s_ytt[rr][zz] = ytt;
-        s_x5[rr][zz] = x5;
-        s_x6[rr][zz] = x6;
-        s_x7[rr][zz] = x7;
     }
     __syncthreads();
-    pdl_launch_dependents();
 
     const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
     if (j >= g.nz) return;
@@ -391,118 +557,124 @@ __global__ void __launch_bounds__(kThreads) k_adj_stress(WinK g, CoefK C, StateK
     for (int p = 0; p < 2; ++p) {
         const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
         if (i >= g.nr) break;
-        const size_t c = (size_t)i * g.P + j;
+        const int c = i * g.P + j;
 
         // ---- gradient correlation with the forward strains of v^{n+1/2}
-        const float arr = s_arr[rr][zz], att = s_att[rr][zz], azz = s_azz[rr][zz];
+        const float arr = sm.arr[rr][zz], att = sm.att[rr][zz], azz = sm.azz[rr][zz];
         {
-            float err = d4(s_fvr[rr + 1][zz], s_fvr[rr][zz], s_fvr[rr + 2][zz], s_fvr[rr - 1][zz]) *
+            float err = d4(sm.fvr[rr + 1][zz], sm.fvr[rr][zz], sm.fvr[rr + 2][zz], sm.fvr[rr - 1][zz]) *
                         g.inv_dr;
-            float ett = 0.5f * (s_fvr[rr][zz] + s_fvr[rr + 1][zz]) * C.inv_r_half[i];
-            float ezz = d4(s_fvz[rr][zz], s_fvz[rr][zz - 1], s_fvz[rr][zz + 1], s_fvz[rr][zz - 2]) *
+            float ett = 0.5f * (sm.fvr[rr][zz] + sm.fvr[rr + 1][zz]) * C.inv_r_half[i];
+            float ezz = d4(sm.fvz[rr][zz], sm.fvz[rr][zz - 1], sm.fvz[rr][zz + 1], sm.fvz[rr][zz - 2]) *
                         g.inv_dz;
             float div = err + ett + ezz;
             kahan_add(q.G_lam, c, dt * div * (arr + att + azz));
             kahan_add(q.G_munn, c, 2.f * dt * (err * arr + ett * att + ezz * azz));
-            q.H_lam[c] += dt * div * div;
-            q.H_munn[c] += 4.f * dt * (err * err + ett * ett + ezz * ezz);
+            q.H_lam[c] = ldcg(q.H_lam + c) + dt * div * div;
+            q.H_munn[c] = ldcg(q.H_munn + c) + 4.f * dt * (err * err + ett * ett + ezz * ezz);
             if (i >= 1) {
-                float gam = d4(s_fvr[rr][zz + 1], s_fvr[rr][zz], s_fvr[rr][zz + 2], s_fvr[rr][zz - 1]) *
+                float gam = d4(sm.fvr[rr][zz + 1], sm.fvr[rr][zz], sm.fvr[rr][zz + 2], sm.fvr[rr][zz - 1]) *
                                 g.inv_dz +
-                            d4(s_fvz[rr][zz], s_fvz[rr - 1][zz], s_fvz[rr + 1][zz], s_fvz[rr - 2][zz]) *
+                            d4(sm.fvz[rr][zz], sm.fvz[rr - 1][zz], sm.fvz[rr + 1][zz], sm.fvz[rr - 2][zz]) *
                                 g.inv_dr;
-                kahan_add(q.G_murz, c, dt * gam * s_arz[rr][zz]);
-                q.H_murz[c] += dt * gam * gam;
+                kahan_add(q.G_murz, c, dt * gam * sm.arz[rr][zz]);
+                q.H_murz[c] = ldcg(q.H_murz + c) + dt * gam * gam;
             }
         }
 
         // ---- transpose of the stress step into Av, and the density term
         if (i >= 1) {
-            float s = d4(s_x4[rr - 1][zz], s_x4[rr][zz], s_x4[rr - 2][zz], s_x4[rr + 1][zz]) * g.inv_dr;
-            s += 0.5f * (s_ytt[rr - 1][zz] * C.inv_r_half[i - 1] + s_ytt[rr][zz] * C.inv_r_half[i]);
-            s += d4(s_x6[rr][zz - 1], s_x6[rr][zz], s_x6[rr][zz - 2], s_x6[rr][zz + 1]) * g.inv_dz;
-            float av = S.vr[c] + s;
+            float s = d4(sm.x4[rr - 1][zz], sm.x4[rr][zz], sm.x4[rr - 2][zz], sm.x4[rr + 1][zz]) * g.inv_dr;
+            s += 0.5f * (sm.ytt[rr - 1][zz] * C.inv_r_half[i - 1] + sm.ytt[rr][zz] * C.inv_r_half[i]);
+            s += d4(sm.x6[rr][zz - 1], sm.x6[rr][zz], sm.x6[rr][zz - 2], sm.x6[rr][zz + 1]) * g.inv_dz;
+            float av = ldcg(S.vr + c) + s;
             S.vr[c] = av;
-            float dv = s_fvr[rr][zz] - (q.n > 0 ? fvr[c - (size_t)2 * g.nr * g.P] : 0.f);
+            float dv = sm.fvr[rr][zz] - (q.n > 0 ? __ldg(fvr + c - (size_t)2 * g.nr * g.P) : 0.f);
             kahan_add(q.G_br, c, dv * av);
         }
         {
-            float s = d4(s_x5[rr][zz], s_x5[rr][zz + 1], s_x5[rr][zz - 1], s_x5[rr][zz + 2]) * g.inv_dz;
-            s += d4(s_x7[rr][zz], s_x7[rr + 1][zz], s_x7[rr - 1][zz], s_x7[rr + 2][zz]) * g.inv_dr;
-            float av = S.vz[c] + s;
+            float s = d4(sm.x5[rr][zz], sm.x5[rr][zz + 1], sm.x5[rr][zz - 1], sm.x5[rr][zz + 2]) * g.inv_dz;
+            s += d4(sm.x7[rr][zz], sm.x7[rr + 1][zz], sm.x7[rr - 1][zz], sm.x7[rr + 2][zz]) * g.inv_dr;
+            float av = ldcg(S.vz + c) + s;
             S.vz[c] = av;
-            float dv = s_fvz[rr][zz] - (q.n > 0 ? fvz[c - (size_t)2 * g.nr * g.P] : 0.f);
+            float dv = sm.fvz[rr][zz] - (q.n > 0 ? __ldg(fvz + c - (size_t)2 * g.nr * g.P) : 0.f);
             kahan_add(q.G_bz, c, dv * av);
         }
 
         // ---- adjoint memories of the stress step (own cell / own shear node)
         {
-            const float lam = s_lam[rr][zz], l2m = lam + 2.f * s_mu[rr][zz];
+            const float lam = sm.lam[rr][zz], l2m = lam + 2.f * sm.mu[rr][zz];
             if (C.ar_half[i] != 0.f)
-                S.psi_w[4][c] = dt * (l2m * arr + lam * (att + azz)) + C.br_half[i] * S.psi[4][c];
+                S.psi_w[4][c] = dt * (l2m * arr + lam * (att + azz)) + C.br_half[i] * ldcg(S.psi[4] + c);
             if (C.az_int[j] != 0.f)
-                S.psi_w[5][c] = dt * (l2m * azz + lam * (arr + att)) + C.bz_int[j] * S.psi[5][c];
+                S.psi_w[5][c] = dt * (l2m * azz + lam * (arr + att)) + C.bz_int[j] * ldcg(S.psi[5] + c);
             if (i >= 1) {
-                const float y = dt * s_muh[rr][zz] * s_arz[rr][zz];
-                if (C.az_half[j] != 0.f) S.psi_w[6][c] = y + C.bz_half[j] * S.psi[6][c];
-                if (C.ar_int[i] != 0.f) S.psi_w[7][c] = y + C.br_int[i] * S.psi[7][c];
+                const float y = dt * sm.muh[rr][zz] * sm.arz[rr][zz];
+                if (C.az_half[j] != 0.f) S.psi_w[6][c] = y + C.bz_half[j] * ldcg(S.psi[6] + c);
+                if (C.ar_int[i] != 0.f) S.psi_w[7][c] = y + C.br_int[i] * ldcg(S.psi[7] + c);
             }
         }
     }
 }
 
-// Transpose of the velocity step at reverse step n: S.{vr,vz} hold
-// dJ/dv^{n+1/2}; S.{trr..trz} accumulate to dJ/dtau^n.  Then the residual
-// of step n-1 is injected at the receivers (transpose of the recording).
-__global__ void __launch_bounds__(kThreads) k_adj_vel(WinK g, CoefK C, StateK S, AdjK q)
+// Transpose of the velocity step of one tile at reverse step n: S.{vr,vz}
+// hold dJ/dv^{n+1/2}; S.{trr..trz} accumulate to dJ/dtau^n.  Then the
+// residual of step n-1 is injected at the receivers (transpose of the
+// recording).
+__device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
+                                             const AdjK& q, int i0, int j0, AdjSmem& sm)
 {
     // W = dt b Av at the velocity nodes (odd about the axis for v_r, even
     // for v_z), and the coefficients on the four stretched derivatives
-    __shared__ float s_wr[kSR][kSZ], s_wz[kSR][kSZ];
-    __shared__ float s_x0[kSR][kSZ], s_x1[kSR][kSZ], s_x2[kSR][kSZ], s_x3[kSR][kSZ];
-    pdl_wait();
-    const int j0 = blockIdx.x * kTZ, i0 = blockIdx.y * kTR;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int k = tid; k < kNS; k += kThreads) {
-        const int rr = k / kSZ, zz = k - rr * kSZ;
-        const int i = i0 - kH + rr, j = j0 - kH + zz;
-        float wr = 0.f, wz = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
-        if (j >= 0 && j < g.nz) {
-            // v_r node: odd extension, zero on the axis and beyond nr
-            const int ir = i < 0 ? -i : i;
-            if (ir >= 1 && ir < g.nr) {
-                const float sg = i < 0 ? -1.f : 1.f;
-                const size_t c = (size_t)ir * g.P + j;
-                const float w = g.dt * ldm(C.bvr, ir, j, g) * S.vr[c];
-                float a = C.ar_int[ir];
-                x0 = (a != 0.f) ? w + a * (w + C.br_int[ir] * S.psi[0][c]) : w;
-                a = C.az_int[j];
-                x1 = (a != 0.f) ? w + a * (w + C.bz_int[j] * S.psi[1][c]) : w;
-                wr = sg * w;
-                x0 *= sg;
-                x1 *= sg;
-            }
-            // v_z node: even extension, zero beyond nr
-            const int iz = i < 0 ? -1 - i : i;
-            if (iz < g.nr) {
-                const size_t c = (size_t)iz * g.P + j;
-                const float w = g.dt * bvz_at(C, g, iz, j) * S.vz[c];
-                float a = C.ar_half[iz];
-                x2 = (a != 0.f) ? w + a * (w + C.br_half[iz] * S.psi[2][c]) : w;
-                a = C.az_half[j];
-                x3 = (a != 0.f) ? w + a * (w + C.bz_half[j] * S.psi[3][c]) : w;
-                wz = w;
+    Tile &s_wr = sm.x4, &s_wz = sm.ytt, &s_x0 = sm.x5, &s_x1 = sm.x6, &s_x2 = sm.x7,
+         &s_x3 = sm.arr;
+    __syncthreads();
+    {
+        const int lane = threadIdx.x;
+        for (int rr = threadIdx.y; rr < kSR; rr += 8) {
+            const int i = i0 - kH + rr;
+            const int ir = i < 0 ? -i : i;       // v_r node mirrored row
+            const float sg = i < 0 ? -1.f : 1.f;
+            const bool rlive = ir >= 1 && ir < g.nr;
+            const int iz = i < 0 ? -1 - i : i;   // v_z node mirrored row
+            const bool zlive = iz < g.nr;
+            const float ari = rlive ? C.ar_int[ir] : 0.f, bri = rlive ? C.br_int[ir] : 0.f;
+            const float arh = zlive ? C.ar_half[iz] : 0.f, brh = zlive ? C.br_half[iz] : 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int zz = lane + 32 * h;
+                if (zz >= kSZ) break;
+                const int j = j0 - kH + zz;
+                float wr = 0.f, wz = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
+                if (j >= 0 && j < g.nz) {
+                    if (rlive) {
+                        const int c = ir * g.P + j;
+                        const float w = g.dt * __ldg(C.bvr + (size_t)ir * g.nzg + g.z0 + j) * ldcg(S.vr + c);
+                        x0 = (ari != 0.f) ? w + ari * (w + bri * ldcg(S.psi[0] + c)) : w;
+                        const float a = C.az_int[j];
+                        x1 = (a != 0.f) ? w + a * (w + C.bz_int[j] * ldcg(S.psi[1] + c)) : w;
+                        wr = sg * w;
+                        x0 *= sg;
+                        x1 *= sg;
+                    }
+                    if (zlive) {
+                        const int c = iz * g.P + j;
+                        const float w = g.dt * bvz_at(C, g, iz, j) * ldcg(S.vz + c);
+                        x2 = (arh != 0.f) ? w + arh * (w + brh * ldcg(S.psi[2] + c)) : w;
+                        const float a = C.az_half[j];
+                        x3 = (a != 0.f) ? w + a * (w + C.bz_half[j] * ldcg(S.psi[3] + c)) : w;
+                        wz = w;
+                    }
+                }
+                s_wr[rr][zz] = wr;
+                s_wz[rr][zz] = wz;
+                s_x0[rr][zz] = x0;
+                s_x1[rr][zz] = x1;
+                s_x2[rr][zz] = x2;
+                s_x3[rr][zz] = x3;
             }
         }
-        s_wr[rr][zz] = wr;
-        s_wz[rr][zz] = wz;
-        s_x0[rr][zz] = x0;
-        s_x1[rr][zz] = x1;
-        s_x2[rr][zz] = x2;
-        s_x3[rr][zz] = x3;
     }
     __syncthreads();
-    pdl_launch_dependents();
 
     const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
     if (j >= g.nz) return;
@@ -510,15 +682,15 @@ __global__ void __launch_bounds__(kThreads) k_adj_vel(WinK g, CoefK C, StateK S,
     for (int p = 0; p < 2; ++p) {
         const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
         if (i >= g.nr) break;
-        const size_t c = (size_t)i * g.P + j;
+        const int c = i * g.P + j;
         // cell (i,j); inv_r_int[0] is 0 and W_r vanishes on the axis
         float hoop = 0.5f * (s_wr[rr][zz] * C.inv_r_int[i] +
                              s_wr[rr + 1][zz] * (i + 1 < g.nr ? C.inv_r_int[i + 1] : 0.f));
         float arr = d4(s_x0[rr][zz], s_x0[rr + 1][zz], s_x0[rr - 1][zz], s_x0[rr + 2][zz]) * g.inv_dr;
         float azz = d4(s_x3[rr][zz - 1], s_x3[rr][zz], s_x3[rr][zz - 2], s_x3[rr][zz + 1]) * g.inv_dz;
-        float trr = S.trr[c] + arr + hoop;
-        float ttt = S.ttt[c] - hoop;
-        float tzz = S.tzz[c] + azz;
+        float trr = ldcg(S.trr + c) + arr + hoop;
+        float ttt = ldcg(S.ttt + c) - hoop;
+        float tzz = ldcg(S.tzz + c) + azz;
         if (i == 0 && q.n > 0) {
             int k = q.recmap[j];
             if (k >= 0) {
@@ -536,16 +708,64 @@ __global__ void __launch_bounds__(kThreads) k_adj_vel(WinK g, CoefK C, StateK S,
             float s = d4(s_x1[rr][zz], s_x1[rr][zz + 1], s_x1[rr][zz - 1], s_x1[rr][zz + 2]) * g.inv_dz;
             s += d4(s_x2[rr - 1][zz], s_x2[rr][zz], s_x2[rr - 2][zz], s_x2[rr + 1][zz]) * g.inv_dr;
             s += 0.5f * (s_wz[rr - 1][zz] * C.inv_r_half[i - 1] + s_wz[rr][zz] * C.inv_r_half[i]);
-            S.trz[c] += s;
+            S.trz[c] = ldcg(S.trz + c) + s;
             const float w = s_wr[rr][zz];
-            if (C.ar_int[i] != 0.f) S.psi_w[0][c] = w + C.br_int[i] * S.psi[0][c];
-            if (C.az_int[j] != 0.f) S.psi_w[1][c] = w + C.bz_int[j] * S.psi[1][c];
+            if (C.ar_int[i] != 0.f) S.psi_w[0][c] = w + C.br_int[i] * ldcg(S.psi[0] + c);
+            if (C.az_int[j] != 0.f) S.psi_w[1][c] = w + C.bz_int[j] * ldcg(S.psi[1] + c);
         }
         {
             const float w = s_wz[rr][zz];
-            if (C.ar_half[i] != 0.f) S.psi_w[2][c] = w + C.br_half[i] * S.psi[2][c];
-            if (C.az_half[j] != 0.f) S.psi_w[3][c] = w + C.bz_half[j] * S.psi[3][c];
+            if (C.ar_half[i] != 0.f) S.psi_w[2][c] = w + C.br_half[i] * ldcg(S.psi[2] + c);
+            if (C.az_half[j] != 0.f) S.psi_w[3][c] = w + C.bz_half[j] * ldcg(S.psi[3] + c);
         }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_adj_stress(WinK g, CoefK C, StateK S, AdjK q)
+{
+    __shared__ AdjSmem sm;
+    pdl_wait();
+    int i0, j0;
+    tile_origin(g, blockIdx.x, &i0, &j0);
+    adj_stress_tile(g, C, S, q, i0, j0, sm);
+    pdl_launch_dependents();
+}
+
+__global__ void __launch_bounds__(kThreads) k_adj_vel(WinK g, CoefK C, StateK S, AdjK q)
+{
+    __shared__ AdjSmem sm;
+    pdl_wait();
+    int i0, j0;
+    tile_origin(g, blockIdx.x, &i0, &j0);
+    adj_vel_tile(g, C, S, q, i0, j0, sm);
+    pdl_launch_dependents();
+}
+
+// Every reverse step of one shot in one launch.  S0 / S1 are the state
+// views of the two adjoint-memory banks (read bank 0 / write bank 1, and the
+// reverse); the banks swap every step.
+__global__ void __launch_bounds__(kThreads, 5) k_adj_persist(WinK g, CoefK C, StateK S0,
+                                                             StateK S1, AdjK q, BarK b)
+{
+    __shared__ AdjSmem sm;
+    const int nt_tiles = tile_count(g);
+    int parity = 0;
+    for (int n = q.nt - 1; n >= 0; --n) {
+        q.n = n;
+        const StateK& S = parity ? S1 : S0;
+        for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
+            int i0, j0;
+            tile_origin(g, t, &i0, &j0);
+            adj_stress_tile(g, C, S, q, i0, j0, sm);
+        }
+        if (!grid_barrier(b)) return;
+        for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
+            int i0, j0;
+            tile_origin(g, t, &i0, &j0);
+            adj_vel_tile(g, C, S, q, i0, j0, sm);
+        }
+        if (!grid_barrier(b)) return;
+        parity ^= 1;
     }
 }
 

@@ -50,6 +50,13 @@ struct bh_model {
     double* d_scal = nullptr;   // small device scalars
     bool have_forward = false, have_gradient = false;
     std::string err;
+    // persistent (one cooperative launch per shot and direction) or one
+    // launch per half-step; co-resident blocks of the persistent kernels
+    int persistent = 1;
+    int fwd_blocks = 0, adj_blocks = 0;
+    unsigned* d_bar = nullptr;          // barrier: count, generation, error flag
+    double barrier_timeout_ms = 2000.0;
+    int barrier_extra = 0;              // test knob: arrivals that never come
     // sampled kernel timing: events around every prof_every-th step's launches
     int prof_every = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -114,6 +121,7 @@ void free_model(bh_model* m)
     cudaFree(m->d_H);
     cudaFree(m->d_Hg);
     cudaFree(m->d_scal);
+    cudaFree(m->d_bar);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     delete m;
 }
@@ -218,8 +226,33 @@ void prof_end(bh_model* m, size_t i)
 
 dim3 block2d() { return dim3(32, 8); }
 dim3 grid2d(int nr, int nz) { return dim3((nz + 31) / 32, (nr + 7) / 8); }
-// grid of the tiled stepping kernels: kTR x kTZ nodes per block
-dim3 grid_tiles(int nr, int nz) { return dim3((nz + kTZ - 1) / kTZ, (nr + kTR - 1) / kTR); }
+// grid of the tiled stepping kernels: one block per kTR x kTZ tile
+int n_tiles(int nr, int nz) { return ((nz + kTZ - 1) / kTZ) * ((nr + kTR - 1) / kTR); }
+dim3 grid_tiles(int nr, int nz) { return dim3(n_tiles(nr, nz)); }
+
+BarK make_bar(const bh_model* m, int blocks)
+{
+    BarK b;
+    b.count = m->d_bar;
+    b.gen = m->d_bar + 1;
+    b.err = (int*)(m->d_bar + 2);
+    b.expected = (unsigned)blocks + (unsigned)m->barrier_extra;
+    b.timeout_ns = (unsigned long long)(m->barrier_timeout_ms * 1e6);
+    return b;
+}
+
+// Read the barrier error flag of the last persistent launch (synchronises).
+bh_status check_barrier(bh_model* m)
+{
+    int err = 0;
+    BH_CUDA(m, cudaMemcpyAsync(&err, m->d_bar + 2, sizeof(int), cudaMemcpyDeviceToHost,
+                               m->stream));
+    BH_CUDA(m, cudaStreamSynchronize(m->stream));
+    if (err)
+        return fail(m, BH_ERR_TIMEOUT,
+                    "a grid barrier of the persistent stepping kernel timed out; results are invalid");
+    return BH_OK;
+}
 
 // Launch a stepping kernel with programmatic stream serialization: its
 // blocks may be scheduled while the previous kernel drains and wait in
@@ -447,6 +480,18 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_H, 3 * nw));
     CK(dalloc(&m->d_Hg, 2 * ng));
     CK(dalloc(&m->d_scal, 16));
+    CK(dalloc(&m->d_bar, 4));
+    {
+        int dev = 0, sms = 0, coop = 0, nb = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist, kThreads, 0));
+        m->fwd_blocks = nb * sms;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist, kThreads, 0));
+        m->adj_blocks = nb * sms;
+        if (!coop || m->fwd_blocks < 1 || m->adj_blocks < 1) m->persistent = 0;
+    }
     m->shots.resize(nshots);
     std::vector<uint8_t> colcov(nz_global, 0);
     for (int s = 0; s < nshots; ++s) {
@@ -515,6 +560,20 @@ bh_status bh_forward(bh_model* m, const float* wavelet, float* seis)
         q.nt = gd.nt;
         q.hist = sd.d_hist;
         const dim3 grd = grid_tiles(gd.nr, sd.nz), blk = block2d();
+        if (m->persistent) {
+            const int blocks = std::min(n_tiles(gd.nr, sd.nz), m->fwd_blocks);
+            BarK b = make_bar(m, blocks);
+            BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
+            q.n = 0;
+            void* args[] = {&g, &C, &S, &q, &b};
+            size_t e = prof_begin(m, BH_KERNEL_FWD_PERSIST, 0);
+            BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_fwd_persist, dim3(blocks), blk,
+                                                   args, 0, m->stream));
+            prof_end(m, e);
+            bh_status st = check_barrier(m);
+            if (st != BH_OK) return st;
+            continue;
+        }
         for (int n = 0; n < gd.nt; ++n) {
             q.n = n;
             size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
@@ -588,6 +647,22 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
         q.n = gd.nt - 1;
         k_adj_inject<<<(sd.nz + 127) / 128, 128, 0, m->stream>>>(g, make_state(m, 0), q,
                                                                  sd.nrec);
+        if (m->persistent) {
+            const int blocks = std::min(n_tiles(gd.nr, sd.nz), m->adj_blocks);
+            BarK b = make_bar(m, blocks);
+            BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
+            StateK S0 = make_state(m, 0), S1 = make_state(m, 1);
+            void* args[] = {&g, &C, &S0, &S1, &q, &b};
+            size_t e = prof_begin(m, BH_KERNEL_ADJ_PERSIST, 0);
+            BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_adj_persist, dim3(blocks), blk,
+                                                   args, 0, m->stream));
+            prof_end(m, e);
+            bh_status st = check_barrier(m);
+            if (st != BH_OK) return st;
+            k_finalize<<<grd, blk, 0, m->stream>>>(g, C, q, f);
+            BH_LAUNCH(m);
+            continue;
+        }
         int parity = 0;
         for (int n = gd.nt - 1; n >= 0; --n) {
             q.n = n;
@@ -669,6 +744,28 @@ bh_status bh_get_model(bh_model* m, float* vp, float* vs)
     k_velocities<<<(unsigned)((ng + 255) / 256), 256, 0, m->stream>>>(ng, m->d_lam, m->d_mu,
                                                                       m->d_rho, vp, vs);
     BH_LAUNCH(m);
+    return BH_OK;
+}
+
+bh_status bh_set_option(bh_model* m, const char* key, double value)
+{
+    if (!m || !key) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
+    const std::string k(key);
+    if (k == "persistent") {
+        if (value != 0.0 && (m->fwd_blocks < 1 || m->adj_blocks < 1))
+            return fail(m, BH_ERR_UNSUPPORTED, "cooperative launch not available");
+        m->persistent = value != 0.0;
+    } else if (k == "barrier_timeout_ms") {
+        if (!(value > 0.0) || value > 600000.0)
+            return fail(m, BH_ERR_INVALID_ARG, "barrier_timeout_ms must be in (0, 600000]");
+        m->barrier_timeout_ms = value;
+    } else if (k == "barrier_extra_arrivals") {
+        if (value < 0.0 || value > 1024.0)
+            return fail(m, BH_ERR_INVALID_ARG, "barrier_extra_arrivals must be in [0, 1024]");
+        m->barrier_extra = (int)value;
+    } else {
+        return fail(m, BH_ERR_INVALID_ARG, "unknown option " + k);
+    }
     return BH_OK;
 }
 

@@ -69,3 +69,34 @@ def test_unsupported_options(bhmod):
     with pytest.raises(bhmod.BhError) as e:
         bhmod.Model(*_args(w), snapshot_precision=3)
     assert e.value.status in (1, 7)
+
+
+def test_barrier_timeout_is_reported(bhmod):
+    """A grid barrier whose wait runs out (it waits for one arrival that
+    never comes) makes every block return; the call reports BH_ERR_TIMEOUT
+    and the context stays usable."""
+    import torch
+    w = tiny_borehole(seed=0, nt=20)
+    m = bhmod.Model(*_args(w))
+    if m.lib.bh_set_option(m.h, b"persistent", 1.0) != 0:
+        pytest.skip("no cooperative launch")
+    m.set_option("barrier_timeout_ms", 50)
+    m.set_option("barrier_extra_arrivals", 1)
+    wav = torch.from_numpy(w.wavelet).cuda()
+    with pytest.raises(bhmod.BhError) as e:
+        m.forward(wav)
+    assert e.value.status == 5
+    m.set_option("barrier_extra_arrivals", 0)
+    seis = m.forward(wav)
+    torch.cuda.synchronize()
+    assert torch.isfinite(seis).all()
+    m.close()
+
+
+def test_bad_option(bhmod):
+    w = tiny_borehole(seed=0, nt=10)
+    m = bhmod.Model(*_args(w))
+    with pytest.raises(bhmod.BhError) as e:
+        m.set_option("no_such_option", 1)
+    assert e.value.status == 1
+    m.close()

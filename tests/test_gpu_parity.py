@@ -106,3 +106,24 @@ def test_deterministic(cuda):
     for k in ("seis", "g_lam", "g_mu", "g_rho", "H_lam"):
         assert np.array_equal(a[k], b[k]), k
     assert a["J"] == b["J"]
+
+
+def test_persistent_matches_per_step(cuda):
+    """The persistent cooperative kernels and the one-launch-per-half-step
+    kernels run the same tile code: bit-identical results."""
+    from paper_2005_00281_gb300.bh import model_from_workload
+    torch = cuda
+    w = tiny_borehole(seed=6, nz=75, nt=220)
+    out = []
+    for persistent in (1, 0):
+        m = model_from_workload(w)
+        m.set_option("persistent", persistent)
+        wav = torch.from_numpy(w.wavelet).cuda()
+        seis = m.forward(wav)
+        resid, J = m.residual_misfit(seis, torch.zeros_like(seis))
+        g = m.adjoint_gradient(resid)
+        torch.cuda.synchronize()
+        out.append([seis.cpu().numpy()] + [x.cpu().numpy() for x in g])
+        m.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
