@@ -87,16 +87,6 @@ __device__ __forceinline__ float muh_at(const CoefK& C, const WinK& g, int i, in
     return C.muh[cg];
 }
 
-__device__ __forceinline__ void kahan_add(float2* __restrict__ acc, size_t k, float x)
-{
-    float2 s = acc[k];
-    float y = __fsub_rn(x, s.y);
-    float t = __fadd_rn(s.x, y);
-    s.y = __fsub_rn(__fsub_rn(t, s.x), y);
-    s.x = t;
-    acc[k] = s;
-}
-
 // ------------------------------------------------------------- tiling
 //
 // Every stepping kernel works on tiles of kTR x kTZ nodes (16 rows of r by
@@ -176,24 +166,46 @@ struct FwdSmem {
 };
 
 // Velocity half-step of one tile: Eq. 2 lines 1-2 with the C-PML memories 0..3.
+// Every own-node input is loaded into registers before the staging, so the
+// tile pays one round trip to L2 (the loads and stores go through pointers
+// the compiler must assume may alias, so it would not reorder them itself).
 __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
                                              int i0, int j0, FwdSmem& sm)
 {
     Tile &s_rr = sm.a, &s_tt = sm.b, &s_rz = sm.c, &s_zz = sm.d;
+    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
+    const bool jok = j < g.nz;
+    float vr0[2], vz0[2], br[2], bz[2], q0[2], q1[2], q2[2], q3[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + threadIdx.y + 8 * p;
+        vr0[p] = vz0[p] = br[p] = bz[p] = q0[p] = q1[p] = q2[p] = q3[p] = 0.f;
+        if (jok && i < g.nr) {
+            const int c = i * g.P + j;
+            vz0[p] = ldcg(S.vz + c);
+            bz[p] = bvz_at(C, g, i, j);
+            if (C.ar_half[i] != 0.f) q2[p] = ldcg(S.psi[2] + c);
+            if (C.az_half[j] != 0.f) q3[p] = ldcg(S.psi[3] + c);
+            if (i >= 1) {
+                vr0[p] = ldcg(S.vr + c);
+                br[p] = __ldg(C.bvr + (size_t)i * g.nzg + g.z0 + j);
+                if (C.ar_int[i] != 0.f) q0[p] = ldcg(S.psi[0] + c);
+                if (C.az_int[j] != 0.f) q1[p] = ldcg(S.psi[1] + c);
+            }
+        }
+    }
     __syncthreads();
     stage<EVEN>(s_rr, S.trr, i0, j0, g);
     stage<EVEN>(s_tt, S.ttt, i0, j0, g);
     stage<ODD>(s_rz, S.trz, i0, j0, g);
     stage<EVEN>(s_zz, S.tzz, i0, j0, g);
     __syncthreads();
-    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
-    if (j >= g.nz) return;
+    if (!jok) return;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
         if (i >= g.nr) break;
         const int c = i * g.P + j;
-        const size_t cg = (size_t)i * g.nzg + g.z0 + j;
         if (i >= 1) {
             float d_trr = d4(s_rr[rr][zz], s_rr[rr - 1][zz], s_rr[rr + 1][zz], s_rr[rr - 2][zz]) *
                           g.inv_dr;
@@ -203,76 +215,101 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
                          C.inv_r_int[i];
             float a = C.ar_int[i];
             if (a != 0.f) {
-                float q = C.br_int[i] * ldcg(S.psi[0] + c) + a * d_trr;
+                float q = C.br_int[i] * q0[p] + a * d_trr;
                 S.psi_w[0][c] = q;
                 d_trr += q;
             }
             a = C.az_int[j];
             if (a != 0.f) {
-                float q = C.bz_int[j] * ldcg(S.psi[1] + c) + a * d_trz;
+                float q = C.bz_int[j] * q1[p] + a * d_trz;
                 S.psi_w[1][c] = q;
                 d_trz += q;
             }
-            S.vr[c] = ldcg(S.vr + c) + g.dt * __ldg(C.bvr + cg) * (d_trr + d_trz + hoop);
+            S.vr[c] = vr0[p] + g.dt * br[p] * (d_trr + d_trz + hoop);
         }
         float d_trz = d4(s_rz[rr + 1][zz], s_rz[rr][zz], s_rz[rr + 2][zz], s_rz[rr - 1][zz]) * g.inv_dr;
         float d_tzz = d4(s_zz[rr][zz + 1], s_zz[rr][zz], s_zz[rr][zz + 2], s_zz[rr][zz - 1]) * g.inv_dz;
         float hoop = 0.5f * (s_rz[rr][zz] + s_rz[rr + 1][zz]) * C.inv_r_half[i];
         float a = C.ar_half[i];
         if (a != 0.f) {
-            float q = C.br_half[i] * ldcg(S.psi[2] + c) + a * d_trz;
+            float q = C.br_half[i] * q2[p] + a * d_trz;
             S.psi_w[2][c] = q;
             d_trz += q;
         }
         a = C.az_half[j];
         if (a != 0.f) {
-            float q = C.bz_half[j] * ldcg(S.psi[3] + c) + a * d_tzz;
+            float q = C.bz_half[j] * q3[p] + a * d_tzz;
             S.psi_w[3][c] = q;
             d_tzz += q;
         }
-        S.vz[c] = ldcg(S.vz + c) + g.dt * bvz_at(C, g, i, j) * (d_trz + d_tzz + hoop);
+        S.vz[c] = vz0[p] + g.dt * bz[p] * (d_trz + d_tzz + hoop);
     }
 }
 
 // Stress half-step of one tile: Eq. 2 lines 3-6 with the C-PML memories
 // 4..7, source injection into the three normal stresses, pressure
-// recording, and the store of v^{n+1/2} for the adjoint.
+// recording, and the store of v^{n+1/2} for the adjoint.  Own-node inputs
+// are prefetched as in the velocity tile.
 __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const SrcRecK& q, int i0, int j0, FwdSmem& sm)
 {
     Tile &s_vr = sm.a, &s_vz = sm.b;
+    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
+    const bool jok = j < g.nz;
+    float t_rr[2], t_tt[2], t_zz[2], t_rz[2], lm[2], mu[2], mh[2], q4[2], q5[2], q6[2], q7[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + threadIdx.y + 8 * p;
+        t_rr[p] = t_tt[p] = t_zz[p] = t_rz[p] = lm[p] = mu[p] = mh[p] = 0.f;
+        q4[p] = q5[p] = q6[p] = q7[p] = 0.f;
+        if (jok && i < g.nr) {
+            const int c = i * g.P + j;
+            const size_t cg = (size_t)i * g.nzg + g.z0 + j;
+            t_rr[p] = ldcg(S.trr + c);
+            t_tt[p] = ldcg(S.ttt + c);
+            t_zz[p] = ldcg(S.tzz + c);
+            lm[p] = __ldg(C.lam + cg);
+            mu[p] = __ldg(C.mu + cg);
+            if (C.ar_half[i] != 0.f) q4[p] = ldcg(S.psi[4] + c);
+            if (C.az_int[j] != 0.f) q5[p] = ldcg(S.psi[5] + c);
+            if (i >= 1) {
+                t_rz[p] = ldcg(S.trz + c);
+                mh[p] = muh_at(C, g, i, j);
+                if (C.az_half[j] != 0.f) q6[p] = ldcg(S.psi[6] + c);
+                if (C.ar_int[i] != 0.f) q7[p] = ldcg(S.psi[7] + c);
+            }
+        }
+    }
     __syncthreads();
     stage<ODD>(s_vr, S.vr, i0, j0, g);
     stage<EVEN>(s_vz, S.vz, i0, j0, g);
     __syncthreads();
-    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
-    if (j >= g.nz) return;
+    if (!jok) return;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
         if (i >= g.nr) break;
         const int c = i * g.P + j;
-        const size_t cg = (size_t)i * g.nzg + g.z0 + j;
         float d_vr = d4(s_vr[rr + 1][zz], s_vr[rr][zz], s_vr[rr + 2][zz], s_vr[rr - 1][zz]) * g.inv_dr;
         float vr_r = 0.5f * (s_vr[rr][zz] + s_vr[rr + 1][zz]) * C.inv_r_half[i];
         float d_vz = d4(s_vz[rr][zz], s_vz[rr][zz - 1], s_vz[rr][zz + 1], s_vz[rr][zz - 2]) * g.inv_dz;
         float a = C.ar_half[i];
         if (a != 0.f) {
-            float w = C.br_half[i] * ldcg(S.psi[4] + c) + a * d_vr;
+            float w = C.br_half[i] * q4[p] + a * d_vr;
             S.psi_w[4][c] = w;
             d_vr += w;
         }
         a = C.az_int[j];
         if (a != 0.f) {
-            float w = C.bz_int[j] * ldcg(S.psi[5] + c) + a * d_vz;
+            float w = C.bz_int[j] * q5[p] + a * d_vz;
             S.psi_w[5][c] = w;
             d_vz += w;
         }
-        const float lam = __ldg(C.lam + cg);
-        const float l2m = lam + 2.f * __ldg(C.mu + cg);
-        float trr = ldcg(S.trr + c) + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
-        float ttt = ldcg(S.ttt + c) + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
-        float tzz = ldcg(S.tzz + c) + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
+        const float lam = lm[p];
+        const float l2m = lam + 2.f * mu[p];
+        float trr = t_rr[p] + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
+        float ttt = t_tt[p] + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
+        float tzz = t_zz[p] + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
         if (c == q.src_c) {
             float inj = q.src_scale * q.wavelet[q.n];
             trr += inj;
@@ -293,17 +330,17 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
                           g.inv_dr;
             a = C.az_half[j];
             if (a != 0.f) {
-                float w = C.bz_half[j] * ldcg(S.psi[6] + c) + a * d_vrz;
+                float w = C.bz_half[j] * q6[p] + a * d_vrz;
                 S.psi_w[6][c] = w;
                 d_vrz += w;
             }
             a = C.ar_int[i];
             if (a != 0.f) {
-                float w = C.br_int[i] * ldcg(S.psi[7] + c) + a * d_vzr;
+                float w = C.br_int[i] * q7[p] + a * d_vzr;
                 S.psi_w[7][c] = w;
                 d_vzr += w;
             }
-            S.trz[c] = ldcg(S.trz + c) + g.dt * muh_at(C, g, i, j) * (d_vrz + d_vzr);
+            S.trz[c] = t_rz[p] + g.dt * mh[p] * (d_vrz + d_vzr);
         }
         if (q.hist) {
             float* h = q.hist + (size_t)q.n * 2 * g.nr * g.P;
@@ -348,10 +385,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd_stress(WinK g, CoefK C, StateK
 // ------------------------------------------------- bounded grid barrier
 
 struct BarK {
-    unsigned* count;               // arrivals in the current generation
-    unsigned* gen;                 // generation number
+    unsigned* count;               // arrivals since the launch began (monotonic)
     int* err;                      // 1 once any wait gave up
-    unsigned expected;             // arrivals that complete a generation
+    unsigned expected;             // arrivals that complete one barrier
     unsigned long long timeout_ns; // give up after this long
 };
 
@@ -362,44 +398,44 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// All blocks of a cooperative launch meet here.  Returns false, in every
-// thread of the block, when the wait ran past timeout_ns or another block
-// reported that it did; the caller then returns from the kernel, and the
-// host reads the error flag.  Writes before the barrier are visible to
-// ld.global.cg loads after it.
-__device__ bool grid_barrier(const BarK& b)
+// All blocks of a cooperative launch meet here; `epoch` counts the block's
+// barriers (the same sequence in every block).  A block arrives with one
+// release-acquire increment of a monotonic counter and waits, polling with
+// acquire loads, until the counter reaches epoch * expected.  The wait is
+// bounded twice, by the wall clock and by a poll count; when it runs out, or
+// another block reports that it did, the function returns false in every
+// thread of the block, the caller returns from the kernel, and the host reads
+// the error flag.  Writes before the barrier are visible to ld.global.cg
+// loads after it.
+__device__ bool grid_barrier(const BarK& b, unsigned& epoch)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        volatile unsigned* vgen = b.gen;
-        volatile int* verr = b.err;
+        ++epoch;
+        const unsigned target = epoch * b.expected;
+        unsigned old;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(b.count) : "memory");
         int ok = 1;
-        const unsigned g0 = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(b.count, 1u) + 1u;
-        if (arrived == b.expected) {
-            atomicExch(b.count, 0u);
-            __threadfence();
-            atomicAdd(b.gen, 1u);
-        } else {
+        if (old + 1u < target) {
             const unsigned long long t0 = global_ns();
-            // second bound, independent of the timer: every pass costs at
-            // least one L2 round trip (hundreds of ns)
-            const unsigned long long max_spins = b.timeout_ns / 64ull + 1024ull;
-            unsigned long long spins = 0;
-            while (*vgen == g0) {
+            const unsigned long long max_polls = b.timeout_ns / 64ull + 1024ull;
+            unsigned long long polls = 0;
+            volatile int* verr = b.err;
+            for (;;) {
+                unsigned cur;
+                asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(b.count) : "memory");
+                if (cur >= target) break;
                 if (*verr) { ok = 0; break; }
-                if (global_ns() - t0 > b.timeout_ns || ++spins > max_spins) {
+                if (global_ns() - t0 > b.timeout_ns || ++polls > max_polls) {
                     atomicExch(b.err, 1);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
-        __threadfence();
-        if (*verr) ok = 0;
+        if (ok && *(volatile int*)b.err) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -412,20 +448,21 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(WinK g, CoefK C, St
 {
     __shared__ FwdSmem sm;
     const int nt_tiles = tile_count(g);
+    unsigned epoch = 0;
     for (int n = 0; n < q.nt; ++n) {
         for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
             int i0, j0;
             tile_origin(g, t, &i0, &j0);
             fwd_vel_tile(g, C, S, i0, j0, sm);
         }
-        if (!grid_barrier(b)) return;
+        if (!grid_barrier(b, epoch)) return;
         q.n = n;
         for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
             int i0, j0;
             tile_origin(g, t, &i0, &j0);
             fwd_stress_tile(g, C, S, q, i0, j0, sm);
         }
-        if (!grid_barrier(b)) return;
+        if (!grid_barrier(b, epoch)) return;
     }
 }
 
@@ -486,6 +523,55 @@ __device__ __forceinline__ void stage_model(Tile& s, const float* __restrict__ f
     }
 }
 
+// Own-node inputs of one row of the transposed stress step.
+struct AdjStressOwn {
+    float av_r, av_z, fvr_prev, fvz_prev;
+    float2 g_lam, g_munn, g_murz, g_br, g_bz;
+    float h_lam, h_munn, h_murz;
+    float q4, q5, q6, q7;
+};
+
+__device__ __forceinline__ void adj_stress_own(const WinK& g, const CoefK& C, const StateK& S,
+                                               const AdjK& q, const float* fvr, int i, int j,
+                                               AdjStressOwn& o)
+{
+    const float2 z2 = make_float2(0.f, 0.f);
+    o.av_r = o.av_z = o.fvr_prev = o.fvz_prev = 0.f;
+    o.g_lam = o.g_munn = o.g_murz = o.g_br = o.g_bz = z2;
+    o.h_lam = o.h_munn = o.h_murz = 0.f;
+    o.q4 = o.q5 = o.q6 = o.q7 = 0.f;
+    if (i >= g.nr || j >= g.nz) return;
+    const int c = i * g.P + j;
+    const int plane = g.nr * g.P;
+    o.av_z = ldcg(S.vz + c);
+    o.g_lam = __ldcg(q.G_lam + c);
+    o.g_munn = __ldcg(q.G_munn + c);
+    o.g_bz = __ldcg(q.G_bz + c);
+    o.h_lam = ldcg(q.H_lam + c);
+    o.h_munn = ldcg(q.H_munn + c);
+    if (q.n > 0) o.fvz_prev = __ldg(fvr + plane + c - (size_t)2 * plane);
+    if (C.ar_half[i] != 0.f) o.q4 = ldcg(S.psi[4] + c);
+    if (C.az_int[j] != 0.f) o.q5 = ldcg(S.psi[5] + c);
+    if (i >= 1) {
+        o.av_r = ldcg(S.vr + c);
+        o.g_murz = __ldcg(q.G_murz + c);
+        o.g_br = __ldcg(q.G_br + c);
+        o.h_murz = ldcg(q.H_murz + c);
+        if (q.n > 0) o.fvr_prev = __ldg(fvr + c - (size_t)2 * plane);
+        if (C.az_half[j] != 0.f) o.q6 = ldcg(S.psi[6] + c);
+        if (C.ar_int[i] != 0.f) o.q7 = ldcg(S.psi[7] + c);
+    }
+}
+
+__device__ __forceinline__ float2 kahan_step(float2 s, float x)
+{
+    float y = __fsub_rn(x, s.y);
+    float t = __fadd_rn(s.x, y);
+    s.y = __fsub_rn(__fsub_rn(t, s.x), y);
+    s.x = t;
+    return s;
+}
+
 // Transpose of the stress step of one tile at reverse step n, fused with
 // the gradient correlations (Eq. 7, Eq. 8, and the density term).
 // S.{trr..trz} hold dJ/dtau^{n+1}; S.{vr,vz} accumulate to dJ/dv^{n+1/2};
@@ -496,6 +582,9 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     const float* fvr = q.hist + (size_t)q.n * 2 * g.nr * g.P;
     const float* fvz = fvr + g.nr * g.P;
     const float dt = g.dt;
+    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
+    AdjStressOwn own;
+    adj_stress_own(g, C, S, q, fvr, i0 + threadIdx.y, j, own);
     __syncthreads();
     stage<EVEN>(sm.arr, S.trr, i0, j0, g);
     stage<EVEN>(sm.att, S.ttt, i0, j0, g);
@@ -506,7 +595,35 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     stage_model<CELL>(sm.lam, C.lam, C, i0, j0, g);
     stage_model<CELL>(sm.mu, C.mu, C, i0, j0, g);
     stage_model<SHEAR>(sm.muh, nullptr, C, i0, j0, g);
+    // adjoint memories read by the staged coefficients (inside the layers only)
+    {
+        const int lane = threadIdx.x;
+        for (int rr = threadIdx.y; rr < kSR; rr += 8) {
+            const int i = i0 - kH + rr;
+            const int ic = i < 0 ? -1 - i : i;
+            const bool row_cell = i < g.nr;
+            const bool arh = row_cell && C.ar_half[ic] != 0.f;
+            const bool ari = i >= 1 && i < g.nr && C.ar_int[i] != 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int zz2 = lane + 32 * h;
+                if (zz2 >= kSZ) break;
+                const int jj = j0 - kH + zz2;
+                float p4 = 0.f, p5 = 0.f, p6 = 0.f, p7 = 0.f;
+                if (jj >= 0 && jj < g.nz && row_cell) {
+                    if (arh) p4 = ldcg(S.psi[4] + ic * g.P + jj);
+                    if (C.az_int[jj] != 0.f) p5 = ldcg(S.psi[5] + ic * g.P + jj);
+                    if (i >= 1 && C.az_half[jj] != 0.f) p6 = ldcg(S.psi[6] + i * g.P + jj);
+                    if (ari) p7 = ldcg(S.psi[7] + i * g.P + jj);
+                }
+                sm.x4[rr][zz2] = p4;
+                sm.x5[rr][zz2] = p5;
+                sm.x6[rr][zz2] = p6;
+                sm.x7[rr][zz2] = p7;
+            }
+        }
+    }
     __syncthreads();
+    // transposed-stencil coefficients over the staged region
     {
         const int lane = threadIdx.x;
         for (int rr = threadIdx.y; rr < kSR; rr += 8) {
@@ -518,101 +635,90 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
             const float ari = (i >= 1 && i < g.nr) ? C.ar_int[i] : 0.f;
             const float bri = (i >= 1 && i < g.nr) ? C.br_int[i] : 0.f;
             for (int h = 0; h < 2; ++h) {
-                const int zz = lane + 32 * h;
-                if (zz >= kSZ) break;
-                const int j = j0 - kH + zz;
+                const int zz2 = lane + 32 * h;
+                if (zz2 >= kSZ) break;
+                const int jj = j0 - kH + zz2;
                 float x4 = 0.f, ytt = 0.f, x5 = 0.f, x6 = 0.f, x7 = 0.f;
-                if (j >= 0 && j < g.nz && row_cell) {
-                    const float lam = sm.lam[rr][zz], l2m = lam + 2.f * sm.mu[rr][zz];
-                    const float arr = sm.arr[rr][zz], att = sm.att[rr][zz], azz = sm.azz[rr][zz];
+                if (jj >= 0 && jj < g.nz && row_cell) {
+                    const float lam = sm.lam[rr][zz2], l2m = lam + 2.f * sm.mu[rr][zz2];
+                    const float arr = sm.arr[rr][zz2], att = sm.att[rr][zz2], azz = sm.azz[rr][zz2];
                     x4 = dt * (l2m * arr + lam * (att + azz));
                     ytt = dt * (l2m * att + lam * (arr + azz));
                     x5 = dt * (l2m * azz + lam * (arr + att));
-                    if (arh != 0.f) x4 = x4 + arh * (x4 + brh * ldcg(S.psi[4] + ic * g.P + j));
-                    const float azi = C.az_int[j];
-                    if (azi != 0.f) x5 = x5 + azi * (x5 + C.bz_int[j] * ldcg(S.psi[5] + ic * g.P + j));
+                    if (arh != 0.f) x4 = x4 + arh * (x4 + brh * sm.x4[rr][zz2]);
+                    const float azi = C.az_int[jj];
+                    if (azi != 0.f) x5 = x5 + azi * (x5 + C.bz_int[jj] * sm.x5[rr][zz2]);
                     // trz node: the staged values are already odd about the axis
-                    const float y = dt * sm.muh[rr][zz] * sm.arz[rr][zz];
+                    const float y = dt * sm.muh[rr][zz2] * sm.arz[rr][zz2];
                     x6 = y;
                     x7 = y;
                     if (i >= 1) {
-                        const float azh = C.az_half[j];
-                        if (azh != 0.f) x6 = y + azh * (y + C.bz_half[j] * ldcg(S.psi[6] + i * g.P + j));
-                        if (ari != 0.f) x7 = y + ari * (y + bri * ldcg(S.psi[7] + i * g.P + j));
+                        const float azh = C.az_half[jj];
+                        if (azh != 0.f) x6 = y + azh * (y + C.bz_half[jj] * sm.x6[rr][zz2]);
+                        if (ari != 0.f) x7 = y + ari * (y + bri * sm.x7[rr][zz2]);
                     }
                 }
-                sm.x4[rr][zz] = x4;
-                sm.ytt[rr][zz] = ytt;
-                sm.x5[rr][zz] = x5;
-                sm.x6[rr][zz] = x6;
-                sm.x7[rr][zz] = x7;
+                // each thread overwrites only the positions it read
+                sm.x4[rr][zz2] = x4;
+                sm.ytt[rr][zz2] = ytt;
+                sm.x5[rr][zz2] = x5;
+                sm.x6[rr][zz2] = x6;
+                sm.x7[rr][zz2] = x7;
             }
         }
     }
     __syncthreads();
 
-    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
     if (j >= g.nz) return;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
         if (i >= g.nr) break;
         const int c = i * g.P + j;
+        if (p == 1) adj_stress_own(g, C, S, q, fvr, i, j, own);
 
         // ---- gradient correlation with the forward strains of v^{n+1/2}
         const float arr = sm.arr[rr][zz], att = sm.att[rr][zz], azz = sm.azz[rr][zz];
-        {
-            float err = d4(sm.fvr[rr + 1][zz], sm.fvr[rr][zz], sm.fvr[rr + 2][zz], sm.fvr[rr - 1][zz]) *
-                        g.inv_dr;
-            float ett = 0.5f * (sm.fvr[rr][zz] + sm.fvr[rr + 1][zz]) * C.inv_r_half[i];
-            float ezz = d4(sm.fvz[rr][zz], sm.fvz[rr][zz - 1], sm.fvz[rr][zz + 1], sm.fvz[rr][zz - 2]) *
-                        g.inv_dz;
-            float div = err + ett + ezz;
-            kahan_add(q.G_lam, c, dt * div * (arr + att + azz));
-            kahan_add(q.G_munn, c, 2.f * dt * (err * arr + ett * att + ezz * azz));
-            q.H_lam[c] = ldcg(q.H_lam + c) + dt * div * div;
-            q.H_munn[c] = ldcg(q.H_munn + c) + 4.f * dt * (err * err + ett * ett + ezz * ezz);
-            if (i >= 1) {
-                float gam = d4(sm.fvr[rr][zz + 1], sm.fvr[rr][zz], sm.fvr[rr][zz + 2], sm.fvr[rr][zz - 1]) *
-                                g.inv_dz +
-                            d4(sm.fvz[rr][zz], sm.fvz[rr - 1][zz], sm.fvz[rr + 1][zz], sm.fvz[rr - 2][zz]) *
-                                g.inv_dr;
-                kahan_add(q.G_murz, c, dt * gam * sm.arz[rr][zz]);
-                q.H_murz[c] = ldcg(q.H_murz + c) + dt * gam * gam;
-            }
-        }
+        float err = d4(sm.fvr[rr + 1][zz], sm.fvr[rr][zz], sm.fvr[rr + 2][zz], sm.fvr[rr - 1][zz]) *
+                    g.inv_dr;
+        float ett = 0.5f * (sm.fvr[rr][zz] + sm.fvr[rr + 1][zz]) * C.inv_r_half[i];
+        float ezz = d4(sm.fvz[rr][zz], sm.fvz[rr][zz - 1], sm.fvz[rr][zz + 1], sm.fvz[rr][zz - 2]) *
+                    g.inv_dz;
+        float div = err + ett + ezz;
+        q.G_lam[c] = kahan_step(own.g_lam, dt * div * (arr + att + azz));
+        q.G_munn[c] = kahan_step(own.g_munn, 2.f * dt * (err * arr + ett * att + ezz * azz));
+        q.H_lam[c] = own.h_lam + dt * div * div;
+        q.H_munn[c] = own.h_munn + 4.f * dt * (err * err + ett * ett + ezz * ezz);
 
         // ---- transpose of the stress step into Av, and the density term
-        if (i >= 1) {
-            float s = d4(sm.x4[rr - 1][zz], sm.x4[rr][zz], sm.x4[rr - 2][zz], sm.x4[rr + 1][zz]) * g.inv_dr;
-            s += 0.5f * (sm.ytt[rr - 1][zz] * C.inv_r_half[i - 1] + sm.ytt[rr][zz] * C.inv_r_half[i]);
-            s += d4(sm.x6[rr][zz - 1], sm.x6[rr][zz], sm.x6[rr][zz - 2], sm.x6[rr][zz + 1]) * g.inv_dz;
-            float av = ldcg(S.vr + c) + s;
-            S.vr[c] = av;
-            float dv = sm.fvr[rr][zz] - (q.n > 0 ? __ldg(fvr + c - (size_t)2 * g.nr * g.P) : 0.f);
-            kahan_add(q.G_br, c, dv * av);
-        }
         {
-            float s = d4(sm.x5[rr][zz], sm.x5[rr][zz + 1], sm.x5[rr][zz - 1], sm.x5[rr][zz + 2]) * g.inv_dz;
-            s += d4(sm.x7[rr][zz], sm.x7[rr + 1][zz], sm.x7[rr - 1][zz], sm.x7[rr + 2][zz]) * g.inv_dr;
-            float av = ldcg(S.vz + c) + s;
+            float sz = d4(sm.x5[rr][zz], sm.x5[rr][zz + 1], sm.x5[rr][zz - 1], sm.x5[rr][zz + 2]) * g.inv_dz;
+            sz += d4(sm.x7[rr][zz], sm.x7[rr + 1][zz], sm.x7[rr - 1][zz], sm.x7[rr + 2][zz]) * g.inv_dr;
+            const float av = own.av_z + sz;
             S.vz[c] = av;
-            float dv = sm.fvz[rr][zz] - (q.n > 0 ? __ldg(fvz + c - (size_t)2 * g.nr * g.P) : 0.f);
-            kahan_add(q.G_bz, c, dv * av);
+            q.G_bz[c] = kahan_step(own.g_bz, (sm.fvz[rr][zz] - own.fvz_prev) * av);
         }
-
-        // ---- adjoint memories of the stress step (own cell / own shear node)
-        {
-            const float lam = sm.lam[rr][zz], l2m = lam + 2.f * sm.mu[rr][zz];
-            if (C.ar_half[i] != 0.f)
-                S.psi_w[4][c] = dt * (l2m * arr + lam * (att + azz)) + C.br_half[i] * ldcg(S.psi[4] + c);
-            if (C.az_int[j] != 0.f)
-                S.psi_w[5][c] = dt * (l2m * azz + lam * (arr + att)) + C.bz_int[j] * ldcg(S.psi[5] + c);
-            if (i >= 1) {
-                const float y = dt * sm.muh[rr][zz] * sm.arz[rr][zz];
-                if (C.az_half[j] != 0.f) S.psi_w[6][c] = y + C.bz_half[j] * ldcg(S.psi[6] + c);
-                if (C.ar_int[i] != 0.f) S.psi_w[7][c] = y + C.br_int[i] * ldcg(S.psi[7] + c);
-            }
+        const float lam = sm.lam[rr][zz], l2m = lam + 2.f * sm.mu[rr][zz];
+        if (C.ar_half[i] != 0.f)
+            S.psi_w[4][c] = dt * (l2m * arr + lam * (att + azz)) + C.br_half[i] * own.q4;
+        if (C.az_int[j] != 0.f)
+            S.psi_w[5][c] = dt * (l2m * azz + lam * (arr + att)) + C.bz_int[j] * own.q5;
+        if (i >= 1) {
+            float gam = d4(sm.fvr[rr][zz + 1], sm.fvr[rr][zz], sm.fvr[rr][zz + 2], sm.fvr[rr][zz - 1]) *
+                            g.inv_dz +
+                        d4(sm.fvz[rr][zz], sm.fvz[rr - 1][zz], sm.fvz[rr + 1][zz], sm.fvz[rr - 2][zz]) *
+                            g.inv_dr;
+            q.G_murz[c] = kahan_step(own.g_murz, dt * gam * sm.arz[rr][zz]);
+            q.H_murz[c] = own.h_murz + dt * gam * gam;
+            float sr = d4(sm.x4[rr - 1][zz], sm.x4[rr][zz], sm.x4[rr - 2][zz], sm.x4[rr + 1][zz]) * g.inv_dr;
+            sr += 0.5f * (sm.ytt[rr - 1][zz] * C.inv_r_half[i - 1] + sm.ytt[rr][zz] * C.inv_r_half[i]);
+            sr += d4(sm.x6[rr][zz - 1], sm.x6[rr][zz], sm.x6[rr][zz - 2], sm.x6[rr][zz + 1]) * g.inv_dz;
+            const float av = own.av_r + sr;
+            S.vr[c] = av;
+            q.G_br[c] = kahan_step(own.g_br, (sm.fvr[rr][zz] - own.fvr_prev) * av);
+            const float y = dt * sm.muh[rr][zz] * sm.arz[rr][zz];
+            if (C.az_half[j] != 0.f) S.psi_w[6][c] = y + C.bz_half[j] * own.q6;
+            if (C.ar_int[i] != 0.f) S.psi_w[7][c] = y + C.br_int[i] * own.q7;
         }
     }
 }
@@ -625,9 +731,29 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
                                              const AdjK& q, int i0, int j0, AdjSmem& sm)
 {
     // W = dt b Av at the velocity nodes (odd about the axis for v_r, even
-    // for v_z), and the coefficients on the four stretched derivatives
+    // for v_z), the coefficients on the four stretched derivatives, and the
+    // old adjoint memories of the own nodes
     Tile &s_wr = sm.x4, &s_wz = sm.ytt, &s_x0 = sm.x5, &s_x1 = sm.x6, &s_x2 = sm.x7,
-         &s_x3 = sm.arr;
+         &s_x3 = sm.arr, &s_p0 = sm.att, &s_p1 = sm.azz, &s_p2 = sm.arz, &s_p3 = sm.lam;
+    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
+    const bool jok = j < g.nz;
+    float o_rr[2], o_tt[2], o_zz[2], o_rz[2], r3[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + threadIdx.y + 8 * p;
+        o_rr[p] = o_tt[p] = o_zz[p] = o_rz[p] = r3[p] = 0.f;
+        if (jok && i < g.nr) {
+            const int c = i * g.P + j;
+            o_rr[p] = ldcg(S.trr + c);
+            o_tt[p] = ldcg(S.ttt + c);
+            o_zz[p] = ldcg(S.tzz + c);
+            if (i >= 1) o_rz[p] = ldcg(S.trz + c);
+            if (i == 0 && q.n > 0) {
+                const int k = q.recmap[j];
+                if (k >= 0) r3[p] = q.resid[(size_t)k * q.nt + (q.n - 1)] * (1.f / 3.f);
+            }
+        }
+    }
     __syncthreads();
     {
         const int lane = threadIdx.x;
@@ -641,43 +767,51 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
             const float ari = rlive ? C.ar_int[ir] : 0.f, bri = rlive ? C.br_int[ir] : 0.f;
             const float arh = zlive ? C.ar_half[iz] : 0.f, brh = zlive ? C.br_half[iz] : 0.f;
             for (int h = 0; h < 2; ++h) {
-                const int zz = lane + 32 * h;
-                if (zz >= kSZ) break;
-                const int j = j0 - kH + zz;
+                const int zz2 = lane + 32 * h;
+                if (zz2 >= kSZ) break;
+                const int jj = j0 - kH + zz2;
                 float wr = 0.f, wz = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
-                if (j >= 0 && j < g.nz) {
+                float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+                if (jj >= 0 && jj < g.nz) {
                     if (rlive) {
-                        const int c = ir * g.P + j;
-                        const float w = g.dt * __ldg(C.bvr + (size_t)ir * g.nzg + g.z0 + j) * ldcg(S.vr + c);
-                        x0 = (ari != 0.f) ? w + ari * (w + bri * ldcg(S.psi[0] + c)) : w;
-                        const float a = C.az_int[j];
-                        x1 = (a != 0.f) ? w + a * (w + C.bz_int[j] * ldcg(S.psi[1] + c)) : w;
+                        const int c = ir * g.P + jj;
+                        const float w = g.dt * __ldg(C.bvr + (size_t)ir * g.nzg + g.z0 + jj) * ldcg(S.vr + c);
+                        if (ari != 0.f) p0 = ldcg(S.psi[0] + c);
+                        const float a = C.az_int[jj];
+                        if (a != 0.f) p1 = ldcg(S.psi[1] + c);
+                        x0 = (ari != 0.f) ? w + ari * (w + bri * p0) : w;
+                        x1 = (a != 0.f) ? w + a * (w + C.bz_int[jj] * p1) : w;
                         wr = sg * w;
                         x0 *= sg;
                         x1 *= sg;
                     }
                     if (zlive) {
-                        const int c = iz * g.P + j;
-                        const float w = g.dt * bvz_at(C, g, iz, j) * ldcg(S.vz + c);
-                        x2 = (arh != 0.f) ? w + arh * (w + brh * ldcg(S.psi[2] + c)) : w;
-                        const float a = C.az_half[j];
-                        x3 = (a != 0.f) ? w + a * (w + C.bz_half[j] * ldcg(S.psi[3] + c)) : w;
+                        const int c = iz * g.P + jj;
+                        const float w = g.dt * bvz_at(C, g, iz, jj) * ldcg(S.vz + c);
+                        if (arh != 0.f) p2 = ldcg(S.psi[2] + c);
+                        const float a = C.az_half[jj];
+                        if (a != 0.f) p3 = ldcg(S.psi[3] + c);
+                        x2 = (arh != 0.f) ? w + arh * (w + brh * p2) : w;
+                        x3 = (a != 0.f) ? w + a * (w + C.bz_half[jj] * p3) : w;
                         wz = w;
                     }
                 }
-                s_wr[rr][zz] = wr;
-                s_wz[rr][zz] = wz;
-                s_x0[rr][zz] = x0;
-                s_x1[rr][zz] = x1;
-                s_x2[rr][zz] = x2;
-                s_x3[rr][zz] = x3;
+                s_wr[rr][zz2] = wr;
+                s_wz[rr][zz2] = wz;
+                s_x0[rr][zz2] = x0;
+                s_x1[rr][zz2] = x1;
+                s_x2[rr][zz2] = x2;
+                s_x3[rr][zz2] = x3;
+                s_p0[rr][zz2] = p0;
+                s_p1[rr][zz2] = p1;
+                s_p2[rr][zz2] = p2;
+                s_p3[rr][zz2] = p3;
             }
         }
     }
     __syncthreads();
 
-    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
-    if (j >= g.nz) return;
+    if (!jok) return;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
@@ -688,35 +822,23 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
                              s_wr[rr + 1][zz] * (i + 1 < g.nr ? C.inv_r_int[i + 1] : 0.f));
         float arr = d4(s_x0[rr][zz], s_x0[rr + 1][zz], s_x0[rr - 1][zz], s_x0[rr + 2][zz]) * g.inv_dr;
         float azz = d4(s_x3[rr][zz - 1], s_x3[rr][zz], s_x3[rr][zz - 2], s_x3[rr][zz + 1]) * g.inv_dz;
-        float trr = ldcg(S.trr + c) + arr + hoop;
-        float ttt = ldcg(S.ttt + c) - hoop;
-        float tzz = ldcg(S.tzz + c) + azz;
-        if (i == 0 && q.n > 0) {
-            int k = q.recmap[j];
-            if (k >= 0) {
-                float r3 = q.resid[(size_t)k * q.nt + (q.n - 1)] * (1.f / 3.f);
-                trr += r3;
-                ttt += r3;
-                tzz += r3;
-            }
-        }
-        S.trr[c] = trr;
-        S.ttt[c] = ttt;
-        S.tzz[c] = tzz;
+        S.trr[c] = o_rr[p] + arr + hoop + r3[p];
+        S.ttt[c] = o_tt[p] - hoop + r3[p];
+        S.tzz[c] = o_zz[p] + azz + r3[p];
 
         if (i >= 1) {
-            float s = d4(s_x1[rr][zz], s_x1[rr][zz + 1], s_x1[rr][zz - 1], s_x1[rr][zz + 2]) * g.inv_dz;
-            s += d4(s_x2[rr - 1][zz], s_x2[rr][zz], s_x2[rr - 2][zz], s_x2[rr + 1][zz]) * g.inv_dr;
-            s += 0.5f * (s_wz[rr - 1][zz] * C.inv_r_half[i - 1] + s_wz[rr][zz] * C.inv_r_half[i]);
-            S.trz[c] = ldcg(S.trz + c) + s;
+            float sr = d4(s_x1[rr][zz], s_x1[rr][zz + 1], s_x1[rr][zz - 1], s_x1[rr][zz + 2]) * g.inv_dz;
+            sr += d4(s_x2[rr - 1][zz], s_x2[rr][zz], s_x2[rr - 2][zz], s_x2[rr + 1][zz]) * g.inv_dr;
+            sr += 0.5f * (s_wz[rr - 1][zz] * C.inv_r_half[i - 1] + s_wz[rr][zz] * C.inv_r_half[i]);
+            S.trz[c] = o_rz[p] + sr;
             const float w = s_wr[rr][zz];
-            if (C.ar_int[i] != 0.f) S.psi_w[0][c] = w + C.br_int[i] * ldcg(S.psi[0] + c);
-            if (C.az_int[j] != 0.f) S.psi_w[1][c] = w + C.bz_int[j] * ldcg(S.psi[1] + c);
+            if (C.ar_int[i] != 0.f) S.psi_w[0][c] = w + C.br_int[i] * s_p0[rr][zz];
+            if (C.az_int[j] != 0.f) S.psi_w[1][c] = w + C.bz_int[j] * s_p1[rr][zz];
         }
         {
             const float w = s_wz[rr][zz];
-            if (C.ar_half[i] != 0.f) S.psi_w[2][c] = w + C.br_half[i] * ldcg(S.psi[2] + c);
-            if (C.az_half[j] != 0.f) S.psi_w[3][c] = w + C.bz_half[j] * ldcg(S.psi[3] + c);
+            if (C.ar_half[i] != 0.f) S.psi_w[2][c] = w + C.br_half[i] * s_p2[rr][zz];
+            if (C.az_half[j] != 0.f) S.psi_w[3][c] = w + C.bz_half[j] * s_p3[rr][zz];
         }
     }
 }
@@ -749,6 +871,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_adj_persist(WinK g, CoefK C, St
 {
     __shared__ AdjSmem sm;
     const int nt_tiles = tile_count(g);
+    unsigned epoch = 0;
     int parity = 0;
     for (int n = q.nt - 1; n >= 0; --n) {
         q.n = n;
@@ -758,13 +881,13 @@ __global__ void __launch_bounds__(kThreads, 5) k_adj_persist(WinK g, CoefK C, St
             tile_origin(g, t, &i0, &j0);
             adj_stress_tile(g, C, S, q, i0, j0, sm);
         }
-        if (!grid_barrier(b)) return;
+        if (!grid_barrier(b, epoch)) return;
         for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
             int i0, j0;
             tile_origin(g, t, &i0, &j0);
             adj_vel_tile(g, C, S, q, i0, j0, sm);
         }
-        if (!grid_barrier(b)) return;
+        if (!grid_barrier(b, epoch)) return;
         parity ^= 1;
     }
 }

@@ -234,7 +234,6 @@ BarK make_bar(const bh_model* m, int blocks)
 {
     BarK b;
     b.count = m->d_bar;
-    b.gen = m->d_bar + 1;
     b.err = (int*)(m->d_bar + 2);
     b.expected = (unsigned)blocks + (unsigned)m->barrier_extra;
     b.timeout_ns = (unsigned long long)(m->barrier_timeout_ms * 1e6);
