@@ -61,8 +61,9 @@ typedef struct {
     double dr, dz, dt;   /* m, m, s                                            */
     double f0;           /* Hz; sets the C-PML frequency shift pi f0           */
     double pml_R;        /* target C-PML reflection; <= 0 means 1e-3           */
-    int snapshot_precision;      /* forward history: 0 fp32 (1 bf16, 2 fp16: reserved) */
-    size_t checkpoint_cap_bytes; /* 0: store every step's v_r, v_z; else cap   */
+    int snapshot_precision;      /* checkpoint snapshots: 0 fp32 (1 bf16, 2 fp16: reserved) */
+    size_t checkpoint_cap_bytes; /* 0: store v_r, v_z of every step; > 0: byte cap
+                                    of the history window plus the checkpoints   */
 } bh_grid_desc;
 
 typedef struct {
@@ -102,6 +103,20 @@ void bh_model_destroy(bh_model* model);
  * Errors: BH_ERR_INVALID_ARG, BH_ERR_CFL.
  */
 bh_status bh_set_model(bh_model* model, const float* vp, const float* vs, const float* rho);
+
+/*
+ * Shots run together: every kernel launch (or every phase of a persistent
+ * launch) covers the tiles of all shots, each shot on its own window state.
+ *
+ * Forward history.  The adjoint correlation needs v^{n+1/2} of every step.
+ * With checkpoint_cap_bytes = 0 every step is stored (nt + 1 slots of v_r,
+ * v_z per shot).  With a cap, the steps are cut into segments of L steps, a
+ * binomial (Griewank-Walther) checkpoint schedule over the segments keeps
+ * at most s full forward states per shot, and each segment is re-run once
+ * into an (L + 1)-slot history window before its adjoint; L and s are the
+ * pair that fits the cap with the fewest recomputed steps.  Results are
+ * bit-identical to storing every step.
+ */
 
 /*
  * Forward modelling (Eq. 2) of every shot: leapfrog steps of the velocity
@@ -255,6 +270,32 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
  *   BH_ERR_UNSUPPORTED (persistent mode without cooperative launch).
  */
 bh_status bh_set_option(bh_model* model, const char* key, double value);
+
+/*
+ * Read-only facts about a model (the paper has no counterpart):
+ * "history_steps" (L), "snapshots" (s), "recompute_steps" (forward steps
+ * re-run by one bh_adjoint_gradient), "tiles", "persistent",
+ * "persistent_blocks_fwd", "persistent_blocks_adj",
+ * "history_snapshot_bytes", "device_bytes".
+ *   value  host double
+ * Errors: BH_ERR_INVALID_ARG (unknown key).
+ */
+bh_status bh_get_info(bh_model* model, const char* key, double* value);
+
+/*
+ * The checkpoint schedule of the forward history (host only, no GPU; the
+ * paper has no counterpart): for nseg segments and nsnap snapshot slots
+ * (slot 0 is the zero initial state, slots 1..nsnap are stored), the
+ * snapshots taken during the forward sweep, spine[k] = (segment, slot), and
+ * the actions of the reversal, actions[k] = (kind, a, b) with kind
+ * 0 ADVANCE from segment a to segment b, 1 TAKE slot a at segment b,
+ * 2 RESTORE slot a (holding segment b), 3 REVERSE segment a.
+ *   actions  host int [max_actions][3];  spine  host int [max_spine][2]
+ * Errors: BH_ERR_INVALID_ARG (bad sizes; *n_actions and *n_spine still give
+ *   the sizes needed).
+ */
+bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
+                             int* n_actions, int* spine, int max_spine, int* n_spine);
 
 /* Static description of a status code. */
 const char* bh_status_string(bh_status status);

@@ -24,7 +24,8 @@ EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
            "bh_residual_misfit", "bh_adjoint_gradient", "bh_get_hessian", "bh_precondition",
            "bh_update", "bh_get_model", "bh_status_string", "bh_last_error",
            "bh_profile_enable", "bh_profile_read", "bh_profile_reset",
-           "bh_residual_misfit_noalloc", "bh_set_option")
+           "bh_residual_misfit_noalloc", "bh_set_option", "bh_get_info",
+           "bh_checkpoint_plan")
 NOALLOC_MAX_SAMPLES = 33554432
 KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel", "fwd_persist", "adj_persist")
 
@@ -99,6 +100,12 @@ def load_library(path: str | None = None):
     lib.bh_profile_reset.restype = st
     lib.bh_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_double]
     lib.bh_set_option.restype = st
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.bh_checkpoint_plan.argtypes = [ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ip, ip,
+                                       ctypes.c_int, ip]
+    lib.bh_checkpoint_plan.restype = st
+    lib.bh_get_info.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
+    lib.bh_get_info.restype = st
     lib.bh_residual_misfit_noalloc.argtypes = [vp, vp, vp, ctypes.c_size_t,
                                                ctypes.POINTER(ctypes.c_double), vp]
     lib.bh_residual_misfit_noalloc.restype = st
@@ -242,6 +249,12 @@ class Model:
         """bh_set_option: "persistent", "barrier_timeout_ms", "barrier_extra_arrivals"."""
         self._rc(self.lib.bh_set_option(self.h, key.encode(), float(value)))
 
+    def info(self, key):
+        """bh_get_info: history_steps, snapshots, recompute_steps, tiles, ..."""
+        v = ctypes.c_double()
+        self._rc(self.lib.bh_get_info(self.h, key.encode(), ctypes.byref(v)))
+        return v.value
+
     def profile(self, every):
         """Sample kernel timing on every every-th step (0 = off)."""
         self._rc(self.lib.bh_profile_enable(self.h, int(every)))
@@ -288,3 +301,23 @@ def residual_misfit_noalloc(seis_mod, seis_obs, resid, stream=None):
     if rc != BH_OK:
         raise BhError(rc, lib.bh_last_error(None).decode())
     return J.value
+
+
+def checkpoint_plan(nseg, nsnap):
+    """bh_checkpoint_plan (host only): (spine [(segment, slot)], actions [(kind, a, b)])."""
+    lib = load_library()
+    na, ns = ctypes.c_int(), ctypes.c_int()
+    cap_a, cap_s = 4 * nseg * (nsnap + 2) + 16, nseg + 1
+    while True:
+        acts = (ctypes.c_int * (3 * cap_a))()
+        sp = (ctypes.c_int * (2 * cap_s))()
+        rc = lib.bh_checkpoint_plan(nseg, nsnap, acts, cap_a, ctypes.byref(na), sp, cap_s,
+                                    ctypes.byref(ns))
+        if rc == BH_OK:
+            break
+        if na.value <= cap_a and ns.value <= cap_s:
+            raise BhError(rc, lib.bh_last_error(None).decode())
+        cap_a, cap_s = max(cap_a, na.value), max(cap_s, ns.value)
+    spine = [(sp[2 * k], sp[2 * k + 1]) for k in range(ns.value)]
+    actions = [(acts[3 * k], acts[3 * k + 1], acts[3 * k + 2]) for k in range(na.value)]
+    return spine, actions

@@ -157,8 +157,7 @@ struct SrcRecK {
     const float* wavelet; // [nt]
     const int* recmap;    // [nz]: receiver number of cell (0, j) or -1
     float* seis;          // [nrec_max][nt] of this shot
-    int nt, n;
-    float* hist;          // [nt][2][nr*P] or nullptr
+    int nt;
 };
 
 struct FwdSmem {
@@ -170,7 +169,7 @@ struct FwdSmem {
 // tile pays one round trip to L2 (the loads and stores go through pointers
 // the compiler must assume may alias, so it would not reorder them itself).
 __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                             int i0, int j0, FwdSmem& sm)
+                                             float* hist0, int i0, int j0, FwdSmem& sm)
 {
     Tile &s_rr = sm.a, &s_tt = sm.b, &s_rz = sm.c, &s_zz = sm.d;
     const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
@@ -243,6 +242,10 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
             d_tzz += q;
         }
         S.vz[c] = vz0[p] + g.dt * bz[p] * (d_trz + d_tzz + hoop);
+        if (hist0) {
+            hist0[c] = vr0[p];
+            hist0[g.nr * g.P + c] = vz0[p];
+        }
     }
 }
 
@@ -251,7 +254,8 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
 // recording, and the store of v^{n+1/2} for the adjoint.  Own-node inputs
 // are prefetched as in the velocity tile.
 __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                                const SrcRecK& q, int i0, int j0, FwdSmem& sm)
+                                                const SrcRecK& q, int n, bool record,
+                                                float* hist, int i0, int j0, FwdSmem& sm)
 {
     Tile &s_vr = sm.a, &s_vz = sm.b;
     const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
@@ -311,7 +315,7 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         float ttt = t_tt[p] + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
         float tzz = t_zz[p] + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
         if (c == q.src_c) {
-            float inj = q.src_scale * q.wavelet[q.n];
+            float inj = q.src_scale * q.wavelet[n];
             trr += inj;
             ttt += inj;
             tzz += inj;
@@ -319,9 +323,9 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         S.trr[c] = trr;
         S.ttt[c] = ttt;
         S.tzz[c] = tzz;
-        if (i == 0) {
+        if (i == 0 && record) {
             int k = q.recmap[j];
-            if (k >= 0) q.seis[(size_t)k * q.nt + q.n] = (trr + ttt + tzz) * (1.f / 3.f);
+            if (k >= 0) q.seis[(size_t)k * q.nt + n] = (trr + ttt + tzz) * (1.f / 3.f);
         }
         if (i >= 1) {
             float d_vrz = d4(s_vr[rr][zz + 1], s_vr[rr][zz], s_vr[rr][zz + 2], s_vr[rr][zz - 1]) *
@@ -342,44 +346,11 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
             }
             S.trz[c] = t_rz[p] + g.dt * mh[p] * (d_vrz + d_vzr);
         }
-        if (q.hist) {
-            float* h = q.hist + (size_t)q.n * 2 * g.nr * g.P;
-            h[c] = s_vr[rr][zz];
-            h[g.nr * g.P + c] = s_vz[rr][zz];
+        if (hist) {
+            hist[c] = s_vr[rr][zz];
+            hist[g.nr * g.P + c] = s_vz[rr][zz];
         }
     }
-}
-
-__device__ __forceinline__ void tile_origin(const WinK& g, int t, int* i0, int* j0)
-{
-    const int ntz = (g.nz + kTZ - 1) / kTZ;
-    *i0 = (t / ntz) * kTR;
-    *j0 = (t % ntz) * kTZ;
-}
-
-__device__ __forceinline__ int tile_count(const WinK& g)
-{
-    return ((g.nz + kTZ - 1) / kTZ) * ((g.nr + kTR - 1) / kTR);
-}
-
-__global__ void __launch_bounds__(kThreads) k_fwd_vel(WinK g, CoefK C, StateK S)
-{
-    __shared__ FwdSmem sm;
-    pdl_wait();
-    int i0, j0;
-    tile_origin(g, blockIdx.x, &i0, &j0);
-    fwd_vel_tile(g, C, S, i0, j0, sm);
-    pdl_launch_dependents();
-}
-
-__global__ void __launch_bounds__(kThreads) k_fwd_stress(WinK g, CoefK C, StateK S, SrcRecK q)
-{
-    __shared__ FwdSmem sm;
-    pdl_wait();
-    int i0, j0;
-    tile_origin(g, blockIdx.x, &i0, &j0);
-    fwd_stress_tile(g, C, S, q, i0, j0, sm);
-    pdl_launch_dependents();
 }
 
 // ------------------------------------------------- bounded grid barrier
@@ -442,30 +413,6 @@ __device__ bool grid_barrier(const BarK& b, unsigned& epoch)
     return s_ok != 0;
 }
 
-// Every time step of one shot's forward modelling in one launch.
-__global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(WinK g, CoefK C, StateK S,
-                                                             SrcRecK q, BarK b)
-{
-    __shared__ FwdSmem sm;
-    const int nt_tiles = tile_count(g);
-    unsigned epoch = 0;
-    for (int n = 0; n < q.nt; ++n) {
-        for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
-            int i0, j0;
-            tile_origin(g, t, &i0, &j0);
-            fwd_vel_tile(g, C, S, i0, j0, sm);
-        }
-        if (!grid_barrier(b, epoch)) return;
-        q.n = n;
-        for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
-            int i0, j0;
-            tile_origin(g, t, &i0, &j0);
-            fwd_stress_tile(g, C, S, q, i0, j0, sm);
-        }
-        if (!grid_barrier(b, epoch)) return;
-    }
-}
-
 // ------------------------------------------ adjoint: transpose of Eq. 2
 //
 // Gather form of the transpose.  The forward step reads ghost values through
@@ -479,8 +426,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(WinK g, CoefK C, St
 struct AdjK {
     const float* resid;   // [nrec_max][nt] of this shot
     const int* recmap;    // [nz]
-    int nt, n;            // reverse step being processed
-    const float* hist;    // [nt][2][nr*P]: v^{n+1/2}
+    int nt;
     float2 *G_lam, *G_munn, *G_murz, *G_br, *G_bz;  // Kahan pairs [nr*P]
     float *H_lam, *H_munn, *H_murz;                 // [nr*P]
 };
@@ -532,7 +478,7 @@ struct AdjStressOwn {
 };
 
 __device__ __forceinline__ void adj_stress_own(const WinK& g, const CoefK& C, const StateK& S,
-                                               const AdjK& q, const float* fvr, int i, int j,
+                                               const AdjK& q, const float* fprev, int i, int j,
                                                AdjStressOwn& o)
 {
     const float2 z2 = make_float2(0.f, 0.f);
@@ -549,7 +495,7 @@ __device__ __forceinline__ void adj_stress_own(const WinK& g, const CoefK& C, co
     o.g_bz = __ldcg(q.G_bz + c);
     o.h_lam = ldcg(q.H_lam + c);
     o.h_munn = ldcg(q.H_munn + c);
-    if (q.n > 0) o.fvz_prev = __ldg(fvr + plane + c - (size_t)2 * plane);
+    o.fvz_prev = __ldg(fprev + plane + c);
     if (C.ar_half[i] != 0.f) o.q4 = ldcg(S.psi[4] + c);
     if (C.az_int[j] != 0.f) o.q5 = ldcg(S.psi[5] + c);
     if (i >= 1) {
@@ -557,7 +503,7 @@ __device__ __forceinline__ void adj_stress_own(const WinK& g, const CoefK& C, co
         o.g_murz = __ldcg(q.G_murz + c);
         o.g_br = __ldcg(q.G_br + c);
         o.h_murz = ldcg(q.H_murz + c);
-        if (q.n > 0) o.fvr_prev = __ldg(fvr + c - (size_t)2 * plane);
+        o.fvr_prev = __ldg(fprev + c);
         if (C.az_half[j] != 0.f) o.q6 = ldcg(S.psi[6] + c);
         if (C.ar_int[i] != 0.f) o.q7 = ldcg(S.psi[7] + c);
     }
@@ -576,15 +522,17 @@ __device__ __forceinline__ float2 kahan_step(float2 s, float x)
 // the gradient correlations (Eq. 7, Eq. 8, and the density term).
 // S.{trr..trz} hold dJ/dtau^{n+1}; S.{vr,vz} accumulate to dJ/dv^{n+1/2};
 // psi[4..7] are the adjoint memories read side, psi_w[4..7] the write side.
+// fcur: v_r, v_z planes of v^{n+1/2}; fprev: those of v^{n-1/2}
 __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                                const AdjK& q, int i0, int j0, AdjSmem& sm)
+                                                const AdjK& q, const float* fcur,
+                                                const float* fprev, int i0, int j0, AdjSmem& sm)
 {
-    const float* fvr = q.hist + (size_t)q.n * 2 * g.nr * g.P;
-    const float* fvz = fvr + g.nr * g.P;
+    const float* fvr = fcur;
+    const float* fvz = fcur + g.nr * g.P;
     const float dt = g.dt;
     const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
     AdjStressOwn own;
-    adj_stress_own(g, C, S, q, fvr, i0 + threadIdx.y, j, own);
+    adj_stress_own(g, C, S, q, fprev, i0 + threadIdx.y, j, own);
     __syncthreads();
     stage<EVEN>(sm.arr, S.trr, i0, j0, g);
     stage<EVEN>(sm.att, S.ttt, i0, j0, g);
@@ -675,7 +623,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
         const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
         if (i >= g.nr) break;
         const int c = i * g.P + j;
-        if (p == 1) adj_stress_own(g, C, S, q, fvr, i, j, own);
+        if (p == 1) adj_stress_own(g, C, S, q, fprev, i, j, own);
 
         // ---- gradient correlation with the forward strains of v^{n+1/2}
         const float arr = sm.arr[rr][zz], att = sm.att[rr][zz], azz = sm.azz[rr][zz];
@@ -728,7 +676,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
 // residual of step n-1 is injected at the receivers (transpose of the
 // recording).
 __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                             const AdjK& q, int i0, int j0, AdjSmem& sm)
+                                             const AdjK& q, int n, int i0, int j0, AdjSmem& sm)
 {
     // W = dt b Av at the velocity nodes (odd about the axis for v_r, even
     // for v_z), the coefficients on the four stretched derivatives, and the
@@ -748,9 +696,9 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
             o_tt[p] = ldcg(S.ttt + c);
             o_zz[p] = ldcg(S.tzz + c);
             if (i >= 1) o_rz[p] = ldcg(S.trz + c);
-            if (i == 0 && q.n > 0) {
+            if (i == 0 && n > 0) {
                 const int k = q.recmap[j];
-                if (k >= 0) r3[p] = q.resid[(size_t)k * q.nt + (q.n - 1)] * (1.f / 3.f);
+                if (k >= 0) r3[p] = q.resid[(size_t)k * q.nt + (n - 1)] * (1.f / 3.f);
             }
         }
     }
@@ -843,63 +791,140 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_adj_stress(WinK g, CoefK C, StateK S, AdjK q)
+// ------------------------------------------------ shots, tiles, runs
+//
+// Every shot has its own window state; all shots of a model advance in
+// lockstep.  One tile table lists (shot, i0, j0) for every tile of every
+// shot, so one launch (or one persistent phase) covers all shots.
+
+struct ShotK {
+    WinK g;
+    CoefK C;
+    StateK Sf;      // forward view: C-PML memories updated in place (bank a)
+    StateK Sa[2];   // adjoint views: read bank a / write bank b, and reverse
+    SrcRecK q;
+    AdjK a;
+    float* hist;    // history window: slot k = v_r, v_z planes of v^{hist_n0 + k - 1/2}
+};
+
+struct RunK {
+    const ShotK* shots;
+    const int4* tiles;  // (shot, i0, j0, 0)
+    int ntiles;
+    int n0, n1;         // forward: steps n0 .. n1-1; adjoint: n1-1 down to n0
+    int hist_n0;        // history slot 0 holds v^{hist_n0 - 1/2}; -1: no history
+    int record;         // forward: write the seismograms
+    int nt;             // steps of the whole run (adjoint memory bank parity)
+};
+
+__device__ __forceinline__ float* hist_slot(const ShotK& sh, const RunK& r, int k)
 {
-    __shared__ AdjSmem sm;
+    return sh.hist + (size_t)k * 2 * sh.g.nr * sh.g.P;
+}
+
+__device__ __forceinline__ void run_fwd_vel(const RunK& r, int n, int t, FwdSmem& sm)
+{
+    const int4 tk = r.tiles[t];
+    const ShotK& sh = r.shots[tk.x];
+    float* h0 = (r.hist_n0 >= 0 && n == r.hist_n0) ? hist_slot(sh, r, 0) : nullptr;
+    fwd_vel_tile(sh.g, sh.C, sh.Sf, h0, tk.y, tk.z, sm);
+}
+
+__device__ __forceinline__ void run_fwd_stress(const RunK& r, int n, int t, FwdSmem& sm)
+{
+    const int4 tk = r.tiles[t];
+    const ShotK& sh = r.shots[tk.x];
+    float* h = r.hist_n0 >= 0 ? hist_slot(sh, r, n - r.hist_n0 + 1) : nullptr;
+    fwd_stress_tile(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, sm);
+}
+
+__device__ __forceinline__ void run_adj_stress(const RunK& r, int n, int t, AdjSmem& sm)
+{
+    const int4 tk = r.tiles[t];
+    const ShotK& sh = r.shots[tk.x];
+    const int parity = (r.nt - 1 - n) & 1;
+    adj_stress_tile(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, r, n - r.hist_n0 + 1),
+                    hist_slot(sh, r, n - r.hist_n0), tk.y, tk.z, sm);
+}
+
+__device__ __forceinline__ void run_adj_vel(const RunK& r, int n, int t, AdjSmem& sm)
+{
+    const int4 tk = r.tiles[t];
+    const ShotK& sh = r.shots[tk.x];
+    const int parity = (r.nt - 1 - n) & 1;
+    adj_vel_tile(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, sm);
+}
+
+// one launch per half-step: one block per tile of every shot
+__global__ void __launch_bounds__(kThreads) k_fwd_vel(RunK r, int n)
+{
+    __shared__ FwdSmem sm;
     pdl_wait();
-    int i0, j0;
-    tile_origin(g, blockIdx.x, &i0, &j0);
-    adj_stress_tile(g, C, S, q, i0, j0, sm);
+    run_fwd_vel(r, n, blockIdx.x, sm);
     pdl_launch_dependents();
 }
 
-__global__ void __launch_bounds__(kThreads) k_adj_vel(WinK g, CoefK C, StateK S, AdjK q)
+__global__ void __launch_bounds__(kThreads) k_fwd_stress(RunK r, int n)
 {
-    __shared__ AdjSmem sm;
+    __shared__ FwdSmem sm;
     pdl_wait();
-    int i0, j0;
-    tile_origin(g, blockIdx.x, &i0, &j0);
-    adj_vel_tile(g, C, S, q, i0, j0, sm);
+    run_fwd_stress(r, n, blockIdx.x, sm);
     pdl_launch_dependents();
 }
 
-// Every reverse step of one shot in one launch.  S0 / S1 are the state
-// views of the two adjoint-memory banks (read bank 0 / write bank 1, and the
-// reverse); the banks swap every step.
-__global__ void __launch_bounds__(kThreads, 5) k_adj_persist(WinK g, CoefK C, StateK S0,
-                                                             StateK S1, AdjK q, BarK b)
+__global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n)
 {
     __shared__ AdjSmem sm;
-    const int nt_tiles = tile_count(g);
+    pdl_wait();
+    run_adj_stress(r, n, blockIdx.x, sm);
+    pdl_launch_dependents();
+}
+
+__global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n)
+{
+    __shared__ AdjSmem sm;
+    pdl_wait();
+    run_adj_vel(r, n, blockIdx.x, sm);
+    pdl_launch_dependents();
+}
+
+// every step n0 .. n1-1 of every shot in one cooperative launch
+__global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(RunK r, BarK b)
+{
+    __shared__ FwdSmem sm;
     unsigned epoch = 0;
-    int parity = 0;
-    for (int n = q.nt - 1; n >= 0; --n) {
-        q.n = n;
-        const StateK& S = parity ? S1 : S0;
-        for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
-            int i0, j0;
-            tile_origin(g, t, &i0, &j0);
-            adj_stress_tile(g, C, S, q, i0, j0, sm);
-        }
+    for (int n = r.n0; n < r.n1; ++n) {
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_fwd_vel(r, n, t, sm);
         if (!grid_barrier(b, epoch)) return;
-        for (int t = blockIdx.x; t < nt_tiles; t += gridDim.x) {
-            int i0, j0;
-            tile_origin(g, t, &i0, &j0);
-            adj_vel_tile(g, C, S, q, i0, j0, sm);
-        }
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_fwd_stress(r, n, t, sm);
         if (!grid_barrier(b, epoch)) return;
-        parity ^= 1;
     }
 }
 
-// transpose of the recording at the last step: dp[nt-1]/3 into each normal stress
-__global__ void k_adj_inject(WinK g, StateK S, AdjK q, int nrec)
+// reverse steps n1-1 down to n0 of every shot in one cooperative launch
+__global__ void __launch_bounds__(kThreads, 5) k_adj_persist(RunK r, BarK b)
 {
+    __shared__ AdjSmem sm;
+    unsigned epoch = 0;
+    for (int n = r.n1 - 1; n >= r.n0; --n) {
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_adj_stress(r, n, t, sm);
+        if (!grid_barrier(b, epoch)) return;
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_adj_vel(r, n, t, sm);
+        if (!grid_barrier(b, epoch)) return;
+    }
+}
+
+// transpose of the recording at the last step, every shot (grid.y = shot):
+// dp[nt-1]/3 into each normal stress of the receiver cells
+__global__ void k_adj_inject(const ShotK* shots, int n)
+{
+    const ShotK& sh = shots[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.nz) return;
-    int r = q.recmap[k];
+    if (k >= sh.g.nz) return;
+    const int r = sh.a.recmap[k];
     if (r < 0) return;
-    float r3 = q.resid[(size_t)r * q.nt + q.n] * (1.f / 3.f);
+    const StateK& S = sh.Sa[0];
+    const float r3 = sh.a.resid[(size_t)r * sh.a.nt + n] * (1.f / 3.f);
     S.trr[k] += r3;
     S.ttt[k] += r3;
     S.tzz[k] += r3;
@@ -919,8 +944,11 @@ __device__ __forceinline__ double kval(const float2* a, size_t k)
 
 // Chain rule from the node accumulators of one shot to per-cell gradients,
 // added into the global FP64 arrays.  Cells of the window's C-PML get nothing.
-__global__ void k_finalize(WinK g, CoefK C, AdjK q, FinK f)
+__global__ void k_finalize(const ShotK* shots, int s, FinK f)
 {
+    const WinK& g = shots[s].g;
+    const CoefK& C = shots[s].C;
+    const AdjK& q = shots[s].a;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= g.nr - g.npml_r || j < g.npml_z || j >= g.nz - g.npml_z) return;

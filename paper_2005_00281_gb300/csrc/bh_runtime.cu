@@ -1,11 +1,13 @@
 // Host runtime and C ABI of libbh (declared in include/bh.h): model object,
-// C-PML profiles, shot plan, forward-history store, and the drivers that
-// enqueue the kernels of bh_kernels.cuh / bh_ops.cuh on the model's stream.
+// C-PML profiles, shot and tile tables, forward-history window, checkpoint
+// schedule, and the drivers that enqueue the kernels of bh_kernels.cuh /
+// bh_ops.cuh on the model's stream.
 #include "bh.h"
 #include "bh_kernels.cuh"
 #include "bh_ops.cuh"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -18,12 +20,20 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct ShotDev {
+// planes (nr x P floats) of one shot's forward and adjoint state
+constexpr int kFwdPlanes = 14;  // v_r v_z trr ttt tzz trz + 8 C-PML memories
+constexpr int kAdjPlanes = 35;  // 6 fields + 2 x 8 memories + 5 Kahan pairs + 3 Hessian
+
+struct ShotHost {
     int z0 = 0, nz = 0, src_ir = 0, src_iz = 0, nrec = 0;
     std::vector<int> rec_iz;
-    int* d_recmap = nullptr;                       // [nz]
-    float* d_zprof = nullptr;                      // az_int, bz_int, az_half, bz_half [4][nz]
-    float* d_hist = nullptr;                       // [nt][2][nr*P]
+    size_t zprof_off = 0, recmap_off = 0;  // offsets into the concatenated tables
+};
+
+// One action of the checkpointed reversal (units: segments of L steps).
+enum { ACT_ADVANCE = 0, ACT_TAKE = 1, ACT_RESTORE = 2, ACT_REVERSE = 3 };
+struct Act {
+    int kind, a, b;  // ADVANCE a->b; TAKE slot a <- seg b; RESTORE slot a (seg b); REVERSE seg a
 };
 
 }  // namespace
@@ -40,21 +50,32 @@ struct bh_model {
     uint8_t* d_colcov = nullptr;
     // radial profiles: inv_r_int, inv_r_half, ar_int, br_int, ar_half, br_half [6][nr]
     float* d_rprof = nullptr;
-    std::vector<ShotDev> shots;
-    // working state of one window
-    float* d_state = nullptr;   // 6 fields [nr*P]
-    float* d_psi = nullptr;     // 16 planes [nr*P]: 8 memories x 2 (ping-pong)
-    float2* d_G = nullptr;      // 5 Kahan planes [nr*P]
-    float* d_H = nullptr;       // 3 planes [nr*P]
+    // shots
+    std::vector<ShotHost> shots;
+    float* d_zprof = nullptr;   // per shot 4 x nz
+    int* d_recmap = nullptr;    // per shot nz
+    float* d_fwd = nullptr;     // per shot kFwdPlanes planes
+    float* d_adj = nullptr;     // per shot kAdjPlanes planes
+    float* d_hist = nullptr;    // per shot (L + 1) x 2 planes
+    float* d_snap = nullptr;    // per shot nsnap x kFwdPlanes planes
+    std::vector<ShotK> h_shots;
+    ShotK* d_shots = nullptr;
+    int4* d_tiles = nullptr;
+    int ntiles = 0;
+    // history window and checkpoint schedule
+    int L = 0;                  // steps per history window (nt: store every step)
+    int nsnap = 0;              // stored snapshot slots (slot 0 is the zero state)
+    std::vector<Act> plan;      // reversal after the forward sweep
+    std::vector<std::pair<int, int>> spine;  // (segment, slot) taken during the sweep
+    long long recompute_steps = 0;
     double* d_Hg = nullptr;     // H_lam, H_mu global [2][nr*nzg]
     double* d_scal = nullptr;   // small device scalars
     bool have_forward = false, have_gradient = false;
     std::string err;
-    // persistent (one cooperative launch per shot and direction) or one
-    // launch per half-step; co-resident blocks of the persistent kernels
+    // persistent (one cooperative launch per run) or one launch per half-step
     int persistent = 1;
     int fwd_blocks = 0, adj_blocks = 0;
-    unsigned* d_bar = nullptr;          // barrier: count, generation, error flag
+    unsigned* d_bar = nullptr;          // barrier: count, -, error flag
     double barrier_timeout_ms = 2000.0;
     int barrier_extra = 0;              // test knob: arrivals that never come
     // sampled kernel timing: events around every prof_every-th step's launches
@@ -90,6 +111,12 @@ bh_status fail(bh_model* m, bh_status s, const std::string& msg)
             return fail((m), BH_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
     } while (0)
 
+#define BH_TRY(expr)                   \
+    do {                               \
+        bh_status s_ = (expr);         \
+        if (s_ != BH_OK) return s_;    \
+    } while (0)
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
 {
@@ -101,27 +128,11 @@ cudaError_t dalloc(T** p, size_t count)
 void free_model(bh_model* m)
 {
     if (!m) return;
-    cudaFree(m->d_lam);
-    cudaFree(m->d_mu);
-    cudaFree(m->d_rho);
-    cudaFree(m->d_bvr);
-    cudaFree(m->d_bvz);
-    cudaFree(m->d_muh);
-    cudaFree(m->d_mask);
-    cudaFree(m->d_colcov);
-    cudaFree(m->d_rprof);
-    for (auto& s : m->shots) {
-        cudaFree(s.d_recmap);
-        cudaFree(s.d_zprof);
-        cudaFree(s.d_hist);
-    }
-    cudaFree(m->d_state);
-    cudaFree(m->d_psi);
-    cudaFree(m->d_G);
-    cudaFree(m->d_H);
-    cudaFree(m->d_Hg);
-    cudaFree(m->d_scal);
-    cudaFree(m->d_bar);
+    void* bufs[] = {m->d_lam,   m->d_mu,     m->d_rho,   m->d_bvr,    m->d_bvz,    m->d_muh,
+                    m->d_mask,  m->d_colcov, m->d_rprof, m->d_zprof,  m->d_recmap, m->d_fwd,
+                    m->d_adj,   m->d_hist,   m->d_snap,  m->d_shots,  m->d_tiles,  m->d_Hg,
+                    m->d_scal,  m->d_bar};
+    for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     delete m;
 }
@@ -136,142 +147,81 @@ void pml_ab(double x, double d0, double alpha_max, double dt, double* a, double*
     *a = d > 0.0 ? d * (*b - 1.0) / (d + alpha) : 0.0;
 }
 
-size_t nrp(const bh_model* m) { return (size_t)m->grid.nr * m->P; }
-
-WinK make_win(const bh_model* m, const ShotDev& s)
-{
-    WinK g;
-    g.nr = m->grid.nr;
-    g.nz = s.nz;
-    g.P = m->P;
-    g.nzg = m->nzg;
-    g.z0 = s.z0;
-    g.npml_r = m->grid.npml_r;
-    g.npml_z = m->grid.npml_z;
-    g.dt = (float)m->grid.dt;
-    g.inv_dr = (float)(1.0 / m->grid.dr);
-    g.inv_dz = (float)(1.0 / m->grid.dz);
-    return g;
-}
-
-CoefK make_coef(const bh_model* m, const ShotDev& s)
-{
-    const int nr = m->grid.nr;
-    CoefK C;
-    C.lam = m->d_lam;
-    C.mu = m->d_mu;
-    C.rho = m->d_rho;
-    C.bvr = m->d_bvr;
-    C.bvz = m->d_bvz;
-    C.muh = m->d_muh;
-    C.inv_r_int = m->d_rprof;
-    C.inv_r_half = m->d_rprof + nr;
-    C.ar_int = m->d_rprof + 2 * nr;
-    C.br_int = m->d_rprof + 3 * nr;
-    C.ar_half = m->d_rprof + 4 * nr;
-    C.br_half = m->d_rprof + 5 * nr;
-    C.az_int = s.d_zprof;
-    C.bz_int = s.d_zprof + s.nz;
-    C.az_half = s.d_zprof + 2 * s.nz;
-    C.bz_half = s.d_zprof + 3 * s.nz;
-    return C;
-}
-
-StateK make_state(const bh_model* m, int parity)
-{
-    const size_t n = nrp(m);
-    StateK S;
-    S.vr = m->d_state;
-    S.vz = m->d_state + n;
-    S.trr = m->d_state + 2 * n;
-    S.ttt = m->d_state + 3 * n;
-    S.tzz = m->d_state + 4 * n;
-    S.trz = m->d_state + 5 * n;
-    for (int k = 0; k < 8; ++k) {
-        float* a = m->d_psi + (size_t)k * n;
-        float* b = m->d_psi + (size_t)(8 + k) * n;
-        if (parity < 0) {          // forward: update in place in bank a
-            S.psi[k] = S.psi_w[k] = a;
-        } else {                   // adjoint: read one bank, write the other
-            S.psi[k] = parity ? b : a;
-            S.psi_w[k] = parity ? a : b;
-        }
-    }
-    return S;
-}
-
-// Sampled timing of one kernel launch: returns the event index to close, or
-// SIZE_MAX when this launch is not sampled.
-size_t prof_begin(bh_model* m, int kernel, int step)
-{
-    if (m->prof_every <= 0 || step % m->prof_every != 0) return SIZE_MAX;
-    if (m->ev_used + 2 > m->ev_pool.size()) {
-        for (int k = 0; k < 64; ++k) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) return SIZE_MAX;
-            m->ev_pool.push_back(e);
-        }
-    }
-    size_t i = m->ev_used;
-    m->ev_used += 2;
-    cudaEventRecord(m->ev_pool[i], m->stream);
-    m->prof_marks.push_back({kernel, i});
-    return i;
-}
-
-void prof_end(bh_model* m, size_t i)
-{
-    if (i != SIZE_MAX) cudaEventRecord(m->ev_pool[i + 1], m->stream);
-}
+size_t plane(const bh_model* m) { return (size_t)m->grid.nr * m->P; }
 
 dim3 block2d() { return dim3(32, 8); }
 dim3 grid2d(int nr, int nz) { return dim3((nz + 31) / 32, (nr + 7) / 8); }
-// grid of the tiled stepping kernels: one block per kTR x kTZ tile
-int n_tiles(int nr, int nz) { return ((nz + kTZ - 1) / kTZ) * ((nr + kTR - 1) / kTR); }
-dim3 grid_tiles(int nr, int nz) { return dim3(n_tiles(nr, nz)); }
 
-BarK make_bar(const bh_model* m, int blocks)
+// ------------------------------------------------------ checkpoint schedule
+//
+// Binomial checkpointing (Griewank and Walther) over segments of L steps:
+// with s free snapshot slots and n segments to reverse, let t be the least
+// repetition number with C(s + t, s) >= n; advancing to the split
+// m = l + max(1, n - C(s - 1 + t, s - 1)) and reversing [m, r) with s - 1
+// slots and [l, m) with s slots keeps every segment within t advances.
+
+double binom(int s, int t)
 {
-    BarK b;
-    b.count = m->d_bar;
-    b.err = (int*)(m->d_bar + 2);
-    b.expected = (unsigned)blocks + (unsigned)m->barrier_extra;
-    b.timeout_ns = (unsigned long long)(m->barrier_timeout_ms * 1e6);
+    double b = 1.0;
+    for (int k = 1; k <= s; ++k) b = b * (t + k) / k;  // C(s + t, s)
     return b;
 }
 
-// Read the barrier error flag of the last persistent launch (synchronises).
-bh_status check_barrier(bh_model* m)
+void rev(int l, int r, int slot_l, int s, int next_slot, std::vector<Act>& out)
 {
-    int err = 0;
-    BH_CUDA(m, cudaMemcpyAsync(&err, m->d_bar + 2, sizeof(int), cudaMemcpyDeviceToHost,
-                               m->stream));
-    BH_CUDA(m, cudaStreamSynchronize(m->stream));
-    if (err)
-        return fail(m, BH_ERR_TIMEOUT,
-                    "a grid barrier of the persistent stepping kernel timed out; results are invalid");
-    return BH_OK;
+    const int n = r - l;
+    if (n <= 0) return;
+    if (n == 1) {
+        out.push_back({ACT_RESTORE, slot_l, l});
+        out.push_back({ACT_REVERSE, l, 0});
+        return;
+    }
+    if (s == 0) {
+        for (int k = r - 1; k >= l; --k) {
+            out.push_back({ACT_RESTORE, slot_l, l});
+            if (k > l) out.push_back({ACT_ADVANCE, l, k});
+            out.push_back({ACT_REVERSE, k, 0});
+        }
+        return;
+    }
+    int t = 1;
+    while (binom(s, t) < n) ++t;
+    int mp = n - (int)std::min<double>(binom(s - 1, t), (double)n);
+    mp = std::max(1, std::min(mp, n - 1));
+    const int m = l + mp;
+    out.push_back({ACT_RESTORE, slot_l, l});
+    out.push_back({ACT_ADVANCE, l, m});
+    out.push_back({ACT_TAKE, next_slot, m});
+    rev(m, r, next_slot, s - 1, next_slot + 1, out);
+    rev(l, m, slot_l, s, next_slot, out);
 }
 
-// Launch a stepping kernel with programmatic stream serialization: its
-// blocks may be scheduled while the previous kernel drains and wait in
-// griddepcontrol.wait for its results.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream,
-                       Args... args)
+// Full action list for nseg segments with nsnap stored slots; the leading
+// RESTORE / ADVANCE / TAKE chain that walks forward from segment 0 is moved
+// into the forward sweep (its snapshots are taken on the way).
+void build_plan(int nseg, int nsnap, std::vector<Act>* plan,
+                std::vector<std::pair<int, int>>* spine, long long* adv_segments)
 {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
+    std::vector<Act> all;
+    rev(0, nseg, 0, nsnap, 1, all);
+    size_t k = 0;
+    int pos = 0, pos_slot = 0;
+    spine->clear();
+    while (k + 2 < all.size() && all[k].kind == ACT_RESTORE && all[k].a == pos_slot &&
+           all[k + 1].kind == ACT_ADVANCE && all[k + 1].a == pos && all[k + 2].kind == ACT_TAKE) {
+        pos = all[k + 2].b;
+        pos_slot = all[k + 2].a;
+        spine->push_back({pos, pos_slot});
+        k += 3;
+    }
+    plan->assign(all.begin() + k, all.end());
+    long long adv = 0;
+    for (const Act& a : *plan)
+        if (a.kind == ACT_ADVANCE) adv += a.b - a.a;
+    *adv_segments = adv;
 }
+
+// ------------------------------------------------------------ model setup
 
 bh_status rebuild_coefficients(bh_model* m)
 {
@@ -317,8 +267,7 @@ bh_status load_model(bh_model* m, const float* vp, const float* vs, const float*
                                                                    m->d_colcov, m->d_mask);
         BH_LAUNCH(m);
     }
-    bh_status st = rebuild_coefficients(m);
-    if (st != BH_OK) return st;
+    BH_TRY(rebuild_coefficients(m));
     m->have_forward = m->have_gradient = false;
     return BH_OK;
 }
@@ -346,35 +295,345 @@ bh_status setup_profiles(bh_model* m)
         rp[4 * nr + i] = (float)a;
         rp[5 * nr + i] = (float)b;
     }
-    BH_CUDA(m, cudaMemcpyAsync(m->d_rprof, rp.data(), rp.size() * sizeof(float),
-                               cudaMemcpyHostToDevice, m->stream));
     const double Lz = g.npml_z * g.dz;
     const double d0z = g.npml_z > 0 ? -3.0 * m->vpmax * std::log(R) / (2.0 * Lz) : 0.0;
+    std::vector<float> zp;
+    std::vector<int> recmap;
     for (auto& s : m->shots) {
         const int nz = s.nz;
-        std::vector<float> zp(4 * (size_t)nz);
+        s.zprof_off = zp.size();
+        s.recmap_off = recmap.size();
+        zp.resize(zp.size() + 4 * (size_t)nz);
+        float* z = zp.data() + s.zprof_off;
         for (int j = 0; j < nz; ++j)
             for (int h = 0; h < 2; ++h) {
-                double z = (j + 0.5 * h) * g.dz, x = 0.0;
+                double zz = (j + 0.5 * h) * g.dz, x = 0.0;
                 if (g.npml_z > 0) {
-                    double xt = ((g.npml_z - 0.5) * g.dz - z) / Lz;
-                    double xb = (z - (nz - g.npml_z - 0.5) * g.dz) / Lz;
+                    double xt = ((g.npml_z - 0.5) * g.dz - zz) / Lz;
+                    double xb = (zz - (nz - g.npml_z - 0.5) * g.dz) / Lz;
                     x = std::max(xt, xb);
                 }
                 double a, b;
                 pml_ab(x, d0z, alpha_max, g.dt, &a, &b);
-                zp[(2 * h) * nz + j] = (float)a;
-                zp[(2 * h + 1) * nz + j] = (float)b;
+                z[(2 * h) * nz + j] = (float)a;
+                z[(2 * h + 1) * nz + j] = (float)b;
             }
-        BH_CUDA(m, cudaMemcpyAsync(s.d_zprof, zp.data(), zp.size() * sizeof(float),
-                                   cudaMemcpyHostToDevice, m->stream));
-        std::vector<int> recmap(nz, -1);
-        for (int k = 0; k < s.nrec; ++k) recmap[s.rec_iz[k]] = k;
-        BH_CUDA(m, cudaMemcpyAsync(s.d_recmap, recmap.data(), nz * sizeof(int),
-                                   cudaMemcpyHostToDevice, m->stream));
-        // host vectors must outlive the copies
-        BH_CUDA(m, cudaStreamSynchronize(m->stream));
+        recmap.resize(recmap.size() + nz, -1);
+        for (int k = 0; k < s.nrec; ++k) recmap[s.recmap_off + s.rec_iz[k]] = k;
     }
+    BH_CUDA(m, dalloc(&m->d_zprof, zp.size()));
+    BH_CUDA(m, dalloc(&m->d_recmap, recmap.size()));
+    BH_CUDA(m, cudaMemcpyAsync(m->d_rprof, rp.data(), rp.size() * sizeof(float),
+                               cudaMemcpyHostToDevice, m->stream));
+    BH_CUDA(m, cudaMemcpyAsync(m->d_zprof, zp.data(), zp.size() * sizeof(float),
+                               cudaMemcpyHostToDevice, m->stream));
+    BH_CUDA(m, cudaMemcpyAsync(m->d_recmap, recmap.data(), recmap.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, m->stream));
+    // host vectors must outlive the copies
+    BH_CUDA(m, cudaStreamSynchronize(m->stream));
+    return BH_OK;
+}
+
+// Per-shot descriptors (pointers into the arenas) and the tile table.
+bh_status setup_shots(bh_model* m)
+{
+    const bh_grid_desc& gd = m->grid;
+    const int nr = gd.nr;
+    const size_t pl = plane(m);
+    m->h_shots.resize(m->nshots);
+    std::vector<int4> tiles;
+    for (int s = 0; s < m->nshots; ++s) {
+        const ShotHost& sh = m->shots[s];
+        ShotK& k = m->h_shots[s];
+        memset(&k, 0, sizeof(k));
+        k.g.nr = nr;
+        k.g.nz = sh.nz;
+        k.g.P = m->P;
+        k.g.nzg = m->nzg;
+        k.g.z0 = sh.z0;
+        k.g.npml_r = gd.npml_r;
+        k.g.npml_z = gd.npml_z;
+        k.g.dt = (float)gd.dt;
+        k.g.inv_dr = (float)(1.0 / gd.dr);
+        k.g.inv_dz = (float)(1.0 / gd.dz);
+        CoefK& C = k.C;
+        C.lam = m->d_lam;
+        C.mu = m->d_mu;
+        C.rho = m->d_rho;
+        C.bvr = m->d_bvr;
+        C.bvz = m->d_bvz;
+        C.muh = m->d_muh;
+        C.inv_r_int = m->d_rprof;
+        C.inv_r_half = m->d_rprof + nr;
+        C.ar_int = m->d_rprof + 2 * nr;
+        C.br_int = m->d_rprof + 3 * nr;
+        C.ar_half = m->d_rprof + 4 * nr;
+        C.br_half = m->d_rprof + 5 * nr;
+        const float* zp = m->d_zprof + sh.zprof_off;
+        C.az_int = zp;
+        C.bz_int = zp + sh.nz;
+        C.az_half = zp + 2 * sh.nz;
+        C.bz_half = zp + 3 * sh.nz;
+        float* f = m->d_fwd + (size_t)s * kFwdPlanes * pl;
+        float* a = m->d_adj + (size_t)s * kAdjPlanes * pl;
+        StateK* views[3] = {&k.Sf, &k.Sa[0], &k.Sa[1]};
+        for (int v = 0; v < 3; ++v) {
+            float* b = v == 0 ? f : a;
+            StateK& S = *views[v];
+            S.vr = b;
+            S.vz = b + pl;
+            S.trr = b + 2 * pl;
+            S.ttt = b + 3 * pl;
+            S.tzz = b + 4 * pl;
+            S.trz = b + 5 * pl;
+            for (int q = 0; q < 8; ++q) {
+                float* bank_a = b + (6 + q) * pl;
+                float* bank_b = a + (14 + q) * pl;
+                if (v == 0) S.psi[q] = S.psi_w[q] = bank_a;
+                else if (v == 1) { S.psi[q] = bank_a; S.psi_w[q] = bank_b; }
+                else { S.psi[q] = bank_b; S.psi_w[q] = bank_a; }
+            }
+        }
+        k.q.src_c = sh.src_ir * m->P + sh.src_iz;
+        const double V = sh.src_ir == 0 ? M_PI * gd.dr * gd.dr * gd.dz
+                                        : 2.0 * M_PI * (sh.src_ir + 0.5) * gd.dr * gd.dr * gd.dz;
+        k.q.src_scale = (float)(gd.dt / V);
+        k.q.recmap = m->d_recmap + sh.recmap_off;
+        k.q.nt = gd.nt;
+        k.a.recmap = k.q.recmap;
+        k.a.nt = gd.nt;
+        k.a.G_lam = (float2*)(a + 22 * pl);
+        k.a.G_munn = (float2*)(a + 24 * pl);
+        k.a.G_murz = (float2*)(a + 26 * pl);
+        k.a.G_br = (float2*)(a + 28 * pl);
+        k.a.G_bz = (float2*)(a + 30 * pl);
+        k.a.H_lam = a + 32 * pl;
+        k.a.H_munn = a + 33 * pl;
+        k.a.H_murz = a + 34 * pl;
+        k.hist = m->d_hist + (size_t)s * (m->L + 1) * 2 * pl;
+        for (int i0 = 0; i0 < nr; i0 += kTR)
+            for (int j0 = 0; j0 < sh.nz; j0 += kTZ) tiles.push_back(make_int4(s, i0, j0, 0));
+    }
+    m->ntiles = (int)tiles.size();
+    BH_CUDA(m, dalloc(&m->d_shots, (size_t)m->nshots));
+    BH_CUDA(m, dalloc(&m->d_tiles, tiles.size()));
+    BH_CUDA(m, cudaMemcpyAsync(m->d_tiles, tiles.data(), tiles.size() * sizeof(int4),
+                               cudaMemcpyHostToDevice, m->stream));
+    BH_CUDA(m, cudaStreamSynchronize(m->stream));
+    return BH_OK;
+}
+
+// Re-upload the shot table after the per-call pointers changed.
+bh_status upload_shots(bh_model* m)
+{
+    BH_CUDA(m, cudaMemcpyAsync(m->d_shots, m->h_shots.data(), m->h_shots.size() * sizeof(ShotK),
+                               cudaMemcpyHostToDevice, m->stream));
+    // the source is pageable host memory: it is staged before the call returns
+    return BH_OK;
+}
+
+// ------------------------------------------------------------------ runs
+
+// Sampled timing of one kernel launch: returns the event index to close, or
+// SIZE_MAX when this launch is not sampled.
+size_t prof_begin(bh_model* m, int kernel, int step)
+{
+    if (m->prof_every <= 0 || step % m->prof_every != 0) return SIZE_MAX;
+    if (m->ev_used + 2 > m->ev_pool.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return SIZE_MAX;
+            m->ev_pool.push_back(e);
+        }
+    }
+    size_t i = m->ev_used;
+    m->ev_used += 2;
+    cudaEventRecord(m->ev_pool[i], m->stream);
+    m->prof_marks.push_back({kernel, i});
+    return i;
+}
+
+void prof_end(bh_model* m, size_t i)
+{
+    if (i != SIZE_MAX) cudaEventRecord(m->ev_pool[i + 1], m->stream);
+}
+
+// Launch a stepping kernel with programmatic stream serialization: its
+// blocks may be scheduled while the previous kernel drains and wait in
+// griddepcontrol.wait for its results.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream,
+                       Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+BarK make_bar(const bh_model* m, int blocks)
+{
+    BarK b;
+    b.count = m->d_bar;
+    b.err = (int*)(m->d_bar + 2);
+    b.expected = (unsigned)blocks + (unsigned)m->barrier_extra;
+    b.timeout_ns = (unsigned long long)(m->barrier_timeout_ms * 1e6);
+    return b;
+}
+
+// Read the barrier error flag of the last persistent launch (synchronises).
+bh_status check_barrier(bh_model* m)
+{
+    int err = 0;
+    BH_CUDA(m, cudaMemcpyAsync(&err, m->d_bar + 2, sizeof(int), cudaMemcpyDeviceToHost,
+                               m->stream));
+    BH_CUDA(m, cudaStreamSynchronize(m->stream));
+    if (err)
+        return fail(m, BH_ERR_TIMEOUT,
+                    "a grid barrier of the persistent stepping kernel timed out; results are invalid");
+    return BH_OK;
+}
+
+RunK make_run(const bh_model* m, int n0, int n1, int hist_n0, bool record)
+{
+    RunK r;
+    r.shots = m->d_shots;
+    r.tiles = m->d_tiles;
+    r.ntiles = m->ntiles;
+    r.n0 = n0;
+    r.n1 = n1;
+    r.hist_n0 = hist_n0;
+    r.record = record ? 1 : 0;
+    r.nt = m->grid.nt;
+    return r;
+}
+
+// Forward steps n0 .. n1-1 of every shot.
+bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record)
+{
+    if (n1 <= n0) return BH_OK;
+    RunK r = make_run(m, n0, n1, hist_n0, record);
+    const dim3 blk = block2d();
+    if (m->persistent) {
+        const int blocks = std::min(m->ntiles, m->fwd_blocks);
+        BarK b = make_bar(m, blocks);
+        BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
+        void* args[] = {&r, &b};
+        size_t e = prof_begin(m, BH_KERNEL_FWD_PERSIST, 0);
+        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_fwd_persist, dim3(blocks), blk, args,
+                                               0, m->stream));
+        prof_end(m, e);
+        return check_barrier(m);
+    }
+    const dim3 grd(m->ntiles);
+    for (int n = n0; n < n1; ++n) {
+        size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
+        BH_CUDA(m, launch_pdl(k_fwd_vel, grd, blk, m->stream, r, n));
+        prof_end(m, e);
+        e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
+        BH_CUDA(m, launch_pdl(k_fwd_stress, grd, blk, m->stream, r, n));
+        prof_end(m, e);
+    }
+    return BH_OK;
+}
+
+// Reverse steps n1-1 down to n0 of every shot; the history window starts at hist_n0.
+bh_status run_adjoint(bh_model* m, int n0, int n1, int hist_n0)
+{
+    if (n1 <= n0) return BH_OK;
+    RunK r = make_run(m, n0, n1, hist_n0, false);
+    const dim3 blk = block2d();
+    if (m->persistent) {
+        const int blocks = std::min(m->ntiles, m->adj_blocks);
+        BarK b = make_bar(m, blocks);
+        BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
+        void* args[] = {&r, &b};
+        size_t e = prof_begin(m, BH_KERNEL_ADJ_PERSIST, 0);
+        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_adj_persist, dim3(blocks), blk, args,
+                                               0, m->stream));
+        prof_end(m, e);
+        return check_barrier(m);
+    }
+    const dim3 grd(m->ntiles);
+    for (int n = n1 - 1; n >= n0; --n) {
+        size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
+        BH_CUDA(m, launch_pdl(k_adj_stress, grd, blk, m->stream, r, n));
+        prof_end(m, e);
+        e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
+        BH_CUDA(m, launch_pdl(k_adj_vel, grd, blk, m->stream, r, n));
+        prof_end(m, e);
+    }
+    return BH_OK;
+}
+
+// forward state of every shot <-> snapshot slot (slot 0 is the zero state)
+bh_status snapshot(bh_model* m, int slot, bool take)
+{
+    const size_t pl = plane(m);
+    const size_t bytes = kFwdPlanes * pl * sizeof(float);
+    if (slot == 0) {
+        if (take) return fail(m, BH_ERR_STATE, "snapshot slot 0 is the initial state");
+        BH_CUDA(m, cudaMemsetAsync(m->d_fwd, 0, bytes * m->nshots, m->stream));
+        return BH_OK;
+    }
+    float* snap = m->d_snap + (size_t)(slot - 1) * m->nshots * kFwdPlanes * pl;
+    if (take)
+        BH_CUDA(m, cudaMemcpyAsync(snap, m->d_fwd, bytes * m->nshots, cudaMemcpyDeviceToDevice,
+                                   m->stream));
+    else
+        BH_CUDA(m, cudaMemcpyAsync(m->d_fwd, snap, bytes * m->nshots, cudaMemcpyDeviceToDevice,
+                                   m->stream));
+    return BH_OK;
+}
+
+// Choose the history window and snapshot count under a byte cap: for each
+// window length, the slots that fit; keep the plan with the fewest
+// recomputed forward steps.
+bh_status plan_checkpoints(bh_model* m, size_t cap)
+{
+    const int nt = m->grid.nt;
+    const double pl_bytes = (double)plane(m) * sizeof(float) * m->nshots;
+    const double snap_bytes = kFwdPlanes * pl_bytes;
+    long long best = LLONG_MAX;
+    int bestL = 0, bests = 0;
+    std::vector<int> Ls;
+    for (int L = 1; L < nt; L *= 2) Ls.push_back(L);
+    for (int L : {3, 5, 6, 10, 12, 20, 24, 40, 48, 80, 96, 100, 160, 200, 250, 400, 500})
+        if (L < nt) Ls.push_back(L);
+    Ls.push_back(nt);
+    for (int L : Ls) {
+        const double hist = (L + 1.0) * 2.0 * pl_bytes;
+        if (hist > (double)cap) continue;
+        const int nseg = (nt + L - 1) / L;
+        long long s = (long long)(((double)cap - hist) / snap_bytes);
+        s = std::min<long long>(s, nseg - 1);
+        if (s < 0) continue;
+        if (nseg > 2000 && s == 0) continue;  // quadratic plans are not worth listing
+        std::vector<Act> plan;
+        std::vector<std::pair<int, int>> spine;
+        long long adv = 0;
+        build_plan(nseg, (int)s, &plan, &spine, &adv);
+        const long long cost = adv * (long long)L + (L < nt ? nt : 0);
+        if (cost < best || (cost == best && s < bests)) {
+            best = cost;
+            bestL = L;
+            bests = (int)s;
+        }
+    }
+    if (bestL == 0)
+        return fail(m, BH_ERR_OOM, "checkpoint_cap_bytes too small for one history window");
+    m->L = bestL;
+    m->nsnap = bests;
+    long long adv = 0;
+    build_plan((nt + bestL - 1) / bestL, bests, &m->plan, &m->spine, &adv);
+    m->recompute_steps = adv * bestL + (bestL < nt ? nt : 0);
     return BH_OK;
 }
 
@@ -420,9 +679,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         g.nz != nz_global)
         return fail(nullptr, BH_ERR_INVALID_ARG, "bad grid description");
     if (g.snapshot_precision != 0)
-        return fail(nullptr, BH_ERR_UNSUPPORTED, "reduced-precision history not built");
-    if (g.checkpoint_cap_bytes != 0)
-        return fail(nullptr, BH_ERR_UNSUPPORTED, "checkpointed history not built");
+        return fail(nullptr, BH_ERR_UNSUPPORTED, "reduced-precision snapshots not built");
     int nzmax = 0, nrec_max = 0;
     for (int s = 0; s < nshots; ++s) {
         const bh_shot_desc& d = shots[s];
@@ -449,7 +706,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     m->stream = (cudaStream_t)stream;
     const int nr = g.nr;
     const size_t ng = (size_t)nr * nz_global;
-    const size_t nw = (size_t)nr * m->P;
+    const size_t pl = plane(m);
 
     auto bail = [&](bh_status s) {
         g_create_error = m->err;
@@ -464,6 +721,16 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
             return bail(e_ == cudaErrorMemoryAllocation ? BH_ERR_OOM : BH_ERR_CUDA);    \
         }                                                                               \
     } while (0)
+    // history window and checkpoints
+    if (g.checkpoint_cap_bytes == 0) {
+        m->L = g.nt;  // store every step
+        m->nsnap = 0;
+        m->plan.assign(1, Act{ACT_REVERSE, 0, 0});
+        m->recompute_steps = 0;
+    } else {
+        bh_status st = plan_checkpoints(m, g.checkpoint_cap_bytes);
+        if (st != BH_OK) return bail(st);
+    }
     CK(dalloc(&m->d_lam, ng));
     CK(dalloc(&m->d_mu, ng));
     CK(dalloc(&m->d_rho, ng));
@@ -473,10 +740,10 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_mask, ng));
     CK(dalloc(&m->d_colcov, (size_t)nz_global));
     CK(dalloc(&m->d_rprof, 6 * (size_t)nr));
-    CK(dalloc(&m->d_state, 6 * nw));
-    CK(dalloc(&m->d_psi, 16 * nw));
-    CK(dalloc(&m->d_G, 5 * nw));
-    CK(dalloc(&m->d_H, 3 * nw));
+    CK(dalloc(&m->d_fwd, (size_t)nshots * kFwdPlanes * pl));
+    CK(dalloc(&m->d_adj, (size_t)nshots * kAdjPlanes * pl));
+    CK(dalloc(&m->d_hist, (size_t)nshots * (m->L + 1) * 2 * pl));
+    CK(dalloc(&m->d_snap, (size_t)m->nsnap * nshots * kFwdPlanes * pl));
     CK(dalloc(&m->d_Hg, 2 * ng));
     CK(dalloc(&m->d_scal, 16));
     CK(dalloc(&m->d_bar, 4));
@@ -494,7 +761,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     m->shots.resize(nshots);
     std::vector<uint8_t> colcov(nz_global, 0);
     for (int s = 0; s < nshots; ++s) {
-        ShotDev& sd = m->shots[s];
+        ShotHost& sd = m->shots[s];
         const bh_shot_desc& d = shots[s];
         sd.z0 = d.z_offset;
         sd.nz = d.nz;
@@ -503,18 +770,16 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         sd.nrec = d.nrec;
         sd.rec_iz.assign(d.rec_iz, d.rec_iz + d.nrec);
         for (int j = g.npml_z; j < d.nz - g.npml_z; ++j) colcov[d.z_offset + j] = 1;
-        CK(dalloc(&sd.d_recmap, (size_t)d.nz));
-        CK(dalloc(&sd.d_zprof, 4 * (size_t)d.nz));
-        CK(dalloc(&sd.d_hist, (size_t)g.nt * 2 * nw));
     }
     CK(cudaMemcpyAsync(m->d_colcov, colcov.data(), nz_global, cudaMemcpyHostToDevice,
                        m->stream));
-    CK(cudaMemsetAsync(m->d_psi, 0, 16 * nw * sizeof(float), m->stream));
     CK(cudaStreamSynchronize(m->stream));
 #undef CK
     bh_status st = load_model(m, vp, vs, rho, true);
     if (st != BH_OK) return bail(st);
     st = setup_profiles(m);
+    if (st != BH_OK) return bail(st);
+    st = setup_shots(m);
     if (st != BH_OK) return bail(st);
     *out = m;
     return BH_OK;
@@ -537,54 +802,33 @@ bh_status bh_forward(bh_model* m, const float* wavelet, float* seis)
 {
     if (!m || !wavelet || !seis) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
     const bh_grid_desc& gd = m->grid;
-    const size_t nw = nrp(m);
+    const size_t pl = plane(m);
     const size_t seis_per_shot = (size_t)m->nrec_max * gd.nt;
-    BH_CUDA(m, cudaMemsetAsync(seis, 0, seis_per_shot * m->nshots * sizeof(float), m->stream));
+    m->have_forward = m->have_gradient = false;
     for (int s = 0; s < m->nshots; ++s) {
-        ShotDev& sd = m->shots[s];
-        WinK g = make_win(m, sd);
-        CoefK C = make_coef(m, sd);
-        StateK S = make_state(m, -1);
-        BH_CUDA(m, cudaMemsetAsync(m->d_state, 0, 6 * nw * sizeof(float), m->stream));
-        BH_CUDA(m, cudaMemsetAsync(m->d_psi, 0, 8 * nw * sizeof(float), m->stream));
-        SrcRecK q;
-        q.src_c = sd.src_ir * m->P + sd.src_iz;
-        const double V = sd.src_ir == 0
-                             ? M_PI * gd.dr * gd.dr * gd.dz
-                             : 2.0 * M_PI * (sd.src_ir + 0.5) * gd.dr * gd.dr * gd.dz;
-        q.src_scale = (float)(gd.dt / V);
-        q.wavelet = wavelet;
-        q.recmap = sd.d_recmap;
-        q.seis = seis + seis_per_shot * s;
-        q.nt = gd.nt;
-        q.hist = sd.d_hist;
-        const dim3 grd = grid_tiles(gd.nr, sd.nz), blk = block2d();
-        if (m->persistent) {
-            const int blocks = std::min(n_tiles(gd.nr, sd.nz), m->fwd_blocks);
-            BarK b = make_bar(m, blocks);
-            BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
-            q.n = 0;
-            void* args[] = {&g, &C, &S, &q, &b};
-            size_t e = prof_begin(m, BH_KERNEL_FWD_PERSIST, 0);
-            BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_fwd_persist, dim3(blocks), blk,
-                                                   args, 0, m->stream));
-            prof_end(m, e);
-            bh_status st = check_barrier(m);
-            if (st != BH_OK) return st;
-            continue;
-        }
-        for (int n = 0; n < gd.nt; ++n) {
-            q.n = n;
-            size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
-            BH_CUDA(m, launch_pdl(k_fwd_vel, grd, blk, m->stream, g, C, S));
-            prof_end(m, e);
-            e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
-            BH_CUDA(m, launch_pdl(k_fwd_stress, grd, blk, m->stream, g, C, S, q));
-            prof_end(m, e);
-        }
+        m->h_shots[s].q.wavelet = wavelet;
+        m->h_shots[s].q.seis = seis + seis_per_shot * s;
     }
+    BH_TRY(upload_shots(m));
+    BH_CUDA(m, cudaMemsetAsync(seis, 0, seis_per_shot * m->nshots * sizeof(float), m->stream));
+    BH_CUDA(m, cudaMemsetAsync(m->d_fwd, 0, (size_t)m->nshots * kFwdPlanes * pl * sizeof(float),
+                               m->stream));
+    if (m->L >= gd.nt) {
+        // store every step: one run with the history window at step 0
+        BH_TRY(run_forward(m, 0, gd.nt, 0, true));
+    } else {
+        // sweep once, recording, and take the schedule's first snapshots on the way
+        int n = 0;
+        for (const auto& sp : m->spine) {
+            const int n1 = std::min(gd.nt, sp.first * m->L);
+            BH_TRY(run_forward(m, n, n1, -1, true));
+            n = n1;
+            BH_TRY(snapshot(m, sp.second, true));
+        }
+        BH_TRY(run_forward(m, n, gd.nt, -1, true));
+    }
+    BH_LAUNCH(m);
     m->have_forward = true;
-    m->have_gradient = false;
     return BH_OK;
 }
 
@@ -607,74 +851,48 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
     if (!m || !resid || !g_lam || !g_mu) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
     if (!m->have_forward) return fail(m, BH_ERR_STATE, "bh_forward must come first");
     const bh_grid_desc& gd = m->grid;
-    const size_t nw = nrp(m);
+    const size_t pl = plane(m);
     const size_t ng = (size_t)gd.nr * m->nzg;
     const size_t seis_per_shot = (size_t)m->nrec_max * gd.nt;
+    for (int s = 0; s < m->nshots; ++s) m->h_shots[s].a.resid = resid + seis_per_shot * s;
+    BH_TRY(upload_shots(m));
     BH_CUDA(m, cudaMemsetAsync(g_lam, 0, ng * sizeof(double), m->stream));
     BH_CUDA(m, cudaMemsetAsync(g_mu, 0, ng * sizeof(double), m->stream));
     if (g_rho) BH_CUDA(m, cudaMemsetAsync(g_rho, 0, ng * sizeof(double), m->stream));
     BH_CUDA(m, cudaMemsetAsync(m->d_Hg, 0, 2 * ng * sizeof(double), m->stream));
+    BH_CUDA(m, cudaMemsetAsync(m->d_adj, 0, (size_t)m->nshots * kAdjPlanes * pl * sizeof(float),
+                               m->stream));
+    {
+        int maxnz = 0;
+        for (const auto& s : m->shots) maxnz = std::max(maxnz, s.nz);
+        k_adj_inject<<<dim3((maxnz + 127) / 128, m->nshots), 128, 0, m->stream>>>(m->d_shots,
+                                                                                 gd.nt - 1);
+        BH_LAUNCH(m);
+    }
+    for (const Act& a : m->plan) {
+        switch (a.kind) {
+        case ACT_RESTORE: BH_TRY(snapshot(m, a.a, false)); break;
+        case ACT_TAKE: BH_TRY(snapshot(m, a.a, true)); break;
+        case ACT_ADVANCE:
+            BH_TRY(run_forward(m, a.a * m->L, std::min(gd.nt, a.b * m->L), -1, false));
+            break;
+        case ACT_REVERSE: {
+            const int n0 = a.a * m->L, n1 = std::min(gd.nt, n0 + m->L);
+            if (m->L < gd.nt) BH_TRY(run_forward(m, n0, n1, n0, false));  // refill the window
+            BH_TRY(run_adjoint(m, n0, n1, n0));
+            break;
+        }
+        }
+    }
     FinK f;
     f.g_lam = g_lam;
     f.g_mu = g_mu;
     f.g_rho = g_rho;
     f.H_lam = m->d_Hg;
     f.H_mu = m->d_Hg + ng;
+    const dim3 blk = block2d();
     for (int s = 0; s < m->nshots; ++s) {
-        ShotDev& sd = m->shots[s];
-        WinK g = make_win(m, sd);
-        CoefK C = make_coef(m, sd);
-        BH_CUDA(m, cudaMemsetAsync(m->d_state, 0, 6 * nw * sizeof(float), m->stream));
-        BH_CUDA(m, cudaMemsetAsync(m->d_psi, 0, 16 * nw * sizeof(float), m->stream));
-        BH_CUDA(m, cudaMemsetAsync(m->d_G, 0, 5 * nw * sizeof(float2), m->stream));
-        BH_CUDA(m, cudaMemsetAsync(m->d_H, 0, 3 * nw * sizeof(float), m->stream));
-        AdjK q;
-        q.resid = resid + seis_per_shot * s;
-        q.recmap = sd.d_recmap;
-        q.nt = gd.nt;
-        q.hist = sd.d_hist;
-        q.G_lam = m->d_G;
-        q.G_munn = m->d_G + nw;
-        q.G_murz = m->d_G + 2 * nw;
-        q.G_br = m->d_G + 3 * nw;
-        q.G_bz = m->d_G + 4 * nw;
-        q.H_lam = m->d_H;
-        q.H_munn = m->d_H + nw;
-        q.H_murz = m->d_H + 2 * nw;
-        const dim3 grd = grid2d(gd.nr, sd.nz), blk = block2d();
-        const dim3 grt = grid_tiles(gd.nr, sd.nz);
-        q.n = gd.nt - 1;
-        k_adj_inject<<<(sd.nz + 127) / 128, 128, 0, m->stream>>>(g, make_state(m, 0), q,
-                                                                 sd.nrec);
-        if (m->persistent) {
-            const int blocks = std::min(n_tiles(gd.nr, sd.nz), m->adj_blocks);
-            BarK b = make_bar(m, blocks);
-            BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
-            StateK S0 = make_state(m, 0), S1 = make_state(m, 1);
-            void* args[] = {&g, &C, &S0, &S1, &q, &b};
-            size_t e = prof_begin(m, BH_KERNEL_ADJ_PERSIST, 0);
-            BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_adj_persist, dim3(blocks), blk,
-                                                   args, 0, m->stream));
-            prof_end(m, e);
-            bh_status st = check_barrier(m);
-            if (st != BH_OK) return st;
-            k_finalize<<<grd, blk, 0, m->stream>>>(g, C, q, f);
-            BH_LAUNCH(m);
-            continue;
-        }
-        int parity = 0;
-        for (int n = gd.nt - 1; n >= 0; --n) {
-            q.n = n;
-            StateK S = make_state(m, parity);
-            size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
-            BH_CUDA(m, launch_pdl(k_adj_stress, grt, blk, m->stream, g, C, S, q));
-            prof_end(m, e);
-            e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
-            BH_CUDA(m, launch_pdl(k_adj_vel, grt, blk, m->stream, g, C, S, q));
-            prof_end(m, e);
-            parity ^= 1;
-        }
-        k_finalize<<<grd, blk, 0, m->stream>>>(g, C, q, f);
+        k_finalize<<<grid2d(gd.nr, m->shots[s].nz), blk, 0, m->stream>>>(m->d_shots, s, f);
         BH_LAUNCH(m);
     }
     m->have_gradient = true;
@@ -721,8 +939,7 @@ bh_status bh_update(bh_model* m, const double* g_lam, const double* g_mu, double
     k_update_apply<<<nb, 256, 0, m->stream>>>(ng, m->d_mask, g_lam, g_mu, m->d_scal + 4,
                                              m->d_rho, m->d_lam, m->d_mu);
     BH_LAUNCH(m);
-    bh_status st = rebuild_coefficients(m);
-    if (st != BH_OK) return st;
+    BH_TRY(rebuild_coefficients(m));
     if (vp_out || vs_out) {
         k_velocities<<<nb, 256, 0, m->stream>>>(ng, m->d_lam, m->d_mu, m->d_rho, vp_out, vs_out);
         BH_LAUNCH(m);
@@ -768,6 +985,54 @@ bh_status bh_set_option(bh_model* m, const char* key, double value)
     return BH_OK;
 }
 
+bh_status bh_get_info(bh_model* m, const char* key, double* value)
+{
+    if (!m || !key || !value) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
+    const std::string k(key);
+    const size_t pl = plane(m), ng = (size_t)m->grid.nr * m->nzg;
+    if (k == "history_steps") *value = m->L;
+    else if (k == "snapshots") *value = m->nsnap;
+    else if (k == "recompute_steps") *value = (double)m->recompute_steps;
+    else if (k == "tiles") *value = m->ntiles;
+    else if (k == "persistent_blocks_fwd") *value = m->fwd_blocks;
+    else if (k == "persistent_blocks_adj") *value = m->adj_blocks;
+    else if (k == "persistent") *value = m->persistent;
+    else if (k == "history_snapshot_bytes")
+        *value = (double)pl * sizeof(float) * m->nshots *
+                 (2.0 * (m->L + 1) + (double)m->nsnap * kFwdPlanes);
+    else if (k == "device_bytes")
+        *value = (double)pl * sizeof(float) * m->nshots *
+                     (kFwdPlanes + kAdjPlanes + 2.0 * (m->L + 1) + (double)m->nsnap * kFwdPlanes) +
+                 (double)ng * (6 * sizeof(float) + 1 + 2 * sizeof(double));
+    else return fail(m, BH_ERR_INVALID_ARG, "unknown key " + k);
+    return BH_OK;
+}
+
+bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
+                             int* n_actions, int* spine, int max_spine, int* n_spine)
+{
+    if (nseg < 1 || nsnap < 0 || !actions || !n_actions || !spine || !n_spine)
+        return fail(nullptr, BH_ERR_INVALID_ARG, "bad argument");
+    std::vector<Act> plan;
+    std::vector<std::pair<int, int>> sp;
+    long long adv = 0;
+    build_plan(nseg, nsnap, &plan, &sp, &adv);
+    *n_actions = (int)plan.size();
+    *n_spine = (int)sp.size();
+    if ((int)plan.size() > max_actions || (int)sp.size() > max_spine)
+        return fail(nullptr, BH_ERR_INVALID_ARG, "output arrays too small");
+    for (size_t k = 0; k < plan.size(); ++k) {
+        actions[3 * k] = plan[k].kind;
+        actions[3 * k + 1] = plan[k].a;
+        actions[3 * k + 2] = plan[k].b;
+    }
+    for (size_t k = 0; k < sp.size(); ++k) {
+        spine[2 * k] = sp[k].first;
+        spine[2 * k + 1] = sp[k].second;
+    }
+    return BH_OK;
+}
+
 bh_status bh_profile_enable(bh_model* m, int every)
 {
     if (!m || every < 0) return fail(m, BH_ERR_INVALID_ARG, "bad argument");
@@ -800,8 +1065,7 @@ bh_status bh_profile_reset(bh_model* m)
     if (!m) return fail(m, BH_ERR_INVALID_ARG, "NULL model");
     double t;
     long n;
-    bh_status st = bh_profile_read(m, 0, &t, &n);
-    if (st != BH_OK) return st;
+    BH_TRY(bh_profile_read(m, 0, &t, &n));
     for (int k = 0; k < BH_KERNEL_COUNT; ++k) {
         m->prof_ms[k] = 0.0;
         m->prof_n[k] = 0;
