@@ -160,12 +160,15 @@ class ClockSampler:
 
 
 def workload_config(w, nt=None):
-    return {"workload": f"{w.name}: single-shot borehole FWI iteration, nr {w.nr} x nz {w.nz} "
-                        f"cells (C-PML {w.npml_r}/{w.npml_z}), {nt or w.nt} steps, "
+    shots = (f"{w.nshots} shots, windows nz {min(s['nz'] for s in w.shots)}-"
+             f"{max(s['nz'] for s in w.shots)} of a {w.nz}-cell model" if w.nshots > 1
+             else f"single shot, nz {w.nz}")
+    return {"workload": f"{w.name}: borehole FWI iteration, {shots}, nr {w.nr} "
+                        f"(C-PML {w.npml_r}/{w.npml_z}), {nt or w.nt} steps, "
                         f"h {w.dr} m, dt {w.dt} s, f0 {w.f0:g} Hz, {w.nrec} receivers",
             "nr": w.nr, "nz": w.nz, "nt": nt or w.nt, "nshots": w.nshots,
             "l2": "inputs larger than L2: the forward history streamed every step is "
-                  f"{2 * 8 * w.nr * w.nz * (nt or w.nt) / 1e9:.1f} GB (write + read)"}
+                  f"{2 * 8 * w.cell_steps() * (nt or w.nt) / w.nt / 1e9:.1f} GB (write + read)"}
 
 
 # ---------------------------------------------------------------- oracle
@@ -247,7 +250,8 @@ def run_gpu(args, w):
     stream = torch.cuda.current_stream(dev)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     # observed data: forward modelling in the true model (outside the timing)
-    true = model_from_workload(w, device=dev)
+    cap = int(args.cap_gb * 1e9)
+    true = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap)
     true.set_model(t(w.vp_true), t(w.vs_true), t(w.rho_true))
     wav = t(w.wavelet)
     obs = true.forward(wav).clone()
@@ -255,7 +259,7 @@ def run_gpu(args, w):
     true.close()
     del true
 
-    m = model_from_workload(w, device=dev)
+    m = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap)
     if args.per_step:
         m.set_option("persistent", 0)
     start_model = (t(w.vp), t(w.vs), t(w.rho))
@@ -339,7 +343,7 @@ def run_gpu(args, w):
     h2d = wav_h.numel() * 4 + obs_h.numel() * 4
     d2h = 8 + vp_h.numel() * 4 * 2
 
-    cells_per_step = 2.0 * w.cell_steps()          # forward + adjoint cell updates
+    cells_per_step = 2.0 * w.cell_steps()          # forward + adjoint cell updates (useful work)
     value = world * cells_per_step * args.steps / (ms / 1e3) / 1e9
     grads_per_s = world * w.nshots * args.steps / (ms / 1e3)
     value_e2e = world * cells_per_step * args.steps / (ms_e2e / 1e3) / 1e9
@@ -349,30 +353,39 @@ def run_gpu(args, w):
     s = w.npml_r / w.nr + 2.0 * w.npml_z / w.nz
     prof = {k: v for k, v in prof.items() if v[1]}
     dom = max(prof, key=lambda k: prof[k][0])
-    tot_ms, nlaunch = prof[dom]
+    win_cells = sum(w.nr * sh["nz"] for sh in w.shots)   # one pass over every window
+    recompute = m.info("recompute_steps")
 
-    def launch_cells(k):
-        # one per-step launch covers the window once; a persistent one nt times
-        return w.nr * w.nz * (w.nt if k in PERSIST_PARTS else 1)
+    def kernel_cells(k):
+        """cells the sampled launches of kernel k processed in the timed region"""
+        if k == "fwd_persist":
+            return win_cells * (w.nt + recompute) * args.steps
+        if k == "adj_persist":
+            return win_cells * w.nt * args.steps
+        return win_cells * prof[k][1]                  # one pass per per-step launch
 
-    alg_bytes = bytes_per_cell_step(dom, s) * launch_cells(dom)
-    achieved = alg_bytes / (tot_ms / nlaunch / 1e3) / 1e9 if nlaunch else None
-    kernels = {k: {"avg_us": 1e3 * v[0] / v[1], "sampled_launches": v[1],
-                   "alg_bytes_per_launch": bytes_per_cell_step(k, s) * launch_cells(k),
-                   "alg_GBps": bytes_per_cell_step(k, s) * launch_cells(k) /
-                               (v[0] / v[1] / 1e3) / 1e9}
-               for k, v in prof.items()}
-    step_bytes = sum(kernel_bytes_per_cell(k, s) for k in PERSIST_PARTS["fwd_persist"] +
-                     PERSIST_PARTS["adj_persist"]) * w.nr * w.nz * w.nt
+    kernels = {}
+    for k, (tms, nl) in prof.items():
+        alg = bytes_per_cell_step(k, s) * kernel_cells(k)
+        kernels[k] = {"avg_us": 1e3 * tms / nl, "sampled_launches": nl,
+                      "alg_bytes_per_launch": alg / nl, "alg_GBps": alg / (tms / 1e3) / 1e9}
+    achieved = kernels[dom]["alg_GBps"]
+    step_bytes = (sum(kernel_bytes_per_cell(k, s) for k in PERSIST_PARTS["fwd_persist"]) *
+                  win_cells * (w.nt + recompute) +
+                  sum(kernel_bytes_per_cell(k, s) for k in PERSIST_PARTS["adj_persist"]) *
+                  win_cells * w.nt)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak if achieved else None,
                 "traffic": ncu_traffic(dom, w.name), "peak_source": f"{peak_kind} (hbm_gbs)",
-                "note": "state of one 240 x 1600 window (~9 MB) stays in the 129 MB L2; "
-                        "algorithmic bytes count every array once per launch"}
+                "note": "algorithmic bytes count every array a launch touches once per cell "
+                        "and step; a single 240 x 1600 window (~9 MB of state) stays in the "
+                        "129 MB L2, so there the kernels run from L2"}
+    # launches of this library per inversion step
+    other = 1 + 2 + 4 + w.nshots + 1            # misfit, precondition, update, finalize, inject
     if args.per_step:
-        launches_per_step = w.nshots * (4 * w.nt + 2) + 1 + 2 + 4
+        launches_per_step = int(m.info("persistent_runs_per_step")) + other
     else:
-        launches_per_step = w.nshots * 4 + 1 + 2 + 4
+        launches_per_step = int(m.info("persistent_runs_per_step")) + other
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -385,6 +398,9 @@ def run_gpu(args, w):
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / args.steps},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(), "J_first_last": [Js[0], Js[-1]],
+            "history": {k: m.info(k) for k in ("history_steps", "snapshots", "recompute_steps",
+                                               "history_snapshot_bytes", "tiles",
+                                               "persistent_blocks_fwd", "persistent_blocks_adj")},
             "source_sha": source_sha()}
     if rank == 0 and not args.no_cpu_baseline:
         v, sec, threads = oracle_sample(w, CPU_SAMPLE_STEPS)
@@ -406,7 +422,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--config", default="c1", choices=["c0", "c1"])
+    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--cap-gb", type=float, default=0.0,
+                    help="checkpoint cap in GB (0: store every step of the forward history)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-step", action="store_true",
                     help="one kernel launch per half-step instead of the persistent kernels")

@@ -126,7 +126,8 @@ bh_status bh_set_model(bh_model* model, const float* vp, const float* vs, const 
  * recorded as the mean normal stress at the receivers ("normal stress ...
  * at the receiver positions", Method section).  Keeps the forward history
  * needed by bh_adjoint_gradient.
- *   wavelet  device [nt] float32
+ *   wavelet  device [nt] float32; with checkpointing it is read again by
+ *            the next bh_adjoint_gradient, so it must stay valid until then
  *   seis     device [nshots][nrec_max][nt] float32, row n = after step n;
  *            entries of receivers a shot does not have are set to 0
  * Errors: BH_ERR_INVALID_ARG, BH_ERR_CUDA.
@@ -275,7 +276,8 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
  * Read-only facts about a model (the paper has no counterpart):
  * "history_steps" (L), "snapshots" (s), "recompute_steps" (forward steps
  * re-run by one bh_adjoint_gradient), "tiles", "persistent",
- * "persistent_blocks_fwd", "persistent_blocks_adj",
+ * "persistent_blocks_fwd", "persistent_blocks_adj", "persistent_runs_per_step"
+ * (stepping-kernel launches of the last bh_forward + bh_adjoint_gradient),
  * "history_snapshot_bytes", "device_bytes".
  *   value  host double
  * Errors: BH_ERR_INVALID_ARG (unknown key).

@@ -68,6 +68,7 @@ struct bh_model {
     std::vector<Act> plan;      // reversal after the forward sweep
     std::vector<std::pair<int, int>> spine;  // (segment, slot) taken during the sweep
     long long recompute_steps = 0;
+    long long runs_fwd = 0, runs_adj = 0;  // stepping runs of the last forward / adjoint call
     double* d_Hg = nullptr;     // H_lam, H_mu global [2][nr*nzg]
     double* d_scal = nullptr;   // small device scalars
     bool have_forward = false, have_gradient = false;
@@ -516,9 +517,10 @@ RunK make_run(const bh_model* m, int n0, int n1, int hist_n0, bool record)
 }
 
 // Forward steps n0 .. n1-1 of every shot.
-bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record)
+bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, long long* runs)
 {
     if (n1 <= n0) return BH_OK;
+    *runs += m->persistent ? 1 : 2 * (n1 - n0);
     RunK r = make_run(m, n0, n1, hist_n0, record);
     const dim3 blk = block2d();
     if (m->persistent) {
@@ -545,9 +547,10 @@ bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record)
 }
 
 // Reverse steps n1-1 down to n0 of every shot; the history window starts at hist_n0.
-bh_status run_adjoint(bh_model* m, int n0, int n1, int hist_n0)
+bh_status run_adjoint(bh_model* m, int n0, int n1, int hist_n0, long long* runs)
 {
     if (n1 <= n0) return BH_OK;
+    *runs += m->persistent ? 1 : 2 * (n1 - n0);
     RunK r = make_run(m, n0, n1, hist_n0, false);
     const dim3 blk = block2d();
     if (m->persistent) {
@@ -805,6 +808,7 @@ bh_status bh_forward(bh_model* m, const float* wavelet, float* seis)
     const size_t pl = plane(m);
     const size_t seis_per_shot = (size_t)m->nrec_max * gd.nt;
     m->have_forward = m->have_gradient = false;
+    m->runs_fwd = 0;
     for (int s = 0; s < m->nshots; ++s) {
         m->h_shots[s].q.wavelet = wavelet;
         m->h_shots[s].q.seis = seis + seis_per_shot * s;
@@ -815,17 +819,17 @@ bh_status bh_forward(bh_model* m, const float* wavelet, float* seis)
                                m->stream));
     if (m->L >= gd.nt) {
         // store every step: one run with the history window at step 0
-        BH_TRY(run_forward(m, 0, gd.nt, 0, true));
+        BH_TRY(run_forward(m, 0, gd.nt, 0, true, &m->runs_fwd));
     } else {
         // sweep once, recording, and take the schedule's first snapshots on the way
         int n = 0;
         for (const auto& sp : m->spine) {
             const int n1 = std::min(gd.nt, sp.first * m->L);
-            BH_TRY(run_forward(m, n, n1, -1, true));
+            BH_TRY(run_forward(m, n, n1, -1, true, &m->runs_fwd));
             n = n1;
             BH_TRY(snapshot(m, sp.second, true));
         }
-        BH_TRY(run_forward(m, n, gd.nt, -1, true));
+        BH_TRY(run_forward(m, n, gd.nt, -1, true, &m->runs_fwd));
     }
     BH_LAUNCH(m);
     m->have_forward = true;
@@ -854,6 +858,7 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
     const size_t pl = plane(m);
     const size_t ng = (size_t)gd.nr * m->nzg;
     const size_t seis_per_shot = (size_t)m->nrec_max * gd.nt;
+    m->runs_adj = 0;
     for (int s = 0; s < m->nshots; ++s) m->h_shots[s].a.resid = resid + seis_per_shot * s;
     BH_TRY(upload_shots(m));
     BH_CUDA(m, cudaMemsetAsync(g_lam, 0, ng * sizeof(double), m->stream));
@@ -874,12 +879,14 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
         case ACT_RESTORE: BH_TRY(snapshot(m, a.a, false)); break;
         case ACT_TAKE: BH_TRY(snapshot(m, a.a, true)); break;
         case ACT_ADVANCE:
-            BH_TRY(run_forward(m, a.a * m->L, std::min(gd.nt, a.b * m->L), -1, false));
+            BH_TRY(run_forward(m, a.a * m->L, std::min(gd.nt, a.b * m->L), -1, false,
+                               &m->runs_adj));
             break;
         case ACT_REVERSE: {
             const int n0 = a.a * m->L, n1 = std::min(gd.nt, n0 + m->L);
-            if (m->L < gd.nt) BH_TRY(run_forward(m, n0, n1, n0, false));  // refill the window
-            BH_TRY(run_adjoint(m, n0, n1, n0));
+            if (m->L < gd.nt)  // refill the window
+                BH_TRY(run_forward(m, n0, n1, n0, false, &m->runs_adj));
+            BH_TRY(run_adjoint(m, n0, n1, n0, &m->runs_adj));
             break;
         }
         }
@@ -994,6 +1001,7 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "snapshots") *value = m->nsnap;
     else if (k == "recompute_steps") *value = (double)m->recompute_steps;
     else if (k == "tiles") *value = m->ntiles;
+    else if (k == "persistent_runs_per_step") *value = (double)(m->runs_fwd + m->runs_adj);
     else if (k == "persistent_blocks_fwd") *value = m->fwd_blocks;
     else if (k == "persistent_blocks_adj") *value = m->adj_blocks;
     else if (k == "persistent") *value = m->persistent;
