@@ -807,9 +807,17 @@ struct ShotK {
     float* hist;    // history window: slot k = v_r, v_z planes of v^{hist_n0 + k - 1/2}
 };
 
+// The shots of one launch travel in the kernel's parameter space (constant
+// bank, no loads in the tile code); batches larger than kGroup run as
+// several launches.
+constexpr int kGroup = 32;
+template <int N>
+struct ShotTable {
+    ShotK s[N];
+};
+
 struct RunK {
-    const ShotK* shots;
-    const int4* tiles;  // (shot, i0, j0, 0)
+    const int4* tiles;  // (shot within the table, i0, j0, 0)
     int ntiles;
     int n0, n1;         // forward: steps n0 .. n1-1; adjoint: n1-1 down to n0
     int hist_n0;        // history slot 0 holds v^{hist_n0 - 1/2}; -1: no history
@@ -817,108 +825,133 @@ struct RunK {
     int nt;             // steps of the whole run (adjoint memory bank parity)
 };
 
-__device__ __forceinline__ float* hist_slot(const ShotK& sh, const RunK& r, int k)
+__device__ __forceinline__ float* hist_slot(const ShotK& sh, int k)
 {
     return sh.hist + (size_t)k * 2 * sh.g.nr * sh.g.P;
 }
 
-__device__ __forceinline__ void run_fwd_vel(const RunK& r, int n, int t, FwdSmem& sm)
+template <int N>
+__device__ __forceinline__ const ShotK& shot_of(const ShotTable<N>& T, int4 tk)
+{
+    return T.s[N == 1 ? 0 : tk.x];
+}
+
+template <int N>
+__device__ __forceinline__ void run_fwd_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
+                                            FwdSmem& sm)
 {
     const int4 tk = r.tiles[t];
-    const ShotK& sh = r.shots[tk.x];
-    float* h0 = (r.hist_n0 >= 0 && n == r.hist_n0) ? hist_slot(sh, r, 0) : nullptr;
+    const ShotK& sh = shot_of(T, tk);
+    float* h0 = (r.hist_n0 >= 0 && n == r.hist_n0) ? hist_slot(sh, 0) : nullptr;
     fwd_vel_tile(sh.g, sh.C, sh.Sf, h0, tk.y, tk.z, sm);
 }
 
-__device__ __forceinline__ void run_fwd_stress(const RunK& r, int n, int t, FwdSmem& sm)
+template <int N>
+__device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>& T, int n,
+                                               int t, FwdSmem& sm)
 {
     const int4 tk = r.tiles[t];
-    const ShotK& sh = r.shots[tk.x];
-    float* h = r.hist_n0 >= 0 ? hist_slot(sh, r, n - r.hist_n0 + 1) : nullptr;
+    const ShotK& sh = shot_of(T, tk);
+    float* h = r.hist_n0 >= 0 ? hist_slot(sh, n - r.hist_n0 + 1) : nullptr;
     fwd_stress_tile(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, sm);
 }
 
-__device__ __forceinline__ void run_adj_stress(const RunK& r, int n, int t, AdjSmem& sm)
+template <int N>
+__device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>& T, int n,
+                                               int t, AdjSmem& sm)
 {
     const int4 tk = r.tiles[t];
-    const ShotK& sh = r.shots[tk.x];
+    const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
-    adj_stress_tile(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, r, n - r.hist_n0 + 1),
-                    hist_slot(sh, r, n - r.hist_n0), tk.y, tk.z, sm);
+    adj_stress_tile(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, n - r.hist_n0 + 1),
+                    hist_slot(sh, n - r.hist_n0), tk.y, tk.z, sm);
 }
 
-__device__ __forceinline__ void run_adj_vel(const RunK& r, int n, int t, AdjSmem& sm)
+template <int N>
+__device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
+                                            AdjSmem& sm)
 {
     const int4 tk = r.tiles[t];
-    const ShotK& sh = r.shots[tk.x];
+    const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
     adj_vel_tile(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, sm);
 }
 
-// one launch per half-step: one block per tile of every shot
-__global__ void __launch_bounds__(kThreads) k_fwd_vel(RunK r, int n)
+// one launch per half-step: one block per tile
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_fwd_vel(RunK r, int n,
+                                                      const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
-    run_fwd_vel(r, n, blockIdx.x, sm);
+    run_fwd_vel(r, T, n, blockIdx.x, sm);
     pdl_launch_dependents();
 }
 
-__global__ void __launch_bounds__(kThreads) k_fwd_stress(RunK r, int n)
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_fwd_stress(RunK r, int n,
+                                                         const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
-    run_fwd_stress(r, n, blockIdx.x, sm);
+    run_fwd_stress(r, T, n, blockIdx.x, sm);
     pdl_launch_dependents();
 }
 
-__global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n)
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n,
+                                                         const __grid_constant__ ShotTable<N> T)
 {
     __shared__ AdjSmem sm;
     pdl_wait();
-    run_adj_stress(r, n, blockIdx.x, sm);
+    run_adj_stress(r, T, n, blockIdx.x, sm);
     pdl_launch_dependents();
 }
 
-__global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n)
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
+                                                      const __grid_constant__ ShotTable<N> T)
 {
     __shared__ AdjSmem sm;
     pdl_wait();
-    run_adj_vel(r, n, blockIdx.x, sm);
+    run_adj_vel(r, T, n, blockIdx.x, sm);
     pdl_launch_dependents();
 }
 
-// every step n0 .. n1-1 of every shot in one cooperative launch
-__global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(RunK r, BarK b)
+// every step n0 .. n1-1 of every shot of the table in one cooperative launch
+template <int N>
+__global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(RunK r, BarK b,
+                                                             const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     unsigned epoch = 0;
     for (int n = r.n0; n < r.n1; ++n) {
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_fwd_vel(r, n, t, sm);
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_fwd_vel(r, T, n, t, sm);
         if (!grid_barrier(b, epoch)) return;
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_fwd_stress(r, n, t, sm);
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_fwd_stress(r, T, n, t, sm);
         if (!grid_barrier(b, epoch)) return;
     }
 }
 
-// reverse steps n1-1 down to n0 of every shot in one cooperative launch
-__global__ void __launch_bounds__(kThreads, 5) k_adj_persist(RunK r, BarK b)
+// reverse steps n1-1 down to n0 of every shot of the table in one cooperative launch
+template <int N>
+__global__ void __launch_bounds__(kThreads, 5) k_adj_persist(RunK r, BarK b,
+                                                             const __grid_constant__ ShotTable<N> T)
 {
     __shared__ AdjSmem sm;
     unsigned epoch = 0;
     for (int n = r.n1 - 1; n >= r.n0; --n) {
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_adj_stress(r, n, t, sm);
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_adj_stress(r, T, n, t, sm);
         if (!grid_barrier(b, epoch)) return;
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_adj_vel(r, n, t, sm);
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_adj_vel(r, T, n, t, sm);
         if (!grid_barrier(b, epoch)) return;
     }
 }
 
-// transpose of the recording at the last step, every shot (grid.y = shot):
-// dp[nt-1]/3 into each normal stress of the receiver cells
-__global__ void k_adj_inject(const ShotK* shots, int n)
+// transpose of the recording at the last step of one shot: dp[nt-1]/3 into
+// each normal stress of the receiver cells
+__global__ void k_adj_inject(const __grid_constant__ ShotK sh, int n)
 {
-    const ShotK& sh = shots[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= sh.g.nz) return;
     const int r = sh.a.recmap[k];
@@ -944,11 +977,11 @@ __device__ __forceinline__ double kval(const float2* a, size_t k)
 
 // Chain rule from the node accumulators of one shot to per-cell gradients,
 // added into the global FP64 arrays.  Cells of the window's C-PML get nothing.
-__global__ void k_finalize(const ShotK* shots, int s, FinK f)
+__global__ void k_finalize(const __grid_constant__ ShotK sh, FinK f)
 {
-    const WinK& g = shots[s].g;
-    const CoefK& C = shots[s].C;
-    const AdjK& q = shots[s].a;
+    const WinK& g = sh.g;
+    const CoefK& C = sh.C;
+    const AdjK& q = sh.a;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= g.nr - g.npml_r || j < g.npml_z || j >= g.nz - g.npml_z) return;
@@ -975,10 +1008,12 @@ __global__ void k_finalize(const ShotK* shots, int s, FinK f)
             hm += mult * 0.25 * (double)q.H_murz[k];
         }
     }
-    f.g_lam[cg] += gl;
-    f.g_mu[cg] += gm;
-    f.H_lam[cg] += hl;
-    f.H_mu[cg] += hm;
+    // plain adds (no fused multiply-add into the running sums): the sum over
+    // shots rounds the same way however the shots are batched
+    f.g_lam[cg] = __dadd_rn(f.g_lam[cg], gl);
+    f.g_mu[cg] = __dadd_rn(f.g_mu[cg], gm);
+    f.H_lam[cg] = __dadd_rn(f.H_lam[cg], hl);
+    f.H_mu[cg] = __dadd_rn(f.H_mu[cg], hm);
     if (f.g_rho) {
         // buoyancy nodes that average this cell: v_r rows i, i+1; v_z columns j-1, j
         double gb = 0.0;
@@ -995,7 +1030,7 @@ __global__ void k_finalize(const ShotK* shots, int s, FinK f)
             size_t k = (size_t)i * g.P + jj;
             gb += mult * kval(q.G_bz, k) / (double)bvz_at(C, g, i, jj);
         }
-        f.g_rho[cg] += -0.5 / (rho * rho) * gb;
+        f.g_rho[cg] = __dadd_rn(f.g_rho[cg], __dmul_rn(-0.5 / (rho * rho), gb));
     }
 }
 

@@ -59,9 +59,9 @@ struct bh_model {
     float* d_hist = nullptr;    // per shot (L + 1) x 2 planes
     float* d_snap = nullptr;    // per shot nsnap x kFwdPlanes planes
     std::vector<ShotK> h_shots;
-    ShotK* d_shots = nullptr;
-    int4* d_tiles = nullptr;
+    int4* d_tiles = nullptr;    // tiles of every shot group, group after group
     int ntiles = 0;
+    std::vector<int> group_tile_off, group_ntiles;  // per group of up to kGroup shots
     // history window and checkpoint schedule
     int L = 0;                  // steps per history window (nt: store every step)
     int nsnap = 0;              // stored snapshot slots (slot 0 is the zero state)
@@ -75,7 +75,8 @@ struct bh_model {
     std::string err;
     // persistent (one cooperative launch per run) or one launch per half-step
     int persistent = 1;
-    int fwd_blocks = 0, adj_blocks = 0;
+    int fwd_blocks = 0, adj_blocks = 0;       // co-resident blocks, 1-shot kernels
+    int fwd_blocks_g = 0, adj_blocks_g = 0;   // same, kGroup-shot kernels
     unsigned* d_bar = nullptr;          // barrier: count, -, error flag
     double barrier_timeout_ms = 2000.0;
     int barrier_extra = 0;              // test knob: arrivals that never come
@@ -131,7 +132,7 @@ void free_model(bh_model* m)
     if (!m) return;
     void* bufs[] = {m->d_lam,   m->d_mu,     m->d_rho,   m->d_bvr,    m->d_bvz,    m->d_muh,
                     m->d_mask,  m->d_colcov, m->d_rprof, m->d_zprof,  m->d_recmap, m->d_fwd,
-                    m->d_adj,   m->d_hist,   m->d_snap,  m->d_shots,  m->d_tiles,  m->d_Hg,
+                    m->d_adj,   m->d_hist,   m->d_snap,  m->d_tiles,  m->d_Hg,
                     m->d_scal,  m->d_bar};
     for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
@@ -412,11 +413,17 @@ bh_status setup_shots(bh_model* m)
         k.a.H_munn = a + 33 * pl;
         k.a.H_murz = a + 34 * pl;
         k.hist = m->d_hist + (size_t)s * (m->L + 1) * 2 * pl;
+        if (s % kGroup == 0) {
+            m->group_tile_off.push_back((int)tiles.size());
+            m->group_ntiles.push_back(0);
+        }
         for (int i0 = 0; i0 < nr; i0 += kTR)
-            for (int j0 = 0; j0 < sh.nz; j0 += kTZ) tiles.push_back(make_int4(s, i0, j0, 0));
+            for (int j0 = 0; j0 < sh.nz; j0 += kTZ) {
+                tiles.push_back(make_int4(s % kGroup, i0, j0, 0));
+                m->group_ntiles.back()++;
+            }
     }
     m->ntiles = (int)tiles.size();
-    BH_CUDA(m, dalloc(&m->d_shots, (size_t)m->nshots));
     BH_CUDA(m, dalloc(&m->d_tiles, tiles.size()));
     BH_CUDA(m, cudaMemcpyAsync(m->d_tiles, tiles.data(), tiles.size() * sizeof(int4),
                                cudaMemcpyHostToDevice, m->stream));
@@ -424,13 +431,14 @@ bh_status setup_shots(bh_model* m)
     return BH_OK;
 }
 
-// Re-upload the shot table after the per-call pointers changed.
-bh_status upload_shots(bh_model* m)
+// shot table of one group, passed by value to the stepping kernels
+template <int N>
+ShotTable<N> group_table(const bh_model* m, int grp)
 {
-    BH_CUDA(m, cudaMemcpyAsync(m->d_shots, m->h_shots.data(), m->h_shots.size() * sizeof(ShotK),
-                               cudaMemcpyHostToDevice, m->stream));
-    // the source is pageable host memory: it is staged before the call returns
-    return BH_OK;
+    ShotTable<N> T;
+    memset(&T, 0, sizeof(T));
+    for (int k = 0; k < N && grp * kGroup + k < m->nshots; ++k) T.s[k] = m->h_shots[grp * kGroup + k];
+    return T;
 }
 
 // ------------------------------------------------------------------ runs
@@ -502,12 +510,11 @@ bh_status check_barrier(bh_model* m)
     return BH_OK;
 }
 
-RunK make_run(const bh_model* m, int n0, int n1, int hist_n0, bool record)
+RunK make_run(const bh_model* m, int grp, int n0, int n1, int hist_n0, bool record)
 {
     RunK r;
-    r.shots = m->d_shots;
-    r.tiles = m->d_tiles;
-    r.ntiles = m->ntiles;
+    r.tiles = m->d_tiles + m->group_tile_off[grp];
+    r.ntiles = m->group_ntiles[grp];
     r.n0 = n0;
     r.n1 = n1;
     r.hist_n0 = hist_n0;
@@ -516,32 +523,75 @@ RunK make_run(const bh_model* m, int n0, int n1, int hist_n0, bool record)
     return r;
 }
 
-// Forward steps n0 .. n1-1 of every shot.
-bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, long long* runs)
+// Forward steps n0 .. n1-1 of the shots of one group.
+template <int N>
+bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, bool record)
 {
-    if (n1 <= n0) return BH_OK;
-    *runs += m->persistent ? 1 : 2 * (n1 - n0);
-    RunK r = make_run(m, n0, n1, hist_n0, record);
+    RunK r = make_run(m, grp, n0, n1, hist_n0, record);
+    ShotTable<N> T = group_table<N>(m, grp);
     const dim3 blk = block2d();
     if (m->persistent) {
-        const int blocks = std::min(m->ntiles, m->fwd_blocks);
+        const int blocks = std::min(r.ntiles, N == 1 ? m->fwd_blocks : m->fwd_blocks_g);
         BarK b = make_bar(m, blocks);
         BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
-        void* args[] = {&r, &b};
+        void* args[] = {&r, &b, &T};
         size_t e = prof_begin(m, BH_KERNEL_FWD_PERSIST, 0);
-        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_fwd_persist, dim3(blocks), blk, args,
-                                               0, m->stream));
+        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_fwd_persist<N>, dim3(blocks), blk,
+                                               args, 0, m->stream));
         prof_end(m, e);
         return check_barrier(m);
     }
-    const dim3 grd(m->ntiles);
+    const dim3 grd(r.ntiles);
     for (int n = n0; n < n1; ++n) {
         size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
-        BH_CUDA(m, launch_pdl(k_fwd_vel, grd, blk, m->stream, r, n));
+        BH_CUDA(m, launch_pdl(k_fwd_vel<N>, grd, blk, m->stream, r, n, T));
         prof_end(m, e);
         e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
-        BH_CUDA(m, launch_pdl(k_fwd_stress, grd, blk, m->stream, r, n));
+        BH_CUDA(m, launch_pdl(k_fwd_stress<N>, grd, blk, m->stream, r, n, T));
         prof_end(m, e);
+    }
+    return BH_OK;
+}
+
+// Reverse steps n1-1 down to n0 of the shots of one group.
+template <int N>
+bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
+{
+    RunK r = make_run(m, grp, n0, n1, hist_n0, false);
+    ShotTable<N> T = group_table<N>(m, grp);
+    const dim3 blk = block2d();
+    if (m->persistent) {
+        const int blocks = std::min(r.ntiles, N == 1 ? m->adj_blocks : m->adj_blocks_g);
+        BarK b = make_bar(m, blocks);
+        BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
+        void* args[] = {&r, &b, &T};
+        size_t e = prof_begin(m, BH_KERNEL_ADJ_PERSIST, 0);
+        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_adj_persist<N>, dim3(blocks), blk,
+                                               args, 0, m->stream));
+        prof_end(m, e);
+        return check_barrier(m);
+    }
+    const dim3 grd(r.ntiles);
+    for (int n = n1 - 1; n >= n0; --n) {
+        size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
+        BH_CUDA(m, launch_pdl(k_adj_stress<N>, grd, blk, m->stream, r, n, T));
+        prof_end(m, e);
+        e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
+        BH_CUDA(m, launch_pdl(k_adj_vel<N>, grd, blk, m->stream, r, n, T));
+        prof_end(m, e);
+    }
+    return BH_OK;
+}
+
+// Forward steps n0 .. n1-1 of every shot, group by group.
+bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, long long* runs)
+{
+    if (n1 <= n0) return BH_OK;
+    const int ngroups = (int)m->group_ntiles.size();
+    for (int grp = 0; grp < ngroups; ++grp) {
+        *runs += m->persistent ? 1 : 2 * (n1 - n0);
+        if (m->nshots == 1) BH_TRY(run_forward_group<1>(m, grp, n0, n1, hist_n0, record));
+        else BH_TRY(run_forward_group<kGroup>(m, grp, n0, n1, hist_n0, record));
     }
     return BH_OK;
 }
@@ -550,28 +600,11 @@ bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, lon
 bh_status run_adjoint(bh_model* m, int n0, int n1, int hist_n0, long long* runs)
 {
     if (n1 <= n0) return BH_OK;
-    *runs += m->persistent ? 1 : 2 * (n1 - n0);
-    RunK r = make_run(m, n0, n1, hist_n0, false);
-    const dim3 blk = block2d();
-    if (m->persistent) {
-        const int blocks = std::min(m->ntiles, m->adj_blocks);
-        BarK b = make_bar(m, blocks);
-        BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
-        void* args[] = {&r, &b};
-        size_t e = prof_begin(m, BH_KERNEL_ADJ_PERSIST, 0);
-        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_adj_persist, dim3(blocks), blk, args,
-                                               0, m->stream));
-        prof_end(m, e);
-        return check_barrier(m);
-    }
-    const dim3 grd(m->ntiles);
-    for (int n = n1 - 1; n >= n0; --n) {
-        size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
-        BH_CUDA(m, launch_pdl(k_adj_stress, grd, blk, m->stream, r, n));
-        prof_end(m, e);
-        e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
-        BH_CUDA(m, launch_pdl(k_adj_vel, grd, blk, m->stream, r, n));
-        prof_end(m, e);
+    const int ngroups = (int)m->group_ntiles.size();
+    for (int grp = 0; grp < ngroups; ++grp) {
+        *runs += m->persistent ? 1 : 2 * (n1 - n0);
+        if (m->nshots == 1) BH_TRY(run_adjoint_group<1>(m, grp, n0, n1, hist_n0));
+        else BH_TRY(run_adjoint_group<kGroup>(m, grp, n0, n1, hist_n0));
     }
     return BH_OK;
 }
@@ -755,11 +788,17 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist, kThreads, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<1>, kThreads, 0));
         m->fwd_blocks = nb * sms;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist, kThreads, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<1>, kThreads, 0));
         m->adj_blocks = nb * sms;
-        if (!coop || m->fwd_blocks < 1 || m->adj_blocks < 1) m->persistent = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<kGroup>, kThreads, 0));
+        m->fwd_blocks_g = nb * sms;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<kGroup>, kThreads, 0));
+        m->adj_blocks_g = nb * sms;
+        if (!coop || std::min(std::min(m->fwd_blocks, m->adj_blocks),
+                              std::min(m->fwd_blocks_g, m->adj_blocks_g)) < 1)
+            m->persistent = 0;
     }
     m->shots.resize(nshots);
     std::vector<uint8_t> colcov(nz_global, 0);
@@ -813,7 +852,6 @@ bh_status bh_forward(bh_model* m, const float* wavelet, float* seis)
         m->h_shots[s].q.wavelet = wavelet;
         m->h_shots[s].q.seis = seis + seis_per_shot * s;
     }
-    BH_TRY(upload_shots(m));
     BH_CUDA(m, cudaMemsetAsync(seis, 0, seis_per_shot * m->nshots * sizeof(float), m->stream));
     BH_CUDA(m, cudaMemsetAsync(m->d_fwd, 0, (size_t)m->nshots * kFwdPlanes * pl * sizeof(float),
                                m->stream));
@@ -860,18 +898,14 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
     const size_t seis_per_shot = (size_t)m->nrec_max * gd.nt;
     m->runs_adj = 0;
     for (int s = 0; s < m->nshots; ++s) m->h_shots[s].a.resid = resid + seis_per_shot * s;
-    BH_TRY(upload_shots(m));
     BH_CUDA(m, cudaMemsetAsync(g_lam, 0, ng * sizeof(double), m->stream));
     BH_CUDA(m, cudaMemsetAsync(g_mu, 0, ng * sizeof(double), m->stream));
     if (g_rho) BH_CUDA(m, cudaMemsetAsync(g_rho, 0, ng * sizeof(double), m->stream));
     BH_CUDA(m, cudaMemsetAsync(m->d_Hg, 0, 2 * ng * sizeof(double), m->stream));
     BH_CUDA(m, cudaMemsetAsync(m->d_adj, 0, (size_t)m->nshots * kAdjPlanes * pl * sizeof(float),
                                m->stream));
-    {
-        int maxnz = 0;
-        for (const auto& s : m->shots) maxnz = std::max(maxnz, s.nz);
-        k_adj_inject<<<dim3((maxnz + 127) / 128, m->nshots), 128, 0, m->stream>>>(m->d_shots,
-                                                                                 gd.nt - 1);
+    for (int s = 0; s < m->nshots; ++s) {
+        k_adj_inject<<<(m->shots[s].nz + 127) / 128, 128, 0, m->stream>>>(m->h_shots[s], gd.nt - 1);
         BH_LAUNCH(m);
     }
     for (const Act& a : m->plan) {
@@ -899,7 +933,7 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
     f.H_mu = m->d_Hg + ng;
     const dim3 blk = block2d();
     for (int s = 0; s < m->nshots; ++s) {
-        k_finalize<<<grid2d(gd.nr, m->shots[s].nz), blk, 0, m->stream>>>(m->d_shots, s, f);
+        k_finalize<<<grid2d(gd.nr, m->shots[s].nz), blk, 0, m->stream>>>(m->h_shots[s], f);
         BH_LAUNCH(m);
     }
     m->have_gradient = true;
@@ -975,7 +1009,8 @@ bh_status bh_set_option(bh_model* m, const char* key, double value)
     if (!m || !key) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
     const std::string k(key);
     if (k == "persistent") {
-        if (value != 0.0 && (m->fwd_blocks < 1 || m->adj_blocks < 1))
+        if (value != 0.0 && std::min(std::min(m->fwd_blocks, m->adj_blocks),
+                                     std::min(m->fwd_blocks_g, m->adj_blocks_g)) < 1)
             return fail(m, BH_ERR_UNSUPPORTED, "cooperative launch not available");
         m->persistent = value != 0.0;
     } else if (k == "barrier_timeout_ms") {
