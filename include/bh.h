@@ -61,7 +61,8 @@ typedef struct {
     double dr, dz, dt;   /* m, m, s                                            */
     double f0;           /* Hz; sets the C-PML frequency shift pi f0           */
     double pml_R;        /* target C-PML reflection; <= 0 means 1e-3           */
-    int snapshot_precision;      /* checkpoint snapshots: 0 fp32 (1 bf16, 2 fp16: reserved) */
+    int snapshot_precision;      /* checkpoint snapshots: 0 fp32, 1 bf16, 2 fp16, each
+                                    plane with its own power-of-two scale        */
     size_t checkpoint_cap_bytes; /* 0: store v_r, v_z of every step; > 0: byte cap
                                     of the history window plus the checkpoints   */
 } bh_grid_desc;
@@ -114,8 +115,14 @@ bh_status bh_set_model(bh_model* model, const float* vp, const float* vs, const 
  * binomial (Griewank-Walther) checkpoint schedule over the segments keeps
  * at most s full forward states per shot, and each segment is re-run once
  * into an (L + 1)-slot history window before its adjoint; L and s are the
- * pair that fits the cap with the fewest recomputed steps.  Results are
- * bit-identical to storing every step.
+ * pair that fits the cap with the fewest recomputed steps.  With FP32
+ * snapshots the results are bit-identical to storing every step.  With
+ * snapshot_precision 1 (BF16) or 2 (FP16) a snapshot takes half the bytes;
+ * every plane (each wavefield and each C-PML memory of each shot) is stored
+ * as x / s, s a power of two from the plane's max |x|, so the restored
+ * trajectory differs from the stored one by the 16-bit rounding and the
+ * gradient by the resulting error (the seismograms and J are unaffected:
+ * they come from the first, unrounded sweep).
  */
 
 /*

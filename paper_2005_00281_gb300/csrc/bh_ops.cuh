@@ -198,3 +198,70 @@ __global__ void k_velocities(size_t n, const float* __restrict__ lam, const floa
 }
 
 }  // namespace bh
+
+// ------------------------------------------------ checkpoint snapshot codec
+//
+// Checkpoint snapshots can be stored in 16 bits.  Every plane of every shot
+// (6 wavefields and 8 C-PML memories) gets its own scale, a power of two so
+// that scaling is exact: FP16 stores x / s with s = 2^(e - 14) where
+// 2^e >= max|x| (so the stored values stay below 2^14, inside FP16's range
+// with headroom); BF16, which has FP32's exponent range, stores x / 2^e.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace bh {
+
+// max |x| of each plane: one block per plane
+__global__ void __launch_bounds__(256) k_plane_maxabs(const float* __restrict__ src,
+                                                      size_t plane, float* maxabs)
+{
+    __shared__ float sh[256];
+    const float* p = src + (size_t)blockIdx.x * plane;
+    float m = 0.f;
+    for (size_t k = threadIdx.x; k < plane; k += blockDim.x) m = fmaxf(m, fabsf(p[k]));
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) maxabs[blockIdx.x] = sh[0];
+}
+
+// power-of-two scale of a plane from its max |x| (prec 1: BF16, 2: FP16)
+__device__ __forceinline__ float snap_scale(float maxabs, int prec)
+{
+    if (!(maxabs > 0.f)) return 1.f;
+    int e;
+    frexpf(maxabs, &e);  // maxabs = f * 2^e, 0.5 <= f < 1
+    return ldexpf(1.f, prec == 2 ? e - 14 : e);
+}
+
+__global__ void k_snap_encode(const float* __restrict__ src, size_t plane, size_t n,
+                              const float* __restrict__ maxabs, int prec, uint16_t* dst)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const float inv = 1.f / snap_scale(maxabs[k / plane], prec);  // exact: power of two
+        const float x = src[k] * inv;
+        uint16_t q;
+        if (prec == 2) q = __half_as_ushort(__float2half_rn(x));
+        else q = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+        dst[k] = q;
+    }
+}
+
+__global__ void k_snap_decode(const uint16_t* __restrict__ src, size_t plane, size_t n,
+                              const float* __restrict__ maxabs, int prec, float* dst)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const float s = snap_scale(maxabs[k / plane], prec);
+        const uint16_t q = src[k];
+        const float x = prec == 2 ? __half2float(__ushort_as_half(q))
+                                  : __bfloat162float(__ushort_as_bfloat16(q));
+        dst[k] = x * s;
+    }
+}
+
+}  // namespace bh

@@ -57,7 +57,9 @@ struct bh_model {
     float* d_fwd = nullptr;     // per shot kFwdPlanes planes
     float* d_adj = nullptr;     // per shot kAdjPlanes planes
     float* d_hist = nullptr;    // per shot (L + 1) x 2 planes
-    float* d_snap = nullptr;    // per shot nsnap x kFwdPlanes planes
+    void* d_snap = nullptr;     // per slot, all shots' kFwdPlanes planes (fp32 or 16-bit)
+    float* d_snap_max = nullptr;  // per slot, max |x| of every plane (16-bit snapshots)
+    int snap_prec = 0;          // 0 fp32, 1 bf16, 2 fp16
     std::vector<ShotK> h_shots;
     int4* d_tiles = nullptr;    // tiles of every shot group, group after group
     int ntiles = 0;
@@ -132,7 +134,7 @@ void free_model(bh_model* m)
     if (!m) return;
     void* bufs[] = {m->d_lam,   m->d_mu,     m->d_rho,   m->d_bvr,    m->d_bvz,    m->d_muh,
                     m->d_mask,  m->d_colcov, m->d_rprof, m->d_zprof,  m->d_recmap, m->d_fwd,
-                    m->d_adj,   m->d_hist,   m->d_snap,  m->d_tiles,  m->d_Hg,
+                    m->d_adj,   m->d_hist,   m->d_snap,  m->d_snap_max, m->d_tiles,  m->d_Hg,
                     m->d_scal,  m->d_bar};
     for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
@@ -619,13 +621,29 @@ bh_status snapshot(bh_model* m, int slot, bool take)
         BH_CUDA(m, cudaMemsetAsync(m->d_fwd, 0, bytes * m->nshots, m->stream));
         return BH_OK;
     }
-    float* snap = m->d_snap + (size_t)(slot - 1) * m->nshots * kFwdPlanes * pl;
-    if (take)
-        BH_CUDA(m, cudaMemcpyAsync(snap, m->d_fwd, bytes * m->nshots, cudaMemcpyDeviceToDevice,
-                                   m->stream));
-    else
-        BH_CUDA(m, cudaMemcpyAsync(m->d_fwd, snap, bytes * m->nshots, cudaMemcpyDeviceToDevice,
-                                   m->stream));
+    const size_t per_slot = (size_t)m->nshots * kFwdPlanes * pl;
+    if (m->snap_prec == 0) {
+        float* snap = (float*)m->d_snap + (size_t)(slot - 1) * per_slot;
+        if (take)
+            BH_CUDA(m, cudaMemcpyAsync(snap, m->d_fwd, bytes * m->nshots,
+                                       cudaMemcpyDeviceToDevice, m->stream));
+        else
+            BH_CUDA(m, cudaMemcpyAsync(m->d_fwd, snap, bytes * m->nshots,
+                                       cudaMemcpyDeviceToDevice, m->stream));
+        return BH_OK;
+    }
+    // 16-bit snapshot with a power-of-two scale per plane
+    uint16_t* snap = (uint16_t*)m->d_snap + (size_t)(slot - 1) * per_slot;
+    float* mx = m->d_snap_max + (size_t)(slot - 1) * m->nshots * kFwdPlanes;
+    const unsigned nb = (unsigned)std::min<size_t>((per_slot + 255) / 256, 152 * 16);
+    if (take) {
+        k_plane_maxabs<<<m->nshots * kFwdPlanes, 256, 0, m->stream>>>(m->d_fwd, pl, mx);
+        BH_LAUNCH(m);
+        k_snap_encode<<<nb, 256, 0, m->stream>>>(m->d_fwd, pl, per_slot, mx, m->snap_prec, snap);
+    } else {
+        k_snap_decode<<<nb, 256, 0, m->stream>>>(snap, pl, per_slot, mx, m->snap_prec, m->d_fwd);
+    }
+    BH_LAUNCH(m);
     return BH_OK;
 }
 
@@ -636,7 +654,7 @@ bh_status plan_checkpoints(bh_model* m, size_t cap)
 {
     const int nt = m->grid.nt;
     const double pl_bytes = (double)plane(m) * sizeof(float) * m->nshots;
-    const double snap_bytes = kFwdPlanes * pl_bytes;
+    const double snap_bytes = kFwdPlanes * pl_bytes * (m->snap_prec ? 0.5 : 1.0);
     long long best = LLONG_MAX;
     int bestL = 0, bests = 0;
     std::vector<int> Ls;
@@ -714,8 +732,8 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         g.nr - g.npml_r < 4 || !(g.dr > 0) || !(g.dz > 0) || !(g.dt > 0) || g.f0 < 0 ||
         g.nz != nz_global)
         return fail(nullptr, BH_ERR_INVALID_ARG, "bad grid description");
-    if (g.snapshot_precision != 0)
-        return fail(nullptr, BH_ERR_UNSUPPORTED, "reduced-precision snapshots not built");
+    if (g.snapshot_precision < 0 || g.snapshot_precision > 2)
+        return fail(nullptr, BH_ERR_INVALID_ARG, "snapshot_precision must be 0, 1 or 2");
     int nzmax = 0, nrec_max = 0;
     for (int s = 0; s < nshots; ++s) {
         const bh_shot_desc& d = shots[s];
@@ -740,6 +758,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     m->nrec_max = nrec_max;
     m->P = (nzmax + 31) / 32 * 32;
     m->stream = (cudaStream_t)stream;
+    m->snap_prec = g.snapshot_precision;
     const int nr = g.nr;
     const size_t ng = (size_t)nr * nz_global;
     const size_t pl = plane(m);
@@ -779,7 +798,9 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_fwd, (size_t)nshots * kFwdPlanes * pl));
     CK(dalloc(&m->d_adj, (size_t)nshots * kAdjPlanes * pl));
     CK(dalloc(&m->d_hist, (size_t)nshots * (m->L + 1) * 2 * pl));
-    CK(dalloc(&m->d_snap, (size_t)m->nsnap * nshots * kFwdPlanes * pl));
+    CK(dalloc((char**)&m->d_snap,
+              (size_t)m->nsnap * nshots * kFwdPlanes * pl * (m->snap_prec ? 2 : 4)));
+    CK(dalloc(&m->d_snap_max, (size_t)m->nsnap * nshots * kFwdPlanes));
     CK(dalloc(&m->d_Hg, 2 * ng));
     CK(dalloc(&m->d_scal, 16));
     CK(dalloc(&m->d_bar, 4));
@@ -1042,7 +1063,8 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "persistent") *value = m->persistent;
     else if (k == "history_snapshot_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
-                 (2.0 * (m->L + 1) + (double)m->nsnap * kFwdPlanes);
+                 (2.0 * (m->L + 1) + (double)m->nsnap * kFwdPlanes * (m->snap_prec ? 0.5 : 1.0));
+    else if (k == "snapshot_precision") *value = m->snap_prec;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
                      (kFwdPlanes + kAdjPlanes + 2.0 * (m->L + 1) + (double)m->nsnap * kFwdPlanes) +

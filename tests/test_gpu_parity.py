@@ -196,3 +196,27 @@ def test_checkpointed_batched_per_step(cuda):
     for a, b in zip(g_0, g_c):
         assert np.array_equal(a, b)
     assert info["snapshots"] >= 1 and info["history_steps"] < w.nt
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_reduced_precision_snapshots(cuda, orc, prec):
+    """BF16 (1) / FP16 (2) checkpoint snapshots: the seismograms and J come
+    from the first, unrounded sweep and stay identical; the gradient carries
+    the 16-bit rounding of the restored states.  Its error against the
+    store-all FP32 run and against the FP64 oracle is measured and bounded."""
+    w = tiny_borehole(seed=11, nt=300)
+    obs = oracle_observed(w)
+    seis_0, g_0, J_0, _ = _run_gpu(w, obs=obs)
+    seis_p, g_p, J_p, info = _run_gpu(w, obs=obs, checkpoint_cap_bytes=150_000,
+                                      snapshot_precision=prec)
+    assert info["snapshots"] >= 1
+    assert np.array_equal(seis_0, seis_p) and J_0 == J_p
+    ref = oracle_gradient(w, obs)
+    errs = {}
+    for k, name in enumerate(("g_lam", "g_mu", "g_rho")):
+        errs[name] = (rel_l2(g_p[k], g_0[k]), rel_l2(g_p[k], ref[name]),
+                      rel_l2(g_0[k], ref[name]))
+    print(f"snapshot precision {prec}: rel L2 (vs FP32 store-all, vs oracle, FP32 vs oracle)",
+          {k: tuple(f"{x:.2e}" for x in v) for k, v in errs.items()})
+    for name, (e_fp32, e_orc, _) in errs.items():
+        assert e_fp32 < 2e-2 and e_orc < 2e-2, (prec, name, errs)
