@@ -207,6 +207,19 @@ bh_status bh_precondition(bh_model* model, double* g_lam, double* g_mu, double e
 bh_status bh_update(bh_model* model, const double* g_lam, const double* g_mu, double kappa,
                     double* alpha_out, float* vp_out, float* vs_out);
 
+/*
+ * Gradients with respect to the velocities and density of the current
+ * model, by the chain rule through Eq. 3 and Eq. 4:
+ * g_Vp = 2 rho Vp g_lambda, g_Vs = 2 rho Vs (g_mu - 2 g_lambda),
+ * g_rho|Vp,Vs = g_rho + (Vp^2 - 2 Vs^2) g_lambda + Vs^2 g_mu.
+ *   g_lam, g_mu  device [nr][nz_global] double (from bh_adjoint_gradient)
+ *   g_rho    device double or NULL (density held fixed)
+ *   g_vp, g_vs, g_rho_v  device [nr][nz_global] float32, each may be NULL
+ * Errors: BH_ERR_INVALID_ARG, BH_ERR_CUDA.
+ */
+bh_status bh_velocity_gradient(bh_model* model, const double* g_lam, const double* g_mu,
+                               const double* g_rho, float* g_vp, float* g_vs, float* g_rho_v);
+
 /* Current model velocities (Eq. 11, Eq. 12).  vp, vs: device [nr][nz_global]. */
 bh_status bh_get_model(bh_model* model, float* vp, float* vs);
 

@@ -25,7 +25,7 @@ EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
            "bh_update", "bh_get_model", "bh_status_string", "bh_last_error",
            "bh_profile_enable", "bh_profile_read", "bh_profile_reset",
            "bh_residual_misfit_noalloc", "bh_set_option", "bh_get_info",
-           "bh_checkpoint_plan")
+           "bh_checkpoint_plan", "bh_velocity_gradient")
 NOALLOC_MAX_SAMPLES = 33554432
 KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel", "fwd_persist", "adj_persist")
 
@@ -89,6 +89,8 @@ def load_library(path: str | None = None):
     lib.bh_update.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                               vp, vp]
     lib.bh_update.restype = st
+    lib.bh_velocity_gradient.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.bh_velocity_gradient.restype = st
     lib.bh_get_model.argtypes = [vp, vp, vp]
     lib.bh_get_model.restype = st
     lib.bh_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -270,6 +272,14 @@ class Model:
 
     def profile_reset(self):
         self._rc(self.lib.bh_profile_reset(self.h))
+
+    def velocity_gradient(self, g_lam, g_mu, g_rho=None):
+        """bh_velocity_gradient: (g_vp, g_vs, g_rho at fixed velocities), float32."""
+        shape = (self.nr, self.nz)
+        out = [torch.empty(shape, dtype=torch.float32, device=self.device) for _ in range(3)]
+        self._rc(self.lib.bh_velocity_gradient(self.h, _ptr(g_lam), _ptr(g_mu), _ptr(g_rho),
+                                               _ptr(out[0]), _ptr(out[1]), _ptr(out[2])))
+        return tuple(out)
 
     def velocities(self):
         vp = torch.empty((self.nr, self.nz), dtype=torch.float32, device=self.device)

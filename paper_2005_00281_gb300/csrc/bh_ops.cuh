@@ -265,3 +265,29 @@ __global__ void k_snap_decode(const uint16_t* __restrict__ src, size_t plane, si
 }
 
 }  // namespace bh
+
+namespace bh {
+
+// Gradients with respect to (Vp, Vs, rho) from those with respect to
+// (lambda, mu, rho), by Eq. 3 and Eq. 4: lambda = rho (Vp^2 - 2 Vs^2),
+// mu = rho Vs^2.  g_rho may be null (then rho is held fixed: output 0).
+__global__ void k_velocity_gradient(size_t n, const float* __restrict__ lam,
+                                    const float* __restrict__ mu, const float* __restrict__ rho,
+                                    const double* __restrict__ g_lam,
+                                    const double* __restrict__ g_mu,
+                                    const double* __restrict__ g_rho, float* g_vp, float* g_vs,
+                                    float* g_rho_v)
+{
+    size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double r = rho[k], m = mu[k], l = lam[k];
+    const double vs2 = m / r, vp2 = (l + 2.0 * m) / r;
+    const double vp = sqrt(vp2), vs = sqrt(vs2);
+    const double gl = g_lam[k], gm = g_mu[k];
+    if (g_vp) g_vp[k] = (float)(2.0 * r * vp * gl);
+    if (g_vs) g_vs[k] = (float)(2.0 * r * vs * (gm - 2.0 * gl));
+    if (g_rho_v)
+        g_rho_v[k] = (float)((g_rho ? g_rho[k] : 0.0) + (vp2 - 2.0 * vs2) * gl + vs2 * gm);
+}
+
+}  // namespace bh

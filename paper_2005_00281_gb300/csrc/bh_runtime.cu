@@ -1015,6 +1015,17 @@ bh_status bh_update(bh_model* m, const double* g_lam, const double* g_mu, double
     return BH_OK;
 }
 
+bh_status bh_velocity_gradient(bh_model* m, const double* g_lam, const double* g_mu,
+                               const double* g_rho, float* g_vp, float* g_vs, float* g_rho_v)
+{
+    if (!m || !g_lam || !g_mu) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
+    const size_t ng = (size_t)m->grid.nr * m->nzg;
+    k_velocity_gradient<<<(unsigned)((ng + 255) / 256), 256, 0, m->stream>>>(
+        ng, m->d_lam, m->d_mu, m->d_rho, g_lam, g_mu, g_rho, g_vp, g_vs, g_rho_v);
+    BH_LAUNCH(m);
+    return BH_OK;
+}
+
 bh_status bh_get_model(bh_model* m, float* vp, float* vs)
 {
     if (!m || !vp || !vs) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
