@@ -36,7 +36,7 @@ def test_autograd_matches_finite_differences(torch_cuda):
     rng = np.random.default_rng(3)
     cells = [(int(rng.integers(w.nr - w.npml_r - 14, w.nr - w.npml_r)),
               int(rng.integers(w.npml_z, w.nz - w.npml_z))) for _ in range(32)]
-    for x, g in ((vp, vp.grad), (vs, vs.grad), (rho, rho.grad)):
+    for k, (x, g) in enumerate(((vp, vp.grad), (vs, vs.grad), (rho, rho.grad))):
         scale = float(g.abs().max())
         for (i, j) in cells:
             h = 1e-3 * float(x[i, j])
@@ -44,7 +44,6 @@ def test_autograd_matches_finite_differences(torch_cuda):
             for sgn in (1, -1):
                 with torch.no_grad():
                     args = [a.detach().clone() for a in (vp, vs, rho)]
-                    k = [vp, vs, rho].index(x)
                     args[k][i, j] += sgn * h
                     vals.append(float(misfit(BhWave.apply(*args, m, wav), obs)))
             fd = (vals[0] - vals[1]) / (2 * h)
