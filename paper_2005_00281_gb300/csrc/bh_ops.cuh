@@ -228,13 +228,15 @@ __global__ void __launch_bounds__(256) k_plane_maxabs(const float* __restrict__ 
     if (threadIdx.x == 0) maxabs[blockIdx.x] = sh[0];
 }
 
-// power-of-two scale of a plane from its max |x| (prec 1: BF16, 2: FP16)
+// power-of-two scale of a plane from its max |x| (prec 1: BF16, 2: FP16),
+// kept a normal FP32 number (exponent >= -126) so that 1/s is finite too;
+// a plane below 2^-112 then keeps its values to FP16's subnormal range
 __device__ __forceinline__ float snap_scale(float maxabs, int prec)
 {
-    if (!(maxabs > 0.f)) return 1.f;
+    if (!(maxabs > 0.f) || !(maxabs < 3.0e38f)) return 1.f;
     int e;
     frexpf(maxabs, &e);  // maxabs = f * 2^e, 0.5 <= f < 1
-    return ldexpf(1.f, prec == 2 ? e - 14 : e);
+    return ldexpf(1.f, max(prec == 2 ? e - 14 : e, -126));
 }
 
 __global__ void k_snap_encode(const float* __restrict__ src, size_t plane, size_t n,
