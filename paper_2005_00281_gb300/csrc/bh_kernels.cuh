@@ -90,23 +90,28 @@ __device__ __forceinline__ float muh_at(const CoefK& C, const WinK& g, int i, in
 // ------------------------------------------------------------- tiling
 //
 // Every stepping kernel works on tiles of kTR x kTZ nodes (16 rows of r by
-// 32 columns of z).  A block of 256 threads (8 warps) first stages what the
-// tile's stencils read, tile plus a 2-node halo, into shared memory (warp w
-// stages rows w, w+8, w+16, one row per pass so that row-level decisions --
-// axis mirror, outer edge -- are warp-uniform), with the mirror and the zero
-// edges applied; then warp w computes rows w and w+8 of the tile, one column
-// per lane.  The adjoint tiles also build the transposed-stencil
-// coefficients once per staged node.
+// 32 columns of z).  A block has 128 threads, 8 column groups x 16 rows:
+// each thread computes 4 consecutive z nodes of one row, with float4 loads
+// and stores.  The block first stages what the tile's stencils read, rows
+// i0-2 .. i0+17 and columns j0-4 .. j0+35 (16-byte aligned), into shared
+// memory with the axis mirror and the zero edges applied; the stencils then
+// read float4 rows of the staged tiles.  The adjoint tiles also build the
+// transposed-stencil coefficients once per staged node.  Tiles that touch no
+// C-PML layer (flag in the tile table) skip every layer branch.
 //
 // The same tile functions serve two launch forms: one kernel per half-step
-// (one tile per block), and one persistent cooperative kernel per shot that
-// runs every time step, with a bounded grid barrier between half-steps.
-// State written inside a launch is read with ld.global.cg (L2, not the
-// SM-private L1, which other SMs' writes do not update).
+// (one tile per block), and one persistent cooperative kernel per run, with a
+// bounded grid barrier between half-steps.  State written inside a launch is
+// read with ld.global.cg (L2, not the SM-private L1, which other SMs' writes
+// do not update).
 constexpr int kTZ = 32, kTR = 16, kH = 2;
-constexpr int kSZ = kTZ + 2 * kH, kSR = kTR + 2 * kH;
-constexpr int kThreads = 256;
+constexpr int kSR = kTR + 2 * kH;  // staged rows
+constexpr int kSZ = kTZ + 8;       // staged columns j0-4 .. j0+35
+constexpr int kQ = kSZ / 4;        // float4 per staged row
+constexpr int kThreads = 128;
 typedef float Tile[kSR][kSZ];
+
+enum { TILE_PML = 1 };  // tile or halo touches a C-PML layer
 
 // Programmatic dependent launch: a kernel may be scheduled while its
 // predecessor drains; it must wait here before touching the predecessor's
@@ -119,17 +124,88 @@ __device__ __forceinline__ void pdl_launch_dependents()
 
 __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
 
-// Stage the tile's rows [i0-2, i0+18) x columns [j0-2, j0+34) of a window
-// field.  EVEN: half-r field (cells, v_z), mirror f[-1-k] = f[k].  ODD:
-// integer-r field (v_r, trz), f[-k] = -f[k], f[0] = 0.  Zero beyond nr and
-// outside 0 <= z < nz.
+// 4 consecutive floats (16-byte aligned) of a row
+struct V4 {
+    float v[4];
+};
+
+__device__ __forceinline__ V4 ld4cg(const float* p)
+{
+    const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+    return V4{{t.x, t.y, t.z, t.w}};
+}
+
+__device__ __forceinline__ V4 lds4(const Tile& s, int rr, int cc)
+{
+    const float4 t = *reinterpret_cast<const float4*>(&s[rr][cc]);
+    return V4{{t.x, t.y, t.z, t.w}};
+}
+
+// 12 consecutive staged values of row rr from column cc (z neighbours)
+struct V12 {
+    float v[12];
+};
+
+__device__ __forceinline__ V12 lds12(const Tile& s, int rr, int cc)
+{
+    V12 r;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 t = *reinterpret_cast<const float4*>(&s[rr][cc + 4 * k]);
+        r.v[4 * k] = t.x;
+        r.v[4 * k + 1] = t.y;
+        r.v[4 * k + 2] = t.z;
+        r.v[4 * k + 3] = t.w;
+    }
+    return r;
+}
+
+// store 4 nodes of a row, columns j .. j+3, only those below nz
+__device__ __forceinline__ void st4(float* p, int j, int nz, const float (&x)[4])
+{
+    if (j + 3 < nz) {
+        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (j + e < nz) p[e] = x[e];
+    }
+}
+
+__device__ __forceinline__ void st4f2(float2* p, int j, int nz, const float2 (&x)[4])
+{
+    if (j + 3 < nz) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
+        reinterpret_cast<float4*>(p)[1] = make_float4(x[2].x, x[2].y, x[3].x, x[3].y);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (j + e < nz) p[e] = x[e];
+    }
+}
+
+__device__ __forceinline__ void ld4f2(const float2* p, float2 (&x)[4])
+{
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(p));
+    const float4 b = __ldcg(reinterpret_cast<const float4*>(p) + 1);
+    x[0] = make_float2(a.x, a.y);
+    x[1] = make_float2(a.z, a.w);
+    x[2] = make_float2(b.x, b.y);
+    x[3] = make_float2(b.z, b.w);
+}
+
+// Stage rows i0-2 .. i0+17, columns j0-4 .. j0+35 of a window field.
+// EVEN: half-r field (cells, v_z), mirror f[-1-k] = f[k].  ODD: integer-r
+// field (v_r, trz), f[-k] = -f[k], f[0] = 0.  Zero beyond nr and outside
+// 0 <= z < nz.
 enum { EVEN = 0, ODD = 1 };
 template <int KIND>
 __device__ __forceinline__ void stage(Tile& s, const float* __restrict__ f, int i0, int j0,
                                       const WinK& g)
 {
-    const int lane = threadIdx.x;
-    for (int rr = threadIdx.y; rr < kSR; rr += 8) {
+    const int tid = threadIdx.y * 8 + threadIdx.x;
+    for (int it = tid; it < kSR * kQ; it += kThreads) {
+        const int rr = it / kQ, q = it - rr * kQ;
         int i = i0 - kH + rr;
         float sg = 1.f;
         if (KIND == EVEN) {
@@ -138,15 +214,68 @@ __device__ __forceinline__ void stage(Tile& s, const float* __restrict__ f, int 
             if (i < 0) { i = -i; sg = -1.f; }
             if (i == 0) sg = 0.f;
         }
-        const bool live = i < g.nr && sg != 0.f;
-        const float* row = f + (live ? i * g.P : 0);
-        int j = j0 - kH + lane;
-        s[rr][lane] = (live && j >= 0 && j < g.nz) ? sg * ldcg(row + j) : 0.f;
-        if (lane < kSZ - 32) {
-            j += 32;
-            s[rr][lane + 32] = (live && j < g.nz) ? sg * ldcg(row + j) : 0.f;
+        const int j = j0 - 4 + 4 * q;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < g.nr && sg != 0.f && j >= 0 && j < g.nz) {
+            v = __ldcg(reinterpret_cast<const float4*>(f + i * g.P + j));
+            if (j + 1 >= g.nz) v.y = 0.f;
+            if (j + 2 >= g.nz) v.z = 0.f;
+            if (j + 3 >= g.nz) v.w = 0.f;
+            v.x *= sg;
+            v.y *= sg;
+            v.z *= sg;
+            v.w *= sg;
         }
+        *reinterpret_cast<float4*>(&s[rr][4 * q]) = v;
     }
+}
+
+// Stage a model field over the tile: cells (CELL) mirror evenly; shear
+// nodes (SHEAR: harmonic mu with the window's own last-row rule) mirror to
+// row |i|.  The window may start at any global row, so loads are scalar.
+enum { CELL = 0, SHEAR = 1 };
+template <int KIND>
+__device__ __forceinline__ void stage_model(Tile& s, const float* __restrict__ f, const CoefK& C,
+                                            int i0, int j0, const WinK& g)
+{
+    const int tid = threadIdx.y * 8 + threadIdx.x;
+    for (int it = tid; it < kSR * kQ; it += kThreads) {
+        const int rr = it / kQ, q = it - rr * kQ;
+        int i = i0 - kH + rr;
+        if (KIND == CELL) {
+            if (i < 0) i = -1 - i;
+        } else {
+            if (i < 0) i = -i;
+        }
+        const bool live = i < g.nr && (KIND == CELL || i >= 1);
+        float x[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = j0 - 4 + 4 * q + e;
+            x[e] = 0.f;
+            if (live && j >= 0 && j < g.nz)
+                x[e] = (KIND == CELL) ? __ldg(f + (size_t)i * g.nzg + g.z0 + j) : muh_at(C, g, i, j);
+        }
+        *reinterpret_cast<float4*>(&s[rr][4 * q]) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+}
+
+// own-node index helpers: thread (x = column group, y = row)
+struct Own {
+    int i, rr, j, cc, c;  // window row, staged row, first column, staged column, plane index
+    bool live;
+};
+
+__device__ __forceinline__ Own own_of(const WinK& g, int i0, int j0)
+{
+    Own o;
+    o.i = i0 + threadIdx.y;
+    o.rr = threadIdx.y + kH;
+    o.j = j0 + 4 * threadIdx.x;
+    o.cc = 4 * threadIdx.x + 4;
+    o.live = o.i < g.nr && o.j < g.nz;
+    o.c = o.i * g.P + o.j;
+    return o;
 }
 
 // ------------------------------------------------------- forward: Eq. 2
@@ -164,32 +293,43 @@ struct FwdSmem {
     Tile a, b, c, d;
 };
 
-// Velocity half-step of one tile: Eq. 2 lines 1-2 with the C-PML memories 0..3.
-// Every own-node input is loaded into registers before the staging, so the
-// tile pays one round trip to L2 (the loads and stores go through pointers
-// the compiler must assume may alias, so it would not reorder them itself).
+// Velocity half-step of one tile: Eq. 2 lines 1-2 with the C-PML memories
+// 0..3.  Own-node inputs are loaded before the staging, so the tile pays
+// one round trip to L2.  hist0 (or null): history slot receiving v^{n-1/2}.
 __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                             float* hist0, int i0, int j0, FwdSmem& sm)
+                                             float* hist0, int i0, int j0, int flags, FwdSmem& sm)
 {
     Tile &s_rr = sm.a, &s_tt = sm.b, &s_rz = sm.c, &s_zz = sm.d;
-    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
-    const bool jok = j < g.nz;
-    float vr0[2], vz0[2], br[2], bz[2], q0[2], q1[2], q2[2], q3[2];
+    const Own o = own_of(g, i0, j0);
+    const bool pml = flags & TILE_PML;
+    V4 vr0{}, vz0{}, br{}, bz{}, q0{}, q1{}, q2{}, q3{};
+    float ari = 0.f, bri = 0.f, arh = 0.f, brh = 0.f;
+    V4 azi{}, bzi{}, azh{}, bzh{};
+    if (o.live) {
+        vz0 = ld4cg(S.vz + o.c);
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + threadIdx.y + 8 * p;
-        vr0[p] = vz0[p] = br[p] = bz[p] = q0[p] = q1[p] = q2[p] = q3[p] = 0.f;
-        if (jok && i < g.nr) {
-            const int c = i * g.P + j;
-            vz0[p] = ldcg(S.vz + c);
-            bz[p] = bvz_at(C, g, i, j);
-            if (C.ar_half[i] != 0.f) q2[p] = ldcg(S.psi[2] + c);
-            if (C.az_half[j] != 0.f) q3[p] = ldcg(S.psi[3] + c);
-            if (i >= 1) {
-                vr0[p] = ldcg(S.vr + c);
-                br[p] = __ldg(C.bvr + (size_t)i * g.nzg + g.z0 + j);
-                if (C.ar_int[i] != 0.f) q0[p] = ldcg(S.psi[0] + c);
-                if (C.az_int[j] != 0.f) q1[p] = ldcg(S.psi[1] + c);
+        for (int e = 0; e < 4; ++e)
+            if (o.j + e < g.nz) bz.v[e] = bvz_at(C, g, o.i, o.j + e);
+        if (o.i >= 1) {
+            vr0 = ld4cg(S.vr + o.c);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (o.j + e < g.nz) br.v[e] = __ldg(C.bvr + (size_t)o.i * g.nzg + g.z0 + o.j + e);
+        }
+        if (pml) {
+            arh = C.ar_half[o.i];
+            brh = C.br_half[o.i];
+            azh = ld4cg(C.az_half + o.j);
+            bzh = ld4cg(C.bz_half + o.j);
+            if (arh != 0.f) q2 = ld4cg(S.psi[2] + o.c);
+            q3 = ld4cg(S.psi[3] + o.c);
+            if (o.i >= 1) {
+                ari = C.ar_int[o.i];
+                bri = C.br_int[o.i];
+                azi = ld4cg(C.az_int + o.j);
+                bzi = ld4cg(C.bz_int + o.j);
+                if (ari != 0.f) q0 = ld4cg(S.psi[0] + o.c);
+                q1 = ld4cg(S.psi[1] + o.c);
             }
         }
     }
@@ -199,88 +339,122 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     stage<ODD>(s_rz, S.trz, i0, j0, g);
     stage<EVEN>(s_zz, S.tzz, i0, j0, g);
     __syncthreads();
-    if (!jok) return;
+    if (!o.live) return;
+    const int rr = o.rr, cc = o.cc;
+    const V12 rz12 = lds12(s_rz, rr, cc - 4);
+    const V4 rzp1 = lds4(s_rz, rr + 1, cc);
+    if (o.i >= 1) {
+        const V4 rm2 = lds4(s_rr, rr - 2, cc), rm1 = lds4(s_rr, rr - 1, cc);
+        const V4 r0 = lds4(s_rr, rr, cc), rp1 = lds4(s_rr, rr + 1, cc);
+        const V4 tm1 = lds4(s_tt, rr - 1, cc), t0 = lds4(s_tt, rr, cc);
+        const float inv_r = C.inv_r_int[o.i];
+        float vr[4], w0[4], w1[4];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
-        if (i >= g.nr) break;
-        const int c = i * g.P + j;
-        if (i >= 1) {
-            float d_trr = d4(s_rr[rr][zz], s_rr[rr - 1][zz], s_rr[rr + 1][zz], s_rr[rr - 2][zz]) *
-                          g.inv_dr;
-            float d_trz = d4(s_rz[rr][zz], s_rz[rr][zz - 1], s_rz[rr][zz + 1], s_rz[rr][zz - 2]) *
-                          g.inv_dz;
-            float hoop = 0.5f * ((s_rr[rr - 1][zz] - s_tt[rr - 1][zz]) + (s_rr[rr][zz] - s_tt[rr][zz])) *
-                         C.inv_r_int[i];
-            float a = C.ar_int[i];
-            if (a != 0.f) {
-                float q = C.br_int[i] * q0[p] + a * d_trr;
-                S.psi_w[0][c] = q;
-                d_trr += q;
+        for (int e = 0; e < 4; ++e) {
+            float d_trr = d4(r0.v[e], rm1.v[e], rp1.v[e], rm2.v[e]) * g.inv_dr;
+            float d_trz = d4(rz12.v[4 + e], rz12.v[3 + e], rz12.v[5 + e], rz12.v[2 + e]) * g.inv_dz;
+            const float hoop = 0.5f * ((rm1.v[e] - tm1.v[e]) + (r0.v[e] - t0.v[e])) * inv_r;
+            if (pml) {
+                if (ari != 0.f) {
+                    w0[e] = bri * q0.v[e] + ari * d_trr;
+                    d_trr += w0[e];
+                }
+                if (azi.v[e] != 0.f) {
+                    w1[e] = bzi.v[e] * q1.v[e] + azi.v[e] * d_trz;
+                    d_trz += w1[e];
+                } else {
+                    w1[e] = q1.v[e];  // outside the layer the memory stays 0
+                }
             }
-            a = C.az_int[j];
-            if (a != 0.f) {
-                float q = C.bz_int[j] * q1[p] + a * d_trz;
-                S.psi_w[1][c] = q;
-                d_trz += q;
+            vr[e] = vr0.v[e] + g.dt * br.v[e] * (d_trr + d_trz + hoop);
+        }
+        st4(S.vr + o.c, o.j, g.nz, vr);
+        if (pml) {
+            if (ari != 0.f) st4(S.psi_w[0] + o.c, o.j, g.nz, w0);
+            st4(S.psi_w[1] + o.c, o.j, g.nz, w1);
+        }
+    }
+    {
+        const V12 zz12 = lds12(s_zz, rr, cc - 4);
+        const V4 rzm1 = lds4(s_rz, rr - 1, cc), rzp2 = lds4(s_rz, rr + 2, cc);
+        const float inv_r = C.inv_r_half[o.i];
+        float vz[4], w2[4], w3[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float d_trz = d4(rzp1.v[e], rz12.v[4 + e], rzp2.v[e], rzm1.v[e]) * g.inv_dr;
+            float d_tzz = d4(zz12.v[5 + e], zz12.v[4 + e], zz12.v[6 + e], zz12.v[3 + e]) * g.inv_dz;
+            const float hoop = 0.5f * (rz12.v[4 + e] + rzp1.v[e]) * inv_r;
+            if (pml) {
+                if (arh != 0.f) {
+                    w2[e] = brh * q2.v[e] + arh * d_trz;
+                    d_trz += w2[e];
+                }
+                if (azh.v[e] != 0.f) {
+                    w3[e] = bzh.v[e] * q3.v[e] + azh.v[e] * d_tzz;
+                    d_tzz += w3[e];
+                } else {
+                    w3[e] = q3.v[e];
+                }
             }
-            S.vr[c] = vr0[p] + g.dt * br[p] * (d_trr + d_trz + hoop);
+            vz[e] = vz0.v[e] + g.dt * bz.v[e] * (d_trz + d_tzz + hoop);
         }
-        float d_trz = d4(s_rz[rr + 1][zz], s_rz[rr][zz], s_rz[rr + 2][zz], s_rz[rr - 1][zz]) * g.inv_dr;
-        float d_tzz = d4(s_zz[rr][zz + 1], s_zz[rr][zz], s_zz[rr][zz + 2], s_zz[rr][zz - 1]) * g.inv_dz;
-        float hoop = 0.5f * (s_rz[rr][zz] + s_rz[rr + 1][zz]) * C.inv_r_half[i];
-        float a = C.ar_half[i];
-        if (a != 0.f) {
-            float q = C.br_half[i] * q2[p] + a * d_trz;
-            S.psi_w[2][c] = q;
-            d_trz += q;
+        st4(S.vz + o.c, o.j, g.nz, vz);
+        if (pml) {
+            if (arh != 0.f) st4(S.psi_w[2] + o.c, o.j, g.nz, w2);
+            st4(S.psi_w[3] + o.c, o.j, g.nz, w3);
         }
-        a = C.az_half[j];
-        if (a != 0.f) {
-            float q = C.bz_half[j] * q3[p] + a * d_tzz;
-            S.psi_w[3][c] = q;
-            d_tzz += q;
-        }
-        S.vz[c] = vz0[p] + g.dt * bz[p] * (d_trz + d_tzz + hoop);
-        if (hist0) {
-            hist0[c] = vr0[p];
-            hist0[g.nr * g.P + c] = vz0[p];
-        }
+    }
+    if (hist0) {
+        st4(hist0 + o.c, o.j, g.nz, vr0.v);
+        st4(hist0 + g.nr * g.P + o.c, o.j, g.nz, vz0.v);
     }
 }
 
 // Stress half-step of one tile: Eq. 2 lines 3-6 with the C-PML memories
 // 4..7, source injection into the three normal stresses, pressure
-// recording, and the store of v^{n+1/2} for the adjoint.  Own-node inputs
-// are prefetched as in the velocity tile.
+// recording, and the store of v^{n+1/2} for the adjoint.
 __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const SrcRecK& q, int n, bool record,
-                                                float* hist, int i0, int j0, FwdSmem& sm)
+                                                float* hist, int i0, int j0, int flags,
+                                                FwdSmem& sm)
 {
     Tile &s_vr = sm.a, &s_vz = sm.b;
-    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
-    const bool jok = j < g.nz;
-    float t_rr[2], t_tt[2], t_zz[2], t_rz[2], lm[2], mu[2], mh[2], q4[2], q5[2], q6[2], q7[2];
+    const Own o = own_of(g, i0, j0);
+    const bool pml = flags & TILE_PML;
+    V4 t_rr{}, t_tt{}, t_zz{}, t_rz{}, lm{}, mu{}, mh{}, q4{}, q5{}, q6{}, q7{};
+    float arh = 0.f, brh = 0.f, ari = 0.f, bri = 0.f;
+    V4 azi{}, bzi{}, azh{}, bzh{};
+    if (o.live) {
+        t_rr = ld4cg(S.trr + o.c);
+        t_tt = ld4cg(S.ttt + o.c);
+        t_zz = ld4cg(S.tzz + o.c);
+        const size_t cg = (size_t)o.i * g.nzg + g.z0 + o.j;
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + threadIdx.y + 8 * p;
-        t_rr[p] = t_tt[p] = t_zz[p] = t_rz[p] = lm[p] = mu[p] = mh[p] = 0.f;
-        q4[p] = q5[p] = q6[p] = q7[p] = 0.f;
-        if (jok && i < g.nr) {
-            const int c = i * g.P + j;
-            const size_t cg = (size_t)i * g.nzg + g.z0 + j;
-            t_rr[p] = ldcg(S.trr + c);
-            t_tt[p] = ldcg(S.ttt + c);
-            t_zz[p] = ldcg(S.tzz + c);
-            lm[p] = __ldg(C.lam + cg);
-            mu[p] = __ldg(C.mu + cg);
-            if (C.ar_half[i] != 0.f) q4[p] = ldcg(S.psi[4] + c);
-            if (C.az_int[j] != 0.f) q5[p] = ldcg(S.psi[5] + c);
-            if (i >= 1) {
-                t_rz[p] = ldcg(S.trz + c);
-                mh[p] = muh_at(C, g, i, j);
-                if (C.az_half[j] != 0.f) q6[p] = ldcg(S.psi[6] + c);
-                if (C.ar_int[i] != 0.f) q7[p] = ldcg(S.psi[7] + c);
+        for (int e = 0; e < 4; ++e)
+            if (o.j + e < g.nz) {
+                lm.v[e] = __ldg(C.lam + cg + e);
+                mu.v[e] = __ldg(C.mu + cg + e);
+            }
+        if (o.i >= 1) {
+            t_rz = ld4cg(S.trz + o.c);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (o.j + e < g.nz) mh.v[e] = muh_at(C, g, o.i, o.j + e);
+        }
+        if (pml) {
+            arh = C.ar_half[o.i];
+            brh = C.br_half[o.i];
+            azi = ld4cg(C.az_int + o.j);
+            bzi = ld4cg(C.bz_int + o.j);
+            if (arh != 0.f) q4 = ld4cg(S.psi[4] + o.c);
+            q5 = ld4cg(S.psi[5] + o.c);
+            if (o.i >= 1) {
+                ari = C.ar_int[o.i];
+                bri = C.br_int[o.i];
+                azh = ld4cg(C.az_half + o.j);
+                bzh = ld4cg(C.bz_half + o.j);
+                q6 = ld4cg(S.psi[6] + o.c);
+                if (ari != 0.f) q7 = ld4cg(S.psi[7] + o.c);
             }
         }
     }
@@ -288,68 +462,90 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     stage<ODD>(s_vr, S.vr, i0, j0, g);
     stage<EVEN>(s_vz, S.vz, i0, j0, g);
     __syncthreads();
-    if (!jok) return;
+    if (!o.live) return;
+    const int rr = o.rr, cc = o.cc;
+    const V12 vr12 = lds12(s_vr, rr, cc - 4), vz12 = lds12(s_vz, rr, cc - 4);
+    const V4 vrm1 = lds4(s_vr, rr - 1, cc), vrp1 = lds4(s_vr, rr + 1, cc),
+             vrp2 = lds4(s_vr, rr + 2, cc);
+    const float inv_rh = C.inv_r_half[o.i];
+    float trr[4], ttt[4], tzz[4], w4[4], w5[4];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
-        if (i >= g.nr) break;
-        const int c = i * g.P + j;
-        float d_vr = d4(s_vr[rr + 1][zz], s_vr[rr][zz], s_vr[rr + 2][zz], s_vr[rr - 1][zz]) * g.inv_dr;
-        float vr_r = 0.5f * (s_vr[rr][zz] + s_vr[rr + 1][zz]) * C.inv_r_half[i];
-        float d_vz = d4(s_vz[rr][zz], s_vz[rr][zz - 1], s_vz[rr][zz + 1], s_vz[rr][zz - 2]) * g.inv_dz;
-        float a = C.ar_half[i];
-        if (a != 0.f) {
-            float w = C.br_half[i] * q4[p] + a * d_vr;
-            S.psi_w[4][c] = w;
-            d_vr += w;
-        }
-        a = C.az_int[j];
-        if (a != 0.f) {
-            float w = C.bz_int[j] * q5[p] + a * d_vz;
-            S.psi_w[5][c] = w;
-            d_vz += w;
-        }
-        const float lam = lm[p];
-        const float l2m = lam + 2.f * mu[p];
-        float trr = t_rr[p] + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
-        float ttt = t_tt[p] + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
-        float tzz = t_zz[p] + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
-        if (c == q.src_c) {
-            float inj = q.src_scale * q.wavelet[n];
-            trr += inj;
-            ttt += inj;
-            tzz += inj;
-        }
-        S.trr[c] = trr;
-        S.ttt[c] = ttt;
-        S.tzz[c] = tzz;
-        if (i == 0 && record) {
-            int k = q.recmap[j];
-            if (k >= 0) q.seis[(size_t)k * q.nt + n] = (trr + ttt + tzz) * (1.f / 3.f);
-        }
-        if (i >= 1) {
-            float d_vrz = d4(s_vr[rr][zz + 1], s_vr[rr][zz], s_vr[rr][zz + 2], s_vr[rr][zz - 1]) *
-                          g.inv_dz;
-            float d_vzr = d4(s_vz[rr][zz], s_vz[rr - 1][zz], s_vz[rr + 1][zz], s_vz[rr - 2][zz]) *
-                          g.inv_dr;
-            a = C.az_half[j];
-            if (a != 0.f) {
-                float w = C.bz_half[j] * q6[p] + a * d_vrz;
-                S.psi_w[6][c] = w;
-                d_vrz += w;
+    for (int e = 0; e < 4; ++e) {
+        float d_vr = d4(vrp1.v[e], vr12.v[4 + e], vrp2.v[e], vrm1.v[e]) * g.inv_dr;
+        const float vr_r = 0.5f * (vr12.v[4 + e] + vrp1.v[e]) * inv_rh;
+        float d_vz = d4(vz12.v[4 + e], vz12.v[3 + e], vz12.v[5 + e], vz12.v[2 + e]) * g.inv_dz;
+        if (pml) {
+            if (arh != 0.f) {
+                w4[e] = brh * q4.v[e] + arh * d_vr;
+                d_vr += w4[e];
             }
-            a = C.ar_int[i];
-            if (a != 0.f) {
-                float w = C.br_int[i] * q7[p] + a * d_vzr;
-                S.psi_w[7][c] = w;
-                d_vzr += w;
+            if (azi.v[e] != 0.f) {
+                w5[e] = bzi.v[e] * q5.v[e] + azi.v[e] * d_vz;
+                d_vz += w5[e];
+            } else {
+                w5[e] = q5.v[e];
             }
-            S.trz[c] = t_rz[p] + g.dt * mh[p] * (d_vrz + d_vzr);
         }
-        if (hist) {
-            hist[c] = s_vr[rr][zz];
-            hist[g.nr * g.P + c] = s_vz[rr][zz];
+        const float lam = lm.v[e];
+        const float l2m = lam + 2.f * mu.v[e];
+        trr[e] = t_rr.v[e] + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
+        ttt[e] = t_tt.v[e] + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
+        tzz[e] = t_zz.v[e] + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
+        if (o.c + e == q.src_c) {
+            const float inj = q.src_scale * q.wavelet[n];
+            trr[e] += inj;
+            ttt[e] += inj;
+            tzz[e] += inj;
         }
+        if (o.i == 0 && record && o.j + e < g.nz) {
+            const int k = q.recmap[o.j + e];
+            if (k >= 0) q.seis[(size_t)k * q.nt + n] = (trr[e] + ttt[e] + tzz[e]) * (1.f / 3.f);
+        }
+    }
+    st4(S.trr + o.c, o.j, g.nz, trr);
+    st4(S.ttt + o.c, o.j, g.nz, ttt);
+    st4(S.tzz + o.c, o.j, g.nz, tzz);
+    if (pml) {
+        if (arh != 0.f) st4(S.psi_w[4] + o.c, o.j, g.nz, w4);
+        st4(S.psi_w[5] + o.c, o.j, g.nz, w5);
+    }
+    if (o.i >= 1) {
+        const V4 vzm1 = lds4(s_vz, rr - 1, cc), vzm2 = lds4(s_vz, rr - 2, cc),
+                 vzp1 = lds4(s_vz, rr + 1, cc);
+        float trz[4], w6[4], w7[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float d_vrz = d4(vr12.v[5 + e], vr12.v[4 + e], vr12.v[6 + e], vr12.v[3 + e]) * g.inv_dz;
+            float d_vzr = d4(vz12.v[4 + e], vzm1.v[e], vzp1.v[e], vzm2.v[e]) * g.inv_dr;
+            if (pml) {
+                if (azh.v[e] != 0.f) {
+                    w6[e] = bzh.v[e] * q6.v[e] + azh.v[e] * d_vrz;
+                    d_vrz += w6[e];
+                } else {
+                    w6[e] = q6.v[e];
+                }
+                if (ari != 0.f) {
+                    w7[e] = bri * q7.v[e] + ari * d_vzr;
+                    d_vzr += w7[e];
+                }
+            }
+            trz[e] = t_rz.v[e] + g.dt * mh.v[e] * (d_vrz + d_vzr);
+        }
+        st4(S.trz + o.c, o.j, g.nz, trz);
+        if (pml) {
+            st4(S.psi_w[6] + o.c, o.j, g.nz, w6);
+            if (ari != 0.f) st4(S.psi_w[7] + o.c, o.j, g.nz, w7);
+        }
+    }
+    if (hist) {
+        float a[4], b[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            a[e] = vr12.v[4 + e];
+            b[e] = vz12.v[4 + e];
+        }
+        st4(hist + o.c, o.j, g.nz, a);
+        st4(hist + g.nr * g.P + o.c, o.j, g.nz, b);
     }
 }
 
@@ -432,82 +628,13 @@ struct AdjK {
 };
 
 struct AdjSmem {
-    // staged: adjoint stresses, lambda, mu, mu_h, forward v^{n+1/2}
-    Tile arr, att, azz, arz, lam, mu, muh, fvr, fvz;
-    // transposed-stencil coefficients: on D_r v_r (x4), v_r/r (ytt), D_z v_z
-    // (x5) at cells; on D_z v_r (x6) and D_r v_z (x7) at trz nodes.  The
-    // velocity-step tile reuses x4..x7, ytt, arr as W_r, W_z, X0..X3.
-    Tile x4, ytt, x5, x6, x7;
+    // staged adjoint stresses and forward v^{n+1/2}; lambda, mu, mu_h are
+    // staged into x4, ytt, x5 and replaced there by the coefficients of the
+    // transposed stencils: on D_r v_r (x4), v_r/r (ytt), D_z v_z (x5) at
+    // cells, on D_z v_r (x6) and D_r v_z (x7) at shear nodes.  The velocity
+    // step reuses the first six tiles.
+    Tile arr, att, azz, arz, fvr, fvz, x4, ytt, x5, x6, x7;
 };
-
-// stage a model field over the tile: cells (CELL) mirror evenly; trz nodes
-// (harmonic mu) mirror about the axis row to row |i| with the window's own
-// last-row rule
-enum { CELL = 0, SHEAR = 1 };
-template <int KIND>
-__device__ __forceinline__ void stage_model(Tile& s, const float* __restrict__ f, const CoefK& C,
-                                            int i0, int j0, const WinK& g)
-{
-    const int lane = threadIdx.x;
-    for (int rr = threadIdx.y; rr < kSR; rr += 8) {
-        int i = i0 - kH + rr;
-        if (KIND == CELL) {
-            if (i < 0) i = -1 - i;
-        } else {
-            if (i < 0) i = -i;
-        }
-        const bool live = i < g.nr && (KIND == CELL || i >= 1);
-        for (int h = 0; h < 2; ++h) {
-            const int zz = lane + 32 * h;
-            if (zz >= kSZ) break;
-            const int j = j0 - kH + zz;
-            float v = 0.f;
-            if (live && j >= 0 && j < g.nz)
-                v = (KIND == CELL) ? __ldg(f + (size_t)i * g.nzg + g.z0 + j) : muh_at(C, g, i, j);
-            s[rr][zz] = v;
-        }
-    }
-}
-
-// Own-node inputs of one row of the transposed stress step.
-struct AdjStressOwn {
-    float av_r, av_z, fvr_prev, fvz_prev;
-    float2 g_lam, g_munn, g_murz, g_br, g_bz;
-    float h_lam, h_munn, h_murz;
-    float q4, q5, q6, q7;
-};
-
-__device__ __forceinline__ void adj_stress_own(const WinK& g, const CoefK& C, const StateK& S,
-                                               const AdjK& q, const float* fprev, int i, int j,
-                                               AdjStressOwn& o)
-{
-    const float2 z2 = make_float2(0.f, 0.f);
-    o.av_r = o.av_z = o.fvr_prev = o.fvz_prev = 0.f;
-    o.g_lam = o.g_munn = o.g_murz = o.g_br = o.g_bz = z2;
-    o.h_lam = o.h_munn = o.h_murz = 0.f;
-    o.q4 = o.q5 = o.q6 = o.q7 = 0.f;
-    if (i >= g.nr || j >= g.nz) return;
-    const int c = i * g.P + j;
-    const int plane = g.nr * g.P;
-    o.av_z = ldcg(S.vz + c);
-    o.g_lam = __ldcg(q.G_lam + c);
-    o.g_munn = __ldcg(q.G_munn + c);
-    o.g_bz = __ldcg(q.G_bz + c);
-    o.h_lam = ldcg(q.H_lam + c);
-    o.h_munn = ldcg(q.H_munn + c);
-    o.fvz_prev = __ldg(fprev + plane + c);
-    if (C.ar_half[i] != 0.f) o.q4 = ldcg(S.psi[4] + c);
-    if (C.az_int[j] != 0.f) o.q5 = ldcg(S.psi[5] + c);
-    if (i >= 1) {
-        o.av_r = ldcg(S.vr + c);
-        o.g_murz = __ldcg(q.G_murz + c);
-        o.g_br = __ldcg(q.G_br + c);
-        o.h_murz = ldcg(q.H_murz + c);
-        o.fvr_prev = __ldg(fprev + c);
-        if (C.az_half[j] != 0.f) o.q6 = ldcg(S.psi[6] + c);
-        if (C.ar_int[i] != 0.f) o.q7 = ldcg(S.psi[7] + c);
-    }
-}
 
 __device__ __forceinline__ float2 kahan_step(float2 s, float x)
 {
@@ -522,151 +649,213 @@ __device__ __forceinline__ float2 kahan_step(float2 s, float x)
 // the gradient correlations (Eq. 7, Eq. 8, and the density term).
 // S.{trr..trz} hold dJ/dtau^{n+1}; S.{vr,vz} accumulate to dJ/dv^{n+1/2};
 // psi[4..7] are the adjoint memories read side, psi_w[4..7] the write side.
-// fcur: v_r, v_z planes of v^{n+1/2}; fprev: those of v^{n-1/2}
+// fcur: v_r, v_z planes of v^{n+1/2}; fprev: those of v^{n-1/2}.
 __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const AdjK& q, const float* fcur,
-                                                const float* fprev, int i0, int j0, AdjSmem& sm)
+                                                const float* fprev, int i0, int j0, int flags,
+                                                AdjSmem& sm)
 {
-    const float* fvr = fcur;
-    const float* fvz = fcur + g.nr * g.P;
+    const int plane = g.nr * g.P;
     const float dt = g.dt;
-    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
-    AdjStressOwn own;
-    adj_stress_own(g, C, S, q, fprev, i0 + threadIdx.y, j, own);
+    const Own o = own_of(g, i0, j0);
+    const bool pml = flags & TILE_PML;
+    V4 av_r{}, av_z{};
+    if (o.live) {
+        av_z = ld4cg(S.vz + o.c);
+        if (o.i >= 1) av_r = ld4cg(S.vr + o.c);
+    }
     __syncthreads();
     stage<EVEN>(sm.arr, S.trr, i0, j0, g);
     stage<EVEN>(sm.att, S.ttt, i0, j0, g);
     stage<EVEN>(sm.azz, S.tzz, i0, j0, g);
     stage<ODD>(sm.arz, S.trz, i0, j0, g);
-    stage<ODD>(sm.fvr, fvr, i0, j0, g);
-    stage<EVEN>(sm.fvz, fvz, i0, j0, g);
-    stage_model<CELL>(sm.lam, C.lam, C, i0, j0, g);
-    stage_model<CELL>(sm.mu, C.mu, C, i0, j0, g);
-    stage_model<SHEAR>(sm.muh, nullptr, C, i0, j0, g);
-    // adjoint memories read by the staged coefficients (inside the layers only)
-    {
-        const int lane = threadIdx.x;
-        for (int rr = threadIdx.y; rr < kSR; rr += 8) {
-            const int i = i0 - kH + rr;
-            const int ic = i < 0 ? -1 - i : i;
-            const bool row_cell = i < g.nr;
-            const bool arh = row_cell && C.ar_half[ic] != 0.f;
-            const bool ari = i >= 1 && i < g.nr && C.ar_int[i] != 0.f;
-            for (int h = 0; h < 2; ++h) {
-                const int zz2 = lane + 32 * h;
-                if (zz2 >= kSZ) break;
-                const int jj = j0 - kH + zz2;
-                float p4 = 0.f, p5 = 0.f, p6 = 0.f, p7 = 0.f;
-                if (jj >= 0 && jj < g.nz && row_cell) {
-                    if (arh) p4 = ldcg(S.psi[4] + ic * g.P + jj);
-                    if (C.az_int[jj] != 0.f) p5 = ldcg(S.psi[5] + ic * g.P + jj);
-                    if (i >= 1 && C.az_half[jj] != 0.f) p6 = ldcg(S.psi[6] + i * g.P + jj);
-                    if (ari) p7 = ldcg(S.psi[7] + i * g.P + jj);
-                }
-                sm.x4[rr][zz2] = p4;
-                sm.x5[rr][zz2] = p5;
-                sm.x6[rr][zz2] = p6;
-                sm.x7[rr][zz2] = p7;
-            }
-        }
-    }
+    stage<ODD>(sm.fvr, fcur, i0, j0, g);
+    stage<EVEN>(sm.fvz, fcur + plane, i0, j0, g);
+    stage_model<CELL>(sm.x4, C.lam, C, i0, j0, g);
+    stage_model<CELL>(sm.ytt, C.mu, C, i0, j0, g);
+    stage_model<SHEAR>(sm.x5, nullptr, C, i0, j0, g);
     __syncthreads();
-    // transposed-stencil coefficients over the staged region
+    const int rr = o.rr, cc = o.cc;
+    const V4 lam_o = lds4(sm.x4, rr, cc), mu_o = lds4(sm.ytt, rr, cc), mh_o = lds4(sm.x5, rr, cc);
+    __syncthreads();
+    // transposed-stencil coefficients over the staged region, in place
     {
-        const int lane = threadIdx.x;
-        for (int rr = threadIdx.y; rr < kSR; rr += 8) {
-            const int i = i0 - kH + rr;
+        const int tid = threadIdx.y * 8 + threadIdx.x;
+        for (int it = tid; it < kSR * kQ; it += kThreads) {
+            const int r2 = it / kQ, q2 = it - r2 * kQ;
+            const int i = i0 - kH + r2, j = j0 - 4 + 4 * q2, c2 = 4 * q2;
             const int ic = i < 0 ? -1 - i : i;
-            const bool row_cell = i < g.nr;
-            const float arh = row_cell ? C.ar_half[ic] : 0.f;
-            const float brh = row_cell ? C.br_half[ic] : 0.f;
-            const float ari = (i >= 1 && i < g.nr) ? C.ar_int[i] : 0.f;
-            const float bri = (i >= 1 && i < g.nr) ? C.br_int[i] : 0.f;
-            for (int h = 0; h < 2; ++h) {
-                const int zz2 = lane + 32 * h;
-                if (zz2 >= kSZ) break;
-                const int jj = j0 - kH + zz2;
-                float x4 = 0.f, ytt = 0.f, x5 = 0.f, x6 = 0.f, x7 = 0.f;
-                if (jj >= 0 && jj < g.nz && row_cell) {
-                    const float lam = sm.lam[rr][zz2], l2m = lam + 2.f * sm.mu[rr][zz2];
-                    const float arr = sm.arr[rr][zz2], att = sm.att[rr][zz2], azz = sm.azz[rr][zz2];
-                    x4 = dt * (l2m * arr + lam * (att + azz));
-                    ytt = dt * (l2m * att + lam * (arr + azz));
-                    x5 = dt * (l2m * azz + lam * (arr + att));
-                    if (arh != 0.f) x4 = x4 + arh * (x4 + brh * sm.x4[rr][zz2]);
-                    const float azi = C.az_int[jj];
-                    if (azi != 0.f) x5 = x5 + azi * (x5 + C.bz_int[jj] * sm.x5[rr][zz2]);
-                    // trz node: the staged values are already odd about the axis
-                    const float y = dt * sm.muh[rr][zz2] * sm.arz[rr][zz2];
-                    x6 = y;
-                    x7 = y;
-                    if (i >= 1) {
-                        const float azh = C.az_half[jj];
-                        if (azh != 0.f) x6 = y + azh * (y + C.bz_half[jj] * sm.x6[rr][zz2]);
-                        if (ari != 0.f) x7 = y + ari * (y + bri * sm.x7[rr][zz2]);
+            const V4 lm = lds4(sm.x4, r2, c2), mu = lds4(sm.ytt, r2, c2), mh = lds4(sm.x5, r2, c2);
+            const V4 ar = lds4(sm.arr, r2, c2), at = lds4(sm.att, r2, c2), az = lds4(sm.azz, r2, c2);
+            const V4 arz = lds4(sm.arz, r2, c2);
+            float x4[4], ytt[4], x5[4], x6[4], x7[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float lam = lm.v[e], l2m = lam + 2.f * mu.v[e];
+                x4[e] = dt * (l2m * ar.v[e] + lam * (at.v[e] + az.v[e]));
+                ytt[e] = dt * (l2m * at.v[e] + lam * (ar.v[e] + az.v[e]));
+                x5[e] = dt * (l2m * az.v[e] + lam * (ar.v[e] + at.v[e]));
+                // shear node: the staged values are already odd about the axis
+                x6[e] = x7[e] = dt * mh.v[e] * arz.v[e];
+            }
+            if (pml && i < g.nr && j >= 0 && j < g.nz) {
+                const float arh = C.ar_half[ic], brh = C.br_half[ic];
+                if (arh != 0.f) {
+                    const V4 p = ld4cg(S.psi[4] + ic * g.P + j);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) x4[e] = x4[e] + arh * (x4[e] + brh * p.v[e]);
+                }
+                const V4 azi = ld4cg(C.az_int + j), bzi = ld4cg(C.bz_int + j);
+                const V4 p5 = ld4cg(S.psi[5] + ic * g.P + j);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (azi.v[e] != 0.f) x5[e] = x5[e] + azi.v[e] * (x5[e] + bzi.v[e] * p5.v[e]);
+                if (i >= 1) {
+                    const V4 azh = ld4cg(C.az_half + j), bzh = ld4cg(C.bz_half + j);
+                    const V4 p6 = ld4cg(S.psi[6] + i * g.P + j);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (azh.v[e] != 0.f) x6[e] = x6[e] + azh.v[e] * (x6[e] + bzh.v[e] * p6.v[e]);
+                    const float ari = C.ar_int[i], bri = C.br_int[i];
+                    if (ari != 0.f) {
+                        const V4 p7 = ld4cg(S.psi[7] + i * g.P + j);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) x7[e] = x7[e] + ari * (x7[e] + bri * p7.v[e]);
                     }
                 }
-                // each thread overwrites only the positions it read
-                sm.x4[rr][zz2] = x4;
-                sm.ytt[rr][zz2] = ytt;
-                sm.x5[rr][zz2] = x5;
-                sm.x6[rr][zz2] = x6;
-                sm.x7[rr][zz2] = x7;
             }
+            *reinterpret_cast<float4*>(&sm.x4[r2][c2]) = make_float4(x4[0], x4[1], x4[2], x4[3]);
+            *reinterpret_cast<float4*>(&sm.ytt[r2][c2]) = make_float4(ytt[0], ytt[1], ytt[2], ytt[3]);
+            *reinterpret_cast<float4*>(&sm.x5[r2][c2]) = make_float4(x5[0], x5[1], x5[2], x5[3]);
+            *reinterpret_cast<float4*>(&sm.x6[r2][c2]) = make_float4(x6[0], x6[1], x6[2], x6[3]);
+            *reinterpret_cast<float4*>(&sm.x7[r2][c2]) = make_float4(x7[0], x7[1], x7[2], x7[3]);
         }
     }
     __syncthreads();
+    if (!o.live) return;
+    const int i = o.i, c = o.c;
 
-    if (j >= g.nz) return;
+    // ---- forward strains of v^{n+1/2} and own adjoint stresses
+    const V12 fr12 = lds12(sm.fvr, rr, cc - 4), fz12 = lds12(sm.fvz, rr, cc - 4);
+    const V4 frm1 = lds4(sm.fvr, rr - 1, cc), frp1 = lds4(sm.fvr, rr + 1, cc),
+             frp2 = lds4(sm.fvr, rr + 2, cc);
+    const V4 Arr = lds4(sm.arr, rr, cc), Att = lds4(sm.att, rr, cc), Azz = lds4(sm.azz, rr, cc),
+             Arz = lds4(sm.arz, rr, cc);
+    const float inv_rh = C.inv_r_half[i];
+    float err[4], ett[4], ezz[4];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
-        if (i >= g.nr) break;
-        const int c = i * g.P + j;
-        if (p == 1) adj_stress_own(g, C, S, q, fprev, i, j, own);
-
-        // ---- gradient correlation with the forward strains of v^{n+1/2}
-        const float arr = sm.arr[rr][zz], att = sm.att[rr][zz], azz = sm.azz[rr][zz];
-        float err = d4(sm.fvr[rr + 1][zz], sm.fvr[rr][zz], sm.fvr[rr + 2][zz], sm.fvr[rr - 1][zz]) *
-                    g.inv_dr;
-        float ett = 0.5f * (sm.fvr[rr][zz] + sm.fvr[rr + 1][zz]) * C.inv_r_half[i];
-        float ezz = d4(sm.fvz[rr][zz], sm.fvz[rr][zz - 1], sm.fvz[rr][zz + 1], sm.fvz[rr][zz - 2]) *
-                    g.inv_dz;
-        float div = err + ett + ezz;
-        q.G_lam[c] = kahan_step(own.g_lam, dt * div * (arr + att + azz));
-        q.G_munn[c] = kahan_step(own.g_munn, 2.f * dt * (err * arr + ett * att + ezz * azz));
-        q.H_lam[c] = own.h_lam + dt * div * div;
-        q.H_munn[c] = own.h_munn + 4.f * dt * (err * err + ett * ett + ezz * ezz);
-
-        // ---- transpose of the stress step into Av, and the density term
-        {
-            float sz = d4(sm.x5[rr][zz], sm.x5[rr][zz + 1], sm.x5[rr][zz - 1], sm.x5[rr][zz + 2]) * g.inv_dz;
-            sz += d4(sm.x7[rr][zz], sm.x7[rr + 1][zz], sm.x7[rr - 1][zz], sm.x7[rr + 2][zz]) * g.inv_dr;
-            const float av = own.av_z + sz;
-            S.vz[c] = av;
-            q.G_bz[c] = kahan_step(own.g_bz, (sm.fvz[rr][zz] - own.fvz_prev) * av);
+    for (int e = 0; e < 4; ++e) {
+        err[e] = d4(frp1.v[e], fr12.v[4 + e], frp2.v[e], frm1.v[e]) * g.inv_dr;
+        ett[e] = 0.5f * (fr12.v[4 + e] + frp1.v[e]) * inv_rh;
+        ezz[e] = d4(fz12.v[4 + e], fz12.v[3 + e], fz12.v[5 + e], fz12.v[2 + e]) * g.inv_dz;
+    }
+    // ---- lambda and normal mu correlations, pseudo-Hessian
+    {
+        float2 gl[4], gm[4];
+        ld4f2(q.G_lam + c, gl);
+        ld4f2(q.G_munn + c, gm);
+        const V4 hl = ld4cg(q.H_lam + c), hm = ld4cg(q.H_munn + c);
+        float hl2[4], hm2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float div = err[e] + ett[e] + ezz[e];
+            gl[e] = kahan_step(gl[e], dt * div * (Arr.v[e] + Att.v[e] + Azz.v[e]));
+            gm[e] = kahan_step(gm[e], 2.f * dt *
+                                          (err[e] * Arr.v[e] + ett[e] * Att.v[e] + ezz[e] * Azz.v[e]));
+            hl2[e] = hl.v[e] + dt * div * div;
+            hm2[e] = hm.v[e] + 4.f * dt * (err[e] * err[e] + ett[e] * ett[e] + ezz[e] * ezz[e]);
         }
-        const float lam = sm.lam[rr][zz], l2m = lam + 2.f * sm.mu[rr][zz];
-        if (C.ar_half[i] != 0.f)
-            S.psi_w[4][c] = dt * (l2m * arr + lam * (att + azz)) + C.br_half[i] * own.q4;
-        if (C.az_int[j] != 0.f)
-            S.psi_w[5][c] = dt * (l2m * azz + lam * (arr + att)) + C.bz_int[j] * own.q5;
+        st4f2(q.G_lam + c, o.j, g.nz, gl);
+        st4f2(q.G_munn + c, o.j, g.nz, gm);
+        st4(q.H_lam + c, o.j, g.nz, hl2);
+        st4(q.H_munn + c, o.j, g.nz, hm2);
+    }
+    // ---- transpose of the stress step into Av
+    float avr[4], avz[4];
+    {
+        const V12 x5r = lds12(sm.x5, rr, cc - 4);
+        const V4 x7m1 = lds4(sm.x7, rr - 1, cc), x70 = lds4(sm.x7, rr, cc),
+                 x7p1 = lds4(sm.x7, rr + 1, cc), x7p2 = lds4(sm.x7, rr + 2, cc);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float s = d4(x5r.v[4 + e], x5r.v[5 + e], x5r.v[3 + e], x5r.v[6 + e]) * g.inv_dz;
+            s += d4(x70.v[e], x7p1.v[e], x7m1.v[e], x7p2.v[e]) * g.inv_dr;
+            avz[e] = av_z.v[e] + s;
+        }
+        st4(S.vz + c, o.j, g.nz, avz);
+    }
+    if (i >= 1) {
+        const V4 x4m2 = lds4(sm.x4, rr - 2, cc), x4m1 = lds4(sm.x4, rr - 1, cc),
+                 x40 = lds4(sm.x4, rr, cc), x4p1 = lds4(sm.x4, rr + 1, cc);
+        const V4 ytm1 = lds4(sm.ytt, rr - 1, cc), yt0 = lds4(sm.ytt, rr, cc);
+        const V12 x6r = lds12(sm.x6, rr, cc - 4);
+        const float irm = C.inv_r_half[i - 1];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float s = d4(x4m1.v[e], x40.v[e], x4m2.v[e], x4p1.v[e]) * g.inv_dr;
+            s += 0.5f * (ytm1.v[e] * irm + yt0.v[e] * inv_rh);
+            s += d4(x6r.v[3 + e], x6r.v[4 + e], x6r.v[2 + e], x6r.v[5 + e]) * g.inv_dz;
+            avr[e] = av_r.v[e] + s;
+        }
+        st4(S.vr + c, o.j, g.nz, avr);
+    }
+    // ---- shear mu and density correlations
+    {
+        float2 gbz[4];
+        ld4f2(q.G_bz + c, gbz);
+        const V4 pz = ld4cg(fprev + plane + c);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) gbz[e] = kahan_step(gbz[e], (fz12.v[4 + e] - pz.v[e]) * avz[e]);
+        st4f2(q.G_bz + c, o.j, g.nz, gbz);
+    }
+    if (i >= 1) {
+        float2 gmr[4], gbr[4];
+        ld4f2(q.G_murz + c, gmr);
+        ld4f2(q.G_br + c, gbr);
+        const V4 hmr = ld4cg(q.H_murz + c), pr = ld4cg(fprev + c);
+        const V4 fzm1 = lds4(sm.fvz, rr - 1, cc), fzm2 = lds4(sm.fvz, rr - 2, cc),
+                 fzp1 = lds4(sm.fvz, rr + 1, cc);
+        float hmr2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float gam =
+                d4(fr12.v[5 + e], fr12.v[4 + e], fr12.v[6 + e], fr12.v[3 + e]) * g.inv_dz +
+                d4(fz12.v[4 + e], fzm1.v[e], fzp1.v[e], fzm2.v[e]) * g.inv_dr;
+            gmr[e] = kahan_step(gmr[e], dt * gam * Arz.v[e]);
+            hmr2[e] = hmr.v[e] + dt * gam * gam;
+            gbr[e] = kahan_step(gbr[e], (fr12.v[4 + e] - pr.v[e]) * avr[e]);
+        }
+        st4f2(q.G_murz + c, o.j, g.nz, gmr);
+        st4(q.H_murz + c, o.j, g.nz, hmr2);
+        st4f2(q.G_br + c, o.j, g.nz, gbr);
+    }
+    // ---- adjoint memories of the stress step (own cell / own shear node)
+    if (pml) {
+        const float arh = C.ar_half[i], brh = C.br_half[i];
+        const V4 bzi = ld4cg(C.bz_int + o.j);
+        const V4 p4 = ld4cg(S.psi[4] + c), p5 = ld4cg(S.psi[5] + c);
+        float w4[4], w5[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float lam = lam_o.v[e], l2m = lam + 2.f * mu_o.v[e];
+            w4[e] = dt * (l2m * Arr.v[e] + lam * (Att.v[e] + Azz.v[e])) + brh * p4.v[e];
+            w5[e] = dt * (l2m * Azz.v[e] + lam * (Arr.v[e] + Att.v[e])) + bzi.v[e] * p5.v[e];
+        }
+        if (arh != 0.f) st4(S.psi_w[4] + c, o.j, g.nz, w4);
+        st4(S.psi_w[5] + c, o.j, g.nz, w5);
         if (i >= 1) {
-            float gam = d4(sm.fvr[rr][zz + 1], sm.fvr[rr][zz], sm.fvr[rr][zz + 2], sm.fvr[rr][zz - 1]) *
-                            g.inv_dz +
-                        d4(sm.fvz[rr][zz], sm.fvz[rr - 1][zz], sm.fvz[rr + 1][zz], sm.fvz[rr - 2][zz]) *
-                            g.inv_dr;
-            q.G_murz[c] = kahan_step(own.g_murz, dt * gam * sm.arz[rr][zz]);
-            q.H_murz[c] = own.h_murz + dt * gam * gam;
-            float sr = d4(sm.x4[rr - 1][zz], sm.x4[rr][zz], sm.x4[rr - 2][zz], sm.x4[rr + 1][zz]) * g.inv_dr;
-            sr += 0.5f * (sm.ytt[rr - 1][zz] * C.inv_r_half[i - 1] + sm.ytt[rr][zz] * C.inv_r_half[i]);
-            sr += d4(sm.x6[rr][zz - 1], sm.x6[rr][zz], sm.x6[rr][zz - 2], sm.x6[rr][zz + 1]) * g.inv_dz;
-            const float av = own.av_r + sr;
-            S.vr[c] = av;
-            q.G_br[c] = kahan_step(own.g_br, (sm.fvr[rr][zz] - own.fvr_prev) * av);
-            const float y = dt * sm.muh[rr][zz] * sm.arz[rr][zz];
-            if (C.az_half[j] != 0.f) S.psi_w[6][c] = y + C.bz_half[j] * own.q6;
-            if (C.ar_int[i] != 0.f) S.psi_w[7][c] = y + C.br_int[i] * own.q7;
+            const float bri = C.br_int[i];
+            const V4 bzh = ld4cg(C.bz_half + o.j);
+            const V4 p6 = ld4cg(S.psi[6] + c), p7 = ld4cg(S.psi[7] + c);
+            float w6[4], w7[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float y = dt * mh_o.v[e] * Arz.v[e];
+                w6[e] = y + bzh.v[e] * p6.v[e];
+                w7[e] = y + bri * p7.v[e];
+            }
+            st4(S.psi_w[6] + c, o.j, g.nz, w6);
+            if (C.ar_int[i] != 0.f) st4(S.psi_w[7] + c, o.j, g.nz, w7);
         }
     }
 }
@@ -676,117 +865,172 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
 // residual of step n-1 is injected at the receivers (transpose of the
 // recording).
 __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                             const AdjK& q, int n, int i0, int j0, AdjSmem& sm)
+                                             const AdjK& q, int n, int i0, int j0, int flags,
+                                             AdjSmem& sm)
 {
     // W = dt b Av at the velocity nodes (odd about the axis for v_r, even
-    // for v_z), the coefficients on the four stretched derivatives, and the
-    // old adjoint memories of the own nodes
-    Tile &s_wr = sm.x4, &s_wz = sm.ytt, &s_x0 = sm.x5, &s_x1 = sm.x6, &s_x2 = sm.x7,
-         &s_x3 = sm.arr, &s_p0 = sm.att, &s_p1 = sm.azz, &s_p2 = sm.arz, &s_p3 = sm.lam;
-    const int j = j0 + threadIdx.x, zz = threadIdx.x + kH;
-    const bool jok = j < g.nz;
-    float o_rr[2], o_tt[2], o_zz[2], o_rz[2], r3[2];
+    // for v_z) and the coefficients on the four stretched derivatives
+    Tile &s_wr = sm.arr, &s_wz = sm.att, &s_x0 = sm.azz, &s_x1 = sm.arz, &s_x2 = sm.fvr,
+         &s_x3 = sm.fvz;
+    const Own o = own_of(g, i0, j0);
+    const bool pml = flags & TILE_PML;
+    V4 o_rr{}, o_tt{}, o_zz{}, o_rz{}, r3{};
+    if (o.live) {
+        o_rr = ld4cg(S.trr + o.c);
+        o_tt = ld4cg(S.ttt + o.c);
+        o_zz = ld4cg(S.tzz + o.c);
+        if (o.i >= 1) o_rz = ld4cg(S.trz + o.c);
+        if (o.i == 0 && n > 0) {
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + threadIdx.y + 8 * p;
-        o_rr[p] = o_tt[p] = o_zz[p] = o_rz[p] = r3[p] = 0.f;
-        if (jok && i < g.nr) {
-            const int c = i * g.P + j;
-            o_rr[p] = ldcg(S.trr + c);
-            o_tt[p] = ldcg(S.ttt + c);
-            o_zz[p] = ldcg(S.tzz + c);
-            if (i >= 1) o_rz[p] = ldcg(S.trz + c);
-            if (i == 0 && n > 0) {
-                const int k = q.recmap[j];
-                if (k >= 0) r3[p] = q.resid[(size_t)k * q.nt + (n - 1)] * (1.f / 3.f);
+            for (int e = 0; e < 4; ++e) {
+                const int k = o.j + e < g.nz ? q.recmap[o.j + e] : -1;
+                if (k >= 0) r3.v[e] = q.resid[(size_t)k * q.nt + (n - 1)] * (1.f / 3.f);
             }
         }
     }
     __syncthreads();
     {
-        const int lane = threadIdx.x;
-        for (int rr = threadIdx.y; rr < kSR; rr += 8) {
-            const int i = i0 - kH + rr;
-            const int ir = i < 0 ? -i : i;       // v_r node mirrored row
-            const float sg = i < 0 ? -1.f : 1.f;
-            const bool rlive = ir >= 1 && ir < g.nr;
-            const int iz = i < 0 ? -1 - i : i;   // v_z node mirrored row
-            const bool zlive = iz < g.nr;
-            const float ari = rlive ? C.ar_int[ir] : 0.f, bri = rlive ? C.br_int[ir] : 0.f;
-            const float arh = zlive ? C.ar_half[iz] : 0.f, brh = zlive ? C.br_half[iz] : 0.f;
-            for (int h = 0; h < 2; ++h) {
-                const int zz2 = lane + 32 * h;
-                if (zz2 >= kSZ) break;
-                const int jj = j0 - kH + zz2;
-                float wr = 0.f, wz = 0.f, x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
-                float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-                if (jj >= 0 && jj < g.nz) {
-                    if (rlive) {
-                        const int c = ir * g.P + jj;
-                        const float w = g.dt * __ldg(C.bvr + (size_t)ir * g.nzg + g.z0 + jj) * ldcg(S.vr + c);
-                        if (ari != 0.f) p0 = ldcg(S.psi[0] + c);
-                        const float a = C.az_int[jj];
-                        if (a != 0.f) p1 = ldcg(S.psi[1] + c);
-                        x0 = (ari != 0.f) ? w + ari * (w + bri * p0) : w;
-                        x1 = (a != 0.f) ? w + a * (w + C.bz_int[jj] * p1) : w;
-                        wr = sg * w;
-                        x0 *= sg;
-                        x1 *= sg;
+        const int tid = threadIdx.y * 8 + threadIdx.x;
+        for (int it = tid; it < kSR * kQ; it += kThreads) {
+            const int r2 = it / kQ, q2 = it - r2 * kQ;
+            const int i = i0 - kH + r2, j = j0 - 4 + 4 * q2, c2 = 4 * q2;
+            float wr[4] = {0.f, 0.f, 0.f, 0.f}, wz[4] = {0.f, 0.f, 0.f, 0.f};
+            float x0[4] = {0.f, 0.f, 0.f, 0.f}, x1[4] = {0.f, 0.f, 0.f, 0.f};
+            float x2[4] = {0.f, 0.f, 0.f, 0.f}, x3[4] = {0.f, 0.f, 0.f, 0.f};
+            if (j >= 0 && j < g.nz) {
+                // v_r node: odd extension, zero on the axis and beyond nr
+                const int ir = i < 0 ? -i : i;
+                if (ir >= 1 && ir < g.nr) {
+                    const float sg = i < 0 ? -1.f : 1.f;
+                    const int cr = ir * g.P + j;
+                    const V4 av = ld4cg(S.vr + cr);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float b =
+                            j + e < g.nz ? __ldg(C.bvr + (size_t)ir * g.nzg + g.z0 + j + e) : 0.f;
+                        const float w = g.dt * b * av.v[e];
+                        x0[e] = x1[e] = w;
+                        wr[e] = w;
                     }
-                    if (zlive) {
-                        const int c = iz * g.P + jj;
-                        const float w = g.dt * bvz_at(C, g, iz, jj) * ldcg(S.vz + c);
-                        if (arh != 0.f) p2 = ldcg(S.psi[2] + c);
-                        const float a = C.az_half[jj];
-                        if (a != 0.f) p3 = ldcg(S.psi[3] + c);
-                        x2 = (arh != 0.f) ? w + arh * (w + brh * p2) : w;
-                        x3 = (a != 0.f) ? w + a * (w + C.bz_half[jj] * p3) : w;
-                        wz = w;
+                    if (pml) {
+                        const float ari = C.ar_int[ir], bri = C.br_int[ir];
+                        if (ari != 0.f) {
+                            const V4 p = ld4cg(S.psi[0] + cr);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) x0[e] = wr[e] + ari * (wr[e] + bri * p.v[e]);
+                        }
+                        const V4 azi = ld4cg(C.az_int + j), bzi = ld4cg(C.bz_int + j);
+                        const V4 p1 = ld4cg(S.psi[1] + cr);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (azi.v[e] != 0.f) x1[e] = wr[e] + azi.v[e] * (wr[e] + bzi.v[e] * p1.v[e]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        wr[e] *= sg;
+                        x0[e] *= sg;
+                        x1[e] *= sg;
                     }
                 }
-                s_wr[rr][zz2] = wr;
-                s_wz[rr][zz2] = wz;
-                s_x0[rr][zz2] = x0;
-                s_x1[rr][zz2] = x1;
-                s_x2[rr][zz2] = x2;
-                s_x3[rr][zz2] = x3;
-                s_p0[rr][zz2] = p0;
-                s_p1[rr][zz2] = p1;
-                s_p2[rr][zz2] = p2;
-                s_p3[rr][zz2] = p3;
+                // v_z node: even extension, zero beyond nr
+                const int iz = i < 0 ? -1 - i : i;
+                if (iz < g.nr) {
+                    const int cz = iz * g.P + j;
+                    const V4 av = ld4cg(S.vz + cz);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float b = j + e < g.nz ? bvz_at(C, g, iz, j + e) : 0.f;
+                        const float w = g.dt * b * av.v[e];
+                        x2[e] = x3[e] = wz[e] = w;
+                    }
+                    if (pml) {
+                        const float arh = C.ar_half[iz], brh = C.br_half[iz];
+                        if (arh != 0.f) {
+                            const V4 p = ld4cg(S.psi[2] + cz);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) x2[e] = wz[e] + arh * (wz[e] + brh * p.v[e]);
+                        }
+                        const V4 azh = ld4cg(C.az_half + j), bzh = ld4cg(C.bz_half + j);
+                        const V4 p3 = ld4cg(S.psi[3] + cz);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (azh.v[e] != 0.f) x3[e] = wz[e] + azh.v[e] * (wz[e] + bzh.v[e] * p3.v[e]);
+                    }
+                }
             }
+            *reinterpret_cast<float4*>(&s_wr[r2][c2]) = make_float4(wr[0], wr[1], wr[2], wr[3]);
+            *reinterpret_cast<float4*>(&s_wz[r2][c2]) = make_float4(wz[0], wz[1], wz[2], wz[3]);
+            *reinterpret_cast<float4*>(&s_x0[r2][c2]) = make_float4(x0[0], x0[1], x0[2], x0[3]);
+            *reinterpret_cast<float4*>(&s_x1[r2][c2]) = make_float4(x1[0], x1[1], x1[2], x1[3]);
+            *reinterpret_cast<float4*>(&s_x2[r2][c2]) = make_float4(x2[0], x2[1], x2[2], x2[3]);
+            *reinterpret_cast<float4*>(&s_x3[r2][c2]) = make_float4(x3[0], x3[1], x3[2], x3[3]);
         }
     }
     __syncthreads();
-
-    if (!jok) return;
+    if (!o.live) return;
+    const int rr = o.rr, cc = o.cc, i = o.i, c = o.c;
+    {
+        const V4 wr0 = lds4(s_wr, rr, cc), wrp1 = lds4(s_wr, rr + 1, cc);
+        const V4 x0m1 = lds4(s_x0, rr - 1, cc), x00 = lds4(s_x0, rr, cc),
+                 x0p1 = lds4(s_x0, rr + 1, cc), x0p2 = lds4(s_x0, rr + 2, cc);
+        const V12 x3r = lds12(s_x3, rr, cc - 4);
+        const float ir0 = C.inv_r_int[i], ir1 = i + 1 < g.nr ? C.inv_r_int[i + 1] : 0.f;
+        float trr[4], ttt[4], tzz[4];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + threadIdx.y + 8 * p, rr = threadIdx.y + 8 * p + kH;
-        if (i >= g.nr) break;
-        const int c = i * g.P + j;
-        // cell (i,j); inv_r_int[0] is 0 and W_r vanishes on the axis
-        float hoop = 0.5f * (s_wr[rr][zz] * C.inv_r_int[i] +
-                             s_wr[rr + 1][zz] * (i + 1 < g.nr ? C.inv_r_int[i + 1] : 0.f));
-        float arr = d4(s_x0[rr][zz], s_x0[rr + 1][zz], s_x0[rr - 1][zz], s_x0[rr + 2][zz]) * g.inv_dr;
-        float azz = d4(s_x3[rr][zz - 1], s_x3[rr][zz], s_x3[rr][zz - 2], s_x3[rr][zz + 1]) * g.inv_dz;
-        S.trr[c] = o_rr[p] + arr + hoop + r3[p];
-        S.ttt[c] = o_tt[p] - hoop + r3[p];
-        S.tzz[c] = o_zz[p] + azz + r3[p];
-
-        if (i >= 1) {
-            float sr = d4(s_x1[rr][zz], s_x1[rr][zz + 1], s_x1[rr][zz - 1], s_x1[rr][zz + 2]) * g.inv_dz;
-            sr += d4(s_x2[rr - 1][zz], s_x2[rr][zz], s_x2[rr - 2][zz], s_x2[rr + 1][zz]) * g.inv_dr;
-            sr += 0.5f * (s_wz[rr - 1][zz] * C.inv_r_half[i - 1] + s_wz[rr][zz] * C.inv_r_half[i]);
-            S.trz[c] = o_rz[p] + sr;
-            const float w = s_wr[rr][zz];
-            if (C.ar_int[i] != 0.f) S.psi_w[0][c] = w + C.br_int[i] * s_p0[rr][zz];
-            if (C.az_int[j] != 0.f) S.psi_w[1][c] = w + C.bz_int[j] * s_p1[rr][zz];
+        for (int e = 0; e < 4; ++e) {
+            // cell (i,j); inv_r_int[0] is 0 and W_r vanishes on the axis
+            const float hoop = 0.5f * (wr0.v[e] * ir0 + wrp1.v[e] * ir1);
+            const float arr = d4(x00.v[e], x0p1.v[e], x0m1.v[e], x0p2.v[e]) * g.inv_dr;
+            const float azz = d4(x3r.v[3 + e], x3r.v[4 + e], x3r.v[2 + e], x3r.v[5 + e]) * g.inv_dz;
+            trr[e] = o_rr.v[e] + arr + hoop + r3.v[e];
+            ttt[e] = o_tt.v[e] - hoop + r3.v[e];
+            tzz[e] = o_zz.v[e] + azz + r3.v[e];
         }
-        {
-            const float w = s_wz[rr][zz];
-            if (C.ar_half[i] != 0.f) S.psi_w[2][c] = w + C.br_half[i] * s_p2[rr][zz];
-            if (C.az_half[j] != 0.f) S.psi_w[3][c] = w + C.bz_half[j] * s_p3[rr][zz];
+        st4(S.trr + c, o.j, g.nz, trr);
+        st4(S.ttt + c, o.j, g.nz, ttt);
+        st4(S.tzz + c, o.j, g.nz, tzz);
+    }
+    if (i >= 1) {
+        const V12 x1r = lds12(s_x1, rr, cc - 4);
+        const V4 x2m2 = lds4(s_x2, rr - 2, cc), x2m1 = lds4(s_x2, rr - 1, cc),
+                 x20 = lds4(s_x2, rr, cc), x2p1 = lds4(s_x2, rr + 1, cc);
+        const V4 wzm1 = lds4(s_wz, rr - 1, cc), wz0 = lds4(s_wz, rr, cc);
+        const float irm = C.inv_r_half[i - 1], ir0 = C.inv_r_half[i];
+        float trz[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float s = d4(x1r.v[4 + e], x1r.v[5 + e], x1r.v[3 + e], x1r.v[6 + e]) * g.inv_dz;
+            s += d4(x2m1.v[e], x20.v[e], x2m2.v[e], x2p1.v[e]) * g.inv_dr;
+            s += 0.5f * (wzm1.v[e] * irm + wz0.v[e] * ir0);
+            trz[e] = o_rz.v[e] + s;
+        }
+        st4(S.trz + c, o.j, g.nz, trz);
+    }
+    // adjoint memories of the velocity step at the own velocity nodes
+    if (pml) {
+        const V4 wr = lds4(s_wr, rr, cc), wz = lds4(s_wz, rr, cc);
+        const V4 bzi = ld4cg(C.bz_int + o.j), bzh = ld4cg(C.bz_half + o.j);
+        const V4 p2 = ld4cg(S.psi[2] + c), p3 = ld4cg(S.psi[3] + c);
+        float w2[4], w3[4];
+        const float brh = C.br_half[i];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            w2[e] = wz.v[e] + brh * p2.v[e];
+            w3[e] = wz.v[e] + bzh.v[e] * p3.v[e];
+        }
+        if (C.ar_half[i] != 0.f) st4(S.psi_w[2] + c, o.j, g.nz, w2);
+        st4(S.psi_w[3] + c, o.j, g.nz, w3);
+        if (i >= 1) {
+            const V4 p0 = ld4cg(S.psi[0] + c), p1 = ld4cg(S.psi[1] + c);
+            const float bri = C.br_int[i];
+            float w0[4], w1[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                w0[e] = wr.v[e] + bri * p0.v[e];
+                w1[e] = wr.v[e] + bzi.v[e] * p1.v[e];
+            }
+            if (C.ar_int[i] != 0.f) st4(S.psi_w[0] + c, o.j, g.nz, w0);
+            st4(S.psi_w[1] + c, o.j, g.nz, w1);
         }
     }
 }
@@ -817,7 +1061,7 @@ struct ShotTable {
 };
 
 struct RunK {
-    const int4* tiles;  // (shot within the table, i0, j0, 0)
+    const int4* tiles;  // (shot within the table, i0, j0, TILE_* flags)
     int ntiles;
     int n0, n1;         // forward: steps n0 .. n1-1; adjoint: n1-1 down to n0
     int hist_n0;        // history slot 0 holds v^{hist_n0 - 1/2}; -1: no history
@@ -843,7 +1087,7 @@ __device__ __forceinline__ void run_fwd_vel(const RunK& r, const ShotTable<N>& T
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     float* h0 = (r.hist_n0 >= 0 && n == r.hist_n0) ? hist_slot(sh, 0) : nullptr;
-    fwd_vel_tile(sh.g, sh.C, sh.Sf, h0, tk.y, tk.z, sm);
+    fwd_vel_tile(sh.g, sh.C, sh.Sf, h0, tk.y, tk.z, tk.w, sm);
 }
 
 template <int N>
@@ -853,7 +1097,7 @@ __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     float* h = r.hist_n0 >= 0 ? hist_slot(sh, n - r.hist_n0 + 1) : nullptr;
-    fwd_stress_tile(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, sm);
+    fwd_stress_tile(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, tk.w, sm);
 }
 
 template <int N>
@@ -864,7 +1108,7 @@ __device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>
     const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
     adj_stress_tile(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, n - r.hist_n0 + 1),
-                    hist_slot(sh, n - r.hist_n0), tk.y, tk.z, sm);
+                    hist_slot(sh, n - r.hist_n0), tk.y, tk.z, tk.w, sm);
 }
 
 template <int N>
@@ -874,7 +1118,7 @@ __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
-    adj_vel_tile(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, sm);
+    adj_vel_tile(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w, sm);
 }
 
 // one launch per half-step: one block per tile

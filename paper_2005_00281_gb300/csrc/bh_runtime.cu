@@ -154,6 +154,8 @@ void pml_ab(double x, double d0, double alpha_max, double dt, double* a, double*
 size_t plane(const bh_model* m) { return (size_t)m->grid.nr * m->P; }
 
 dim3 block2d() { return dim3(32, 8); }
+// block of the stepping kernels: 8 column groups of 4 nodes x 16 rows
+dim3 block_tiles() { return dim3(8, 16); }
 dim3 grid2d(int nr, int nz) { return dim3((nz + 31) / 32, (nr + 7) / 8); }
 
 // ------------------------------------------------------ checkpoint schedule
@@ -304,10 +306,11 @@ bh_status setup_profiles(bh_model* m)
     std::vector<float> zp;
     std::vector<int> recmap;
     for (auto& s : m->shots) {
-        const int nz = s.nz;
+        const int nz = s.nz, P = m->P;
         s.zprof_off = zp.size();
         s.recmap_off = recmap.size();
-        zp.resize(zp.size() + 4 * (size_t)nz);
+        // 4 profiles of P entries each (zero beyond nz: read as float4 rows)
+        zp.resize(zp.size() + 4 * (size_t)P, 0.f);
         float* z = zp.data() + s.zprof_off;
         for (int j = 0; j < nz; ++j)
             for (int h = 0; h < 2; ++h) {
@@ -319,8 +322,8 @@ bh_status setup_profiles(bh_model* m)
                 }
                 double a, b;
                 pml_ab(x, d0z, alpha_max, g.dt, &a, &b);
-                z[(2 * h) * nz + j] = (float)a;
-                z[(2 * h + 1) * nz + j] = (float)b;
+                z[(2 * h) * P + j] = (float)a;
+                z[(2 * h + 1) * P + j] = (float)b;
             }
         recmap.resize(recmap.size() + nz, -1);
         for (int k = 0; k < s.nrec; ++k) recmap[s.recmap_off + s.rec_iz[k]] = k;
@@ -375,9 +378,9 @@ bh_status setup_shots(bh_model* m)
         C.br_half = m->d_rprof + 5 * nr;
         const float* zp = m->d_zprof + sh.zprof_off;
         C.az_int = zp;
-        C.bz_int = zp + sh.nz;
-        C.az_half = zp + 2 * sh.nz;
-        C.bz_half = zp + 3 * sh.nz;
+        C.bz_int = zp + m->P;
+        C.az_half = zp + 2 * m->P;
+        C.bz_half = zp + 3 * m->P;
         float* f = m->d_fwd + (size_t)s * kFwdPlanes * pl;
         float* a = m->d_adj + (size_t)s * kAdjPlanes * pl;
         StateK* views[3] = {&k.Sf, &k.Sa[0], &k.Sa[1]};
@@ -421,7 +424,13 @@ bh_status setup_shots(bh_model* m)
         }
         for (int i0 = 0; i0 < nr; i0 += kTR)
             for (int j0 = 0; j0 < sh.nz; j0 += kTZ) {
-                tiles.push_back(make_int4(s % kGroup, i0, j0, 0));
+                // a tile reads nodes i0-2 .. i0+17, j0-4 .. j0+35; a layer
+                // coefficient is non-zero from row nr - npml_r and in the
+                // first / last npml_z columns (one node of margin each way)
+                const bool radial = gd.npml_r > 0 && i0 + kTR + kH >= nr - gd.npml_r - 1;
+                const bool axial = gd.npml_z > 0 &&
+                                   (j0 - 4 <= gd.npml_z + 1 || j0 + kTZ + 4 >= sh.nz - gd.npml_z - 2);
+                tiles.push_back(make_int4(s % kGroup, i0, j0, (radial || axial) ? TILE_PML : 0));
                 m->group_ntiles.back()++;
             }
     }
@@ -531,7 +540,7 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
 {
     RunK r = make_run(m, grp, n0, n1, hist_n0, record);
     ShotTable<N> T = group_table<N>(m, grp);
-    const dim3 blk = block2d();
+    const dim3 blk = block_tiles();
     if (m->persistent) {
         const int blocks = std::min(r.ntiles, N == 1 ? m->fwd_blocks : m->fwd_blocks_g);
         BarK b = make_bar(m, blocks);
@@ -561,7 +570,7 @@ bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
 {
     RunK r = make_run(m, grp, n0, n1, hist_n0, false);
     ShotTable<N> T = group_table<N>(m, grp);
-    const dim3 blk = block2d();
+    const dim3 blk = block_tiles();
     if (m->persistent) {
         const int blocks = std::min(r.ntiles, N == 1 ? m->adj_blocks : m->adj_blocks_g);
         BarK b = make_bar(m, blocks);
