@@ -316,22 +316,6 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
             for (int e = 0; e < 4; ++e)
                 if (o.j + e < g.nz) br.v[e] = __ldg(C.bvr + (size_t)o.i * g.nzg + g.z0 + o.j + e);
         }
-        if (pml) {
-            arh = C.ar_half[o.i];
-            brh = C.br_half[o.i];
-            azh = ld4cg(C.az_half + o.j);
-            bzh = ld4cg(C.bz_half + o.j);
-            if (arh != 0.f) q2 = ld4cg(S.psi[2] + o.c);
-            q3 = ld4cg(S.psi[3] + o.c);
-            if (o.i >= 1) {
-                ari = C.ar_int[o.i];
-                bri = C.br_int[o.i];
-                azi = ld4cg(C.az_int + o.j);
-                bzi = ld4cg(C.bz_int + o.j);
-                if (ari != 0.f) q0 = ld4cg(S.psi[0] + o.c);
-                q1 = ld4cg(S.psi[1] + o.c);
-            }
-        }
     }
     __syncthreads();
     stage<EVEN>(s_rr, S.trr, i0, j0, g);
@@ -340,6 +324,24 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     stage<EVEN>(s_zz, S.tzz, i0, j0, g);
     __syncthreads();
     if (!o.live) return;
+    // layer tiles only: memories and profiles (kept out of the prefetch to
+    // spare registers)
+    if (pml) {
+        arh = C.ar_half[o.i];
+        brh = C.br_half[o.i];
+        azh = ld4cg(C.az_half + o.j);
+        bzh = ld4cg(C.bz_half + o.j);
+        if (arh != 0.f) q2 = ld4cg(S.psi[2] + o.c);
+        q3 = ld4cg(S.psi[3] + o.c);
+        if (o.i >= 1) {
+            ari = C.ar_int[o.i];
+            bri = C.br_int[o.i];
+            azi = ld4cg(C.az_int + o.j);
+            bzi = ld4cg(C.bz_int + o.j);
+            if (ari != 0.f) q0 = ld4cg(S.psi[0] + o.c);
+            q1 = ld4cg(S.psi[1] + o.c);
+        }
+    }
     const int rr = o.rr, cc = o.cc;
     const V12 rz12 = lds12(s_rz, rr, cc - 4);
     const V4 rzp1 = lds4(s_rz, rr + 1, cc);
@@ -441,28 +443,28 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
             for (int e = 0; e < 4; ++e)
                 if (o.j + e < g.nz) mh.v[e] = muh_at(C, g, o.i, o.j + e);
         }
-        if (pml) {
-            arh = C.ar_half[o.i];
-            brh = C.br_half[o.i];
-            azi = ld4cg(C.az_int + o.j);
-            bzi = ld4cg(C.bz_int + o.j);
-            if (arh != 0.f) q4 = ld4cg(S.psi[4] + o.c);
-            q5 = ld4cg(S.psi[5] + o.c);
-            if (o.i >= 1) {
-                ari = C.ar_int[o.i];
-                bri = C.br_int[o.i];
-                azh = ld4cg(C.az_half + o.j);
-                bzh = ld4cg(C.bz_half + o.j);
-                q6 = ld4cg(S.psi[6] + o.c);
-                if (ari != 0.f) q7 = ld4cg(S.psi[7] + o.c);
-            }
-        }
     }
     __syncthreads();
     stage<ODD>(s_vr, S.vr, i0, j0, g);
     stage<EVEN>(s_vz, S.vz, i0, j0, g);
     __syncthreads();
     if (!o.live) return;
+    if (pml) {
+        arh = C.ar_half[o.i];
+        brh = C.br_half[o.i];
+        azi = ld4cg(C.az_int + o.j);
+        bzi = ld4cg(C.bz_int + o.j);
+        if (arh != 0.f) q4 = ld4cg(S.psi[4] + o.c);
+        q5 = ld4cg(S.psi[5] + o.c);
+        if (o.i >= 1) {
+            ari = C.ar_int[o.i];
+            bri = C.br_int[o.i];
+            azh = ld4cg(C.az_half + o.j);
+            bzh = ld4cg(C.bz_half + o.j);
+            q6 = ld4cg(S.psi[6] + o.c);
+            if (ari != 0.f) q7 = ld4cg(S.psi[7] + o.c);
+        }
+    }
     const int rr = o.rr, cc = o.cc;
     const V12 vr12 = lds12(s_vr, rr, cc - 4), vz12 = lds12(s_vz, rr, cc - 4);
     const V4 vrm1 = lds4(s_vr, rr - 1, cc), vrp1 = lds4(s_vr, rr + 1, cc),
