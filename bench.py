@@ -251,6 +251,7 @@ def run_gpu(args, w):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     # observed data: forward modelling in the true model (outside the timing)
     cap = int(args.cap_gb * 1e9)
+    prec = {"fp32": 0, "bf16": 1, "fp16": 2}[args.snap]
     true = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap)
     true.set_model(t(w.vp_true), t(w.vs_true), t(w.rho_true))
     wav = t(w.wavelet)
@@ -259,7 +260,7 @@ def run_gpu(args, w):
     true.close()
     del true
 
-    m = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap)
+    m = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap, snapshot_precision=prec)
     if args.per_step:
         m.set_option("persistent", 0)
     start_model = (t(w.vp), t(w.vs), t(w.rho))
@@ -399,6 +400,7 @@ def run_gpu(args, w):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(), "J_first_last": [Js[0], Js[-1]],
             "history": {k: m.info(k) for k in ("history_steps", "snapshots", "recompute_steps",
+                                               "snapshot_precision",
                                                "history_snapshot_bytes", "tiles",
                                                "persistent_blocks_fwd", "persistent_blocks_adj")},
             "source_sha": source_sha()}
@@ -425,6 +427,8 @@ def main():
     ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
     ap.add_argument("--cap-gb", type=float, default=0.0,
                     help="checkpoint cap in GB (0: store every step of the forward history)")
+    ap.add_argument("--snap", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="precision of the checkpoint snapshots")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-step", action="store_true",
                     help="one kernel launch per half-step instead of the persistent kernels")
