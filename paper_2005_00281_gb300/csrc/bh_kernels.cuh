@@ -32,6 +32,10 @@ struct CoefK {
     const float *inv_r_int, *inv_r_half;          // [nr]
     const float *ar_int, *br_int, *ar_half, *br_half;  // radial C-PML [nr]
     const float *az_int, *bz_int, *az_half, *bz_half;  // axial C-PML of the window [nz]
+    // the window's own copies, [nr][P], zero beyond nz: lambda, mu (cells),
+    // harmonic mu (trz nodes), buoyancy at v_r and v_z nodes, the last two
+    // with the window's last-row rule (muh_at, bvz_at)
+    const float *w_lam, *w_mu, *w_muh, *w_bvr, *w_bvz;
 };
 
 struct StateK {
@@ -135,6 +139,13 @@ __device__ __forceinline__ V4 ld4cg(const float* p)
     return V4{{t.x, t.y, t.z, t.w}};
 }
 
+// read-only data (model planes): non-coherent path
+__device__ __forceinline__ V4 ld4g(const float* p)
+{
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    return V4{{t.x, t.y, t.z, t.w}};
+}
+
 __device__ __forceinline__ V4 lds4(const Tile& s, int rr, int cc)
 {
     const float4 t = *reinterpret_cast<const float4*>(&s[rr][cc]);
@@ -196,9 +207,9 @@ __device__ __forceinline__ void ld4f2(const float2* p, float2 (&x)[4])
 
 // Stage rows i0-2 .. i0+17, columns j0-4 .. j0+35 of a window field.
 // EVEN: half-r field (cells, v_z), mirror f[-1-k] = f[k].  ODD: integer-r
-// field (v_r, trz), f[-k] = -f[k], f[0] = 0.  Zero beyond nr and outside
-// 0 <= z < nz.
-enum { EVEN = 0, ODD = 1 };
+// field (v_r, trz), f[-k] = -f[k], f[0] = 0.  ABS: integer-r coefficient
+// (harmonic mu), f[-k] = f[k].  Zero beyond nr and outside 0 <= z < nz.
+enum { EVEN = 0, ODD = 1, ABS = 2 };
 template <int KIND>
 __device__ __forceinline__ void stage(Tile& s, const float* __restrict__ f, int i0, int j0,
                                       const WinK& g)
@@ -210,9 +221,11 @@ __device__ __forceinline__ void stage(Tile& s, const float* __restrict__ f, int 
         float sg = 1.f;
         if (KIND == EVEN) {
             if (i < 0) i = -1 - i;
-        } else {
+        } else if (KIND == ODD) {
             if (i < 0) { i = -i; sg = -1.f; }
             if (i == 0) sg = 0.f;
+        } else {
+            if (i < 0) i = -i;
         }
         const int j = j0 - 4 + 4 * q;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -227,36 +240,6 @@ __device__ __forceinline__ void stage(Tile& s, const float* __restrict__ f, int 
             v.w *= sg;
         }
         *reinterpret_cast<float4*>(&s[rr][4 * q]) = v;
-    }
-}
-
-// Stage a model field over the tile: cells (CELL) mirror evenly; shear
-// nodes (SHEAR: harmonic mu with the window's own last-row rule) mirror to
-// row |i|.  The window may start at any global row, so loads are scalar.
-enum { CELL = 0, SHEAR = 1 };
-template <int KIND>
-__device__ __forceinline__ void stage_model(Tile& s, const float* __restrict__ f, const CoefK& C,
-                                            int i0, int j0, const WinK& g)
-{
-    const int tid = threadIdx.y * 8 + threadIdx.x;
-    for (int it = tid; it < kSR * kQ; it += kThreads) {
-        const int rr = it / kQ, q = it - rr * kQ;
-        int i = i0 - kH + rr;
-        if (KIND == CELL) {
-            if (i < 0) i = -1 - i;
-        } else {
-            if (i < 0) i = -i;
-        }
-        const bool live = i < g.nr && (KIND == CELL || i >= 1);
-        float x[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int j = j0 - 4 + 4 * q + e;
-            x[e] = 0.f;
-            if (live && j >= 0 && j < g.nz)
-                x[e] = (KIND == CELL) ? __ldg(f + (size_t)i * g.nzg + g.z0 + j) : muh_at(C, g, i, j);
-        }
-        *reinterpret_cast<float4*>(&s[rr][4 * q]) = make_float4(x[0], x[1], x[2], x[3]);
     }
 }
 
@@ -307,14 +290,10 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     V4 azi{}, bzi{}, azh{}, bzh{};
     if (o.live) {
         vz0 = ld4cg(S.vz + o.c);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            if (o.j + e < g.nz) bz.v[e] = bvz_at(C, g, o.i, o.j + e);
+        bz = ld4g(C.w_bvz + o.c);
         if (o.i >= 1) {
             vr0 = ld4cg(S.vr + o.c);
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (o.j + e < g.nz) br.v[e] = __ldg(C.bvr + (size_t)o.i * g.nzg + g.z0 + o.j + e);
+            br = ld4g(C.w_bvr + o.c);
         }
     }
     __syncthreads();
@@ -423,40 +402,87 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     Tile &s_vr = sm.a, &s_vz = sm.b;
     const Own o = own_of(g, i0, j0);
     const bool pml = flags & TILE_PML;
-    V4 t_rr{}, t_tt{}, t_zz{}, t_rz{}, lm{}, mu{}, mh{}, q4{}, q5{}, q6{}, q7{};
-    float arh = 0.f, brh = 0.f, ari = 0.f, bri = 0.f;
-    V4 azi{}, bzi{}, azh{}, bzh{};
+    V4 t_rr{}, t_tt{}, t_zz{}, lm{}, mu{};
     if (o.live) {
         t_rr = ld4cg(S.trr + o.c);
         t_tt = ld4cg(S.ttt + o.c);
         t_zz = ld4cg(S.tzz + o.c);
-        const size_t cg = (size_t)o.i * g.nzg + g.z0 + o.j;
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            if (o.j + e < g.nz) {
-                lm.v[e] = __ldg(C.lam + cg + e);
-                mu.v[e] = __ldg(C.mu + cg + e);
-            }
-        if (o.i >= 1) {
-            t_rz = ld4cg(S.trz + o.c);
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (o.j + e < g.nz) mh.v[e] = muh_at(C, g, o.i, o.j + e);
-        }
+        lm = ld4g(C.w_lam + o.c);
+        mu = ld4g(C.w_mu + o.c);
     }
     __syncthreads();
     stage<ODD>(s_vr, S.vr, i0, j0, g);
     stage<EVEN>(s_vz, S.vz, i0, j0, g);
     __syncthreads();
     if (!o.live) return;
-    if (pml) {
-        arh = C.ar_half[o.i];
-        brh = C.br_half[o.i];
-        azi = ld4cg(C.az_int + o.j);
-        bzi = ld4cg(C.bz_int + o.j);
-        if (arh != 0.f) q4 = ld4cg(S.psi[4] + o.c);
-        q5 = ld4cg(S.psi[5] + o.c);
-        if (o.i >= 1) {
+    const int rr = o.rr, cc = o.cc;
+    // shear inputs: issued now, used after the normal stresses
+    V4 t_rz{}, mh{};
+    if (o.i >= 1) {
+        t_rz = ld4cg(S.trz + o.c);
+        mh = ld4g(C.w_muh + o.c);
+    }
+    {
+        float arh = 0.f, brh = 0.f;
+        V4 azi{}, bzi{}, q4{}, q5{};
+        if (pml) {
+            arh = C.ar_half[o.i];
+            brh = C.br_half[o.i];
+            azi = ld4cg(C.az_int + o.j);
+            bzi = ld4cg(C.bz_int + o.j);
+            if (arh != 0.f) q4 = ld4cg(S.psi[4] + o.c);
+            q5 = ld4cg(S.psi[5] + o.c);
+        }
+        const V12 vr12 = lds12(s_vr, rr, cc - 4), vz12 = lds12(s_vz, rr, cc - 4);
+        const V4 vrp1 = lds4(s_vr, rr + 1, cc);
+        const float inv_rh = C.inv_r_half[o.i];
+        float trr[4], ttt[4], tzz[4], w4[4], w5[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float d_vr = d4(vrp1.v[e], vr12.v[4 + e], s_vr[rr + 2][cc + e], s_vr[rr - 1][cc + e]) *
+                         g.inv_dr;
+            const float vr_r = 0.5f * (vr12.v[4 + e] + vrp1.v[e]) * inv_rh;
+            float d_vz = d4(vz12.v[4 + e], vz12.v[3 + e], vz12.v[5 + e], vz12.v[2 + e]) * g.inv_dz;
+            if (pml) {
+                if (arh != 0.f) {
+                    w4[e] = brh * q4.v[e] + arh * d_vr;
+                    d_vr += w4[e];
+                }
+                if (azi.v[e] != 0.f) {
+                    w5[e] = bzi.v[e] * q5.v[e] + azi.v[e] * d_vz;
+                    d_vz += w5[e];
+                } else {
+                    w5[e] = q5.v[e];
+                }
+            }
+            const float lam = lm.v[e];
+            const float l2m = lam + 2.f * mu.v[e];
+            trr[e] = t_rr.v[e] + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
+            ttt[e] = t_tt.v[e] + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
+            tzz[e] = t_zz.v[e] + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
+            if (o.c + e == q.src_c) {
+                const float inj = q.src_scale * q.wavelet[n];
+                trr[e] += inj;
+                ttt[e] += inj;
+                tzz[e] += inj;
+            }
+            if (o.i == 0 && record && o.j + e < g.nz) {
+                const int k = q.recmap[o.j + e];
+                if (k >= 0) q.seis[(size_t)k * q.nt + n] = (trr[e] + ttt[e] + tzz[e]) * (1.f / 3.f);
+            }
+        }
+        st4(S.trr + o.c, o.j, g.nz, trr);
+        st4(S.ttt + o.c, o.j, g.nz, ttt);
+        st4(S.tzz + o.c, o.j, g.nz, tzz);
+        if (pml) {
+            if (arh != 0.f) st4(S.psi_w[4] + o.c, o.j, g.nz, w4);
+            st4(S.psi_w[5] + o.c, o.j, g.nz, w5);
+        }
+    }
+    if (o.i >= 1) {
+        float ari = 0.f, bri = 0.f;
+        V4 azh{}, bzh{}, q6{}, q7{};
+        if (pml) {
             ari = C.ar_int[o.i];
             bri = C.br_int[o.i];
             azh = ld4cg(C.az_half + o.j);
@@ -464,61 +490,14 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
             q6 = ld4cg(S.psi[6] + o.c);
             if (ari != 0.f) q7 = ld4cg(S.psi[7] + o.c);
         }
-    }
-    const int rr = o.rr, cc = o.cc;
-    const V12 vr12 = lds12(s_vr, rr, cc - 4), vz12 = lds12(s_vz, rr, cc - 4);
-    const V4 vrm1 = lds4(s_vr, rr - 1, cc), vrp1 = lds4(s_vr, rr + 1, cc),
-             vrp2 = lds4(s_vr, rr + 2, cc);
-    const float inv_rh = C.inv_r_half[o.i];
-    float trr[4], ttt[4], tzz[4], w4[4], w5[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        float d_vr = d4(vrp1.v[e], vr12.v[4 + e], vrp2.v[e], vrm1.v[e]) * g.inv_dr;
-        const float vr_r = 0.5f * (vr12.v[4 + e] + vrp1.v[e]) * inv_rh;
-        float d_vz = d4(vz12.v[4 + e], vz12.v[3 + e], vz12.v[5 + e], vz12.v[2 + e]) * g.inv_dz;
-        if (pml) {
-            if (arh != 0.f) {
-                w4[e] = brh * q4.v[e] + arh * d_vr;
-                d_vr += w4[e];
-            }
-            if (azi.v[e] != 0.f) {
-                w5[e] = bzi.v[e] * q5.v[e] + azi.v[e] * d_vz;
-                d_vz += w5[e];
-            } else {
-                w5[e] = q5.v[e];
-            }
-        }
-        const float lam = lm.v[e];
-        const float l2m = lam + 2.f * mu.v[e];
-        trr[e] = t_rr.v[e] + g.dt * (l2m * d_vr + lam * (vr_r + d_vz));
-        ttt[e] = t_tt.v[e] + g.dt * (l2m * vr_r + lam * (d_vr + d_vz));
-        tzz[e] = t_zz.v[e] + g.dt * (l2m * d_vz + lam * (d_vr + vr_r));
-        if (o.c + e == q.src_c) {
-            const float inj = q.src_scale * q.wavelet[n];
-            trr[e] += inj;
-            ttt[e] += inj;
-            tzz[e] += inj;
-        }
-        if (o.i == 0 && record && o.j + e < g.nz) {
-            const int k = q.recmap[o.j + e];
-            if (k >= 0) q.seis[(size_t)k * q.nt + n] = (trr[e] + ttt[e] + tzz[e]) * (1.f / 3.f);
-        }
-    }
-    st4(S.trr + o.c, o.j, g.nz, trr);
-    st4(S.ttt + o.c, o.j, g.nz, ttt);
-    st4(S.tzz + o.c, o.j, g.nz, tzz);
-    if (pml) {
-        if (arh != 0.f) st4(S.psi_w[4] + o.c, o.j, g.nz, w4);
-        st4(S.psi_w[5] + o.c, o.j, g.nz, w5);
-    }
-    if (o.i >= 1) {
-        const V4 vzm1 = lds4(s_vz, rr - 1, cc), vzm2 = lds4(s_vz, rr - 2, cc),
-                 vzp1 = lds4(s_vz, rr + 1, cc);
+        const V12 vr12 = lds12(s_vr, rr, cc - 4);
+        const V4 vz0 = lds4(s_vz, rr, cc), vzm1 = lds4(s_vz, rr - 1, cc),
+                 vzm2 = lds4(s_vz, rr - 2, cc), vzp1 = lds4(s_vz, rr + 1, cc);
         float trz[4], w6[4], w7[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             float d_vrz = d4(vr12.v[5 + e], vr12.v[4 + e], vr12.v[6 + e], vr12.v[3 + e]) * g.inv_dz;
-            float d_vzr = d4(vz12.v[4 + e], vzm1.v[e], vzp1.v[e], vzm2.v[e]) * g.inv_dr;
+            float d_vzr = d4(vz0.v[e], vzm1.v[e], vzp1.v[e], vzm2.v[e]) * g.inv_dr;
             if (pml) {
                 if (azh.v[e] != 0.f) {
                     w6[e] = bzh.v[e] * q6.v[e] + azh.v[e] * d_vrz;
@@ -540,14 +519,9 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         }
     }
     if (hist) {
-        float a[4], b[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            a[e] = vr12.v[4 + e];
-            b[e] = vz12.v[4 + e];
-        }
-        st4(hist + o.c, o.j, g.nz, a);
-        st4(hist + g.nr * g.P + o.c, o.j, g.nz, b);
+        const V4 a = lds4(s_vr, rr, cc), b = lds4(s_vz, rr, cc);
+        st4(hist + o.c, o.j, g.nz, a.v);
+        st4(hist + g.nr * g.P + o.c, o.j, g.nz, b.v);
     }
 }
 
@@ -588,6 +562,8 @@ __device__ bool grid_barrier(const BarK& b, unsigned& epoch)
         int ok = 1;
         if (old + 1u < target) {
             const unsigned long long t0 = global_ns();
+            // every poll is an L2 round trip (>= 64 ns); the error flag and
+            // the clock are checked every 8th poll
             const unsigned long long max_polls = b.timeout_ns / 64ull + 1024ull;
             unsigned long long polls = 0;
             volatile int* verr = b.err;
@@ -595,13 +571,14 @@ __device__ bool grid_barrier(const BarK& b, unsigned& epoch)
                 unsigned cur;
                 asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(b.count) : "memory");
                 if (cur >= target) break;
-                if (*verr) { ok = 0; break; }
-                if (global_ns() - t0 > b.timeout_ns || ++polls > max_polls) {
-                    atomicExch(b.err, 1);
-                    ok = 0;
-                    break;
+                if ((++polls & 7ull) == 0) {
+                    if (*verr) { ok = 0; break; }
+                    if (global_ns() - t0 > b.timeout_ns || polls > max_polls) {
+                        atomicExch(b.err, 1);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(32);
             }
         }
         if (ok && *(volatile int*)b.err) ok = 0;
@@ -661,11 +638,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     const float dt = g.dt;
     const Own o = own_of(g, i0, j0);
     const bool pml = flags & TILE_PML;
-    V4 av_r{}, av_z{};
-    if (o.live) {
-        av_z = ld4cg(S.vz + o.c);
-        if (o.i >= 1) av_r = ld4cg(S.vr + o.c);
-    }
+    const int rr = o.rr, cc = o.cc, i = o.i, c = o.c;
     __syncthreads();
     stage<EVEN>(sm.arr, S.trr, i0, j0, g);
     stage<EVEN>(sm.att, S.ttt, i0, j0, g);
@@ -673,20 +646,27 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     stage<ODD>(sm.arz, S.trz, i0, j0, g);
     stage<ODD>(sm.fvr, fcur, i0, j0, g);
     stage<EVEN>(sm.fvz, fcur + plane, i0, j0, g);
-    stage_model<CELL>(sm.x4, C.lam, C, i0, j0, g);
-    stage_model<CELL>(sm.ytt, C.mu, C, i0, j0, g);
-    stage_model<SHEAR>(sm.x5, nullptr, C, i0, j0, g);
+    stage<EVEN>(sm.x4, C.w_lam, i0, j0, g);
+    stage<EVEN>(sm.ytt, C.w_mu, i0, j0, g);
+    stage<ABS>(sm.x5, C.w_muh, i0, j0, g);
     __syncthreads();
-    const int rr = o.rr, cc = o.cc;
-    const V4 lam_o = lds4(sm.x4, rr, cc), mu_o = lds4(sm.ytt, rr, cc), mh_o = lds4(sm.x5, rr, cc);
-    __syncthreads();
+    // own accumulators of the lambda and normal-mu correlations: issued
+    // here so that their latency overlaps the coefficient build
+    float2 gl[4], gm[4];
+    V4 hl{}, hm{};
+    if (o.live) {
+        ld4f2(q.G_lam + c, gl);
+        ld4f2(q.G_munn + c, gm);
+        hl = ld4cg(q.H_lam + c);
+        hm = ld4cg(q.H_munn + c);
+    }
     // transposed-stencil coefficients over the staged region, in place
     {
         const int tid = threadIdx.y * 8 + threadIdx.x;
         for (int it = tid; it < kSR * kQ; it += kThreads) {
             const int r2 = it / kQ, q2 = it - r2 * kQ;
-            const int i = i0 - kH + r2, j = j0 - 4 + 4 * q2, c2 = 4 * q2;
-            const int ic = i < 0 ? -1 - i : i;
+            const int ii = i0 - kH + r2, j = j0 - 4 + 4 * q2, c2 = 4 * q2;
+            const int ic = ii < 0 ? -1 - ii : ii;
             const V4 lm = lds4(sm.x4, r2, c2), mu = lds4(sm.ytt, r2, c2), mh = lds4(sm.x5, r2, c2);
             const V4 ar = lds4(sm.arr, r2, c2), at = lds4(sm.att, r2, c2), az = lds4(sm.azz, r2, c2);
             const V4 arz = lds4(sm.arz, r2, c2);
@@ -700,7 +680,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
                 // shear node: the staged values are already odd about the axis
                 x6[e] = x7[e] = dt * mh.v[e] * arz.v[e];
             }
-            if (pml && i < g.nr && j >= 0 && j < g.nz) {
+            if (pml && ii < g.nr && j >= 0 && j < g.nz) {
                 const float arh = C.ar_half[ic], brh = C.br_half[ic];
                 if (arh != 0.f) {
                     const V4 p = ld4cg(S.psi[4] + ic * g.P + j);
@@ -712,15 +692,15 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                     if (azi.v[e] != 0.f) x5[e] = x5[e] + azi.v[e] * (x5[e] + bzi.v[e] * p5.v[e]);
-                if (i >= 1) {
+                if (ii >= 1) {
                     const V4 azh = ld4cg(C.az_half + j), bzh = ld4cg(C.bz_half + j);
-                    const V4 p6 = ld4cg(S.psi[6] + i * g.P + j);
+                    const V4 p6 = ld4cg(S.psi[6] + ii * g.P + j);
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
                         if (azh.v[e] != 0.f) x6[e] = x6[e] + azh.v[e] * (x6[e] + bzh.v[e] * p6.v[e]);
-                    const float ari = C.ar_int[i], bri = C.br_int[i];
+                    const float ari = C.ar_int[ii], bri = C.br_int[ii];
                     if (ari != 0.f) {
-                        const V4 p7 = ld4cg(S.psi[7] + i * g.P + j);
+                        const V4 p7 = ld4cg(S.psi[7] + ii * g.P + j);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) x7[e] = x7[e] + ari * (x7[e] + bri * p7.v[e]);
                     }
@@ -735,63 +715,71 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     }
     __syncthreads();
     if (!o.live) return;
-    const int i = o.i, c = o.c;
 
-    // ---- forward strains of v^{n+1/2} and own adjoint stresses
-    const V12 fr12 = lds12(sm.fvr, rr, cc - 4), fz12 = lds12(sm.fvz, rr, cc - 4);
-    const V4 frm1 = lds4(sm.fvr, rr - 1, cc), frp1 = lds4(sm.fvr, rr + 1, cc),
-             frp2 = lds4(sm.fvr, rr + 2, cc);
-    const V4 Arr = lds4(sm.arr, rr, cc), Att = lds4(sm.att, rr, cc), Azz = lds4(sm.azz, rr, cc),
-             Arz = lds4(sm.arz, rr, cc);
-    const float inv_rh = C.inv_r_half[i];
-    float err[4], ett[4], ezz[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        err[e] = d4(frp1.v[e], fr12.v[4 + e], frp2.v[e], frm1.v[e]) * g.inv_dr;
-        ett[e] = 0.5f * (fr12.v[4 + e] + frp1.v[e]) * inv_rh;
-        ezz[e] = d4(fz12.v[4 + e], fz12.v[3 + e], fz12.v[5 + e], fz12.v[2 + e]) * g.inv_dz;
-    }
+    // ---- remaining own-node inputs, issued before any store of this tile
+    float2 gbz[4];
+    const V4 av_z = ld4cg(S.vz + c);
+    ld4f2(q.G_bz + c, gbz);
+    const V4 pz = ld4cg(fprev + plane + c);
+
     // ---- lambda and normal mu correlations, pseudo-Hessian
     {
-        float2 gl[4], gm[4];
-        ld4f2(q.G_lam + c, gl);
-        ld4f2(q.G_munn + c, gm);
-        const V4 hl = ld4cg(q.H_lam + c), hm = ld4cg(q.H_munn + c);
+        const V12 fr12 = lds12(sm.fvr, rr, cc - 4), fz12 = lds12(sm.fvz, rr, cc - 4);
+        const V4 frm1 = lds4(sm.fvr, rr - 1, cc), frp1 = lds4(sm.fvr, rr + 1, cc),
+                 frp2 = lds4(sm.fvr, rr + 2, cc);
+        const V4 Arr = lds4(sm.arr, rr, cc), Att = lds4(sm.att, rr, cc), Azz = lds4(sm.azz, rr, cc);
+        const float inv_rh = C.inv_r_half[i];
         float hl2[4], hm2[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float div = err[e] + ett[e] + ezz[e];
+            const float err = d4(frp1.v[e], fr12.v[4 + e], frp2.v[e], frm1.v[e]) * g.inv_dr;
+            const float ett = 0.5f * (fr12.v[4 + e] + frp1.v[e]) * inv_rh;
+            const float ezz = d4(fz12.v[4 + e], fz12.v[3 + e], fz12.v[5 + e], fz12.v[2 + e]) * g.inv_dz;
+            const float div = err + ett + ezz;
             gl[e] = kahan_step(gl[e], dt * div * (Arr.v[e] + Att.v[e] + Azz.v[e]));
-            gm[e] = kahan_step(gm[e], 2.f * dt *
-                                          (err[e] * Arr.v[e] + ett[e] * Att.v[e] + ezz[e] * Azz.v[e]));
+            gm[e] = kahan_step(gm[e], 2.f * dt * (err * Arr.v[e] + ett * Att.v[e] + ezz * Azz.v[e]));
             hl2[e] = hl.v[e] + dt * div * div;
-            hm2[e] = hm.v[e] + 4.f * dt * (err[e] * err[e] + ett[e] * ett[e] + ezz[e] * ezz[e]);
+            hm2[e] = hm.v[e] + 4.f * dt * (err * err + ett * ett + ezz * ezz);
         }
         st4f2(q.G_lam + c, o.j, g.nz, gl);
         st4f2(q.G_munn + c, o.j, g.nz, gm);
         st4(q.H_lam + c, o.j, g.nz, hl2);
         st4(q.H_munn + c, o.j, g.nz, hm2);
     }
-    // ---- transpose of the stress step into Av
-    float avr[4], avz[4];
+    float2 gmr[4];
+    V4 hmr{}, pr{}, av_r{};
+    if (i >= 1) {
+        av_r = ld4cg(S.vr + c);
+        ld4f2(q.G_murz + c, gmr);
+        hmr = ld4cg(q.H_murz + c);
+        pr = ld4cg(fprev + c);
+    }
+    // ---- transpose of the stress step into Av, density and shear correlations
     {
         const V12 x5r = lds12(sm.x5, rr, cc - 4);
         const V4 x7m1 = lds4(sm.x7, rr - 1, cc), x70 = lds4(sm.x7, rr, cc),
                  x7p1 = lds4(sm.x7, rr + 1, cc), x7p2 = lds4(sm.x7, rr + 2, cc);
+        const V4 fz0 = lds4(sm.fvz, rr, cc);
+        float avz[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             float s = d4(x5r.v[4 + e], x5r.v[5 + e], x5r.v[3 + e], x5r.v[6 + e]) * g.inv_dz;
             s += d4(x70.v[e], x7p1.v[e], x7m1.v[e], x7p2.v[e]) * g.inv_dr;
             avz[e] = av_z.v[e] + s;
+            gbz[e] = kahan_step(gbz[e], (fz0.v[e] - pz.v[e]) * avz[e]);
         }
         st4(S.vz + c, o.j, g.nz, avz);
+        st4f2(q.G_bz + c, o.j, g.nz, gbz);
     }
     if (i >= 1) {
+        float2 gbr[4];
+        ld4f2(q.G_br + c, gbr);
         const V4 x4m2 = lds4(sm.x4, rr - 2, cc), x4m1 = lds4(sm.x4, rr - 1, cc),
                  x40 = lds4(sm.x4, rr, cc), x4p1 = lds4(sm.x4, rr + 1, cc);
         const V4 ytm1 = lds4(sm.ytt, rr - 1, cc), yt0 = lds4(sm.ytt, rr, cc);
         const V12 x6r = lds12(sm.x6, rr, cc - 4);
-        const float irm = C.inv_r_half[i - 1];
+        const float irm = C.inv_r_half[i - 1], inv_rh = C.inv_r_half[i];
+        float avr[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             float s = d4(x4m1.v[e], x40.v[e], x4m2.v[e], x4p1.v[e]) * g.inv_dr;
@@ -800,29 +788,16 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
             avr[e] = av_r.v[e] + s;
         }
         st4(S.vr + c, o.j, g.nz, avr);
-    }
-    // ---- shear mu and density correlations
-    {
-        float2 gbz[4];
-        ld4f2(q.G_bz + c, gbz);
-        const V4 pz = ld4cg(fprev + plane + c);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) gbz[e] = kahan_step(gbz[e], (fz12.v[4 + e] - pz.v[e]) * avz[e]);
-        st4f2(q.G_bz + c, o.j, g.nz, gbz);
-    }
-    if (i >= 1) {
-        float2 gmr[4], gbr[4];
-        ld4f2(q.G_murz + c, gmr);
-        ld4f2(q.G_br + c, gbr);
-        const V4 hmr = ld4cg(q.H_murz + c), pr = ld4cg(fprev + c);
-        const V4 fzm1 = lds4(sm.fvz, rr - 1, cc), fzm2 = lds4(sm.fvz, rr - 2, cc),
-                 fzp1 = lds4(sm.fvz, rr + 1, cc);
+        const V12 fr12 = lds12(sm.fvr, rr, cc - 4);
+        const V4 fz0 = lds4(sm.fvz, rr, cc), fzm1 = lds4(sm.fvz, rr - 1, cc),
+                 fzm2 = lds4(sm.fvz, rr - 2, cc), fzp1 = lds4(sm.fvz, rr + 1, cc);
+        const V4 Arz = lds4(sm.arz, rr, cc);
         float hmr2[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float gam =
                 d4(fr12.v[5 + e], fr12.v[4 + e], fr12.v[6 + e], fr12.v[3 + e]) * g.inv_dz +
-                d4(fz12.v[4 + e], fzm1.v[e], fzp1.v[e], fzm2.v[e]) * g.inv_dr;
+                d4(fz0.v[e], fzm1.v[e], fzp1.v[e], fzm2.v[e]) * g.inv_dr;
             gmr[e] = kahan_step(gmr[e], dt * gam * Arz.v[e]);
             hmr2[e] = hmr.v[e] + dt * gam * gam;
             gbr[e] = kahan_step(gbr[e], (fr12.v[4 + e] - pr.v[e]) * avr[e]);
@@ -836,6 +811,8 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
         const float arh = C.ar_half[i], brh = C.br_half[i];
         const V4 bzi = ld4cg(C.bz_int + o.j);
         const V4 p4 = ld4cg(S.psi[4] + c), p5 = ld4cg(S.psi[5] + c);
+        const V4 lam_o = ld4g(C.w_lam + c), mu_o = ld4g(C.w_mu + c);
+        const V4 Arr = lds4(sm.arr, rr, cc), Att = lds4(sm.att, rr, cc), Azz = lds4(sm.azz, rr, cc);
         float w4[4], w5[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -849,6 +826,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
             const float bri = C.br_int[i];
             const V4 bzh = ld4cg(C.bz_half + o.j);
             const V4 p6 = ld4cg(S.psi[6] + c), p7 = ld4cg(S.psi[7] + c);
+            const V4 mh_o = ld4g(C.w_muh + c), Arz = lds4(sm.arz, rr, cc);
             float w6[4], w7[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -906,11 +884,10 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
                     const float sg = i < 0 ? -1.f : 1.f;
                     const int cr = ir * g.P + j;
                     const V4 av = ld4cg(S.vr + cr);
+                    const V4 bv = ld4g(C.w_bvr + cr);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const float b =
-                            j + e < g.nz ? __ldg(C.bvr + (size_t)ir * g.nzg + g.z0 + j + e) : 0.f;
-                        const float w = g.dt * b * av.v[e];
+                        const float w = g.dt * bv.v[e] * av.v[e];
                         x0[e] = x1[e] = w;
                         wr[e] = w;
                     }
@@ -939,10 +916,10 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
                 if (iz < g.nr) {
                     const int cz = iz * g.P + j;
                     const V4 av = ld4cg(S.vz + cz);
+                    const V4 bv = ld4g(C.w_bvz + cz);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const float b = j + e < g.nz ? bvz_at(C, g, iz, j + e) : 0.f;
-                        const float w = g.dt * b * av.v[e];
+                        const float w = g.dt * bv.v[e] * av.v[e];
                         x2[e] = x3[e] = wz[e] = w;
                     }
                     if (pml) {

@@ -46,6 +46,47 @@ __global__ void k_setup_nodes(int nr, int nzg, const float* __restrict__ mu,
     }
 }
 
+// Window copies of the coefficients for every shot, [nshots][5][nr][P]:
+// lambda, mu, harmonic mu at trz nodes, buoyancy at v_r and v_z nodes.  The
+// window's last row follows its own rule (its v_z and trz nodes see only the
+// window's cells, as muh_at and bvz_at state); columns nz .. P-1 are zero.
+// wins[s] = (first global row, nz) of shot s; blockIdx.z = shot.
+__global__ void k_window_coefs(int nr, int nzg, int P, const int2* __restrict__ wins,
+                               const float* __restrict__ lam, const float* __restrict__ mu,
+                               const float* __restrict__ rho, const float* __restrict__ bvr,
+                               const float* __restrict__ bvz, const float* __restrict__ muh,
+                               float* out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nr || j >= P) return;
+    const int2 w = wins[blockIdx.z];
+    const size_t pl = (size_t)nr * P;
+    float* o = out + (size_t)blockIdx.z * 5 * pl + (size_t)i * P + j;
+    float v_lam = 0.f, v_mu = 0.f, v_muh = 0.f, v_bvr = 0.f, v_bvz = 0.f;
+    if (j < w.y) {
+        const size_t cg = (size_t)i * nzg + w.x + j;
+        const bool last = j == w.y - 1;
+        v_lam = lam[cg];
+        v_mu = mu[cg];
+        v_bvz = last ? 1.f / rho[cg] : bvz[cg];
+        if (i >= 1) {
+            v_bvr = bvr[cg];
+            if (last) {
+                const float a = mu[cg - nzg], b = mu[cg];
+                v_muh = (a <= 0.f || b <= 0.f) ? 0.f : 2.f / (1.f / a + 1.f / b);
+            } else {
+                v_muh = muh[cg];
+            }
+        }
+    }
+    o[0] = v_lam;
+    o[pl] = v_mu;
+    o[2 * pl] = v_muh;
+    o[3 * pl] = v_bvr;
+    o[4 * pl] = v_bvz;
+}
+
 // inversion mask: formation cell (vs > 0), outside the radial C-PML, and
 // inside the axial interior of at least one shot window (colcov[j] != 0)
 __global__ void k_setup_mask(int nr, int nzg, int npml_r, const float* __restrict__ vs,

@@ -56,6 +56,8 @@ struct bh_model {
     int* d_recmap = nullptr;    // per shot nz
     float* d_fwd = nullptr;     // per shot kFwdPlanes planes
     float* d_adj = nullptr;     // per shot kAdjPlanes planes
+    float* d_wcoef = nullptr;   // per shot 5 coefficient planes of its window
+    int2* d_wins = nullptr;     // per shot (first global row, nz)
     float* d_hist = nullptr;    // per shot (L + 1) x 2 planes
     void* d_snap = nullptr;     // per slot, all shots' kFwdPlanes planes (fp32 or 16-bit)
     float* d_snap_max = nullptr;  // per slot, max |x| of every plane (16-bit snapshots)
@@ -135,7 +137,7 @@ void free_model(bh_model* m)
     void* bufs[] = {m->d_lam,   m->d_mu,     m->d_rho,   m->d_bvr,    m->d_bvz,    m->d_muh,
                     m->d_mask,  m->d_colcov, m->d_rprof, m->d_zprof,  m->d_recmap, m->d_fwd,
                     m->d_adj,   m->d_hist,   m->d_snap,  m->d_snap_max, m->d_tiles,  m->d_Hg,
-                    m->d_scal,  m->d_bar};
+                    m->d_scal,  m->d_bar,    m->d_wcoef, m->d_wins};
     for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     delete m;
@@ -234,6 +236,12 @@ bh_status rebuild_coefficients(bh_model* m)
     const int nr = m->grid.nr, nzg = m->nzg;
     k_setup_nodes<<<grid2d(nr, nzg), block2d(), 0, m->stream>>>(nr, nzg, m->d_mu, m->d_rho,
                                                                 m->d_bvr, m->d_bvz, m->d_muh);
+    BH_LAUNCH(m);
+    dim3 gw = grid2d(nr, m->P);
+    gw.z = (unsigned)m->nshots;
+    k_window_coefs<<<gw, block2d(), 0, m->stream>>>(nr, nzg, m->P, m->d_wins, m->d_lam, m->d_mu,
+                                                    m->d_rho, m->d_bvr, m->d_bvz, m->d_muh,
+                                                    m->d_wcoef);
     BH_LAUNCH(m);
     return BH_OK;
 }
@@ -381,6 +389,12 @@ bh_status setup_shots(bh_model* m)
         C.bz_int = zp + m->P;
         C.az_half = zp + 2 * m->P;
         C.bz_half = zp + 3 * m->P;
+        const float* wc = m->d_wcoef + (size_t)s * 5 * pl;
+        C.w_lam = wc;
+        C.w_mu = wc + pl;
+        C.w_muh = wc + 2 * pl;
+        C.w_bvr = wc + 3 * pl;
+        C.w_bvz = wc + 4 * pl;
         float* f = m->d_fwd + (size_t)s * kFwdPlanes * pl;
         float* a = m->d_adj + (size_t)s * kAdjPlanes * pl;
         StateK* views[3] = {&k.Sf, &k.Sa[0], &k.Sa[1]};
@@ -806,6 +820,8 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_rprof, 6 * (size_t)nr));
     CK(dalloc(&m->d_fwd, (size_t)nshots * kFwdPlanes * pl));
     CK(dalloc(&m->d_adj, (size_t)nshots * kAdjPlanes * pl));
+    CK(dalloc(&m->d_wcoef, (size_t)nshots * 5 * pl));
+    CK(dalloc(&m->d_wins, (size_t)nshots));
     CK(dalloc(&m->d_hist, (size_t)nshots * (m->L + 1) * 2 * pl));
     CK(dalloc((char**)&m->d_snap,
               (size_t)m->nsnap * nshots * kFwdPlanes * pl * (m->snap_prec ? 2 : 4)));
@@ -844,6 +860,10 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         for (int j = g.npml_z; j < d.nz - g.npml_z; ++j) colcov[d.z_offset + j] = 1;
     }
     CK(cudaMemcpyAsync(m->d_colcov, colcov.data(), nz_global, cudaMemcpyHostToDevice,
+                       m->stream));
+    std::vector<int2> wins(nshots);
+    for (int s = 0; s < nshots; ++s) wins[s] = make_int2(shots[s].z_offset, shots[s].nz);
+    CK(cudaMemcpyAsync(m->d_wins, wins.data(), nshots * sizeof(int2), cudaMemcpyHostToDevice,
                        m->stream));
     CK(cudaStreamSynchronize(m->stream));
 #undef CK
@@ -1087,7 +1107,8 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "snapshot_precision") *value = m->snap_prec;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
-                     (kFwdPlanes + kAdjPlanes + 2.0 * (m->L + 1) + (double)m->nsnap * kFwdPlanes) +
+                     (kFwdPlanes + kAdjPlanes + 5.0 + 2.0 * (m->L + 1)) +
+                 (double)pl * (m->snap_prec ? 2 : 4) * m->nshots * m->nsnap * kFwdPlanes +
                  (double)ng * (6 * sizeof(float) + 1 + 2 * sizeof(double));
     else return fail(m, BH_ERR_INVALID_ARG, "unknown key " + k);
     return BH_OK;
