@@ -205,42 +205,61 @@ __device__ __forceinline__ void ld4f2(const float2* p, float2 (&x)[4])
     x[3] = make_float2(b.z, b.w);
 }
 
-// Stage rows i0-2 .. i0+17, columns j0-4 .. j0+35 of a window field.
-// EVEN: half-r field (cells, v_z), mirror f[-1-k] = f[k].  ODD: integer-r
-// field (v_r, trz), f[-k] = -f[k], f[0] = 0.  ABS: integer-r coefficient
-// (harmonic mu), f[-k] = f[k].  Zero beyond nr and outside 0 <= z < nz.
+// Staging: rows i0-2 .. i0+17, columns j0-4 .. j0+35 of a window field go
+// into a Tile.  EVEN: half-r field (cells, v_z), mirror f[-1-k] = f[k].
+// ODD: integer-r field (v_r, trz), f[-k] = -f[k], f[0] = 0.  ABS: integer-r
+// coefficient (harmonic mu), f[-k] = f[k], zero on the axis.  Zero beyond nr
+// and outside 0 <= z < nz.  The geometry of a staged float4 (a Slot) is the
+// same for every field of a tile, so it is computed once and every field's
+// load goes through it.
 enum { EVEN = 0, ODD = 1, ABS = 2 };
-template <int KIND>
-__device__ __forceinline__ void stage(Tile& s, const float* __restrict__ f, int i0, int j0,
-                                      const WinK& g)
+
+struct Slot {
+    int rr, cq;  // staged row, first staged column
+    int off_e;   // plane offset of the even-mirrored source row, -1: zero
+    int off_o;   // plane offset of the odd/abs-mirrored source row, -1: zero
+    int zlim;    // source floats inside 0 <= z < nz (4: all of them)
+    bool neg;    // the row is a mirror image (odd fields change sign)
+};
+
+__device__ __forceinline__ int tid_of() { return threadIdx.y * 8 + threadIdx.x; }
+
+__device__ __forceinline__ Slot slot_of(int it, int i0, int j0, const WinK& g)
 {
-    const int tid = threadIdx.y * 8 + threadIdx.x;
-    for (int it = tid; it < kSR * kQ; it += kThreads) {
-        const int rr = it / kQ, q = it - rr * kQ;
-        int i = i0 - kH + rr;
-        float sg = 1.f;
-        if (KIND == EVEN) {
-            if (i < 0) i = -1 - i;
-        } else if (KIND == ODD) {
-            if (i < 0) { i = -i; sg = -1.f; }
-            if (i == 0) sg = 0.f;
-        } else {
-            if (i < 0) i = -i;
+    Slot s;
+    s.rr = it / kQ;
+    s.cq = 4 * (it - s.rr * kQ);
+    const int i = i0 - kH + s.rr, j = j0 - 4 + s.cq;
+    const bool zin = j >= 0 && j < g.nz;
+    s.zlim = zin ? min(4, g.nz - j) : 0;
+    const int ie = i < 0 ? -1 - i : i;
+    const int io = i < 0 ? -i : i;
+    s.neg = i < 0;
+    s.off_e = (zin && ie < g.nr) ? ie * g.P + j : -1;
+    s.off_o = (zin && io >= 1 && io < g.nr) ? io * g.P + j : -1;
+    return s;
+}
+
+template <int KIND>
+__device__ __forceinline__ void stage_slot(Tile& t, const float* __restrict__ f, const Slot& s)
+{
+    const int off = KIND == EVEN ? s.off_e : s.off_o;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (off >= 0) {
+        v = __ldcg(reinterpret_cast<const float4*>(f + off));
+        if (s.zlim < 4) {
+            if (s.zlim < 2) v.y = 0.f;
+            if (s.zlim < 3) v.z = 0.f;
+            v.w = 0.f;
         }
-        const int j = j0 - 4 + 4 * q;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < g.nr && sg != 0.f && j >= 0 && j < g.nz) {
-            v = __ldcg(reinterpret_cast<const float4*>(f + i * g.P + j));
-            if (j + 1 >= g.nz) v.y = 0.f;
-            if (j + 2 >= g.nz) v.z = 0.f;
-            if (j + 3 >= g.nz) v.w = 0.f;
-            v.x *= sg;
-            v.y *= sg;
-            v.z *= sg;
-            v.w *= sg;
+        if (KIND == ODD && s.neg) {
+            v.x = -v.x;
+            v.y = -v.y;
+            v.z = -v.z;
+            v.w = -v.w;
         }
-        *reinterpret_cast<float4*>(&s[rr][4 * q]) = v;
     }
+    *reinterpret_cast<float4*>(&t[s.rr][s.cq]) = v;
 }
 
 // own-node index helpers: thread (x = column group, y = row)
@@ -297,10 +316,13 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
         }
     }
     __syncthreads();
-    stage<EVEN>(s_rr, S.trr, i0, j0, g);
-    stage<EVEN>(s_tt, S.ttt, i0, j0, g);
-    stage<ODD>(s_rz, S.trz, i0, j0, g);
-    stage<EVEN>(s_zz, S.tzz, i0, j0, g);
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_slot<EVEN>(s_rr, S.trr, sl);
+        stage_slot<EVEN>(s_tt, S.ttt, sl);
+        stage_slot<ODD>(s_rz, S.trz, sl);
+        stage_slot<EVEN>(s_zz, S.tzz, sl);
+    }
     __syncthreads();
     if (!o.live) return;
     // layer tiles only: memories and profiles (kept out of the prefetch to
@@ -310,14 +332,14 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
         brh = C.br_half[o.i];
         azh = ld4cg(C.az_half + o.j);
         bzh = ld4cg(C.bz_half + o.j);
-        if (arh != 0.f) q2 = ld4cg(S.psi[2] + o.c);
+        q2 = ld4cg(S.psi[2] + o.c);
         q3 = ld4cg(S.psi[3] + o.c);
         if (o.i >= 1) {
             ari = C.ar_int[o.i];
             bri = C.br_int[o.i];
             azi = ld4cg(C.az_int + o.j);
             bzi = ld4cg(C.bz_int + o.j);
-            if (ari != 0.f) q0 = ld4cg(S.psi[0] + o.c);
+            q0 = ld4cg(S.psi[0] + o.c);
             q1 = ld4cg(S.psi[1] + o.c);
         }
     }
@@ -411,8 +433,11 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         mu = ld4g(C.w_mu + o.c);
     }
     __syncthreads();
-    stage<ODD>(s_vr, S.vr, i0, j0, g);
-    stage<EVEN>(s_vz, S.vz, i0, j0, g);
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_slot<ODD>(s_vr, S.vr, sl);
+        stage_slot<EVEN>(s_vz, S.vz, sl);
+    }
     __syncthreads();
     if (!o.live) return;
     const int rr = o.rr, cc = o.cc;
@@ -430,7 +455,7 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
             brh = C.br_half[o.i];
             azi = ld4cg(C.az_int + o.j);
             bzi = ld4cg(C.bz_int + o.j);
-            if (arh != 0.f) q4 = ld4cg(S.psi[4] + o.c);
+            q4 = ld4cg(S.psi[4] + o.c);
             q5 = ld4cg(S.psi[5] + o.c);
         }
         const V12 vr12 = lds12(s_vr, rr, cc - 4), vz12 = lds12(s_vz, rr, cc - 4);
@@ -488,7 +513,7 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
             azh = ld4cg(C.az_half + o.j);
             bzh = ld4cg(C.bz_half + o.j);
             q6 = ld4cg(S.psi[6] + o.c);
-            if (ari != 0.f) q7 = ld4cg(S.psi[7] + o.c);
+            q7 = ld4cg(S.psi[7] + o.c);
         }
         const V12 vr12 = lds12(s_vr, rr, cc - 4);
         const V4 vz0 = lds4(s_vz, rr, cc), vzm1 = lds4(s_vz, rr - 1, cc),
@@ -640,15 +665,18 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     const bool pml = flags & TILE_PML;
     const int rr = o.rr, cc = o.cc, i = o.i, c = o.c;
     __syncthreads();
-    stage<EVEN>(sm.arr, S.trr, i0, j0, g);
-    stage<EVEN>(sm.att, S.ttt, i0, j0, g);
-    stage<EVEN>(sm.azz, S.tzz, i0, j0, g);
-    stage<ODD>(sm.arz, S.trz, i0, j0, g);
-    stage<ODD>(sm.fvr, fcur, i0, j0, g);
-    stage<EVEN>(sm.fvz, fcur + plane, i0, j0, g);
-    stage<EVEN>(sm.x4, C.w_lam, i0, j0, g);
-    stage<EVEN>(sm.ytt, C.w_mu, i0, j0, g);
-    stage<ABS>(sm.x5, C.w_muh, i0, j0, g);
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_slot<EVEN>(sm.arr, S.trr, sl);
+        stage_slot<EVEN>(sm.att, S.ttt, sl);
+        stage_slot<EVEN>(sm.azz, S.tzz, sl);
+        stage_slot<ODD>(sm.arz, S.trz, sl);
+        stage_slot<ODD>(sm.fvr, fcur, sl);
+        stage_slot<EVEN>(sm.fvz, fcur + plane, sl);
+        stage_slot<EVEN>(sm.x4, C.w_lam, sl);
+        stage_slot<EVEN>(sm.ytt, C.w_mu, sl);
+        stage_slot<ABS>(sm.x5, C.w_muh, sl);
+    }
     __syncthreads();
     // own accumulators of the lambda and normal-mu correlations: issued
     // here so that their latency overlaps the coefficient build
@@ -682,8 +710,8 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
             }
             if (pml && ii < g.nr && j >= 0 && j < g.nz) {
                 const float arh = C.ar_half[ic], brh = C.br_half[ic];
+                const V4 p = ld4cg(S.psi[4] + ic * g.P + j);
                 if (arh != 0.f) {
-                    const V4 p = ld4cg(S.psi[4] + ic * g.P + j);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) x4[e] = x4[e] + arh * (x4[e] + brh * p.v[e]);
                 }
@@ -699,8 +727,8 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
                     for (int e = 0; e < 4; ++e)
                         if (azh.v[e] != 0.f) x6[e] = x6[e] + azh.v[e] * (x6[e] + bzh.v[e] * p6.v[e]);
                     const float ari = C.ar_int[ii], bri = C.br_int[ii];
+                    const V4 p7 = ld4cg(S.psi[7] + ii * g.P + j);
                     if (ari != 0.f) {
-                        const V4 p7 = ld4cg(S.psi[7] + ii * g.P + j);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) x7[e] = x7[e] + ari * (x7[e] + bri * p7.v[e]);
                     }
@@ -893,8 +921,8 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
                     }
                     if (pml) {
                         const float ari = C.ar_int[ir], bri = C.br_int[ir];
+                        const V4 p = ld4cg(S.psi[0] + cr);
                         if (ari != 0.f) {
-                            const V4 p = ld4cg(S.psi[0] + cr);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) x0[e] = wr[e] + ari * (wr[e] + bri * p.v[e]);
                         }
@@ -924,8 +952,8 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
                     }
                     if (pml) {
                         const float arh = C.ar_half[iz], brh = C.br_half[iz];
+                        const V4 p = ld4cg(S.psi[2] + cz);
                         if (arh != 0.f) {
-                            const V4 p = ld4cg(S.psi[2] + cz);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) x2[e] = wz[e] + arh * (wz[e] + brh * p.v[e]);
                         }
