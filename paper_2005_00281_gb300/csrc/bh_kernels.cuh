@@ -240,26 +240,48 @@ __device__ __forceinline__ Slot slot_of(int it, int i0, int j0, const WinK& g)
     return s;
 }
 
-template <int KIND>
-__device__ __forceinline__ void stage_slot(Tile& t, const float* __restrict__ f, const Slot& s)
+// Asynchronous staging (cp.async, 16 bytes per slot, through L2 only): the
+// copy lands in the tile without passing through registers and zero-fills
+// whatever lies outside the source (src-size below 16).  Odd fields then
+// need their mirrored rows negated (negate_slot) after the wait.  POS: an
+// integer-r field read only at rows i >= 1, not mirrored (zero elsewhere).
+enum { POS = 3 };
+
+__device__ __forceinline__ unsigned smem_addr(const void* p)
 {
-    const int off = KIND == EVEN ? s.off_e : s.off_o;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (off >= 0) {
-        v = __ldcg(reinterpret_cast<const float4*>(f + off));
-        if (s.zlim < 4) {
-            if (s.zlim < 2) v.y = 0.f;
-            if (s.zlim < 3) v.z = 0.f;
-            v.w = 0.f;
-        }
-        if (KIND == ODD && s.neg) {
-            v.x = -v.x;
-            v.y = -v.y;
-            v.z = -v.z;
-            v.w = -v.w;
-        }
-    }
-    *reinterpret_cast<float4*>(&t[s.rr][s.cq]) = v;
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+template <int KIND>
+__device__ __forceinline__ void stage_async(Tile& t, const float* __restrict__ f, const Slot& s)
+{
+    int off = KIND == EVEN ? s.off_e : s.off_o;
+    if (KIND == POS && s.neg) off = -1;
+    const float* src = f + (off >= 0 ? off : 0);
+    const unsigned bytes = off >= 0 ? 4u * (unsigned)s.zlim : 0u;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(&t[s.rr][s.cq])),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+
+// this thread's copies have landed (other threads' need a __syncthreads)
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void negate_slot(Tile& t, const Slot& s)
+{
+    float4* p = reinterpret_cast<float4*>(&t[s.rr][s.cq]);
+    float4 v = *p;
+    v.x = -v.x;
+    v.y = -v.y;
+    v.z = -v.z;
+    v.w = -v.w;
+    *p = v;
+}
+
+// slot of the staged region that is one of the tile's own float4 groups
+__device__ __forceinline__ bool own_slot(const Slot& s)
+{
+    return s.rr >= kH && s.rr < kH + kTR && s.cq >= 4 && s.cq < 4 + kTZ;
 }
 
 // own-node index helpers: thread (x = column group, y = row)
@@ -291,7 +313,7 @@ struct SrcRecK {
     int nt;
 };
 
-struct FwdSmem {
+struct __align__(16) FwdSmem {
     Tile a, b, c, d;
 };
 
@@ -307,6 +329,15 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     V4 vr0{}, vz0{}, br{}, bz{}, q0{}, q1{}, q2{}, q3{};
     float ari = 0.f, bri = 0.f, arh = 0.f, brh = 0.f;
     V4 azi{}, bzi{}, azh{}, bzh{};
+    __syncthreads();
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_async<EVEN>(s_rr, S.trr, sl);
+        stage_async<EVEN>(s_tt, S.ttt, sl);
+        stage_async<ODD>(s_rz, S.trz, sl);
+        stage_async<EVEN>(s_zz, S.tzz, sl);
+    }
+    // own-node inputs, in flight together with the copies
     if (o.live) {
         vz0 = ld4cg(S.vz + o.c);
         bz = ld4g(C.w_bvz + o.c);
@@ -314,33 +345,35 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
             vr0 = ld4cg(S.vr + o.c);
             br = ld4g(C.w_bvr + o.c);
         }
+        if (pml) {
+            q2 = ld4cg(S.psi[2] + o.c);
+            q3 = ld4cg(S.psi[3] + o.c);
+            if (o.i >= 1) {
+                q0 = ld4cg(S.psi[0] + o.c);
+                q1 = ld4cg(S.psi[1] + o.c);
+            }
+        }
     }
-    __syncthreads();
-    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
-        const Slot sl = slot_of(it, i0, j0, g);
-        stage_slot<EVEN>(s_rr, S.trr, sl);
-        stage_slot<EVEN>(s_tt, S.ttt, sl);
-        stage_slot<ODD>(s_rz, S.trz, sl);
-        stage_slot<EVEN>(s_zz, S.tzz, sl);
+    async_wait_all();
+    if (i0 < kH) {
+        for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+            const Slot sl = slot_of(it, i0, j0, g);
+            if (sl.neg && sl.off_o >= 0) negate_slot(s_rz, sl);
+        }
     }
     __syncthreads();
     if (!o.live) return;
-    // layer tiles only: memories and profiles (kept out of the prefetch to
-    // spare registers)
+    // C-PML profiles: small read-only arrays, L1 hits after the first step
     if (pml) {
-        arh = C.ar_half[o.i];
-        brh = C.br_half[o.i];
-        azh = ld4cg(C.az_half + o.j);
-        bzh = ld4cg(C.bz_half + o.j);
-        q2 = ld4cg(S.psi[2] + o.c);
-        q3 = ld4cg(S.psi[3] + o.c);
+        arh = __ldg(C.ar_half + o.i);
+        brh = __ldg(C.br_half + o.i);
+        azh = ld4g(C.az_half + o.j);
+        bzh = ld4g(C.bz_half + o.j);
         if (o.i >= 1) {
-            ari = C.ar_int[o.i];
-            bri = C.br_int[o.i];
-            azi = ld4cg(C.az_int + o.j);
-            bzi = ld4cg(C.bz_int + o.j);
-            q0 = ld4cg(S.psi[0] + o.c);
-            q1 = ld4cg(S.psi[1] + o.c);
+            ari = __ldg(C.ar_int + o.i);
+            bri = __ldg(C.br_int + o.i);
+            azi = ld4g(C.az_int + o.j);
+            bzi = ld4g(C.bz_int + o.j);
         }
     }
     const int rr = o.rr, cc = o.cc;
@@ -350,7 +383,7 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
         const V4 rm2 = lds4(s_rr, rr - 2, cc), rm1 = lds4(s_rr, rr - 1, cc);
         const V4 r0 = lds4(s_rr, rr, cc), rp1 = lds4(s_rr, rr + 1, cc);
         const V4 tm1 = lds4(s_tt, rr - 1, cc), t0 = lds4(s_tt, rr, cc);
-        const float inv_r = C.inv_r_int[o.i];
+        const float inv_r = __ldg(C.inv_r_int + o.i);
         float vr[4], w0[4], w1[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -380,7 +413,7 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     {
         const V12 zz12 = lds12(s_zz, rr, cc - 4);
         const V4 rzm1 = lds4(s_rz, rr - 1, cc), rzp2 = lds4(s_rz, rr + 2, cc);
-        const float inv_r = C.inv_r_half[o.i];
+        const float inv_r = __ldg(C.inv_r_half + o.i);
         float vz[4], w2[4], w3[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -424,43 +457,50 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     Tile &s_vr = sm.a, &s_vz = sm.b;
     const Own o = own_of(g, i0, j0);
     const bool pml = flags & TILE_PML;
-    V4 t_rr{}, t_tt{}, t_zz{}, lm{}, mu{};
+    __syncthreads();
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_async<ODD>(s_vr, S.vr, sl);
+        stage_async<EVEN>(s_vz, S.vz, sl);
+    }
+    V4 t_rr{}, t_tt{}, t_zz{}, lm{}, mu{}, t_rz{}, mh{};
+    float arh = 0.f, brh = 0.f;
+    V4 azi{}, bzi{}, q4{}, q5{};
     if (o.live) {
         t_rr = ld4cg(S.trr + o.c);
         t_tt = ld4cg(S.ttt + o.c);
         t_zz = ld4cg(S.tzz + o.c);
         lm = ld4g(C.w_lam + o.c);
         mu = ld4g(C.w_mu + o.c);
+        if (o.i >= 1) {
+            t_rz = ld4cg(S.trz + o.c);
+            mh = ld4g(C.w_muh + o.c);
+        }
+        if (pml) {
+            q4 = ld4cg(S.psi[4] + o.c);
+            q5 = ld4cg(S.psi[5] + o.c);
+        }
     }
-    __syncthreads();
-    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
-        const Slot sl = slot_of(it, i0, j0, g);
-        stage_slot<ODD>(s_vr, S.vr, sl);
-        stage_slot<EVEN>(s_vz, S.vz, sl);
+    async_wait_all();
+    if (i0 < kH) {
+        for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+            const Slot sl = slot_of(it, i0, j0, g);
+            if (sl.neg && sl.off_o >= 0) negate_slot(s_vr, sl);
+        }
     }
     __syncthreads();
     if (!o.live) return;
     const int rr = o.rr, cc = o.cc;
-    // shear inputs: issued now, used after the normal stresses
-    V4 t_rz{}, mh{};
-    if (o.i >= 1) {
-        t_rz = ld4cg(S.trz + o.c);
-        mh = ld4g(C.w_muh + o.c);
-    }
     {
-        float arh = 0.f, brh = 0.f;
-        V4 azi{}, bzi{}, q4{}, q5{};
         if (pml) {
-            arh = C.ar_half[o.i];
-            brh = C.br_half[o.i];
-            azi = ld4cg(C.az_int + o.j);
-            bzi = ld4cg(C.bz_int + o.j);
-            q4 = ld4cg(S.psi[4] + o.c);
-            q5 = ld4cg(S.psi[5] + o.c);
+            arh = __ldg(C.ar_half + o.i);
+            brh = __ldg(C.br_half + o.i);
+            azi = ld4g(C.az_int + o.j);
+            bzi = ld4g(C.bz_int + o.j);
         }
         const V12 vr12 = lds12(s_vr, rr, cc - 4), vz12 = lds12(s_vz, rr, cc - 4);
         const V4 vrp1 = lds4(s_vr, rr + 1, cc);
-        const float inv_rh = C.inv_r_half[o.i];
+        const float inv_rh = __ldg(C.inv_r_half + o.i);
         float trr[4], ttt[4], tzz[4], w4[4], w5[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -508,10 +548,10 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         float ari = 0.f, bri = 0.f;
         V4 azh{}, bzh{}, q6{}, q7{};
         if (pml) {
-            ari = C.ar_int[o.i];
-            bri = C.br_int[o.i];
-            azh = ld4cg(C.az_half + o.j);
-            bzh = ld4cg(C.bz_half + o.j);
+            ari = __ldg(C.ar_int + o.i);
+            bri = __ldg(C.br_int + o.i);
+            azh = ld4g(C.az_half + o.j);
+            bzh = ld4g(C.bz_half + o.j);
             q6 = ld4cg(S.psi[6] + o.c);
             q7 = ld4cg(S.psi[7] + o.c);
         }
@@ -631,13 +671,16 @@ struct AdjK {
     float *H_lam, *H_munn, *H_murz;                 // [nr*P]
 };
 
-struct AdjSmem {
-    // staged adjoint stresses and forward v^{n+1/2}; lambda, mu, mu_h are
-    // staged into x4, ytt, x5 and replaced there by the coefficients of the
-    // transposed stencils: on D_r v_r (x4), v_r/r (ytt), D_z v_z (x5) at
-    // cells, on D_z v_r (x6) and D_r v_z (x7) at shear nodes.  The velocity
-    // step reuses the first six tiles.
-    Tile arr, att, azz, arz, fvr, fvz, x4, ytt, x5, x6, x7;
+struct __align__(16) AdjSmem {
+    // Stress step: staged adjoint stresses and forward v^{n+1/2}; lambda,
+    // mu, mu_h are staged into x4, ytt, x5 and replaced there by the
+    // coefficients of the transposed stencils: on D_r v_r (x4), v_r/r (ytt),
+    // D_z v_z (x5) at cells, on D_z v_r (x6) and D_r v_z (x7) at shear
+    // nodes; C-PML tiles stage the adjoint memories 4, 5 into p4, p5 and
+    // 6, 7 into x6, x7.  Velocity step: adjoint velocities into arr, att,
+    // buoyancies into x4, x5, memories 0..3 into azz, arz, fvr, fvz, each
+    // replaced in place by W = dt b Av and the four coefficients.
+    Tile arr, att, azz, arz, fvr, fvz, x4, ytt, x5, x6, x7, p4, p5;
 };
 
 __device__ __forceinline__ float2 kahan_step(float2 s, float x)
@@ -667,19 +710,24 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     __syncthreads();
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const Slot sl = slot_of(it, i0, j0, g);
-        stage_slot<EVEN>(sm.arr, S.trr, sl);
-        stage_slot<EVEN>(sm.att, S.ttt, sl);
-        stage_slot<EVEN>(sm.azz, S.tzz, sl);
-        stage_slot<ODD>(sm.arz, S.trz, sl);
-        stage_slot<ODD>(sm.fvr, fcur, sl);
-        stage_slot<EVEN>(sm.fvz, fcur + plane, sl);
-        stage_slot<EVEN>(sm.x4, C.w_lam, sl);
-        stage_slot<EVEN>(sm.ytt, C.w_mu, sl);
-        stage_slot<ABS>(sm.x5, C.w_muh, sl);
+        stage_async<EVEN>(sm.arr, S.trr, sl);
+        stage_async<EVEN>(sm.att, S.ttt, sl);
+        stage_async<EVEN>(sm.azz, S.tzz, sl);
+        stage_async<ODD>(sm.arz, S.trz, sl);
+        stage_async<ODD>(sm.fvr, fcur, sl);
+        stage_async<EVEN>(sm.fvz, fcur + plane, sl);
+        stage_async<EVEN>(sm.x4, C.w_lam, sl);
+        stage_async<EVEN>(sm.ytt, C.w_mu, sl);
+        stage_async<ABS>(sm.x5, C.w_muh, sl);
+        if (pml) {
+            stage_async<EVEN>(sm.p4, S.psi[4], sl);
+            stage_async<EVEN>(sm.p5, S.psi[5], sl);
+            stage_async<POS>(sm.x6, S.psi[6], sl);
+            stage_async<POS>(sm.x7, S.psi[7], sl);
+        }
     }
-    __syncthreads();
-    // own accumulators of the lambda and normal-mu correlations: issued
-    // here so that their latency overlaps the coefficient build
+    // own accumulators of the lambda and normal-mu correlations, in flight
+    // together with the copies
     float2 gl[4], gm[4];
     V4 hl{}, hm{};
     if (o.live) {
@@ -688,75 +736,25 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
         hl = ld4cg(q.H_lam + c);
         hm = ld4cg(q.H_munn + c);
     }
-    // transposed-stencil coefficients over the staged region, in place
-    {
-        const int tid = threadIdx.y * 8 + threadIdx.x;
-        for (int it = tid; it < kSR * kQ; it += kThreads) {
-            const int r2 = it / kQ, q2 = it - r2 * kQ;
-            const int ii = i0 - kH + r2, j = j0 - 4 + 4 * q2, c2 = 4 * q2;
-            const int ic = ii < 0 ? -1 - ii : ii;
-            const V4 lm = lds4(sm.x4, r2, c2), mu = lds4(sm.ytt, r2, c2), mh = lds4(sm.x5, r2, c2);
-            const V4 ar = lds4(sm.arr, r2, c2), at = lds4(sm.att, r2, c2), az = lds4(sm.azz, r2, c2);
-            const V4 arz = lds4(sm.arz, r2, c2);
-            float x4[4], ytt[4], x5[4], x6[4], x7[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float lam = lm.v[e], l2m = lam + 2.f * mu.v[e];
-                x4[e] = dt * (l2m * ar.v[e] + lam * (at.v[e] + az.v[e]));
-                ytt[e] = dt * (l2m * at.v[e] + lam * (ar.v[e] + az.v[e]));
-                x5[e] = dt * (l2m * az.v[e] + lam * (ar.v[e] + at.v[e]));
-                // shear node: the staged values are already odd about the axis
-                x6[e] = x7[e] = dt * mh.v[e] * arz.v[e];
+    async_wait_all();
+    if (i0 < kH) {
+        for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+            const Slot sl = slot_of(it, i0, j0, g);
+            if (sl.neg && sl.off_o >= 0) {
+                negate_slot(sm.arz, sl);
+                negate_slot(sm.fvr, sl);
             }
-            if (pml && ii < g.nr && j >= 0 && j < g.nz) {
-                const float arh = C.ar_half[ic], brh = C.br_half[ic];
-                const V4 p = ld4cg(S.psi[4] + ic * g.P + j);
-                if (arh != 0.f) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) x4[e] = x4[e] + arh * (x4[e] + brh * p.v[e]);
-                }
-                const V4 azi = ld4cg(C.az_int + j), bzi = ld4cg(C.bz_int + j);
-                const V4 p5 = ld4cg(S.psi[5] + ic * g.P + j);
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (azi.v[e] != 0.f) x5[e] = x5[e] + azi.v[e] * (x5[e] + bzi.v[e] * p5.v[e]);
-                if (ii >= 1) {
-                    const V4 azh = ld4cg(C.az_half + j), bzh = ld4cg(C.bz_half + j);
-                    const V4 p6 = ld4cg(S.psi[6] + ii * g.P + j);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (azh.v[e] != 0.f) x6[e] = x6[e] + azh.v[e] * (x6[e] + bzh.v[e] * p6.v[e]);
-                    const float ari = C.ar_int[ii], bri = C.br_int[ii];
-                    const V4 p7 = ld4cg(S.psi[7] + ii * g.P + j);
-                    if (ari != 0.f) {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) x7[e] = x7[e] + ari * (x7[e] + bri * p7.v[e]);
-                    }
-                }
-            }
-            *reinterpret_cast<float4*>(&sm.x4[r2][c2]) = make_float4(x4[0], x4[1], x4[2], x4[3]);
-            *reinterpret_cast<float4*>(&sm.ytt[r2][c2]) = make_float4(ytt[0], ytt[1], ytt[2], ytt[3]);
-            *reinterpret_cast<float4*>(&sm.x5[r2][c2]) = make_float4(x5[0], x5[1], x5[2], x5[3]);
-            *reinterpret_cast<float4*>(&sm.x6[r2][c2]) = make_float4(x6[0], x6[1], x6[2], x6[3]);
-            *reinterpret_cast<float4*>(&sm.x7[r2][c2]) = make_float4(x7[0], x7[1], x7[2], x7[3]);
         }
     }
     __syncthreads();
-    if (!o.live) return;
-
-    // ---- remaining own-node inputs, issued before any store of this tile
-    float2 gbz[4];
-    const V4 av_z = ld4cg(S.vz + c);
-    ld4f2(q.G_bz + c, gbz);
-    const V4 pz = ld4cg(fprev + plane + c);
 
     // ---- lambda and normal mu correlations, pseudo-Hessian
-    {
+    if (o.live) {
         const V12 fr12 = lds12(sm.fvr, rr, cc - 4), fz12 = lds12(sm.fvz, rr, cc - 4);
         const V4 frm1 = lds4(sm.fvr, rr - 1, cc), frp1 = lds4(sm.fvr, rr + 1, cc),
                  frp2 = lds4(sm.fvr, rr + 2, cc);
         const V4 Arr = lds4(sm.arr, rr, cc), Att = lds4(sm.att, rr, cc), Azz = lds4(sm.azz, rr, cc);
-        const float inv_rh = C.inv_r_half[i];
+        const float inv_rh = __ldg(C.inv_r_half + i);
         float hl2[4], hm2[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -774,13 +772,96 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
         st4(q.H_lam + c, o.j, g.nz, hl2);
         st4(q.H_munn + c, o.j, g.nz, hm2);
     }
-    float2 gmr[4];
+    // own inputs of the transposes and the remaining correlations: in flight
+    // during the coefficient pass
+    float2 gbz[4];
+    V4 av_z{}, pz{};
+    if (o.live) {
+        av_z = ld4cg(S.vz + c);
+        ld4f2(q.G_bz + c, gbz);
+        pz = ld4cg(fprev + plane + c);
+    }
+    // transposed-stencil coefficients, in place over this thread's slots;
+    // own C-PML nodes also update their adjoint memories here
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        const int r2 = sl.rr, c2 = sl.cq;
+        const int ii = i0 - kH + r2, j = j0 - 4 + c2;
+        const V4 lm = lds4(sm.x4, r2, c2), mu = lds4(sm.ytt, r2, c2), mh = lds4(sm.x5, r2, c2);
+        const V4 ar = lds4(sm.arr, r2, c2), at = lds4(sm.att, r2, c2), az = lds4(sm.azz, r2, c2);
+        const V4 arz = lds4(sm.arz, r2, c2);
+        float x4[4], ytt[4], x5[4], x6[4], x7[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float lam = lm.v[e], l2m = lam + 2.f * mu.v[e];
+            x4[e] = dt * (l2m * ar.v[e] + lam * (at.v[e] + az.v[e]));
+            ytt[e] = dt * (l2m * at.v[e] + lam * (ar.v[e] + az.v[e]));
+            x5[e] = dt * (l2m * az.v[e] + lam * (ar.v[e] + at.v[e]));
+            // shear node: the staged values are already odd about the axis
+            x6[e] = x7[e] = dt * mh.v[e] * arz.v[e];
+        }
+        if (pml && ii < g.nr && j >= 0 && j < g.nz) {
+            const int ic = ii < 0 ? -1 - ii : ii;
+            const bool own = own_slot(sl);
+            const float arh = __ldg(C.ar_half + ic), brh = __ldg(C.br_half + ic);
+            const V4 p4 = lds4(sm.p4, r2, c2), p5 = lds4(sm.p5, r2, c2);
+            const V4 azi = ld4g(C.az_int + j), bzi = ld4g(C.bz_int + j);
+            if (own) {
+                float w4[4], w5[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    w4[e] = x4[e] + brh * p4.v[e];
+                    w5[e] = x5[e] + bzi.v[e] * p5.v[e];
+                }
+                if (arh != 0.f) st4(S.psi_w[4] + ii * g.P + j, j, g.nz, w4);
+                st4(S.psi_w[5] + ii * g.P + j, j, g.nz, w5);
+            }
+            if (arh != 0.f) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x4[e] = x4[e] + arh * (x4[e] + brh * p4.v[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (azi.v[e] != 0.f) x5[e] = x5[e] + azi.v[e] * (x5[e] + bzi.v[e] * p5.v[e]);
+            if (ii >= 1) {
+                const V4 azh = ld4g(C.az_half + j), bzh = ld4g(C.bz_half + j);
+                const float ari = __ldg(C.ar_int + ii), bri = __ldg(C.br_int + ii);
+                const V4 p6 = lds4(sm.x6, r2, c2), p7 = lds4(sm.x7, r2, c2);
+                if (own) {
+                    float w6[4], w7[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        w6[e] = x6[e] + bzh.v[e] * p6.v[e];
+                        w7[e] = x7[e] + bri * p7.v[e];
+                    }
+                    st4(S.psi_w[6] + ii * g.P + j, j, g.nz, w6);
+                    if (ari != 0.f) st4(S.psi_w[7] + ii * g.P + j, j, g.nz, w7);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (azh.v[e] != 0.f) x6[e] = x6[e] + azh.v[e] * (x6[e] + bzh.v[e] * p6.v[e]);
+                if (ari != 0.f) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) x7[e] = x7[e] + ari * (x7[e] + bri * p7.v[e]);
+                }
+            }
+        }
+        *reinterpret_cast<float4*>(&sm.x4[r2][c2]) = make_float4(x4[0], x4[1], x4[2], x4[3]);
+        *reinterpret_cast<float4*>(&sm.ytt[r2][c2]) = make_float4(ytt[0], ytt[1], ytt[2], ytt[3]);
+        *reinterpret_cast<float4*>(&sm.x5[r2][c2]) = make_float4(x5[0], x5[1], x5[2], x5[3]);
+        *reinterpret_cast<float4*>(&sm.x6[r2][c2]) = make_float4(x6[0], x6[1], x6[2], x6[3]);
+        *reinterpret_cast<float4*>(&sm.x7[r2][c2]) = make_float4(x7[0], x7[1], x7[2], x7[3]);
+    }
+    __syncthreads();
+    if (!o.live) return;
+    float2 gmr[4], gbr[4];
     V4 hmr{}, pr{}, av_r{};
     if (i >= 1) {
         av_r = ld4cg(S.vr + c);
         ld4f2(q.G_murz + c, gmr);
         hmr = ld4cg(q.H_murz + c);
         pr = ld4cg(fprev + c);
+        ld4f2(q.G_br + c, gbr);
     }
     // ---- transpose of the stress step into Av, density and shear correlations
     {
@@ -800,13 +881,11 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
         st4f2(q.G_bz + c, o.j, g.nz, gbz);
     }
     if (i >= 1) {
-        float2 gbr[4];
-        ld4f2(q.G_br + c, gbr);
         const V4 x4m2 = lds4(sm.x4, rr - 2, cc), x4m1 = lds4(sm.x4, rr - 1, cc),
                  x40 = lds4(sm.x4, rr, cc), x4p1 = lds4(sm.x4, rr + 1, cc);
         const V4 ytm1 = lds4(sm.ytt, rr - 1, cc), yt0 = lds4(sm.ytt, rr, cc);
         const V12 x6r = lds12(sm.x6, rr, cc - 4);
-        const float irm = C.inv_r_half[i - 1], inv_rh = C.inv_r_half[i];
+        const float irm = __ldg(C.inv_r_half + i - 1), inv_rh = __ldg(C.inv_r_half + i);
         float avr[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -834,38 +913,6 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
         st4(q.H_murz + c, o.j, g.nz, hmr2);
         st4f2(q.G_br + c, o.j, g.nz, gbr);
     }
-    // ---- adjoint memories of the stress step (own cell / own shear node)
-    if (pml) {
-        const float arh = C.ar_half[i], brh = C.br_half[i];
-        const V4 bzi = ld4cg(C.bz_int + o.j);
-        const V4 p4 = ld4cg(S.psi[4] + c), p5 = ld4cg(S.psi[5] + c);
-        const V4 lam_o = ld4g(C.w_lam + c), mu_o = ld4g(C.w_mu + c);
-        const V4 Arr = lds4(sm.arr, rr, cc), Att = lds4(sm.att, rr, cc), Azz = lds4(sm.azz, rr, cc);
-        float w4[4], w5[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float lam = lam_o.v[e], l2m = lam + 2.f * mu_o.v[e];
-            w4[e] = dt * (l2m * Arr.v[e] + lam * (Att.v[e] + Azz.v[e])) + brh * p4.v[e];
-            w5[e] = dt * (l2m * Azz.v[e] + lam * (Arr.v[e] + Att.v[e])) + bzi.v[e] * p5.v[e];
-        }
-        if (arh != 0.f) st4(S.psi_w[4] + c, o.j, g.nz, w4);
-        st4(S.psi_w[5] + c, o.j, g.nz, w5);
-        if (i >= 1) {
-            const float bri = C.br_int[i];
-            const V4 bzh = ld4cg(C.bz_half + o.j);
-            const V4 p6 = ld4cg(S.psi[6] + c), p7 = ld4cg(S.psi[7] + c);
-            const V4 mh_o = ld4g(C.w_muh + c), Arz = lds4(sm.arz, rr, cc);
-            float w6[4], w7[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float y = dt * mh_o.v[e] * Arz.v[e];
-                w6[e] = y + bzh.v[e] * p6.v[e];
-                w7[e] = y + bri * p7.v[e];
-            }
-            st4(S.psi_w[6] + c, o.j, g.nz, w6);
-            if (C.ar_int[i] != 0.f) st4(S.psi_w[7] + c, o.j, g.nz, w7);
-        }
-    }
 }
 
 // Transpose of the velocity step of one tile at reverse step n: S.{vr,vz}
@@ -879,9 +926,23 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
     // W = dt b Av at the velocity nodes (odd about the axis for v_r, even
     // for v_z) and the coefficients on the four stretched derivatives
     Tile &s_wr = sm.arr, &s_wz = sm.att, &s_x0 = sm.azz, &s_x1 = sm.arz, &s_x2 = sm.fvr,
-         &s_x3 = sm.fvz;
+         &s_x3 = sm.fvz, &s_br = sm.x4, &s_bz = sm.x5;
     const Own o = own_of(g, i0, j0);
     const bool pml = flags & TILE_PML;
+    __syncthreads();
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_async<ODD>(s_wr, S.vr, sl);
+        stage_async<ABS>(s_br, C.w_bvr, sl);
+        stage_async<EVEN>(s_wz, S.vz, sl);
+        stage_async<EVEN>(s_bz, C.w_bvz, sl);
+        if (pml) {
+            stage_async<ODD>(s_x0, S.psi[0], sl);
+            stage_async<ODD>(s_x1, S.psi[1], sl);
+            stage_async<EVEN>(s_x2, S.psi[2], sl);
+            stage_async<EVEN>(s_x3, S.psi[3], sl);
+        }
+    }
     V4 o_rr{}, o_tt{}, o_zz{}, o_rz{}, r3{};
     if (o.live) {
         o_rr = ld4cg(S.trr + o.c);
@@ -896,79 +957,84 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
             }
         }
     }
-    __syncthreads();
-    {
-        const int tid = threadIdx.y * 8 + threadIdx.x;
-        for (int it = tid; it < kSR * kQ; it += kThreads) {
-            const int r2 = it / kQ, q2 = it - r2 * kQ;
-            const int i = i0 - kH + r2, j = j0 - 4 + 4 * q2, c2 = 4 * q2;
-            float wr[4] = {0.f, 0.f, 0.f, 0.f}, wz[4] = {0.f, 0.f, 0.f, 0.f};
-            float x0[4] = {0.f, 0.f, 0.f, 0.f}, x1[4] = {0.f, 0.f, 0.f, 0.f};
-            float x2[4] = {0.f, 0.f, 0.f, 0.f}, x3[4] = {0.f, 0.f, 0.f, 0.f};
-            if (j >= 0 && j < g.nz) {
-                // v_r node: odd extension, zero on the axis and beyond nr
-                const int ir = i < 0 ? -i : i;
-                if (ir >= 1 && ir < g.nr) {
-                    const float sg = i < 0 ? -1.f : 1.f;
-                    const int cr = ir * g.P + j;
-                    const V4 av = ld4cg(S.vr + cr);
-                    const V4 bv = ld4g(C.w_bvr + cr);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float w = g.dt * bv.v[e] * av.v[e];
-                        x0[e] = x1[e] = w;
-                        wr[e] = w;
-                    }
-                    if (pml) {
-                        const float ari = C.ar_int[ir], bri = C.br_int[ir];
-                        const V4 p = ld4cg(S.psi[0] + cr);
-                        if (ari != 0.f) {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) x0[e] = wr[e] + ari * (wr[e] + bri * p.v[e]);
-                        }
-                        const V4 azi = ld4cg(C.az_int + j), bzi = ld4cg(C.bz_int + j);
-                        const V4 p1 = ld4cg(S.psi[1] + cr);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (azi.v[e] != 0.f) x1[e] = wr[e] + azi.v[e] * (wr[e] + bzi.v[e] * p1.v[e]);
-                    }
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        wr[e] *= sg;
-                        x0[e] *= sg;
-                        x1[e] *= sg;
-                    }
-                }
-                // v_z node: even extension, zero beyond nr
-                const int iz = i < 0 ? -1 - i : i;
-                if (iz < g.nr) {
-                    const int cz = iz * g.P + j;
-                    const V4 av = ld4cg(S.vz + cz);
-                    const V4 bv = ld4g(C.w_bvz + cz);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float w = g.dt * bv.v[e] * av.v[e];
-                        x2[e] = x3[e] = wz[e] = w;
-                    }
-                    if (pml) {
-                        const float arh = C.ar_half[iz], brh = C.br_half[iz];
-                        const V4 p = ld4cg(S.psi[2] + cz);
-                        if (arh != 0.f) {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) x2[e] = wz[e] + arh * (wz[e] + brh * p.v[e]);
-                        }
-                        const V4 azh = ld4cg(C.az_half + j), bzh = ld4cg(C.bz_half + j);
-                        const V4 p3 = ld4cg(S.psi[3] + cz);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (azh.v[e] != 0.f) x3[e] = wz[e] + azh.v[e] * (wz[e] + bzh.v[e] * p3.v[e]);
-                    }
-                }
+    async_wait_all();
+    // in place over this thread's slots (read by other threads only after
+    // the barrier below); own C-PML nodes also update their adjoint memories
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        const int r2 = sl.rr, c2 = sl.cq;
+        const int ii = i0 - kH + r2, j = j0 - 4 + c2;
+        const bool own = own_slot(sl);
+        if (sl.neg && sl.off_o >= 0) {
+            negate_slot(s_wr, sl);
+            if (pml) {
+                negate_slot(s_x0, sl);
+                negate_slot(s_x1, sl);
             }
-            *reinterpret_cast<float4*>(&s_wr[r2][c2]) = make_float4(wr[0], wr[1], wr[2], wr[3]);
-            *reinterpret_cast<float4*>(&s_wz[r2][c2]) = make_float4(wz[0], wz[1], wz[2], wz[3]);
+        }
+        // v_r node (zero-filled where there is none)
+        {
+            const V4 av = lds4(s_wr, r2, c2), bv = lds4(s_br, r2, c2);
+            float w[4], x0[4], x1[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) x0[e] = x1[e] = w[e] = g.dt * bv.v[e] * av.v[e];
+            if (pml && sl.off_o >= 0) {
+                const int ir = ii < 0 ? -ii : ii;
+                const float ari = __ldg(C.ar_int + ir), bri = __ldg(C.br_int + ir);
+                const V4 p0 = lds4(s_x0, r2, c2), p1 = lds4(s_x1, r2, c2);
+                const V4 azi = ld4g(C.az_int + j), bzi = ld4g(C.bz_int + j);
+                if (own) {
+                    float w0[4], w1[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        w0[e] = w[e] + bri * p0.v[e];
+                        w1[e] = w[e] + bzi.v[e] * p1.v[e];
+                    }
+                    if (ari != 0.f) st4(S.psi_w[0] + ii * g.P + j, j, g.nz, w0);
+                    st4(S.psi_w[1] + ii * g.P + j, j, g.nz, w1);
+                }
+                if (ari != 0.f) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) x0[e] = w[e] + ari * (w[e] + bri * p0.v[e]);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (azi.v[e] != 0.f) x1[e] = w[e] + azi.v[e] * (w[e] + bzi.v[e] * p1.v[e]);
+            }
+            *reinterpret_cast<float4*>(&s_wr[r2][c2]) = make_float4(w[0], w[1], w[2], w[3]);
             *reinterpret_cast<float4*>(&s_x0[r2][c2]) = make_float4(x0[0], x0[1], x0[2], x0[3]);
             *reinterpret_cast<float4*>(&s_x1[r2][c2]) = make_float4(x1[0], x1[1], x1[2], x1[3]);
+        }
+        // v_z node
+        {
+            const V4 av = lds4(s_wz, r2, c2), bv = lds4(s_bz, r2, c2);
+            float w[4], x2[4], x3[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) x2[e] = x3[e] = w[e] = g.dt * bv.v[e] * av.v[e];
+            if (pml && sl.off_e >= 0) {
+                const int iz = ii < 0 ? -1 - ii : ii;
+                const float arh = __ldg(C.ar_half + iz), brh = __ldg(C.br_half + iz);
+                const V4 p2 = lds4(s_x2, r2, c2), p3 = lds4(s_x3, r2, c2);
+                const V4 azh = ld4g(C.az_half + j), bzh = ld4g(C.bz_half + j);
+                if (own) {
+                    float w2[4], w3[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        w2[e] = w[e] + brh * p2.v[e];
+                        w3[e] = w[e] + bzh.v[e] * p3.v[e];
+                    }
+                    if (arh != 0.f) st4(S.psi_w[2] + ii * g.P + j, j, g.nz, w2);
+                    st4(S.psi_w[3] + ii * g.P + j, j, g.nz, w3);
+                }
+                if (arh != 0.f) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) x2[e] = w[e] + arh * (w[e] + brh * p2.v[e]);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (azh.v[e] != 0.f) x3[e] = w[e] + azh.v[e] * (w[e] + bzh.v[e] * p3.v[e]);
+            }
+            *reinterpret_cast<float4*>(&s_wz[r2][c2]) = make_float4(w[0], w[1], w[2], w[3]);
             *reinterpret_cast<float4*>(&s_x2[r2][c2]) = make_float4(x2[0], x2[1], x2[2], x2[3]);
             *reinterpret_cast<float4*>(&s_x3[r2][c2]) = make_float4(x3[0], x3[1], x3[2], x3[3]);
         }
@@ -981,7 +1047,7 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         const V4 x0m1 = lds4(s_x0, rr - 1, cc), x00 = lds4(s_x0, rr, cc),
                  x0p1 = lds4(s_x0, rr + 1, cc), x0p2 = lds4(s_x0, rr + 2, cc);
         const V12 x3r = lds12(s_x3, rr, cc - 4);
-        const float ir0 = C.inv_r_int[i], ir1 = i + 1 < g.nr ? C.inv_r_int[i + 1] : 0.f;
+        const float ir0 = __ldg(C.inv_r_int + i), ir1 = i + 1 < g.nr ? __ldg(C.inv_r_int + i + 1) : 0.f;
         float trr[4], ttt[4], tzz[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -1002,7 +1068,7 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         const V4 x2m2 = lds4(s_x2, rr - 2, cc), x2m1 = lds4(s_x2, rr - 1, cc),
                  x20 = lds4(s_x2, rr, cc), x2p1 = lds4(s_x2, rr + 1, cc);
         const V4 wzm1 = lds4(s_wz, rr - 1, cc), wz0 = lds4(s_wz, rr, cc);
-        const float irm = C.inv_r_half[i - 1], ir0 = C.inv_r_half[i];
+        const float irm = __ldg(C.inv_r_half + i - 1), ir0 = __ldg(C.inv_r_half + i);
         float trz[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -1012,33 +1078,6 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
             trz[e] = o_rz.v[e] + s;
         }
         st4(S.trz + c, o.j, g.nz, trz);
-    }
-    // adjoint memories of the velocity step at the own velocity nodes
-    if (pml) {
-        const V4 wr = lds4(s_wr, rr, cc), wz = lds4(s_wz, rr, cc);
-        const V4 bzi = ld4cg(C.bz_int + o.j), bzh = ld4cg(C.bz_half + o.j);
-        const V4 p2 = ld4cg(S.psi[2] + c), p3 = ld4cg(S.psi[3] + c);
-        float w2[4], w3[4];
-        const float brh = C.br_half[i];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            w2[e] = wz.v[e] + brh * p2.v[e];
-            w3[e] = wz.v[e] + bzh.v[e] * p3.v[e];
-        }
-        if (C.ar_half[i] != 0.f) st4(S.psi_w[2] + c, o.j, g.nz, w2);
-        st4(S.psi_w[3] + c, o.j, g.nz, w3);
-        if (i >= 1) {
-            const V4 p0 = ld4cg(S.psi[0] + c), p1 = ld4cg(S.psi[1] + c);
-            const float bri = C.br_int[i];
-            float w0[4], w1[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                w0[e] = wr.v[e] + bri * p0.v[e];
-                w1[e] = wr.v[e] + bzi.v[e] * p1.v[e];
-            }
-            if (C.ar_int[i] != 0.f) st4(S.psi_w[0] + c, o.j, g.nz, w0);
-            st4(S.psi_w[1] + c, o.j, g.nz, w1);
-        }
     }
 }
 

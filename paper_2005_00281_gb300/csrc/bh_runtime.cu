@@ -834,6 +834,13 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        // the adjoint tiles want 5 blocks of ~42 KB shared memory per SM
+        const void* big_smem[] = {(const void*)k_adj_persist<1>, (const void*)k_adj_persist<kGroup>,
+                                  (const void*)k_adj_stress<1>, (const void*)k_adj_stress<kGroup>,
+                                  (const void*)k_adj_vel<1>, (const void*)k_adj_vel<kGroup>};
+        for (const void* f : big_smem)
+            CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared));
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<1>, kThreads, 0));
         m->fwd_blocks = nb * sms;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<1>, kThreads, 0));
