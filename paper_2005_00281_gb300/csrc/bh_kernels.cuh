@@ -284,6 +284,43 @@ __device__ __forceinline__ bool own_slot(const Slot& s)
     return s.rr >= kH && s.rr < kH + kTR && s.cq >= 4 && s.cq < 4 + kTZ;
 }
 
+// C-PML profiles of a tile's staged region, read from shared memory by the
+// layer branches (the profile arrays would otherwise come from L2 on every
+// slot: L1 is small next to the staged tiles).  r: per staged row, a and b
+// of the half-r profile at the even-mirrored row and of the integer-r
+// profile at row |i|; z: per staged column, the axial a and b at integer
+// and half positions (zero outside 0 <= z < nz).
+struct __align__(16) Prof {
+    float r[4][kSR];  // ar_half, br_half (even row), ar_int, br_int (|i|)
+    float z[4][kSZ];  // az_int, bz_int, az_half, bz_half
+};
+
+__device__ __forceinline__ void stage_prof(Prof& p, const CoefK& C, const WinK& g, int i0, int j0)
+{
+    const int tid = tid_of();
+    if (tid < kSR) {
+        const int i = i0 - kH + tid;
+        const int ie = i < 0 ? -1 - i : i, io = i < 0 ? -i : i;
+        p.r[0][tid] = ie < g.nr ? __ldg(C.ar_half + ie) : 0.f;
+        p.r[1][tid] = ie < g.nr ? __ldg(C.br_half + ie) : 0.f;
+        p.r[2][tid] = io < g.nr ? __ldg(C.ar_int + io) : 0.f;
+        p.r[3][tid] = io < g.nr ? __ldg(C.br_int + io) : 0.f;
+    } else if (tid >= 32 && tid < 32 + kSZ) {
+        const int cz = tid - 32, j = j0 - 4 + cz;
+        const bool in = j >= 0 && j < g.nz;
+        p.z[0][cz] = in ? __ldg(C.az_int + j) : 0.f;
+        p.z[1][cz] = in ? __ldg(C.bz_int + j) : 0.f;
+        p.z[2][cz] = in ? __ldg(C.az_half + j) : 0.f;
+        p.z[3][cz] = in ? __ldg(C.bz_half + j) : 0.f;
+    }
+}
+
+__device__ __forceinline__ V4 prof4(const float* row, int cz)
+{
+    const float4 t = *reinterpret_cast<const float4*>(row + cz);
+    return V4{{t.x, t.y, t.z, t.w}};
+}
+
 // own-node index helpers: thread (x = column group, y = row)
 struct Own {
     int i, rr, j, cc, c;  // window row, staged row, first column, staged column, plane index
@@ -315,6 +352,7 @@ struct SrcRecK {
 
 struct __align__(16) FwdSmem {
     Tile a, b, c, d;
+    Prof pf;
 };
 
 // Velocity half-step of one tile: Eq. 2 lines 1-2 with the C-PML memories
@@ -337,6 +375,7 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
         stage_async<ODD>(s_rz, S.trz, sl);
         stage_async<EVEN>(s_zz, S.tzz, sl);
     }
+    if (pml) stage_prof(sm.pf, C, g, i0, j0);
     // own-node inputs, in flight together with the copies
     if (o.live) {
         vz0 = ld4cg(S.vz + o.c);
@@ -363,17 +402,16 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     }
     __syncthreads();
     if (!o.live) return;
-    // C-PML profiles: small read-only arrays, L1 hits after the first step
     if (pml) {
-        arh = __ldg(C.ar_half + o.i);
-        brh = __ldg(C.br_half + o.i);
-        azh = ld4g(C.az_half + o.j);
-        bzh = ld4g(C.bz_half + o.j);
+        arh = sm.pf.r[0][o.rr];
+        brh = sm.pf.r[1][o.rr];
+        azh = prof4(sm.pf.z[2], o.cc);
+        bzh = prof4(sm.pf.z[3], o.cc);
         if (o.i >= 1) {
-            ari = __ldg(C.ar_int + o.i);
-            bri = __ldg(C.br_int + o.i);
-            azi = ld4g(C.az_int + o.j);
-            bzi = ld4g(C.bz_int + o.j);
+            ari = sm.pf.r[2][o.rr];
+            bri = sm.pf.r[3][o.rr];
+            azi = prof4(sm.pf.z[0], o.cc);
+            bzi = prof4(sm.pf.z[1], o.cc);
         }
     }
     const int rr = o.rr, cc = o.cc;
@@ -463,6 +501,7 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         stage_async<ODD>(s_vr, S.vr, sl);
         stage_async<EVEN>(s_vz, S.vz, sl);
     }
+    if (pml) stage_prof(sm.pf, C, g, i0, j0);
     V4 t_rr{}, t_tt{}, t_zz{}, lm{}, mu{}, t_rz{}, mh{};
     float arh = 0.f, brh = 0.f;
     V4 azi{}, bzi{}, q4{}, q5{};
@@ -493,10 +532,10 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     const int rr = o.rr, cc = o.cc;
     {
         if (pml) {
-            arh = __ldg(C.ar_half + o.i);
-            brh = __ldg(C.br_half + o.i);
-            azi = ld4g(C.az_int + o.j);
-            bzi = ld4g(C.bz_int + o.j);
+            arh = sm.pf.r[0][rr];
+            brh = sm.pf.r[1][rr];
+            azi = prof4(sm.pf.z[0], cc);
+            bzi = prof4(sm.pf.z[1], cc);
         }
         const V12 vr12 = lds12(s_vr, rr, cc - 4), vz12 = lds12(s_vz, rr, cc - 4);
         const V4 vrp1 = lds4(s_vr, rr + 1, cc);
@@ -548,10 +587,10 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         float ari = 0.f, bri = 0.f;
         V4 azh{}, bzh{}, q6{}, q7{};
         if (pml) {
-            ari = __ldg(C.ar_int + o.i);
-            bri = __ldg(C.br_int + o.i);
-            azh = ld4g(C.az_half + o.j);
-            bzh = ld4g(C.bz_half + o.j);
+            ari = sm.pf.r[2][rr];
+            bri = sm.pf.r[3][rr];
+            azh = prof4(sm.pf.z[2], cc);
+            bzh = prof4(sm.pf.z[3], cc);
             q6 = ld4cg(S.psi[6] + o.c);
             q7 = ld4cg(S.psi[7] + o.c);
         }
@@ -606,51 +645,67 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// All blocks of a cooperative launch meet here; `epoch` counts the block's
-// barriers (the same sequence in every block).  A block arrives with one
-// release-acquire increment of a monotonic counter and waits, polling with
-// acquire loads, until the counter reaches epoch * expected.  The wait is
-// bounded twice, by the wall clock and by a poll count; when it runs out, or
-// another block reports that it did, the function returns false in every
-// thread of the block, the caller returns from the kernel, and the host reads
-// the error flag.  Writes before the barrier are visible to ld.global.cg
-// loads after it.
-__device__ bool grid_barrier(const BarK& b, unsigned& epoch)
+// All blocks of a cooperative launch meet at every barrier; `epoch` counts
+// the block's barriers (the same sequence in every block).  The barrier is
+// split in two: grid_arrive publishes the block's writes with one
+// release-acquire increment of a monotonic counter; grid_wait polls it with acquire loads
+// until it reaches epoch * expected.  Between the two a block may do work
+// that no other block reads in the next phase (its own accumulators), which
+// then overlaps the barrier latency.  The wait is bounded twice, by the wall
+// clock and by a poll count; when it runs out, or another block reports that
+// it did, grid_wait returns false in every thread of the block, the caller
+// returns from the kernel, and the host reads the error flag.  Writes before
+// the arrival are visible to ld.global.cg loads and cp.async.cg copies after
+// the wait.  Both halves are called by every thread of the block.
+__device__ __forceinline__ void grid_arrive(const BarK& b, unsigned& epoch)
 {
-    __shared__ int s_ok;
     __syncthreads();
+    ++epoch;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        ++epoch;
-        const unsigned target = epoch * b.expected;
+        // an acq_rel atomic measured ~1 us faster per barrier than a
+        // release reduction or a fence + relaxed atomic on GB300
         unsigned old;
         asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(b.count) : "memory");
+        (void)old;
+    }
+}
+
+__device__ bool grid_wait(const BarK& b, unsigned epoch)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const unsigned target = epoch * b.expected;
         int ok = 1;
-        if (old + 1u < target) {
-            const unsigned long long t0 = global_ns();
-            // every poll is an L2 round trip (>= 64 ns); the error flag and
-            // the clock are checked every 8th poll
-            const unsigned long long max_polls = b.timeout_ns / 64ull + 1024ull;
-            unsigned long long polls = 0;
-            volatile int* verr = b.err;
-            for (;;) {
-                unsigned cur;
-                asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(b.count) : "memory");
-                if (cur >= target) break;
-                if ((++polls & 7ull) == 0) {
-                    if (*verr) { ok = 0; break; }
-                    if (global_ns() - t0 > b.timeout_ns || polls > max_polls) {
-                        atomicExch(b.err, 1);
-                        ok = 0;
-                        break;
-                    }
+        const unsigned long long t0 = global_ns();
+        // every poll is an L2 round trip (>= 64 ns); the error flag and the
+        // clock are checked every 8th poll
+        const unsigned long long max_polls = b.timeout_ns / 64ull + 1024ull;
+        unsigned long long polls = 0;
+        volatile int* verr = b.err;
+        for (;;) {
+            unsigned cur;
+            asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(b.count) : "memory");
+            if (cur >= target) break;
+            if ((++polls & 7ull) == 0) {
+                if (*verr) { ok = 0; break; }
+                if (global_ns() - t0 > b.timeout_ns || polls > max_polls) {
+                    atomicExch(b.err, 1);
+                    ok = 0;
+                    break;
                 }
             }
         }
-        if (ok && *(volatile int*)b.err) ok = 0;
+        if (ok && *verr) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(const BarK& b, unsigned& epoch)
+{
+    grid_arrive(b, epoch);
+    return grid_wait(b, epoch);
 }
 
 // ------------------------------------------ adjoint: transpose of Eq. 2
@@ -672,16 +727,35 @@ struct AdjK {
 };
 
 struct __align__(16) AdjSmem {
-    // Stress step: staged adjoint stresses and forward v^{n+1/2}; lambda,
-    // mu, mu_h are staged into x4, ytt, x5 and replaced there by the
-    // coefficients of the transposed stencils: on D_r v_r (x4), v_r/r (ytt),
-    // D_z v_z (x5) at cells, on D_z v_r (x6) and D_r v_z (x7) at shear
-    // nodes; C-PML tiles stage the adjoint memories 4, 5 into p4, p5 and
-    // 6, 7 into x6, x7.  Velocity step: adjoint velocities into arr, att,
-    // buoyancies into x4, x5, memories 0..3 into azz, arz, fvr, fvz, each
+    // d: tiles of both half-steps.  Stress step: adjoint stresses (d0..d3),
+    // adjoint memories 4..7 (d4..d7; d6, d7 then hold the coefficients on
+    // D_z v_r and D_r v_z at shear nodes).  Velocity step: adjoint
+    // velocities (d0, d1), memories 0..3 (d2..d5), buoyancies (d6, d7), each
     // replaced in place by W = dt b Av and the four coefficients.
-    Tile arr, att, azz, arz, fvr, fvz, x4, ytt, x5, x6, x7, p4, p5;
+    // f: stress step only, data that do not change within a launch: forward
+    // v_r, v_z of v^{n+1/2} (f0, f1) and lambda, mu, mu_h (f2..f4, replaced
+    // in place by the coefficients on D_r v_r, v_r/r and D_z v_z at cells).
+    // The velocity step of reverse step n stages f for step n-1 once its
+    // own tiles are built, so those copies run during the grid barrier.
+    Tile d[8];
+    Tile f[5];
+    Prof pf;
 };
+
+// the stress step's launch-invariant tiles (see AdjSmem)
+__device__ __forceinline__ void stage_adj_statics(AdjSmem& sm, const CoefK& C, const float* fcur,
+                                                  int i0, int j0, const WinK& g)
+{
+    const int plane = g.nr * g.P;
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_async<ODD>(sm.f[0], fcur, sl);
+        stage_async<EVEN>(sm.f[1], fcur + plane, sl);
+        stage_async<EVEN>(sm.f[2], C.w_lam, sl);
+        stage_async<EVEN>(sm.f[3], C.w_mu, sl);
+        stage_async<ABS>(sm.f[4], C.w_muh, sl);
+    }
+}
 
 __device__ __forceinline__ float2 kahan_step(float2 s, float x)
 {
@@ -697,9 +771,13 @@ __device__ __forceinline__ float2 kahan_step(float2 s, float x)
 // S.{trr..trz} hold dJ/dtau^{n+1}; S.{vr,vz} accumulate to dJ/dv^{n+1/2};
 // psi[4..7] are the adjoint memories read side, psi_w[4..7] the write side.
 // fcur: v_r, v_z planes of v^{n+1/2}; fprev: those of v^{n-1/2}.
+// statics: the f tiles were staged by the preceding velocity step.
+// bar (or null): the block arrives at the grid barrier once the adjoint
+// velocities are stored; the own-node correlations follow the arrival.
 __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const AdjK& q, const float* fcur,
                                                 const float* fprev, int i0, int j0, int flags,
+                                                bool statics, const BarK* bar, unsigned& epoch,
                                                 AdjSmem& sm)
 {
     const int plane = g.nr * g.P;
@@ -707,89 +785,52 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     const Own o = own_of(g, i0, j0);
     const bool pml = flags & TILE_PML;
     const int rr = o.rr, cc = o.cc, i = o.i, c = o.c;
+    Tile &T_rr = sm.d[0], &T_tt = sm.d[1], &T_zz = sm.d[2], &T_rz = sm.d[3];
+    Tile &T_p4 = sm.d[4], &T_p5 = sm.d[5], &T_x6 = sm.d[6], &T_x7 = sm.d[7];
+    Tile &T_fr = sm.f[0], &T_fz = sm.f[1], &T_x4 = sm.f[2], &T_yt = sm.f[3], &T_x5 = sm.f[4];
     __syncthreads();
+    if (!statics) stage_adj_statics(sm, C, fcur, i0, j0, g);
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const Slot sl = slot_of(it, i0, j0, g);
-        stage_async<EVEN>(sm.arr, S.trr, sl);
-        stage_async<EVEN>(sm.att, S.ttt, sl);
-        stage_async<EVEN>(sm.azz, S.tzz, sl);
-        stage_async<ODD>(sm.arz, S.trz, sl);
-        stage_async<ODD>(sm.fvr, fcur, sl);
-        stage_async<EVEN>(sm.fvz, fcur + plane, sl);
-        stage_async<EVEN>(sm.x4, C.w_lam, sl);
-        stage_async<EVEN>(sm.ytt, C.w_mu, sl);
-        stage_async<ABS>(sm.x5, C.w_muh, sl);
+        stage_async<EVEN>(T_rr, S.trr, sl);
+        stage_async<EVEN>(T_tt, S.ttt, sl);
+        stage_async<EVEN>(T_zz, S.tzz, sl);
+        stage_async<ODD>(T_rz, S.trz, sl);
         if (pml) {
-            stage_async<EVEN>(sm.p4, S.psi[4], sl);
-            stage_async<EVEN>(sm.p5, S.psi[5], sl);
-            stage_async<POS>(sm.x6, S.psi[6], sl);
-            stage_async<POS>(sm.x7, S.psi[7], sl);
+            stage_async<EVEN>(T_p4, S.psi[4], sl);
+            stage_async<EVEN>(T_p5, S.psi[5], sl);
+            stage_async<POS>(T_x6, S.psi[6], sl);
+            stage_async<POS>(T_x7, S.psi[7], sl);
         }
     }
-    // own accumulators of the lambda and normal-mu correlations, in flight
-    // together with the copies
-    float2 gl[4], gm[4];
-    V4 hl{}, hm{};
+    if (pml) stage_prof(sm.pf, C, g, i0, j0);
+    // own adjoint velocities, in flight together with the copies
+    V4 av_z{}, av_r{};
     if (o.live) {
-        ld4f2(q.G_lam + c, gl);
-        ld4f2(q.G_munn + c, gm);
-        hl = ld4cg(q.H_lam + c);
-        hm = ld4cg(q.H_munn + c);
+        av_z = ld4cg(S.vz + c);
+        if (i >= 1) av_r = ld4cg(S.vr + c);
     }
     async_wait_all();
     if (i0 < kH) {
         for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
             const Slot sl = slot_of(it, i0, j0, g);
             if (sl.neg && sl.off_o >= 0) {
-                negate_slot(sm.arz, sl);
-                negate_slot(sm.fvr, sl);
+                negate_slot(T_rz, sl);
+                negate_slot(T_fr, sl);
             }
         }
     }
     __syncthreads();
 
-    // ---- lambda and normal mu correlations, pseudo-Hessian
-    if (o.live) {
-        const V12 fr12 = lds12(sm.fvr, rr, cc - 4), fz12 = lds12(sm.fvz, rr, cc - 4);
-        const V4 frm1 = lds4(sm.fvr, rr - 1, cc), frp1 = lds4(sm.fvr, rr + 1, cc),
-                 frp2 = lds4(sm.fvr, rr + 2, cc);
-        const V4 Arr = lds4(sm.arr, rr, cc), Att = lds4(sm.att, rr, cc), Azz = lds4(sm.azz, rr, cc);
-        const float inv_rh = __ldg(C.inv_r_half + i);
-        float hl2[4], hm2[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float err = d4(frp1.v[e], fr12.v[4 + e], frp2.v[e], frm1.v[e]) * g.inv_dr;
-            const float ett = 0.5f * (fr12.v[4 + e] + frp1.v[e]) * inv_rh;
-            const float ezz = d4(fz12.v[4 + e], fz12.v[3 + e], fz12.v[5 + e], fz12.v[2 + e]) * g.inv_dz;
-            const float div = err + ett + ezz;
-            gl[e] = kahan_step(gl[e], dt * div * (Arr.v[e] + Att.v[e] + Azz.v[e]));
-            gm[e] = kahan_step(gm[e], 2.f * dt * (err * Arr.v[e] + ett * Att.v[e] + ezz * Azz.v[e]));
-            hl2[e] = hl.v[e] + dt * div * div;
-            hm2[e] = hm.v[e] + 4.f * dt * (err * err + ett * ett + ezz * ezz);
-        }
-        st4f2(q.G_lam + c, o.j, g.nz, gl);
-        st4f2(q.G_munn + c, o.j, g.nz, gm);
-        st4(q.H_lam + c, o.j, g.nz, hl2);
-        st4(q.H_munn + c, o.j, g.nz, hm2);
-    }
-    // own inputs of the transposes and the remaining correlations: in flight
-    // during the coefficient pass
-    float2 gbz[4];
-    V4 av_z{}, pz{};
-    if (o.live) {
-        av_z = ld4cg(S.vz + c);
-        ld4f2(q.G_bz + c, gbz);
-        pz = ld4cg(fprev + plane + c);
-    }
     // transposed-stencil coefficients, in place over this thread's slots;
     // own C-PML nodes also update their adjoint memories here
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const Slot sl = slot_of(it, i0, j0, g);
         const int r2 = sl.rr, c2 = sl.cq;
         const int ii = i0 - kH + r2, j = j0 - 4 + c2;
-        const V4 lm = lds4(sm.x4, r2, c2), mu = lds4(sm.ytt, r2, c2), mh = lds4(sm.x5, r2, c2);
-        const V4 ar = lds4(sm.arr, r2, c2), at = lds4(sm.att, r2, c2), az = lds4(sm.azz, r2, c2);
-        const V4 arz = lds4(sm.arz, r2, c2);
+        const V4 lm = lds4(T_x4, r2, c2), mu = lds4(T_yt, r2, c2), mh = lds4(T_x5, r2, c2);
+        const V4 ar = lds4(T_rr, r2, c2), at = lds4(T_tt, r2, c2), az = lds4(T_zz, r2, c2);
+        const V4 arz = lds4(T_rz, r2, c2);
         float x4[4], ytt[4], x5[4], x6[4], x7[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -801,11 +842,10 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
             x6[e] = x7[e] = dt * mh.v[e] * arz.v[e];
         }
         if (pml && ii < g.nr && j >= 0 && j < g.nz) {
-            const int ic = ii < 0 ? -1 - ii : ii;
             const bool own = own_slot(sl);
-            const float arh = __ldg(C.ar_half + ic), brh = __ldg(C.br_half + ic);
-            const V4 p4 = lds4(sm.p4, r2, c2), p5 = lds4(sm.p5, r2, c2);
-            const V4 azi = ld4g(C.az_int + j), bzi = ld4g(C.bz_int + j);
+            const float arh = sm.pf.r[0][r2], brh = sm.pf.r[1][r2];
+            const V4 p4 = lds4(T_p4, r2, c2), p5 = lds4(T_p5, r2, c2);
+            const V4 azi = prof4(sm.pf.z[0], c2), bzi = prof4(sm.pf.z[1], c2);
             if (own) {
                 float w4[4], w5[4];
 #pragma unroll
@@ -824,9 +864,9 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
             for (int e = 0; e < 4; ++e)
                 if (azi.v[e] != 0.f) x5[e] = x5[e] + azi.v[e] * (x5[e] + bzi.v[e] * p5.v[e]);
             if (ii >= 1) {
-                const V4 azh = ld4g(C.az_half + j), bzh = ld4g(C.bz_half + j);
-                const float ari = __ldg(C.ar_int + ii), bri = __ldg(C.br_int + ii);
-                const V4 p6 = lds4(sm.x6, r2, c2), p7 = lds4(sm.x7, r2, c2);
+                const V4 azh = prof4(sm.pf.z[2], c2), bzh = prof4(sm.pf.z[3], c2);
+                const float ari = sm.pf.r[2][r2], bri = sm.pf.r[3][r2];
+                const V4 p6 = lds4(T_x6, r2, c2), p7 = lds4(T_x7, r2, c2);
                 if (own) {
                     float w6[4], w7[4];
 #pragma unroll
@@ -846,59 +886,92 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
                 }
             }
         }
-        *reinterpret_cast<float4*>(&sm.x4[r2][c2]) = make_float4(x4[0], x4[1], x4[2], x4[3]);
-        *reinterpret_cast<float4*>(&sm.ytt[r2][c2]) = make_float4(ytt[0], ytt[1], ytt[2], ytt[3]);
-        *reinterpret_cast<float4*>(&sm.x5[r2][c2]) = make_float4(x5[0], x5[1], x5[2], x5[3]);
-        *reinterpret_cast<float4*>(&sm.x6[r2][c2]) = make_float4(x6[0], x6[1], x6[2], x6[3]);
-        *reinterpret_cast<float4*>(&sm.x7[r2][c2]) = make_float4(x7[0], x7[1], x7[2], x7[3]);
+        *reinterpret_cast<float4*>(&T_x4[r2][c2]) = make_float4(x4[0], x4[1], x4[2], x4[3]);
+        *reinterpret_cast<float4*>(&T_yt[r2][c2]) = make_float4(ytt[0], ytt[1], ytt[2], ytt[3]);
+        *reinterpret_cast<float4*>(&T_x5[r2][c2]) = make_float4(x5[0], x5[1], x5[2], x5[3]);
+        *reinterpret_cast<float4*>(&T_x6[r2][c2]) = make_float4(x6[0], x6[1], x6[2], x6[3]);
+        *reinterpret_cast<float4*>(&T_x7[r2][c2]) = make_float4(x7[0], x7[1], x7[2], x7[3]);
     }
     __syncthreads();
-    if (!o.live) return;
-    float2 gmr[4], gbr[4];
-    V4 hmr{}, pr{}, av_r{};
-    if (i >= 1) {
-        av_r = ld4cg(S.vr + c);
-        ld4f2(q.G_murz + c, gmr);
-        hmr = ld4cg(q.H_murz + c);
-        pr = ld4cg(fprev + c);
-        ld4f2(q.G_br + c, gbr);
-    }
-    // ---- transpose of the stress step into Av, density and shear correlations
-    {
-        const V12 x5r = lds12(sm.x5, rr, cc - 4);
-        const V4 x7m1 = lds4(sm.x7, rr - 1, cc), x70 = lds4(sm.x7, rr, cc),
-                 x7p1 = lds4(sm.x7, rr + 1, cc), x7p2 = lds4(sm.x7, rr + 2, cc);
-        const V4 fz0 = lds4(sm.fvz, rr, cc);
-        float avz[4];
+
+    // ---- transpose of the stress step into Av
+    float avz[4] = {0.f, 0.f, 0.f, 0.f}, avr[4] = {0.f, 0.f, 0.f, 0.f};
+    if (o.live) {
+        const V12 x5r = lds12(T_x5, rr, cc - 4);
+        const V4 x7m1 = lds4(T_x7, rr - 1, cc), x70 = lds4(T_x7, rr, cc),
+                 x7p1 = lds4(T_x7, rr + 1, cc), x7p2 = lds4(T_x7, rr + 2, cc);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             float s = d4(x5r.v[4 + e], x5r.v[5 + e], x5r.v[3 + e], x5r.v[6 + e]) * g.inv_dz;
             s += d4(x70.v[e], x7p1.v[e], x7m1.v[e], x7p2.v[e]) * g.inv_dr;
             avz[e] = av_z.v[e] + s;
-            gbz[e] = kahan_step(gbz[e], (fz0.v[e] - pz.v[e]) * avz[e]);
         }
         st4(S.vz + c, o.j, g.nz, avz);
-        st4f2(q.G_bz + c, o.j, g.nz, gbz);
+        if (i >= 1) {
+            const V4 x4m2 = lds4(T_x4, rr - 2, cc), x4m1 = lds4(T_x4, rr - 1, cc),
+                     x40 = lds4(T_x4, rr, cc), x4p1 = lds4(T_x4, rr + 1, cc);
+            const V4 ytm1 = lds4(T_yt, rr - 1, cc), yt0 = lds4(T_yt, rr, cc);
+            const V12 x6r = lds12(T_x6, rr, cc - 4);
+            const float irm = __ldg(C.inv_r_half + i - 1), inv_rh = __ldg(C.inv_r_half + i);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float s = d4(x4m1.v[e], x40.v[e], x4m2.v[e], x4p1.v[e]) * g.inv_dr;
+                s += 0.5f * (ytm1.v[e] * irm + yt0.v[e] * inv_rh);
+                s += d4(x6r.v[3 + e], x6r.v[4 + e], x6r.v[2 + e], x6r.v[5 + e]) * g.inv_dz;
+                avr[e] = av_r.v[e] + s;
+            }
+            st4(S.vr + c, o.j, g.nz, avr);
+        }
     }
-    if (i >= 1) {
-        const V4 x4m2 = lds4(sm.x4, rr - 2, cc), x4m1 = lds4(sm.x4, rr - 1, cc),
-                 x40 = lds4(sm.x4, rr, cc), x4p1 = lds4(sm.x4, rr + 1, cc);
-        const V4 ytm1 = lds4(sm.ytt, rr - 1, cc), yt0 = lds4(sm.ytt, rr, cc);
-        const V12 x6r = lds12(sm.x6, rr, cc - 4);
-        const float irm = __ldg(C.inv_r_half + i - 1), inv_rh = __ldg(C.inv_r_half + i);
-        float avr[4];
+    // everything the next phase reads from this tile is stored
+    if (bar) grid_arrive(*bar, epoch);
+    if (!o.live) return;
+
+    // ---- correlations (Eq. 7, Eq. 8, density) and pseudo-Hessian, own nodes
+    float2 gl[4], gm[4], gbz[4];
+    ld4f2(q.G_lam + c, gl);
+    ld4f2(q.G_munn + c, gm);
+    const V4 hl = ld4cg(q.H_lam + c), hm = ld4cg(q.H_munn + c);
+    ld4f2(q.G_bz + c, gbz);
+    const V4 pz = ld4cg(fprev + plane + c);
+    float hl2[4], hm2[4];
+    {
+        const V12 fr12 = lds12(T_fr, rr, cc - 4), fz12 = lds12(T_fz, rr, cc - 4);
+        const V4 frm1 = lds4(T_fr, rr - 1, cc), frp1 = lds4(T_fr, rr + 1, cc),
+                 frp2 = lds4(T_fr, rr + 2, cc);
+        const V4 Arr = lds4(T_rr, rr, cc), Att = lds4(T_tt, rr, cc), Azz = lds4(T_zz, rr, cc);
+        const float inv_rh = __ldg(C.inv_r_half + i);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            float s = d4(x4m1.v[e], x40.v[e], x4m2.v[e], x4p1.v[e]) * g.inv_dr;
-            s += 0.5f * (ytm1.v[e] * irm + yt0.v[e] * inv_rh);
-            s += d4(x6r.v[3 + e], x6r.v[4 + e], x6r.v[2 + e], x6r.v[5 + e]) * g.inv_dz;
-            avr[e] = av_r.v[e] + s;
+            const float err = d4(frp1.v[e], fr12.v[4 + e], frp2.v[e], frm1.v[e]) * g.inv_dr;
+            const float ett = 0.5f * (fr12.v[4 + e] + frp1.v[e]) * inv_rh;
+            const float ezz = d4(fz12.v[4 + e], fz12.v[3 + e], fz12.v[5 + e], fz12.v[2 + e]) * g.inv_dz;
+            const float div = err + ett + ezz;
+            gl[e] = kahan_step(gl[e], dt * div * (Arr.v[e] + Att.v[e] + Azz.v[e]));
+            gm[e] = kahan_step(gm[e], 2.f * dt * (err * Arr.v[e] + ett * Att.v[e] + ezz * Azz.v[e]));
+            hl2[e] = hl.v[e] + dt * div * div;
+            hm2[e] = hm.v[e] + 4.f * dt * (err * err + ett * ett + ezz * ezz);
+            gbz[e] = kahan_step(gbz[e], (fz12.v[4 + e] - pz.v[e]) * avz[e]);
         }
-        st4(S.vr + c, o.j, g.nz, avr);
-        const V12 fr12 = lds12(sm.fvr, rr, cc - 4);
-        const V4 fz0 = lds4(sm.fvz, rr, cc), fzm1 = lds4(sm.fvz, rr - 1, cc),
-                 fzm2 = lds4(sm.fvz, rr - 2, cc), fzp1 = lds4(sm.fvz, rr + 1, cc);
-        const V4 Arz = lds4(sm.arz, rr, cc);
+    }
+    float2 gmr[4], gbr[4];
+    V4 hmr{}, pr{};
+    if (i >= 1) {
+        ld4f2(q.G_murz + c, gmr);
+        hmr = ld4cg(q.H_murz + c);
+        pr = ld4cg(fprev + c);
+        ld4f2(q.G_br + c, gbr);
+    }
+    st4f2(q.G_lam + c, o.j, g.nz, gl);
+    st4f2(q.G_munn + c, o.j, g.nz, gm);
+    st4(q.H_lam + c, o.j, g.nz, hl2);
+    st4(q.H_munn + c, o.j, g.nz, hm2);
+    st4f2(q.G_bz + c, o.j, g.nz, gbz);
+    if (i >= 1) {
+        const V12 fr12 = lds12(T_fr, rr, cc - 4);
+        const V4 fz0 = lds4(T_fz, rr, cc), fzm1 = lds4(T_fz, rr - 1, cc),
+                 fzm2 = lds4(T_fz, rr - 2, cc), fzp1 = lds4(T_fz, rr + 1, cc);
+        const V4 Arz = lds4(T_rz, rr, cc);
         float hmr2[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -919,14 +992,18 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
 // hold dJ/dv^{n+1/2}; S.{trr..trz} accumulate to dJ/dtau^n.  Then the
 // residual of step n-1 is injected at the receivers (transpose of the
 // recording).
+// next_fcur (or null): v^{n-1/2}, whose stress step (reverse step n-1) runs
+// next on this tile; its launch-invariant tiles are staged here, after the
+// block's arrival at the grid barrier (bar, or null: no barrier).
 __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
                                              const AdjK& q, int n, int i0, int j0, int flags,
-                                             AdjSmem& sm)
+                                             const float* next_fcur, const BarK* bar,
+                                             unsigned& epoch, AdjSmem& sm)
 {
     // W = dt b Av at the velocity nodes (odd about the axis for v_r, even
     // for v_z) and the coefficients on the four stretched derivatives
-    Tile &s_wr = sm.arr, &s_wz = sm.att, &s_x0 = sm.azz, &s_x1 = sm.arz, &s_x2 = sm.fvr,
-         &s_x3 = sm.fvz, &s_br = sm.x4, &s_bz = sm.x5;
+    Tile &s_wr = sm.d[0], &s_wz = sm.d[1], &s_x0 = sm.d[2], &s_x1 = sm.d[3], &s_x2 = sm.d[4],
+         &s_x3 = sm.d[5], &s_br = sm.d[6], &s_bz = sm.d[7];
     const Own o = own_of(g, i0, j0);
     const bool pml = flags & TILE_PML;
     __syncthreads();
@@ -943,6 +1020,7 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
             stage_async<EVEN>(s_x3, S.psi[3], sl);
         }
     }
+    if (pml) stage_prof(sm.pf, C, g, i0, j0);
     V4 o_rr{}, o_tt{}, o_zz{}, o_rz{}, r3{};
     if (o.live) {
         o_rr = ld4cg(S.trr + o.c);
@@ -958,6 +1036,7 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         }
     }
     async_wait_all();
+    if (pml) __syncthreads();  // the profiles come from other threads
     // in place over this thread's slots (read by other threads only after
     // the barrier below); own C-PML nodes also update their adjoint memories
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
@@ -979,10 +1058,9 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
 #pragma unroll
             for (int e = 0; e < 4; ++e) x0[e] = x1[e] = w[e] = g.dt * bv.v[e] * av.v[e];
             if (pml && sl.off_o >= 0) {
-                const int ir = ii < 0 ? -ii : ii;
-                const float ari = __ldg(C.ar_int + ir), bri = __ldg(C.br_int + ir);
+                const float ari = sm.pf.r[2][r2], bri = sm.pf.r[3][r2];
                 const V4 p0 = lds4(s_x0, r2, c2), p1 = lds4(s_x1, r2, c2);
-                const V4 azi = ld4g(C.az_int + j), bzi = ld4g(C.bz_int + j);
+                const V4 azi = prof4(sm.pf.z[0], c2), bzi = prof4(sm.pf.z[1], c2);
                 if (own) {
                     float w0[4], w1[4];
 #pragma unroll
@@ -1012,10 +1090,9 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
 #pragma unroll
             for (int e = 0; e < 4; ++e) x2[e] = x3[e] = w[e] = g.dt * bv.v[e] * av.v[e];
             if (pml && sl.off_e >= 0) {
-                const int iz = ii < 0 ? -1 - ii : ii;
-                const float arh = __ldg(C.ar_half + iz), brh = __ldg(C.br_half + iz);
+                const float arh = sm.pf.r[0][r2], brh = sm.pf.r[1][r2];
                 const V4 p2 = lds4(s_x2, r2, c2), p3 = lds4(s_x3, r2, c2);
-                const V4 azh = ld4g(C.az_half + j), bzh = ld4g(C.bz_half + j);
+                const V4 azh = prof4(sm.pf.z[2], c2), bzh = prof4(sm.pf.z[3], c2);
                 if (own) {
                     float w2[4], w3[4];
 #pragma unroll
@@ -1040,9 +1117,8 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         }
     }
     __syncthreads();
-    if (!o.live) return;
     const int rr = o.rr, cc = o.cc, i = o.i, c = o.c;
-    {
+    if (o.live) {
         const V4 wr0 = lds4(s_wr, rr, cc), wrp1 = lds4(s_wr, rr + 1, cc);
         const V4 x0m1 = lds4(s_x0, rr - 1, cc), x00 = lds4(s_x0, rr, cc),
                  x0p1 = lds4(s_x0, rr + 1, cc), x0p2 = lds4(s_x0, rr + 2, cc);
@@ -1063,7 +1139,7 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         st4(S.ttt + c, o.j, g.nz, ttt);
         st4(S.tzz + c, o.j, g.nz, tzz);
     }
-    if (i >= 1) {
+    if (o.live && i >= 1) {
         const V12 x1r = lds12(s_x1, rr, cc - 4);
         const V4 x2m2 = lds4(s_x2, rr - 2, cc), x2m1 = lds4(s_x2, rr - 1, cc),
                  x20 = lds4(s_x2, rr, cc), x2p1 = lds4(s_x2, rr + 1, cc);
@@ -1079,6 +1155,10 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         }
         st4(S.trz + c, o.j, g.nz, trz);
     }
+    if (bar) grid_arrive(*bar, epoch);
+    // the next stress step's launch-invariant tiles: the copies run during
+    // the grid barrier
+    if (next_fcur) stage_adj_statics(sm, C, next_fcur, i0, j0, g);
 }
 
 // ------------------------------------------------ shots, tiles, runs
@@ -1146,25 +1226,31 @@ __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>
     fwd_stress_tile(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, tk.w, sm);
 }
 
+// statics / prefetch: the block keeps one tile for the whole run, so the
+// velocity step of reverse step n stages the stress step's launch-invariant
+// tiles for step n-1 (AdjSmem)
 template <int N>
 __device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>& T, int n,
-                                               int t, AdjSmem& sm)
+                                               int t, bool statics, const BarK* bar,
+                                               unsigned& epoch, AdjSmem& sm)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
     adj_stress_tile(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, n - r.hist_n0 + 1),
-                    hist_slot(sh, n - r.hist_n0), tk.y, tk.z, tk.w, sm);
+                    hist_slot(sh, n - r.hist_n0), tk.y, tk.z, tk.w, statics, bar, epoch, sm);
 }
 
 template <int N>
 __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
+                                            bool prefetch, const BarK* bar, unsigned& epoch,
                                             AdjSmem& sm)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
-    adj_vel_tile(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w, sm);
+    const float* next = prefetch ? hist_slot(sh, n - r.hist_n0) : nullptr;
+    adj_vel_tile(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w, next, bar, epoch, sm);
 }
 
 // one launch per half-step: one block per tile
@@ -1194,7 +1280,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n,
 {
     __shared__ AdjSmem sm;
     pdl_wait();
-    run_adj_stress(r, T, n, blockIdx.x, sm);
+    unsigned epoch = 0;
+    run_adj_stress(r, T, n, blockIdx.x, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1204,7 +1291,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
 {
     __shared__ AdjSmem sm;
     pdl_wait();
-    run_adj_vel(r, T, n, blockIdx.x, sm);
+    unsigned epoch = 0;
+    run_adj_vel(r, T, n, blockIdx.x, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1230,11 +1318,20 @@ __global__ void __launch_bounds__(kThreads, 5) k_adj_persist(RunK r, BarK b,
 {
     __shared__ AdjSmem sm;
     unsigned epoch = 0;
+    const bool one = r.ntiles <= (int)gridDim.x;  // at most one tile per block
+    const bool idle = (int)blockIdx.x >= r.ntiles;
     for (int n = r.n1 - 1; n >= r.n0; --n) {
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_adj_stress(r, T, n, t, sm);
-        if (!grid_barrier(b, epoch)) return;
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_adj_vel(r, T, n, t, sm);
-        if (!grid_barrier(b, epoch)) return;
+        // the block's last tile of a phase arrives at the barrier itself
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
+            run_adj_stress(r, T, n, t, one && n < r.n1 - 1,
+                           t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
+        if (idle) grid_arrive(b, epoch);
+        if (!grid_wait(b, epoch)) return;
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
+            run_adj_vel(r, T, n, t, one && n > r.n0,
+                        t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
+        if (idle) grid_arrive(b, epoch);
+        if (!grid_wait(b, epoch)) return;
     }
 }
 
