@@ -664,9 +664,8 @@ __device__ __forceinline__ void grid_arrive(const BarK& b, unsigned& epoch)
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         // an acq_rel atomic measured ~1 us faster per barrier than a
         // release reduction or a fence + relaxed atomic on GB300
-        unsigned old;
-        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(b.count) : "memory");
-        (void)old;
+        asm volatile("{\n\t.reg .u32 t;\n\tatom.add.acq_rel.gpu.u32 t, [%0], 1;\n}" ::"l"(b.count)
+                     : "memory");
     }
 }
 
