@@ -339,6 +339,78 @@ __device__ __forceinline__ Own own_of(const WinK& g, int i0, int j0)
     return o;
 }
 
+// ------------------------------------------------- bounded grid barrier
+
+struct BarK {
+    unsigned* count;               // arrivals since the launch began (monotonic)
+    int* err;                      // 1 once any wait gave up
+    unsigned expected;             // arrivals that complete one barrier
+    unsigned long long timeout_ns; // give up after this long
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All blocks of a cooperative launch meet at every barrier; `epoch` counts
+// the block's barriers (the same sequence in every block).  The barrier is
+// split in two: grid_arrive publishes the block's writes with one
+// release-acquire increment of a monotonic counter; grid_wait polls it with acquire loads
+// until it reaches epoch * expected.  Between the two a block may do work
+// that no other block reads in the next phase (its own accumulators), which
+// then overlaps the barrier latency.  The wait is bounded twice, by the wall
+// clock and by a poll count; when it runs out, or another block reports that
+// it did, grid_wait returns false in every thread of the block, the caller
+// returns from the kernel, and the host reads the error flag.  Writes before
+// the arrival are visible to ld.global.cg loads and cp.async.cg copies after
+// the wait.  Both halves are called by every thread of the block.
+__device__ __forceinline__ void grid_arrive(const BarK& b, unsigned& epoch)
+{
+    __syncthreads();
+    ++epoch;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        // an acq_rel atomic measured ~1 us faster per barrier than a
+        // release reduction or a fence + relaxed atomic on GB300
+        asm volatile("{\n\t.reg .u32 t;\n\tatom.add.acq_rel.gpu.u32 t, [%0], 1;\n}" ::"l"(b.count)
+                     : "memory");
+    }
+}
+
+__device__ bool grid_wait(const BarK& b, unsigned epoch)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const unsigned target = epoch * b.expected;
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        // every poll is an L2 round trip (>= 64 ns); the error flag and the
+        // clock are checked every 8th poll
+        const unsigned long long max_polls = b.timeout_ns / 64ull + 1024ull;
+        unsigned long long polls = 0;
+        volatile int* verr = b.err;
+        for (;;) {
+            unsigned cur;
+            asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(b.count) : "memory");
+            if (cur >= target) break;
+            if ((++polls & 7ull) == 0) {
+                if (*verr) { ok = 0; break; }
+                if (global_ns() - t0 > b.timeout_ns || polls > max_polls) {
+                    atomicExch(b.err, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        if (ok && *verr) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // ------------------------------------------------------- forward: Eq. 2
 
 struct SrcRecK {
@@ -359,7 +431,8 @@ struct __align__(16) FwdSmem {
 // 0..3.  Own-node inputs are loaded before the staging, so the tile pays
 // one round trip to L2.  hist0 (or null): history slot receiving v^{n-1/2}.
 __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                             float* hist0, int i0, int j0, int flags, FwdSmem& sm)
+                                             float* hist0, int i0, int j0, int flags,
+                                             const BarK* bar, unsigned& epoch, FwdSmem& sm)
 {
     Tile &s_rr = sm.a, &s_tt = sm.b, &s_rz = sm.c, &s_zz = sm.d;
     const Own o = own_of(g, i0, j0);
@@ -401,7 +474,7 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
         }
     }
     __syncthreads();
-    if (!o.live) return;
+    if (o.live) {
     if (pml) {
         arh = sm.pf.r[0][o.rr];
         brh = sm.pf.r[1][o.rr];
@@ -478,7 +551,9 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
             st4(S.psi_w[3] + o.c, o.j, g.nz, w3);
         }
     }
-    if (hist0) {
+    }
+    if (bar) grid_arrive(*bar, epoch);
+    if (o.live && hist0) {
         st4(hist0 + o.c, o.j, g.nz, vr0.v);
         st4(hist0 + g.nr * g.P + o.c, o.j, g.nz, vz0.v);
     }
@@ -490,7 +565,7 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
 __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const SrcRecK& q, int n, bool record,
                                                 float* hist, int i0, int j0, int flags,
-                                                FwdSmem& sm)
+                                                const BarK* bar, unsigned& epoch, FwdSmem& sm)
 {
     Tile &s_vr = sm.a, &s_vz = sm.b;
     const Own o = own_of(g, i0, j0);
@@ -528,9 +603,8 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         }
     }
     __syncthreads();
-    if (!o.live) return;
     const int rr = o.rr, cc = o.cc;
-    {
+    if (o.live) {
         if (pml) {
             arh = sm.pf.r[0][rr];
             brh = sm.pf.r[1][rr];
@@ -583,7 +657,7 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
             st4(S.psi_w[5] + o.c, o.j, g.nz, w5);
         }
     }
-    if (o.i >= 1) {
+    if (o.live && o.i >= 1) {
         float ari = 0.f, bri = 0.f;
         V4 azh{}, bzh{}, q6{}, q7{};
         if (pml) {
@@ -622,89 +696,13 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
             if (ari != 0.f) st4(S.psi_w[7] + o.c, o.j, g.nz, w7);
         }
     }
-    if (hist) {
+    // the history is read only by the adjoint, after this launch
+    if (bar) grid_arrive(*bar, epoch);
+    if (o.live && hist) {
         const V4 a = lds4(s_vr, rr, cc), b = lds4(s_vz, rr, cc);
         st4(hist + o.c, o.j, g.nz, a.v);
         st4(hist + g.nr * g.P + o.c, o.j, g.nz, b.v);
     }
-}
-
-// ------------------------------------------------- bounded grid barrier
-
-struct BarK {
-    unsigned* count;               // arrivals since the launch began (monotonic)
-    int* err;                      // 1 once any wait gave up
-    unsigned expected;             // arrivals that complete one barrier
-    unsigned long long timeout_ns; // give up after this long
-};
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// All blocks of a cooperative launch meet at every barrier; `epoch` counts
-// the block's barriers (the same sequence in every block).  The barrier is
-// split in two: grid_arrive publishes the block's writes with one
-// release-acquire increment of a monotonic counter; grid_wait polls it with acquire loads
-// until it reaches epoch * expected.  Between the two a block may do work
-// that no other block reads in the next phase (its own accumulators), which
-// then overlaps the barrier latency.  The wait is bounded twice, by the wall
-// clock and by a poll count; when it runs out, or another block reports that
-// it did, grid_wait returns false in every thread of the block, the caller
-// returns from the kernel, and the host reads the error flag.  Writes before
-// the arrival are visible to ld.global.cg loads and cp.async.cg copies after
-// the wait.  Both halves are called by every thread of the block.
-__device__ __forceinline__ void grid_arrive(const BarK& b, unsigned& epoch)
-{
-    __syncthreads();
-    ++epoch;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        // an acq_rel atomic measured ~1 us faster per barrier than a
-        // release reduction or a fence + relaxed atomic on GB300
-        asm volatile("{\n\t.reg .u32 t;\n\tatom.add.acq_rel.gpu.u32 t, [%0], 1;\n}" ::"l"(b.count)
-                     : "memory");
-    }
-}
-
-__device__ bool grid_wait(const BarK& b, unsigned epoch)
-{
-    __shared__ int s_ok;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const unsigned target = epoch * b.expected;
-        int ok = 1;
-        const unsigned long long t0 = global_ns();
-        // every poll is an L2 round trip (>= 64 ns); the error flag and the
-        // clock are checked every 8th poll
-        const unsigned long long max_polls = b.timeout_ns / 64ull + 1024ull;
-        unsigned long long polls = 0;
-        volatile int* verr = b.err;
-        for (;;) {
-            unsigned cur;
-            asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(b.count) : "memory");
-            if (cur >= target) break;
-            if ((++polls & 7ull) == 0) {
-                if (*verr) { ok = 0; break; }
-                if (global_ns() - t0 > b.timeout_ns || polls > max_polls) {
-                    atomicExch(b.err, 1);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        if (ok && *verr) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-__device__ __forceinline__ bool grid_barrier(const BarK& b, unsigned& epoch)
-{
-    grid_arrive(b, epoch);
-    return grid_wait(b, epoch);
 }
 
 // ------------------------------------------ adjoint: transpose of Eq. 2
@@ -1207,22 +1205,24 @@ __device__ __forceinline__ const ShotK& shot_of(const ShotTable<N>& T, int4 tk)
 
 template <int N>
 __device__ __forceinline__ void run_fwd_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
-                                            FwdSmem& sm)
+                                            const BarK* bar, unsigned& epoch, FwdSmem& sm)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     float* h0 = (r.hist_n0 >= 0 && n == r.hist_n0) ? hist_slot(sh, 0) : nullptr;
-    fwd_vel_tile(sh.g, sh.C, sh.Sf, h0, tk.y, tk.z, tk.w, sm);
+    fwd_vel_tile(sh.g, sh.C, sh.Sf, h0, tk.y, tk.z, tk.w, bar, epoch, sm);
 }
 
 template <int N>
 __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>& T, int n,
-                                               int t, FwdSmem& sm)
+                                               int t, const BarK* bar, unsigned& epoch,
+                                               FwdSmem& sm)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     float* h = r.hist_n0 >= 0 ? hist_slot(sh, n - r.hist_n0 + 1) : nullptr;
-    fwd_stress_tile(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, tk.w, sm);
+    fwd_stress_tile(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, tk.w, bar, epoch,
+                    sm);
 }
 
 // statics / prefetch: the block keeps one tile for the whole run, so the
@@ -1259,7 +1259,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_vel(RunK r, int n,
 {
     __shared__ FwdSmem sm;
     pdl_wait();
-    run_fwd_vel(r, T, n, blockIdx.x, sm);
+    unsigned epoch = 0;
+    run_fwd_vel(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1269,7 +1270,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_stress(RunK r, int n,
 {
     __shared__ FwdSmem sm;
     pdl_wait();
-    run_fwd_stress(r, T, n, blockIdx.x, sm);
+    unsigned epoch = 0;
+    run_fwd_stress(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1302,11 +1304,17 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(RunK r, BarK b,
 {
     __shared__ FwdSmem sm;
     unsigned epoch = 0;
+    const bool idle = (int)blockIdx.x >= r.ntiles;
     for (int n = r.n0; n < r.n1; ++n) {
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_fwd_vel(r, T, n, t, sm);
-        if (!grid_barrier(b, epoch)) return;
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) run_fwd_stress(r, T, n, t, sm);
-        if (!grid_barrier(b, epoch)) return;
+        // the block's last tile of a phase arrives at the barrier itself
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
+            run_fwd_vel(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
+        if (idle) grid_arrive(b, epoch);
+        if (!grid_wait(b, epoch)) return;
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
+            run_fwd_stress(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
+        if (idle) grid_arrive(b, epoch);
+        if (!grid_wait(b, epoch)) return;
     }
 }
 
