@@ -1,0 +1,151 @@
+"""Checks at the benchmark workloads' full spatial sizes, in the launch
+configuration bench.py times (one persistent cooperative launch per run over
+the production shot's 750 tiles).
+
+- The production shot (240 x 1600 cells) against the FP64 oracle element by
+  element, with the run shortened to 450 steps and the receivers moved to
+  0.1-0.4 m from the source so that the waves reach them (the tile table,
+  grid and kernels are the same as in the 8000-step run).  The data are
+  zero, so the adjoint source is the whole seismogram: with near receivers
+  and a short run the damage-zone residual would be a small difference of
+  nearly equal traces, whose relative error is the seismogram's relative
+  error (1e-5) times their ratio.
+- The full 8000-step run: the adjoint gradient against a central difference
+  of the forward misfit along a random direction (a property of the exact
+  discrete adjoint at any size), and two runs bit for bit.
+- The 400 x 4000 shot under a checkpoint byte cap against storing every step
+  (bit for bit), shortened to 1000 steps.
+"""
+import numpy as np
+import pytest
+
+from synthetic import PRESETS
+from tests.gpu_common import gpu_gradient, oracle_gradient, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_00281_gb300.bh import load_library
+    load_library()
+    return torch
+
+
+def _shortened_c1(nt):
+    w = PRESETS["c1"](seed=0)
+    w.nt = nt
+    w.wavelet = np.ascontiguousarray(w.wavelet[:nt])
+    src = w.shots[0]["src"][1]
+    w.shots[0]["rec_iz"] = [src + 20 * k for k in range(1, 5)]
+    return w
+
+
+def test_c1_window_parity(cuda, orc):
+    w = _shortened_c1(450)
+    obs = np.zeros((1, len(w.shots[0]["rec_iz"]), w.nt))
+    m, gpu = gpu_gradient(w, obs)
+    assert m.info("tiles") == 750 and m.info("persistent") == 1
+    m.close()
+    ref = oracle_gradient(w, obs)
+    assert np.abs(ref["seis"][0]).max() > 0
+    assert rel_l2(gpu["seis"][0], ref["seis"][0]) <= 1e-5
+    assert abs(gpu["J"] - ref["J"]) <= 1e-5 * ref["J"]
+    for k in ("g_lam", "g_mu", "g_rho", "H_lam", "H_mu"):
+        e = rel_l2(gpu[k], ref[k])
+        assert e <= 1e-4, (k, e)
+
+
+def _c1_run(torch, m, w, obs, wav):
+    seis = m.forward(wav)
+    resid, J = m.residual_misfit(seis, obs)
+    g = m.adjoint_gradient(resid)
+    torch.cuda.synchronize()
+    return J, [x.clone() for x in g]
+
+
+def test_c1_full_run_gradient_and_determinism(cuda):
+    """8000 steps on 240 x 1600 cells: <g, dm> against (J(m + h dm) -
+    J(m - h dm)) / 2h for a smooth random change of lambda and mu in the
+    formation, and a second run identical bit for bit."""
+    torch = cuda
+    from paper_2005_00281_gb300.bh import model_from_workload
+
+    w = PRESETS["c1"](seed=0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    truth = model_from_workload(w)
+    truth.set_model(t(w.vp_true), t(w.vs_true), t(w.rho_true))
+    wav = t(w.wavelet)
+    obs = truth.forward(wav).clone()
+    truth.close()
+    m = model_from_workload(w)
+    assert m.info("tiles") == 750 and m.info("persistent") == 1
+    J0, g = _c1_run(torch, m, w, obs, wav)
+    J0b, g_b = _c1_run(torch, m, w, obs, wav)
+    assert J0 == J0b
+    for a, b in zip(g, g_b):
+        assert torch.equal(a, b)
+    # smooth direction in (lambda, mu) on formation cells away from the layers
+    rng = np.random.default_rng(7)
+    nr, nz = w.nr, w.nz
+    ii, jj = np.meshgrid(np.arange(nr), np.arange(nz), indexing="ij")
+    dm = np.zeros((nr, nz))
+    for _ in range(6):
+        ci, cj = rng.uniform(30, nr - w.npml_r - 30), rng.uniform(w.npml_z + 60, nz - w.npml_z - 60)
+        dm += rng.normal() * np.exp(-((ii - ci) ** 2 / 200.0 + (jj - cj) ** 2 / 800.0))
+    dm[w.vs <= 0] = 0.0
+    dm[nr - w.npml_r:, :] = 0.0
+    dm[:, : w.npml_z] = 0.0
+    dm[:, nz - w.npml_z:] = 0.0
+    lam = w.rho * (w.vp ** 2 - 2 * w.vs ** 2)
+    mu = w.rho * w.vs ** 2
+    dlam, dmu = 0.5 * lam * dm, 0.5 * mu * dm
+    pred = float((g[0].cpu().numpy() * dlam).sum() + (g[1].cpu().numpy() * dmu).sum())
+    vals = []
+    h = 1e-3
+    for sgn in (1, -1):
+        lam2, mu2 = lam + sgn * h * dlam, mu + sgn * h * dmu
+        vs2 = np.sqrt(np.maximum(mu2, 0) / w.rho)
+        vp2 = np.sqrt((lam2 + 2 * mu2) / w.rho)
+        m.set_model(t(vp2.astype(np.float32)), t(vs2.astype(np.float32)), t(w.rho))
+        seis = m.forward(wav)
+        _, J = m.residual_misfit(seis, obs)
+        vals.append(J)
+    fd = (vals[0] - vals[1]) / (2 * h)
+    m.close()
+    assert abs(pred) > 0
+    assert abs(fd - pred) <= 2e-2 * abs(pred), (fd, pred)
+
+
+@pytest.mark.parametrize("prec", [0])
+def test_c3_checkpointed_matches_store_all(cuda, prec):
+    torch = cuda
+    from paper_2005_00281_gb300.bh import model_from_workload
+
+    w = PRESETS["c3"](seed=0)
+    nt = 1000
+    w.nt = nt
+    w.wavelet = np.ascontiguousarray(w.wavelet[:nt])
+    src = w.shots[0]["src"][1]
+    w.shots[0]["rec_iz"] = [src + 20 * k for k in range(1, 5)]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    wav = t(w.wavelet)
+    out = []
+    for cap in (0, 400 << 20):
+        m = model_from_workload(w, checkpoint_cap_bytes=cap, snapshot_precision=prec)
+        if cap:
+            assert m.info("recompute_steps") > 0
+        seis = m.forward(wav)
+        obs = torch.zeros_like(seis)
+        resid, J = m.residual_misfit(seis, obs)
+        g = m.adjoint_gradient(resid)
+        torch.cuda.synchronize()
+        out.append((J, [x.cpu() for x in g], seis.cpu()))
+        m.close()
+    assert out[0][0] == out[1][0]
+    assert torch.equal(out[0][2], out[1][2])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert torch.equal(a, b)
