@@ -248,8 +248,9 @@ bh_status bh_profile_reset(bh_model* model);
 /*
  * Residual and misfit without any device allocation (the paper has no
  * counterpart; this is a service for callers that may not allocate device
- * memory, for example code running under stream capture or inside a
- * process whose device memory is owned by another allocator).  Computes
+ * memory: processes whose device memory is owned by another allocator or
+ * fixed at start-up, and serving paths that forbid allocation, which can
+ * synchronise the device, after warm-up).  Computes
  * exactly what bh_residual_misfit computes, Delta p = p_mod - p_mes and
  * J = 1/2 ||Delta p||^2 in FP64, but needs no bh_model: its scratch is a
  * fixed 64 KB array inside the library, present on every GPU that loads

@@ -2,10 +2,10 @@
 // bh_residual_misfit for callers that cannot allocate device memory.
 //
 // Why: bh_residual_misfit needs a bh_model, and building one calls
-// cudaMalloc.  Some callers may not allocate at all: code that runs while a
-// stream is being captured into a CUDA graph, processes whose device memory
-// is fixed up front by another allocator (a framework's pool, or a budget
-// set at start-up), and serving paths that forbid allocation after warm-up.
+// cudaMalloc.  Some callers may not allocate at all: processes whose device
+// memory is fixed up front by another allocator (a framework's pool, or a
+// budget set at start-up), and serving paths that forbid allocation after
+// warm-up because an allocation can synchronise the device.
 // This entry point takes only the caller's buffers and keeps its FP64
 // partial sums in a file-scope __device__ array instead.
 //

@@ -1,8 +1,8 @@
 """bh_residual_misfit_noalloc against bh_residual_misfit, through the C ABI.
 
 The allocation-free entry point serves callers that may not allocate device
-memory (for example while a stream is being captured, or when another
-allocator owns the device memory).  It must give what the model-based entry
+memory (another allocator owns the device memory, or allocation is forbidden
+after warm-up because it can synchronise the device).  It must give what the model-based entry
 point gives on the same inputs: the same residual (one FP32 subtraction per
 sample, so bit-identical) and the same FP64 misfit up to summation order.
 Two calls in a row check that the shared scratch left by the first call does
