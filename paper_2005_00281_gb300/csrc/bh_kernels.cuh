@@ -768,16 +768,62 @@ __device__ __forceinline__ float2 kahan_step(float2 s, float x)
 // S.{trr..trz} hold dJ/dtau^{n+1}; S.{vr,vz} accumulate to dJ/dv^{n+1/2};
 // psi[4..7] are the adjoint memories read side, psi_w[4..7] the write side.
 // fcur: v_r, v_z planes of v^{n+1/2}; fprev: those of v^{n-1/2}.
+// Density and shear-mu correlations (Eq. 8 and the density term) and the
+// shear pseudo-Hessian at one tile's own nodes for reverse step n, from the
+// staged forward velocities v^{n+1/2} (fr, fz), v^{n-1/2} (fprev), the own
+// adjoint velocities Av^{n+1/2} and the own adjoint trz of step n+1.
+__device__ __forceinline__ void adj_corr_shear(const WinK& g, const AdjK& q, const Own& o,
+                                               const float* fprev, const Tile& T_fr,
+                                               const Tile& T_fz, const V4& Arz,
+                                               const float (&avz)[4], const float (&avr)[4])
+{
+    const int plane = g.nr * g.P, c = o.c, rr = o.rr, cc = o.cc, i = o.i;
+    const float dt = g.dt;
+    float2 gbz[4], gmr[4], gbr[4];
+    ld4f2(q.G_bz + c, gbz);
+    const V4 pz = ld4cg(fprev + plane + c);
+    V4 hmr{}, pr{};
+    if (i >= 1) {
+        ld4f2(q.G_murz + c, gmr);
+        hmr = ld4cg(q.H_murz + c);
+        pr = ld4cg(fprev + c);
+        ld4f2(q.G_br + c, gbr);
+    }
+    const V4 fz0 = lds4(T_fz, rr, cc);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) gbz[e] = kahan_step(gbz[e], (fz0.v[e] - pz.v[e]) * avz[e]);
+    st4f2(q.G_bz + c, o.j, g.nz, gbz);
+    if (i >= 1) {
+        const V12 fr12 = lds12(T_fr, rr, cc - 4);
+        const V4 fzm1 = lds4(T_fz, rr - 1, cc), fzm2 = lds4(T_fz, rr - 2, cc),
+                 fzp1 = lds4(T_fz, rr + 1, cc);
+        float hmr2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float gam =
+                d4(fr12.v[5 + e], fr12.v[4 + e], fr12.v[6 + e], fr12.v[3 + e]) * g.inv_dz +
+                d4(fz0.v[e], fzm1.v[e], fzp1.v[e], fzm2.v[e]) * g.inv_dr;
+            gmr[e] = kahan_step(gmr[e], dt * gam * Arz.v[e]);
+            hmr2[e] = hmr.v[e] + dt * gam * gam;
+            gbr[e] = kahan_step(gbr[e], (fr12.v[4 + e] - pr.v[e]) * avr[e]);
+        }
+        st4f2(q.G_murz + c, o.j, g.nz, gmr);
+        st4(q.H_murz + c, o.j, g.nz, hmr2);
+        st4f2(q.G_br + c, o.j, g.nz, gbr);
+    }
+}
+
 // statics: the f tiles were staged by the preceding velocity step.
+// defer: adj_corr_shear runs in the velocity step of the same reverse step
+// (the block keeps this tile, so the f tiles are still in shared memory).
 // bar (or null): the block arrives at the grid barrier once the adjoint
 // velocities are stored; the own-node correlations follow the arrival.
 __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const AdjK& q, const float* fcur,
                                                 const float* fprev, int i0, int j0, int flags,
-                                                bool statics, const BarK* bar, unsigned& epoch,
-                                                AdjSmem& sm)
+                                                bool statics, bool defer, const BarK* bar,
+                                                unsigned& epoch, AdjSmem& sm)
 {
-    const int plane = g.nr * g.P;
     const float dt = g.dt;
     const Own o = own_of(g, i0, j0);
     const bool pml = flags & TILE_PML;
@@ -924,13 +970,11 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     if (bar) grid_arrive(*bar, epoch);
     if (!o.live) return;
 
-    // ---- correlations (Eq. 7, Eq. 8, density) and pseudo-Hessian, own nodes
-    float2 gl[4], gm[4], gbz[4];
+    // ---- lambda and normal-mu correlations (Eq. 7, Eq. 8) and pseudo-Hessian
+    float2 gl[4], gm[4];
     ld4f2(q.G_lam + c, gl);
     ld4f2(q.G_munn + c, gm);
     const V4 hl = ld4cg(q.H_lam + c), hm = ld4cg(q.H_munn + c);
-    ld4f2(q.G_bz + c, gbz);
-    const V4 pz = ld4cg(fprev + plane + c);
     float hl2[4], hm2[4];
     {
         const V12 fr12 = lds12(T_fr, rr, cc - 4), fz12 = lds12(T_fz, rr, cc - 4);
@@ -948,41 +992,13 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
             gm[e] = kahan_step(gm[e], 2.f * dt * (err * Arr.v[e] + ett * Att.v[e] + ezz * Azz.v[e]));
             hl2[e] = hl.v[e] + dt * div * div;
             hm2[e] = hm.v[e] + 4.f * dt * (err * err + ett * ett + ezz * ezz);
-            gbz[e] = kahan_step(gbz[e], (fz12.v[4 + e] - pz.v[e]) * avz[e]);
         }
-    }
-    float2 gmr[4], gbr[4];
-    V4 hmr{}, pr{};
-    if (i >= 1) {
-        ld4f2(q.G_murz + c, gmr);
-        hmr = ld4cg(q.H_murz + c);
-        pr = ld4cg(fprev + c);
-        ld4f2(q.G_br + c, gbr);
     }
     st4f2(q.G_lam + c, o.j, g.nz, gl);
     st4f2(q.G_munn + c, o.j, g.nz, gm);
     st4(q.H_lam + c, o.j, g.nz, hl2);
     st4(q.H_munn + c, o.j, g.nz, hm2);
-    st4f2(q.G_bz + c, o.j, g.nz, gbz);
-    if (i >= 1) {
-        const V12 fr12 = lds12(T_fr, rr, cc - 4);
-        const V4 fz0 = lds4(T_fz, rr, cc), fzm1 = lds4(T_fz, rr - 1, cc),
-                 fzm2 = lds4(T_fz, rr - 2, cc), fzp1 = lds4(T_fz, rr + 1, cc);
-        const V4 Arz = lds4(T_rz, rr, cc);
-        float hmr2[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float gam =
-                d4(fr12.v[5 + e], fr12.v[4 + e], fr12.v[6 + e], fr12.v[3 + e]) * g.inv_dz +
-                d4(fz0.v[e], fzm1.v[e], fzp1.v[e], fzm2.v[e]) * g.inv_dr;
-            gmr[e] = kahan_step(gmr[e], dt * gam * Arz.v[e]);
-            hmr2[e] = hmr.v[e] + dt * gam * gam;
-            gbr[e] = kahan_step(gbr[e], (fr12.v[4 + e] - pr.v[e]) * avr[e]);
-        }
-        st4f2(q.G_murz + c, o.j, g.nz, gmr);
-        st4(q.H_murz + c, o.j, g.nz, hmr2);
-        st4f2(q.G_br + c, o.j, g.nz, gbr);
-    }
+    if (!defer) adj_corr_shear(g, q, o, fprev, T_fr, T_fz, lds4(T_rz, rr, cc), avz, avr);
 }
 
 // Transpose of the velocity step of one tile at reverse step n: S.{vr,vz}
@@ -991,11 +1007,12 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
 // recording).
 // next_fcur (or null): v^{n-1/2}, whose stress step (reverse step n-1) runs
 // next on this tile; its launch-invariant tiles are staged here, after the
-// block's arrival at the grid barrier (bar, or null: no barrier).
+// block's arrival at the grid barrier (bar, or null: no barrier), and after
+// the correlations deferred by the stress step (fprev_b, or null).
 __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
                                              const AdjK& q, int n, int i0, int j0, int flags,
-                                             const float* next_fcur, const BarK* bar,
-                                             unsigned& epoch, AdjSmem& sm)
+                                             const float* next_fcur, const float* fprev_b,
+                                             const BarK* bar, unsigned& epoch, AdjSmem& sm)
 {
     // W = dt b Av at the velocity nodes (odd about the axis for v_r, even
     // for v_z) and the coefficients on the four stretched derivatives
@@ -1153,6 +1170,17 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         st4(S.trz + c, o.j, g.nz, trz);
     }
     if (bar) grid_arrive(*bar, epoch);
+    // fprev_b (or null): v^{n-1/2}; the stress step deferred its density and
+    // shear correlations to here (own nodes only: no other block reads them)
+    if (fprev_b) {
+        if (o.live) {
+            const V4 az = ld4cg(S.vz + c);
+            V4 ar{};
+            if (i >= 1) ar = ld4cg(S.vr + c);
+            adj_corr_shear(g, q, o, fprev_b, sm.f[0], sm.f[1], o_rz, az.v, ar.v);
+        }
+        __syncthreads();  // the f tiles are read above and refilled below
+    }
     // the next stress step's launch-invariant tiles: the copies run during
     // the grid barrier
     if (next_fcur) stage_adj_statics(sm, C, next_fcur, i0, j0, g);
@@ -1230,26 +1258,29 @@ __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>
 // tiles for step n-1 (AdjSmem)
 template <int N>
 __device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>& T, int n,
-                                               int t, bool statics, const BarK* bar,
-                                               unsigned& epoch, AdjSmem& sm)
+                                               int t, bool statics, bool defer,
+                                               const BarK* bar, unsigned& epoch, AdjSmem& sm)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
     adj_stress_tile(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, n - r.hist_n0 + 1),
-                    hist_slot(sh, n - r.hist_n0), tk.y, tk.z, tk.w, statics, bar, epoch, sm);
+                    hist_slot(sh, n - r.hist_n0), tk.y, tk.z, tk.w, statics, defer, bar, epoch,
+                    sm);
 }
 
 template <int N>
 __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
-                                            bool prefetch, const BarK* bar, unsigned& epoch,
-                                            AdjSmem& sm)
+                                            bool prefetch, bool deferred, const BarK* bar,
+                                            unsigned& epoch, AdjSmem& sm)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
-    const float* next = prefetch ? hist_slot(sh, n - r.hist_n0) : nullptr;
-    adj_vel_tile(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w, next, bar, epoch, sm);
+    // v^{n-1/2}: fcur of step n-1 (prefetch) and fprev of step n (deferred)
+    const float* prev = hist_slot(sh, n - r.hist_n0);
+    adj_vel_tile(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w, prefetch ? prev : nullptr,
+                 deferred ? prev : nullptr, bar, epoch, sm);
 }
 
 // one launch per half-step: one block per tile
@@ -1282,7 +1313,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n,
     __shared__ AdjSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_adj_stress(r, T, n, blockIdx.x, false, nullptr, epoch, sm);
+    run_adj_stress(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1293,7 +1324,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
     __shared__ AdjSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_adj_vel(r, T, n, blockIdx.x, false, nullptr, epoch, sm);
+    run_adj_vel(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1330,12 +1361,12 @@ __global__ void __launch_bounds__(kThreads, 5) k_adj_persist(RunK r, BarK b,
     for (int n = r.n1 - 1; n >= r.n0; --n) {
         // the block's last tile of a phase arrives at the barrier itself
         for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_adj_stress(r, T, n, t, one && n < r.n1 - 1,
+            run_adj_stress(r, T, n, t, one && n < r.n1 - 1, one,
                            t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
         for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_adj_vel(r, T, n, t, one && n > r.n0,
+            run_adj_vel(r, T, n, t, one && n > r.n0, one,
                         t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
