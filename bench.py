@@ -221,6 +221,35 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------- multi-rank host logic
+#
+# With N > 1 every rank inverts its own independent shot of the same sizes
+# (seed = rank): the path shards by shots with no data-path collective.  The
+# barrier and the max over ranks serve the timing only; the job's value is
+# the cells of all ranks over the slowest rank's time.
+
+def rank_workload(config: str, rank: int):
+    """The workload rank `rank` inverts: the named preset, seeded by rank."""
+    from synthetic import PRESETS
+    return PRESETS[config](seed=rank)
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over the ranks of the default process group."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(cells_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job Gcell-updates/s: every rank's cells over the max-over-ranks time."""
+    return world * cells_per_rank / (ms / 1e3) / 1e9
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_gpu(args, w):
@@ -244,8 +273,7 @@ def run_gpu(args, w):
 
     if world > 1 and rank > 0:
         # every rank inverts its own independent shot: same sizes, other seed
-        from synthetic import PRESETS
-        w = PRESETS[args.config](seed=rank)
+        w = rank_workload(args.config, rank)
 
     stream = torch.cuda.current_stream(dev)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -290,13 +318,6 @@ def run_gpu(args, w):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        tt = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
-
     # ---- device-resident inputs
     for _ in range(args.warmup):
         step(wav, obs)
@@ -315,7 +336,7 @@ def run_gpu(args, w):
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     prof = m.profile_read()
     m.profile(0)
 
@@ -340,14 +361,14 @@ def run_gpu(args, w):
     f1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = max_over_ranks(f0.elapsed_time(f1))
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1), world, dev)
     h2d = wav_h.numel() * 4 + obs_h.numel() * 4
     d2h = 8 + vp_h.numel() * 4 * 2
 
     cells_per_step = 2.0 * w.cell_steps()          # forward + adjoint cell updates (useful work)
-    value = world * cells_per_step * args.steps / (ms / 1e3) / 1e9
+    value = job_rate(cells_per_step * args.steps, world, ms)
     grads_per_s = world * w.nshots * args.steps / (ms / 1e3)
-    value_e2e = world * cells_per_step * args.steps / (ms_e2e / 1e3) / 1e9
+    value_e2e = job_rate(cells_per_step * args.steps, world, ms_e2e)
 
     # ---- roofline of the dominant kernel (largest sampled time)
     peak, peak_kind = measured_peaks()
@@ -418,7 +439,7 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -434,7 +455,11 @@ def main():
                     help="one kernel launch per half-step instead of the persistent kernels")
     ap.add_argument("--nt", type=int, default=None,
                     help="override the step count (small cases for ncu captures only)")
-    args = ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def main():
+    args = parse_args()
     from synthetic import PRESETS, ricker
     w = PRESETS[args.config](seed=0)
     if args.nt:
