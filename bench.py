@@ -273,7 +273,7 @@ def run_gpu(args, w):
 
     if world > 1 and rank > 0:
         # every rank inverts its own independent shot: same sizes, other seed
-        w = rank_workload(args.config, rank)
+        w = apply_overrides(rank_workload(args.config, rank), args)
 
     stream = torch.cuda.current_stream(dev)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -439,6 +439,17 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+def apply_overrides(w, args):
+    """--nt and --shots applied to a workload (every rank applies the same)."""
+    from synthetic import ricker
+    if args.nt:
+        w.nt = args.nt
+        w.wavelet = ricker(w.nt, w.dt, w.f0)
+    if args.shots:
+        w.shots = w.shots[: args.shots]
+    return w
+
+
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -455,16 +466,16 @@ def parse_args(argv=None):
                     help="one kernel launch per half-step instead of the persistent kernels")
     ap.add_argument("--nt", type=int, default=None,
                     help="override the step count (small cases for ncu captures only)")
+    ap.add_argument("--shots", type=int, default=None,
+                    help="keep only the first K shots of a batched workload (a sub-batch)")
     return ap.parse_args(argv)
 
 
 def main():
     args = parse_args()
-    from synthetic import PRESETS, ricker
+    from synthetic import PRESETS
     w = PRESETS[args.config](seed=0)
-    if args.nt:
-        w.nt = args.nt
-        w.wavelet = ricker(w.nt, w.dt, w.f0)
+    apply_overrides(w, args)
     if args.impl == "reference":
         run_reference(args, w)
     else:
