@@ -160,9 +160,13 @@ class ClockSampler:
 
 
 def workload_config(w, nt=None):
-    shots = (f"{w.nshots} shots, windows nz {min(s['nz'] for s in w.shots)}-"
-             f"{max(s['nz'] for s in w.shots)} of a {w.nz}-cell model" if w.nshots > 1
-             else f"single shot, nz {w.nz}")
+    if w.nshots > 1:
+        shots = (f"{w.nshots} shots, windows nz {min(s['nz'] for s in w.shots)}-"
+                 f"{max(s['nz'] for s in w.shots)} of a {w.nz}-cell model")
+    elif w.shots[0]["nz"] != w.nz:
+        shots = f"single shot, window nz {w.shots[0]['nz']} of a {w.nz}-cell model"
+    else:
+        shots = f"single shot, nz {w.nz}"
     return {"workload": f"{w.name}: borehole FWI iteration, {shots}, nr {w.nr} "
                         f"(C-PML {w.npml_r}/{w.npml_z}), {nt or w.nt} steps, "
                         f"h {w.dr} m, dt {w.dt} s, f0 {w.f0:g} Hz, {w.nrec} receivers",
@@ -446,7 +450,7 @@ def apply_overrides(w, args):
         w.nt = args.nt
         w.wavelet = ricker(w.nt, w.dt, w.f0)
     if args.shots:
-        w.shots = w.shots[: args.shots]
+        w.shots = w.shots[args.first_shot: args.first_shot + args.shots]
     return w
 
 
@@ -467,7 +471,9 @@ def parse_args(argv=None):
     ap.add_argument("--nt", type=int, default=None,
                     help="override the step count (small cases for ncu captures only)")
     ap.add_argument("--shots", type=int, default=None,
-                    help="keep only the first K shots of a batched workload (a sub-batch)")
+                    help="keep K shots of a batched workload (a sub-batch), from --first-shot")
+    ap.add_argument("--first-shot", type=int, default=0,
+                    help="index of the first shot kept by --shots")
     return ap.parse_args(argv)
 
 
