@@ -579,7 +579,7 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     if (pml) stage_prof(sm.pf, C, g, i0, j0);
     V4 t_rr{}, t_tt{}, t_zz{}, lm{}, mu{}, t_rz{}, mh{};
     float arh = 0.f, brh = 0.f;
-    V4 azi{}, bzi{}, q4{}, q5{};
+    V4 azi{}, bzi{}, q4{}, q5{}, q6{}, q7{};
     if (o.live) {
         t_rr = ld4cg(S.trr + o.c);
         t_tt = ld4cg(S.ttt + o.c);
@@ -593,6 +593,10 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         if (pml) {
             q4 = ld4cg(S.psi[4] + o.c);
             q5 = ld4cg(S.psi[5] + o.c);
+            if (o.i >= 1) {
+                q6 = ld4cg(S.psi[6] + o.c);
+                q7 = ld4cg(S.psi[7] + o.c);
+            }
         }
     }
     async_wait_all();
@@ -659,14 +663,12 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     }
     if (o.live && o.i >= 1) {
         float ari = 0.f, bri = 0.f;
-        V4 azh{}, bzh{}, q6{}, q7{};
+        V4 azh{}, bzh{};
         if (pml) {
             ari = sm.pf.r[2][rr];
             bri = sm.pf.r[3][rr];
             azh = prof4(sm.pf.z[2], cc);
             bzh = prof4(sm.pf.z[3], cc);
-            q6 = ld4cg(S.psi[6] + o.c);
-            q7 = ld4cg(S.psi[7] + o.c);
         }
         const V12 vr12 = lds12(s_vr, rr, cc - 4);
         const V4 vz0 = lds4(s_vz, rr, cc), vzm1 = lds4(s_vz, rr - 1, cc),
