@@ -438,7 +438,7 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     const Own o = own_of(g, i0, j0);
     const bool pml = flags & TILE_PML;
     V4 vr0{}, vz0{}, br{}, bz{}, q0{}, q1{}, q2{}, q3{};
-    float ari = 0.f, bri = 0.f, arh = 0.f, brh = 0.f;
+    float ari = 0.f, bri = 0.f, arh = 0.f, brh = 0.f, ivr = 0.f, ivh = 0.f;
     V4 azi{}, bzi{}, azh{}, bzh{};
     __syncthreads();
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
@@ -451,6 +451,8 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     if (pml) stage_prof(sm.pf, C, g, i0, j0);
     // own-node inputs, in flight together with the copies
     if (o.live) {
+        ivr = __ldg(C.inv_r_int + o.i);
+        ivh = __ldg(C.inv_r_half + o.i);
         vz0 = ld4cg(S.vz + o.c);
         bz = ld4g(C.w_bvz + o.c);
         if (o.i >= 1) {
@@ -494,7 +496,7 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
         const V4 rm2 = lds4(s_rr, rr - 2, cc), rm1 = lds4(s_rr, rr - 1, cc);
         const V4 r0 = lds4(s_rr, rr, cc), rp1 = lds4(s_rr, rr + 1, cc);
         const V4 tm1 = lds4(s_tt, rr - 1, cc), t0 = lds4(s_tt, rr, cc);
-        const float inv_r = __ldg(C.inv_r_int + o.i);
+        const float inv_r = ivr;
         float vr[4], w0[4], w1[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -524,7 +526,7 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     {
         const V12 zz12 = lds12(s_zz, rr, cc - 4);
         const V4 rzm1 = lds4(s_rz, rr - 1, cc), rzp2 = lds4(s_rz, rr + 2, cc);
-        const float inv_r = __ldg(C.inv_r_half + o.i);
+        const float inv_r = ivh;
         float vz[4], w2[4], w3[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -578,9 +580,10 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     }
     if (pml) stage_prof(sm.pf, C, g, i0, j0);
     V4 t_rr{}, t_tt{}, t_zz{}, lm{}, mu{}, t_rz{}, mh{};
-    float arh = 0.f, brh = 0.f;
+    float arh = 0.f, brh = 0.f, ivh = 0.f;
     V4 azi{}, bzi{}, q4{}, q5{}, q6{}, q7{};
     if (o.live) {
+        ivh = __ldg(C.inv_r_half + o.i);
         t_rr = ld4cg(S.trr + o.c);
         t_tt = ld4cg(S.ttt + o.c);
         t_zz = ld4cg(S.tzz + o.c);
@@ -617,7 +620,7 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         }
         const V12 vr12 = lds12(s_vr, rr, cc - 4), vz12 = lds12(s_vz, rr, cc - 4);
         const V4 vrp1 = lds4(s_vr, rr + 1, cc);
-        const float inv_rh = __ldg(C.inv_r_half + o.i);
+        const float inv_rh = ivh;
         float trr[4], ttt[4], tzz[4], w4[4], w5[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -851,9 +854,14 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     if (pml) stage_prof(sm.pf, C, g, i0, j0);
     // own adjoint velocities, in flight together with the copies
     V4 av_z{}, av_r{};
+    float ivh = 0.f, ivm = 0.f;
     if (o.live) {
         av_z = ld4cg(S.vz + c);
-        if (i >= 1) av_r = ld4cg(S.vr + c);
+        ivh = __ldg(C.inv_r_half + i);
+        if (i >= 1) {
+            av_r = ld4cg(S.vr + c);
+            ivm = __ldg(C.inv_r_half + i - 1);
+        }
     }
     async_wait_all();
     if (i0 < kH) {
@@ -957,7 +965,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
                      x40 = lds4(T_x4, rr, cc), x4p1 = lds4(T_x4, rr + 1, cc);
             const V4 ytm1 = lds4(T_yt, rr - 1, cc), yt0 = lds4(T_yt, rr, cc);
             const V12 x6r = lds12(T_x6, rr, cc - 4);
-            const float irm = __ldg(C.inv_r_half + i - 1), inv_rh = __ldg(C.inv_r_half + i);
+            const float irm = ivm, inv_rh = ivh;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 float s = d4(x4m1.v[e], x40.v[e], x4m2.v[e], x4p1.v[e]) * g.inv_dr;
@@ -983,7 +991,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
         const V4 frm1 = lds4(T_fr, rr - 1, cc), frp1 = lds4(T_fr, rr + 1, cc),
                  frp2 = lds4(T_fr, rr + 2, cc);
         const V4 Arr = lds4(T_rr, rr, cc), Att = lds4(T_tt, rr, cc), Azz = lds4(T_zz, rr, cc);
-        const float inv_rh = __ldg(C.inv_r_half + i);
+        const float inv_rh = ivh;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float err = d4(frp1.v[e], fr12.v[4 + e], frp2.v[e], frm1.v[e]) * g.inv_dr;
@@ -1038,7 +1046,12 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
     }
     if (pml) stage_prof(sm.pf, C, g, i0, j0);
     V4 o_rr{}, o_tt{}, o_zz{}, o_rz{}, r3{};
+    float ir0 = 0.f, ir1 = 0.f, irm = 0.f, irh = 0.f;
     if (o.live) {
+        ir0 = __ldg(C.inv_r_int + o.i);
+        irh = __ldg(C.inv_r_half + o.i);
+        if (o.i + 1 < g.nr) ir1 = __ldg(C.inv_r_int + o.i + 1);
+        if (o.i >= 1) irm = __ldg(C.inv_r_half + o.i - 1);
         o_rr = ld4cg(S.trr + o.c);
         o_tt = ld4cg(S.ttt + o.c);
         o_zz = ld4cg(S.tzz + o.c);
@@ -1139,7 +1152,6 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         const V4 x0m1 = lds4(s_x0, rr - 1, cc), x00 = lds4(s_x0, rr, cc),
                  x0p1 = lds4(s_x0, rr + 1, cc), x0p2 = lds4(s_x0, rr + 2, cc);
         const V12 x3r = lds12(s_x3, rr, cc - 4);
-        const float ir0 = __ldg(C.inv_r_int + i), ir1 = i + 1 < g.nr ? __ldg(C.inv_r_int + i + 1) : 0.f;
         float trr[4], ttt[4], tzz[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -1160,13 +1172,12 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         const V4 x2m2 = lds4(s_x2, rr - 2, cc), x2m1 = lds4(s_x2, rr - 1, cc),
                  x20 = lds4(s_x2, rr, cc), x2p1 = lds4(s_x2, rr + 1, cc);
         const V4 wzm1 = lds4(s_wz, rr - 1, cc), wz0 = lds4(s_wz, rr, cc);
-        const float irm = __ldg(C.inv_r_half + i - 1), ir0 = __ldg(C.inv_r_half + i);
         float trz[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             float s = d4(x1r.v[4 + e], x1r.v[5 + e], x1r.v[3 + e], x1r.v[6 + e]) * g.inv_dz;
             s += d4(x2m1.v[e], x20.v[e], x2m2.v[e], x2p1.v[e]) * g.inv_dr;
-            s += 0.5f * (wzm1.v[e] * irm + wz0.v[e] * ir0);
+            s += 0.5f * (wzm1.v[e] * irm + wz0.v[e] * irh);
             trz[e] = o_rz.v[e] + s;
         }
         st4(S.trz + c, o.j, g.nz, trz);
