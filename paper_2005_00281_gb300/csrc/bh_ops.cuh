@@ -142,24 +142,63 @@ __global__ void __launch_bounds__(kRedThreads) k_misfit(size_t n, const float* _
     if (threadIdx.x == 0) *J = 0.5 * sh[0];
 }
 
-// masked maxima: out[0] = max H_lam, out[1] = max H_mu
-__global__ void __launch_bounds__(kRedThreads) k_masked_max2(size_t n, const uint8_t* __restrict__ mask,
-                                                             const double* __restrict__ a,
-                                                             const double* __restrict__ b,
-                                                             double* out)
+// Masked maxima over many blocks: each block writes its maxima to
+// part[q * gridDim.x + blockIdx.x]; a one-block pass takes the maximum of the
+// parts.  A maximum is exact in any order, so the result does not depend on
+// the grid.
+constexpr int kPartThreads = 256;
+constexpr int kMaxParts = 608;  // blocks of the first pass at most
+
+template <int NQ>
+__device__ __forceinline__ void block_max_parts(double (&v)[NQ], double* part)
 {
-    __shared__ double sh[kRedThreads];
-    double ma = 0.0, mb = 0.0;
-    for (size_t k = threadIdx.x; k < n; k += blockDim.x)
+    __shared__ double sh[kPartThreads];
+    for (int q = 0; q < NQ; ++q) {
+        block_reduce_max(sh, v[q]);
+        if (threadIdx.x == 0) part[q * gridDim.x + blockIdx.x] = sh[0];
+        __syncthreads();
+    }
+}
+
+template <int NQ>
+__device__ __forceinline__ void finish_max_parts(const double* part, int nparts, double (&r)[NQ])
+{
+    __shared__ double sh[kPartThreads];
+    for (int q = 0; q < NQ; ++q) {
+        double m = 0.0;
+        for (int k = threadIdx.x; k < nparts; k += blockDim.x) m = fmax(m, part[q * nparts + k]);
+        block_reduce_max(sh, m);
+        r[q] = sh[0];
+        __syncthreads();
+    }
+}
+
+// pass 1 of the masked maxima max |H_lam|, max |H_mu|
+__global__ void __launch_bounds__(kPartThreads) k_masked_max2_part(size_t n, const uint8_t* __restrict__ mask,
+                                                                   const double* __restrict__ a,
+                                                                   const double* __restrict__ b,
+                                                                   double* part)
+{
+    double v[2] = {0.0, 0.0};
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
         if (mask[k]) {
-            ma = fmax(ma, fabs(a[k]));
-            mb = fmax(mb, fabs(b[k]));
+            v[0] = fmax(v[0], fabs(a[k]));
+            v[1] = fmax(v[1], fabs(b[k]));
         }
-    block_reduce_max(sh, ma);
-    if (threadIdx.x == 0) out[0] = sh[0];
-    __syncthreads();
-    block_reduce_max(sh, mb);
-    if (threadIdx.x == 0) out[1] = sh[0];
+    block_max_parts<2>(v, part);
+}
+
+// pass 2: out[0] = max H_lam, out[1] = max H_mu
+__global__ void __launch_bounds__(kPartThreads) k_masked_max2_finish(const double* __restrict__ part,
+                                                                     int nparts, double* out)
+{
+    double r[2];
+    finish_max_parts<2>(part, nparts, r);
+    if (threadIdx.x == 0) {
+        out[0] = r[0];
+        out[1] = r[1];
+    }
 }
 
 // g <- g / (H + eps max H) inside the mask, 0 outside
@@ -181,29 +220,33 @@ __global__ void k_precondition(size_t n, const uint8_t* __restrict__ mask,
     g_mu[k] = dm > 0.0 ? g_mu[k] / dm : 0.0;
 }
 
-// step lengths: alpha_m = kappa max|m| / max|g_m| over the mask
-__global__ void __launch_bounds__(kRedThreads) k_update_alpha(size_t n, const uint8_t* __restrict__ mask,
-                                                              const float* __restrict__ lam,
-                                                              const float* __restrict__ mu,
-                                                              const double* __restrict__ g_lam,
-                                                              const double* __restrict__ g_mu,
-                                                              double kappa, double* alpha)
+// step lengths alpha_m = kappa max|m| / max|g_m| over the mask: pass 1
+__global__ void __launch_bounds__(kPartThreads) k_update_alpha_part(size_t n, const uint8_t* __restrict__ mask,
+                                                                    const float* __restrict__ lam,
+                                                                    const float* __restrict__ mu,
+                                                                    const double* __restrict__ g_lam,
+                                                                    const double* __restrict__ g_mu,
+                                                                    double* part)
 {
-    __shared__ double sh[kRedThreads];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (size_t k = threadIdx.x; k < n; k += blockDim.x)
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
         if (mask[k]) {
             v[0] = fmax(v[0], fabs((double)lam[k]));
             v[1] = fmax(v[1], fabs((double)mu[k]));
             v[2] = fmax(v[2], fabs(g_lam[k]));
             v[3] = fmax(v[3], fabs(g_mu[k]));
         }
+    block_max_parts<4>(v, part);
+}
+
+// pass 2: alpha[0], alpha[1]
+__global__ void __launch_bounds__(kPartThreads) k_update_alpha_finish(const double* __restrict__ part,
+                                                                      int nparts, double kappa,
+                                                                      double* alpha)
+{
     double r[4];
-    for (int q = 0; q < 4; ++q) {
-        block_reduce_max(sh, v[q]);
-        r[q] = sh[0];
-        __syncthreads();
-    }
+    finish_max_parts<4>(part, nparts, r);
     if (threadIdx.x == 0) {
         alpha[0] = r[2] > 0.0 ? kappa * r[0] / r[2] : 0.0;
         alpha[1] = r[3] > 0.0 ? kappa * r[1] / r[3] : 0.0;

@@ -75,6 +75,7 @@ struct bh_model {
     long long runs_fwd = 0, runs_adj = 0;  // stepping runs of the last forward / adjoint call
     double* d_Hg = nullptr;     // H_lam, H_mu global [2][nr*nzg]
     double* d_scal = nullptr;   // small device scalars
+    double* d_part = nullptr;   // per-block partial maxima, 4 x kMaxParts
     bool have_forward = false, have_gradient = false;
     std::string err;
     // persistent (one cooperative launch per run) or one launch per half-step
@@ -137,7 +138,7 @@ void free_model(bh_model* m)
     void* bufs[] = {m->d_lam,   m->d_mu,     m->d_rho,   m->d_bvr,    m->d_bvz,    m->d_muh,
                     m->d_mask,  m->d_colcov, m->d_rprof, m->d_zprof,  m->d_recmap, m->d_fwd,
                     m->d_adj,   m->d_hist,   m->d_snap,  m->d_snap_max, m->d_tiles,  m->d_Hg,
-                    m->d_scal,  m->d_bar,    m->d_wcoef, m->d_wins};
+                    m->d_scal,  m->d_bar,    m->d_wcoef, m->d_wins,   m->d_part};
     for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     delete m;
@@ -159,6 +160,14 @@ dim3 block2d() { return dim3(32, 8); }
 // block of the stepping kernels: 8 column groups of 4 nodes x 16 rows
 dim3 block_tiles() { return dim3(8, 16); }
 dim3 grid2d(int nr, int nz) { return dim3((nz + 31) / 32, (nr + 7) / 8); }
+
+// blocks of the first pass of the masked maxima: about 4 elements per
+// thread, at most kMaxParts
+int parts_for(size_t n)
+{
+    const size_t b = (n + 4 * kPartThreads - 1) / (4 * kPartThreads);
+    return (int)std::max<size_t>(1, std::min<size_t>(b, kMaxParts));
+}
 
 // ------------------------------------------------------ checkpoint schedule
 //
@@ -828,6 +837,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_snap_max, (size_t)m->nsnap * nshots * kFwdPlanes));
     CK(dalloc(&m->d_Hg, 2 * ng));
     CK(dalloc(&m->d_scal, 16));
+    CK(dalloc(&m->d_part, 4 * (size_t)kMaxParts));
     CK(dalloc(&m->d_bar, 4));
     {
         int dev = 0, sms = 0, coop = 0, nb = 0;
@@ -1015,8 +1025,11 @@ bh_status bh_precondition(bh_model* m, double* g_lam, double* g_mu, double eps_r
     if (!(eps_rel >= 0.0)) return fail(m, BH_ERR_INVALID_ARG, "eps_rel must be >= 0");
     if (!m->have_gradient) return fail(m, BH_ERR_STATE, "bh_adjoint_gradient must come first");
     const size_t ng = (size_t)m->grid.nr * m->nzg;
-    k_masked_max2<<<1, kRedThreads, 0, m->stream>>>(ng, m->d_mask, m->d_Hg, m->d_Hg + ng,
-                                                    m->d_scal + 2);
+    const int np = parts_for(ng);
+    k_masked_max2_part<<<np, kPartThreads, 0, m->stream>>>(ng, m->d_mask, m->d_Hg, m->d_Hg + ng,
+                                                           m->d_part);
+    BH_LAUNCH(m);
+    k_masked_max2_finish<<<1, kPartThreads, 0, m->stream>>>(m->d_part, np, m->d_scal + 2);
     BH_LAUNCH(m);
     k_precondition<<<(unsigned)((ng + 255) / 256), 256, 0, m->stream>>>(
         ng, m->d_mask, m->d_Hg, m->d_Hg + ng, m->d_scal + 2, eps_rel, g_lam, g_mu);
@@ -1030,8 +1043,12 @@ bh_status bh_update(bh_model* m, const double* g_lam, const double* g_mu, double
     if (!m || !g_lam || !g_mu) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
     if (!(kappa >= 0.0)) return fail(m, BH_ERR_INVALID_ARG, "kappa must be >= 0");
     const size_t ng = (size_t)m->grid.nr * m->nzg;
-    k_update_alpha<<<1, kRedThreads, 0, m->stream>>>(ng, m->d_mask, m->d_lam, m->d_mu, g_lam,
-                                                     g_mu, kappa, m->d_scal + 4);
+    const int np = parts_for(ng);
+    k_update_alpha_part<<<np, kPartThreads, 0, m->stream>>>(ng, m->d_mask, m->d_lam, m->d_mu,
+                                                            g_lam, g_mu, m->d_part);
+    BH_LAUNCH(m);
+    k_update_alpha_finish<<<1, kPartThreads, 0, m->stream>>>(m->d_part, np, kappa,
+                                                             m->d_scal + 4);
     BH_LAUNCH(m);
     const unsigned nb = (unsigned)((ng + 255) / 256);
     k_update_apply<<<nb, 256, 0, m->stream>>>(ng, m->d_mask, g_lam, g_mu, m->d_scal + 4,
