@@ -332,6 +332,7 @@ def run_gpu(args, w):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = m.info("kernel_launches")
     Js = []
     with ClockSampler(local) as clk:
         e0.record(stream)
@@ -341,6 +342,7 @@ def run_gpu(args, w):
         torch.cuda.synchronize()
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    launches = int(m.info("kernel_launches") - launches0)  # this library's kernels, timed steps
     prof = m.profile_read()
     m.profile(0)
 
@@ -406,12 +408,6 @@ def run_gpu(args, w):
                 "note": "algorithmic bytes count every array a launch touches once per cell "
                         "and step; a single 240 x 1600 window (~9 MB of state) stays in the "
                         "129 MB L2, so there the kernels run from L2"}
-    # launches of this library per inversion step
-    other = 1 + 2 + 4 + w.nshots + 1            # misfit, precondition, update, finalize, inject
-    if args.per_step:
-        launches_per_step = int(m.info("persistent_runs_per_step")) + other
-    else:
-        launches_per_step = int(m.info("persistent_runs_per_step")) + other
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -422,7 +418,7 @@ def run_gpu(args, w):
             "roofline": roofline, "kernels": kernels,
             "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / args.steps},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": launches,
             "clocks": clk.summary(), "J_first_last": [Js[0], Js[-1]],
             "history": {k: m.info(k) for k in ("history_steps", "snapshots", "recompute_steps",
                                                "snapshot_precision",

@@ -299,7 +299,9 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
  * re-run by one bh_adjoint_gradient), "tiles", "persistent",
  * "persistent_blocks_fwd", "persistent_blocks_adj", "persistent_runs_per_step"
  * (stepping-kernel launches of the last bh_forward + bh_adjoint_gradient),
- * "history_snapshot_bytes", "device_bytes".
+ * "history_snapshot_bytes", "device_bytes", "kernel_launches" (kernels the
+ * model has launched since it was created, for counting the launches of a
+ * timed region).
  *   value  host double
  * Errors: BH_ERR_INVALID_ARG (unknown key).
  */

@@ -73,6 +73,7 @@ struct bh_model {
     std::vector<std::pair<int, int>> spine;  // (segment, slot) taken during the sweep
     long long recompute_steps = 0;
     long long runs_fwd = 0, runs_adj = 0;  // stepping runs of the last forward / adjoint call
+    long long launches = 0;     // kernels this model has launched
     double* d_Hg = nullptr;     // H_lam, H_mu global [2][nr*nzg]
     double* d_scal = nullptr;   // small device scalars
     double* d_part = nullptr;   // per-block partial maxima, 4 x kMaxParts
@@ -116,6 +117,13 @@ bh_status fail(bh_model* m, bh_status s, const std::string& msg)
         cudaError_t e_ = cudaGetLastError();                                              \
         if (e_ != cudaSuccess)                                                            \
             return fail((m), BH_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+// after a kernel launch: count it (bh_get_info "kernel_launches") and check it
+#define BH_KERNEL(m)      \
+    do {                  \
+        ++(m)->launches;  \
+        BH_LAUNCH(m);     \
     } while (0)
 
 #define BH_TRY(expr)                   \
@@ -245,13 +253,13 @@ bh_status rebuild_coefficients(bh_model* m)
     const int nr = m->grid.nr, nzg = m->nzg;
     k_setup_nodes<<<grid2d(nr, nzg), block2d(), 0, m->stream>>>(nr, nzg, m->d_mu, m->d_rho,
                                                                 m->d_bvr, m->d_bvz, m->d_muh);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     dim3 gw = grid2d(nr, m->P);
     gw.z = (unsigned)m->nshots;
     k_window_coefs<<<gw, block2d(), 0, m->stream>>>(nr, nzg, m->P, m->d_wins, m->d_lam, m->d_mu,
                                                     m->d_rho, m->d_bvr, m->d_bvz, m->d_muh,
                                                     m->d_wcoef);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     return BH_OK;
 }
 
@@ -262,7 +270,7 @@ bh_status load_model(bh_model* m, const float* vp, const float* vs, const float*
     const size_t n = (size_t)nr * nzg;
     // CFL check and C-PML d0 need max Vp
     k_max_f32<<<1, kRedThreads, 0, m->stream>>>(n, vp, m->d_scal);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     double vpmax = 0.0;
     BH_CUDA(m, cudaMemcpyAsync(&vpmax, m->d_scal, sizeof(double), cudaMemcpyDeviceToHost,
                                m->stream));
@@ -284,11 +292,11 @@ bh_status load_model(bh_model* m, const float* vp, const float* vs, const float*
     k_setup_cells<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, m->stream>>>((int)n, vp, vs, rho,
                                                                          m->d_lam, m->d_mu,
                                                                          m->d_rho);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     if (first) {
         k_setup_mask<<<grid2d(nr, nzg), block2d(), 0, m->stream>>>(nr, nzg, g.npml_r, vs,
                                                                    m->d_colcov, m->d_mask);
-        BH_LAUNCH(m);
+        BH_KERNEL(m);
     }
     BH_TRY(rebuild_coefficients(m));
     m->have_forward = m->have_gradient = false;
@@ -572,6 +580,7 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
         size_t e = prof_begin(m, BH_KERNEL_FWD_PERSIST, 0);
         BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_fwd_persist<N>, dim3(blocks), blk,
                                                args, 0, m->stream));
+        ++m->launches;
         prof_end(m, e);
         return check_barrier(m);
     }
@@ -579,9 +588,11 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
     for (int n = n0; n < n1; ++n) {
         size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
         BH_CUDA(m, launch_pdl(k_fwd_vel<N>, grd, blk, m->stream, r, n, T));
+        ++m->launches;
         prof_end(m, e);
         e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
         BH_CUDA(m, launch_pdl(k_fwd_stress<N>, grd, blk, m->stream, r, n, T));
+        ++m->launches;
         prof_end(m, e);
     }
     return BH_OK;
@@ -602,6 +613,7 @@ bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
         size_t e = prof_begin(m, BH_KERNEL_ADJ_PERSIST, 0);
         BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_adj_persist<N>, dim3(blocks), blk,
                                                args, 0, m->stream));
+        ++m->launches;
         prof_end(m, e);
         return check_barrier(m);
     }
@@ -609,9 +621,11 @@ bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
     for (int n = n1 - 1; n >= n0; --n) {
         size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
         BH_CUDA(m, launch_pdl(k_adj_stress<N>, grd, blk, m->stream, r, n, T));
+        ++m->launches;
         prof_end(m, e);
         e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
         BH_CUDA(m, launch_pdl(k_adj_vel<N>, grd, blk, m->stream, r, n, T));
+        ++m->launches;
         prof_end(m, e);
     }
     return BH_OK;
@@ -670,12 +684,12 @@ bh_status snapshot(bh_model* m, int slot, bool take)
     const unsigned nb = (unsigned)std::min<size_t>((per_slot + 255) / 256, 152 * 16);
     if (take) {
         k_plane_maxabs<<<m->nshots * kFwdPlanes, 256, 0, m->stream>>>(m->d_fwd, pl, mx);
-        BH_LAUNCH(m);
+        BH_KERNEL(m);
         k_snap_encode<<<nb, 256, 0, m->stream>>>(m->d_fwd, pl, per_slot, mx, m->snap_prec, snap);
     } else {
         k_snap_decode<<<nb, 256, 0, m->stream>>>(snap, pl, per_slot, mx, m->snap_prec, m->d_fwd);
     }
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     return BH_OK;
 }
 
@@ -948,7 +962,7 @@ bh_status bh_residual_misfit(bh_model* m, const float* seis_mod, const float* se
         return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
     const size_t n = (size_t)m->nshots * m->nrec_max * m->grid.nt;
     k_misfit<<<1, kRedThreads, 0, m->stream>>>(n, seis_mod, seis_obs, resid, m->d_scal);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     BH_CUDA(m, cudaMemcpyAsync(J, m->d_scal, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
     BH_CUDA(m, cudaStreamSynchronize(m->stream));
     return BH_OK;
@@ -973,7 +987,7 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
                                m->stream));
     for (int s = 0; s < m->nshots; ++s) {
         k_adj_inject<<<(m->shots[s].nz + 127) / 128, 128, 0, m->stream>>>(m->h_shots[s], gd.nt - 1);
-        BH_LAUNCH(m);
+        BH_KERNEL(m);
     }
     for (const Act& a : m->plan) {
         switch (a.kind) {
@@ -1001,7 +1015,7 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
     const dim3 blk = block2d();
     for (int s = 0; s < m->nshots; ++s) {
         k_finalize<<<grid2d(gd.nr, m->shots[s].nz), blk, 0, m->stream>>>(m->h_shots[s], f);
-        BH_LAUNCH(m);
+        BH_KERNEL(m);
     }
     m->have_gradient = true;
     return BH_OK;
@@ -1028,12 +1042,12 @@ bh_status bh_precondition(bh_model* m, double* g_lam, double* g_mu, double eps_r
     const int np = parts_for(ng);
     k_masked_max2_part<<<np, kPartThreads, 0, m->stream>>>(ng, m->d_mask, m->d_Hg, m->d_Hg + ng,
                                                            m->d_part);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     k_masked_max2_finish<<<1, kPartThreads, 0, m->stream>>>(m->d_part, np, m->d_scal + 2);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     k_precondition<<<(unsigned)((ng + 255) / 256), 256, 0, m->stream>>>(
         ng, m->d_mask, m->d_Hg, m->d_Hg + ng, m->d_scal + 2, eps_rel, g_lam, g_mu);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     return BH_OK;
 }
 
@@ -1046,18 +1060,18 @@ bh_status bh_update(bh_model* m, const double* g_lam, const double* g_mu, double
     const int np = parts_for(ng);
     k_update_alpha_part<<<np, kPartThreads, 0, m->stream>>>(ng, m->d_mask, m->d_lam, m->d_mu,
                                                             g_lam, g_mu, m->d_part);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     k_update_alpha_finish<<<1, kPartThreads, 0, m->stream>>>(m->d_part, np, kappa,
                                                              m->d_scal + 4);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     const unsigned nb = (unsigned)((ng + 255) / 256);
     k_update_apply<<<nb, 256, 0, m->stream>>>(ng, m->d_mask, g_lam, g_mu, m->d_scal + 4,
                                              m->d_rho, m->d_lam, m->d_mu);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     BH_TRY(rebuild_coefficients(m));
     if (vp_out || vs_out) {
         k_velocities<<<nb, 256, 0, m->stream>>>(ng, m->d_lam, m->d_mu, m->d_rho, vp_out, vs_out);
-        BH_LAUNCH(m);
+        BH_KERNEL(m);
     }
     if (alpha_out) {
         BH_CUDA(m, cudaMemcpyAsync(alpha_out, m->d_scal + 4, 2 * sizeof(double),
@@ -1075,7 +1089,7 @@ bh_status bh_velocity_gradient(bh_model* m, const double* g_lam, const double* g
     const size_t ng = (size_t)m->grid.nr * m->nzg;
     k_velocity_gradient<<<(unsigned)((ng + 255) / 256), 256, 0, m->stream>>>(
         ng, m->d_lam, m->d_mu, m->d_rho, g_lam, g_mu, g_rho, g_vp, g_vs, g_rho_v);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     return BH_OK;
 }
 
@@ -1085,7 +1099,7 @@ bh_status bh_get_model(bh_model* m, float* vp, float* vs)
     const size_t ng = (size_t)m->grid.nr * m->nzg;
     k_velocities<<<(unsigned)((ng + 255) / 256), 256, 0, m->stream>>>(ng, m->d_lam, m->d_mu,
                                                                       m->d_rho, vp, vs);
-    BH_LAUNCH(m);
+    BH_KERNEL(m);
     return BH_OK;
 }
 
@@ -1129,6 +1143,7 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
         *value = (double)pl * sizeof(float) * m->nshots *
                  (2.0 * (m->L + 1) + (double)m->nsnap * kFwdPlanes * (m->snap_prec ? 0.5 : 1.0));
     else if (k == "snapshot_precision") *value = m->snap_prec;
+    else if (k == "kernel_launches") *value = (double)m->launches;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
                      (kFwdPlanes + kAdjPlanes + 5.0 + 2.0 * (m->L + 1)) +

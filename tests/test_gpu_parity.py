@@ -108,6 +108,31 @@ def test_deterministic(cuda):
     assert a["J"] == b["J"]
 
 
+def test_kernel_launch_count(cuda):
+    """The model counts the kernels it launches: one persistent launch per
+    forward run, and per adjoint the residual injection, the persistent
+    launch and the finalisation of the one shot."""
+    import torch
+    from paper_2005_00281_gb300.bh import model_from_workload
+
+    w = tiny_borehole(seed=5, nt=60)
+    m = model_from_workload(w)
+    if m.info("persistent") != 1:
+        m.close()
+        pytest.skip("no cooperative launch")
+    wav = torch.from_numpy(w.wavelet).cuda()
+    n0 = m.info("kernel_launches")
+    seis = m.forward(wav)
+    n1 = m.info("kernel_launches")
+    resid, _ = m.residual_misfit(seis, torch.zeros_like(seis))
+    n2 = m.info("kernel_launches")
+    m.adjoint_gradient(resid)
+    n3 = m.info("kernel_launches")
+    torch.cuda.synchronize()
+    m.close()
+    assert (n1 - n0, n2 - n1, n3 - n2) == (1, 1, 3)
+
+
 def test_persistent_matches_per_step(cuda):
     """The persistent cooperative kernels and the one-launch-per-half-step
     kernels run the same tile code: bit-identical results."""
