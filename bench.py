@@ -295,6 +295,8 @@ def run_gpu(args, w):
     m = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap, snapshot_precision=prec)
     if args.per_step:
         m.set_option("persistent", 0)
+    elif args.persistent:
+        m.set_option("persistent", 1)
     start_model = (t(w.vp), t(w.vs), t(w.rho))
     seis = m.empty_seis()
     resid = torch.empty_like(seis)
@@ -390,7 +392,10 @@ def run_gpu(args, w):
             return win_cells * (w.nt + recompute) * args.steps
         if k == "adj_persist":
             return win_cells * w.nt * args.steps
-        return win_cells * prof[k][1]                  # one pass per per-step launch
+        # one launch per half-step and shot group: the sampled steps launch
+        # every group once, and the groups together cover every window
+        ngroups = (w.nshots + 31) // 32
+        return win_cells * prof[k][1] / ngroups
 
     kernels = {}
     for k, (tms, nl) in prof.items():
@@ -463,7 +468,10 @@ def parse_args(argv=None):
                     help="precision of the checkpoint snapshots")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-step", action="store_true",
-                    help="one kernel launch per half-step instead of the persistent kernels")
+                    help="one kernel launch per half-step for every run")
+    ap.add_argument("--persistent", action="store_true",
+                    help="one cooperative launch per run for every shot group (default: "
+                         "only where a group's tiles fit the co-resident blocks)")
     ap.add_argument("--nt", type=int, default=None,
                     help="override the step count (small cases for ncu captures only)")
     ap.add_argument("--shots", type=int, default=None,

@@ -273,11 +273,12 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
 
 /*
  * Execution options (the paper has no counterpart).
- *   "persistent"      1 (default where the device supports cooperative
- *                     launch): one cooperative launch runs every time step
- *                     of a shot, with a bounded grid barrier between half
- *                     steps; 0: one kernel launch per half-step.  Both give
- *                     bit-identical results.
+ *   "persistent"      1: one cooperative launch runs every time step of a
+ *                     shot group, with a bounded grid barrier between half
+ *                     steps; 0: one kernel launch per half-step; 2 (default
+ *                     where the device supports cooperative launch): 1 for a
+ *                     group whose tiles fit the co-resident blocks (one tile
+ *                     per block), else 0.  All give bit-identical results.
  *   "barrier_timeout_ms"  wall-clock limit of one barrier wait (default
  *                     2000).  A wait that runs out sets a device error flag,
  *                     every block returns, and bh_forward /
@@ -286,8 +287,8 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
  *   "barrier_extra_arrivals"  test knob: the barrier waits for this many
  *                     arrivals beyond the blocks launched, so every wait
  *                     runs out (default 0).
- * In persistent mode bh_forward and bh_adjoint_gradient synchronise the
- * stream once per shot to read the barrier status.
+ * With cooperative launches bh_forward and bh_adjoint_gradient synchronise
+ * the stream once per launch to read the barrier status.
  * Errors: BH_ERR_INVALID_ARG (unknown key, value out of range),
  *   BH_ERR_UNSUPPORTED (persistent mode without cooperative launch).
  */

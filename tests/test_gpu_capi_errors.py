@@ -99,4 +99,7 @@ def test_bad_option(bhmod):
     with pytest.raises(bhmod.BhError) as e:
         m.set_option("no_such_option", 1)
     assert e.value.status == 1
+    with pytest.raises(bhmod.BhError) as e:
+        m.set_option("persistent", 3)
+    assert e.value.status == 1
     m.close()

@@ -1,6 +1,6 @@
 """Checks at the benchmark workloads' full spatial sizes, in the launch
-configuration bench.py times (one persistent cooperative launch per run over
-the production shot's 750 tiles).
+configuration bench.py times (at the production shot: one cooperative launch
+per run over its 750 tiles).
 
 - The production shot (240 x 1600 cells) against the FP64 oracle element by
   element, with the run shortened to 450 steps and the receivers moved to
@@ -48,7 +48,8 @@ def test_c1_window_parity(cuda, orc):
     w = _shortened_c1(450)
     obs = np.zeros((1, len(w.shots[0]["rec_iz"]), w.nt))
     m, gpu = gpu_gradient(w, obs)
-    assert m.info("tiles") == 750 and m.info("persistent") == 1
+    # one cooperative launch for the forward run and one for the adjoint
+    assert m.info("tiles") == 750 and m.info("persistent_runs_per_step") == 2
     m.close()
     ref = oracle_gradient(w, obs)
     assert np.abs(ref["seis"][0]).max() > 0
@@ -82,8 +83,8 @@ def test_c1_full_run_gradient_and_determinism(cuda):
     obs = truth.forward(wav).clone()
     truth.close()
     m = model_from_workload(w)
-    assert m.info("tiles") == 750 and m.info("persistent") == 1
     J0, g = _c1_run(torch, m, w, obs, wav)
+    assert m.info("tiles") == 750 and m.info("persistent_runs_per_step") == 2
     J0b, g_b = _c1_run(torch, m, w, obs, wav)
     assert J0 == J0b
     for a, b in zip(g, g_b):
