@@ -1298,7 +1298,7 @@ __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T
 
 // one launch per half-step: one block per tile
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_fwd_vel(RunK r, int n,
+__global__ void __launch_bounds__(kThreads, 5) k_fwd_vel(RunK r, int n,
                                                       const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
@@ -1309,7 +1309,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_vel(RunK r, int n,
 }
 
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_fwd_stress(RunK r, int n,
+__global__ void __launch_bounds__(kThreads, 5) k_fwd_stress(RunK r, int n,
                                                          const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
