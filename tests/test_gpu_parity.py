@@ -173,6 +173,32 @@ def _run_gpu(w, obs=None, persistent=None, **kw):
     return out
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_batched_checkpointed_precision(cuda, orc, prec):
+    """Batching, checkpointing and snapshot precision together: three shots
+    with uneven windows of one model under a checkpoint cap that forces
+    snapshots, FP32 (0) / BF16 (1) / FP16 (2) snapshots; misfit and
+    gradients against the FP64 oracle."""
+    w = tiny_borehole(seed=14, nz=96, nt=300)
+    w.shots = [dict(z_offset=0, nz=70, src=(0, 10), rec_iz=[25, 40, 58]),
+               dict(z_offset=13, nz=83, src=(0, 12), rec_iz=[30, 50, 66]),
+               dict(z_offset=40, nz=56, src=(0, 9), rec_iz=[20, 33, 41])]
+    obs = oracle_observed(w)
+    seis, g, J, info = _run_gpu(w, obs=obs, checkpoint_cap_bytes=1_500_000,
+                                snapshot_precision=prec)
+    assert info["snapshots"] >= 1 and info["recompute_steps"] > 0
+    ref = oracle_gradient(w, obs)
+    e_J = abs(J - ref["J"]) / ref["J"]
+    errs = {name: rel_l2(g[k], ref[name]) for k, name in enumerate(("g_lam", "g_mu", "g_rho"))}
+    print(f"3 shots, cap 1.5 MB, snapshot precision {prec}: J rel {e_J:.2e}, gradient rel L2 "
+          + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    # the misfit comes from the first, unrounded sweep
+    assert e_J <= 1e-5
+    bound = GRAD_TOL if prec == 0 else 2e-2
+    for name, e in errs.items():
+        assert e <= bound, (prec, name, e)
+
+
 def test_batched_shots_match_single_shots(cuda):
     """All shots advance in the same launches; shot k of the batch equals
     shot k run alone, bit for bit, and the global gradient is their sum."""
