@@ -67,3 +67,85 @@ def run(model, wavelet, seis_obs, iterations, *, kappa=0.02, eps_rel=1e-3, thres
             save(tmp, model, st, rho)
             os.replace(tmp, checkpoint_path)
     return st
+
+
+def main(argv=None):
+    """Inversion of a synthetic workload from the command line: the observed
+    data are modelled in the true model, the gradient of the misfit with
+    respect to Vp (through BhWave, the library's adjoint) is checked against
+    central differences at random formation cells, then `--iterations`
+    preconditioned gradient-descent steps run from the start model.  Prints
+    one JSON line."""
+    import argparse
+    import json
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from synthetic import PRESETS
+
+    from .autograd import BhWave, misfit
+    from .bh import model_from_workload
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2005_00281_gb300.fwi")
+    ap.add_argument("--config", default="c3", choices=sorted(PRESETS))
+    ap.add_argument("--iterations", type=int, default=10)
+    ap.add_argument("--cap-gb", type=float, default=4.0, help="checkpoint cap (0: store all)")
+    ap.add_argument("--fd-cells", type=int, default=32)
+    ap.add_argument("--fd-step", type=float, default=1e-2, help="relative Vp change")
+    ap.add_argument("--kappa", type=float, default=0.02)
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args(argv)
+    if not torch.cuda.is_available():
+        raise SystemExit("the inversion needs a CUDA device (there is no CPU fallback)")
+    w = PRESETS[args.config]() if args.config == "c0" else PRESETS[args.config](seed=args.seed)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    cap = int(args.cap_gb * 1e9)
+    m = model_from_workload(w, checkpoint_cap_bytes=cap)
+    wav = t(w.wavelet)
+    with torch.no_grad():
+        obs = BhWave.apply(t(w.vp_true), t(w.vs_true), t(w.rho_true), m, wav).clone()
+
+    # gradient of J with respect to Vp at the start model, against central differences
+    vp = t(w.vp).requires_grad_(True)
+    vs, rho = t(w.vs), t(w.rho)
+    J0 = misfit(BhWave.apply(vp, vs, rho, m, wav), obs)
+    J0.backward()
+    g = vp.grad.detach().cpu().numpy()
+    rng = np.random.default_rng(args.seed)
+    form = np.argwhere((w.vs > 0) & (np.arange(w.nr)[:, None] < w.nr - w.npml_r) &
+                       (np.arange(w.nz)[None, :] >= w.npml_z) &
+                       (np.arange(w.nz)[None, :] < w.nz - w.npml_z))
+    cells = form[rng.choice(len(form), size=args.fd_cells, replace=False)]
+    fd_rows = []
+    with torch.no_grad():
+        for i, j in cells:
+            h = args.fd_step * float(w.vp[i, j])
+            vals = []
+            for sgn in (1.0, -1.0):
+                vp2 = t(w.vp).clone()
+                vp2[i, j] += sgn * h
+                vals.append(float(misfit(BhWave.apply(vp2, vs, rho, m, wav), obs)))
+            fd_rows.append((int(i), int(j), (vals[0] - vals[1]) / (2 * h), float(g[i, j])))
+    gmax = float(np.abs(g).max())
+    fd_err = max(abs(fd - ad) for _, _, fd, ad in fd_rows) / gmax
+
+    # the inversion loop from the start model
+    m.set_model(t(w.vp), vs, rho)
+    st = run(m, wav, obs, args.iterations, kappa=args.kappa,
+             log=lambda s: print(s, file=sys.stderr, flush=True))
+    info = {k: m.info(k) for k in ("history_steps", "snapshots", "recompute_steps",
+                                   "history_snapshot_bytes")}
+    m.close()
+    print(json.dumps({
+        "workload": args.config, "nr": w.nr, "nz": w.nz, "nt": w.nt, "nshots": w.nshots,
+        "checkpoint": info, "J": [float(x) for x in st.J],
+        "seconds_per_iteration": [float(x) for x in st.seconds],
+        "fd_check": {"cells": args.fd_cells, "relative_step": args.fd_step,
+                     "max_abs_error_over_max_gradient": fd_err,
+                     "rows": [list(r) for r in fd_rows]}}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
