@@ -73,7 +73,9 @@ def main(argv=None):
     """Inversion of a synthetic workload from the command line: the observed
     data are modelled in the true model, the gradient of the misfit with
     respect to Vp (through BhWave, the library's adjoint) is checked against
-    central differences at random formation cells, then `--iterations`
+    central differences at random formation cells and at the formation cells
+    of largest gradient (at random cells far from the wave paths a change of
+    J is near the FP32 rounding of the seismograms), then `--iterations`
     preconditioned gradient-descent steps run from the start model.  Prints
     one JSON line."""
     import argparse
@@ -117,10 +119,12 @@ def main(argv=None):
     form = np.argwhere((w.vs > 0) & (np.arange(w.nr)[:, None] < w.nr - w.npml_r) &
                        (np.arange(w.nz)[None, :] >= w.npml_z) &
                        (np.arange(w.nz)[None, :] < w.nz - w.npml_z))
-    cells = form[rng.choice(len(form), size=args.fd_cells, replace=False)]
+    rand = form[rng.choice(len(form), size=args.fd_cells, replace=False)]
+    gform = np.abs(g[form[:, 0], form[:, 1]])
+    top = form[np.argsort(gform)[-args.fd_cells:]]
     fd_rows = []
     with torch.no_grad():
-        for i, j in cells:
+        for i, j in np.concatenate([rand, top]):
             h = args.fd_step * float(w.vp[i, j])
             vals = []
             for sgn in (1.0, -1.0):
@@ -130,6 +134,7 @@ def main(argv=None):
             fd_rows.append((int(i), int(j), (vals[0] - vals[1]) / (2 * h), float(g[i, j])))
     gmax = float(np.abs(g).max())
     fd_err = max(abs(fd - ad) for _, _, fd, ad in fd_rows) / gmax
+    rel = [abs(fd - ad) / abs(ad) for _, _, fd, ad in fd_rows[args.fd_cells:]]
 
     # the inversion loop from the start model
     m.set_model(t(w.vp), vs, rho)
@@ -144,7 +149,10 @@ def main(argv=None):
         "seconds_per_iteration": [float(x) for x in st.seconds],
         "fd_check": {"cells": args.fd_cells, "relative_step": args.fd_step,
                      "max_abs_error_over_max_gradient": fd_err,
-                     "rows": [list(r) for r in fd_rows]}}), flush=True)
+                     "largest_cells_relative_error_median": float(np.median(rel)),
+                     "largest_cells_relative_error_max": float(np.max(rel)),
+                     "rows_random": [list(r) for r in fd_rows[: args.fd_cells]],
+                     "rows_largest": [list(r) for r in fd_rows[args.fd_cells:]]}}), flush=True)
 
 
 if __name__ == "__main__":
