@@ -88,7 +88,8 @@ typedef struct {
  * Errors: BH_ERR_INVALID_ARG (bad sizes or indices), BH_ERR_CFL when
  *   dt Vmax sqrt(1/dr^2 + 1/dz^2) (9/8 + 1/24) >= 1, BH_ERR_OOM, BH_ERR_CUDA.
  * Citation: Method section, Eq. 2-4; C-PML and axis conditions as cited
- *   there (finite differences, PML on top, bottom and radial boundaries).
+ *   there (finite differences; absorbing layers at the two axial ends and the
+ *   outer radius).
  */
 bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* vp,
                           const float* vs, const float* rho, const bh_shot_desc* shots,
