@@ -199,6 +199,33 @@ def test_batched_checkpointed_precision(cuda, orc, prec):
         assert e <= bound, (prec, name, e)
 
 
+def test_two_shot_groups(cuda):
+    """More shots than one launch carries (32): the shots run in groups.  Both
+    launch forms agree bit for bit, the seismograms equal those of two
+    separate models (shots 0-31 and 32-39) bit for bit, and the FP64 global
+    gradient equals their sum up to the order of the shot sum."""
+    import copy
+    w = tiny_borehole(seed=15, nz=200, nt=150)
+    w.shots = [dict(z_offset=3 * k, nz=48 + (k % 5) * 4, src=(0, 12), rec_iz=[24, 30])
+               for k in range(40)]
+    out = {}
+    for persistent in (1, 0):
+        seis, g, J, _ = _run_gpu(w, persistent=persistent)
+        out[persistent] = (seis, g, J)
+    for a, b in zip([out[1][0]] + out[1][1], [out[0][0]] + out[0][1]):
+        assert np.array_equal(a, b)
+    assert out[1][2] == out[0][2]
+    parts = []
+    for lo, hi in ((0, 32), (32, 40)):
+        wp = copy.deepcopy(w)
+        wp.shots = w.shots[lo:hi]
+        parts.append(_run_gpu(wp))
+    assert np.array_equal(out[1][0][:32], parts[0][0]) and np.array_equal(out[1][0][32:], parts[1][0])
+    for k in range(3):
+        total = parts[0][1][k] + parts[1][1][k]
+        assert np.max(np.abs(out[1][1][k] - total)) <= 1e-12 * np.max(np.abs(total)), k
+
+
 def test_batched_shots_match_single_shots(cuda):
     """All shots advance in the same launches; shot k of the batch equals
     shot k run alone, bit for bit, and the global gradient is their sum."""
