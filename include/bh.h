@@ -107,8 +107,9 @@ void bh_model_destroy(bh_model* model);
 bh_status bh_set_model(bh_model* model, const float* vp, const float* vs, const float* rho);
 
 /*
- * Shots run together: every kernel launch (or every phase of a persistent
- * launch) covers the tiles of all shots, each shot on its own window state.
+ * Shots run together, in groups of up to 32: every kernel launch (or every
+ * phase of a cooperative launch) covers the tiles of one group's shots, each
+ * shot on its own window state.
  *
  * Forward history.  The adjoint correlation needs v^{n+1/2} of every step.
  * With checkpoint_cap_bytes = 0 every step is stored (nt + 1 slots of v_r,
@@ -131,8 +132,8 @@ bh_status bh_set_model(bh_model* model, const float* vp, const float* vs, const 
  * and stress equations; the source rate wavelet[n] (sampled at
  * t = (n + 1/2) dt) is injected as dt * wavelet[n] / V into the three
  * normal stresses of the source cell (V the cell volume); the pressure is
- * recorded as the mean normal stress at the receivers ("normal stress ...
- * at the receiver positions", Method section).  Keeps the forward history
+ * recorded as the mean normal stress at the receivers (the Method section
+ * records normal stresses at the receiver positions).  Keeps the forward history
  * needed by bh_adjoint_gradient.
  *   wavelet  device [nt] float32; with checkpointing it is read again by
  *            the next bh_adjoint_gradient, so it must stay valid until then
@@ -195,7 +196,7 @@ bh_status bh_precondition(bh_model* model, double* g_lam, double* g_mu, double e
 /*
  * Gradient-descent update (Eq. 9, Eq. 10) with alpha chosen per parameter
  * so that no cell changes by more than kappa times the largest modulus
- * ("alpha ... controlling the greatest change", Method section):
+ * (the Method section has alpha set the largest change of the model):
  * alpha_m = kappa max|m| / max|g_m| over the inversion mask; then mu >= 0,
  * lambda + 2 mu >= rho (1 m/s)^2, and Vp, Vs from Eq. 11, Eq. 12.  The
  * model's own coefficients are rebuilt; any stored history is invalidated.
@@ -238,8 +239,8 @@ enum {
     BH_KERNEL_FWD_STRESS = 1,  /* stress half-step, Eq. 2 lines 3-6            */
     BH_KERNEL_ADJ_STRESS = 2,  /* transposed stress step + Eq. 7 / Eq. 8        */
     BH_KERNEL_ADJ_VEL = 3,     /* transposed velocity step                     */
-    BH_KERNEL_FWD_PERSIST = 4, /* persistent forward: all steps of one shot     */
-    BH_KERNEL_ADJ_PERSIST = 5, /* persistent adjoint + correlation, one shot     */
+    BH_KERNEL_FWD_PERSIST = 4, /* cooperative forward: all steps of a run       */
+    BH_KERNEL_ADJ_PERSIST = 5, /* cooperative adjoint + correlation of a run    */
     BH_KERNEL_COUNT = 6
 };
 bh_status bh_profile_enable(bh_model* model, int every);
