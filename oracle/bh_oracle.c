@@ -12,8 +12,8 @@
  *     (leapfrog), with the axis symmetry condition at r = 0, a C-PML on the
  *     outer radial edge and on the top and bottom edges, a volume source in
  *     the three normal stresses, and pressure recording as the mean normal
- *     stress (Method section, Eq. 2, "normal stress ... at the receiver
- *     positions");
+ *     stress at the receivers (Method section, Eq. 2: the recorded data are
+ *     normal stresses);
  *   - the adjoint of that discrete map (the discrete form of Eq. 6), driven
  *     by the data residual of Eq. 5.  Every loop of the forward step is
  *     transposed literally: each gather "y += w * x[k]" of the forward
