@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 METRIC = "Gcell-updates/s and gradient evals/s (fwd+adj+grad) at 1 GB300; % of HBM roofline"
 UNIT = "Gcell-updates/s"
 PROFILE_EVERY = 64
-CPU_SAMPLE_STEPS = 100
+CPU_SAMPLE_STEPS = 150
 REF_SAMPLE_STEPS = 100
 
 # Algorithmic bytes per cell and launch of each stepping kernel: every array
