@@ -241,10 +241,18 @@ def chain_to_velocity(g_lam, g_mu, g_rho, vp, vs, rho):
     return g_vp, g_vs, g_rho_v
 
 
-def inversion_mask(nr, nz, npml_r, npml_z, vs):
-    """Cells that are unknowns: outside the C-PML and in the formation."""
+def inversion_mask(nr, nz, npml_r, npml_z, vs, windows=None):
+    """Cells that are unknowns: formation cells (Vs > 0) outside the radial
+    C-PML and inside the axial interior (outside the top and bottom C-PML) of
+    at least one shot window.  windows: list of (z_offset, nz_window); None
+    means one window covering the whole model."""
+    if windows is None:
+        windows = [(0, nz)]
+    cols = np.zeros(nz, dtype=bool)
+    for z0, nzs in windows:
+        cols[z0 + npml_z: z0 + nzs - npml_z] = True
     m = np.zeros((nr, nz), dtype=bool)
-    m[: nr - npml_r, npml_z: nz - npml_z] = True
+    m[: nr - npml_r, :] = cols[None, :]
     return m & (np.asarray(vs).reshape(nr, nz) > 0)
 
 

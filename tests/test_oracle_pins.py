@@ -311,3 +311,181 @@ def test_update_by_hand(orc):
     np.testing.assert_allclose(mu2, [[1.0e9 - 4.0e7, 2.0e9 - 2.0e7]])
     np.testing.assert_allclose(vp, np.sqrt((lam2 + 2 * mu2) / rho))
     np.testing.assert_allclose(vs, np.sqrt(mu2 / rho))
+
+
+# ---------------------------------------------------------------------------
+# Several shots with uneven windows of one global model (the multi-shot sum of
+# Eq. 1): the global gradient at a cell is the sum, over the windows whose
+# axial interior holds the cell, of the derivative of that window's misfit.
+# A window whose top or bottom C-PML holds the cell contributes nothing
+# (cells inside a C-PML are not unknowns of that window).
+
+MW_SHOTS = [dict(z_offset=0, nz=60, src=(0, 9), rec_iz=[20, 35, 48]),
+            dict(z_offset=17, nz=73, src=(0, 9), rec_iz=[20, 35, 61]),
+            dict(z_offset=30, nz=55, src=(0, 9), rec_iz=[20, 35, 43])]
+
+# (row, global column): overlap of all three interiors; a column only window 0
+# covers; window 0's top interior edge; window 0's bottom interior edge (inside
+# windows 1 and 2); window 1's top edge; window 2's bottom edge; a cell in
+# window 0's bottom C-PML but inside windows 1 and 2; window 1's bottom edge,
+# in window 2's bottom C-PML; the wall row in window 1's top C-PML; the last
+# row before the radial C-PML
+MW_CELLS = [(8, 40), (10, 10), (7, 6), (9, 53), (6, 23), (12, 78), (5, 56), (11, 83),
+            (4, 20), (17, 45)]
+
+
+def _mw_window_J(orc, w, s, vp, vs, rho, obs, vpmax):
+    sh = w.shots[s]
+    z0, nzs = sh["z_offset"], sh["nz"]
+    sl = np.s_[:, z0: z0 + nzs]
+    g = orc.Grid(w.nr, nzs, w.nt, w.npml_r, w.npml_z, w.dr, w.dz, w.dt, w.f0, w.pml_R)
+    seis, _ = orc.forward(g, *(np.ascontiguousarray(a[sl]) for a in (vp, vs, rho)),
+                          w.wavelet, sh["src"], sh["rec_iz"], store_v=False, vpmax=vpmax)
+    return orc.residual_misfit(seis, obs[s])[1]
+
+
+@pytest.fixture(scope="module")
+def multiwindow(orc):
+    w = tiny_borehole(seed=3, nz=90, nt=240)
+    w.shots = MW_SHOTS
+    vpmax = float(w.vp.max())
+    obs = []
+    for sh in w.shots:
+        z0, nzs = sh["z_offset"], sh["nz"]
+        sl = np.s_[:, z0: z0 + nzs]
+        g = orc.Grid(w.nr, nzs, w.nt, w.npml_r, w.npml_z, w.dr, w.dz, w.dt, w.f0, w.pml_R)
+        s, _ = orc.forward(g, *(np.ascontiguousarray(a[sl]) for a in (w.vp_true, w.vs_true,
+                                                                      w.rho_true)),
+                           w.wavelet, sh["src"], sh["rec_iz"], store_v=False, vpmax=vpmax)
+        obs.append(s)
+    g = orc.Grid(w.nr, w.nz, w.nt, w.npml_r, w.npml_z, w.dr, w.dz, w.dt, w.f0, w.pml_R)
+    out = orc.shot_gradient(g, w.vp, w.vs, w.rho, w.wavelet, w.shots, obs)
+    return w, obs, out, vpmax
+
+
+def _interior(w, s, jg):
+    sh = w.shots[s]
+    return sh["z_offset"] + w.npml_z <= jg < sh["z_offset"] + sh["nz"] - w.npml_z
+
+
+def _covers(w, s, jg):
+    sh = w.shots[s]
+    return sh["z_offset"] <= jg < sh["z_offset"] + sh["nz"]
+
+
+@pytest.mark.parametrize("param", ["lam", "mu", "rho"])
+def test_multiwindow_fd_gradient(orc, multiwindow, param):
+    """Central differences of every window's misfit at cells inside the
+    overlap of the windows, at each window's top and bottom interior edge,
+    in a column only one window covers, and in cells that one window holds in
+    its C-PML and another in its interior: the oracle's global gradient is
+    the sum over the windows whose interior holds the cell, to 1e-8 of the
+    largest gradient.  Pins the window offsets of the shot sum and the
+    per-window masking of the C-PML cells."""
+    w, obs, out, vpmax = multiwindow
+    lam, mu = orc.lame(w.vp, w.vs, w.rho)
+    base = {"lam": lam, "mu": mu, "rho": w.rho.astype(np.float64)}
+    gk = out["g_" + param]
+    scale = np.abs(gk).max()
+    assert scale > 0
+    pml_sizes = []
+    for (i, jg) in MW_CELLS:
+        m = base[param]
+        if m[i, jg] == 0.0:
+            continue
+        hs = 1e-5 * abs(m[i, jg])
+        fd = {}
+        for s in range(len(w.shots)):
+            if not _covers(w, s, jg):
+                continue
+            vals = []
+            for sgn in (1, -1):
+                p = {k: v.copy() for k, v in base.items()}
+                p[param][i, jg] += sgn * hs
+                vp = np.sqrt((p["lam"] + 2 * p["mu"]) / p["rho"])
+                vs = np.sqrt(p["mu"] / p["rho"])
+                vals.append(_mw_window_J(orc, w, s, vp, vs, p["rho"], obs, vpmax))
+            fd[s] = (vals[0] - vals[1]) / (2 * hs)
+        expect = sum(v for s, v in fd.items() if _interior(w, s, jg))
+        assert abs(gk[i, jg] - expect) <= 1e-8 * scale, (param, i, jg, gk[i, jg], expect, fd)
+        pml_sizes += [abs(v) for s, v in fd.items() if not _interior(w, s, jg)]
+    # the windows that hold a checked cell in their C-PML do see it: leaving
+    # them out of the sum is a real difference that the checks above resolve
+    assert max(pml_sizes) > 1e-5 * scale, pml_sizes
+    # radial C-PML cells and columns no window interior covers are not unknowns
+    assert np.all(gk[-w.npml_r:, :] == 0) and np.all(gk[:, : w.npml_z] == 0)
+    assert np.all(gk[:, 84:] == 0)
+
+
+def test_multiwindow_sum_of_single_windows(orc, multiwindow):
+    """The global arrays are the per-window results placed at each window's
+    own offset: running every window as its own one-shot model (global model
+    = the window) and adding the results at the offsets gives the same
+    arrays, and the misfit is the sum of the windows' misfits."""
+    w, obs, out, vpmax = multiwindow
+    total = {k: np.zeros((w.nr, w.nz)) for k in ("g_lam", "g_mu", "g_rho", "H_lam", "H_mu")}
+    J = 0.0
+    for s, sh in enumerate(w.shots):
+        z0, nzs = sh["z_offset"], sh["nz"]
+        sl = np.s_[:, z0: z0 + nzs]
+        g = orc.Grid(w.nr, nzs, w.nt, w.npml_r, w.npml_z, w.dr, w.dz, w.dt, w.f0, w.pml_R)
+        win = [np.ascontiguousarray(a[sl]) for a in (w.vp, w.vs, w.rho)]
+        seis, vh = orc.forward(g, *win, w.wavelet, sh["src"], sh["rec_iz"], vpmax=vpmax)
+        resid, Js = orc.residual_misfit(seis, obs[s])
+        acc, _, _ = orc.adjoint(g, *win, resid, sh["src"], sh["rec_iz"], vh, vpmax=vpmax)
+        fin = orc.finalize(g, *win, acc, vpmax=vpmax)
+        for k in total:
+            total[k][sl] += fin[k]
+            # a window's own C-PML rows and columns are zero
+            assert np.all(fin[k][:, : w.npml_z] == 0) and np.all(fin[k][:, nzs - w.npml_z:] == 0)
+        J += Js
+    assert out["J"] == pytest.approx(J, rel=1e-14)
+    for k in total:
+        np.testing.assert_array_equal(out[k], total[k])
+
+
+def test_inversion_mask_by_hand(orc):
+    """Unknowns: formation (Vs > 0), outside the radial C-PML, inside the
+    axial interior of at least one window."""
+    nr, nz, npml_r, npml_z = 6, 14, 2, 2
+    vs = np.full((nr, nz), 1000.0)
+    vs[0, :] = 0.0          # fluid row
+    vs[3, 7] = 0.0          # a fluid cell inside the formation
+    got = orc.inversion_mask(nr, nz, npml_r, npml_z, vs)
+    want = np.zeros((nr, nz), dtype=bool)
+    want[1:4, 2:12] = True
+    want[3, 7] = False
+    np.testing.assert_array_equal(got, want)
+    # two windows, columns 0..7 and 5..13: interiors 2..5 and 7..11; column 6
+    # lies in the bottom C-PML of the first and the top C-PML of the second
+    got2 = orc.inversion_mask(nr, nz, npml_r, npml_z, vs, windows=[(0, 8), (5, 9)])
+    want2 = np.zeros((nr, nz), dtype=bool)
+    want2[1:4, 2:6] = True
+    want2[1:4, 7:12] = True
+    want2[3, 7] = False
+    np.testing.assert_array_equal(got2, want2)
+
+
+def test_update_clamps_by_hand(orc):
+    """Both clamps of the update: a cell whose mu would turn negative keeps
+    mu = 0; a cell whose lambda + 2 mu would fall below rho (1 m/s)^2 keeps
+    lambda = rho - 2 mu, i.e. Vp = 1 m/s."""
+    rho = np.array([[2000.0, 2000.0, 2500.0]])
+    lam = np.array([[4.0e9, 1.0e6, 6.0e9]])
+    mu = np.array([[1.0e9, 1.0e7, 2.0e9]])
+    g_lam = np.array([[0.5, 1.0, 0.1]])
+    g_mu = np.array([[0.1, 1.0, -0.5]])
+    mask = np.array([[True, True, True]])
+    lam2, mu2, vp, vs, (al, am) = orc.update(lam, mu, rho, g_lam, g_mu, mask, 0.02)
+    # alpha_lam = 0.02 * 6e9 / 1.0, alpha_mu = 0.02 * 2e9 / 1.0
+    assert al == pytest.approx(1.2e8) and am == pytest.approx(4.0e7)
+    # cell 0: both steps stay inside the bounds
+    assert lam2[0, 0] == pytest.approx(4.0e9 - 0.5 * 1.2e8)
+    assert mu2[0, 0] == pytest.approx(1.0e9 - 0.1 * 4.0e7)
+    # cell 1: mu = 1e7 - 4e7 < 0 -> 0; lambda = 1e6 - 1.2e8 < rho -> rho
+    assert mu2[0, 1] == 0.0 and vs[0, 1] == 0.0
+    assert lam2[0, 1] == rho[0, 1]
+    assert vp[0, 1] == pytest.approx(1.0)
+    # cell 2: a negative gradient raises mu
+    assert mu2[0, 2] == pytest.approx(2.0e9 + 0.5 * 4.0e7)
+    assert lam2[0, 2] == pytest.approx(6.0e9 - 0.1 * 1.2e8)
