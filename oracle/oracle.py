@@ -241,6 +241,34 @@ def chain_to_velocity(g_lam, g_mu, g_rho, vp, vs, rho):
     return g_vp, g_vs, g_rho_v
 
 
+def update_velocity(vp, vs, rho, g_lam, g_mu, g_rho, mask, kappa, update_rho=False):
+    """Eq. 9 and Eq. 10 taken in the velocities (and, with update_rho, the
+    density) instead of the Lame parameters: the gradients with respect to
+    (Vp, Vs, rho) come from those with respect to (lambda, mu, rho) by the
+    chain rule of Eq. 3 and Eq. 4 (chain_to_velocity; g_rho None means rho
+    has no gradient of its own), each parameter steps by
+    alpha_m = kappa max|m| / max|g_m| over the mask, then Vs >= 0,
+    Vp >= 1 m/s, rho >= 1 kg/m^3, and lambda, mu follow from Eq. 3, Eq. 4.
+
+    Returns (vp, vs, rho, lam, mu, (alpha_vp, alpha_vs, alpha_rho))."""
+    vp, vs, rho = _f64(vp).copy(), _f64(vs).copy(), _f64(rho).copy()
+    g_rho = np.zeros_like(vp) if g_rho is None else _f64(g_rho)
+    g_vp, g_vs, g_rho_v = chain_to_velocity(g_lam, g_mu, g_rho, vp, vs, rho)
+    steps = [(vp, g_vp), (vs, g_vs)] + ([(rho, g_rho_v)] if update_rho else [])
+    alphas = [0.0, 0.0, 0.0]
+    for q, (m, gm) in enumerate(steps):
+        gmax = float(np.abs(gm[mask]).max()) if mask.any() else 0.0
+        mmax = float(np.abs(m[mask]).max()) if mask.any() else 0.0
+        alphas[q] = kappa * mmax / gmax if gmax > 0 else 0.0
+    for q, (m, gm) in enumerate(steps):
+        m[mask] -= alphas[q] * gm[mask]
+    vs = np.maximum(vs, 0.0)
+    vp = np.maximum(vp, 1.0)
+    rho = np.maximum(rho, 1.0)
+    lam, mu = lame(vp, vs, rho)
+    return vp, vs, rho, lam, mu, tuple(alphas)
+
+
 def inversion_mask(nr, nz, npml_r, npml_z, vs, windows=None):
     """Cells that are unknowns: formation cells (Vs > 0) outside the radial
     C-PML and inside the axial interior (outside the top and bottom C-PML) of

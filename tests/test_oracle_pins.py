@@ -489,3 +489,68 @@ def test_update_clamps_by_hand(orc):
     # cell 2: a negative gradient raises mu
     assert mu2[0, 2] == pytest.approx(2.0e9 + 0.5 * 4.0e7)
     assert lam2[0, 2] == pytest.approx(6.0e9 - 0.1 * 1.2e8)
+
+
+def test_update_velocity_by_hand(orc):
+    """Velocity-space update on hand-computed arrays: chain rule
+    g_Vp = 2 rho Vp g_lam, g_Vs = 2 rho Vs (g_mu - 2 g_lam),
+    g_rho|V = g_rho + (Vp^2 - 2 Vs^2) g_lam + Vs^2 g_mu, then
+    alpha = kappa max|m| / max|g| per parameter, the clamps, Eq. 3 / Eq. 4."""
+    vp = np.array([[3000.0, 4000.0]])
+    vs = np.array([[1500.0, 2000.0]])
+    rho = np.array([[2000.0, 2500.0]])
+    g_lam = np.array([[1e-12, -2e-12]])
+    g_mu = np.array([[3e-12, 1e-12]])
+    g_rho = np.array([[1e-6, 0.0]])
+    mask = np.array([[True, True]])
+    vp2, vs2, rho2, lam2, mu2, (av, aw, ar) = orc.update_velocity(
+        vp, vs, rho, g_lam, g_mu, g_rho, mask, 0.01, update_rho=True)
+    gvp = np.array([[2 * 2000 * 3000 * 1e-12, 2 * 2500 * 4000 * -2e-12]])
+    gvs = np.array([[2 * 2000 * 1500 * (3e-12 - 2e-12), 2 * 2500 * 2000 * (1e-12 + 4e-12)]])
+    grh = np.array([[1e-6 + (9e6 - 4.5e6) * 1e-12 + 2.25e6 * 3e-12,
+                     (16e6 - 8e6) * -2e-12 + 4e6 * 1e-12]])
+    assert av == pytest.approx(0.01 * 4000 / np.abs(gvp).max(), rel=1e-14)
+    assert aw == pytest.approx(0.01 * 2000 / np.abs(gvs).max(), rel=1e-14)
+    assert ar == pytest.approx(0.01 * 2500 / np.abs(grh).max(), rel=1e-14)
+    np.testing.assert_allclose(vp2, vp - av * gvp, rtol=1e-14)
+    np.testing.assert_allclose(vs2, vs - aw * gvs, rtol=1e-14)
+    np.testing.assert_allclose(rho2, rho - ar * grh, rtol=1e-14)
+    np.testing.assert_allclose(mu2, rho2 * vs2 ** 2, rtol=1e-14)
+    np.testing.assert_allclose(lam2, rho2 * vp2 ** 2 - 2 * rho2 * vs2 ** 2, rtol=1e-14)
+    # the largest relative change of each parameter is kappa of its largest value
+    assert np.abs(vp2 - vp).max() == pytest.approx(0.01 * 4000, rel=1e-12)
+    # without the density step rho is untouched and alpha_rho is 0
+    _, _, rho3, _, _, (_, _, ar3) = orc.update_velocity(vp, vs, rho, g_lam, g_mu, g_rho,
+                                                        mask, 0.01)
+    np.testing.assert_array_equal(rho3, rho)
+    assert ar3 == 0.0
+    # clamps: a cell whose Vs would turn negative keeps Vs = 0
+    vs4 = np.array([[10.0, 2000.0]])
+    _, vs5, _, _, mu5, _ = orc.update_velocity(vp, vs4, rho, g_lam, np.array([[1e-6, 0.0]]),
+                                               None, mask, 0.01)
+    assert vs5[0, 0] == 0.0 and mu5[0, 0] == 0.0
+
+
+@pytest.mark.parametrize("update_rho", [False, True])
+def test_update_velocity_descends(orc, tiny_gradient, update_rho):
+    """A small step of the velocity-space update lowers the misfit by what
+    the first-order expansion of J predicts, sum over the mask of
+    -alpha_m g_m^2 (FD-consistent gradient, correct sign, correct chain
+    rule and step)."""
+    w, fin, J = tiny_gradient
+    mask = orc.inversion_mask(w.nr, w.nz, w.npml_r, w.npml_z, w.vs)
+    vp, vs, rho = (w.vp.astype(np.float64), w.vs.astype(np.float64), w.rho.astype(np.float64))
+    kappa = 2e-6
+    vp2, vs2, rho2, _, _, (av, aw, ar) = orc.update_velocity(
+        vp, vs, rho, fin["g_lam"], fin["g_mu"], fin["g_rho"], mask, kappa,
+        update_rho=update_rho)
+    g_vp, g_vs, g_rho_v = orc.chain_to_velocity(fin["g_lam"], fin["g_mu"], fin["g_rho"], vp, vs,
+                                                rho)
+    pred = -(av * np.sum(g_vp[mask] ** 2) + aw * np.sum(g_vs[mask] ** 2))
+    if update_rho:
+        pred -= ar * np.sum(g_rho_v[mask] ** 2)
+    J0 = J(vp, vs, rho)
+    dJ = J(vp2, vs2, rho2) - J0
+    assert pred < 0 and dJ < 0
+    # the second-order remainder is ~1e-4 of the change at this step
+    assert abs(dJ - pred) <= 1e-3 * abs(pred), (dJ, pred)
