@@ -1,16 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the borehole FWI hot path on GB300.
 
-One step = one full inversion iteration of the production single-shot
-workload (nr 240 x nz 1600 cells, 8000 steps, 10 kHz): forward modelling,
-residual and misfit, adjoint modelling with the fused gradient correlation,
-per-cell gradients, preconditioner, and model update, all through the C ABI
-of libbh.
+One step = one full inversion iteration of the batched logging run (64
+shots stepped 0.15 m along a 20 m layered model, windows of 1400-2000 cells
+by 240, 8000 steps, 10 kHz): forward modelling of every shot, residual and
+misfit, adjoint modelling with the fused gradient correlation, per-cell
+gradients summed over the shots, preconditioner, and model update, all
+through the C ABI of libbh.  The density is known (the paper takes it from
+logs), so the iteration asks for the lambda and mu gradients only.  The
+single production shot (240 x 1600, 8000 steps) is timed after it as a
+secondary line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                  [--config c0..c4] [--cap-gb GB] [--snap fp32|bf16|fp16]
 
 Prints one JSON line (rank 0).  With N > 1 (launched by torchrun) every rank
-inverts its own independent shot (weak scaling, no data-path collective).
+inverts its own independent workload (weak scaling, no data-path collective).
 """
 from __future__ import annotations
 
@@ -33,34 +38,59 @@ UNIT = "Gcell-updates/s"
 PROFILE_EVERY = 64
 CPU_SAMPLE_STEPS = 150
 REF_SAMPLE_STEPS = 100
+L2_BYTES = 129e6
+# checkpoint byte cap per workload when --cap-gb is not given (0: every step
+# of the forward history stored)
+DEFAULT_CAP_GB = {"c0": 0.0, "c1": 0.0, "c2": 200.0, "c3": 4.0, "c4": 60.0}
+DEFAULT_SNAP = {"c4": "bf16"}
+E2E_STEPS = 3
+SECONDARY_STEPS = 10
 
-# Algorithmic bytes per cell and launch of each stepping kernel: every array
-# the kernel must touch, streamed once (FP32 fields, FP32 model/coefficients,
-# Kahan pairs, FP32 history), C-PML memories weighted by the fraction of
-# cells inside the layers (s = npml_r / nr + 2 npml_z / nz).
-def kernel_bytes_per_cell(kernel: str, s: float) -> float:
+# Algorithmic bytes per cell and step of each stepping kernel, from the FP32
+# byte model of the method: each of the six wavefields read and written once
+# per step (the velocity half-step owns v_r, v_z, the stress half-step the
+# four stresses); lambda, mu, rho read once per step (the stress half-step
+# reads lambda and mu, the velocity half-step rho), not counted when several
+# shots share one model (it then stays in L2); the C-PML memories read and
+# written in their strips only (s = npml_r / nr + 2 npml_z / nz of the
+# window; 16 s per half-step); the forward history v_r, v_z written by the
+# forward stress half-step of a stored step and read once by the adjoint;
+# the three gradient accumulators G_lambda, G_mu,nn, G_mu,rz read and
+# written.  Kahan compensation, the pseudo-Hessian and the density
+# correlation are not counted (implementation extras).
+def survey_bytes_per_cell(kernel: str, s: float, shared_model: bool, hist: float = 1.0) -> float:
+    m = 0.0 if shared_model else 1.0
+    return {
+        "fwd_vel": 16 + 4 * m + 16 * s,
+        "fwd_stress": 32 + 8 * m + 8 * hist + 16 * s,
+        "adj_stress": 16 + 8 * m + 8 + 24 + 16 * s,
+        "adj_vel": 32 + 4 * m + 16 * s,
+    }[kernel]
+
+
+# Every array a launch of this implementation touches, once per cell and
+# step (FP32 fields, per-window coefficient planes, Kahan pairs, pseudo-
+# Hessian, both history planes the adjoint reads): the traffic the kernels
+# would move with no cache reuse at all.
+def all_array_bytes_per_cell(kernel: str, s: float, with_rho: bool, hist: float = 1.0) -> float:
     return {
         # 4 stresses read, v_r v_z read+write, 2 buoyancies, 4 memories r+w
         "fwd_vel": 16 + 16 + 8 + 16 * s,
         # v_r v_z read, 4 stresses read+write, lambda mu mu_h, history write, 4 memories
-        "fwd_stress": 8 + 32 + 12 + 8 + 16 * s,
+        "fwd_stress": 8 + 32 + 12 + 8 * hist + 16 * s,
         # 4 adjoint stresses read, 2 adjoint velocities r+w, lambda mu mu_h,
-        # history v^{n+1/2} and v^{n-1/2}, 5 Kahan pairs r+w, 3 Hessian r+w,
-        # 4 adjoint memories (read one bank, write the other)
-        "adj_stress": 16 + 16 + 12 + 16 + 80 + 24 + 16 * s,
+        # history v^{n+1/2} (and v^{n-1/2} for rho), 3 (5) Kahan pairs r+w,
+        # 3 Hessian r+w, 4 adjoint memories (read one bank, write the other)
+        "adj_stress": 16 + 16 + 12 + 8 + 48 + 24 + 16 * s + (8 + 32 if with_rho else 0),
         # 2 adjoint velocities read, 4 adjoint stresses r+w, 2 buoyancies, 4 memories
         "adj_vel": 8 + 32 + 8 + 16 * s,
     }[kernel]
 
 
-# persistent kernels run both half-steps of every time step of a shot
-PERSIST_PARTS = {"fwd_persist": ("fwd_vel", "fwd_stress"), "adj_persist": ("adj_stress", "adj_vel")}
-
-
-def bytes_per_cell_step(kernel: str, s: float) -> float:
-    if kernel in PERSIST_PARTS:
-        return sum(kernel_bytes_per_cell(k, s) for k in PERSIST_PARTS[kernel])
-    return kernel_bytes_per_cell(kernel, s)
+# persistent kernels run both half-steps of every time step of a shot group
+PERSIST_PARTS = {"fwd_persist": ("fwd_vel", "fwd_stress"), "adj_persist": ("adj_stress", "adj_vel"),
+                 "fwd_vel": ("fwd_vel",), "fwd_stress": ("fwd_stress",),
+                 "adj_stress": ("adj_stress",), "adj_vel": ("adj_vel",)}
 
 
 def measured_peaks():
@@ -82,8 +112,9 @@ def source_sha():
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    """DRAM bytes per cell and step of a kernel from a committed ncu summary
+    (profiles/traffic_<kernel>_<workload>.txt), if it was taken on the
+    current kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.txt")
     if not os.path.exists(p):
         return None
@@ -96,7 +127,7 @@ def ncu_traffic(kernel: str, workload: str):
     if vals.get("source_sha") != source_sha():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals["dram_bytes_per_cell_step"])
     except (KeyError, ValueError):
         return None
 
@@ -256,34 +287,40 @@ def job_rate(cells_per_rank: float, world: int, ms: float) -> float:
 
 # ---------------------------------------------------------------- GPU arm
 
-def run_gpu(args, w):
+def shot_pml_fraction(w):
+    """Cell-weighted s = npml_r / nr + 2 npml_z / nz over the shot windows."""
+    cells = [w.nr * sh["nz"] for sh in w.shots]
+    ss = [w.npml_r / w.nr + 2.0 * w.npml_z / sh["nz"] for sh in w.shots]
+    return sum(c * x for c, x in zip(cells, ss)) / sum(cells)
+
+
+def state_bytes_per_group(w, group=32):
+    """Bytes of window state one shot group's launch touches: 6 fields and
+    the C-PML memories (strips) of the forward and adjoint, the per-window
+    coefficient planes, the Kahan pairs and pseudo-Hessian planes."""
+    P = (max(sh["nz"] for sh in w.shots) + 31) // 32 * 32
+    plane = w.nr * P * 4
+    s = shot_pml_fraction(w)
+    planes = 6 + 8 * s + 6 + 16 * s + 13 + 5
+    return min(group, w.nshots) * planes * plane
+
+
+def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_steps,
+            label):
+    """Time `steps` inversion iterations of workload w through the C ABI
+    (after `warmup`), then `e2e_steps` with host inputs; returns the JSON
+    fields of one bench line."""
+    import ctypes
     import numpy as np
     import torch
     import torch.distributed as dist
 
-    from paper_2005_00281_gb300.build import build_library
     from paper_2005_00281_gb300.bh import model_from_workload
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
-    build_library()
-
-    if world > 1 and rank > 0:
-        # every rank inverts its own independent shot: same sizes, other seed
-        w = apply_overrides(rank_workload(args.config, rank), args)
-
+    local = dev.index
     stream = torch.cuda.current_stream(dev)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     # observed data: forward modelling in the true model (outside the timing)
-    cap = int(args.cap_gb * 1e9)
-    prec = {"fp32": 0, "bf16": 1, "fp16": 2}[args.snap]
     true = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap)
     true.set_model(t(w.vp_true), t(w.vs_true), t(w.rho_true))
     wav = t(w.wavelet)
@@ -302,19 +339,18 @@ def run_gpu(args, w):
     resid = torch.empty_like(seis)
     shape = (w.nr, w.nz)
     g = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(3)]
+    g_rho = g[2] if with_rho else None
     vp_out = torch.empty(shape, dtype=torch.float32, device=dev)
     vs_out = torch.empty_like(vp_out)
     lib = m.lib
-    import ctypes
-    P = lambda x: ctypes.c_void_p(x.data_ptr())
+    P = lambda x: ctypes.c_void_p(x.data_ptr()) if x is not None else None
     Jc = ctypes.c_double()
-    alpha = (ctypes.c_double * 2)()
 
     def step(wav_d, obs_d):
         """One inversion iteration through the C ABI."""
         m._rc(lib.bh_forward(m.h, P(wav_d), P(seis)))
         m._rc(lib.bh_residual_misfit(m.h, P(seis), P(obs_d), P(resid), ctypes.byref(Jc)))
-        m._rc(lib.bh_adjoint_gradient(m.h, P(resid), P(g[0]), P(g[1]), P(g[2])))
+        m._rc(lib.bh_adjoint_gradient(m.h, P(resid), P(g[0]), P(g[1]), P(g_rho)))
         m._rc(lib.bh_precondition(m.h, P(g[0]), P(g[1]), ctypes.c_double(1e-3)))
         m._rc(lib.bh_update(m.h, P(g[0]), P(g[1]), ctypes.c_double(0.02), None, P(vp_out),
                             P(vs_out)))
@@ -325,7 +361,7 @@ def run_gpu(args, w):
             dist.barrier()
 
     # ---- device-resident inputs
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(wav, obs)
     m.set_model(*start_model)
     torch.cuda.synchronize()
@@ -338,7 +374,7 @@ def run_gpu(args, w):
     Js = []
     with ClockSampler(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             Js.append(step(wav, obs))
         e1.record(stream)
         torch.cuda.synchronize()
@@ -360,7 +396,7 @@ def run_gpu(args, w):
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         wav_d.copy_(wav_h, non_blocking=True)
         obs_d.copy_(obs_h, non_blocking=True)
         step(wav_d, obs_d)
@@ -374,72 +410,147 @@ def run_gpu(args, w):
     d2h = 8 + vp_h.numel() * 4 * 2
 
     cells_per_step = 2.0 * w.cell_steps()          # forward + adjoint cell updates (useful work)
-    value = job_rate(cells_per_step * args.steps, world, ms)
-    grads_per_s = world * w.nshots * args.steps / (ms / 1e3)
-    value_e2e = job_rate(cells_per_step * args.steps, world, ms_e2e)
+    value = job_rate(cells_per_step * steps, world, ms)
+    grads_per_s = world * w.nshots * steps / (ms / 1e3)
+    value_e2e = job_rate(cells_per_step * e2e_steps, world, ms_e2e)
 
     # ---- roofline of the dominant kernel (largest sampled time)
     peak, peak_kind = measured_peaks()
-    s = w.npml_r / w.nr + 2.0 * w.npml_z / w.nz
+    s = shot_pml_fraction(w)
+    shared = w.nshots > 1
     prof = {k: v for k, v in prof.items() if v[1]}
     dom = max(prof, key=lambda k: prof[k][0])
     win_cells = sum(w.nr * sh["nz"] for sh in w.shots)   # one pass over every window
     recompute = m.info("recompute_steps")
+    L = m.info("history_steps")
+    fwd_steps = w.nt + recompute
+    # forward steps that store history: every step when all are stored,
+    # else each segment once when it is re-run before its adjoint
+    hist_frac = 1.0 if L >= w.nt else w.nt / fwd_steps
+    ngroups = (w.nshots + 31) // 32
 
     def kernel_cells(k):
         """cells the sampled launches of kernel k processed in the timed region"""
         if k == "fwd_persist":
-            return win_cells * (w.nt + recompute) * args.steps
+            return win_cells * fwd_steps * steps
         if k == "adj_persist":
-            return win_cells * w.nt * args.steps
+            return win_cells * w.nt * steps
         # one launch per half-step and shot group: the sampled steps launch
         # every group once, and the groups together cover every window
-        ngroups = (w.nshots + 31) // 32
         return win_cells * prof[k][1] / ngroups
+
+    def per_cell(k, model):
+        hf = hist_frac if k.startswith("fwd") else 1.0
+        if model == "survey":
+            return sum(survey_bytes_per_cell(p, s, shared, hf) for p in PERSIST_PARTS[k])
+        return sum(all_array_bytes_per_cell(p, s, with_rho, hf) for p in PERSIST_PARTS[k])
 
     kernels = {}
     for k, (tms, nl) in prof.items():
-        alg = bytes_per_cell_step(k, s) * kernel_cells(k)
+        cells = kernel_cells(k)
+        sec = tms / 1e3
         kernels[k] = {"avg_us": 1e3 * tms / nl, "sampled_launches": nl,
-                      "alg_bytes_per_launch": alg / nl, "alg_GBps": alg / (tms / 1e3) / 1e9}
+                      "cells_per_launch": cells / nl,
+                      "alg_bytes_per_launch": per_cell(k, "survey") * cells / nl,
+                      "alg_GBps": per_cell(k, "survey") * cells / sec / 1e9,
+                      "all_array_GBps": per_cell(k, "all") * cells / sec / 1e9}
     achieved = kernels[dom]["alg_GBps"]
-    step_bytes = (sum(kernel_bytes_per_cell(k, s) for k in PERSIST_PARTS["fwd_persist"]) *
-                  win_cells * (w.nt + recompute) +
-                  sum(kernel_bytes_per_cell(k, s) for k in PERSIST_PARTS["adj_persist"]) *
-                  win_cells * w.nt)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+    dram_per_cell = ncu_traffic(dom, w.name)
+    ws = state_bytes_per_group(w)
+    if ws > L2_BYTES:
+        bound = "hbm"
+        bound_note = (f"window state of one shot group {ws / 1e9:.2f} GB > L2 129 MB: "
+                      "the state streams from HBM every half-step")
+    else:
+        bound = "l2"
+        bound_note = (f"window state {ws / 1e6:.0f} MB < L2 129 MB: the state stays in L2 "
+                      "and DRAM carries the forward history; latency- and barrier-bound, "
+                      "the HBM fraction is algorithmic bytes over time")
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak if achieved else None,
-                "traffic": ncu_traffic(dom, w.name), "peak_source": f"{peak_kind} (hbm_gbs)",
-                "note": "algorithmic bytes count every array a launch touches once per cell "
-                        "and step; a single 240 x 1600 window (~9 MB of state) stays in the "
-                        "129 MB L2, so there the kernels run from L2"}
+                "traffic": (dram_per_cell * kernels[dom]["cells_per_launch"]
+                            if dram_per_cell is not None else None),
+                "alg_bytes_per_cell_step": per_cell(dom, "survey"),
+                "frac_all_arrays": kernels[dom]["all_array_GBps"] / peak,
+                "all_array_bytes_per_cell_step": per_cell(dom, "all"),
+                "peak_source": f"{peak_kind} (hbm_gbs)", "note": bound_note}
+    step_bytes = (sum(survey_bytes_per_cell(k, s, shared, hist_frac)
+                      for k in PERSIST_PARTS["fwd_persist"]) * win_cells * fwd_steps +
+                  sum(survey_bytes_per_cell(k, s, shared)
+                      for k in PERSIST_PARTS["adj_persist"]) * win_cells * w.nt)
+    out = {"value": value, "ms_per_step": ms / steps, "config": workload_config(w),
+           "gradient_evals_per_s": grads_per_s,
+           "step_alg_GBps": world * step_bytes * steps / (ms / 1e3) / 1e9,
+           "step_frac": world * step_bytes * steps / (ms / 1e3) / 1e9 / peak,
+           "roofline": roofline, "kernels": kernels,
+           "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / e2e_steps,
+                   "steps": e2e_steps},
+           "gpu_launches": launches,
+           "clocks": clk.summary(), "J_first_last": [Js[0], Js[-1]],
+           "history": {k: m.info(k) for k in ("history_steps", "snapshots", "recompute_steps",
+                                              "snapshot_precision", "history_snapshot_bytes",
+                                              "tiles", "persistent_blocks_fwd",
+                                              "persistent_blocks_adj")},
+           "gradients": "lambda, mu and rho" if with_rho else "lambda and mu (rho known)"}
+    m.close()
+    return out
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+
+def run_gpu(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_00281_gb300.build import build_library
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    build_library()
+
+    if world > 1 and rank > 0:
+        # every rank inverts its own independent workload: same sizes, other seed
+        w = apply_overrides(rank_workload(args.config, rank), args)
+
+    cap_gb = DEFAULT_CAP_GB[args.config] if args.cap_gb is None else args.cap_gb
+    snap = args.snap or DEFAULT_SNAP.get(args.config, "fp32")
+    prec = {"fp32": 0, "bf16": 1, "fp16": 2}[snap]
+    res = measure(w, args, dev, world, rank, args.steps, args.warmup, int(cap_gb * 1e9), prec,
+                  args.with_rho, min(args.steps, E2E_STEPS), w.name)
+    line = {"metric": METRIC, "value": res.pop("value"), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res.pop("ms_per_step"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config(w),
-            "gradient_evals_per_s": grads_per_s,
-            "step_alg_GBps": world * step_bytes * args.steps / (ms / 1e3) / 1e9,
-            "roofline": roofline, "kernels": kernels,
-            "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / args.steps},
-            "gpu_launches": launches,
-            "clocks": clk.summary(), "J_first_last": [Js[0], Js[-1]],
-            "history": {k: m.info(k) for k in ("history_steps", "snapshots", "recompute_steps",
-                                               "snapshot_precision",
-                                               "history_snapshot_bytes", "tiles",
-                                               "persistent_blocks_fwd", "persistent_blocks_adj")},
-            "source_sha": source_sha()}
+            "data": "synthetic", "config": res.pop("config")}
+    line["config"]["checkpoint_cap_gb"] = cap_gb
+    line["config"]["snapshots"] = snap
+    line.update(res)
+    line["source_sha"] = source_sha()
+    if args.secondary and args.config != "c1" and not args.nt and not args.shots:
+        from synthetic import PRESETS
+        w1 = PRESETS["c1"](seed=rank)
+        sec = measure(w1, args, dev, world, rank, min(args.steps, SECONDARY_STEPS),
+                      min(args.warmup, 3), 0, 0, args.with_rho, 1, "c1")
+        line["secondary_c1"] = {
+            "value": sec["value"], "unit": UNIT, "ms_per_step": sec["ms_per_step"],
+            "steps": min(args.steps, SECONDARY_STEPS), "config": sec["config"],
+            "gradient_evals_per_s": sec["gradient_evals_per_s"], "roofline": sec["roofline"],
+            "kernels": sec["kernels"], "step_frac": sec["step_frac"], "clocks": sec["clocks"],
+            "gpu_launches": sec["gpu_launches"]}
     if rank == 0 and not args.no_cpu_baseline:
-        v, sec, threads = oracle_sample(w, CPU_SAMPLE_STEPS)
+        v, sec_s, threads = oracle_sample(w, CPU_SAMPLE_STEPS)
         line["cpu_baseline"] = {
             "value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first shot of {w.name}, nt truncated to {CPU_SAMPLE_STEPS} of {w.nt} "
-                      f"steps (forward + adjoint + gradient, {sec:.1f} s); forward loops "
+                      f"steps (forward + adjoint + gradient, {sec_s:.1f} s); forward loops "
                       f"OpenMP on {threads} threads, adjoint serial"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    m.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -461,11 +572,16 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
-    ap.add_argument("--cap-gb", type=float, default=0.0,
-                    help="checkpoint cap in GB (0: store every step of the forward history)")
-    ap.add_argument("--snap", default="fp32", choices=["fp32", "bf16", "fp16"],
-                    help="precision of the checkpoint snapshots")
+    ap.add_argument("--config", default="c2", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--cap-gb", type=float, default=None,
+                    help="checkpoint cap in GB (0: store every step of the forward history; "
+                         "default per workload: c2 200, c3 4, c4 60, else 0)")
+    ap.add_argument("--snap", default=None, choices=["fp32", "bf16", "fp16"],
+                    help="precision of the checkpoint snapshots (default fp32; c4 bf16)")
+    ap.add_argument("--with-rho", action="store_true",
+                    help="also compute the density gradient (the iteration does not use it)")
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false",
+                    help="skip the secondary single-shot (c1) line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-step", action="store_true",
                     help="one kernel launch per half-step for every run")

@@ -198,8 +198,10 @@ bh_status bh_precondition(bh_model* model, double* g_lam, double* g_mu, double e
  * so that no cell changes by more than kappa times the largest modulus
  * (the Method section has alpha set the largest change of the model):
  * alpha_m = kappa max|m| / max|g_m| over the inversion mask; then mu >= 0,
- * lambda + 2 mu >= rho (1 m/s)^2, and Vp, Vs from Eq. 11, Eq. 12.  The
- * model's own coefficients are rebuilt; any stored history is invalidated.
+ * lambda + 2 mu >= rho (1 m/s)^2, and Vp, Vs from Eq. 11, Eq. 12 in the
+ * updated cells; cells outside the mask keep the Vp, Vs the model was given
+ * bit for bit.  The model's own coefficients are rebuilt; any stored
+ * history is invalidated.
  *   g_lam, g_mu  device [nr][nz_global] double
  *   alpha_out    host double[2] (alpha_lambda, alpha_mu) or NULL; when
  *                given, the call synchronises the stream
@@ -222,8 +224,35 @@ bh_status bh_update(bh_model* model, const double* g_lam, const double* g_mu, do
 bh_status bh_velocity_gradient(bh_model* model, const double* g_lam, const double* g_mu,
                                const double* g_rho, float* g_vp, float* g_vs, float* g_rho_v);
 
-/* Current model velocities (Eq. 11, Eq. 12).  vp, vs: device [nr][nz_global]. */
+/*
+ * Gradient-descent update in the velocities, and optionally the density,
+ * instead of the Lame parameters (Eq. 9, Eq. 10 applied to Vp, Vs, rho; the
+ * Method section derives Vp, Vs from lambda, mu by Eq. 11, Eq. 12 and takes
+ * rho from density logs, so stepping rho is optional).  The gradients with
+ * respect to (Vp, Vs, rho) follow from g_lam, g_mu, g_rho by the chain rule
+ * of bh_velocity_gradient, in FP64; each parameter m steps by
+ * alpha_m = kappa max|m| / max|g_m| over the inversion mask; then
+ * Vs >= 0, Vp >= 1 m/s, rho >= 1 kg/m^3, and lambda, mu follow from Eq. 3,
+ * Eq. 4.  Cells outside the mask keep their values bit for bit.  The
+ * model's own coefficients are rebuilt; any stored history is invalidated.
+ *   g_lam, g_mu  device [nr][nz_global] double (raw or preconditioned)
+ *   g_rho    device [nr][nz_global] double or NULL (no density gradient)
+ *   update_rho  0: rho is held fixed; 1: rho steps too
+ *   alpha_out   host double[3] (alpha_Vp, alpha_Vs, alpha_rho) or NULL;
+ *               when given, the call synchronises the stream
+ *   vp_out, vs_out, rho_out  device [nr][nz_global] float32 or NULL
+ * Errors: BH_ERR_INVALID_ARG (kappa < 0, update_rho not 0 or 1), BH_ERR_CUDA.
+ */
+bh_status bh_update_velocity(bh_model* model, const double* g_lam, const double* g_mu,
+                             const double* g_rho, int update_rho, double kappa,
+                             double* alpha_out, float* vp_out, float* vs_out, float* rho_out);
+
+/* Current model velocities: those given to bh_model_create / bh_set_model,
+ * as the updates left them.  vp, vs: device [nr][nz_global] float32. */
 bh_status bh_get_model(bh_model* model, float* vp, float* vs);
+
+/* Current model density.  rho: device [nr][nz_global] float32. */
+bh_status bh_get_density(bh_model* model, float* rho);
 
 /*
  * Sampled kernel timing (tracing aid; the paper has no counterpart).  With
@@ -263,7 +292,9 @@ bh_status bh_profile_reset(bh_model* model);
  *   J        host double; the call synchronises `stream`
  *   stream   cudaStream_t (NULL = legacy default stream)
  * The first call on a device looks up the scratch address on that device
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture.  A device reset (cudaDeviceReset)
+ * after the first call is not supported: the kept address would be stale.
  * All calls share the one scratch array: calls whose work overlaps on the
  * GPU (unordered streams) race and may return a wrong J.
  * Errors: BH_ERR_INVALID_ARG (NULL pointer, n > BH_NOALLOC_MAX_SAMPLES),
@@ -304,7 +335,10 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
  * (stepping-kernel launches of the last bh_forward + bh_adjoint_gradient),
  * "history_snapshot_bytes", "device_bytes", "kernel_launches" (kernels the
  * model has launched since it was created, for counting the launches of a
- * timed region).
+ * timed region), "state_version" (changes whenever the stored forward
+ * history is replaced or invalidated: bh_forward, bh_set_model, bh_update,
+ * bh_update_velocity; a caller that keeps a forward run for a later
+ * bh_adjoint_gradient can check that it is still the stored one).
  *   value  host double
  * Errors: BH_ERR_INVALID_ARG (unknown key).
  */

@@ -25,7 +25,8 @@ EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
            "bh_update", "bh_get_model", "bh_status_string", "bh_last_error",
            "bh_profile_enable", "bh_profile_read", "bh_profile_reset",
            "bh_residual_misfit_noalloc", "bh_set_option", "bh_get_info",
-           "bh_checkpoint_plan", "bh_velocity_gradient")
+           "bh_checkpoint_plan", "bh_velocity_gradient", "bh_update_velocity",
+           "bh_get_density")
 NOALLOC_MAX_SAMPLES = 33554432
 KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel", "fwd_persist", "adj_persist")
 
@@ -93,6 +94,11 @@ def load_library(path: str | None = None):
     lib.bh_velocity_gradient.restype = st
     lib.bh_get_model.argtypes = [vp, vp, vp]
     lib.bh_get_model.restype = st
+    lib.bh_get_density.argtypes = [vp, vp]
+    lib.bh_get_density.restype = st
+    lib.bh_update_velocity.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_double), vp, vp, vp]
+    lib.bh_update_velocity.restype = st
     lib.bh_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.bh_profile_enable.restype = st
     lib.bh_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -246,6 +252,25 @@ class Model:
         self._rc(self.lib.bh_update(self.h, _ptr(g_lam), _ptr(g_mu), float(kappa), alpha,
                                     _ptr(vp), _ptr(vs)))
         return (alpha[0], alpha[1]), vp, vs
+
+    def update_velocity(self, g_lam, g_mu, g_rho=None, update_rho=False, kappa=0.02,
+                        want_model=True):
+        """bh_update_velocity: step in (Vp, Vs) and, with update_rho, rho.
+        Returns ((alpha_vp, alpha_vs, alpha_rho), vp, vs, rho)."""
+        alpha = (ctypes.c_double * 3)()
+        out = [None, None, None]
+        if want_model:
+            out = [torch.empty((self.nr, self.nz), dtype=torch.float32, device=self.device)
+                   for _ in range(3)]
+        self._rc(self.lib.bh_update_velocity(self.h, _ptr(g_lam), _ptr(g_mu), _ptr(g_rho),
+                                             int(bool(update_rho)), float(kappa), alpha,
+                                             *(_ptr(x) for x in out)))
+        return (alpha[0], alpha[1], alpha[2]), out[0], out[1], out[2]
+
+    def density(self):
+        rho = torch.empty((self.nr, self.nz), dtype=torch.float32, device=self.device)
+        self._rc(self.lib.bh_get_density(self.h, _ptr(rho)))
+        return rho
 
     def set_option(self, key, value):
         """bh_set_option: "persistent", "barrier_timeout_ms", "barrier_extra_arrivals"."""

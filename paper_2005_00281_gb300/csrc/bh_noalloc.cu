@@ -36,7 +36,9 @@ static_assert((size_t)kMaxBlocks * kPerBlock == BH_NOALLOC_MAX_SAMPLES, "limit")
 static __device__ __align__(256) double g_noalloc_scratch[kMaxBlocks + 1];
 
 // pass 1: residual and per-block sum of squares, fixed order inside a block
-__global__ void __launch_bounds__(kThreads) k_misfit_partial(size_t n, const float* __restrict__ mod,
+// resid may alias mod (each element is read, then written, by one thread),
+// so neither carries __restrict__
+__global__ void __launch_bounds__(kThreads) k_misfit_partial(size_t n, const float* mod,
                                                              const float* __restrict__ obs,
                                                              float* resid, double* scratch)
 {

@@ -10,17 +10,26 @@ namespace bh {
 
 constexpr int kRedThreads = 1024;
 
-// lambda, mu (Eq. 3, Eq. 4) and rho per cell, plus the fluid flag source
+// lambda, mu (Eq. 3, Eq. 4) per cell from velocities and density
+__device__ __forceinline__ void lame_f32(float vp, float vs, float rho, float* lam, float* mu)
+{
+    *mu = rho * vs * vs;
+    *lam = rho * vp * vp - 2.f * rho * vs * vs;
+}
+
+// lambda, mu and rho per cell; the caller's Vp, Vs are kept as given (cells
+// that no update touches report them back unchanged)
 __global__ void k_setup_cells(int n, const float* __restrict__ vp, const float* __restrict__ vs,
                               const float* __restrict__ rho, float* lam, float* mu,
-                              float* rho_out)
+                              float* rho_out, float* vp_out, float* vs_out)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     float r = rho[k], a = vp[k], b = vs[k];
     rho_out[k] = r;
-    mu[k] = r * b * b;
-    lam[k] = r * a * a - 2.f * r * b * b;
+    vp_out[k] = a;
+    vs_out[k] = b;
+    lame_f32(a, b, r, &lam[k], &mu[k]);
 }
 
 // buoyancy at v_r / v_z nodes and harmonic mu at trz nodes of the global
@@ -122,7 +131,8 @@ __global__ void __launch_bounds__(kRedThreads) k_max_f32(size_t n, const float* 
 
 // Eq. 5 residual and Eq. 1 misfit, J summed in FP64 in a fixed order:
 // thread t adds elements t, t + T, t + 2T, ... then a fixed binary tree.
-__global__ void __launch_bounds__(kRedThreads) k_misfit(size_t n, const float* __restrict__ mod,
+// resid may alias mod (each element is read, then written, by one thread).
+__global__ void __launch_bounds__(kRedThreads) k_misfit(size_t n, const float* mod,
                                                         const float* __restrict__ obs,
                                                         float* resid, double* J)
 {
@@ -253,11 +263,13 @@ __global__ void __launch_bounds__(kPartThreads) k_update_alpha_finish(const doub
     }
 }
 
-// Eq. 9, Eq. 10 inside the mask, then mu >= 0, lambda + 2 mu >= rho (1 m/s)^2
+// Eq. 9, Eq. 10 inside the mask, then mu >= 0, lambda + 2 mu >= rho (1 m/s)^2,
+// and the cell's velocities from Eq. 11, Eq. 12 (cells outside the mask keep
+// theirs)
 __global__ void k_update_apply(size_t n, const uint8_t* __restrict__ mask,
                                const double* __restrict__ g_lam, const double* __restrict__ g_mu,
                                const double* __restrict__ alpha, const float* __restrict__ rho,
-                               float* lam, float* mu)
+                               float* lam, float* mu, float* vp, float* vs)
 {
     size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || !mask[k]) return;
@@ -266,19 +278,85 @@ __global__ void k_update_apply(size_t n, const uint8_t* __restrict__ mask,
     if (m < 0.0) m = 0.0;
     double floor = (double)rho[k] - 2.0 * m;
     if (l < floor) l = floor;
-    lam[k] = (float)l;
-    mu[k] = (float)m;
+    const float lf = (float)l, mf = (float)m;
+    lam[k] = lf;
+    mu[k] = mf;
+    const double r = rho[k];
+    vp[k] = (float)sqrt(((double)lf + 2.0 * (double)mf) / r);
+    vs[k] = (float)sqrt((double)mf / r);
 }
 
-// Eq. 11, Eq. 12
-__global__ void k_velocities(size_t n, const float* __restrict__ lam, const float* __restrict__ mu,
-                             const float* __restrict__ rho, float* vp, float* vs)
+// ---- update in (Vp, Vs) and optionally rho (Eq. 9, Eq. 10 applied to the
+// velocities; chain rule of Eq. 3, Eq. 4 in FP64)
+
+struct VelGrad {
+    double vp, vs, rho;
+};
+
+__device__ __forceinline__ VelGrad vel_grad(double vp, double vs, double rho, double gl, double gm,
+                                            double gr)
+{
+    VelGrad g;
+    g.vp = 2.0 * rho * vp * gl;
+    g.vs = 2.0 * rho * vs * (gm - 2.0 * gl);
+    g.rho = gr + (vp * vp - 2.0 * vs * vs) * gl + vs * vs * gm;
+    return g;
+}
+
+// pass 1: masked maxima of |Vp|, |Vs|, |rho|, |g_Vp|, |g_Vs|, |g_rho|
+__global__ void __launch_bounds__(kPartThreads) k_vupdate_part(
+    size_t n, const uint8_t* __restrict__ mask, const float* __restrict__ vp,
+    const float* __restrict__ vs, const float* __restrict__ rho, const double* __restrict__ g_lam,
+    const double* __restrict__ g_mu, const double* __restrict__ g_rho, double* part)
+{
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        if (mask[k]) {
+            const double a = vp[k], b = vs[k], r = rho[k];
+            const VelGrad g = vel_grad(a, b, r, g_lam[k], g_mu[k], g_rho ? g_rho[k] : 0.0);
+            v[0] = fmax(v[0], fabs(a));
+            v[1] = fmax(v[1], fabs(b));
+            v[2] = fmax(v[2], fabs(r));
+            v[3] = fmax(v[3], fabs(g.vp));
+            v[4] = fmax(v[4], fabs(g.vs));
+            v[5] = fmax(v[5], fabs(g.rho));
+        }
+    block_max_parts<6>(v, part);
+}
+
+// pass 2: alpha[0..2] for Vp, Vs, rho (alpha[2] = 0 unless rho steps)
+__global__ void __launch_bounds__(kPartThreads) k_vupdate_finish(const double* __restrict__ part,
+                                                                 int nparts, double kappa,
+                                                                 int update_rho, double* alpha)
+{
+    double r[6];
+    finish_max_parts<6>(part, nparts, r);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 3; ++q) alpha[q] = r[3 + q] > 0.0 ? kappa * r[q] / r[3 + q] : 0.0;
+        if (!update_rho) alpha[2] = 0.0;
+    }
+}
+
+// pass 3: the step inside the mask, clamps Vs >= 0, Vp >= 1 m/s,
+// rho >= 1 kg/m^3, then lambda, mu by Eq. 3, Eq. 4 (FP32, as at set-up)
+__global__ void k_vupdate_apply(size_t n, const uint8_t* __restrict__ mask,
+                                const double* __restrict__ g_lam, const double* __restrict__ g_mu,
+                                const double* __restrict__ g_rho, const double* __restrict__ alpha,
+                                int update_rho, float* vp, float* vs, float* rho, float* lam,
+                                float* mu)
 {
     size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    double l = lam[k], m = mu[k], r = rho[k];
-    if (vp) vp[k] = (float)sqrt((l + 2.0 * m) / r);
-    if (vs) vs[k] = (float)sqrt(m / r);
+    if (k >= n || !mask[k]) return;
+    const double a = vp[k], b = vs[k], r = rho[k];
+    const VelGrad g = vel_grad(a, b, r, g_lam[k], g_mu[k], g_rho ? g_rho[k] : 0.0);
+    const float na = (float)fmax(a - alpha[0] * g.vp, 1.0);
+    const float nb = (float)fmax(b - alpha[1] * g.vs, 0.0);
+    const float nr = update_rho ? (float)fmax(r - alpha[2] * g.rho, 1.0) : rho[k];
+    vp[k] = na;
+    vs[k] = nb;
+    rho[k] = nr;
+    lame_f32(na, nb, nr, &lam[k], &mu[k]);
 }
 
 }  // namespace bh
@@ -357,8 +435,10 @@ namespace bh {
 // Gradients with respect to (Vp, Vs, rho) from those with respect to
 // (lambda, mu, rho), by Eq. 3 and Eq. 4: lambda = rho (Vp^2 - 2 Vs^2),
 // mu = rho Vs^2.  g_rho may be null (then rho is held fixed: output 0).
-__global__ void k_velocity_gradient(size_t n, const float* __restrict__ lam,
-                                    const float* __restrict__ mu, const float* __restrict__ rho,
+// Vp, Vs are the model's own velocities (as given, or as the last update
+// left them).
+__global__ void k_velocity_gradient(size_t n, const float* __restrict__ vp,
+                                    const float* __restrict__ vs, const float* __restrict__ rho,
                                     const double* __restrict__ g_lam,
                                     const double* __restrict__ g_mu,
                                     const double* __restrict__ g_rho, float* g_vp, float* g_vs,
@@ -366,14 +446,10 @@ __global__ void k_velocity_gradient(size_t n, const float* __restrict__ lam,
 {
     size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const double r = rho[k], m = mu[k], l = lam[k];
-    const double vs2 = m / r, vp2 = (l + 2.0 * m) / r;
-    const double vp = sqrt(vp2), vs = sqrt(vs2);
-    const double gl = g_lam[k], gm = g_mu[k];
-    if (g_vp) g_vp[k] = (float)(2.0 * r * vp * gl);
-    if (g_vs) g_vs[k] = (float)(2.0 * r * vs * (gm - 2.0 * gl));
-    if (g_rho_v)
-        g_rho_v[k] = (float)((g_rho ? g_rho[k] : 0.0) + (vp2 - 2.0 * vs2) * gl + vs2 * gm);
+    const VelGrad g = vel_grad(vp[k], vs[k], rho[k], g_lam[k], g_mu[k], g_rho ? g_rho[k] : 0.0);
+    if (g_vp) g_vp[k] = (float)g.vp;
+    if (g_vs) g_vs[k] = (float)g.vs;
+    if (g_rho_v) g_rho_v[k] = (float)g.rho;
 }
 
 }  // namespace bh

@@ -45,6 +45,7 @@ struct bh_model {
     double vpmax = 0.0;
     // model, global [nr][nzg]
     float *d_lam = nullptr, *d_mu = nullptr, *d_rho = nullptr;
+    float *d_vp = nullptr, *d_vs = nullptr;  // the model's velocities (as given or as updated)
     float *d_bvr = nullptr, *d_bvz = nullptr, *d_muh = nullptr;
     uint8_t* d_mask = nullptr;
     uint8_t* d_colcov = nullptr;
@@ -78,6 +79,9 @@ struct bh_model {
     double* d_scal = nullptr;   // small device scalars
     double* d_part = nullptr;   // per-block partial maxima, 4 x kMaxParts
     bool have_forward = false, have_gradient = false;
+    // changes whenever the stored forward history is replaced or invalidated
+    // (bh_forward, bh_set_model, bh_update, bh_update_velocity)
+    long long state_version = 0;
     std::string err;
     // 1: one cooperative launch per run; 0: one launch per half-step; 2 (auto):
     // cooperative when every block of a shot group has at most one tile
@@ -145,6 +149,7 @@ void free_model(bh_model* m)
 {
     if (!m) return;
     void* bufs[] = {m->d_lam,   m->d_mu,     m->d_rho,   m->d_bvr,    m->d_bvz,    m->d_muh,
+                    m->d_vp,    m->d_vs,
                     m->d_mask,  m->d_colcov, m->d_rprof, m->d_zprof,  m->d_recmap, m->d_fwd,
                     m->d_adj,   m->d_hist,   m->d_snap,  m->d_snap_max, m->d_tiles,  m->d_Hg,
                     m->d_scal,  m->d_bar,    m->d_wcoef, m->d_wins,   m->d_part};
@@ -290,9 +295,8 @@ bh_status load_model(bh_model* m, const float* vp, const float* vs, const float*
     // the C-PML profiles keep the max Vp of the model given at creation
     if (first) m->vpmax = vpmax;
     const int tpb = 256;
-    k_setup_cells<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, m->stream>>>((int)n, vp, vs, rho,
-                                                                         m->d_lam, m->d_mu,
-                                                                         m->d_rho);
+    k_setup_cells<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, m->stream>>>(
+        (int)n, vp, vs, rho, m->d_lam, m->d_mu, m->d_rho, m->d_vp, m->d_vs);
     BH_KERNEL(m);
     if (first) {
         k_setup_mask<<<grid2d(nr, nzg), block2d(), 0, m->stream>>>(nr, nzg, g.npml_r, vs,
@@ -301,6 +305,7 @@ bh_status load_model(bh_model* m, const float* vp, const float* vs, const float*
     }
     BH_TRY(rebuild_coefficients(m));
     m->have_forward = m->have_gradient = false;
+    ++m->state_version;
     return BH_OK;
 }
 
@@ -753,6 +758,18 @@ bh_status plan_checkpoints(bh_model* m, size_t cap)
     return BH_OK;
 }
 
+// the model's velocities / density into caller buffers (each may be NULL)
+bh_status copy_model_out(bh_model* m, float* vp, float* vs, float* rho)
+{
+    const size_t bytes = (size_t)m->grid.nr * m->nzg * sizeof(float);
+    const float* src[3] = {m->d_vp, m->d_vs, m->d_rho};
+    float* dst[3] = {vp, vs, rho};
+    for (int q = 0; q < 3; ++q)
+        if (dst[q])
+            BH_CUDA(m, cudaMemcpyAsync(dst[q], src[q], bytes, cudaMemcpyDeviceToDevice, m->stream));
+    return BH_OK;
+}
+
 }  // namespace
 
 // error text of calls that have no model (read with bh_last_error(NULL))
@@ -851,6 +868,8 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_lam, ng));
     CK(dalloc(&m->d_mu, ng));
     CK(dalloc(&m->d_rho, ng));
+    CK(dalloc(&m->d_vp, ng));
+    CK(dalloc(&m->d_vs, ng));
     CK(dalloc(&m->d_bvr, ng));
     CK(dalloc(&m->d_bvz, ng));
     CK(dalloc(&m->d_muh, ng));
@@ -867,7 +886,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_snap_max, (size_t)m->nsnap * nshots * kFwdPlanes));
     CK(dalloc(&m->d_Hg, 2 * ng));
     CK(dalloc(&m->d_scal, 16));
-    CK(dalloc(&m->d_part, 4 * (size_t)kMaxParts));
+    CK(dalloc(&m->d_part, 8 * (size_t)kMaxParts));
     CK(dalloc(&m->d_bar, 4));
     {
         int dev = 0, sms = 0, coop = 0, nb = 0;
@@ -944,6 +963,7 @@ bh_status bh_forward(bh_model* m, const float* wavelet, float* seis)
     const size_t pl = plane(m);
     const size_t seis_per_shot = (size_t)m->nrec_max * gd.nt;
     m->have_forward = m->have_gradient = false;
+    ++m->state_version;
     m->runs_fwd = 0;
     for (int s = 0; s < m->nshots; ++s) {
         m->h_shots[s].q.wavelet = wavelet;
@@ -1082,19 +1102,49 @@ bh_status bh_update(bh_model* m, const double* g_lam, const double* g_mu, double
     BH_KERNEL(m);
     const unsigned nb = (unsigned)((ng + 255) / 256);
     k_update_apply<<<nb, 256, 0, m->stream>>>(ng, m->d_mask, g_lam, g_mu, m->d_scal + 4,
-                                             m->d_rho, m->d_lam, m->d_mu);
+                                             m->d_rho, m->d_lam, m->d_mu, m->d_vp, m->d_vs);
     BH_KERNEL(m);
     BH_TRY(rebuild_coefficients(m));
-    if (vp_out || vs_out) {
-        k_velocities<<<nb, 256, 0, m->stream>>>(ng, m->d_lam, m->d_mu, m->d_rho, vp_out, vs_out);
-        BH_KERNEL(m);
-    }
+    BH_TRY(copy_model_out(m, vp_out, vs_out, nullptr));
     if (alpha_out) {
         BH_CUDA(m, cudaMemcpyAsync(alpha_out, m->d_scal + 4, 2 * sizeof(double),
                                    cudaMemcpyDeviceToHost, m->stream));
         BH_CUDA(m, cudaStreamSynchronize(m->stream));
     }
     m->have_forward = m->have_gradient = false;
+    ++m->state_version;
+    return BH_OK;
+}
+
+bh_status bh_update_velocity(bh_model* m, const double* g_lam, const double* g_mu,
+                             const double* g_rho, int update_rho, double kappa, double* alpha_out,
+                             float* vp_out, float* vs_out, float* rho_out)
+{
+    if (!m || !g_lam || !g_mu) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
+    if (!(kappa >= 0.0)) return fail(m, BH_ERR_INVALID_ARG, "kappa must be >= 0");
+    if (update_rho != 0 && update_rho != 1)
+        return fail(m, BH_ERR_INVALID_ARG, "update_rho must be 0 or 1");
+    const size_t ng = (size_t)m->grid.nr * m->nzg;
+    const int np = parts_for(ng);
+    k_vupdate_part<<<np, kPartThreads, 0, m->stream>>>(ng, m->d_mask, m->d_vp, m->d_vs, m->d_rho,
+                                                       g_lam, g_mu, g_rho, m->d_part);
+    BH_KERNEL(m);
+    k_vupdate_finish<<<1, kPartThreads, 0, m->stream>>>(m->d_part, np, kappa, update_rho,
+                                                        m->d_scal + 8);
+    BH_KERNEL(m);
+    k_vupdate_apply<<<(unsigned)((ng + 255) / 256), 256, 0, m->stream>>>(
+        ng, m->d_mask, g_lam, g_mu, g_rho, m->d_scal + 8, update_rho, m->d_vp, m->d_vs, m->d_rho,
+        m->d_lam, m->d_mu);
+    BH_KERNEL(m);
+    BH_TRY(rebuild_coefficients(m));
+    BH_TRY(copy_model_out(m, vp_out, vs_out, rho_out));
+    if (alpha_out) {
+        BH_CUDA(m, cudaMemcpyAsync(alpha_out, m->d_scal + 8, 3 * sizeof(double),
+                                   cudaMemcpyDeviceToHost, m->stream));
+        BH_CUDA(m, cudaStreamSynchronize(m->stream));
+    }
+    m->have_forward = m->have_gradient = false;
+    ++m->state_version;
     return BH_OK;
 }
 
@@ -1104,7 +1154,7 @@ bh_status bh_velocity_gradient(bh_model* m, const double* g_lam, const double* g
     if (!m || !g_lam || !g_mu) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
     const size_t ng = (size_t)m->grid.nr * m->nzg;
     k_velocity_gradient<<<(unsigned)((ng + 255) / 256), 256, 0, m->stream>>>(
-        ng, m->d_lam, m->d_mu, m->d_rho, g_lam, g_mu, g_rho, g_vp, g_vs, g_rho_v);
+        ng, m->d_vp, m->d_vs, m->d_rho, g_lam, g_mu, g_rho, g_vp, g_vs, g_rho_v);
     BH_KERNEL(m);
     return BH_OK;
 }
@@ -1112,11 +1162,13 @@ bh_status bh_velocity_gradient(bh_model* m, const double* g_lam, const double* g
 bh_status bh_get_model(bh_model* m, float* vp, float* vs)
 {
     if (!m || !vp || !vs) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
-    const size_t ng = (size_t)m->grid.nr * m->nzg;
-    k_velocities<<<(unsigned)((ng + 255) / 256), 256, 0, m->stream>>>(ng, m->d_lam, m->d_mu,
-                                                                      m->d_rho, vp, vs);
-    BH_KERNEL(m);
-    return BH_OK;
+    return copy_model_out(m, vp, vs, nullptr);
+}
+
+bh_status bh_get_density(bh_model* m, float* rho)
+{
+    if (!m || !rho) return fail(m, BH_ERR_INVALID_ARG, "NULL argument");
+    return copy_model_out(m, nullptr, nullptr, rho);
 }
 
 bh_status bh_set_option(bh_model* m, const char* key, double value)
@@ -1162,6 +1214,7 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
                  (2.0 * (m->L + 1) + (double)m->nsnap * kFwdPlanes * (m->snap_prec ? 0.5 : 1.0));
     else if (k == "snapshot_precision") *value = m->snap_prec;
     else if (k == "kernel_launches") *value = (double)m->launches;
+    else if (k == "state_version") *value = (double)m->state_version;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
                      (kFwdPlanes + kAdjPlanes + 5.0 + 2.0 * (m->L + 1)) +

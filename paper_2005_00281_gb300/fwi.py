@@ -112,7 +112,7 @@ def main(argv=None):
     # gradient of J with respect to Vp at the start model, against central differences
     vp = t(w.vp).requires_grad_(True)
     vs, rho = t(w.vs), t(w.rho)
-    J0 = misfit(BhWave.apply(vp, vs, rho, m, wav), obs)
+    J0 = misfit(BhWave.apply(vp, vs, rho, m, wav), obs, m)
     J0.backward()
     g = vp.grad.detach().cpu().numpy()
     rng = np.random.default_rng(args.seed)
@@ -130,7 +130,7 @@ def main(argv=None):
             for sgn in (1.0, -1.0):
                 vp2 = t(w.vp).clone()
                 vp2[i, j] += sgn * h
-                vals.append(float(misfit(BhWave.apply(vp2, vs, rho, m, wav), obs)))
+                vals.append(float(misfit(BhWave.apply(vp2, vs, rho, m, wav), obs, m)))
             fd_rows.append((int(i), int(j), (vals[0] - vals[1]) / (2 * h), float(g[i, j])))
     gmax = float(np.abs(g).max())
     fd_err = max(abs(fd - ad) for _, _, fd, ad in fd_rows) / gmax

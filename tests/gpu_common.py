@@ -59,3 +59,43 @@ def oracle_gradient(w, obs):
     rounded to float32 like the GPU copy)."""
     obs32 = obs.astype(np.float32).astype(np.float64)
     return O.shot_gradient(oracle_grid(w), w.vp, w.vs, w.rho, w.wavelet, w.shots, obs32)
+
+
+def regions(w):
+    """Named index sets of one window (window = global model): the axis row,
+    the rows on both sides of the fluid-solid wall, the last rows and columns
+    before the C-PML, and the neighbourhoods of the source and of every
+    receiver.  Relative errors over a whole array can hide a wrong band of
+    small values; these are checked one by one."""
+    nr, nz, pr, pz = w.nr, w.nz, w.npml_r, w.npml_z
+    fl = int(np.argmax(w.vs[:, nz // 2] > 0))      # first formation row
+    sh = w.shots[0]
+    si, sj = sh["src"]
+    out = {
+        "axis": np.s_[0:1, pz: nz - pz],
+        "wall": np.s_[max(fl - 1, 0): fl + 1, pz: nz - pz],
+        "radial_pml_edge": np.s_[nr - pr - 2: nr - pr, pz: nz - pz],
+        "top_pml_edge": np.s_[0: nr - pr, pz: pz + 2],
+        "bottom_pml_edge": np.s_[0: nr - pr, nz - pz - 2: nz - pz],
+        "source": np.s_[max(si - 3, 0): si + 4, max(sj - 3, pz): min(sj + 4, nz - pz)],
+    }
+    for k, rj in enumerate(sh["rec_iz"]):
+        out[f"receiver{k}"] = np.s_[0:3, max(rj - 2, pz): min(rj + 3, nz - pz)]
+    return out
+
+
+def region_errors(w, a, b):
+    """{region: relative L2 error of a against b over the region} for the
+    regions where b is not zero."""
+    out = {}
+    for name, sl in regions(w).items():
+        ref = np.asarray(b)[sl]
+        if np.linalg.norm(ref) > 0:
+            out[name] = rel_l2(np.asarray(a)[sl], ref)
+    return out
+
+
+def max_abs_error(a, b):
+    """max |a - b| / max |b|"""
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(np.asarray(a, dtype=np.float64) - b)) / np.max(np.abs(b)))

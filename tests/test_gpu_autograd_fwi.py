@@ -31,7 +31,7 @@ def test_autograd_matches_finite_differences(torch_cuda):
     vp = t(w.vp).requires_grad_(True)
     vs = t(w.vs).requires_grad_(True)
     rho = t(w.rho).requires_grad_(True)
-    J = misfit(BhWave.apply(vp, vs, rho, m, wav), obs)
+    J = misfit(BhWave.apply(vp, vs, rho, m, wav), obs, m)
     J.backward()
     rng = np.random.default_rng(3)
     cells = [(int(rng.integers(w.nr - w.npml_r - 14, w.nr - w.npml_r)),
@@ -45,7 +45,7 @@ def test_autograd_matches_finite_differences(torch_cuda):
                 with torch.no_grad():
                     args = [a.detach().clone() for a in (vp, vs, rho)]
                     args[k][i, j] += sgn * h
-                    vals.append(float(misfit(BhWave.apply(*args, m, wav), obs)))
+                    vals.append(float(misfit(BhWave.apply(*args, m, wav), obs, m)))
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(fd - float(g[i, j])) <= 2e-2 * scale, (i, j, fd, float(g[i, j]))
     m.close()
@@ -76,3 +76,45 @@ def test_fwi_loop_reduces_misfit_and_resumes(torch_cuda, tmp_path):
     assert st2.iteration == 5 and st2.J[-1] < st.J[0]
     m.close()
     m2.close()
+
+
+def test_backward_checks_the_stored_forward(torch_cuda):
+    """The model keeps one forward history: a backward after another forward
+    on the same model raises instead of returning the other run's gradient."""
+    torch = torch_cuda
+    from paper_2005_00281_gb300.autograd import BhWave, misfit
+    from paper_2005_00281_gb300.bh import model_from_workload
+
+    w = tiny_borehole(seed=12, nt=120)
+    m = model_from_workload(w)
+    t = lambda a: torch.from_numpy(a).cuda()
+    wav = t(w.wavelet)
+    vp = t(w.vp).requires_grad_(True)
+    seis = BhWave.apply(vp, t(w.vs), t(w.rho), m, wav)
+    J = misfit(seis, torch.zeros_like(seis), m)
+    with torch.no_grad():
+        BhWave.apply(t(w.vp_true), t(w.vs_true), t(w.rho_true), m, wav)
+    with pytest.raises(RuntimeError, match="another forward"):
+        J.backward()
+    m.close()
+
+
+def test_misfit_is_the_library_misfit(torch_cuda):
+    """BhMisfit's value is bh_residual_misfit's FP64 J and its gradient the
+    library's residual."""
+    torch = torch_cuda
+    from paper_2005_00281_gb300.autograd import misfit
+    from paper_2005_00281_gb300.bh import model_from_workload
+
+    w = tiny_borehole(seed=2, nt=64)
+    m = model_from_workload(w)
+    rng = np.random.default_rng(0)
+    shape = m.seis_shape()
+    a = torch.from_numpy(rng.standard_normal(shape).astype(np.float32)).cuda().requires_grad_(True)
+    b = torch.from_numpy(rng.standard_normal(shape).astype(np.float32)).cuda()
+    J = misfit(a, b, m)
+    resid, J_lib = m.residual_misfit(a.detach(), b)
+    assert float(J) == J_lib
+    (3.0 * J).backward()
+    assert torch.equal(a.grad, 3.0 * resid)
+    m.close()

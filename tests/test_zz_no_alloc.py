@@ -58,6 +58,11 @@ def test_noalloc_matches_model_entry_point(env):
         torch.cuda.synchronize()
         assert torch.equal(resid, ref_resid), call
         assert J == pytest.approx(ref_J, rel=1e-12), (call, J, ref_J)
+        # the residual may overwrite the modelled data in place
+        inplace = mod.clone()
+        J2 = _noalloc(bh, torch, inplace, obs, inplace)
+        torch.cuda.synchronize()
+        assert torch.equal(inplace, ref_resid) and J2 == J, call
     m.close()
 
 
