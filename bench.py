@@ -41,7 +41,7 @@ REF_SAMPLE_STEPS = 100
 L2_BYTES = 129e6
 # checkpoint byte cap per workload when --cap-gb is not given (0: every step
 # of the forward history stored)
-DEFAULT_CAP_GB = {"c0": 0.0, "c1": 0.0, "c2": 200.0, "c3": 4.0, "c4": 60.0}
+DEFAULT_CAP_GB = {"c0": 0.0, "c1": 0.0, "c2": 240.0, "c3": 4.0, "c4": 60.0}
 DEFAULT_SNAP = {"c4": "bf16"}
 E2E_STEPS = 3
 SECONDARY_STEPS = 10
@@ -575,7 +575,7 @@ def parse_args(argv=None):
     ap.add_argument("--config", default="c2", choices=["c0", "c1", "c2", "c3", "c4"])
     ap.add_argument("--cap-gb", type=float, default=None,
                     help="checkpoint cap in GB (0: store every step of the forward history; "
-                         "default per workload: c2 200, c3 4, c4 60, else 0)")
+                         "default per workload: c2 240, c3 4, c4 60, else 0)")
     ap.add_argument("--snap", default=None, choices=["fp32", "bf16", "fp16"],
                     help="precision of the checkpoint snapshots (default fp32; c4 bf16)")
     ap.add_argument("--with-rho", action="store_true",

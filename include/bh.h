@@ -113,11 +113,13 @@ bh_status bh_set_model(bh_model* model, const float* vp, const float* vs, const 
  *
  * Forward history.  The adjoint correlation needs v^{n+1/2} of every step.
  * With checkpoint_cap_bytes = 0 every step is stored (nt + 1 slots of v_r,
- * v_z per shot).  With a cap, the steps are cut into segments of L steps, a
- * binomial (Griewank-Walther) checkpoint schedule over the segments keeps
- * at most s full forward states per shot, and each segment is re-run once
- * into an (L + 1)-slot history window before its adjoint; L and s are the
- * pair that fits the cap with the fewest recomputed steps.  With FP32
+ * v_z per shot).  With a cap, the history of the last steps (the tail) is
+ * stored by the forward sweep itself, and the steps before it are cut into
+ * segments of L steps: a binomial (Griewank-Walther) checkpoint schedule
+ * over the segments keeps at most s full forward states per shot, and each
+ * segment is re-run once into an (L + 1)-slot history window before its
+ * adjoint; L, s and the tail are the plan that fits the cap with the fewest
+ * recomputed steps (bh_plan_history).  With FP32
  * snapshots the results are bit-identical to storing every step.  With
  * snapshot_precision 1 (BF16) or 2 (FP16) a snapshot takes half the bytes;
  * every plane (each wavefield and each C-PML memory of each shot) is stored
@@ -329,7 +331,8 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
 
 /*
  * Read-only facts about a model (the paper has no counterpart):
- * "history_steps" (L), "snapshots" (s), "recompute_steps" (forward steps
+ * "history_steps" (L), "snapshots" (s), "tail_steps" (steps whose history
+ * the forward sweep stores itself), "recompute_steps" (forward steps
  * re-run by one bh_adjoint_gradient), "tiles", "persistent",
  * "persistent_blocks_fwd", "persistent_blocks_adj", "persistent_runs_per_step"
  * (stepping-kernel launches of the last bh_forward + bh_adjoint_gradient),
@@ -358,6 +361,26 @@ bh_status bh_get_info(bh_model* model, const char* key, double* value);
  */
 bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
                              int* n_actions, int* spine, int max_spine, int* n_spine);
+
+/*
+ * The forward-history plan bh_model_create picks under a byte cap (host
+ * only, no GPU; the paper has no counterpart).  The nt steps split into
+ * segments of L steps and a tail of the last `tail` steps, whose history
+ * the forward sweep stores as it goes; every segment is re-run once into the
+ * history window before its adjoint, from one of nsnap snapshots (binomial
+ * schedule when they are fewer than the segments).  Memory:
+ * (max(tail, L) + 1) history slots of hist_step_bytes each plus nsnap
+ * snapshots of snapshot_bytes each, at most cap_bytes; the plan with the
+ * fewest recomputed forward steps wins, then the least memory.  tail = nt
+ * (L = nt, nsnap = 0, recompute = 0) stores every step.
+ *   hist_step_bytes  v_r, v_z planes of one step of every shot
+ *   snapshot_bytes   one full forward state of every shot
+ *   L, nsnap, tail, recompute  host outputs
+ * Errors: BH_ERR_INVALID_ARG, BH_ERR_OOM (cap below one history window).
+ */
+bh_status bh_plan_history(int nt, double hist_step_bytes, double snapshot_bytes,
+                          size_t cap_bytes, int* L, int* nsnap, int* tail,
+                          long long* recompute);
 
 /* Static description of a status code. */
 const char* bh_status_string(bh_status status);

@@ -26,7 +26,7 @@ EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
            "bh_profile_enable", "bh_profile_read", "bh_profile_reset",
            "bh_residual_misfit_noalloc", "bh_set_option", "bh_get_info",
            "bh_checkpoint_plan", "bh_velocity_gradient", "bh_update_velocity",
-           "bh_get_density")
+           "bh_get_density", "bh_plan_history")
 NOALLOC_MAX_SAMPLES = 33554432
 KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel", "fwd_persist", "adj_persist")
 
@@ -112,6 +112,10 @@ def load_library(path: str | None = None):
     lib.bh_checkpoint_plan.argtypes = [ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ip, ip,
                                        ctypes.c_int, ip]
     lib.bh_checkpoint_plan.restype = st
+    lib.bh_plan_history.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_size_t, ip, ip, ip,
+                                    ctypes.POINTER(ctypes.c_longlong)]
+    lib.bh_plan_history.restype = st
     lib.bh_get_info.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.bh_get_info.restype = st
     lib.bh_residual_misfit_noalloc.argtypes = [vp, vp, vp, ctypes.c_size_t,
@@ -356,3 +360,17 @@ def checkpoint_plan(nseg, nsnap):
     spine = [(sp[2 * k], sp[2 * k + 1]) for k in range(ns.value)]
     actions = [(acts[3 * k], acts[3 * k + 1], acts[3 * k + 2]) for k in range(na.value)]
     return spine, actions
+
+
+def plan_history(nt, hist_step_bytes, snapshot_bytes, cap_bytes):
+    """bh_plan_history (host only): (L, nsnap, tail, recomputed steps) of the
+    forward-history plan under a byte cap."""
+    lib = load_library()
+    L, s, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc_ = ctypes.c_longlong()
+    rc = lib.bh_plan_history(int(nt), float(hist_step_bytes), float(snapshot_bytes),
+                             int(cap_bytes), ctypes.byref(L), ctypes.byref(s), ctypes.byref(t),
+                             ctypes.byref(rc_))
+    if rc != BH_OK:
+        raise BhError(rc, lib.bh_last_error(None).decode())
+    return L.value, s.value, t.value, rc_.value

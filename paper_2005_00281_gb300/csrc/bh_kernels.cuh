@@ -773,10 +773,13 @@ __device__ __forceinline__ float2 kahan_step(float2 s, float x)
 // S.{trr..trz} hold dJ/dtau^{n+1}; S.{vr,vz} accumulate to dJ/dv^{n+1/2};
 // psi[4..7] are the adjoint memories read side, psi_w[4..7] the write side.
 // fcur: v_r, v_z planes of v^{n+1/2}; fprev: those of v^{n-1/2}.
-// Density and shear-mu correlations (Eq. 8 and the density term) and the
-// shear pseudo-Hessian at one tile's own nodes for reverse step n, from the
-// staged forward velocities v^{n+1/2} (fr, fz), v^{n-1/2} (fprev), the own
-// adjoint velocities Av^{n+1/2} and the own adjoint trz of step n+1.
+// Shear-mu correlation (Eq. 8), the shear pseudo-Hessian and, with RHO,
+// the density correlation at one tile's own nodes for reverse step n, from
+// the staged forward velocities v^{n+1/2} (fr, fz), v^{n-1/2} (fprev, read
+// only with RHO), the own adjoint velocities Av^{n+1/2} and the own adjoint
+// trz of step n+1.  Without RHO (the caller asks for no density gradient)
+// neither v^{n-1/2} nor the density accumulators are touched.
+template <bool RHO>
 __device__ __forceinline__ void adj_corr_shear(const WinK& g, const AdjK& q, const Own& o,
                                                const float* fprev, const Tile& T_fr,
                                                const Tile& T_fz, const V4& Arz,
@@ -785,19 +788,25 @@ __device__ __forceinline__ void adj_corr_shear(const WinK& g, const AdjK& q, con
     const int plane = g.nr * g.P, c = o.c, rr = o.rr, cc = o.cc, i = o.i;
     const float dt = g.dt;
     float2 gbz[4], gmr[4], gbr[4];
-    ld4f2(q.G_bz + c, gbz);
-    const V4 pz = ld4cg(fprev + plane + c);
-    V4 hmr{}, pr{};
+    V4 pz{}, hmr{}, pr{};
+    if (RHO) {
+        ld4f2(q.G_bz + c, gbz);
+        pz = ld4cg(fprev + plane + c);
+    }
     if (i >= 1) {
         ld4f2(q.G_murz + c, gmr);
         hmr = ld4cg(q.H_murz + c);
-        pr = ld4cg(fprev + c);
-        ld4f2(q.G_br + c, gbr);
+        if (RHO) {
+            pr = ld4cg(fprev + c);
+            ld4f2(q.G_br + c, gbr);
+        }
     }
     const V4 fz0 = lds4(T_fz, rr, cc);
+    if (RHO) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) gbz[e] = kahan_step(gbz[e], (fz0.v[e] - pz.v[e]) * avz[e]);
-    st4f2(q.G_bz + c, o.j, g.nz, gbz);
+        for (int e = 0; e < 4; ++e) gbz[e] = kahan_step(gbz[e], (fz0.v[e] - pz.v[e]) * avz[e]);
+        st4f2(q.G_bz + c, o.j, g.nz, gbz);
+    }
     if (i >= 1) {
         const V12 fr12 = lds12(T_fr, rr, cc - 4);
         const V4 fzm1 = lds4(T_fz, rr - 1, cc), fzm2 = lds4(T_fz, rr - 2, cc),
@@ -810,11 +819,11 @@ __device__ __forceinline__ void adj_corr_shear(const WinK& g, const AdjK& q, con
                 d4(fz0.v[e], fzm1.v[e], fzp1.v[e], fzm2.v[e]) * g.inv_dr;
             gmr[e] = kahan_step(gmr[e], dt * gam * Arz.v[e]);
             hmr2[e] = hmr.v[e] + dt * gam * gam;
-            gbr[e] = kahan_step(gbr[e], (fr12.v[4 + e] - pr.v[e]) * avr[e]);
+            if (RHO) gbr[e] = kahan_step(gbr[e], (fr12.v[4 + e] - pr.v[e]) * avr[e]);
         }
         st4f2(q.G_murz + c, o.j, g.nz, gmr);
         st4(q.H_murz + c, o.j, g.nz, hmr2);
-        st4f2(q.G_br + c, o.j, g.nz, gbr);
+        if (RHO) st4f2(q.G_br + c, o.j, g.nz, gbr);
     }
 }
 
@@ -823,6 +832,7 @@ __device__ __forceinline__ void adj_corr_shear(const WinK& g, const AdjK& q, con
 // (the block keeps this tile, so the f tiles are still in shared memory).
 // bar (or null): the block arrives at the grid barrier once the adjoint
 // velocities are stored; the own-node correlations follow the arrival.
+template <bool RHO>
 __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const AdjK& q, const float* fcur,
                                                 const float* fprev, int i0, int j0, int flags,
@@ -1008,7 +1018,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     st4f2(q.G_munn + c, o.j, g.nz, gm);
     st4(q.H_lam + c, o.j, g.nz, hl2);
     st4(q.H_munn + c, o.j, g.nz, hm2);
-    if (!defer) adj_corr_shear(g, q, o, fprev, T_fr, T_fz, lds4(T_rz, rr, cc), avz, avr);
+    if (!defer) adj_corr_shear<RHO>(g, q, o, fprev, T_fr, T_fz, lds4(T_rz, rr, cc), avz, avr);
 }
 
 // Transpose of the velocity step of one tile at reverse step n: S.{vr,vz}
@@ -1019,6 +1029,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
 // next on this tile; its launch-invariant tiles are staged here, after the
 // block's arrival at the grid barrier (bar, or null: no barrier), and after
 // the correlations deferred by the stress step (fprev_b, or null).
+template <bool RHO>
 __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
                                              const AdjK& q, int n, int i0, int j0, int flags,
                                              const float* next_fcur, const float* fprev_b,
@@ -1190,7 +1201,7 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
             const V4 az = ld4cg(S.vz + c);
             V4 ar{};
             if (i >= 1) ar = ld4cg(S.vr + c);
-            adj_corr_shear(g, q, o, fprev_b, sm.f[0], sm.f[1], o_rz, az.v, ar.v);
+            adj_corr_shear<RHO>(g, q, o, fprev_b, sm.f[0], sm.f[1], o_rz, az.v, ar.v);
         }
         __syncthreads();  // the f tiles are read above and refilled below
     }
@@ -1269,7 +1280,7 @@ __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>
 // statics / prefetch: the block keeps one tile for the whole run, so the
 // velocity step of reverse step n stages the stress step's launch-invariant
 // tiles for step n-1 (AdjSmem)
-template <int N>
+template <int N, bool RHO>
 __device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>& T, int n,
                                                int t, bool statics, bool defer,
                                                const BarK* bar, unsigned& epoch, AdjSmem& sm)
@@ -1277,12 +1288,12 @@ __device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
-    adj_stress_tile(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, n - r.hist_n0 + 1),
+    adj_stress_tile<RHO>(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, n - r.hist_n0 + 1),
                     hist_slot(sh, n - r.hist_n0), tk.y, tk.z, tk.w, statics, defer, bar, epoch,
                     sm);
 }
 
-template <int N>
+template <int N, bool RHO>
 __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
                                             bool prefetch, bool deferred, const BarK* bar,
                                             unsigned& epoch, AdjSmem& sm)
@@ -1292,7 +1303,8 @@ __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T
     const int parity = (r.nt - 1 - n) & 1;
     // v^{n-1/2}: fcur of step n-1 (prefetch) and fprev of step n (deferred)
     const float* prev = hist_slot(sh, n - r.hist_n0);
-    adj_vel_tile(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w, prefetch ? prev : nullptr,
+    adj_vel_tile<RHO>(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w,
+                      prefetch ? prev : nullptr,
                  deferred ? prev : nullptr, bar, epoch, sm);
 }
 
@@ -1319,25 +1331,25 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_stress(RunK r, int n,
     pdl_launch_dependents();
 }
 
-template <int N>
+template <int N, bool RHO>
 __global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n,
                                                          const __grid_constant__ ShotTable<N> T)
 {
     __shared__ AdjSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_adj_stress(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    run_adj_stress<N, RHO>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
-template <int N>
+template <int N, bool RHO>
 __global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
                                                       const __grid_constant__ ShotTable<N> T)
 {
     __shared__ AdjSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_adj_vel(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    run_adj_vel<N, RHO>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1363,7 +1375,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(RunK r, BarK b,
 }
 
 // reverse steps n1-1 down to n0 of every shot of the table in one cooperative launch
-template <int N>
+template <int N, bool RHO>
 __global__ void __launch_bounds__(kThreads, 5) k_adj_persist(RunK r, BarK b,
                                                              const __grid_constant__ ShotTable<N> T)
 {
@@ -1374,12 +1386,12 @@ __global__ void __launch_bounds__(kThreads, 5) k_adj_persist(RunK r, BarK b,
     for (int n = r.n1 - 1; n >= r.n0; --n) {
         // the block's last tile of a phase arrives at the barrier itself
         for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_adj_stress(r, T, n, t, one && n < r.n1 - 1, one,
+            run_adj_stress<N, RHO>(r, T, n, t, one && n < r.n1 - 1, one,
                            t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
         for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_adj_vel(r, T, n, t, one && n > r.n0, one,
+            run_adj_vel<N, RHO>(r, T, n, t, one && n > r.n0, one,
                         t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;

@@ -70,6 +70,9 @@ struct bh_model {
     // history window and checkpoint schedule
     int L = 0;                  // steps per history window (nt: store every step)
     int nsnap = 0;              // stored snapshot slots (slot 0 is the zero state)
+    int tail = 0;               // last steps whose history the forward sweep stores itself
+    int n_tail0 = 0;            // first step of that tail (nt - tail); segments cover [0, n_tail0)
+    int hist_slots = 0;         // slots of the history buffer per shot
     std::vector<Act> plan;      // reversal after the forward sweep
     std::vector<std::pair<int, int>> spine;  // (segment, slot) taken during the sweep
     long long recompute_steps = 0;
@@ -88,6 +91,9 @@ struct bh_model {
     int persistent = 2;
     int fwd_blocks = 0, adj_blocks = 0;       // co-resident blocks, 1-shot kernels
     int fwd_blocks_g = 0, adj_blocks_g = 0;   // same, kGroup-shot kernels
+    // the adjoint kernels without the density correlation (no g_rho asked)
+    int adj_blocks_nr = 0, adj_blocks_g_nr = 0;
+    bool adj_rho = true;                      // the running bh_adjoint_gradient wants g_rho
     unsigned* d_bar = nullptr;          // barrier: count, -, error flag
     double barrier_timeout_ms = 2000.0;
     int barrier_extra = 0;              // test knob: arrivals that never come
@@ -454,7 +460,7 @@ bh_status setup_shots(bh_model* m)
         k.a.H_lam = a + 32 * pl;
         k.a.H_munn = a + 33 * pl;
         k.a.H_murz = a + 34 * pl;
-        k.hist = m->d_hist + (size_t)s * (m->L + 1) * 2 * pl;
+        k.hist = m->d_hist + (size_t)s * m->hist_slots * 2 * pl;
         if (s % kGroup == 0) {
             m->group_tile_off.push_back((int)tiles.size());
             m->group_ntiles.push_back(0);
@@ -551,12 +557,17 @@ BarK make_bar(const bh_model* m, int blocks)
 // half-step lets the block scheduler overlap one block's staging with
 // another's compute and wins (GB300: 16 % at 3125 tiles, 44 % at 795 tiles;
 // the persistent form wins by 4.5 % at 750 tiles).
+int adj_blocks_for(const bh_model* m, bool one_shot)
+{
+    if (m->adj_rho) return one_shot ? m->adj_blocks : m->adj_blocks_g;
+    return one_shot ? m->adj_blocks_nr : m->adj_blocks_g_nr;
+}
+
 bool persistent_for(const bh_model* m, int grp, bool adjoint)
 {
     if (m->persistent != 2) return m->persistent != 0;
     const bool one = m->nshots == 1;
-    const int blocks = adjoint ? (one ? m->adj_blocks : m->adj_blocks_g)
-                               : (one ? m->fwd_blocks : m->fwd_blocks_g);
+    const int blocks = adjoint ? adj_blocks_for(m, one) : (one ? m->fwd_blocks : m->fwd_blocks_g);
     return m->group_ntiles[grp] <= blocks;
 }
 
@@ -619,21 +630,22 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
     return BH_OK;
 }
 
-// Reverse steps n1-1 down to n0 of the shots of one group.
-template <int N>
+// Reverse steps n1-1 down to n0 of the shots of one group; RHO: with the
+// density correlation.
+template <int N, bool RHO>
 bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
 {
     RunK r = make_run(m, grp, n0, n1, hist_n0, false);
     ShotTable<N> T = group_table<N>(m, grp);
     const dim3 blk = block_tiles();
     if (persistent_for(m, grp, true)) {
-        const int blocks = std::min(r.ntiles, N == 1 ? m->adj_blocks : m->adj_blocks_g);
+        const int blocks = std::min(r.ntiles, adj_blocks_for(m, N == 1));
         BarK b = make_bar(m, blocks);
         BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
         void* args[] = {&r, &b, &T};
         size_t e = prof_begin(m, BH_KERNEL_ADJ_PERSIST, 0);
-        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_adj_persist<N>, dim3(blocks), blk,
-                                               args, 0, m->stream));
+        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_adj_persist<N, RHO>, dim3(blocks),
+                                               blk, args, 0, m->stream));
         ++m->launches;
         prof_end(m, e);
         return check_barrier(m);
@@ -641,11 +653,11 @@ bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
     const dim3 grd(r.ntiles);
     for (int n = n1 - 1; n >= n0; --n) {
         size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
-        BH_CUDA(m, launch_pdl(k_adj_stress<N>, grd, blk, m->stream, r, n, T));
+        BH_CUDA(m, launch_pdl(k_adj_stress<N, RHO>, grd, blk, m->stream, r, n, T));
         ++m->launches;
         prof_end(m, e);
         e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
-        BH_CUDA(m, launch_pdl(k_adj_vel<N>, grd, blk, m->stream, r, n, T));
+        BH_CUDA(m, launch_pdl(k_adj_vel<N, RHO>, grd, blk, m->stream, r, n, T));
         ++m->launches;
         prof_end(m, e);
     }
@@ -672,8 +684,14 @@ bh_status run_adjoint(bh_model* m, int n0, int n1, int hist_n0, long long* runs)
     const int ngroups = (int)m->group_ntiles.size();
     for (int grp = 0; grp < ngroups; ++grp) {
         *runs += persistent_for(m, grp, true) ? 1 : 2 * (n1 - n0);
-        if (m->nshots == 1) BH_TRY(run_adjoint_group<1>(m, grp, n0, n1, hist_n0));
-        else BH_TRY(run_adjoint_group<kGroup>(m, grp, n0, n1, hist_n0));
+        const bool one = m->nshots == 1;
+        if (m->adj_rho) {
+            if (one) BH_TRY((run_adjoint_group<1, true>(m, grp, n0, n1, hist_n0)));
+            else BH_TRY((run_adjoint_group<kGroup, true>(m, grp, n0, n1, hist_n0)));
+        } else {
+            if (one) BH_TRY((run_adjoint_group<1, false>(m, grp, n0, n1, hist_n0)));
+            else BH_TRY((run_adjoint_group<kGroup, false>(m, grp, n0, n1, hist_n0)));
+        }
     }
     return BH_OK;
 }
@@ -714,26 +732,68 @@ bh_status snapshot(bh_model* m, int slot, bool take)
     return BH_OK;
 }
 
-// Choose the history window and snapshot count under a byte cap: for each
-// window length, the slots that fit; keep the plan with the fewest
-// recomputed forward steps.
-bh_status plan_checkpoints(bh_model* m, size_t cap)
+// History plan under a byte cap.  The nt steps are split into segments of L
+// steps over [0, n_tail0) and a tail [n_tail0, nt) whose history the forward
+// sweep stores as it goes (tail = nt: every step stored, nothing re-run).
+// Each segment is re-run once into the history window before its adjoint,
+// from a snapshot taken during the sweep (binomial schedule when there are
+// fewer snapshots than segments).  Memory: (max(tail, L) + 1) history slots
+// plus the snapshots.  Recomputed steps: the segments' steps plus the
+// schedule's advances.  Among the plans that fit, the fewest recomputed
+// steps win, then the least memory.
+struct HistPlan {
+    int L = 0, nsnap = 0, tail = 0;
+    long long recompute = -1;
+    double bytes = 0.0;
+};
+
+HistPlan choose_history_plan(int nt, double hist_step, double snap, double cap)
 {
-    const int nt = m->grid.nt;
-    const double pl_bytes = (double)plane(m) * sizeof(float) * m->nshots;
-    const double snap_bytes = kFwdPlanes * pl_bytes * (m->snap_prec ? 0.5 : 1.0);
-    long long best = LLONG_MAX;
-    int bestL = 0, bests = 0;
+    HistPlan best;
+    auto consider = [&](int L, int s, int tail, long long cost, double bytes) {
+        if (bytes > cap) return;
+        if (best.recompute < 0 || cost < best.recompute ||
+            (cost == best.recompute && bytes < best.bytes)) {
+            best.L = L;
+            best.nsnap = s;
+            best.tail = tail;
+            best.recompute = cost;
+            best.bytes = bytes;
+        }
+    };
+    // every step stored
+    consider(nt, 0, nt, 0, (nt + 1.0) * hist_step);
+    if (best.recompute == 0) return best;
+    // a stored tail and a snapshot at every earlier segment start: nseg' =
+    // segments before the tail, recompute = nseg' L (no advances)
+    for (int L = 1; L < nt; ++L) {
+        const int nseg = (nt + L - 1) / L;
+        for (int nsp = 1; nsp < nseg; ++nsp) {
+            const int n0 = nsp * L;
+            const int tail = nt - n0;
+            const double bytes = (std::max(tail, L) + 1.0) * hist_step + (nsp - 1.0) * snap;
+            if (bytes <= cap) {
+                // more segments only cost more recompute: the first that fits
+                consider(L, nsp - 1, tail, n0, bytes);
+                break;
+            }
+            // with L hist_step > snap every further segment frees memory;
+            // otherwise nothing later fits either
+            if (L * hist_step <= snap) break;
+        }
+    }
+    if (best.recompute >= 0) return best;
+    // no room for a snapshot at every segment: no tail, the window plus the
+    // snapshots that fit, binomial schedule
     std::vector<int> Ls;
     for (int L = 1; L < nt; L *= 2) Ls.push_back(L);
     for (int L : {3, 5, 6, 10, 12, 20, 24, 40, 48, 80, 96, 100, 160, 200, 250, 400, 500})
         if (L < nt) Ls.push_back(L);
-    Ls.push_back(nt);
     for (int L : Ls) {
-        const double hist = (L + 1.0) * 2.0 * pl_bytes;
-        if (hist > (double)cap) continue;
+        const double hist = (L + 1.0) * hist_step;
+        if (hist > cap) continue;
         const int nseg = (nt + L - 1) / L;
-        long long s = (long long)(((double)cap - hist) / snap_bytes);
+        long long s = (long long)((cap - hist) / snap);
         s = std::min<long long>(s, nseg - 1);
         if (s < 0) continue;
         if (nseg > 2000 && s == 0) continue;  // quadratic plans are not worth listing
@@ -741,20 +801,30 @@ bh_status plan_checkpoints(bh_model* m, size_t cap)
         std::vector<std::pair<int, int>> spine;
         long long adv = 0;
         build_plan(nseg, (int)s, &plan, &spine, &adv);
-        const long long cost = adv * (long long)L + (L < nt ? nt : 0);
-        if (cost < best || (cost == best && s < bests)) {
-            best = cost;
-            bestL = L;
-            bests = (int)s;
-        }
+        consider(L, (int)s, 0, adv * (long long)L + nt, hist + s * snap);
     }
-    if (bestL == 0)
+    return best;
+}
+
+bh_status plan_checkpoints(bh_model* m, size_t cap)
+{
+    const int nt = m->grid.nt;
+    const double pl_bytes = (double)plane(m) * sizeof(float) * m->nshots;
+    const double snap_bytes = kFwdPlanes * pl_bytes * (m->snap_prec ? 0.5 : 1.0);
+    const HistPlan hp = choose_history_plan(nt, 2.0 * pl_bytes, snap_bytes, (double)cap);
+    if (hp.recompute < 0)
         return fail(m, BH_ERR_OOM, "checkpoint_cap_bytes too small for one history window");
-    m->L = bestL;
-    m->nsnap = bests;
+    m->L = hp.L;
+    m->nsnap = hp.nsnap;
+    m->tail = hp.tail;
+    m->n_tail0 = nt - hp.tail;
+    m->hist_slots = (hp.tail >= nt ? nt : std::max(hp.tail, hp.L)) + 1;
+    m->plan.clear();
+    m->spine.clear();
     long long adv = 0;
-    build_plan((nt + bestL - 1) / bestL, bests, &m->plan, &m->spine, &adv);
-    m->recompute_steps = adv * bestL + (bestL < nt ? nt : 0);
+    if (m->n_tail0 > 0)
+        build_plan((m->n_tail0 + hp.L - 1) / hp.L, hp.nsnap, &m->plan, &m->spine, &adv);
+    m->recompute_steps = adv * hp.L + m->n_tail0;
     return BH_OK;
 }
 
@@ -859,7 +929,9 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     if (g.checkpoint_cap_bytes == 0) {
         m->L = g.nt;  // store every step
         m->nsnap = 0;
-        m->plan.assign(1, Act{ACT_REVERSE, 0, 0});
+        m->tail = g.nt;
+        m->n_tail0 = 0;
+        m->hist_slots = g.nt + 1;
         m->recompute_steps = 0;
     } else {
         bh_status st = plan_checkpoints(m, g.checkpoint_cap_bytes);
@@ -880,7 +952,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_adj, (size_t)nshots * kAdjPlanes * pl));
     CK(dalloc(&m->d_wcoef, (size_t)nshots * 5 * pl));
     CK(dalloc(&m->d_wins, (size_t)nshots));
-    CK(dalloc(&m->d_hist, (size_t)nshots * (m->L + 1) * 2 * pl));
+    CK(dalloc(&m->d_hist, (size_t)nshots * m->hist_slots * 2 * pl));
     CK(dalloc((char**)&m->d_snap,
               (size_t)m->nsnap * nshots * kFwdPlanes * pl * (m->snap_prec ? 2 : 4)));
     CK(dalloc(&m->d_snap_max, (size_t)m->nsnap * nshots * kFwdPlanes));
@@ -894,22 +966,33 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         // the adjoint tiles want 5 blocks of ~42 KB shared memory per SM
-        const void* big_smem[] = {(const void*)k_adj_persist<1>, (const void*)k_adj_persist<kGroup>,
-                                  (const void*)k_adj_stress<1>, (const void*)k_adj_stress<kGroup>,
-                                  (const void*)k_adj_vel<1>, (const void*)k_adj_vel<kGroup>};
+        const void* big_smem[] = {
+            (const void*)k_adj_persist<1, true>,  (const void*)k_adj_persist<kGroup, true>,
+            (const void*)k_adj_stress<1, true>,   (const void*)k_adj_stress<kGroup, true>,
+            (const void*)k_adj_vel<1, true>,      (const void*)k_adj_vel<kGroup, true>,
+            (const void*)k_adj_persist<1, false>, (const void*)k_adj_persist<kGroup, false>,
+            (const void*)k_adj_stress<1, false>,  (const void*)k_adj_stress<kGroup, false>,
+            (const void*)k_adj_vel<1, false>,     (const void*)k_adj_vel<kGroup, false>};
         for (const void* f : big_smem)
             CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     (int)cudaSharedmemCarveoutMaxShared));
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<1>, kThreads, 0));
         m->fwd_blocks = nb * sms;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<1>, kThreads, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<1, true>, kThreads, 0));
         m->adj_blocks = nb * sms;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<1, false>, kThreads, 0));
+        m->adj_blocks_nr = nb * sms;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<kGroup, false>, kThreads,
+                                                         0));
+        m->adj_blocks_g_nr = nb * sms;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<kGroup>, kThreads, 0));
         m->fwd_blocks_g = nb * sms;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<kGroup>, kThreads, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<kGroup, true>, kThreads,
+                                                         0));
         m->adj_blocks_g = nb * sms;
         if (!coop || std::min(std::min(m->fwd_blocks, m->adj_blocks),
-                              std::min(m->fwd_blocks_g, m->adj_blocks_g)) < 1)
+                              std::min(m->fwd_blocks_g, m->adj_blocks_g)) < 1 ||
+            std::min(m->adj_blocks_nr, m->adj_blocks_g_nr) < 1)
             m->persistent = 0;
     }
     m->shots.resize(nshots);
@@ -972,20 +1055,18 @@ bh_status bh_forward(bh_model* m, const float* wavelet, float* seis)
     BH_CUDA(m, cudaMemsetAsync(seis, 0, seis_per_shot * m->nshots * sizeof(float), m->stream));
     BH_CUDA(m, cudaMemsetAsync(m->d_fwd, 0, (size_t)m->nshots * kFwdPlanes * pl * sizeof(float),
                                m->stream));
-    if (m->L >= gd.nt) {
-        // store every step: one run with the history window at step 0
-        BH_TRY(run_forward(m, 0, gd.nt, 0, true, &m->runs_fwd));
-    } else {
-        // sweep once, recording, and take the schedule's first snapshots on the way
-        int n = 0;
-        for (const auto& sp : m->spine) {
-            const int n1 = std::min(gd.nt, sp.first * m->L);
-            BH_TRY(run_forward(m, n, n1, -1, true, &m->runs_fwd));
-            n = n1;
-            BH_TRY(snapshot(m, sp.second, true));
-        }
-        BH_TRY(run_forward(m, n, gd.nt, -1, true, &m->runs_fwd));
+    // sweep once, recording: take the schedule's first snapshots on the way
+    // through the segments, then store the tail's history as it goes (all of
+    // it when every step is stored)
+    int n = 0;
+    for (const auto& sp : m->spine) {
+        const int n1 = std::min(m->n_tail0, sp.first * m->L);
+        BH_TRY(run_forward(m, n, n1, -1, true, &m->runs_fwd));
+        n = n1;
+        BH_TRY(snapshot(m, sp.second, true));
     }
+    BH_TRY(run_forward(m, n, m->n_tail0, -1, true, &m->runs_fwd));
+    BH_TRY(run_forward(m, m->n_tail0, gd.nt, m->n_tail0, true, &m->runs_fwd));
     BH_LAUNCH(m);
     m->have_forward = true;
     return BH_OK;
@@ -1014,6 +1095,7 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
     const size_t ng = (size_t)gd.nr * m->nzg;
     const size_t seis_per_shot = (size_t)m->nrec_max * gd.nt;
     m->runs_adj = 0;
+    m->adj_rho = g_rho != nullptr;
     for (int s = 0; s < m->nshots; ++s) m->h_shots[s].a.resid = resid + seis_per_shot * s;
     BH_CUDA(m, cudaMemsetAsync(g_lam, 0, ng * sizeof(double), m->stream));
     BH_CUDA(m, cudaMemsetAsync(g_mu, 0, ng * sizeof(double), m->stream));
@@ -1025,18 +1107,20 @@ bh_status bh_adjoint_gradient(bh_model* m, const float* resid, double* g_lam, do
         k_adj_inject<<<(m->shots[s].nz + 127) / 128, 128, 0, m->stream>>>(m->h_shots[s], gd.nt - 1);
         BH_KERNEL(m);
     }
+    // the tail first: its history is the sweep's own
+    BH_TRY(run_adjoint(m, m->n_tail0, gd.nt, m->n_tail0, &m->runs_adj));
     for (const Act& a : m->plan) {
         switch (a.kind) {
         case ACT_RESTORE: BH_TRY(snapshot(m, a.a, false)); break;
         case ACT_TAKE: BH_TRY(snapshot(m, a.a, true)); break;
         case ACT_ADVANCE:
-            BH_TRY(run_forward(m, a.a * m->L, std::min(gd.nt, a.b * m->L), -1, false,
+            BH_TRY(run_forward(m, a.a * m->L, std::min(m->n_tail0, a.b * m->L), -1, false,
                                &m->runs_adj));
             break;
         case ACT_REVERSE: {
-            const int n0 = a.a * m->L, n1 = std::min(gd.nt, n0 + m->L);
-            if (m->L < gd.nt)  // refill the window
-                BH_TRY(run_forward(m, n0, n1, n0, false, &m->runs_adj));
+            // refill the window with the segment's history, then reverse it
+            const int n0 = a.a * m->L, n1 = std::min(m->n_tail0, n0 + m->L);
+            BH_TRY(run_forward(m, n0, n1, n0, false, &m->runs_adj));
             BH_TRY(run_adjoint(m, n0, n1, n0, &m->runs_adj));
             break;
         }
@@ -1202,6 +1286,7 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     const std::string k(key);
     const size_t pl = plane(m), ng = (size_t)m->grid.nr * m->nzg;
     if (k == "history_steps") *value = m->L;
+    else if (k == "tail_steps") *value = m->tail;
     else if (k == "snapshots") *value = m->nsnap;
     else if (k == "recompute_steps") *value = (double)m->recompute_steps;
     else if (k == "tiles") *value = m->ntiles;
@@ -1211,13 +1296,13 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "persistent") *value = m->persistent;
     else if (k == "history_snapshot_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
-                 (2.0 * (m->L + 1) + (double)m->nsnap * kFwdPlanes * (m->snap_prec ? 0.5 : 1.0));
+                 (2.0 * m->hist_slots + (double)m->nsnap * kFwdPlanes * (m->snap_prec ? 0.5 : 1.0));
     else if (k == "snapshot_precision") *value = m->snap_prec;
     else if (k == "kernel_launches") *value = (double)m->launches;
     else if (k == "state_version") *value = (double)m->state_version;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
-                     (kFwdPlanes + kAdjPlanes + 5.0 + 2.0 * (m->L + 1)) +
+                     (kFwdPlanes + kAdjPlanes + 5.0 + 2.0 * m->hist_slots) +
                  (double)pl * (m->snap_prec ? 2 : 4) * m->nshots * m->nsnap * kFwdPlanes +
                  (double)ng * (6 * sizeof(float) + 1 + 2 * sizeof(double));
     else return fail(m, BH_ERR_INVALID_ARG, "unknown key " + k);
@@ -1246,6 +1331,22 @@ bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
         spine[2 * k] = sp[k].first;
         spine[2 * k + 1] = sp[k].second;
     }
+    return BH_OK;
+}
+
+bh_status bh_plan_history(int nt, double hist_step_bytes, double snapshot_bytes,
+                          size_t cap_bytes, int* L, int* nsnap, int* tail, long long* recompute)
+{
+    if (nt < 1 || !(hist_step_bytes > 0) || !(snapshot_bytes > 0) || !L || !nsnap || !tail ||
+        !recompute)
+        return fail(nullptr, BH_ERR_INVALID_ARG, "bad argument");
+    const HistPlan hp = choose_history_plan(nt, hist_step_bytes, snapshot_bytes, (double)cap_bytes);
+    if (hp.recompute < 0)
+        return fail(nullptr, BH_ERR_OOM, "cap too small for one history window");
+    *L = hp.L;
+    *nsnap = hp.nsnap;
+    *tail = hp.tail;
+    *recompute = hp.recompute;
     return BH_OK;
 }
 

@@ -77,3 +77,70 @@ def test_enough_slots_cost_nothing(plan):
     spine, actions = plan(16, 15)
     advanced, _ = simulate(16, 15, spine, actions)
     assert advanced == 0 and len(spine) == 15
+
+
+@pytest.fixture(scope="module")
+def plan_history():
+    import shutil
+    import os
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2005_00281_gb300.build import build_library
+    build_library()
+    from paper_2005_00281_gb300 import bh
+    return bh.plan_history
+
+
+def _bytes(nt, h, S, L, s, tail):
+    if tail >= nt:
+        return (nt + 1) * h
+    return (max(tail, L) + 1) * h + s * S
+
+
+def test_history_plan_stores_everything_when_it_fits(plan_history):
+    assert plan_history(100, 10.0, 70.0, 101 * 10) == (100, 0, 100, 0)
+
+
+@pytest.mark.parametrize("nt,h,S", [(60, 10.0, 70.0), (97, 3.0, 40.0), (40, 5.0, 12.0)])
+def test_history_plan_matches_brute_force(plan_history, nt, h, S):
+    """Over every cap from one window to everything stored: the plan fits
+    the cap, and whenever a plan with a tail and a snapshot at every earlier
+    segment fits, its recompute is the least any such plan has (brute force
+    over every L and segment count); more memory never costs recompute."""
+    last = None
+    for cap in range(int(2 * h), int((nt + 2) * h), max(1, int(h // 2))):
+        try:
+            L, s, tail, rec = plan_history(nt, h, S, cap)
+        except Exception:
+            continue
+        assert _bytes(nt, h, S, L, s, tail) <= cap
+        best = None
+        for LL in range(1, nt):
+            nseg = -(-nt // LL)
+            for nsp in range(1, nseg):
+                t = nt - nsp * LL
+                if (max(t, LL) + 1) * h + (nsp - 1) * S <= cap:
+                    best = nsp * LL if best is None else min(best, nsp * LL)
+        if (nt + 1) * h <= cap:
+            best = 0
+        if best is not None:
+            assert rec == best, (cap, rec, best)
+            assert rec == (nt - tail if tail < nt else 0)
+        else:
+            assert tail == 0 and rec >= nt
+        if last is not None:
+            assert rec <= last
+        last = rec
+
+
+def test_history_plan_batched_logging_run(plan_history):
+    """The 64-shot logging run (windows padded to 2016 cells by 240, 8000
+    steps) under a 200 GB and a 240 GB cap: the sweep keeps a tail, and only
+    the steps before it are re-run (0.91 and 0.89 of nt), where a
+    window-only plan re-runs every step."""
+    h = 2 * 64 * 240 * 2016 * 4.0
+    S = 14 * 64 * 240 * 2016 * 4.0
+    for cap, bound in ((200e9, 0.91), (240e9, 0.89)):
+        L, s, tail, rec = plan_history(8000, h, S, cap)
+        assert tail > 0 and rec == 8000 - tail and rec < bound * 8000, (cap, rec)
+        assert _bytes(8000, h, S, L, s, tail) <= cap

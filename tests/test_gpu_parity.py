@@ -16,9 +16,8 @@ GRAD_TOL = 1e-4
 # array's largest value
 ELEM_TOL = 1e-3
 # relative L2 over each band of the model (axis, wall, C-PML edges, source and
-# receiver neighbourhoods): values there can be orders of magnitude below the
-# array's largest, so FP32 rounding weighs more than over the whole array
-REGION_TOL = 1e-3
+# receiver neighbourhoods), the whole-array tolerance: observed at most 3.5e-5
+REGION_TOL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -163,17 +162,14 @@ def test_update_velocity_parity(cuda, orc, update_rho):
         np.testing.assert_array_equal(a.cpu().numpy()[~mask], b[~mask])
     if not update_rho:
         np.testing.assert_array_equal(rho.cpu().numpy(), w.rho)
-    # the model now steps from the updated velocities: a forward run in it
-    # equals one in a fresh model built from them
-    from paper_2005_00281_gb300.bh import model_from_workload
-    import copy
-    w2 = copy.copy(w)
-    w2.vp, w2.vs, w2.rho = vp.cpu().numpy(), vs.cpu().numpy(), rho.cpu().numpy()
-    m2 = model_from_workload(w2)
+    # the model now steps from the updated velocities: a forward run equals
+    # one after setting those velocities (the C-PML keeps the creation's max
+    # Vp either way)
     wav = torch.from_numpy(w.wavelet).cuda()
-    assert torch.equal(m.forward(wav), m2.forward(wav))
+    a = m.forward(wav).clone()
+    m.set_model(vp, vs, rho)
+    assert torch.equal(a, m.forward(wav))
     m.close()
-    m2.close()
 
 
 def test_deterministic(cuda):
@@ -377,3 +373,62 @@ def test_reduced_precision_snapshots(cuda, orc, prec):
           {k: tuple(f"{x:.2e}" for x in v) for k, v in errs.items()})
     for name, (e_fp32, e_orc, _) in errs.items():
         assert e_fp32 < 2e-2 and e_orc < 2e-2, (prec, name, errs)
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_no_density_gradient_same_lame_gradients(cuda, persistent):
+    """Asking for no density gradient (g_rho NULL) runs the adjoint without
+    the density correlation; the lambda and mu gradients and the
+    pseudo-Hessians stay bit for bit those of the full run."""
+    from paper_2005_00281_gb300.bh import model_from_workload
+    torch = cuda
+    w = tiny_borehole(seed=17, nz=75, nt=200)
+    w.shots = [dict(z_offset=0, nz=75, src=(0, 10), rec_iz=[30, 50, 62])]
+    out = []
+    for with_rho in (True, False):
+        m = model_from_workload(w)
+        m.set_option("persistent", persistent)
+        wav = torch.from_numpy(w.wavelet).cuda()
+        seis = m.forward(wav)
+        resid, _ = m.residual_misfit(seis, torch.zeros_like(seis))
+        g = m.adjoint_gradient(resid, with_rho=with_rho)
+        H = m.hessian()
+        torch.cuda.synchronize()
+        out.append([g[0].cpu().numpy(), g[1].cpu().numpy()] + [h.cpu().numpy() for h in H])
+        m.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("cap", [1_000_000, 1_600_000, 2_200_000])
+def test_stored_tail_matches_store_all(cuda, cap):
+    """Caps under which the forward sweep stores the history of its last
+    steps (the tail) and only the steps before it are re-run: the gradient
+    equals the store-every-step gradient bit for bit."""
+    w = tiny_borehole(seed=9, nt=300)
+    seis_0, g_0, J_0, _ = _run_gpu(w)
+    seis_c, g_c, J_c, info = _run_gpu(w, checkpoint_cap_bytes=cap)
+    from paper_2005_00281_gb300.bh import model_from_workload
+    m = model_from_workload(w, checkpoint_cap_bytes=cap)
+    tail, rec = m.info("tail_steps"), m.info("recompute_steps")
+    m.close()
+    assert 0 < tail < w.nt and rec == w.nt - tail
+    assert np.array_equal(seis_0, seis_c) and J_0 == J_c
+    for a, b in zip(g_0, g_c):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_stored_tail_batched(cuda, persistent):
+    """Three uneven windows under a cap with a stored tail and snapshots,
+    both launch forms: bit for bit the store-every-step result."""
+    w = tiny_borehole(seed=14, nz=96, nt=300)
+    w.shots = [dict(z_offset=0, nz=70, src=(0, 10), rec_iz=[25, 40, 58]),
+               dict(z_offset=13, nz=83, src=(0, 12), rec_iz=[30, 50, 66]),
+               dict(z_offset=40, nz=56, src=(0, 9), rec_iz=[20, 33, 41])]
+    seis_0, g_0, _, _ = _run_gpu(w, persistent=persistent)
+    seis_c, g_c, _, info = _run_gpu(w, persistent=persistent, checkpoint_cap_bytes=5_000_000)
+    assert info["snapshots"] >= 1 and info["recompute_steps"] < w.nt
+    assert np.array_equal(seis_0, seis_c)
+    for a, b in zip(g_0, g_c):
+        assert np.array_equal(a, b)
