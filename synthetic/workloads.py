@@ -232,3 +232,96 @@ def tiny_borehole(seed=0, nr=24, nz=48, npml=6, nt=300, h=0.01, dt=1e-6, f0=15e3
 
 
 PRESETS = {"c0": config0, "c1": config1, "c2": config2, "c3": config3, "c4": config4}
+
+
+# ---------------------------------------------------------------------------
+# Multi-source logging tool (Numerical Examples, Fig. 2): thirteen receiver
+# stations 0.5 ft apart above three monopoles (lower-near, far, ultra-far);
+# the tool logs every 0.5 ft.  The paper realigns the records of the three
+# sources to one source and thirty-nine receivers.  Reading (the paper prints
+# no source offsets): the far and ultra-far monopoles sit 13 and 26 stations
+# (6.5 ft and 13 ft) below the lower-near one, so the three arrays, seen from
+# one source depth, cover 39 consecutive stations; the lower-near source is
+# `near_offset` below the first receiver.
+
+FT = 0.3048
+STATION = 0.5 * FT
+TOOL_SOURCES = ("lower-near", "far", "ultra-far")
+TOOL_STATIONS = 13
+
+
+def tool_records(ndepths: int, z_first: float, near_offset: float = 3.0,
+                 step: float = STATION, spacing: float = STATION):
+    """The raw acquisition table of a logging run: one record per (tool
+    depth, monopole): source depth and the depths of the 13 receivers.  The
+    tool moves `step` per depth; z grows downwards and the receivers sit
+    above the sources (smaller z).  z_first: depth of the lower-near source
+    at the first tool depth."""
+    recs = []
+    for d in range(ndepths):
+        z_near = z_first + d * step
+        for k, name in enumerate(TOOL_SOURCES):
+            zs = z_near + k * TOOL_STATIONS * spacing
+            rz = [z_near - near_offset - q * spacing for q in range(TOOL_STATIONS)]
+            recs.append(dict(depth=d, source=name, z_src=zs, z_rec=rz))
+    return recs
+
+
+def realign(recs, spacing: float = STATION, tol: float = 1e-9):
+    """Realigned gathers: records whose sources sit at the same depth merge
+    into one gather of one source and the union of their receivers, ordered
+    by offset.  Returns {source depth: [(offset, record index, receiver
+    index), ...]} for the source depths that all three monopoles visit."""
+    by_src = {}
+    for i, r in enumerate(recs):
+        key = round(r["z_src"] / spacing)
+        by_src.setdefault(key, []).append(i)
+    out = {}
+    for key, idx in by_src.items():
+        if len(idx) != len(TOOL_SOURCES):
+            continue
+        zs = recs[idx[0]]["z_src"]
+        rows = []
+        for i in idx:
+            assert abs(recs[i]["z_src"] - zs) < tol
+            for q, zr in enumerate(recs[i]["z_rec"]):
+                rows.append((zs - zr, i, q))
+        out[zs] = sorted(rows)
+    return out
+
+
+def tool_logging_run(seed=0, ndepths=16, nt=6000, near_offset=3.0, h=0.005, dt=0.5e-6,
+                     f0=1e4, npml=40, nr=240, margin=0.5, name="tool"):
+    """Batched workload of the realigned tool geometry: one shot per source
+    depth that all three monopoles visit, each with its 39 receivers on the
+    axis, its own window (margin above the farthest receiver and below the
+    source) of a layered model with a damaged annulus like the production
+    shot's."""
+    rng = np.random.default_rng(seed)
+    recs_probe = tool_records(1, 0.0, near_offset)
+    span = near_offset + (3 * TOOL_STATIONS - 1) * STATION  # source to farthest receiver
+    top = npml * h + margin
+    # every source depth realigned needs 2 * 13 further tool depths
+    ndep_raw = ndepths + 2 * TOOL_STATIONS
+    z_first = top + span
+    recs = tool_records(ndep_raw, z_first, near_offset)
+    gathers = realign(recs)
+    zs_sorted = sorted(gathers)[:ndepths]
+    length_m = zs_sorted[-1] + margin + npml * h
+    nzg = int(np.ceil(length_m / h)) + 1
+    vp, vs, rho, vpt, vst = _layered(rng, nr, nzg, h, _borehole(nr, 0, h))
+    vp, vs, rho, vpt, vst = _f32(vp, vs, rho, vpt, vst)
+    shots = []
+    for zs in zs_sorted:
+        rows = gathers[zs]
+        z_top_rec = zs - max(o for o, _, _ in rows)
+        z0 = int(np.floor((z_top_rec - margin) / h)) - npml
+        z1 = int(np.ceil((zs + margin) / h)) + npml
+        z0 = max(z0, 0)
+        z1 = min(z1, nzg)
+        src_iz = int(round(zs / h)) - z0
+        rec_iz = [int(round((zs - o) / h)) - z0 for o, _, _ in rows]
+        shots.append(dict(z_offset=z0, nz=z1 - z0, src=(0, src_iz), rec_iz=sorted(rec_iz)))
+    del recs_probe
+    return Workload(name, nr, nzg, nt, npml, npml, h, h, dt, f0, vp, vs, rho, vpt, vst,
+                    rho.copy(), shots, ricker(nt, dt, f0))
