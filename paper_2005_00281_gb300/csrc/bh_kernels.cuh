@@ -21,6 +21,7 @@ constexpr float kC2 = -0.041666666666666664f; // -1/24
 
 struct WinK {
     int nr, nz, P;      // window rows, columns, row pitch of the state arrays
+    int Pw;             // row pitch of the shared coefficient copies (CoefK w_*)
     int nzg, z0;        // global model pitch and the window's first global row
     int npml_r, npml_z;
     float dt, inv_dr, inv_dz;
@@ -32,9 +33,14 @@ struct CoefK {
     const float *inv_r_int, *inv_r_half;          // [nr]
     const float *ar_int, *br_int, *ar_half, *br_half;  // radial C-PML [nr]
     const float *az_int, *bz_int, *az_half, *bz_half;  // axial C-PML of the window [nz]
-    // the window's own copies, [nr][P], zero beyond nz: lambda, mu (cells),
-    // harmonic mu (trz nodes), buoyancy at v_r and v_z nodes, the last two
-    // with the window's last-row rule (muh_at, bvz_at)
+    // lambda, mu (cells), harmonic mu (trz nodes), buoyancy at v_r and v_z
+    // nodes of the global model, read through a copy shifted so that the
+    // window's column 0 is 16-byte aligned: window node (i, j) is
+    // w_*[i * Pw + j].  Several shots share one copy (one per z0 mod 4).
+    // Beyond the window they hold the global model's neighbours, so staging
+    // zero-fills outside 0 <= j < nz; at the window's last row the v_z
+    // buoyancy and the trz harmonic mu follow the window's own rule instead
+    // (bvz_at, muh_at), which the tiles with TILE_LAST patch in.
     const float *w_lam, *w_mu, *w_muh, *w_bvr, *w_bvz;
 };
 
@@ -115,7 +121,10 @@ constexpr int kQ = kSZ / 4;        // float4 per staged row
 constexpr int kThreads = 128;
 typedef float Tile[kSR][kSZ];
 
-enum { TILE_PML = 1 };  // tile or halo touches a C-PML layer
+enum {
+    TILE_PML = 1,   // tile or halo touches a C-PML layer
+    TILE_LAST = 2   // the staged columns hold the window's last node row
+};
 
 // Programmatic dependent launch: a kernel may be scheduled while its
 // predecessor drains; it must wait here before touching the predecessor's
@@ -218,6 +227,7 @@ struct Slot {
     int rr, cq;  // staged row, first staged column
     int off_e;   // plane offset of the even-mirrored source row, -1: zero
     int off_o;   // plane offset of the odd/abs-mirrored source row, -1: zero
+    int offw_e, offw_o;  // the same in the coefficient copies (pitch Pw)
     int zlim;    // source floats inside 0 <= z < nz (4: all of them)
     bool neg;    // the row is a mirror image (odd fields change sign)
 };
@@ -237,6 +247,8 @@ __device__ __forceinline__ Slot slot_of(int it, int i0, int j0, const WinK& g)
     s.neg = i < 0;
     s.off_e = (zin && ie < g.nr) ? ie * g.P + j : -1;
     s.off_o = (zin && io >= 1 && io < g.nr) ? io * g.P + j : -1;
+    s.offw_e = (zin && ie < g.nr) ? ie * g.Pw + j : -1;
+    s.offw_o = (zin && io >= 1 && io < g.nr) ? io * g.Pw + j : -1;
     return s;
 }
 
@@ -252,10 +264,11 @@ __device__ __forceinline__ unsigned smem_addr(const void* p)
     return (unsigned)__cvta_generic_to_shared(p);
 }
 
-template <int KIND>
+// W: f is a shared coefficient copy (pitch Pw) rather than a window plane
+template <int KIND, bool W = false>
 __device__ __forceinline__ void stage_async(Tile& t, const float* __restrict__ f, const Slot& s)
 {
-    int off = KIND == EVEN ? s.off_e : s.off_o;
+    int off = W ? (KIND == EVEN ? s.offw_e : s.offw_o) : (KIND == EVEN ? s.off_e : s.off_o);
     if (KIND == POS && s.neg) off = -1;
     const float* src = f + (off >= 0 ? off : 0);
     const unsigned bytes = off >= 0 ? 4u * (unsigned)s.zlim : 0u;
@@ -324,6 +337,7 @@ __device__ __forceinline__ V4 prof4(const float* row, int cz)
 // own-node index helpers: thread (x = column group, y = row)
 struct Own {
     int i, rr, j, cc, c;  // window row, staged row, first column, staged column, plane index
+    int cw;               // index in the coefficient copies
     bool live;
 };
 
@@ -336,7 +350,17 @@ __device__ __forceinline__ Own own_of(const WinK& g, int i0, int j0)
     o.cc = 4 * threadIdx.x + 4;
     o.live = o.i < g.nr && o.j < g.nz;
     o.c = o.i * g.P + o.j;
+    o.cw = o.i * g.Pw + o.j;
     return o;
+}
+
+// Replace element j_last - j of a 4-node group starting at column j (if it
+// lies there) by val: the window's last-row coefficients.
+__device__ __forceinline__ void patch4(V4& x, int j, int j_last, float val)
+{
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (j + e == j_last) x.v[e] = val;
 }
 
 // ------------------------------------------------- bounded grid barrier
@@ -454,10 +478,11 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
         ivr = __ldg(C.inv_r_int + o.i);
         ivh = __ldg(C.inv_r_half + o.i);
         vz0 = ld4cg(S.vz + o.c);
-        bz = ld4g(C.w_bvz + o.c);
+        bz = ld4g(C.w_bvz + o.cw);
+        if (flags & TILE_LAST) patch4(bz, o.j, g.nz - 1, bvz_at(C, g, o.i, g.nz - 1));
         if (o.i >= 1) {
             vr0 = ld4cg(S.vr + o.c);
-            br = ld4g(C.w_bvr + o.c);
+            br = ld4g(C.w_bvr + o.cw);
         }
         if (pml) {
             q2 = ld4cg(S.psi[2] + o.c);
@@ -587,11 +612,12 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         t_rr = ld4cg(S.trr + o.c);
         t_tt = ld4cg(S.ttt + o.c);
         t_zz = ld4cg(S.tzz + o.c);
-        lm = ld4g(C.w_lam + o.c);
-        mu = ld4g(C.w_mu + o.c);
+        lm = ld4g(C.w_lam + o.cw);
+        mu = ld4g(C.w_mu + o.cw);
         if (o.i >= 1) {
             t_rz = ld4cg(S.trz + o.c);
-            mh = ld4g(C.w_muh + o.c);
+            mh = ld4g(C.w_muh + o.cw);
+            if (flags & TILE_LAST) patch4(mh, o.j, g.nz - 1, muh_at(C, g, o.i, g.nz - 1));
         }
         if (pml) {
             q4 = ld4cg(S.psi[4] + o.c);
@@ -753,9 +779,9 @@ __device__ __forceinline__ void stage_adj_statics(AdjSmem& sm, const CoefK& C, c
         const Slot sl = slot_of(it, i0, j0, g);
         stage_async<ODD>(sm.f[0], fcur, sl);
         stage_async<EVEN>(sm.f[1], fcur + plane, sl);
-        stage_async<EVEN>(sm.f[2], C.w_lam, sl);
-        stage_async<EVEN>(sm.f[3], C.w_mu, sl);
-        stage_async<ABS>(sm.f[4], C.w_muh, sl);
+        stage_async<EVEN, true>(sm.f[2], C.w_lam, sl);
+        stage_async<EVEN, true>(sm.f[3], C.w_mu, sl);
+        stage_async<ABS, true>(sm.f[4], C.w_muh, sl);
     }
 }
 
@@ -891,7 +917,13 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
         const Slot sl = slot_of(it, i0, j0, g);
         const int r2 = sl.rr, c2 = sl.cq;
         const int ii = i0 - kH + r2, j = j0 - 4 + c2;
-        const V4 lm = lds4(T_x4, r2, c2), mu = lds4(T_yt, r2, c2), mh = lds4(T_x5, r2, c2);
+        const V4 lm = lds4(T_x4, r2, c2), mu = lds4(T_yt, r2, c2);
+        V4 mh = lds4(T_x5, r2, c2);
+        if ((flags & TILE_LAST) && sl.offw_o >= 0) {
+            // the window's last trz row (the copy holds the global model's)
+            const int io = ii < 0 ? -ii : ii;
+            patch4(mh, j, g.nz - 1, muh_at(C, g, io, g.nz - 1));
+        }
         const V4 ar = lds4(T_rr, r2, c2), at = lds4(T_tt, r2, c2), az = lds4(T_zz, r2, c2);
         const V4 arz = lds4(T_rz, r2, c2);
         float x4[4], ytt[4], x5[4], x6[4], x7[4];
@@ -1045,9 +1077,9 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const Slot sl = slot_of(it, i0, j0, g);
         stage_async<ODD>(s_wr, S.vr, sl);
-        stage_async<ABS>(s_br, C.w_bvr, sl);
+        stage_async<ABS, true>(s_br, C.w_bvr, sl);
         stage_async<EVEN>(s_wz, S.vz, sl);
-        stage_async<EVEN>(s_bz, C.w_bvz, sl);
+        stage_async<EVEN, true>(s_bz, C.w_bvz, sl);
         if (pml) {
             stage_async<ODD>(s_x0, S.psi[0], sl);
             stage_async<ODD>(s_x1, S.psi[1], sl);
@@ -1125,7 +1157,13 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         }
         // v_z node
         {
-            const V4 av = lds4(s_wz, r2, c2), bv = lds4(s_bz, r2, c2);
+            const V4 av = lds4(s_wz, r2, c2);
+            V4 bv = lds4(s_bz, r2, c2);
+            if ((flags & TILE_LAST) && sl.offw_e >= 0) {
+                // the window's last v_z row (the copy holds the global model's)
+                const int ie = ii < 0 ? -1 - ii : ii;
+                patch4(bv, j, g.nz - 1, bvz_at(C, g, ie, g.nz - 1));
+            }
             float w[4], x2[4], x3[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) x2[e] = x3[e] = w[e] = g.dt * bv.v[e] * av.v[e];

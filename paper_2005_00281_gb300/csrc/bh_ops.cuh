@@ -55,45 +55,30 @@ __global__ void k_setup_nodes(int nr, int nzg, const float* __restrict__ mu,
     }
 }
 
-// Window copies of the coefficients for every shot, [nshots][5][nr][P]:
-// lambda, mu, harmonic mu at trz nodes, buoyancy at v_r and v_z nodes.  The
-// window's last row follows its own rule (its v_z and trz nodes see only the
-// window's cells, as muh_at and bvz_at state); columns nz .. P-1 are zero.
-// wins[s] = (first global row, nz) of shot s; blockIdx.z = shot.
-__global__ void k_window_coefs(int nr, int nzg, int P, const int2* __restrict__ wins,
-                               const float* __restrict__ lam, const float* __restrict__ mu,
-                               const float* __restrict__ rho, const float* __restrict__ bvr,
-                               const float* __restrict__ bvz, const float* __restrict__ muh,
-                               float* out)
+// Shifted copies of the node and cell coefficients, [4][5][nr][Pw]:
+// lambda, mu, harmonic mu at trz nodes, buoyancy at v_r and v_z nodes of the
+// global model; copy k holds global column c - k at column c (zero outside
+// the model), so a window starting at global column z0 reads copy
+// (4 - z0 % 4) % 4 from a 16-byte aligned column.  blockIdx.z = copy.
+__global__ void k_shift_coefs(int nr, int nzg, int Pw, const float* __restrict__ lam,
+                              const float* __restrict__ mu, const float* __restrict__ muh,
+                              const float* __restrict__ bvr, const float* __restrict__ bvz,
+                              float* out)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= nr || j >= P) return;
-    const int2 w = wins[blockIdx.z];
-    const size_t pl = (size_t)nr * P;
-    float* o = out + (size_t)blockIdx.z * 5 * pl + (size_t)i * P + j;
-    float v_lam = 0.f, v_mu = 0.f, v_muh = 0.f, v_bvr = 0.f, v_bvz = 0.f;
-    if (j < w.y) {
-        const size_t cg = (size_t)i * nzg + w.x + j;
-        const bool last = j == w.y - 1;
-        v_lam = lam[cg];
-        v_mu = mu[cg];
-        v_bvz = last ? 1.f / rho[cg] : bvz[cg];
-        if (i >= 1) {
-            v_bvr = bvr[cg];
-            if (last) {
-                const float a = mu[cg - nzg], b = mu[cg];
-                v_muh = (a <= 0.f || b <= 0.f) ? 0.f : 2.f / (1.f / a + 1.f / b);
-            } else {
-                v_muh = muh[cg];
-            }
-        }
-    }
-    o[0] = v_lam;
-    o[pl] = v_mu;
-    o[2 * pl] = v_muh;
-    o[3 * pl] = v_bvr;
-    o[4 * pl] = v_bvz;
+    if (i >= nr || c >= Pw) return;
+    const int k = blockIdx.z;
+    const size_t pl = (size_t)nr * Pw;
+    float* o = out + (size_t)k * 5 * pl + (size_t)i * Pw + c;
+    const int j = c - k;
+    const bool in = j >= 0 && j < nzg;
+    const size_t cg = (size_t)i * nzg + j;
+    o[0] = in ? lam[cg] : 0.f;
+    o[pl] = in ? mu[cg] : 0.f;
+    o[2 * pl] = in ? muh[cg] : 0.f;
+    o[3 * pl] = in ? bvr[cg] : 0.f;
+    o[4 * pl] = in ? bvz[cg] : 0.f;
 }
 
 // inversion mask: formation cell (vs > 0), outside the radial C-PML, and

@@ -41,6 +41,7 @@ struct Act {
 struct bh_model {
     bh_grid_desc grid{};
     int nzg = 0, nshots = 0, nrec_max = 0, P = 0;
+    int Pw = 0;                 // row pitch of the shifted coefficient copies
     cudaStream_t stream = nullptr;
     double vpmax = 0.0;
     // model, global [nr][nzg]
@@ -57,8 +58,7 @@ struct bh_model {
     int* d_recmap = nullptr;    // per shot nz
     float* d_fwd = nullptr;     // per shot kFwdPlanes planes
     float* d_adj = nullptr;     // per shot kAdjPlanes planes
-    float* d_wcoef = nullptr;   // per shot 5 coefficient planes of its window
-    int2* d_wins = nullptr;     // per shot (first global row, nz)
+    float* d_wcoef = nullptr;   // 4 shifted copies x 5 coefficient planes [nr][Pw]
     float* d_hist = nullptr;    // per shot (L + 1) x 2 planes
     void* d_snap = nullptr;     // per slot, all shots' kFwdPlanes planes (fp32 or 16-bit)
     float* d_snap_max = nullptr;  // per slot, max |x| of every plane (16-bit snapshots)
@@ -158,7 +158,7 @@ void free_model(bh_model* m)
                     m->d_vp,    m->d_vs,
                     m->d_mask,  m->d_colcov, m->d_rprof, m->d_zprof,  m->d_recmap, m->d_fwd,
                     m->d_adj,   m->d_hist,   m->d_snap,  m->d_snap_max, m->d_tiles,  m->d_Hg,
-                    m->d_scal,  m->d_bar,    m->d_wcoef, m->d_wins,   m->d_part};
+                    m->d_scal,  m->d_bar,    m->d_wcoef, m->d_part};
     for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     delete m;
@@ -266,11 +266,10 @@ bh_status rebuild_coefficients(bh_model* m)
     k_setup_nodes<<<grid2d(nr, nzg), block2d(), 0, m->stream>>>(nr, nzg, m->d_mu, m->d_rho,
                                                                 m->d_bvr, m->d_bvz, m->d_muh);
     BH_KERNEL(m);
-    dim3 gw = grid2d(nr, m->P);
-    gw.z = (unsigned)m->nshots;
-    k_window_coefs<<<gw, block2d(), 0, m->stream>>>(nr, nzg, m->P, m->d_wins, m->d_lam, m->d_mu,
-                                                    m->d_rho, m->d_bvr, m->d_bvz, m->d_muh,
-                                                    m->d_wcoef);
+    dim3 gw = grid2d(nr, m->Pw);
+    gw.z = 4;
+    k_shift_coefs<<<gw, block2d(), 0, m->stream>>>(nr, nzg, m->Pw, m->d_lam, m->d_mu, m->d_muh,
+                                                   m->d_bvr, m->d_bvz, m->d_wcoef);
     BH_KERNEL(m);
     return BH_OK;
 }
@@ -393,6 +392,7 @@ bh_status setup_shots(bh_model* m)
         k.g.nr = nr;
         k.g.nz = sh.nz;
         k.g.P = m->P;
+        k.g.Pw = m->Pw;
         k.g.nzg = m->nzg;
         k.g.z0 = sh.z0;
         k.g.npml_r = gd.npml_r;
@@ -418,12 +418,15 @@ bh_status setup_shots(bh_model* m)
         C.bz_int = zp + m->P;
         C.az_half = zp + 2 * m->P;
         C.bz_half = zp + 3 * m->P;
-        const float* wc = m->d_wcoef + (size_t)s * 5 * pl;
+        // the shifted copy in which the window's column 0 is 16-byte aligned
+        const int kc = (4 - (sh.z0 & 3)) & 3;
+        const size_t plw = (size_t)nr * m->Pw;
+        const float* wc = m->d_wcoef + (size_t)kc * 5 * plw + sh.z0 + kc;
         C.w_lam = wc;
-        C.w_mu = wc + pl;
-        C.w_muh = wc + 2 * pl;
-        C.w_bvr = wc + 3 * pl;
-        C.w_bvz = wc + 4 * pl;
+        C.w_mu = wc + plw;
+        C.w_muh = wc + 2 * plw;
+        C.w_bvr = wc + 3 * plw;
+        C.w_bvz = wc + 4 * plw;
         float* f = m->d_fwd + (size_t)s * kFwdPlanes * pl;
         float* a = m->d_adj + (size_t)s * kAdjPlanes * pl;
         StateK* views[3] = {&k.Sf, &k.Sa[0], &k.Sa[1]};
@@ -473,9 +476,25 @@ bh_status setup_shots(bh_model* m)
                 const bool radial = gd.npml_r > 0 && i0 + kTR + kH >= nr - gd.npml_r - 1;
                 const bool axial = gd.npml_z > 0 &&
                                    (j0 - 4 <= gd.npml_z + 1 || j0 + kTZ + 4 >= sh.nz - gd.npml_z - 2);
-                tiles.push_back(make_int4(s % kGroup, i0, j0, (radial || axial) ? TILE_PML : 0));
+                const bool last = j0 - 4 <= sh.nz - 1 && sh.nz - 1 <= j0 + kTZ + 3;
+                tiles.push_back(make_int4(s % kGroup, i0, j0,
+                                          ((radial || axial) ? TILE_PML : 0) |
+                                              (last ? TILE_LAST : 0)));
                 m->group_ntiles.back()++;
             }
+        // the group's tiles ordered by global column, then row, then shot:
+        // tiles of several shots at one place of the model run together and
+        // share the coefficient copies' lines in L2
+        if (s % kGroup == kGroup - 1 || s == m->nshots - 1) {
+            const int g0 = m->group_tile_off.back();
+            const int sbase = s - s % kGroup;
+            std::stable_sort(tiles.begin() + g0, tiles.end(), [&](const int4& a, const int4& b) {
+                const int za = m->shots[sbase + a.x].z0 + a.z, zb = m->shots[sbase + b.x].z0 + b.z;
+                if (za != zb) return za < zb;
+                if (a.y != b.y) return a.y < b.y;
+                return a.x < b.x;
+            });
+        }
     }
     m->ntiles = (int)tiles.size();
     BH_CUDA(m, dalloc(&m->d_tiles, tiles.size()));
@@ -906,6 +925,8 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     m->nshots = nshots;
     m->nrec_max = nrec_max;
     m->P = (nzmax + 31) / 32 * 32;
+    // a window's own loads reach 3 columns past its end, plus the copy shift
+    m->Pw = (nz_global + 8 + 31) / 32 * 32;
     m->stream = (cudaStream_t)stream;
     m->snap_prec = g.snapshot_precision;
     const int nr = g.nr;
@@ -950,8 +971,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_rprof, 6 * (size_t)nr));
     CK(dalloc(&m->d_fwd, (size_t)nshots * kFwdPlanes * pl));
     CK(dalloc(&m->d_adj, (size_t)nshots * kAdjPlanes * pl));
-    CK(dalloc(&m->d_wcoef, (size_t)nshots * 5 * pl));
-    CK(dalloc(&m->d_wins, (size_t)nshots));
+    CK(dalloc(&m->d_wcoef, (size_t)4 * 5 * nr * m->Pw));
     CK(dalloc(&m->d_hist, (size_t)nshots * m->hist_slots * 2 * pl));
     CK(dalloc((char**)&m->d_snap,
               (size_t)m->nsnap * nshots * kFwdPlanes * pl * (m->snap_prec ? 2 : 4)));
@@ -1009,10 +1029,6 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         for (int j = g.npml_z; j < d.nz - g.npml_z; ++j) colcov[d.z_offset + j] = 1;
     }
     CK(cudaMemcpyAsync(m->d_colcov, colcov.data(), nz_global, cudaMemcpyHostToDevice,
-                       m->stream));
-    std::vector<int2> wins(nshots);
-    for (int s = 0; s < nshots; ++s) wins[s] = make_int2(shots[s].z_offset, shots[s].nz);
-    CK(cudaMemcpyAsync(m->d_wins, wins.data(), nshots * sizeof(int2), cudaMemcpyHostToDevice,
                        m->stream));
     CK(cudaStreamSynchronize(m->stream));
 #undef CK
@@ -1302,7 +1318,8 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "state_version") *value = (double)m->state_version;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
-                     (kFwdPlanes + kAdjPlanes + 5.0 + 2.0 * m->hist_slots) +
+                     (kFwdPlanes + kAdjPlanes + 2.0 * m->hist_slots) +
+                 20.0 * m->grid.nr * m->Pw * sizeof(float) +
                  (double)pl * (m->snap_prec ? 2 : 4) * m->nshots * m->nsnap * kFwdPlanes +
                  (double)ng * (6 * sizeof(float) + 1 + 2 * sizeof(double));
     else return fail(m, BH_ERR_INVALID_ARG, "unknown key " + k);
