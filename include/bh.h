@@ -363,6 +363,29 @@ bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
                              int* n_actions, int* spine, int max_spine, int* n_spine);
 
 /*
+ * Starting model (Numerical Examples, Fig. 3 and Fig. 4): the paper takes
+ * the formation velocities at the borehole wall from the semblance of the
+ * near-monopole data, those one meter into the formation from the
+ * ultra-far-monopole data, and interpolates linearly in r between them.
+ * Per depth j: cells whose centre r = (i + 1/2) dr lies inside r_wall get
+ * the fluid (vp_fluid, Vs = 0); others get
+ * v = v_wall + t (v_far - v_wall), t = (r - r_wall) / (r_far - r_wall)
+ * clamped to [0, 1] (the far values beyond r_far).  The semblance analysis
+ * itself is not part of this library: the four velocity logs are inputs.
+ * Needs no model.
+ *   vp_wall, vs_wall, vp_far, vs_far  device [nz] float32
+ *   vp, vs   device [nr][nz] float32, written
+ *   stream   cudaStream_t (NULL = legacy default stream); the call
+ *            returns once the work is enqueued
+ * Errors: BH_ERR_INVALID_ARG (sizes, NULL, r_far <= r_wall), BH_ERR_CUDA;
+ *   bh_last_error(NULL) gives the message.
+ */
+bh_status bh_starting_model(int nr, int nz, double dr, double r_wall, double r_far,
+                            const float* vp_wall, const float* vs_wall, const float* vp_far,
+                            const float* vs_far, float vp_fluid, float* vp, float* vs,
+                            void* stream);
+
+/*
  * The forward-history plan bh_model_create picks under a byte cap (host
  * only, no GPU; the paper has no counterpart).  The nt steps split into
  * segments of L steps and a tail of the last `tail` steps, whose history
@@ -386,7 +409,8 @@ bh_status bh_plan_history(int nt, double hist_step_bytes, double snapshot_bytes,
 const char* bh_status_string(bh_status status);
 
 /* Text of the last error on this model ("" if none); NULL model: the last
- * error of bh_model_create or bh_residual_misfit_noalloc on this thread. */
+ * error of bh_model_create, bh_residual_misfit_noalloc, bh_starting_model or
+ * bh_plan_history on this thread. */
 const char* bh_last_error(const bh_model* model);
 
 #ifdef __cplusplus

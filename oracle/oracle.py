@@ -269,6 +269,24 @@ def update_velocity(vp, vs, rho, g_lam, g_mu, g_rho, mask, kappa, update_rho=Fal
     return vp, vs, rho, lam, mu, tuple(alphas)
 
 
+def starting_model(nr, dr, r_wall, r_far, vp_wall, vs_wall, vp_far, vs_far, vp_fluid):
+    """Starting model of the Numerical Examples (Fig. 3, Fig. 4): per depth,
+    the P and S velocities at the borehole wall (from the near-monopole data)
+    and at r_far (one meter into the formation, from the ultra-far-monopole
+    data), linear in r in between, the far values beyond r_far, and the
+    borehole fluid (Vs = 0) in the cells whose centre lies inside r_wall.
+    vp_wall, vs_wall, vp_far, vs_far: [nz].  Returns (vp, vs) [nr, nz]."""
+    r = (np.arange(nr) + 0.5) * dr
+    t = np.clip((r - r_wall) / (r_far - r_wall), 0.0, 1.0)[:, None]
+    vpw, vsw, vpf, vsf = (_f64(a)[None, :] for a in (vp_wall, vs_wall, vp_far, vs_far))
+    vp = vpw + t * (vpf - vpw)
+    vs = vsw + t * (vsf - vsw)
+    fluid = r < r_wall
+    vp[fluid, :] = vp_fluid
+    vs[fluid, :] = 0.0
+    return vp, vs
+
+
 def inversion_mask(nr, nz, npml_r, npml_z, vs, windows=None):
     """Cells that are unknowns: formation cells (Vs > 0) outside the radial
     C-PML and inside the axial interior (outside the top and bottom C-PML) of

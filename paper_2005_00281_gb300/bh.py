@@ -26,7 +26,7 @@ EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
            "bh_profile_enable", "bh_profile_read", "bh_profile_reset",
            "bh_residual_misfit_noalloc", "bh_set_option", "bh_get_info",
            "bh_checkpoint_plan", "bh_velocity_gradient", "bh_update_velocity",
-           "bh_get_density", "bh_plan_history")
+           "bh_get_density", "bh_plan_history", "bh_starting_model")
 NOALLOC_MAX_SAMPLES = 33554432
 KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel", "fwd_persist", "adj_persist")
 
@@ -116,6 +116,10 @@ def load_library(path: str | None = None):
                                     ctypes.c_size_t, ip, ip, ip,
                                     ctypes.POINTER(ctypes.c_longlong)]
     lib.bh_plan_history.restype = st
+    dbl = ctypes.c_double
+    lib.bh_starting_model.argtypes = [ctypes.c_int, ctypes.c_int, dbl, dbl, dbl, vp, vp, vp, vp,
+                                      ctypes.c_float, vp, vp, vp]
+    lib.bh_starting_model.restype = st
     lib.bh_get_info.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.bh_get_info.restype = st
     lib.bh_residual_misfit_noalloc.argtypes = [vp, vp, vp, ctypes.c_size_t,
@@ -374,3 +378,24 @@ def plan_history(nt, hist_step_bytes, snapshot_bytes, cap_bytes):
     if rc != BH_OK:
         raise BhError(rc, lib.bh_last_error(None).decode())
     return L.value, s.value, t.value, rc_.value
+
+
+def starting_model(nr, dr, r_wall, r_far, vp_wall, vs_wall, vp_far, vs_far, vp_fluid=1500.0,
+                   stream=None):
+    """bh_starting_model: (vp, vs) [nr, nz] float32 CUDA tensors from the
+    velocity logs at the wall and at r_far ([nz] float32 CUDA tensors)."""
+    lib = load_library()
+    nz = vp_wall.numel()
+    for name, t in (("vp_wall", vp_wall), ("vs_wall", vs_wall), ("vp_far", vp_far),
+                    ("vs_far", vs_far)):
+        _check(t, torch.float32, (nz,), name)
+    vp = torch.empty((nr, nz), dtype=torch.float32, device=vp_wall.device)
+    vs = torch.empty_like(vp)
+    stream = stream if stream is not None else torch.cuda.current_stream(vp_wall.device)
+    rc = lib.bh_starting_model(int(nr), int(nz), float(dr), float(r_wall), float(r_far),
+                               _ptr(vp_wall), _ptr(vs_wall), _ptr(vp_far), _ptr(vs_far),
+                               float(vp_fluid), _ptr(vp), _ptr(vs),
+                               ctypes.c_void_p(stream.cuda_stream))
+    if rc != BH_OK:
+        raise BhError(rc, lib.bh_last_error(None).decode())
+    return vp, vs

@@ -271,6 +271,33 @@ __global__ void k_update_apply(size_t n, const uint8_t* __restrict__ mask,
     vs[k] = (float)sqrt((double)mf / r);
 }
 
+// Starting model (Numerical Examples, Fig. 3, Fig. 4): per depth j, the
+// velocities at the borehole wall and at r_far, linear in r in between (no
+// fused multiply-add, so the rounding is that of the plain expression), the
+// far values beyond, the fluid in the cells whose centre lies inside the wall.
+__global__ void k_starting_model(int nr, int nz, double dr, double r_wall, double r_far,
+                                 const float* __restrict__ vp_wall,
+                                 const float* __restrict__ vs_wall,
+                                 const float* __restrict__ vp_far,
+                                 const float* __restrict__ vs_far, float vp_fluid, float* vp,
+                                 float* vs)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nr || j >= nz) return;
+    const size_t c = (size_t)i * nz + j;
+    const double r = __dmul_rn(i + 0.5, dr);
+    if (r < r_wall) {
+        vp[c] = vp_fluid;
+        vs[c] = 0.f;
+        return;
+    }
+    const double t = fmin(fmax(__ddiv_rn(__dsub_rn(r, r_wall), __dsub_rn(r_far, r_wall)), 0.0), 1.0);
+    const double pw = vp_wall[j], sw = vs_wall[j];
+    vp[c] = (float)__dadd_rn(pw, __dmul_rn(t, __dsub_rn((double)vp_far[j], pw)));
+    vs[c] = (float)__dadd_rn(sw, __dmul_rn(t, __dsub_rn((double)vs_far[j], sw)));
+}
+
 // ---- update in (Vp, Vs) and optionally rho (Eq. 9, Eq. 10 applied to the
 // velocities; chain rule of Eq. 3, Eq. 4 in FP64)
 

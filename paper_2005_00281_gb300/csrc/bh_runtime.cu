@@ -1351,6 +1351,24 @@ bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
     return BH_OK;
 }
 
+bh_status bh_starting_model(int nr, int nz, double dr, double r_wall, double r_far,
+                            const float* vp_wall, const float* vs_wall, const float* vp_far,
+                            const float* vs_far, float vp_fluid, float* vp, float* vs,
+                            void* stream)
+{
+    if (nr < 1 || nz < 1 || !(dr > 0) || !(r_wall >= 0) || !(r_far > r_wall) || !vp_wall ||
+        !vs_wall || !vp_far || !vs_far || !vp || !vs)
+        return fail(nullptr, BH_ERR_INVALID_ARG, "bh_starting_model: bad argument");
+    const cudaStream_t st = (cudaStream_t)stream;
+    k_starting_model<<<grid2d(nr, nz), block2d(), 0, st>>>(nr, nz, dr, r_wall, r_far, vp_wall,
+                                                           vs_wall, vp_far, vs_far, vp_fluid,
+                                                           vp, vs);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(nullptr, BH_ERR_CUDA, std::string("bh_starting_model: ") + cudaGetErrorString(e));
+    return BH_OK;
+}
+
 bh_status bh_plan_history(int nt, double hist_step_bytes, double snapshot_bytes,
                           size_t cap_bytes, int* L, int* nsnap, int* tail, long long* recompute)
 {

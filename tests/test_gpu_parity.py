@@ -432,3 +432,23 @@ def test_stored_tail_batched(cuda, persistent):
     assert np.array_equal(seis_0, seis_c)
     for a, b in zip(g_0, g_c):
         assert np.array_equal(a, b)
+
+
+def test_starting_model_parity(cuda, orc):
+    """bh_starting_model against the oracle's starting_model with depth-
+    varying logs (the paper's semblance values as one of them)."""
+    from oracle import oracle as O
+    from paper_2005_00281_gb300.bh import starting_model
+    torch = cuda
+    rng = np.random.default_rng(4)
+    nr, nz, dr = 240, 97, 0.005
+    vpw = rng.uniform(2500, 3200, nz).astype(np.float32)
+    vsw = (vpw / 1.8).astype(np.float32)
+    vpf = rng.uniform(3000, 3600, nz).astype(np.float32)
+    vsf = (vpf / 1.75).astype(np.float32)
+    vpw[0], vsw[0], vpf[0], vsf[0] = 2930.0, 1647.0, 3278.0, 1929.0
+    t = lambda a: torch.from_numpy(a).cuda()
+    vp, vs = starting_model(nr, dr, 0.10, 1.10, t(vpw), t(vsw), t(vpf), t(vsf))
+    vp_o, vs_o = O.starting_model(nr, dr, 0.10, 1.10, vpw, vsw, vpf, vsf, 1500.0)
+    np.testing.assert_array_equal(vp.cpu().numpy(), vp_o.astype(np.float32))
+    np.testing.assert_array_equal(vs.cpu().numpy(), vs_o.astype(np.float32))

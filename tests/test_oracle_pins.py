@@ -554,3 +554,39 @@ def test_update_velocity_descends(orc, tiny_gradient, update_rho):
     assert pred < 0 and dJ < 0
     # the second-order remainder is ~1e-4 of the change at this step
     assert abs(dJ - pred) <= 1e-3 * abs(pred), (dJ, pred)
+
+
+def test_starting_model_from_the_paper_semblance(orc):
+    """The starting model built from the velocities the paper's semblance
+    gives (Fig. 4 caption): at the wall the near-monopole values, from one
+    meter into the formation the ultra-far values, linear in between, water
+    inside the 0.10 m borehole."""
+    from tests.test_golden import _paper_values
+    vals = _paper_values()
+    f = lambda k: float(vals[k][0])
+    nr, nz, dr = 300, 3, 0.005
+    r_wall = 0.10
+    r_far = r_wall + f("far_velocity_distance")
+    one = np.ones(nz)
+    vp, vs = orc.starting_model(nr, dr, r_wall, r_far, f("near_p_velocity") * one,
+                                f("near_s_velocity") * one, f("ultrafar_p_velocity") * one,
+                                f("ultrafar_s_velocity") * one, 1500.0)
+    r = (np.arange(nr) + 0.5) * dr
+    assert np.all(vp[r < r_wall] == 1500.0) and np.all(vs[r < r_wall] == 0.0)
+    # beyond one meter: the ultra-far values
+    assert np.all(vp[r >= r_far] == 3278.0) and np.all(vs[r >= r_far] == 1929.0)
+    # half-way (r = 0.60 m lies between two cell centres): the mean of the two
+    i = int(round((r_wall + r_far) / 2 / dr))
+    np.testing.assert_allclose((vp[i - 1] + vp[i]) / 2, (2930.0 + 3278.0) / 2, rtol=1e-14)
+    np.testing.assert_allclose((vs[i - 1] + vs[i]) / 2, (1647.0 + 1929.0) / 2, rtol=1e-14)
+    # the first formation cell, dr/2 beyond the wall
+    np.testing.assert_allclose(vp[20], 2930.0 + (3278.0 - 2930.0) * (dr / 2) / 1.0, rtol=1e-14)
+    # linear in r: constant second differences between wall and 1 m
+    band = (r > r_wall) & (r < r_far)
+    assert np.max(np.abs(np.diff(vp[band, 0], 2))) < 1e-9
+    # depth-dependent logs: each depth follows its own pair
+    vp2, _ = orc.starting_model(nr, dr, r_wall, r_far, np.array([2000.0, 3000.0, 4000.0]),
+                                np.zeros(3), np.array([2500.0, 3000.0, 3500.0]), np.zeros(3),
+                                1500.0)
+    np.testing.assert_allclose(vp2[-1], [2500.0, 3000.0, 3500.0])
+    np.testing.assert_allclose(vp2[20], [2000.0 + 500 * 0.0025, 3000.0, 4000.0 - 500 * 0.0025])
