@@ -41,7 +41,8 @@ REF_SAMPLE_STEPS = 100
 L2_BYTES = 129e6
 # checkpoint byte cap per workload when --cap-gb is not given (0: every step
 # of the forward history stored)
-DEFAULT_CAP_GB = {"c0": 0.0, "c1": 0.0, "c2": 240.0, "c3": 4.0, "c4": 60.0}
+DEFAULT_CAP_GB = {"c0": 0.0, "c1": 0.0, "c2": 240.0, "c3": 4.0, "c4": 60.0, "flushed": 100.0,
+                  "tool": 150.0}
 DEFAULT_SNAP = {"c4": "bf16"}
 E2E_STEPS = 3
 SECONDARY_STEPS = 10
@@ -572,7 +573,8 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--config", default="c2",
+                    choices=["c0", "c1", "c2", "c3", "c4", "flushed", "tool"])
     ap.add_argument("--cap-gb", type=float, default=None,
                     help="checkpoint cap in GB (0: store every step of the forward history; "
                          "default per workload: c2 240, c3 4, c4 60, else 0)")

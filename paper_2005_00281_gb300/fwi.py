@@ -39,9 +39,13 @@ def load(path, model, device="cuda"):
 
 
 def run(model, wavelet, seis_obs, iterations, *, kappa=0.02, eps_rel=1e-3, threshold=0.0,
-        precondition=True, state: FwiState | None = None, checkpoint_path=None, rho=None,
-        log=None):
-    """Run up to `iterations` more inversion steps.  Returns the FwiState."""
+        rel_threshold=0.0, precondition=True, param="lame", update_rho=False,
+        state: FwiState | None = None, checkpoint_path=None, rho=None, log=None):
+    """Run up to `iterations` more inversion steps, stopping once the misfit
+    falls to `threshold` or to `rel_threshold` times the first iteration's
+    (the stop rule of the Method section).  param "lame" steps lambda and mu
+    (Eq. 9, Eq. 10); "velocity" steps Vp, Vs and, with update_rho, rho.
+    Returns the FwiState."""
     st = state or FwiState()
     seis = model.empty_seis()
     resid = torch.empty_like(seis)
@@ -49,13 +53,18 @@ def run(model, wavelet, seis_obs, iterations, *, kappa=0.02, eps_rel=1e-3, thres
         t0 = time.perf_counter()
         model.forward(wavelet, seis)
         _, J = model.residual_misfit(seis, seis_obs, resid)
-        if J <= threshold:
+        if J <= threshold or (st.J and rel_threshold > 0 and J <= rel_threshold * st.J[0]):
             st.J.append(J)
             break
-        g_lam, g_mu, _ = model.adjoint_gradient(resid, with_rho=False)
+        want_rho = param == "velocity" and update_rho
+        g_lam, g_mu, g_rho = model.adjoint_gradient(resid, with_rho=want_rho)
         if precondition:
             model.precondition(g_lam, g_mu, eps_rel)
-        alpha, _, _ = model.update(g_lam, g_mu, kappa, want_velocities=False)
+        if param == "velocity":
+            alpha, _, _, _ = model.update_velocity(g_lam, g_mu, g_rho, update_rho=update_rho,
+                                                   kappa=kappa, want_model=False)
+        else:
+            alpha, _, _ = model.update(g_lam, g_mu, kappa, want_velocities=False)
         st.iteration += 1
         st.J.append(J)
         st.alpha.append(alpha)
@@ -98,11 +107,26 @@ def main(argv=None):
     ap.add_argument("--fd-step", type=float, default=1e-2, help="relative Vp change")
     ap.add_argument("--kappa", type=float, default=0.02)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--start", default="workload", choices=["workload", "logs"],
+                    help="start model: the workload's, or the velocity logs at the wall and "
+                         "one meter beyond interpolated in r (bh_starting_model)")
+    ap.add_argument("--rel-threshold", type=float, default=0.0,
+                    help="stop once J falls to this fraction of the first iteration's")
+    ap.add_argument("--param", default="lame", choices=["lame", "velocity"])
+    ap.add_argument("--no-precondition", dest="precondition", action="store_false")
     args = ap.parse_args(argv)
     if not torch.cuda.is_available():
         raise SystemExit("the inversion needs a CUDA device (there is no CPU fallback)")
     w = PRESETS[args.config]() if args.config == "c0" else PRESETS[args.config](seed=args.seed)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    if args.start == "logs":
+        from .bh import starting_model
+        if w.logs is None:
+            raise SystemExit(f"workload {args.config} has no velocity logs")
+        lg = w.logs
+        vp_s, vs_s = starting_model(w.nr, w.dr, lg["r_wall"], lg["r_far"], t(lg["vp_wall"]),
+                                    t(lg["vs_wall"]), t(lg["vp_far"]), t(lg["vs_far"]))
+        w.vp, w.vs = vp_s.cpu().numpy(), vs_s.cpu().numpy()
     cap = int(args.cap_gb * 1e9)
     m = model_from_workload(w, checkpoint_cap_bytes=cap)
     wav = t(w.wavelet)
@@ -110,6 +134,49 @@ def main(argv=None):
         obs = BhWave.apply(t(w.vp_true), t(w.vs_true), t(w.rho_true), m, wav).clone()
 
     # gradient of J with respect to Vp at the start model, against central differences
+    fd_rows, fd_err, rel = [], None, [float("nan")]
+    if args.fd_cells > 0:
+        fd_rows, fd_err, rel = _fd_check(args, w, m, wav, obs, t)
+
+    # the inversion loop from the start model
+    vs, rho = t(w.vs), t(w.rho)
+    m.set_model(t(w.vp), vs, rho)
+    mask = ((w.vs > 0) & (np.arange(w.nr)[:, None] < w.nr - w.npml_r) &
+            (np.arange(w.nz)[None, :] >= w.npml_z) & (np.arange(w.nz)[None, :] < w.nz - w.npml_z))
+
+    def model_error():
+        vp_c, vs_c = m.velocities()
+        vp_c, vs_c = vp_c.cpu().numpy(), vs_c.cpu().numpy()
+        e = lambda a, b: float(np.linalg.norm((a - b)[mask]) / np.linalg.norm(b[mask]))
+        return {"vp": e(vp_c, w.vp_true), "vs": e(vs_c, w.vs_true)}
+
+    err0 = model_error()
+    st = run(m, wav, obs, args.iterations, kappa=args.kappa, rel_threshold=args.rel_threshold,
+             precondition=args.precondition, param=args.param,
+             log=lambda s: print(s, file=sys.stderr, flush=True))
+    err1 = model_error()
+    info = {k: m.info(k) for k in ("history_steps", "snapshots", "tail_steps", "recompute_steps",
+                                   "history_snapshot_bytes")}
+    m.close()
+    print(json.dumps({
+        "workload": args.config, "nr": w.nr, "nz": w.nz, "nt": w.nt, "nshots": w.nshots,
+        "start": args.start, "param": args.param, "precondition": args.precondition,
+        "rel_threshold": args.rel_threshold, "iterations_run": st.iteration,
+        "model_rel_error_start": err0, "model_rel_error_end": err1,
+        "checkpoint": info, "J": [float(x) for x in st.J],
+        "seconds_per_iteration": [float(x) for x in st.seconds],
+        "fd_check": {"cells": args.fd_cells, "relative_step": args.fd_step,
+                     "max_abs_error_over_max_gradient": fd_err,
+                     "largest_cells_relative_error_median": float(np.median(rel)),
+                     "largest_cells_relative_error_max": float(np.max(rel)),
+                     "rows_random": [list(r) for r in fd_rows[: args.fd_cells]],
+                     "rows_largest": [list(r) for r in fd_rows[args.fd_cells:]]}}), flush=True)
+
+
+def _fd_check(args, w, m, wav, obs, t):
+    """Central differences of J in Vp at random formation cells and at the
+    cells of largest gradient, against BhWave's gradient."""
+    from .autograd import BhWave, misfit
     vp = t(w.vp).requires_grad_(True)
     vs, rho = t(w.vs), t(w.rho)
     J0 = misfit(BhWave.apply(vp, vs, rho, m, wav), obs, m)
@@ -135,24 +202,7 @@ def main(argv=None):
     gmax = float(np.abs(g).max())
     fd_err = max(abs(fd - ad) for _, _, fd, ad in fd_rows) / gmax
     rel = [abs(fd - ad) / abs(ad) for _, _, fd, ad in fd_rows[args.fd_cells:]]
-
-    # the inversion loop from the start model
-    m.set_model(t(w.vp), vs, rho)
-    st = run(m, wav, obs, args.iterations, kappa=args.kappa,
-             log=lambda s: print(s, file=sys.stderr, flush=True))
-    info = {k: m.info(k) for k in ("history_steps", "snapshots", "recompute_steps",
-                                   "history_snapshot_bytes")}
-    m.close()
-    print(json.dumps({
-        "workload": args.config, "nr": w.nr, "nz": w.nz, "nt": w.nt, "nshots": w.nshots,
-        "checkpoint": info, "J": [float(x) for x in st.J],
-        "seconds_per_iteration": [float(x) for x in st.seconds],
-        "fd_check": {"cells": args.fd_cells, "relative_step": args.fd_step,
-                     "max_abs_error_over_max_gradient": fd_err,
-                     "largest_cells_relative_error_median": float(np.median(rel)),
-                     "largest_cells_relative_error_max": float(np.max(rel)),
-                     "rows_random": [list(r) for r in fd_rows[: args.fd_cells]],
-                     "rows_largest": [list(r) for r in fd_rows[args.fd_cells:]]}}), flush=True)
+    return fd_rows, fd_err, rel
 
 
 if __name__ == "__main__":

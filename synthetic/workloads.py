@@ -43,6 +43,7 @@ class Workload:
     shots: list = field(default_factory=list)  # dicts: z_offset, nz, src, rec_iz
     wavelet: np.ndarray | None = None          # [nt] float32, s(t_{n+1/2})
     pml_R: float = 1e-3
+    logs: dict | None = None                   # velocity logs at the wall and 1 m beyond
 
     @property
     def nshots(self):
@@ -231,7 +232,7 @@ def tiny_borehole(seed=0, nr=24, nz=48, npml=6, nt=300, h=0.01, dt=1e-6, f0=15e3
                     rho.copy(), [shot], ricker(nt, dt, f0))
 
 
-PRESETS = {"c0": config0, "c1": config1, "c2": config2, "c3": config3, "c4": config4}
+
 
 
 # ---------------------------------------------------------------------------
@@ -325,3 +326,61 @@ def tool_logging_run(seed=0, ndepths=16, nt=6000, near_offset=3.0, h=0.005, dt=0
     del recs_probe
     return Workload(name, nr, nzg, nt, npml, npml, h, h, dt, f0, vp, vs, rho, vpt, vst,
                     rho.copy(), shots, ricker(nt, dt, f0))
+
+
+def flushed_zone(seed=0, nshots=8, nt=8000, h=0.005, dt=0.5e-6, f0=1e4, npml=40, nr=240,
+                 nz_window=1700, name="flushed"):
+    """A layered formation with a low-velocity flushed (invaded) zone around
+    the borehole whose depth changes from bed to bed: velocity variation in
+    both the radial and the axial direction, like the paper's second model
+    (Numerical Examples, Fig. 7; its values are not printed).  Beds 0.3-1.0 m
+    thick as in the production shot; in each bed the flushed zone reaches
+    U(0.05, 0.35) m beyond the wall with Vp lowered by U(8, 15) % and Vs by
+    half as much.  The true model has the flushed zone, the start model is the
+    virgin formation.  `logs` holds what the near- and far-offset data see at
+    every depth: the velocities at the wall and one meter beyond it.  Shots
+    step 0.15 m with windows of nz_window cells, geometry as the production
+    shot."""
+    rng = np.random.default_rng(seed)
+    step = int(round(0.15 / h))
+    nzg = (nshots - 1) * step + nz_window
+    fluid = _borehole(nr, 0, h)
+    vp = np.empty((nr, nzg))
+    vs = np.empty((nr, nzg))
+    rho = np.empty((nr, nzg))
+    vpt = np.empty((nr, nzg))
+    vst = np.empty((nr, nzg))
+    r = (np.arange(nr) + 0.5) * h
+    z = 0
+    while z < nzg:
+        thick = max(1, int(round(rng.uniform(0.3, 1.0) / h)))
+        bvp = rng.uniform(3000.0, 5000.0)
+        bvs = bvp / rng.uniform(1.7, 1.9)
+        brho = rng.uniform(2200.0, 2600.0)
+        depth = rng.uniform(0.05, 0.35)
+        drop = rng.uniform(0.08, 0.15)
+        sl = np.s_[:, z: z + thick]
+        vp[sl], vs[sl], rho[sl] = bvp, bvs, brho
+        inv = (r >= BOREHOLE_RADIUS) & (r < BOREHOLE_RADIUS + depth)
+        vpt[sl] = bvp
+        vst[sl] = bvs
+        vpt[inv, z: z + thick] = bvp * (1.0 - drop)
+        vst[inv, z: z + thick] = bvs * (1.0 - drop / 2)
+        z += thick
+    _fill_fluid(vp, vs, rho, fluid)
+    vpt[fluid], vst[fluid] = vp[fluid], vs[fluid]
+    vp, vs, rho, vpt, vst = _f32(vp, vs, rho, vpt, vst)
+    shots = [_shot(s * step, nz_window, npml, h) for s in range(nshots)]
+    w = Workload(name, nr, nzg, nt, npml, npml, h, h, dt, f0, vp, vs, rho, vpt, vst,
+                 rho.copy(), shots, ricker(nt, dt, f0))
+    i_wall = int(np.argmax(~fluid))
+    i_far = int(np.argmin(np.abs(r - (BOREHOLE_RADIUS + 1.0))))
+    w.logs = dict(r_wall=BOREHOLE_RADIUS, r_far=BOREHOLE_RADIUS + 1.0,
+                  vp_wall=np.ascontiguousarray(vpt[i_wall]), vs_wall=np.ascontiguousarray(vst[i_wall]),
+                  vp_far=np.ascontiguousarray(vpt[min(i_far, nr - npml - 1)]),
+                  vs_far=np.ascontiguousarray(vst[min(i_far, nr - npml - 1)]))
+    return w
+
+
+PRESETS = {"c0": config0, "c1": config1, "c2": config2, "c3": config3, "c4": config4,
+           "flushed": flushed_zone, "tool": tool_logging_run}
