@@ -126,6 +126,18 @@ enum {
     TILE_LAST = 2   // the staged columns hold the window's last node row
 };
 
+// Tile class a launch covers: interior tiles only, C-PML tiles only (one
+// launch each per half-step, so the interior code, which holds no layer
+// state, gets its own register budget and occupancy), or either with the
+// flag read per tile (the persistent kernels).
+enum { PM_INTERIOR = 0, PM_PML = 1, PM_ANY = 2 };
+
+template <int PM>
+__device__ __forceinline__ bool tile_pml(int flags)
+{
+    return PM == PM_ANY ? (flags & TILE_PML) != 0 : PM == PM_PML;
+}
+
 // Programmatic dependent launch: a kernel may be scheduled while its
 // predecessor drains; it must wait here before touching the predecessor's
 // outputs.  No-op when launched without the attribute.
@@ -454,13 +466,14 @@ struct __align__(16) FwdSmem {
 // Velocity half-step of one tile: Eq. 2 lines 1-2 with the C-PML memories
 // 0..3.  Own-node inputs are loaded before the staging, so the tile pays
 // one round trip to L2.  hist0 (or null): history slot receiving v^{n-1/2}.
+template <int PM>
 __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
                                              float* hist0, int i0, int j0, int flags,
                                              const BarK* bar, unsigned& epoch, FwdSmem& sm)
 {
     Tile &s_rr = sm.a, &s_tt = sm.b, &s_rz = sm.c, &s_zz = sm.d;
     const Own o = own_of(g, i0, j0);
-    const bool pml = flags & TILE_PML;
+    const bool pml = tile_pml<PM>(flags);
     V4 vr0{}, vz0{}, br{}, bz{}, q0{}, q1{}, q2{}, q3{};
     float ari = 0.f, bri = 0.f, arh = 0.f, brh = 0.f, ivr = 0.f, ivh = 0.f;
     V4 azi{}, bzi{}, azh{}, bzh{};
@@ -589,6 +602,7 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
 // Stress half-step of one tile: Eq. 2 lines 3-6 with the C-PML memories
 // 4..7, source injection into the three normal stresses, pressure
 // recording, and the store of v^{n+1/2} for the adjoint.
+template <int PM>
 __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const SrcRecK& q, int n, bool record,
                                                 float* hist, int i0, int j0, int flags,
@@ -596,7 +610,7 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
 {
     Tile &s_vr = sm.a, &s_vz = sm.b;
     const Own o = own_of(g, i0, j0);
-    const bool pml = flags & TILE_PML;
+    const bool pml = tile_pml<PM>(flags);
     __syncthreads();
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const Slot sl = slot_of(it, i0, j0, g);
@@ -770,6 +784,15 @@ struct __align__(16) AdjSmem {
     Prof pf;
 };
 
+// Shared memory of a velocity-step launch of its own (no stress-step tiles
+// kept): K = 8 tiles (W_r, W_z, the four coefficient tiles, two buoyancies),
+// or K = 4 for interior tiles, whose coefficients equal W.
+template <int K>
+struct __align__(16) AdjVelSmem {
+    Tile d[K];
+    Prof pf;
+};
+
 // the stress step's launch-invariant tiles (see AdjSmem)
 __device__ __forceinline__ void stage_adj_statics(AdjSmem& sm, const CoefK& C, const float* fcur,
                                                   int i0, int j0, const WinK& g)
@@ -858,7 +881,7 @@ __device__ __forceinline__ void adj_corr_shear(const WinK& g, const AdjK& q, con
 // (the block keeps this tile, so the f tiles are still in shared memory).
 // bar (or null): the block arrives at the grid barrier once the adjoint
 // velocities are stored; the own-node correlations follow the arrival.
-template <bool RHO>
+template <bool RHO, int PM>
 __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const AdjK& q, const float* fcur,
                                                 const float* fprev, int i0, int j0, int flags,
@@ -867,7 +890,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
 {
     const float dt = g.dt;
     const Own o = own_of(g, i0, j0);
-    const bool pml = flags & TILE_PML;
+    const bool pml = tile_pml<PM>(flags);
     const int rr = o.rr, cc = o.cc, i = o.i, c = o.c;
     Tile &T_rr = sm.d[0], &T_tt = sm.d[1], &T_zz = sm.d[2], &T_rz = sm.d[3];
     Tile &T_p4 = sm.d[4], &T_p5 = sm.d[5], &T_x6 = sm.d[6], &T_x7 = sm.d[7];
@@ -1061,18 +1084,21 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
 // next on this tile; its launch-invariant tiles are staged here, after the
 // block's arrival at the grid barrier (bar, or null: no barrier), and after
 // the correlations deferred by the stress step (fprev_b, or null).
-template <bool RHO>
+template <bool RHO, int PM, typename SM>
 __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
                                              const AdjK& q, int n, int i0, int j0, int flags,
                                              const float* next_fcur, const float* fprev_b,
-                                             const BarK* bar, unsigned& epoch, AdjSmem& sm)
+                                             const BarK* bar, unsigned& epoch, SM& sm)
 {
     // W = dt b Av at the velocity nodes (odd about the axis for v_r, even
-    // for v_z) and the coefficients on the four stretched derivatives
-    Tile &s_wr = sm.d[0], &s_wz = sm.d[1], &s_x0 = sm.d[2], &s_x1 = sm.d[3], &s_x2 = sm.d[4],
-         &s_x3 = sm.d[5], &s_br = sm.d[6], &s_bz = sm.d[7];
+    // for v_z) and the coefficients on the four stretched derivatives; on
+    // interior tiles the coefficients are W itself and share its tiles
+    constexpr bool kInt = PM == PM_INTERIOR;
+    Tile &s_wr = sm.d[0], &s_wz = sm.d[1];
+    Tile &s_x0 = sm.d[kInt ? 0 : 2], &s_x1 = sm.d[kInt ? 0 : 3], &s_x2 = sm.d[kInt ? 1 : 4],
+         &s_x3 = sm.d[kInt ? 1 : 5], &s_br = sm.d[kInt ? 2 : 6], &s_bz = sm.d[kInt ? 3 : 7];
     const Own o = own_of(g, i0, j0);
-    const bool pml = flags & TILE_PML;
+    const bool pml = tile_pml<PM>(flags);
     __syncthreads();
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const Slot sl = slot_of(it, i0, j0, g);
@@ -1152,8 +1178,10 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
                     if (azi.v[e] != 0.f) x1[e] = w[e] + azi.v[e] * (w[e] + bzi.v[e] * p1.v[e]);
             }
             *reinterpret_cast<float4*>(&s_wr[r2][c2]) = make_float4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<float4*>(&s_x0[r2][c2]) = make_float4(x0[0], x0[1], x0[2], x0[3]);
-            *reinterpret_cast<float4*>(&s_x1[r2][c2]) = make_float4(x1[0], x1[1], x1[2], x1[3]);
+            if (!kInt) {
+                *reinterpret_cast<float4*>(&s_x0[r2][c2]) = make_float4(x0[0], x0[1], x0[2], x0[3]);
+                *reinterpret_cast<float4*>(&s_x1[r2][c2]) = make_float4(x1[0], x1[1], x1[2], x1[3]);
+            }
         }
         // v_z node
         {
@@ -1190,8 +1218,10 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
                     if (azh.v[e] != 0.f) x3[e] = w[e] + azh.v[e] * (w[e] + bzh.v[e] * p3.v[e]);
             }
             *reinterpret_cast<float4*>(&s_wz[r2][c2]) = make_float4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<float4*>(&s_x2[r2][c2]) = make_float4(x2[0], x2[1], x2[2], x2[3]);
-            *reinterpret_cast<float4*>(&s_x3[r2][c2]) = make_float4(x3[0], x3[1], x3[2], x3[3]);
+            if (!kInt) {
+                *reinterpret_cast<float4*>(&s_x2[r2][c2]) = make_float4(x2[0], x2[1], x2[2], x2[3]);
+                *reinterpret_cast<float4*>(&s_x3[r2][c2]) = make_float4(x3[0], x3[1], x3[2], x3[3]);
+            }
         }
     }
     __syncthreads();
@@ -1232,20 +1262,23 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         st4(S.trz + c, o.j, g.nz, trz);
     }
     if (bar) grid_arrive(*bar, epoch);
-    // fprev_b (or null): v^{n-1/2}; the stress step deferred its density and
-    // shear correlations to here (own nodes only: no other block reads them)
-    if (fprev_b) {
-        if (o.live) {
-            const V4 az = ld4cg(S.vz + c);
-            V4 ar{};
-            if (i >= 1) ar = ld4cg(S.vr + c);
-            adj_corr_shear<RHO>(g, q, o, fprev_b, sm.f[0], sm.f[1], o_rz, az.v, ar.v);
+    if constexpr (PM == PM_ANY) {
+        // fprev_b (or null): v^{n-1/2}; the stress step deferred its density
+        // and shear correlations to here (own nodes only: no other block
+        // reads them)
+        if (fprev_b) {
+            if (o.live) {
+                const V4 az = ld4cg(S.vz + c);
+                V4 ar{};
+                if (i >= 1) ar = ld4cg(S.vr + c);
+                adj_corr_shear<RHO>(g, q, o, fprev_b, sm.f[0], sm.f[1], o_rz, az.v, ar.v);
+            }
+            __syncthreads();  // the f tiles are read above and refilled below
         }
-        __syncthreads();  // the f tiles are read above and refilled below
+        // the next stress step's launch-invariant tiles: the copies run during
+        // the grid barrier
+        if (next_fcur) stage_adj_statics(sm, C, next_fcur, i0, j0, g);
     }
-    // the next stress step's launch-invariant tiles: the copies run during
-    // the grid barrier
-    if (next_fcur) stage_adj_statics(sm, C, next_fcur, i0, j0, g);
 }
 
 // ------------------------------------------------ shots, tiles, runs
@@ -1293,17 +1326,17 @@ __device__ __forceinline__ const ShotK& shot_of(const ShotTable<N>& T, int4 tk)
     return T.s[N == 1 ? 0 : tk.x];
 }
 
-template <int N>
+template <int N, int PM>
 __device__ __forceinline__ void run_fwd_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
                                             const BarK* bar, unsigned& epoch, FwdSmem& sm)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     float* h0 = (r.hist_n0 >= 0 && n == r.hist_n0) ? hist_slot(sh, 0) : nullptr;
-    fwd_vel_tile(sh.g, sh.C, sh.Sf, h0, tk.y, tk.z, tk.w, bar, epoch, sm);
+    fwd_vel_tile<PM>(sh.g, sh.C, sh.Sf, h0, tk.y, tk.z, tk.w, bar, epoch, sm);
 }
 
-template <int N>
+template <int N, int PM>
 __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>& T, int n,
                                                int t, const BarK* bar, unsigned& epoch,
                                                FwdSmem& sm)
@@ -1311,14 +1344,14 @@ __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     float* h = r.hist_n0 >= 0 ? hist_slot(sh, n - r.hist_n0 + 1) : nullptr;
-    fwd_stress_tile(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, tk.w, bar, epoch,
-                    sm);
+    fwd_stress_tile<PM>(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, tk.w, bar,
+                        epoch, sm);
 }
 
 // statics / prefetch: the block keeps one tile for the whole run, so the
 // velocity step of reverse step n stages the stress step's launch-invariant
 // tiles for step n-1 (AdjSmem)
-template <int N, bool RHO>
+template <int N, bool RHO, int PM>
 __device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>& T, int n,
                                                int t, bool statics, bool defer,
                                                const BarK* bar, unsigned& epoch, AdjSmem& sm)
@@ -1326,68 +1359,71 @@ __device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
-    adj_stress_tile<RHO>(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, n - r.hist_n0 + 1),
+    adj_stress_tile<RHO, PM>(sh.g, sh.C, sh.Sa[parity], sh.a, hist_slot(sh, n - r.hist_n0 + 1),
                     hist_slot(sh, n - r.hist_n0), tk.y, tk.z, tk.w, statics, defer, bar, epoch,
                     sm);
 }
 
-template <int N, bool RHO>
+template <int N, bool RHO, int PM, typename SM>
 __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
                                             bool prefetch, bool deferred, const BarK* bar,
-                                            unsigned& epoch, AdjSmem& sm)
+                                            unsigned& epoch, SM& sm)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     const int parity = (r.nt - 1 - n) & 1;
     // v^{n-1/2}: fcur of step n-1 (prefetch) and fprev of step n (deferred)
     const float* prev = hist_slot(sh, n - r.hist_n0);
-    adj_vel_tile<RHO>(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w,
+    adj_vel_tile<RHO, PM>(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w,
                       prefetch ? prev : nullptr,
                  deferred ? prev : nullptr, bar, epoch, sm);
 }
 
-// one launch per half-step: one block per tile
-template <int N>
-__global__ void __launch_bounds__(kThreads, 5) k_fwd_vel(RunK r, int n,
-                                                      const __grid_constant__ ShotTable<N> T)
+// One launch per half-step and tile class: one block per tile.  Interior
+// tiles hold no C-PML state, so their kernels fit more blocks per SM (the
+// forward velocity and adjoint velocity steps 8, the forward stress step 6,
+// against 5 for C-PML tiles).
+template <int N, int PM>
+__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
+    k_fwd_vel(RunK r, int n, const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_fwd_vel(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    run_fwd_vel<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads, 5) k_fwd_stress(RunK r, int n,
-                                                         const __grid_constant__ ShotTable<N> T)
+template <int N, int PM>
+__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 6 : 5)
+    k_fwd_stress(RunK r, int n, const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_fwd_stress(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    run_fwd_stress<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
-template <int N, bool RHO>
+template <int N, bool RHO, int PM>
 __global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n,
                                                          const __grid_constant__ ShotTable<N> T)
 {
     __shared__ AdjSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_adj_stress<N, RHO>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    run_adj_stress<N, RHO, PM>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
-template <int N, bool RHO>
-__global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
-                                                      const __grid_constant__ ShotTable<N> T)
+template <int N, bool RHO, int PM>
+__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
+    k_adj_vel(RunK r, int n, const __grid_constant__ ShotTable<N> T)
 {
-    __shared__ AdjSmem sm;
+    __shared__ AdjVelSmem<PM == PM_INTERIOR ? 4 : 8> sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_adj_vel<N, RHO>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    run_adj_vel<N, RHO, PM>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1402,11 +1438,13 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(RunK r, BarK b,
     for (int n = r.n0; n < r.n1; ++n) {
         // the block's last tile of a phase arrives at the barrier itself
         for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_fwd_vel(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
+            run_fwd_vel<N, PM_ANY>(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr,
+                                   epoch, sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
         for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_fwd_stress(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
+            run_fwd_stress<N, PM_ANY>(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr,
+                                      epoch, sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
     }
@@ -1424,12 +1462,12 @@ __global__ void __launch_bounds__(kThreads, 5) k_adj_persist(RunK r, BarK b,
     for (int n = r.n1 - 1; n >= r.n0; --n) {
         // the block's last tile of a phase arrives at the barrier itself
         for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_adj_stress<N, RHO>(r, T, n, t, one && n < r.n1 - 1, one,
+            run_adj_stress<N, RHO, PM_ANY>(r, T, n, t, one && n < r.n1 - 1, one,
                            t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
         for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_adj_vel<N, RHO>(r, T, n, t, one && n > r.n0, one,
+            run_adj_vel<N, RHO, PM_ANY>(r, T, n, t, one && n > r.n0, one,
                         t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;

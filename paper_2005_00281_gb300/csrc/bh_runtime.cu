@@ -66,7 +66,9 @@ struct bh_model {
     std::vector<ShotK> h_shots;
     int4* d_tiles = nullptr;    // tiles of every shot group, group after group
     int ntiles = 0;
-    std::vector<int> group_tile_off, group_ntiles;  // per group of up to kGroup shots
+    int G = 1;                  // shots per launch group (1 .. kGroup)
+    std::vector<int> group_tile_off, group_ntiles;  // per group of G shots
+    std::vector<int> group_nint;  // interior tiles of each group (listed first)
     // history window and checkpoint schedule
     int L = 0;                  // steps per history window (nt: store every step)
     int nsnap = 0;              // stored snapshot slots (slot 0 is the zero state)
@@ -377,6 +379,8 @@ bh_status setup_profiles(bh_model* m)
     return BH_OK;
 }
 
+bh_status build_tiles(bh_model* m);
+
 // Per-shot descriptors (pointers into the arenas) and the tile table.
 bh_status setup_shots(bh_model* m)
 {
@@ -384,7 +388,6 @@ bh_status setup_shots(bh_model* m)
     const int nr = gd.nr;
     const size_t pl = plane(m);
     m->h_shots.resize(m->nshots);
-    std::vector<int4> tiles;
     for (int s = 0; s < m->nshots; ++s) {
         const ShotHost& sh = m->shots[s];
         ShotK& k = m->h_shots[s];
@@ -464,7 +467,26 @@ bh_status setup_shots(bh_model* m)
         k.a.H_munn = a + 33 * pl;
         k.a.H_murz = a + 34 * pl;
         k.hist = m->d_hist + (size_t)s * m->hist_slots * 2 * pl;
-        if (s % kGroup == 0) {
+    }
+    return build_tiles(m);
+}
+
+// Tile table of every shot group of G shots, group after group.  Within a
+// group the tiles are ordered by global column, then row, then shot (tiles
+// of several shots at one place of the model run together and share the
+// coefficient copies' lines in L2), interior tiles first (the per-half-step
+// form launches the two classes separately).
+bh_status build_tiles(bh_model* m)
+{
+    const bh_grid_desc& gd = m->grid;
+    const int nr = gd.nr, G = m->G;
+    std::vector<int4> tiles;
+    m->group_tile_off.clear();
+    m->group_ntiles.clear();
+    m->group_nint.clear();
+    for (int s = 0; s < m->nshots; ++s) {
+        const ShotHost& sh = m->shots[s];
+        if (s % G == 0) {
             m->group_tile_off.push_back((int)tiles.size());
             m->group_ntiles.push_back(0);
         }
@@ -477,26 +499,28 @@ bh_status setup_shots(bh_model* m)
                 const bool axial = gd.npml_z > 0 &&
                                    (j0 - 4 <= gd.npml_z + 1 || j0 + kTZ + 4 >= sh.nz - gd.npml_z - 2);
                 const bool last = j0 - 4 <= sh.nz - 1 && sh.nz - 1 <= j0 + kTZ + 3;
-                tiles.push_back(make_int4(s % kGroup, i0, j0,
+                tiles.push_back(make_int4(s % G, i0, j0,
                                           ((radial || axial) ? TILE_PML : 0) |
                                               (last ? TILE_LAST : 0)));
                 m->group_ntiles.back()++;
             }
-        // the group's tiles ordered by global column, then row, then shot:
-        // tiles of several shots at one place of the model run together and
-        // share the coefficient copies' lines in L2
-        if (s % kGroup == kGroup - 1 || s == m->nshots - 1) {
+        if (s % G == G - 1 || s == m->nshots - 1) {
             const int g0 = m->group_tile_off.back();
-            const int sbase = s - s % kGroup;
+            const int sbase = s - s % G;
             std::stable_sort(tiles.begin() + g0, tiles.end(), [&](const int4& a, const int4& b) {
                 const int za = m->shots[sbase + a.x].z0 + a.z, zb = m->shots[sbase + b.x].z0 + b.z;
                 if (za != zb) return za < zb;
                 if (a.y != b.y) return a.y < b.y;
                 return a.x < b.x;
             });
+            auto mid = std::stable_partition(tiles.begin() + g0, tiles.end(),
+                                             [](const int4& t) { return !(t.w & TILE_PML); });
+            m->group_nint.push_back((int)(mid - (tiles.begin() + g0)));
         }
     }
     m->ntiles = (int)tiles.size();
+    cudaFree(m->d_tiles);
+    m->d_tiles = nullptr;
     BH_CUDA(m, dalloc(&m->d_tiles, tiles.size()));
     BH_CUDA(m, cudaMemcpyAsync(m->d_tiles, tiles.data(), tiles.size() * sizeof(int4),
                                cudaMemcpyHostToDevice, m->stream));
@@ -510,7 +534,8 @@ ShotTable<N> group_table(const bh_model* m, int grp)
 {
     ShotTable<N> T;
     memset(&T, 0, sizeof(T));
-    for (int k = 0; k < N && grp * kGroup + k < m->nshots; ++k) T.s[k] = m->h_shots[grp * kGroup + k];
+    for (int k = 0; k < N && k < m->G && grp * m->G + k < m->nshots; ++k)
+        T.s[k] = m->h_shots[grp * m->G + k];
     return T;
 }
 
@@ -585,7 +610,7 @@ int adj_blocks_for(const bh_model* m, bool one_shot)
 bool persistent_for(const bh_model* m, int grp, bool adjoint)
 {
     if (m->persistent != 2) return m->persistent != 0;
-    const bool one = m->nshots == 1;
+    const bool one = m->G == 1;
     const int blocks = adjoint ? adj_blocks_for(m, one) : (one ? m->fwd_blocks : m->fwd_blocks_g);
     return m->group_ntiles[grp] <= blocks;
 }
@@ -635,15 +660,35 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
         prof_end(m, e);
         return check_barrier(m);
     }
-    const dim3 grd(r.ntiles);
+    // interior tiles and C-PML tiles in a launch each
+    RunK ri = r, rp = r;
+    ri.ntiles = m->group_nint[grp];
+    rp.tiles = r.tiles + ri.ntiles;
+    rp.ntiles = r.ntiles - ri.ntiles;
     for (int n = n0; n < n1; ++n) {
         size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
-        BH_CUDA(m, launch_pdl(k_fwd_vel<N>, grd, blk, m->stream, r, n, T));
-        ++m->launches;
+        if (ri.ntiles) {
+            BH_CUDA(m, launch_pdl(k_fwd_vel<N, PM_INTERIOR>, dim3(ri.ntiles), blk, m->stream, ri,
+                                  n, T));
+            ++m->launches;
+        }
+        if (rp.ntiles) {
+            BH_CUDA(m, launch_pdl(k_fwd_vel<N, PM_PML>, dim3(rp.ntiles), blk, m->stream, rp, n,
+                                  T));
+            ++m->launches;
+        }
         prof_end(m, e);
         e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
-        BH_CUDA(m, launch_pdl(k_fwd_stress<N>, grd, blk, m->stream, r, n, T));
-        ++m->launches;
+        if (ri.ntiles) {
+            BH_CUDA(m, launch_pdl(k_fwd_stress<N, PM_INTERIOR>, dim3(ri.ntiles), blk, m->stream,
+                                  ri, n, T));
+            ++m->launches;
+        }
+        if (rp.ntiles) {
+            BH_CUDA(m, launch_pdl(k_fwd_stress<N, PM_PML>, dim3(rp.ntiles), blk, m->stream, rp,
+                                  n, T));
+            ++m->launches;
+        }
         prof_end(m, e);
     }
     return BH_OK;
@@ -669,18 +714,43 @@ bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
         prof_end(m, e);
         return check_barrier(m);
     }
-    const dim3 grd(r.ntiles);
+    RunK ri = r, rp = r;
+    ri.ntiles = m->group_nint[grp];
+    rp.tiles = r.tiles + ri.ntiles;
+    rp.ntiles = r.ntiles - ri.ntiles;
     for (int n = n1 - 1; n >= n0; --n) {
         size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
-        BH_CUDA(m, launch_pdl(k_adj_stress<N, RHO>, grd, blk, m->stream, r, n, T));
-        ++m->launches;
+        if (ri.ntiles) {
+            BH_CUDA(m, launch_pdl(k_adj_stress<N, RHO, PM_INTERIOR>, dim3(ri.ntiles), blk,
+                                  m->stream, ri, n, T));
+            ++m->launches;
+        }
+        if (rp.ntiles) {
+            BH_CUDA(m, launch_pdl(k_adj_stress<N, RHO, PM_PML>, dim3(rp.ntiles), blk, m->stream,
+                                  rp, n, T));
+            ++m->launches;
+        }
         prof_end(m, e);
         e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
-        BH_CUDA(m, launch_pdl(k_adj_vel<N, RHO>, grd, blk, m->stream, r, n, T));
-        ++m->launches;
+        if (ri.ntiles) {
+            BH_CUDA(m, launch_pdl(k_adj_vel<N, RHO, PM_INTERIOR>, dim3(ri.ntiles), blk,
+                                  m->stream, ri, n, T));
+            ++m->launches;
+        }
+        if (rp.ntiles) {
+            BH_CUDA(m, launch_pdl(k_adj_vel<N, RHO, PM_PML>, dim3(rp.ntiles), blk, m->stream, rp,
+                                  n, T));
+            ++m->launches;
+        }
         prof_end(m, e);
     }
     return BH_OK;
+}
+
+// launches of one half-step of a group in the per-half-step form
+int launches_per_half_step(const bh_model* m, int grp)
+{
+    return (m->group_nint[grp] > 0) + (m->group_ntiles[grp] - m->group_nint[grp] > 0);
 }
 
 // Forward steps n0 .. n1-1 of every shot, group by group.
@@ -689,8 +759,8 @@ bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, lon
     if (n1 <= n0) return BH_OK;
     const int ngroups = (int)m->group_ntiles.size();
     for (int grp = 0; grp < ngroups; ++grp) {
-        *runs += persistent_for(m, grp, false) ? 1 : 2 * (n1 - n0);
-        if (m->nshots == 1) BH_TRY(run_forward_group<1>(m, grp, n0, n1, hist_n0, record));
+        *runs += persistent_for(m, grp, false) ? 1 : 2 * (n1 - n0) * launches_per_half_step(m, grp);
+        if (m->G == 1) BH_TRY(run_forward_group<1>(m, grp, n0, n1, hist_n0, record));
         else BH_TRY(run_forward_group<kGroup>(m, grp, n0, n1, hist_n0, record));
     }
     return BH_OK;
@@ -702,8 +772,8 @@ bh_status run_adjoint(bh_model* m, int n0, int n1, int hist_n0, long long* runs)
     if (n1 <= n0) return BH_OK;
     const int ngroups = (int)m->group_ntiles.size();
     for (int grp = 0; grp < ngroups; ++grp) {
-        *runs += persistent_for(m, grp, true) ? 1 : 2 * (n1 - n0);
-        const bool one = m->nshots == 1;
+        *runs += persistent_for(m, grp, true) ? 1 : 2 * (n1 - n0) * launches_per_half_step(m, grp);
+        const bool one = m->G == 1;
         if (m->adj_rho) {
             if (one) BH_TRY((run_adjoint_group<1, true>(m, grp, n0, n1, hist_n0)));
             else BH_TRY((run_adjoint_group<kGroup, true>(m, grp, n0, n1, hist_n0)));
@@ -925,6 +995,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     m->nshots = nshots;
     m->nrec_max = nrec_max;
     m->P = (nzmax + 31) / 32 * 32;
+    m->G = std::min(nshots, kGroup);
     // a window's own loads reach 3 columns past its end, plus the copy shift
     m->Pw = (nz_global + 8 + 31) / 32 * 32;
     m->stream = (cudaStream_t)stream;
@@ -986,13 +1057,21 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         // the adjoint tiles want 5 blocks of ~42 KB shared memory per SM
+        // the stepping kernels want several blocks of up to ~42 KB shared
+        // memory per SM
         const void* big_smem[] = {
             (const void*)k_adj_persist<1, true>,  (const void*)k_adj_persist<kGroup, true>,
-            (const void*)k_adj_stress<1, true>,   (const void*)k_adj_stress<kGroup, true>,
-            (const void*)k_adj_vel<1, true>,      (const void*)k_adj_vel<kGroup, true>,
             (const void*)k_adj_persist<1, false>, (const void*)k_adj_persist<kGroup, false>,
-            (const void*)k_adj_stress<1, false>,  (const void*)k_adj_stress<kGroup, false>,
-            (const void*)k_adj_vel<1, false>,     (const void*)k_adj_vel<kGroup, false>};
+            (const void*)k_fwd_persist<1>,        (const void*)k_fwd_persist<kGroup>,
+#define BH_STEP_KERNELS(PM)                                                                     \
+    (const void*)k_adj_stress<1, true, PM>, (const void*)k_adj_stress<kGroup, true, PM>,        \
+        (const void*)k_adj_stress<1, false, PM>, (const void*)k_adj_stress<kGroup, false, PM>,  \
+        (const void*)k_adj_vel<1, true, PM>, (const void*)k_adj_vel<kGroup, true, PM>,          \
+        (const void*)k_adj_vel<1, false, PM>, (const void*)k_adj_vel<kGroup, false, PM>,        \
+        (const void*)k_fwd_vel<1, PM>, (const void*)k_fwd_vel<kGroup, PM>,                      \
+        (const void*)k_fwd_stress<1, PM>, (const void*)k_fwd_stress<kGroup, PM>
+            BH_STEP_KERNELS(PM_INTERIOR), BH_STEP_KERNELS(PM_PML)};
+#undef BH_STEP_KERNELS
         for (const void* f : big_smem)
             CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     (int)cudaSharedmemCarveoutMaxShared));
