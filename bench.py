@@ -316,7 +316,7 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
     import torch
     import torch.distributed as dist
 
-    from paper_2005_00281_gb300.bh import model_from_workload
+    from paper_2005_00281_gb300.bh import TUNE_CACHE, model_from_workload
 
     local = dev.index
     stream = torch.cuda.current_stream(dev)
@@ -331,10 +331,14 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
     del true
 
     m = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap, snapshot_precision=prec)
+    tuning = None
     if args.per_step:
         m.set_option("persistent", 0)
     elif args.persistent:
         m.set_option("persistent", 1)
+    elif not args.no_tune:
+        # launch configuration from the autotuner (cached per GPU and shape)
+        tuning = m.tune(steps=32, cache_path=args.tune_cache or TUNE_CACHE)
     start_model = (t(w.vp), t(w.vs), t(w.rho))
     seis = m.empty_seis()
     resid = torch.empty_like(seis)
@@ -493,7 +497,9 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
                                               "snapshot_precision", "history_snapshot_bytes",
                                               "tiles", "persistent_blocks_fwd",
                                               "persistent_blocks_adj")},
-           "gradients": "lambda, mu and rho" if with_rho else "lambda and mu (rho known)"}
+           "gradients": "lambda, mu and rho" if with_rho else "lambda and mu (rho known)",
+           "launch": {"group": m.info("group"), "persistent": m.info("persistent"),
+                      "tuning": tuning}}
     m.close()
     return out
 
@@ -584,6 +590,10 @@ def parse_args(argv=None):
                     help="also compute the density gradient (the iteration does not use it)")
     ap.add_argument("--no-secondary", dest="secondary", action="store_false",
                     help="skip the secondary single-shot (c1) line")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch configuration (no autotuner)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file (default: the one in the package)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-step", action="store_true",
                     help="one kernel launch per half-step for every run")

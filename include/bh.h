@@ -314,6 +314,12 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
  *                     where the device supports cooperative launch): 1 for a
  *                     group whose tiles fit the co-resident blocks (one tile
  *                     per block), else 0.  All give bit-identical results.
+ *   "group"           shots per launch group, 1 .. min(32, nshots) (default
+ *                     the largest): one launch, or one cooperative phase,
+ *                     covers the tiles of a group's shots; groups run one
+ *                     after the other over a run's steps.  Invalidates any
+ *                     stored forward history.  All values give bit-identical
+ *                     results.
  *   "barrier_timeout_ms"  wall-clock limit of one barrier wait (default
  *                     2000).  A wait that runs out sets a device error flag,
  *                     every block returns, and bh_forward /
@@ -330,6 +336,38 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
 bh_status bh_set_option(bh_model* model, const char* key, double value);
 
 /*
+ * Autotuner of the stepping kernels' launch configuration (the paper has no
+ * counterpart).  The candidates are the shot group sizes 1, 2, 4, ... up to
+ * min(32, nshots) (and nshots itself) and the launch forms of the
+ * "persistent" option that differ for that grouping; each is timed twice
+ * over `steps` forward and `steps` adjoint steps of every shot (CUDA events
+ * on the model's stream, the second run kept) and the fastest is applied
+ * (options "group" and "persistent").  With cache_path, a line
+ * "<key> <group> <form> <ms> ..." whose key (GPU name with blanks as '_',
+ * nr, window pitch, nshots, as bh_tune_lookup forms it) matches is applied
+ * without timing; otherwise the timed choice is appended to the file.  The
+ * timed runs overwrite the model's wavefields and history: any stored
+ * forward history is invalidated.  Results of later calls do not depend on
+ * the choice (bit for bit).
+ *   steps       >= 1 (clamped to nt and to the history window)
+ *   cache_path  host path or NULL
+ *   choice      host char[choice_len] or NULL: the choice and the timings
+ * Errors: BH_ERR_INVALID_ARG, BH_ERR_STATE (history window below one
+ *   step), BH_ERR_OOM, BH_ERR_CUDA.
+ */
+bh_status bh_tune(bh_model* model, int steps, const char* cache_path, char* choice,
+                  int choice_len);
+
+/*
+ * The cached launch configuration for a key (host only, no GPU): the last
+ * line of cache_path whose key is gpu_name (blanks as '_') | nr |
+ * window_pitch (the largest window length rounded up to 32) | nshots.
+ * Errors: BH_ERR_INVALID_ARG, BH_ERR_STATE (no such line, or no file).
+ */
+bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr,
+                         int window_pitch, int nshots, int* group, int* form);
+
+/*
  * Read-only facts about a model (the paper has no counterpart):
  * "history_steps" (L), "snapshots" (s), "tail_steps" (steps whose history
  * the forward sweep stores itself), "recompute_steps" (forward steps
@@ -338,7 +376,8 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
  * (stepping-kernel launches of the last bh_forward + bh_adjoint_gradient),
  * "history_snapshot_bytes", "device_bytes", "kernel_launches" (kernels the
  * model has launched since it was created, for counting the launches of a
- * timed region), "state_version" (changes whenever the stored forward
+ * timed region), "group" (shots per launch group), "state_version"
+ * (changes whenever the stored forward
  * history is replaced or invalidated: bh_forward, bh_set_model, bh_update,
  * bh_update_velocity; a caller that keeps a forward run for a later
  * bh_adjoint_gradient can check that it is still the stored one).

@@ -26,7 +26,9 @@ EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
            "bh_profile_enable", "bh_profile_read", "bh_profile_reset",
            "bh_residual_misfit_noalloc", "bh_set_option", "bh_get_info",
            "bh_checkpoint_plan", "bh_velocity_gradient", "bh_update_velocity",
-           "bh_get_density", "bh_plan_history", "bh_starting_model")
+           "bh_get_density", "bh_plan_history", "bh_starting_model", "bh_tune",
+           "bh_tune_lookup")
+TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.txt")
 NOALLOC_MAX_SAMPLES = 33554432
 KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel", "fwd_persist", "adj_persist")
 
@@ -120,6 +122,11 @@ def load_library(path: str | None = None):
     lib.bh_starting_model.argtypes = [ctypes.c_int, ctypes.c_int, dbl, dbl, dbl, vp, vp, vp, vp,
                                       ctypes.c_float, vp, vp, vp]
     lib.bh_starting_model.restype = st
+    lib.bh_tune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int]
+    lib.bh_tune.restype = st
+    lib.bh_tune_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ip, ip]
+    lib.bh_tune_lookup.restype = st
     lib.bh_get_info.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.bh_get_info.restype = st
     lib.bh_residual_misfit_noalloc.argtypes = [vp, vp, vp, ctypes.c_size_t,
@@ -280,6 +287,15 @@ class Model:
         self._rc(self.lib.bh_get_density(self.h, _ptr(rho)))
         return rho
 
+    def tune(self, steps=32, cache_path=TUNE_CACHE):
+        """bh_tune: pick the shot group size and launch form (cached per GPU
+        and workload shape in cache_path, timed on a miss).  Returns the
+        library's description of the choice."""
+        buf = ctypes.create_string_buffer(2048)
+        path = cache_path.encode() if cache_path else None
+        self._rc(self.lib.bh_tune(self.h, int(steps), path, buf, len(buf)))
+        return buf.value.decode()
+
     def set_option(self, key, value):
         """bh_set_option: "persistent", "barrier_timeout_ms", "barrier_extra_arrivals"."""
         self._rc(self.lib.bh_set_option(self.h, key.encode(), float(value)))
@@ -399,3 +415,16 @@ def starting_model(nr, dr, r_wall, r_far, vp_wall, vs_wall, vp_far, vs_far, vp_f
     if rc != BH_OK:
         raise BhError(rc, lib.bh_last_error(None).decode())
     return vp, vs
+
+
+def tune_lookup(cache_path, gpu_name, nr, window_pitch, nshots):
+    """bh_tune_lookup (host only): (group, form) cached for the key, or None."""
+    lib = load_library()
+    g, f = ctypes.c_int(), ctypes.c_int()
+    rc = lib.bh_tune_lookup(cache_path.encode(), gpu_name.encode(), int(nr), int(window_pitch),
+                            int(nshots), ctypes.byref(g), ctypes.byref(f))
+    if rc == 6:
+        return None
+    if rc != BH_OK:
+        raise BhError(rc, lib.bh_last_error(None).decode())
+    return g.value, f.value

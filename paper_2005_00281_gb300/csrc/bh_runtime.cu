@@ -11,6 +11,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -929,6 +931,59 @@ bh_status copy_model_out(bh_model* m, float* vp, float* vs, float* rho)
     return BH_OK;
 }
 
+// ------------------------------------------------------------- autotuner
+//
+// The launch configuration of the stepping kernels: G, the shots of one
+// launch group (one launch, or one cooperative phase, covers the tiles of G
+// shots; small groups keep a group's window state in L2, large ones give a
+// launch more tiles to overlap), and the launch form (2: cooperative when a
+// group's tiles fit the co-resident blocks, else one launch per half-step;
+// 0: always per half-step; 1: always cooperative).  bh_tune times the
+// candidates on the model and keeps the fastest; a cache file maps a key
+// (GPU name, nr, window pitch, shots) to the choice.
+
+std::string tune_key(const char* gpu, int nr, int P, int nshots)
+{
+    std::string name(gpu);
+    for (char& c : name)
+        if (c == ' ' || c == '\t' || c == '|') c = '_';
+    char buf[96];
+    snprintf(buf, sizeof buf, "|nr%d|P%d|shots%d", nr, P, nshots);
+    return name + buf;
+}
+
+// the last line of the cache with this key: "<key> <G> <form> ..."
+bool tune_lookup(const char* path, const std::string& key, int* G, int* form)
+{
+    std::ifstream f(path);
+    if (!f) return false;
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {
+        if (line.empty() || line[0] == '#') continue;
+        std::istringstream is(line);
+        std::string k;
+        int g = 0, p = -1;
+        if (!(is >> k >> g >> p)) continue;
+        if (k != key || g < 1 || g > kGroup || p < 0 || p > 2) continue;
+        *G = g;
+        *form = p;
+        found = true;
+    }
+    return found;
+}
+
+bh_status set_group(bh_model* m, int G)
+{
+    if (G < 1 || G > std::min(kGroup, m->nshots))
+        return fail(m, BH_ERR_INVALID_ARG, "group must be in [1, min(32, nshots)]");
+    if (G == m->G) return BH_OK;
+    m->G = G;
+    m->have_forward = m->have_gradient = false;
+    ++m->state_version;
+    return build_tiles(m);
+}
+
 }  // namespace
 
 // error text of calls that have no model (read with bh_last_error(NULL))
@@ -1361,6 +1416,9 @@ bh_status bh_set_option(bh_model* m, const char* key, double value)
                                      std::min(m->fwd_blocks_g, m->adj_blocks_g)) < 1)
             return fail(m, BH_ERR_UNSUPPORTED, "cooperative launch not available");
         m->persistent = (int)value;
+    } else if (k == "group") {
+        if (value != std::floor(value)) return fail(m, BH_ERR_INVALID_ARG, "group must be an integer");
+        return set_group(m, (int)value);
     } else if (k == "barrier_timeout_ms") {
         if (!(value > 0.0) || value > 600000.0)
             return fail(m, BH_ERR_INVALID_ARG, "barrier_timeout_ms must be in (0, 600000]");
@@ -1395,6 +1453,7 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "snapshot_precision") *value = m->snap_prec;
     else if (k == "kernel_launches") *value = (double)m->launches;
     else if (k == "state_version") *value = (double)m->state_version;
+    else if (k == "group") *value = m->G;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
                      (kFwdPlanes + kAdjPlanes + 2.0 * m->hist_slots) +
@@ -1426,6 +1485,120 @@ bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
     for (size_t k = 0; k < sp.size(); ++k) {
         spine[2 * k] = sp[k].first;
         spine[2 * k + 1] = sp[k].second;
+    }
+    return BH_OK;
+}
+
+bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr, int window_pitch,
+                         int nshots, int* group, int* form)
+{
+    if (!cache_path || !gpu_name || !group || !form)
+        return fail(nullptr, BH_ERR_INVALID_ARG, "bh_tune_lookup: NULL argument");
+    if (!tune_lookup(cache_path, tune_key(gpu_name, nr, window_pitch, nshots), group, form))
+        return fail(nullptr, BH_ERR_STATE, "bh_tune_lookup: no entry for this key");
+    return BH_OK;
+}
+
+bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, int choice_len)
+{
+    if (!m || steps < 1) return fail(m, BH_ERR_INVALID_ARG, "bad argument");
+    int dev = 0;
+    BH_CUDA(m, cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    BH_CUDA(m, cudaGetDeviceProperties(&prop, dev));
+    const std::string key = tune_key(prop.name, m->grid.nr, m->P, m->nshots);
+    const bool coop = std::min(std::min(m->fwd_blocks, m->adj_blocks),
+                               std::min(m->fwd_blocks_g, m->adj_blocks_g)) >= 1;
+    int bestG = m->G, bestForm = m->persistent;
+    double best_ms = -1.0;
+    std::string how = "cached";
+    if (!(cache_path && tune_lookup(cache_path, key, &bestG, &bestForm))) {
+        const int S = std::min(std::min(steps, m->grid.nt), m->hist_slots - 1);
+        if (S < 1) return fail(m, BH_ERR_STATE, "history window too short to time a step");
+        // inputs the timed runs read: a zero wavelet and residual
+        const size_t nbuf = std::max((size_t)m->nshots * m->nrec_max * m->grid.nt,
+                                     (size_t)m->grid.nt);
+        float* zero = nullptr;
+        BH_CUDA(m, dalloc(&zero, nbuf));
+        BH_CUDA(m, cudaMemsetAsync(zero, 0, nbuf * sizeof(float), m->stream));
+        for (int sh = 0; sh < m->nshots; ++sh) {
+            m->h_shots[sh].q.wavelet = zero;
+            m->h_shots[sh].q.seis = zero;
+            m->h_shots[sh].a.resid = zero;
+        }
+        const bool rho_saved = m->adj_rho;
+        m->adj_rho = false;
+        cudaEvent_t e0, e1;
+        BH_CUDA(m, cudaEventCreate(&e0));
+        BH_CUDA(m, cudaEventCreate(&e1));
+        std::vector<int> Gs;
+        for (int g = 1; g <= std::min(kGroup, m->nshots); g *= 2) Gs.push_back(g);
+        if (m->nshots <= kGroup && Gs.back() != m->nshots) Gs.push_back(m->nshots);
+        char line[160];
+        std::string log;
+        bh_status st = BH_OK;
+        for (int g : Gs) {
+            if ((st = set_group(m, g)) != BH_OK) break;
+            // the launch forms that differ for this grouping
+            int fit = 0;
+            const int ng = (int)m->group_ntiles.size();
+            for (int grp = 0; grp < ng; ++grp) {
+                m->persistent = 2;
+                fit += persistent_for(m, grp, false) && persistent_for(m, grp, true);
+            }
+            std::vector<int> forms = {0};
+            if (coop) {
+                forms.push_back(1);
+                if (fit > 0 && fit < ng) forms.push_back(2);
+            }
+            for (int f : forms) {
+                m->persistent = f;
+                float ms = 0.f;
+                long long runs = 0;
+                for (int rep = 0; rep < 2 && st == BH_OK; ++rep) {
+                    cudaEventRecord(e0, m->stream);
+                    if ((st = run_forward(m, 0, S, 0, false, &runs)) != BH_OK) break;
+                    if ((st = run_adjoint(m, 0, S, 0, &runs)) != BH_OK) break;
+                    cudaEventRecord(e1, m->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                        st = fail(m, BH_ERR_CUDA, "bh_tune: event timing failed");
+                }
+                if (st != BH_OK) break;
+                snprintf(line, sizeof line, "%sG=%d form=%d %.3f ms", log.empty() ? "" : "; ", g,
+                         f, ms);
+                log += line;
+                if (best_ms < 0 || ms < best_ms) {
+                    best_ms = ms;
+                    bestG = g;
+                    bestForm = f;
+                }
+            }
+            if (st != BH_OK) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        m->adj_rho = rho_saved;
+        cudaStreamSynchronize(m->stream);
+        cudaFree(zero);
+        if (st != BH_OK) return st;
+        snprintf(line, sizeof line, "timed %d forward + %d adjoint steps per candidate: ", S, S);
+        how = line + log;
+        if (cache_path) {
+            std::ofstream f(cache_path, std::ios::app);
+            if (f) f << key << " " << bestG << " " << bestForm << " " << best_ms << " ms/" << S
+                     << "-step-pair\n";
+        }
+    }
+    BH_TRY(set_group(m, bestG));
+    if (bestForm != 0 && !coop) bestForm = 0;
+    m->persistent = bestForm;
+    m->have_forward = m->have_gradient = false;
+    ++m->state_version;
+    if (choice && choice_len > 0) {
+        std::string txt = "group " + std::to_string(bestG) + ", form " +
+                          std::to_string(bestForm) + " (" + how + ")";
+        snprintf(choice, (size_t)choice_len, "%s", txt.c_str());
     }
     return BH_OK;
 }

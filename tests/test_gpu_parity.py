@@ -452,3 +452,45 @@ def test_starting_model_parity(cuda, orc):
     vp_o, vs_o = O.starting_model(nr, dr, 0.10, 1.10, vpw, vsw, vpf, vsf, 1500.0)
     np.testing.assert_array_equal(vp.cpu().numpy(), vp_o.astype(np.float32))
     np.testing.assert_array_equal(vs.cpu().numpy(), vs_o.astype(np.float32))
+
+
+def test_group_sizes_and_tuner(cuda, tmp_path):
+    """Every shot group size gives the same seismograms and gradients bit for
+    bit; bh_tune times the candidates, applies one, appends its choice to the
+    cache, and a second model of the same shape takes it from the cache."""
+    from paper_2005_00281_gb300.bh import model_from_workload
+    torch = cuda
+    w = tiny_borehole(seed=15, nz=200, nt=120)
+    w.shots = [dict(z_offset=4 * k, nz=52 + 6 * k, src=(0, 12), rec_iz=[24, 30])
+               for k in range(5)]
+    wav = torch.from_numpy(w.wavelet).cuda()
+
+    def run(m):
+        seis = m.forward(wav)
+        resid, J = m.residual_misfit(seis, torch.zeros_like(seis))
+        g = m.adjoint_gradient(resid)
+        torch.cuda.synchronize()
+        return [seis.cpu().numpy()] + [x.cpu().numpy() for x in g]
+
+    m = model_from_workload(w)
+    assert m.info("group") == 5
+    ref = run(m)
+    for G in (1, 2, 3):
+        m.set_option("group", G)
+        assert m.info("group") == G
+        for a, b in zip(ref, run(m)):
+            assert np.array_equal(a, b), G
+    cache = str(tmp_path / "tune.txt")
+    desc = m.tune(steps=8, cache_path=cache)
+    assert desc.startswith("group ") and "timed" in desc, desc
+    for a, b in zip(ref, run(m)):
+        assert np.array_equal(a, b)
+    m.close()
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and lines[0].split()[0].endswith("|nr24|P96|shots5")
+    m2 = model_from_workload(w)
+    desc2 = m2.tune(steps=8, cache_path=cache)
+    assert "cached" in desc2 and desc2.split("(")[0] == desc.split("(")[0]
+    for a, b in zip(ref, run(m2)):
+        assert np.array_equal(a, b)
+    m2.close()
