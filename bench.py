@@ -504,6 +504,48 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
     return out
 
 
+def snapshot_study(w, dev, cap):
+    """One gradient of the start model per checkpoint-snapshot precision
+    (FP32, BF16, FP16) under the same byte cap: relative L2 of the BF16 and
+    FP16 gradients and misfits against the FP32-snapshot run (which equals
+    the store-every-step result bit for bit)."""
+    import numpy as np
+    import torch
+
+    from paper_2005_00281_gb300.bh import model_from_workload
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    true = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap)
+    true.set_model(t(w.vp_true), t(w.vs_true), t(w.rho_true))
+    wav = t(w.wavelet)
+    obs = true.forward(wav).clone()
+    true.close()
+    out, ref = {}, None
+    for name, prec in (("fp32", 0), ("bf16", 1), ("fp16", 2)):
+        m = model_from_workload(w, device=dev, checkpoint_cap_bytes=cap, snapshot_precision=prec)
+        m.tune(steps=32)
+        t0 = time.perf_counter()
+        seis = m.forward(wav)
+        resid, J = m.residual_misfit(seis, obs)
+        g = m.adjoint_gradient(resid, with_rho=False)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        gl, gm = g[0].cpu().numpy(), g[1].cpu().numpy()
+        row = {"J": J, "seconds": sec, "snapshots": m.info("snapshots"),
+               "history_steps": m.info("history_steps"), "tail_steps": m.info("tail_steps"),
+               "recompute_steps": m.info("recompute_steps")}
+        if ref is None:
+            ref = (gl, gm, J)
+        else:
+            rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+            row["g_lam_rel_l2_vs_fp32"] = rel(gl, ref[0])
+            row["g_mu_rel_l2_vs_fp32"] = rel(gm, ref[1])
+            row["J_rel_vs_fp32"] = abs(J - ref[2]) / abs(ref[2])
+        out[name] = row
+        m.close()
+    return out
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -538,6 +580,8 @@ def run_gpu(args, w):
     line["config"]["snapshots"] = snap
     line.update(res)
     line["source_sha"] = source_sha()
+    if args.compare_snapshots:
+        line["snapshot_precision_study"] = snapshot_study(w, dev, int(cap_gb * 1e9))
     if args.secondary and args.config != "c1" and not args.nt and not args.shots:
         from synthetic import PRESETS
         w1 = PRESETS["c1"](seed=rank)
@@ -590,6 +634,9 @@ def parse_args(argv=None):
                     help="also compute the density gradient (the iteration does not use it)")
     ap.add_argument("--no-secondary", dest="secondary", action="store_false",
                     help="skip the secondary single-shot (c1) line")
+    ap.add_argument("--compare-snapshots", action="store_true",
+                    help="also compute one gradient per snapshot precision and report the "
+                         "BF16 / FP16 errors against the FP32-snapshot gradient")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch configuration (no autotuner)")
     ap.add_argument("--tune-cache", default=None,

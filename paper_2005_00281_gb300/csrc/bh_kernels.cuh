@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace bh {
 
 constexpr float kC1 = 1.125f;              // 9/8
@@ -126,16 +128,18 @@ enum {
     TILE_LAST = 2   // the staged columns hold the window's last node row
 };
 
-// Tile class a launch covers: interior tiles only, C-PML tiles only (one
-// launch each per half-step, so the interior code, which holds no layer
-// state, gets its own register budget and occupancy), or either with the
-// flag read per tile (the persistent kernels).
-enum { PM_INTERIOR = 0, PM_PML = 1, PM_ANY = 2 };
+// Tile class: interior tiles or C-PML tiles.  Every tile function is
+// compiled once per class; the per-half-step form launches the classes
+// separately (the interior code, which holds no layer state, gets its own
+// register budget and occupancy), the persistent kernels branch on the
+// tile's flag to the same two instantiations, so both forms run the same
+// arithmetic on every tile and agree bit for bit.
+enum { PM_INTERIOR = 0, PM_PML = 1 };
 
 template <int PM>
-__device__ __forceinline__ bool tile_pml(int flags)
+__device__ __forceinline__ bool tile_pml(int)
 {
-    return PM == PM_ANY ? (flags & TILE_PML) != 0 : PM == PM_PML;
+    return PM == PM_PML;
 }
 
 // Programmatic dependent launch: a kernel may be scheduled while its
@@ -793,8 +797,18 @@ struct __align__(16) AdjVelSmem {
     Prof pf;
 };
 
+// Shared memory of a stress-step launch of interior tiles: no C-PML
+// memories are staged, and the two shear coefficient tiles (x6, x7) hold the
+// same values there, so they share d[4]; 10 tiles instead of 13.
+struct __align__(16) AdjStressIntSmem {
+    Tile d[5];
+    Tile f[5];
+    Prof pf;
+};
+
 // the stress step's launch-invariant tiles (see AdjSmem)
-__device__ __forceinline__ void stage_adj_statics(AdjSmem& sm, const CoefK& C, const float* fcur,
+template <typename SM>
+__device__ __forceinline__ void stage_adj_statics(SM& sm, const CoefK& C, const float* fcur,
                                                   int i0, int j0, const WinK& g)
 {
     const int plane = g.nr * g.P;
@@ -881,19 +895,22 @@ __device__ __forceinline__ void adj_corr_shear(const WinK& g, const AdjK& q, con
 // (the block keeps this tile, so the f tiles are still in shared memory).
 // bar (or null): the block arrives at the grid barrier once the adjoint
 // velocities are stored; the own-node correlations follow the arrival.
-template <bool RHO, int PM>
+template <bool RHO, int PM, typename SM>
 __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
                                                 const AdjK& q, const float* fcur,
                                                 const float* fprev, int i0, int j0, int flags,
                                                 bool statics, bool defer, const BarK* bar,
-                                                unsigned& epoch, AdjSmem& sm)
+                                                unsigned& epoch, SM& sm)
 {
     const float dt = g.dt;
     const Own o = own_of(g, i0, j0);
     const bool pml = tile_pml<PM>(flags);
     const int rr = o.rr, cc = o.cc, i = o.i, c = o.c;
+    // interior tiles (AdjStressIntSmem): no C-PML memory tiles, x6 and x7 share
+    constexpr bool kInt = PM == PM_INTERIOR;
     Tile &T_rr = sm.d[0], &T_tt = sm.d[1], &T_zz = sm.d[2], &T_rz = sm.d[3];
-    Tile &T_p4 = sm.d[4], &T_p5 = sm.d[5], &T_x6 = sm.d[6], &T_x7 = sm.d[7];
+    Tile &T_p4 = sm.d[kInt ? 0 : 4], &T_p5 = sm.d[kInt ? 0 : 5], &T_x6 = sm.d[kInt ? 4 : 6],
+         &T_x7 = sm.d[kInt ? 4 : 7];
     Tile &T_fr = sm.f[0], &T_fz = sm.f[1], &T_x4 = sm.f[2], &T_yt = sm.f[3], &T_x5 = sm.f[4];
     __syncthreads();
     if (!statics) stage_adj_statics(sm, C, fcur, i0, j0, g);
@@ -1084,7 +1101,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
 // next on this tile; its launch-invariant tiles are staged here, after the
 // block's arrival at the grid barrier (bar, or null: no barrier), and after
 // the correlations deferred by the stress step (fprev_b, or null).
-template <bool RHO, int PM, typename SM>
+template <bool RHO, int PM, bool PERSIST, typename SM>
 __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
                                              const AdjK& q, int n, int i0, int j0, int flags,
                                              const float* next_fcur, const float* fprev_b,
@@ -1262,7 +1279,7 @@ __device__ __forceinline__ void adj_vel_tile(const WinK& g, const CoefK& C, cons
         st4(S.trz + c, o.j, g.nz, trz);
     }
     if (bar) grid_arrive(*bar, epoch);
-    if constexpr (PM == PM_ANY) {
+    if constexpr (PERSIST) {
         // fprev_b (or null): v^{n-1/2}; the stress step deferred its density
         // and shear correlations to here (own nodes only: no other block
         // reads them)
@@ -1351,10 +1368,10 @@ __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>
 // statics / prefetch: the block keeps one tile for the whole run, so the
 // velocity step of reverse step n stages the stress step's launch-invariant
 // tiles for step n-1 (AdjSmem)
-template <int N, bool RHO, int PM>
+template <int N, bool RHO, int PM, typename SM>
 __device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>& T, int n,
                                                int t, bool statics, bool defer,
-                                               const BarK* bar, unsigned& epoch, AdjSmem& sm)
+                                               const BarK* bar, unsigned& epoch, SM& sm)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
@@ -1364,7 +1381,7 @@ __device__ __forceinline__ void run_adj_stress(const RunK& r, const ShotTable<N>
                     sm);
 }
 
-template <int N, bool RHO, int PM, typename SM>
+template <int N, bool RHO, int PM, bool PERSIST, typename SM>
 __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
                                             bool prefetch, bool deferred, const BarK* bar,
                                             unsigned& epoch, SM& sm)
@@ -1374,15 +1391,15 @@ __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T
     const int parity = (r.nt - 1 - n) & 1;
     // v^{n-1/2}: fcur of step n-1 (prefetch) and fprev of step n (deferred)
     const float* prev = hist_slot(sh, n - r.hist_n0);
-    adj_vel_tile<RHO, PM>(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w,
+    adj_vel_tile<RHO, PM, PERSIST>(sh.g, sh.C, sh.Sa[parity], sh.a, n, tk.y, tk.z, tk.w,
                       prefetch ? prev : nullptr,
                  deferred ? prev : nullptr, bar, epoch, sm);
 }
 
 // One launch per half-step and tile class: one block per tile.  Interior
 // tiles hold no C-PML state, so their kernels fit more blocks per SM (the
-// forward velocity and adjoint velocity steps 8, the forward stress step 6,
-// against 5 for C-PML tiles).
+// forward velocity and adjoint velocity steps 8, the forward and adjoint
+// stress steps 6, against 5 for C-PML tiles).
 template <int N, int PM>
 __global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
     k_fwd_vel(RunK r, int n, const __grid_constant__ ShotTable<N> T)
@@ -1406,10 +1423,10 @@ __global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 6 : 5)
 }
 
 template <int N, bool RHO, int PM>
-__global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n,
-                                                         const __grid_constant__ ShotTable<N> T)
+__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 6 : 5)
+    k_adj_stress(RunK r, int n, const __grid_constant__ ShotTable<N> T)
 {
-    __shared__ AdjSmem sm;
+    __shared__ typename std::conditional<PM == PM_INTERIOR, AdjStressIntSmem, AdjSmem>::type sm;
     pdl_wait();
     unsigned epoch = 0;
     run_adj_stress<N, RHO, PM>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
@@ -1423,7 +1440,7 @@ __global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
     __shared__ AdjVelSmem<PM == PM_INTERIOR ? 4 : 8> sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_adj_vel<N, RHO, PM>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    run_adj_vel<N, RHO, PM, false>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1437,14 +1454,18 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(RunK r, BarK b,
     const bool idle = (int)blockIdx.x >= r.ntiles;
     for (int n = r.n0; n < r.n1; ++n) {
         // the block's last tile of a phase arrives at the barrier itself
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_fwd_vel<N, PM_ANY>(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr,
-                                   epoch, sm);
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) {
+            const BarK* bb = t + (int)gridDim.x >= r.ntiles ? &b : nullptr;
+            if (r.tiles[t].w & TILE_PML) run_fwd_vel<N, PM_PML>(r, T, n, t, bb, epoch, sm);
+            else run_fwd_vel<N, PM_INTERIOR>(r, T, n, t, bb, epoch, sm);
+        }
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_fwd_stress<N, PM_ANY>(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr,
-                                      epoch, sm);
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) {
+            const BarK* bb = t + (int)gridDim.x >= r.ntiles ? &b : nullptr;
+            if (r.tiles[t].w & TILE_PML) run_fwd_stress<N, PM_PML>(r, T, n, t, bb, epoch, sm);
+            else run_fwd_stress<N, PM_INTERIOR>(r, T, n, t, bb, epoch, sm);
+        }
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
     }
@@ -1461,14 +1482,24 @@ __global__ void __launch_bounds__(kThreads, 5) k_adj_persist(RunK r, BarK b,
     const bool idle = (int)blockIdx.x >= r.ntiles;
     for (int n = r.n1 - 1; n >= r.n0; --n) {
         // the block's last tile of a phase arrives at the barrier itself
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_adj_stress<N, RHO, PM_ANY>(r, T, n, t, one && n < r.n1 - 1, one,
-                           t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) {
+            const BarK* bb = t + (int)gridDim.x >= r.ntiles ? &b : nullptr;
+            const bool st = one && n < r.n1 - 1;
+            if (r.tiles[t].w & TILE_PML)
+                run_adj_stress<N, RHO, PM_PML>(r, T, n, t, st, one, bb, epoch, sm);
+            else
+                run_adj_stress<N, RHO, PM_INTERIOR>(r, T, n, t, st, one, bb, epoch, sm);
+        }
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
-            run_adj_vel<N, RHO, PM_ANY>(r, T, n, t, one && n > r.n0, one,
-                        t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch, sm);
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) {
+            const BarK* bb = t + (int)gridDim.x >= r.ntiles ? &b : nullptr;
+            const bool pf = one && n > r.n0;
+            if (r.tiles[t].w & TILE_PML)
+                run_adj_vel<N, RHO, PM_PML, true>(r, T, n, t, pf, one, bb, epoch, sm);
+            else
+                run_adj_vel<N, RHO, PM_INTERIOR, true>(r, T, n, t, pf, one, bb, epoch, sm);
+        }
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
     }
