@@ -129,11 +129,10 @@ enum {
 };
 
 // Tile class: interior tiles or C-PML tiles.  Every tile function is
-// compiled once per class; the per-half-step form launches the classes
-// separately (the interior code, which holds no layer state, gets its own
-// register budget and occupancy), the persistent kernels branch on the
-// tile's flag to the same two instantiations, so both forms run the same
-// arithmetic on every tile and agree bit for bit.
+// compiled once per class, so interior tiles run code without any layer
+// state (fewer live registers, no layer branches); every kernel branches on
+// the tile's flag to the same two instantiations, so all launch forms run
+// the same arithmetic on every tile and agree bit for bit.
 enum { PM_INTERIOR = 0, PM_PML = 1 };
 
 template <int PM>
@@ -788,24 +787,6 @@ struct __align__(16) AdjSmem {
     Prof pf;
 };
 
-// Shared memory of a velocity-step launch of its own (no stress-step tiles
-// kept): K = 8 tiles (W_r, W_z, the four coefficient tiles, two buoyancies),
-// or K = 4 for interior tiles, whose coefficients equal W.
-template <int K>
-struct __align__(16) AdjVelSmem {
-    Tile d[K];
-    Prof pf;
-};
-
-// Shared memory of a stress-step launch of interior tiles: no C-PML
-// memories are staged, and the two shear coefficient tiles (x6, x7) hold the
-// same values there, so they share d[4]; 10 tiles instead of 13.
-struct __align__(16) AdjStressIntSmem {
-    Tile d[5];
-    Tile f[5];
-    Prof pf;
-};
-
 // the stress step's launch-invariant tiles (see AdjSmem)
 template <typename SM>
 __device__ __forceinline__ void stage_adj_statics(SM& sm, const CoefK& C, const float* fcur,
@@ -906,7 +887,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
     const Own o = own_of(g, i0, j0);
     const bool pml = tile_pml<PM>(flags);
     const int rr = o.rr, cc = o.cc, i = o.i, c = o.c;
-    // interior tiles (AdjStressIntSmem): no C-PML memory tiles, x6 and x7 share
+    // interior tiles stage no C-PML memories, and their x6 and x7 are equal
     constexpr bool kInt = PM == PM_INTERIOR;
     Tile &T_rr = sm.d[0], &T_tt = sm.d[1], &T_zz = sm.d[2], &T_rz = sm.d[3];
     Tile &T_p4 = sm.d[kInt ? 0 : 4], &T_p5 = sm.d[kInt ? 0 : 5], &T_x6 = sm.d[kInt ? 4 : 6],
@@ -1396,51 +1377,64 @@ __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T
                  deferred ? prev : nullptr, bar, epoch, sm);
 }
 
-// One launch per half-step and tile class: one block per tile.  Interior
-// tiles hold no C-PML state, so their kernels fit more blocks per SM (the
-// forward velocity and adjoint velocity steps 8, the forward and adjoint
-// stress steps 6, against 5 for C-PML tiles).
-template <int N, int PM>
-__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
-    k_fwd_vel(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+// One launch per half-step: one block per tile, branching on the tile's
+// class like the persistent kernels (a launch with both classes keeps the
+// block scheduler's overlap of one block's staging with another's compute;
+// separate launches per class measured slower).
+template <int N>
+__global__ void __launch_bounds__(kThreads, 5) k_fwd_vel(RunK r, int n,
+                                                      const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_fwd_vel<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    if (r.tiles[blockIdx.x].w & TILE_PML)
+        run_fwd_vel<N, PM_PML>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    else
+        run_fwd_vel<N, PM_INTERIOR>(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
-template <int N, int PM>
-__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 6 : 5)
-    k_fwd_stress(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+template <int N>
+__global__ void __launch_bounds__(kThreads, 5) k_fwd_stress(RunK r, int n,
+                                                         const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_fwd_stress<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    if (r.tiles[blockIdx.x].w & TILE_PML)
+        run_fwd_stress<N, PM_PML>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    else
+        run_fwd_stress<N, PM_INTERIOR>(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
-template <int N, bool RHO, int PM>
-__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 6 : 5)
-    k_adj_stress(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+template <int N, bool RHO>
+__global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n,
+                                                         const __grid_constant__ ShotTable<N> T)
 {
-    __shared__ typename std::conditional<PM == PM_INTERIOR, AdjStressIntSmem, AdjSmem>::type sm;
+    __shared__ AdjSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_adj_stress<N, RHO, PM>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    if (r.tiles[blockIdx.x].w & TILE_PML)
+        run_adj_stress<N, RHO, PM_PML>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    else
+        run_adj_stress<N, RHO, PM_INTERIOR>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
-template <int N, bool RHO, int PM>
-__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
-    k_adj_vel(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+template <int N, bool RHO>
+__global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
+                                                      const __grid_constant__ ShotTable<N> T)
 {
-    __shared__ AdjVelSmem<PM == PM_INTERIOR ? 4 : 8> sm;
+    __shared__ AdjSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_adj_vel<N, RHO, PM, false>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    if (r.tiles[blockIdx.x].w & TILE_PML)
+        run_adj_vel<N, RHO, PM_PML, false>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    else
+        run_adj_vel<N, RHO, PM_INTERIOR, false>(r, T, n, blockIdx.x, false, false, nullptr, epoch,
+                                                sm);
     pdl_launch_dependents();
 }
 

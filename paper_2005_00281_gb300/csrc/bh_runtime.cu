@@ -70,7 +70,6 @@ struct bh_model {
     int ntiles = 0;
     int G = 1;                  // shots per launch group (1 .. kGroup)
     std::vector<int> group_tile_off, group_ntiles;  // per group of G shots
-    std::vector<int> group_nint;  // interior tiles of each group (listed first)
     // history window and checkpoint schedule
     int L = 0;                  // steps per history window (nt: store every step)
     int nsnap = 0;              // stored snapshot slots (slot 0 is the zero state)
@@ -474,10 +473,9 @@ bh_status setup_shots(bh_model* m)
 }
 
 // Tile table of every shot group of G shots, group after group.  Within a
-// group the tiles are ordered by global column, then row, then shot (tiles
+// group the tiles are ordered by global column, then row, then shot: tiles
 // of several shots at one place of the model run together and share the
-// coefficient copies' lines in L2), interior tiles first (the per-half-step
-// form launches the two classes separately).
+// coefficient copies' lines in L2.
 bh_status build_tiles(bh_model* m)
 {
     const bh_grid_desc& gd = m->grid;
@@ -485,7 +483,6 @@ bh_status build_tiles(bh_model* m)
     std::vector<int4> tiles;
     m->group_tile_off.clear();
     m->group_ntiles.clear();
-    m->group_nint.clear();
     for (int s = 0; s < m->nshots; ++s) {
         const ShotHost& sh = m->shots[s];
         if (s % G == 0) {
@@ -515,9 +512,6 @@ bh_status build_tiles(bh_model* m)
                 if (a.y != b.y) return a.y < b.y;
                 return a.x < b.x;
             });
-            auto mid = std::stable_partition(tiles.begin() + g0, tiles.end(),
-                                             [](const int4& t) { return !(t.w & TILE_PML); });
-            m->group_nint.push_back((int)(mid - (tiles.begin() + g0)));
         }
     }
     m->ntiles = (int)tiles.size();
@@ -662,35 +656,15 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
         prof_end(m, e);
         return check_barrier(m);
     }
-    // interior tiles and C-PML tiles in a launch each
-    RunK ri = r, rp = r;
-    ri.ntiles = m->group_nint[grp];
-    rp.tiles = r.tiles + ri.ntiles;
-    rp.ntiles = r.ntiles - ri.ntiles;
+    const dim3 grd(r.ntiles);
     for (int n = n0; n < n1; ++n) {
         size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
-        if (ri.ntiles) {
-            BH_CUDA(m, launch_pdl(k_fwd_vel<N, PM_INTERIOR>, dim3(ri.ntiles), blk, m->stream, ri,
-                                  n, T));
-            ++m->launches;
-        }
-        if (rp.ntiles) {
-            BH_CUDA(m, launch_pdl(k_fwd_vel<N, PM_PML>, dim3(rp.ntiles), blk, m->stream, rp, n,
-                                  T));
-            ++m->launches;
-        }
+        BH_CUDA(m, launch_pdl(k_fwd_vel<N>, grd, blk, m->stream, r, n, T));
+        ++m->launches;
         prof_end(m, e);
         e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
-        if (ri.ntiles) {
-            BH_CUDA(m, launch_pdl(k_fwd_stress<N, PM_INTERIOR>, dim3(ri.ntiles), blk, m->stream,
-                                  ri, n, T));
-            ++m->launches;
-        }
-        if (rp.ntiles) {
-            BH_CUDA(m, launch_pdl(k_fwd_stress<N, PM_PML>, dim3(rp.ntiles), blk, m->stream, rp,
-                                  n, T));
-            ++m->launches;
-        }
+        BH_CUDA(m, launch_pdl(k_fwd_stress<N>, grd, blk, m->stream, r, n, T));
+        ++m->launches;
         prof_end(m, e);
     }
     return BH_OK;
@@ -716,43 +690,18 @@ bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
         prof_end(m, e);
         return check_barrier(m);
     }
-    RunK ri = r, rp = r;
-    ri.ntiles = m->group_nint[grp];
-    rp.tiles = r.tiles + ri.ntiles;
-    rp.ntiles = r.ntiles - ri.ntiles;
+    const dim3 grd(r.ntiles);
     for (int n = n1 - 1; n >= n0; --n) {
         size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
-        if (ri.ntiles) {
-            BH_CUDA(m, launch_pdl(k_adj_stress<N, RHO, PM_INTERIOR>, dim3(ri.ntiles), blk,
-                                  m->stream, ri, n, T));
-            ++m->launches;
-        }
-        if (rp.ntiles) {
-            BH_CUDA(m, launch_pdl(k_adj_stress<N, RHO, PM_PML>, dim3(rp.ntiles), blk, m->stream,
-                                  rp, n, T));
-            ++m->launches;
-        }
+        BH_CUDA(m, launch_pdl(k_adj_stress<N, RHO>, grd, blk, m->stream, r, n, T));
+        ++m->launches;
         prof_end(m, e);
         e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
-        if (ri.ntiles) {
-            BH_CUDA(m, launch_pdl(k_adj_vel<N, RHO, PM_INTERIOR>, dim3(ri.ntiles), blk,
-                                  m->stream, ri, n, T));
-            ++m->launches;
-        }
-        if (rp.ntiles) {
-            BH_CUDA(m, launch_pdl(k_adj_vel<N, RHO, PM_PML>, dim3(rp.ntiles), blk, m->stream, rp,
-                                  n, T));
-            ++m->launches;
-        }
+        BH_CUDA(m, launch_pdl(k_adj_vel<N, RHO>, grd, blk, m->stream, r, n, T));
+        ++m->launches;
         prof_end(m, e);
     }
     return BH_OK;
-}
-
-// launches of one half-step of a group in the per-half-step form
-int launches_per_half_step(const bh_model* m, int grp)
-{
-    return (m->group_nint[grp] > 0) + (m->group_ntiles[grp] - m->group_nint[grp] > 0);
 }
 
 // Forward steps n0 .. n1-1 of every shot, group by group.
@@ -761,7 +710,7 @@ bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, lon
     if (n1 <= n0) return BH_OK;
     const int ngroups = (int)m->group_ntiles.size();
     for (int grp = 0; grp < ngroups; ++grp) {
-        *runs += persistent_for(m, grp, false) ? 1 : 2 * (n1 - n0) * launches_per_half_step(m, grp);
+        *runs += persistent_for(m, grp, false) ? 1 : 2 * (n1 - n0);
         if (m->G == 1) BH_TRY(run_forward_group<1>(m, grp, n0, n1, hist_n0, record));
         else BH_TRY(run_forward_group<kGroup>(m, grp, n0, n1, hist_n0, record));
     }
@@ -774,7 +723,7 @@ bh_status run_adjoint(bh_model* m, int n0, int n1, int hist_n0, long long* runs)
     if (n1 <= n0) return BH_OK;
     const int ngroups = (int)m->group_ntiles.size();
     for (int grp = 0; grp < ngroups; ++grp) {
-        *runs += persistent_for(m, grp, true) ? 1 : 2 * (n1 - n0) * launches_per_half_step(m, grp);
+        *runs += persistent_for(m, grp, true) ? 1 : 2 * (n1 - n0);
         const bool one = m->G == 1;
         if (m->adj_rho) {
             if (one) BH_TRY((run_adjoint_group<1, true>(m, grp, n0, n1, hist_n0)));
@@ -1118,15 +1067,12 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
             (const void*)k_adj_persist<1, true>,  (const void*)k_adj_persist<kGroup, true>,
             (const void*)k_adj_persist<1, false>, (const void*)k_adj_persist<kGroup, false>,
             (const void*)k_fwd_persist<1>,        (const void*)k_fwd_persist<kGroup>,
-#define BH_STEP_KERNELS(PM)                                                                     \
-    (const void*)k_adj_stress<1, true, PM>, (const void*)k_adj_stress<kGroup, true, PM>,        \
-        (const void*)k_adj_stress<1, false, PM>, (const void*)k_adj_stress<kGroup, false, PM>,  \
-        (const void*)k_adj_vel<1, true, PM>, (const void*)k_adj_vel<kGroup, true, PM>,          \
-        (const void*)k_adj_vel<1, false, PM>, (const void*)k_adj_vel<kGroup, false, PM>,        \
-        (const void*)k_fwd_vel<1, PM>, (const void*)k_fwd_vel<kGroup, PM>,                      \
-        (const void*)k_fwd_stress<1, PM>, (const void*)k_fwd_stress<kGroup, PM>
-            BH_STEP_KERNELS(PM_INTERIOR), BH_STEP_KERNELS(PM_PML)};
-#undef BH_STEP_KERNELS
+            (const void*)k_adj_stress<1, true>,   (const void*)k_adj_stress<kGroup, true>,
+            (const void*)k_adj_stress<1, false>,  (const void*)k_adj_stress<kGroup, false>,
+            (const void*)k_adj_vel<1, true>,      (const void*)k_adj_vel<kGroup, true>,
+            (const void*)k_adj_vel<1, false>,     (const void*)k_adj_vel<kGroup, false>,
+            (const void*)k_fwd_vel<1>,            (const void*)k_fwd_vel<kGroup>,
+            (const void*)k_fwd_stress<1>,         (const void*)k_fwd_stress<kGroup>};
         for (const void* f : big_smem)
             CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     (int)cudaSharedmemCarveoutMaxShared));

@@ -150,3 +150,42 @@ def test_c3_checkpointed_matches_store_all(cuda, prec):
     assert torch.equal(out[0][2], out[1][2])
     for a, b in zip(out[0][1], out[1][1]):
         assert torch.equal(a, b)
+
+
+def test_c4_subbatch_snapshot_precisions_vs_oracle(cuda, orc):
+    """Two shots of the 256-shot run (their full windows, 240 rows) under a
+    byte cap that forces checkpoint snapshots, shortened to 400 steps with
+    the receivers moved near the source: the FP32-snapshot gradient against
+    the FP64 oracle within the parity tolerance, and the BF16 / FP16
+    snapshot gradients with their errors against both printed and bounded."""
+    torch = cuda
+    from paper_2005_00281_gb300.bh import model_from_workload
+
+    w = PRESETS["c4"](seed=0)
+    w.shots = [dict(sh) for sh in w.shots[:2]]
+    w.nt = 400
+    w.wavelet = np.ascontiguousarray(w.wavelet[:400])
+    for sh in w.shots:
+        sh["rec_iz"] = [sh["src"][1] + 20 * k for k in range(1, 5)]
+    obs = np.zeros((2, 4, w.nt))
+    ref = oracle_gradient(w, obs)
+    grads = {}
+    for prec in (0, 1, 2):
+        m = model_from_workload(w, checkpoint_cap_bytes=400_000_000, snapshot_precision=prec)
+        assert m.info("snapshots") >= 1 and m.info("recompute_steps") > 0
+        wav = torch.from_numpy(w.wavelet).cuda()
+        seis = m.forward(wav)
+        resid, J = m.residual_misfit(seis, torch.zeros_like(seis))
+        g = m.adjoint_gradient(resid, with_rho=False)
+        torch.cuda.synchronize()
+        grads[prec] = [x.cpu().numpy() for x in g[:2]]
+        m.close()
+    errs = {}
+    for prec, name in ((0, "fp32"), (1, "bf16"), (2, "fp16")):
+        errs[name] = {k: (rel_l2(grads[prec][q], ref[k]), rel_l2(grads[prec][q], grads[0][q]))
+                      for q, k in enumerate(("g_lam", "g_mu"))}
+    print("c4 two-shot sub-batch, rel L2 (vs oracle, vs FP32 snapshots):",
+          {n: {k: tuple(f"{x:.2e}" for x in v) for k, v in e.items()} for n, e in errs.items()})
+    for k in ("g_lam", "g_mu"):
+        assert errs["fp32"][k][0] <= 1e-4 and errs["fp32"][k][1] == 0.0
+        assert errs["fp16"][k][0] <= 5e-3 and errs["bf16"][k][0] <= 2e-2
