@@ -34,8 +34,15 @@ def _compare(gpu, ref, nshots, w=None):
     for s in range(nshots):
         n = ref["seis"][s].shape[0]
         assert rel_l2(gpu["seis"][s, :n], ref["seis"][s]) <= SEIS_TOL, s
-        for r in range(n):   # every receiver's trace on its own
-            assert rel_l2(gpu["seis"][s, r], ref["seis"][s][r]) <= SEIS_TOL, (s, r)
+        # every receiver's trace on its own; traces the waves have not yet
+        # reached (FP64 noise far below FP32's range) against the largest
+        norms = np.linalg.norm(ref["seis"][s], axis=1)
+        for r in range(n):
+            if norms[r] > 1e-3 * norms.max():
+                assert rel_l2(gpu["seis"][s, r], ref["seis"][s][r]) <= SEIS_TOL, (s, r)
+            else:
+                err = np.linalg.norm(gpu["seis"][s, r] - ref["seis"][s][r])
+                assert err <= SEIS_TOL * norms.max(), (s, r)
     assert abs(gpu["J"] - ref["J"]) <= 1e-5 * ref["J"]
     for k in ("g_lam", "g_mu", "g_rho", "H_lam", "H_mu"):
         e = rel_l2(gpu[k], ref[k])
