@@ -314,6 +314,11 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
  *                     where the device supports cooperative launch): 1 for a
  *                     group whose tiles fit the co-resident blocks (one tile
  *                     per block), else 0.  All give bit-identical results.
+ *   "tile_code"       forward tile code: 0 (default) one code path that reads
+ *                     each tile's C-PML flag, 1 one instantiation per tile
+ *                     class (interior tiles without any layer state).  The
+ *                     two differ in how the compiler contracts multiply-adds
+ *                     (results agree to rounding, not bit for bit).
  *   "group"           shots per launch group, 1 .. min(32, nshots) (default
  *                     the largest): one launch, or one cooperative phase,
  *                     covers the tiles of a group's shots; groups run one
@@ -337,18 +342,20 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
 
 /*
  * Autotuner of the stepping kernels' launch configuration (the paper has no
- * counterpart).  The candidates are the shot group sizes 1, 2, 4, ... up to
- * min(32, nshots) (and nshots itself) and the launch forms of the
- * "persistent" option that differ for that grouping; each is timed twice
+ * counterpart).  The candidates are both forward tile codes ("tile_code"),
+ * the shot group sizes 1, 2, 4, ... up to min(32, nshots) (and nshots
+ * itself) and the launch forms of the "persistent" option that differ for
+ * that grouping; each is timed twice
  * over `steps` forward and `steps` adjoint steps of every shot (CUDA events
  * on the model's stream, the second run kept) and the fastest is applied
- * (options "group" and "persistent").  With cache_path, a line
- * "<key> <group> <form> <ms> ..." whose key (GPU name with blanks as '_',
+ * (options "tile_code", "group" and "persistent").  With cache_path, a line
+ * "<key> <group> <form> <tile code> <ms> ..." whose key (GPU name with blanks as '_',
  * nr, window pitch, nshots, as bh_tune_lookup forms it) matches is applied
  * without timing; otherwise the timed choice is appended to the file.  The
  * timed runs overwrite the model's wavefields and history: any stored
  * forward history is invalidated.  Results of later calls do not depend on
- * the choice (bit for bit).
+ * the group or the form (bit for bit); the tile code changes them at the
+ * rounding level (see "tile_code").
  *   steps       >= 1 (clamped to nt and to the history window)
  *   cache_path  host path or NULL
  *   choice      host char[choice_len] or NULL: the choice and the timings
@@ -359,13 +366,14 @@ bh_status bh_tune(bh_model* model, int steps, const char* cache_path, char* choi
                   int choice_len);
 
 /*
- * The cached launch configuration for a key (host only, no GPU): the last
+ * The cached launch configuration (group, form, tile code) for a key (host
+ * only, no GPU): the last
  * line of cache_path whose key is gpu_name (blanks as '_') | nr |
  * window_pitch (the largest window length rounded up to 32) | nshots.
  * Errors: BH_ERR_INVALID_ARG, BH_ERR_STATE (no such line, or no file).
  */
 bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr,
-                         int window_pitch, int nshots, int* group, int* form);
+                         int window_pitch, int nshots, int* group, int* form, int* tile_code);
 
 /*
  * Read-only facts about a model (the paper has no counterpart):

@@ -128,17 +128,23 @@ enum {
     TILE_LAST = 2   // the staged columns hold the window's last node row
 };
 
-// Tile class: interior tiles or C-PML tiles.  Every tile function is
-// compiled once per class, so interior tiles run code without any layer
-// state (fewer live registers, no layer branches); every kernel branches on
-// the tile's flag to the same two instantiations, so all launch forms run
-// the same arithmetic on every tile and agree bit for bit.
-enum { PM_INTERIOR = 0, PM_PML = 1 };
+// Tile class: interior tiles or C-PML tiles.  A tile function compiled per
+// class runs interior tiles without any layer state (fewer live registers,
+// no layer branches); PM_ANY compiles one code path that reads the tile's
+// flag.  The adjoint kernels always branch on the flag to the per-class
+// instantiations; the forward kernels come in both variants (tile code 0:
+// one path, 1: per class), chosen per model (option "tile_code", the
+// autotuner): the per-class code is faster where the state stays in L2,
+// the single path where it streams from HBM.  Every launch form of one
+// variant runs the same arithmetic on every tile and agrees bit for bit;
+// the two variants differ in the compiler's contraction of multiply-adds
+// (rounding level).
+enum { PM_INTERIOR = 0, PM_PML = 1, PM_ANY = 2 };
 
 template <int PM>
-__device__ __forceinline__ bool tile_pml(int)
+__device__ __forceinline__ bool tile_pml(int flags)
 {
-    return PM == PM_PML;
+    return PM == PM_ANY ? (flags & TILE_PML) != 0 : PM == PM_PML;
 }
 
 // Programmatic dependent launch: a kernel may be scheduled while its
@@ -803,6 +809,42 @@ __device__ __forceinline__ void stage_adj_statics(SM& sm, const CoefK& C, const 
     }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// The tile's own accumulator lines (Kahan pairs, pseudo-Hessian; with RHO
+// also the density pairs and v^{n-1/2}) are read only at the end of the
+// stress step: ask for them in L2 while the tile is staged.  Rows of 32
+// nodes start 128-byte aligned (P and j0 are multiples of 32); only rows
+// inside the window are touched.
+template <bool RHO>
+__device__ __forceinline__ void prefetch_accumulators(const WinK& g, const AdjK& q,
+                                                      const float* fprev, int i0, int j0)
+{
+    constexpr int kLines = RHO ? 14 : 9;  // 128-byte lines per tile row
+    for (int k = tid_of(); k < kTR * kLines; k += kThreads) {
+        const int row = k / kLines, l = k - row * kLines;
+        const int i = i0 + row;
+        if (i >= g.nr) continue;
+        const size_t c = (size_t)i * g.P + j0;
+        const char* p;
+        switch (l) {
+        case 0: case 1: p = (const char*)(q.G_lam + c) + 128 * l; break;
+        case 2: case 3: p = (const char*)(q.G_munn + c) + 128 * (l - 2); break;
+        case 4: case 5: p = (const char*)(q.G_murz + c) + 128 * (l - 4); break;
+        case 6: p = (const char*)(q.H_lam + c); break;
+        case 7: p = (const char*)(q.H_munn + c); break;
+        case 8: p = (const char*)(q.H_murz + c); break;
+        case 9: case 10: p = (const char*)(q.G_br + c) + 128 * (l - 9); break;
+        case 11: case 12: p = (const char*)(q.G_bz + c) + 128 * (l - 11); break;
+        default: p = (const char*)(fprev + c); break;
+        }
+        prefetch_l2(p);
+    }
+}
+
 __device__ __forceinline__ float2 kahan_step(float2 s, float x)
 {
     float y = __fsub_rn(x, s.y);
@@ -909,6 +951,7 @@ __device__ __forceinline__ void adj_stress_tile(const WinK& g, const CoefK& C, c
         }
     }
     if (pml) stage_prof(sm.pf, C, g, i0, j0);
+    prefetch_accumulators<RHO>(g, q, fprev, i0, j0);
     // own adjoint velocities, in flight together with the copies
     V4 av_z{}, av_r{};
     float ivh = 0.f, ivm = 0.f;
@@ -1346,6 +1389,26 @@ __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>
                         epoch, sm);
 }
 
+// forward tiles of either code variant (V 0: one path, 1: per tile class)
+template <int N, int V>
+__device__ __forceinline__ void run_fwd_vel_v(const RunK& r, const ShotTable<N>& T, int n, int t,
+                                              const BarK* bar, unsigned& epoch, FwdSmem& sm)
+{
+    if (V == 0) run_fwd_vel<N, PM_ANY>(r, T, n, t, bar, epoch, sm);
+    else if (r.tiles[t].w & TILE_PML) run_fwd_vel<N, PM_PML>(r, T, n, t, bar, epoch, sm);
+    else run_fwd_vel<N, PM_INTERIOR>(r, T, n, t, bar, epoch, sm);
+}
+
+template <int N, int V>
+__device__ __forceinline__ void run_fwd_stress_v(const RunK& r, const ShotTable<N>& T, int n,
+                                                 int t, const BarK* bar, unsigned& epoch,
+                                                 FwdSmem& sm)
+{
+    if (V == 0) run_fwd_stress<N, PM_ANY>(r, T, n, t, bar, epoch, sm);
+    else if (r.tiles[t].w & TILE_PML) run_fwd_stress<N, PM_PML>(r, T, n, t, bar, epoch, sm);
+    else run_fwd_stress<N, PM_INTERIOR>(r, T, n, t, bar, epoch, sm);
+}
+
 // statics / prefetch: the block keeps one tile for the whole run, so the
 // velocity step of reverse step n stages the stress step's launch-invariant
 // tiles for step n-1 (AdjSmem)
@@ -1381,31 +1444,25 @@ __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T
 // class like the persistent kernels (a launch with both classes keeps the
 // block scheduler's overlap of one block's staging with another's compute;
 // separate launches per class measured slower).
-template <int N>
+template <int N, int V>
 __global__ void __launch_bounds__(kThreads, 5) k_fwd_vel(RunK r, int n,
                                                       const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    if (r.tiles[blockIdx.x].w & TILE_PML)
-        run_fwd_vel<N, PM_PML>(r, T, n, blockIdx.x, nullptr, epoch, sm);
-    else
-        run_fwd_vel<N, PM_INTERIOR>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    run_fwd_vel_v<N, V>(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
-template <int N>
+template <int N, int V>
 __global__ void __launch_bounds__(kThreads, 5) k_fwd_stress(RunK r, int n,
                                                          const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    if (r.tiles[blockIdx.x].w & TILE_PML)
-        run_fwd_stress<N, PM_PML>(r, T, n, blockIdx.x, nullptr, epoch, sm);
-    else
-        run_fwd_stress<N, PM_INTERIOR>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    run_fwd_stress_v<N, V>(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 
@@ -1439,7 +1496,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
 }
 
 // every step n0 .. n1-1 of every shot of the table in one cooperative launch
-template <int N>
+template <int N, int V>
 __global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(RunK r, BarK b,
                                                              const __grid_constant__ ShotTable<N> T)
 {
@@ -1448,18 +1505,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_persist(RunK r, BarK b,
     const bool idle = (int)blockIdx.x >= r.ntiles;
     for (int n = r.n0; n < r.n1; ++n) {
         // the block's last tile of a phase arrives at the barrier itself
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) {
-            const BarK* bb = t + (int)gridDim.x >= r.ntiles ? &b : nullptr;
-            if (r.tiles[t].w & TILE_PML) run_fwd_vel<N, PM_PML>(r, T, n, t, bb, epoch, sm);
-            else run_fwd_vel<N, PM_INTERIOR>(r, T, n, t, bb, epoch, sm);
-        }
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
+            run_fwd_vel_v<N, V>(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr, epoch,
+                                sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
-        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x) {
-            const BarK* bb = t + (int)gridDim.x >= r.ntiles ? &b : nullptr;
-            if (r.tiles[t].w & TILE_PML) run_fwd_stress<N, PM_PML>(r, T, n, t, bb, epoch, sm);
-            else run_fwd_stress<N, PM_INTERIOR>(r, T, n, t, bb, epoch, sm);
-        }
+        for (int t = blockIdx.x; t < r.ntiles; t += gridDim.x)
+            run_fwd_stress_v<N, V>(r, T, n, t, t + (int)gridDim.x >= r.ntiles ? &b : nullptr,
+                                   epoch, sm);
         if (idle) grid_arrive(b, epoch);
         if (!grid_wait(b, epoch)) return;
     }

@@ -92,6 +92,7 @@ struct bh_model {
     // 1: one cooperative launch per run; 0: one launch per half-step; 2 (auto):
     // cooperative when every block of a shot group has at most one tile
     int persistent = 2;
+    int tile_code = 0;          // forward tile code variant (0: one path, 1: per tile class)
     int fwd_blocks = 0, adj_blocks = 0;       // co-resident blocks, 1-shot kernels
     int fwd_blocks_g = 0, adj_blocks_g = 0;   // same, kGroup-shot kernels
     // the adjoint kernels without the density correlation (no g_rho asked)
@@ -637,8 +638,8 @@ RunK make_run(const bh_model* m, int grp, int n0, int n1, int hist_n0, bool reco
     return r;
 }
 
-// Forward steps n0 .. n1-1 of the shots of one group.
-template <int N>
+// Forward steps n0 .. n1-1 of the shots of one group, tile code variant V.
+template <int N, int V>
 bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, bool record)
 {
     RunK r = make_run(m, grp, n0, n1, hist_n0, record);
@@ -650,7 +651,7 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
         BH_CUDA(m, cudaMemsetAsync(m->d_bar, 0, 4 * sizeof(unsigned), m->stream));
         void* args[] = {&r, &b, &T};
         size_t e = prof_begin(m, BH_KERNEL_FWD_PERSIST, 0);
-        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_fwd_persist<N>, dim3(blocks), blk,
+        BH_CUDA(m, cudaLaunchCooperativeKernel((const void*)k_fwd_persist<N, V>, dim3(blocks), blk,
                                                args, 0, m->stream));
         ++m->launches;
         prof_end(m, e);
@@ -659,11 +660,11 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
     const dim3 grd(r.ntiles);
     for (int n = n0; n < n1; ++n) {
         size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
-        BH_CUDA(m, launch_pdl(k_fwd_vel<N>, grd, blk, m->stream, r, n, T));
+        BH_CUDA(m, launch_pdl(k_fwd_vel<N, V>, grd, blk, m->stream, r, n, T));
         ++m->launches;
         prof_end(m, e);
         e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
-        BH_CUDA(m, launch_pdl(k_fwd_stress<N>, grd, blk, m->stream, r, n, T));
+        BH_CUDA(m, launch_pdl(k_fwd_stress<N, V>, grd, blk, m->stream, r, n, T));
         ++m->launches;
         prof_end(m, e);
     }
@@ -711,8 +712,14 @@ bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, lon
     const int ngroups = (int)m->group_ntiles.size();
     for (int grp = 0; grp < ngroups; ++grp) {
         *runs += persistent_for(m, grp, false) ? 1 : 2 * (n1 - n0);
-        if (m->G == 1) BH_TRY(run_forward_group<1>(m, grp, n0, n1, hist_n0, record));
-        else BH_TRY(run_forward_group<kGroup>(m, grp, n0, n1, hist_n0, record));
+        const bool one = m->G == 1;
+        if (m->tile_code == 0) {
+            if (one) BH_TRY((run_forward_group<1, 0>(m, grp, n0, n1, hist_n0, record)));
+            else BH_TRY((run_forward_group<kGroup, 0>(m, grp, n0, n1, hist_n0, record)));
+        } else {
+            if (one) BH_TRY((run_forward_group<1, 1>(m, grp, n0, n1, hist_n0, record)));
+            else BH_TRY((run_forward_group<kGroup, 1>(m, grp, n0, n1, hist_n0, record)));
+        }
     }
     return BH_OK;
 }
@@ -885,11 +892,12 @@ bh_status copy_model_out(bh_model* m, float* vp, float* vs, float* rho)
 // The launch configuration of the stepping kernels: G, the shots of one
 // launch group (one launch, or one cooperative phase, covers the tiles of G
 // shots; small groups keep a group's window state in L2, large ones give a
-// launch more tiles to overlap), and the launch form (2: cooperative when a
+// launch more tiles to overlap), the launch form (2: cooperative when a
 // group's tiles fit the co-resident blocks, else one launch per half-step;
-// 0: always per half-step; 1: always cooperative).  bh_tune times the
-// candidates on the model and keeps the fastest; a cache file maps a key
-// (GPU name, nr, window pitch, shots) to the choice.
+// 0: always per half-step; 1: always cooperative), and the forward tile
+// code variant.  bh_tune times the candidates on the model and keeps the
+// fastest; a cache file maps a key (GPU name, nr, window pitch, shots) to
+// the choice.
 
 std::string tune_key(const char* gpu, int nr, int P, int nshots)
 {
@@ -901,8 +909,8 @@ std::string tune_key(const char* gpu, int nr, int P, int nshots)
     return name + buf;
 }
 
-// the last line of the cache with this key: "<key> <G> <form> ..."
-bool tune_lookup(const char* path, const std::string& key, int* G, int* form)
+// the last line of the cache with this key: "<key> <G> <form> <tile code> ..."
+bool tune_lookup(const char* path, const std::string& key, int* G, int* form, int* code)
 {
     std::ifstream f(path);
     if (!f) return false;
@@ -912,11 +920,12 @@ bool tune_lookup(const char* path, const std::string& key, int* G, int* form)
         if (line.empty() || line[0] == '#') continue;
         std::istringstream is(line);
         std::string k;
-        int g = 0, p = -1;
-        if (!(is >> k >> g >> p)) continue;
-        if (k != key || g < 1 || g > kGroup || p < 0 || p > 2) continue;
+        int g = 0, p = -1, v = -1;
+        if (!(is >> k >> g >> p >> v)) continue;
+        if (k != key || g < 1 || g > kGroup || p < 0 || p > 2 || v < 0 || v > 1) continue;
         *G = g;
         *form = p;
+        *code = v;
         found = true;
     }
     return found;
@@ -1066,18 +1075,25 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         const void* big_smem[] = {
             (const void*)k_adj_persist<1, true>,  (const void*)k_adj_persist<kGroup, true>,
             (const void*)k_adj_persist<1, false>, (const void*)k_adj_persist<kGroup, false>,
-            (const void*)k_fwd_persist<1>,        (const void*)k_fwd_persist<kGroup>,
+            (const void*)k_fwd_persist<1, 0>,     (const void*)k_fwd_persist<kGroup, 0>,
+            (const void*)k_fwd_persist<1, 1>,     (const void*)k_fwd_persist<kGroup, 1>,
             (const void*)k_adj_stress<1, true>,   (const void*)k_adj_stress<kGroup, true>,
             (const void*)k_adj_stress<1, false>,  (const void*)k_adj_stress<kGroup, false>,
             (const void*)k_adj_vel<1, true>,      (const void*)k_adj_vel<kGroup, true>,
             (const void*)k_adj_vel<1, false>,     (const void*)k_adj_vel<kGroup, false>,
-            (const void*)k_fwd_vel<1>,            (const void*)k_fwd_vel<kGroup>,
-            (const void*)k_fwd_stress<1>,         (const void*)k_fwd_stress<kGroup>};
+            (const void*)k_fwd_vel<1, 0>,         (const void*)k_fwd_vel<kGroup, 0>,
+            (const void*)k_fwd_vel<1, 1>,         (const void*)k_fwd_vel<kGroup, 1>,
+            (const void*)k_fwd_stress<1, 0>,      (const void*)k_fwd_stress<kGroup, 0>,
+            (const void*)k_fwd_stress<1, 1>,      (const void*)k_fwd_stress<kGroup, 1>};
         for (const void* f : big_smem)
             CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     (int)cudaSharedmemCarveoutMaxShared));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<1>, kThreads, 0));
+        // both forward variants are bounded to 5 blocks of 128 threads; the
+        // smaller of their counts serves both
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<1, 0>, kThreads, 0));
         m->fwd_blocks = nb * sms;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<1, 1>, kThreads, 0));
+        m->fwd_blocks = std::min(m->fwd_blocks, nb * sms);
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<1, true>, kThreads, 0));
         m->adj_blocks = nb * sms;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<1, false>, kThreads, 0));
@@ -1085,8 +1101,12 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<kGroup, false>, kThreads,
                                                          0));
         m->adj_blocks_g_nr = nb * sms;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<kGroup>, kThreads, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<kGroup, 0>, kThreads,
+                                                         0));
         m->fwd_blocks_g = nb * sms;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<kGroup, 1>, kThreads,
+                                                         0));
+        m->fwd_blocks_g = std::min(m->fwd_blocks_g, nb * sms);
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_persist<kGroup, true>, kThreads,
                                                          0));
         m->adj_blocks_g = nb * sms;
@@ -1362,6 +1382,10 @@ bh_status bh_set_option(bh_model* m, const char* key, double value)
                                      std::min(m->fwd_blocks_g, m->adj_blocks_g)) < 1)
             return fail(m, BH_ERR_UNSUPPORTED, "cooperative launch not available");
         m->persistent = (int)value;
+    } else if (k == "tile_code") {
+        if (value != 0.0 && value != 1.0)
+            return fail(m, BH_ERR_INVALID_ARG, "tile_code must be 0 or 1");
+        m->tile_code = (int)value;
     } else if (k == "group") {
         if (value != std::floor(value)) return fail(m, BH_ERR_INVALID_ARG, "group must be an integer");
         return set_group(m, (int)value);
@@ -1400,6 +1424,7 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "kernel_launches") *value = (double)m->launches;
     else if (k == "state_version") *value = (double)m->state_version;
     else if (k == "group") *value = m->G;
+    else if (k == "tile_code") *value = m->tile_code;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
                      (kFwdPlanes + kAdjPlanes + 2.0 * m->hist_slots) +
@@ -1436,11 +1461,12 @@ bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
 }
 
 bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr, int window_pitch,
-                         int nshots, int* group, int* form)
+                         int nshots, int* group, int* form, int* tile_code)
 {
-    if (!cache_path || !gpu_name || !group || !form)
+    if (!cache_path || !gpu_name || !group || !form || !tile_code)
         return fail(nullptr, BH_ERR_INVALID_ARG, "bh_tune_lookup: NULL argument");
-    if (!tune_lookup(cache_path, tune_key(gpu_name, nr, window_pitch, nshots), group, form))
+    if (!tune_lookup(cache_path, tune_key(gpu_name, nr, window_pitch, nshots), group, form,
+                     tile_code))
         return fail(nullptr, BH_ERR_STATE, "bh_tune_lookup: no entry for this key");
     return BH_OK;
 }
@@ -1455,10 +1481,10 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
     const std::string key = tune_key(prop.name, m->grid.nr, m->P, m->nshots);
     const bool coop = std::min(std::min(m->fwd_blocks, m->adj_blocks),
                                std::min(m->fwd_blocks_g, m->adj_blocks_g)) >= 1;
-    int bestG = m->G, bestForm = m->persistent;
+    int bestG = m->G, bestForm = m->persistent, bestCode = m->tile_code;
     double best_ms = -1.0;
     std::string how = "cached";
-    if (!(cache_path && tune_lookup(cache_path, key, &bestG, &bestForm))) {
+    if (!(cache_path && tune_lookup(cache_path, key, &bestG, &bestForm, &bestCode))) {
         const int S = std::min(std::min(steps, m->grid.nt), m->hist_slots - 1);
         if (S < 1) return fail(m, BH_ERR_STATE, "history window too short to time a step");
         // inputs the timed runs read: a zero wavelet and residual
@@ -1483,7 +1509,9 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
         char line[160];
         std::string log;
         bh_status st = BH_OK;
+        for (int code = 0; code <= 1 && st == BH_OK; ++code)
         for (int g : Gs) {
+            m->tile_code = code;
             if ((st = set_group(m, g)) != BH_OK) break;
             // the launch forms that differ for this grouping
             int fit = 0;
@@ -1511,13 +1539,14 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
                         st = fail(m, BH_ERR_CUDA, "bh_tune: event timing failed");
                 }
                 if (st != BH_OK) break;
-                snprintf(line, sizeof line, "%sG=%d form=%d %.3f ms", log.empty() ? "" : "; ", g,
-                         f, ms);
+                snprintf(line, sizeof line, "%scode=%d G=%d form=%d %.3f ms",
+                         log.empty() ? "" : "; ", code, g, f, ms);
                 log += line;
                 if (best_ms < 0 || ms < best_ms) {
                     best_ms = ms;
                     bestG = g;
                     bestForm = f;
+                    bestCode = code;
                 }
             }
             if (st != BH_OK) break;
@@ -1532,18 +1561,20 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
         how = line + log;
         if (cache_path) {
             std::ofstream f(cache_path, std::ios::app);
-            if (f) f << key << " " << bestG << " " << bestForm << " " << best_ms << " ms/" << S
-                     << "-step-pair\n";
+            if (f) f << key << " " << bestG << " " << bestForm << " " << bestCode << " " << best_ms
+                     << " ms/" << S << "-step-pair\n";
         }
     }
     BH_TRY(set_group(m, bestG));
     if (bestForm != 0 && !coop) bestForm = 0;
     m->persistent = bestForm;
+    m->tile_code = bestCode;
     m->have_forward = m->have_gradient = false;
     ++m->state_version;
     if (choice && choice_len > 0) {
         std::string txt = "group " + std::to_string(bestG) + ", form " +
-                          std::to_string(bestForm) + " (" + how + ")";
+                          std::to_string(bestForm) + ", tile code " + std::to_string(bestCode) +
+                          " (" + how + ")";
         snprintf(choice, (size_t)choice_len, "%s", txt.c_str());
     }
     return BH_OK;

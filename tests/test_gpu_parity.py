@@ -487,17 +487,25 @@ def test_group_sizes_and_tuner(cuda, tmp_path):
         assert m.info("group") == G
         for a, b in zip(ref, run(m)):
             assert np.array_equal(a, b), G
+    # the other forward tile code agrees to rounding
+    m.set_option("tile_code", 1 - m.info("tile_code"))
+    for a, b in zip(ref, run(m)):
+        assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b))
     cache = str(tmp_path / "tune.txt")
     desc = m.tune(steps=8, cache_path=cache)
     assert desc.startswith("group ") and "timed" in desc, desc
-    for a, b in zip(ref, run(m)):
-        assert np.array_equal(a, b)
+    code = m.info("tile_code")
+    m.close()
+    m = model_from_workload(w)
+    m.set_option("tile_code", code)
+    ref = run(m)
     m.close()
     lines = open(cache).read().splitlines()
     assert len(lines) == 1 and lines[0].split()[0].endswith("|nr24|P96|shots5")
     m2 = model_from_workload(w)
     desc2 = m2.tune(steps=8, cache_path=cache)
     assert "cached" in desc2 and desc2.split("(")[0] == desc.split("(")[0]
+    assert m2.info("tile_code") == code
     for a, b in zip(ref, run(m2)):
         assert np.array_equal(a, b)
     m2.close()
