@@ -338,7 +338,10 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
         m.set_option("persistent", 1)
     elif not args.no_tune:
         # launch configuration from the autotuner (cached per GPU and shape)
-        tuning = m.tune(steps=32, cache_path=args.tune_cache or TUNE_CACHE)
+        tuning = m.tune(steps=64, cache_path=args.tune_cache or TUNE_CACHE)
+    for kv in args.opt or []:
+        key, val = kv.split("=")
+        m.set_option(key, float(val))
     start_model = (t(w.vp), t(w.vs), t(w.rho))
     seis = m.empty_seis()
     resid = torch.empty_like(seis)
@@ -499,7 +502,8 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
                                               "persistent_blocks_adj")},
            "gradients": "lambda, mu and rho" if with_rho else "lambda and mu (rho known)",
            "launch": {"group": m.info("group"), "persistent": m.info("persistent"),
-                      "tuning": tuning}}
+                      "tile_code": m.info("tile_code"),
+                      "prefetch_ahead": m.info("prefetch_ahead"), "tuning": tuning}}
     m.close()
     return out
 
@@ -639,6 +643,8 @@ def parse_args(argv=None):
                          "BF16 / FP16 errors against the FP32-snapshot gradient")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch configuration (no autotuner)")
+    ap.add_argument("--opt", action="append",
+                    help="library option key=value set after the autotuner (repeatable)")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file (default: the one in the package)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
