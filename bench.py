@@ -502,8 +502,7 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
                                               "persistent_blocks_adj")},
            "gradients": "lambda, mu and rho" if with_rho else "lambda and mu (rho known)",
            "launch": {"group": m.info("group"), "persistent": m.info("persistent"),
-                      "tile_code": m.info("tile_code"),
-                      "prefetch_ahead": m.info("prefetch_ahead"), "tuning": tuning}}
+                      "tile_code": m.info("tile_code"), "tuning": tuning}}
     m.close()
     return out
 

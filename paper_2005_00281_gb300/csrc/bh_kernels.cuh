@@ -1354,51 +1354,7 @@ struct RunK {
     int hist_n0;        // history slot 0 holds v^{hist_n0 - 1/2}; -1: no history
     int record;         // forward: write the seismograms
     int nt;             // steps of the whole run (adjoint memory bank parity)
-    int ahead;          // one launch per half-step: tile t prefetches tile t + ahead (0: off)
 };
-
-// ----------------------------------------- prefetch of a later tile (L2)
-//
-// In the one-launch-per-half-step form the block scheduler starts blocks in
-// tile order as slots free up, so the tile that starts about one resident
-// set after this one is t + (co-resident blocks).  While this tile is
-// staged, the block asks for that tile's wavefield rows in L2 with bulk
-// prefetches; when it starts, its staging then comes from L2 instead of
-// HBM.  A prefetch moves no data into the SM and changes no result.
-
-__device__ __forceinline__ void prefetch_bulk_l2(const void* p, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Planes of one tile: the first ns over the staged region (rows i0-2 ..
-// i0+17, columns j0-4 .. j0+35), the others over the tile's own nodes
-// (rows i0 .. i0+15, columns j0 .. j0+31); rows and columns clipped to the
-// window, each row one prefetch of a 16-byte multiple that starts 16-byte
-// aligned (j0 - 4 is a multiple of 4) and ends inside the row pitch P.
-template <int NP>
-__device__ __forceinline__ void prefetch_tile(const float* const (&pl)[NP], int np, int ns,
-                                              const WinK& g, int i0, int j0)
-{
-    const int total = ns * kSR + (np - ns) * kTR;
-    for (int k = tid_of(); k < total; k += kThreads) {
-        int q, row, c0, c1;
-        if (k < ns * kSR) {
-            q = k / kSR;
-            row = i0 - kH + (k - q * kSR);
-            c0 = max(0, j0 - 4);
-            c1 = min(g.nz, j0 + kTZ + 4);
-        } else {
-            const int kk = k - ns * kSR;
-            q = ns + kk / kTR;
-            row = i0 + (kk - (q - ns) * kTR);
-            c0 = j0;
-            c1 = min(g.nz, j0 + kTZ);
-        }
-        if (row < 0 || row >= g.nr || c1 <= c0) continue;
-        prefetch_bulk_l2(pl[q] + (size_t)row * g.P + c0, ((unsigned)(c1 - c0) * 4u + 15u) & ~15u);
-    }
-}
 
 __device__ __forceinline__ float* hist_slot(const ShotK& sh, int k)
 {
@@ -1409,67 +1365,6 @@ template <int N>
 __device__ __forceinline__ const ShotK& shot_of(const ShotTable<N>& T, int4 tk)
 {
     return T.s[N == 1 ? 0 : tk.x];
-}
-
-// the planes the next tiles' staging reads, per half-step kind
-template <int N>
-__device__ __forceinline__ void prefetch_fwd_vel(const RunK& r, const ShotTable<N>& T, int t)
-{
-    if (r.ahead <= 0 || t + r.ahead >= r.ntiles) return;
-    const int4 tk = r.tiles[t + r.ahead];
-    const StateK& S = shot_of(T, tk).Sf;
-    const float* const pl[10] = {S.trr, S.ttt, S.tzz, S.trz, S.vr, S.vz,
-                                 S.psi[0], S.psi[1], S.psi[2], S.psi[3]};
-    prefetch_tile(pl, (tk.w & TILE_PML) ? 10 : 6, 4, shot_of(T, tk).g, tk.y, tk.z);
-}
-
-template <int N>
-__device__ __forceinline__ void prefetch_fwd_stress(const RunK& r, const ShotTable<N>& T, int t)
-{
-    if (r.ahead <= 0 || t + r.ahead >= r.ntiles) return;
-    const int4 tk = r.tiles[t + r.ahead];
-    const StateK& S = shot_of(T, tk).Sf;
-    const float* const pl[10] = {S.vr, S.vz, S.trr, S.ttt, S.tzz, S.trz,
-                                 S.psi[4], S.psi[5], S.psi[6], S.psi[7]};
-    prefetch_tile(pl, (tk.w & TILE_PML) ? 10 : 6, 2, shot_of(T, tk).g, tk.y, tk.z);
-}
-
-template <int N>
-__device__ __forceinline__ void prefetch_adj_stress(const RunK& r, const ShotTable<N>& T, int n,
-                                                    int t)
-{
-    if (r.ahead <= 0 || t + r.ahead >= r.ntiles) return;
-    const int4 tk = r.tiles[t + r.ahead];
-    const ShotK& sh = shot_of(T, tk);
-    const StateK& S = sh.Sa[(r.nt - 1 - n) & 1];
-    const float* fcur = hist_slot(sh, n - r.hist_n0 + 1);
-    const int plane = sh.g.nr * sh.g.P;
-    const float* const pl[12] = {S.trr, S.ttt, S.tzz, S.trz, fcur, fcur + plane,
-                                 S.psi[4], S.psi[5], S.psi[6], S.psi[7], S.vr, S.vz};
-    if (tk.w & TILE_PML) {
-        prefetch_tile(pl, 12, 10, sh.g, tk.y, tk.z);
-    } else {
-        const float* const pi[8] = {S.trr, S.ttt, S.tzz, S.trz, fcur, fcur + plane, S.vr, S.vz};
-        prefetch_tile(pi, 8, 6, sh.g, tk.y, tk.z);
-    }
-}
-
-template <int N>
-__device__ __forceinline__ void prefetch_adj_vel(const RunK& r, const ShotTable<N>& T, int n,
-                                                 int t)
-{
-    if (r.ahead <= 0 || t + r.ahead >= r.ntiles) return;
-    const int4 tk = r.tiles[t + r.ahead];
-    const ShotK& sh = shot_of(T, tk);
-    const StateK& S = sh.Sa[(r.nt - 1 - n) & 1];
-    const float* const pl[10] = {S.vr, S.vz, S.psi[0], S.psi[1], S.psi[2], S.psi[3],
-                                 S.trr, S.ttt, S.tzz, S.trz};
-    if (tk.w & TILE_PML) {
-        prefetch_tile(pl, 10, 6, sh.g, tk.y, tk.z);
-    } else {
-        const float* const pi[6] = {S.vr, S.vz, S.trr, S.ttt, S.tzz, S.trz};
-        prefetch_tile(pi, 6, 2, sh.g, tk.y, tk.z);
-    }
 }
 
 template <int N, int PM>
@@ -1556,7 +1451,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_vel(RunK r, int n,
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    prefetch_fwd_vel(r, T, blockIdx.x);
     run_fwd_vel_v<N, V>(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
@@ -1568,7 +1462,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_fwd_stress(RunK r, int n,
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    prefetch_fwd_stress(r, T, blockIdx.x);
     run_fwd_stress_v<N, V>(r, T, n, blockIdx.x, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
@@ -1580,7 +1473,6 @@ __global__ void __launch_bounds__(kThreads) k_adj_stress(RunK r, int n,
     __shared__ AdjSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    prefetch_adj_stress(r, T, n, blockIdx.x);
     if (r.tiles[blockIdx.x].w & TILE_PML)
         run_adj_stress<N, RHO, PM_PML>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     else
@@ -1595,7 +1487,6 @@ __global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
     __shared__ AdjSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    prefetch_adj_vel(r, T, n, blockIdx.x);
     if (r.tiles[blockIdx.x].w & TILE_PML)
         run_adj_vel<N, RHO, PM_PML, false>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     else

@@ -93,7 +93,6 @@ struct bh_model {
     // cooperative when every block of a shot group has at most one tile
     int persistent = 2;
     int tile_code = 0;          // forward tile code variant (0: one path, 1: per tile class)
-    int ahead = -1;             // per-half-step prefetch distance in tiles (-1: resident blocks)
     int fwd_blocks = 0, adj_blocks = 0;       // co-resident blocks, 1-shot kernels
     int fwd_blocks_g = 0, adj_blocks_g = 0;   // same, kGroup-shot kernels
     // the adjoint kernels without the density correlation (no g_rho asked)
@@ -636,8 +635,6 @@ RunK make_run(const bh_model* m, int grp, int n0, int n1, int hist_n0, bool reco
     r.hist_n0 = hist_n0;
     r.record = record ? 1 : 0;
     r.nt = m->grid.nt;
-    // the tile that starts about one resident set of blocks later
-    r.ahead = m->ahead >= 0 ? m->ahead : m->fwd_blocks;
     return r;
 }
 
@@ -1073,21 +1070,17 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         // the adjoint tiles want 5 blocks of ~42 KB shared memory per SM
-        // the stepping kernels want several blocks of up to ~42 KB shared
-        // memory per SM
+        // the adjoint kernels want 5 blocks of ~42 KB shared memory per SM;
+        // the forward kernels (14 KB per block) keep the default split, which
+        // leaves L1 room for their read-only coefficient loads (the maximum
+        // shared-memory carveout made them 9-23 % slower)
         const void* big_smem[] = {
             (const void*)k_adj_persist<1, true>,  (const void*)k_adj_persist<kGroup, true>,
             (const void*)k_adj_persist<1, false>, (const void*)k_adj_persist<kGroup, false>,
-            (const void*)k_fwd_persist<1, 0>,     (const void*)k_fwd_persist<kGroup, 0>,
-            (const void*)k_fwd_persist<1, 1>,     (const void*)k_fwd_persist<kGroup, 1>,
             (const void*)k_adj_stress<1, true>,   (const void*)k_adj_stress<kGroup, true>,
             (const void*)k_adj_stress<1, false>,  (const void*)k_adj_stress<kGroup, false>,
             (const void*)k_adj_vel<1, true>,      (const void*)k_adj_vel<kGroup, true>,
-            (const void*)k_adj_vel<1, false>,     (const void*)k_adj_vel<kGroup, false>,
-            (const void*)k_fwd_vel<1, 0>,         (const void*)k_fwd_vel<kGroup, 0>,
-            (const void*)k_fwd_vel<1, 1>,         (const void*)k_fwd_vel<kGroup, 1>,
-            (const void*)k_fwd_stress<1, 0>,      (const void*)k_fwd_stress<kGroup, 0>,
-            (const void*)k_fwd_stress<1, 1>,      (const void*)k_fwd_stress<kGroup, 1>};
+            (const void*)k_adj_vel<1, false>,     (const void*)k_adj_vel<kGroup, false>};
         for (const void* f : big_smem)
             CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     (int)cudaSharedmemCarveoutMaxShared));
@@ -1385,10 +1378,6 @@ bh_status bh_set_option(bh_model* m, const char* key, double value)
                                      std::min(m->fwd_blocks_g, m->adj_blocks_g)) < 1)
             return fail(m, BH_ERR_UNSUPPORTED, "cooperative launch not available");
         m->persistent = (int)value;
-    } else if (k == "prefetch_ahead") {
-        if (value < -1.0 || value > 1e6 || value != std::floor(value))
-            return fail(m, BH_ERR_INVALID_ARG, "prefetch_ahead must be an integer >= -1");
-        m->ahead = (int)value;
     } else if (k == "tile_code") {
         if (value != 0.0 && value != 1.0)
             return fail(m, BH_ERR_INVALID_ARG, "tile_code must be 0 or 1");
@@ -1432,7 +1421,6 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "state_version") *value = (double)m->state_version;
     else if (k == "group") *value = m->G;
     else if (k == "tile_code") *value = m->tile_code;
-    else if (k == "prefetch_ahead") *value = m->ahead >= 0 ? m->ahead : m->fwd_blocks;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
                      (kFwdPlanes + kAdjPlanes + 2.0 * m->hist_slots) +
