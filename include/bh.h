@@ -319,6 +319,12 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
  *                     class (interior tiles without any layer state).  The
  *                     two differ in how the compiler contracts multiply-adds
  *                     (results agree to rounding, not bit for bit).
+ *   "split"           0 (default) one launch per half-step covers every tile
+ *                     of a shot group; 1: one launch per half-step and tile
+ *                     class (interior tiles, C-PML tiles), so that interior
+ *                     tiles run more blocks per SM; applies to the adjoint
+ *                     and, with "tile_code" 1, to the forward (bit for bit
+ *                     the same results).
  *   "group"           shots per launch group, 1 .. min(32, nshots) (default
  *                     the largest): one launch, or one cooperative phase,
  *                     covers the tiles of a group's shots; groups run one
@@ -345,11 +351,13 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
  * counterpart).  The candidates are both forward tile codes ("tile_code"),
  * the shot group sizes 1, 2, 4, ... up to min(32, nshots) (and nshots
  * itself) and the launch forms of the "persistent" option that differ for
- * that grouping; each is timed twice
- * over `steps` forward and `steps` adjoint steps of every shot (CUDA events
- * on the model's stream, the second run kept) and the fastest is applied
- * (options "tile_code", "group" and "persistent").  With cache_path, a line
- * "<key> <group> <form> <tile code> <ms> ..." whose key (GPU name with blanks as '_',
+ * that grouping (and, for one launch per half-step, "split" 0 and 1); each
+ * is timed four times over `steps` forward and `steps` adjoint steps of
+ * every shot (CUDA events on the model's stream, the best of the last three
+ * kept) and the fastest is applied (options "tile_code", "group",
+ * "persistent" and "split").  With cache_path, a line
+ * "<key> <group> <form> <tile code> <split> <ms> ..." whose key (GPU name
+ * with blanks as '_',
  * nr, window pitch, nshots, as bh_tune_lookup forms it) matches is applied
  * without timing; otherwise the timed choice is appended to the file.  The
  * timed runs overwrite the model's wavefields and history: any stored
@@ -366,14 +374,15 @@ bh_status bh_tune(bh_model* model, int steps, const char* cache_path, char* choi
                   int choice_len);
 
 /*
- * The cached launch configuration (group, form, tile code) for a key (host
+ * The cached launch configuration (group, form, tile code, split) for a key (host
  * only, no GPU): the last
  * line of cache_path whose key is gpu_name (blanks as '_') | nr |
  * window_pitch (the largest window length rounded up to 32) | nshots.
  * Errors: BH_ERR_INVALID_ARG, BH_ERR_STATE (no such line, or no file).
  */
 bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr,
-                         int window_pitch, int nshots, int* group, int* form, int* tile_code);
+                         int window_pitch, int nshots, int* group, int* form, int* tile_code,
+                         int* split);
 
 /*
  * Read-only facts about a model (the paper has no counterpart):

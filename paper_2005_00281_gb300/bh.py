@@ -125,7 +125,7 @@ def load_library(path: str | None = None):
     lib.bh_tune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int]
     lib.bh_tune.restype = st
     lib.bh_tune_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
-                                   ctypes.c_int, ip, ip, ip]
+                                   ctypes.c_int, ip, ip, ip, ip]
     lib.bh_tune_lookup.restype = st
     lib.bh_get_info.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.bh_get_info.restype = st
@@ -297,8 +297,8 @@ class Model:
         return buf.value.decode()
 
     def set_option(self, key, value):
-        """bh_set_option: "persistent", "group", "tile_code", "barrier_timeout_ms",
-        "barrier_extra_arrivals"."""
+        """bh_set_option: "persistent", "group", "tile_code", "split",
+        "barrier_timeout_ms", "barrier_extra_arrivals"."""
         self._rc(self.lib.bh_set_option(self.h, key.encode(), float(value)))
 
     def info(self, key):
@@ -419,14 +419,15 @@ def starting_model(nr, dr, r_wall, r_far, vp_wall, vs_wall, vp_far, vs_far, vp_f
 
 
 def tune_lookup(cache_path, gpu_name, nr, window_pitch, nshots):
-    """bh_tune_lookup (host only): (group, form, tile code) cached for the
-    key, or None."""
+    """bh_tune_lookup (host only): (group, form, tile code, split) cached
+    for the key, or None."""
     lib = load_library()
-    g, f, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    g, f, v, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     rc = lib.bh_tune_lookup(cache_path.encode(), gpu_name.encode(), int(nr), int(window_pitch),
-                            int(nshots), ctypes.byref(g), ctypes.byref(f), ctypes.byref(v))
+                            int(nshots), ctypes.byref(g), ctypes.byref(f), ctypes.byref(v),
+                            ctypes.byref(sp))
     if rc == 6:
         return None
     if rc != BH_OK:
         raise BhError(rc, lib.bh_last_error(None).decode())
-    return g.value, f.value, v.value
+    return g.value, f.value, v.value, sp.value

@@ -793,6 +793,23 @@ struct __align__(16) AdjSmem {
     Prof pf;
 };
 
+// Shared memory of launches that cover one tile class only.  Interior
+// tiles stage no C-PML memories and their shear coefficient tiles x6, x7
+// hold equal values, so the stress step needs 10 tiles (6 blocks per SM
+// instead of 5); the velocity step keeps W, the coefficients (equal to W on
+// interior tiles) and the buoyancies: 8 tiles, or 4 on interior tiles.
+struct __align__(16) AdjStressIntSmem {
+    Tile d[5];
+    Tile f[5];
+    Prof pf;
+};
+
+template <int K>
+struct __align__(16) AdjVelSmem {
+    Tile d[K];
+    Prof pf;
+};
+
 // the stress step's launch-invariant tiles (see AdjSmem)
 template <typename SM>
 __device__ __forceinline__ void stage_adj_statics(SM& sm, const CoefK& C, const float* fcur,
@@ -1492,6 +1509,54 @@ __global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
     else
         run_adj_vel<N, RHO, PM_INTERIOR, false>(r, T, n, blockIdx.x, false, false, nullptr, epoch,
                                                 sm);
+    pdl_launch_dependents();
+}
+
+// One launch per half-step and tile class (option "split"): a launch of
+// interior tiles carries no C-PML state and fits more blocks per SM (the
+// velocity steps 8, the stress steps 6, C-PML tiles 5); it runs the same
+// per-class tile code as the kernels above with the forward tile code 1.
+template <int N, int PM>
+__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
+    k_fwd_vel_c(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+{
+    __shared__ FwdSmem sm;
+    pdl_wait();
+    unsigned epoch = 0;
+    run_fwd_vel<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    pdl_launch_dependents();
+}
+
+template <int N, int PM>
+__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 6 : 5)
+    k_fwd_stress_c(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+{
+    __shared__ FwdSmem sm;
+    pdl_wait();
+    unsigned epoch = 0;
+    run_fwd_stress<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    pdl_launch_dependents();
+}
+
+template <int N, bool RHO, int PM>
+__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 6 : 5)
+    k_adj_stress_c(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+{
+    __shared__ typename std::conditional<PM == PM_INTERIOR, AdjStressIntSmem, AdjSmem>::type sm;
+    pdl_wait();
+    unsigned epoch = 0;
+    run_adj_stress<N, RHO, PM>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    pdl_launch_dependents();
+}
+
+template <int N, bool RHO, int PM>
+__global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
+    k_adj_vel_c(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+{
+    __shared__ AdjVelSmem<PM == PM_INTERIOR ? 4 : 8> sm;
+    pdl_wait();
+    unsigned epoch = 0;
+    run_adj_vel<N, RHO, PM, false>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
     pdl_launch_dependents();
 }
 

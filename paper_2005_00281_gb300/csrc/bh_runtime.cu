@@ -93,6 +93,11 @@ struct bh_model {
     // cooperative when every block of a shot group has at most one tile
     int persistent = 2;
     int tile_code = 0;          // forward tile code variant (0: one path, 1: per tile class)
+    // one launch per half-step and tile class (per-class code only: the
+    // adjoint, and the forward with tile code 1)
+    int split = 0;
+    int4* d_tiles_cls = nullptr;          // every group's tiles, interior first
+    std::vector<int> group_nint;          // interior tiles of each group
     int fwd_blocks = 0, adj_blocks = 0;       // co-resident blocks, 1-shot kernels
     int fwd_blocks_g = 0, adj_blocks_g = 0;   // same, kGroup-shot kernels
     // the adjoint kernels without the density correlation (no g_rho asked)
@@ -162,7 +167,7 @@ void free_model(bh_model* m)
                     m->d_vp,    m->d_vs,
                     m->d_mask,  m->d_colcov, m->d_rprof, m->d_zprof,  m->d_recmap, m->d_fwd,
                     m->d_adj,   m->d_hist,   m->d_snap,  m->d_snap_max, m->d_tiles,  m->d_Hg,
-                    m->d_scal,  m->d_bar,    m->d_wcoef, m->d_part};
+                    m->d_scal,  m->d_bar,    m->d_wcoef, m->d_part, m->d_tiles_cls};
     for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     delete m;
@@ -516,10 +521,24 @@ bh_status build_tiles(bh_model* m)
         }
     }
     m->ntiles = (int)tiles.size();
+    // the same tables with every group's interior tiles first, for launches
+    // of one tile class
+    std::vector<int4> cls(tiles);
+    m->group_nint.clear();
+    for (size_t grp = 0; grp < m->group_tile_off.size(); ++grp) {
+        auto b = cls.begin() + m->group_tile_off[grp];
+        auto mid = std::stable_partition(b, b + m->group_ntiles[grp],
+                                         [](const int4& t) { return !(t.w & TILE_PML); });
+        m->group_nint.push_back((int)(mid - b));
+    }
     cudaFree(m->d_tiles);
-    m->d_tiles = nullptr;
+    cudaFree(m->d_tiles_cls);
+    m->d_tiles = m->d_tiles_cls = nullptr;
     BH_CUDA(m, dalloc(&m->d_tiles, tiles.size()));
+    BH_CUDA(m, dalloc(&m->d_tiles_cls, cls.size()));
     BH_CUDA(m, cudaMemcpyAsync(m->d_tiles, tiles.data(), tiles.size() * sizeof(int4),
+                               cudaMemcpyHostToDevice, m->stream));
+    BH_CUDA(m, cudaMemcpyAsync(m->d_tiles_cls, cls.data(), cls.size() * sizeof(int4),
                                cudaMemcpyHostToDevice, m->stream));
     BH_CUDA(m, cudaStreamSynchronize(m->stream));
     return BH_OK;
@@ -625,6 +644,17 @@ bh_status check_barrier(bh_model* m)
     return BH_OK;
 }
 
+// the interior and C-PML runs of a group for launches of one tile class
+void class_runs(const bh_model* m, int grp, const RunK& r, RunK* ri, RunK* rp)
+{
+    *ri = r;
+    *rp = r;
+    ri->tiles = m->d_tiles_cls + m->group_tile_off[grp];
+    ri->ntiles = m->group_nint[grp];
+    rp->tiles = ri->tiles + ri->ntiles;
+    rp->ntiles = r.ntiles - ri->ntiles;
+}
+
 RunK make_run(const bh_model* m, int grp, int n0, int n1, int hist_n0, bool record)
 {
     RunK r;
@@ -658,6 +688,37 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
         return check_barrier(m);
     }
     const dim3 grd(r.ntiles);
+    if (V == 1 && m->split) {
+        RunK ri, rp;
+        class_runs(m, grp, r, &ri, &rp);
+        for (int n = n0; n < n1; ++n) {
+            size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
+            if (ri.ntiles) {
+                BH_CUDA(m, launch_pdl(k_fwd_vel_c<N, PM_INTERIOR>, dim3(ri.ntiles), blk,
+                                      m->stream, ri, n, T));
+                ++m->launches;
+            }
+            if (rp.ntiles) {
+                BH_CUDA(m, launch_pdl(k_fwd_vel_c<N, PM_PML>, dim3(rp.ntiles), blk, m->stream,
+                                      rp, n, T));
+                ++m->launches;
+            }
+            prof_end(m, e);
+            e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
+            if (ri.ntiles) {
+                BH_CUDA(m, launch_pdl(k_fwd_stress_c<N, PM_INTERIOR>, dim3(ri.ntiles), blk,
+                                      m->stream, ri, n, T));
+                ++m->launches;
+            }
+            if (rp.ntiles) {
+                BH_CUDA(m, launch_pdl(k_fwd_stress_c<N, PM_PML>, dim3(rp.ntiles), blk,
+                                      m->stream, rp, n, T));
+                ++m->launches;
+            }
+            prof_end(m, e);
+        }
+        return BH_OK;
+    }
     for (int n = n0; n < n1; ++n) {
         size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
         BH_CUDA(m, launch_pdl(k_fwd_vel<N, V>, grd, blk, m->stream, r, n, T));
@@ -692,6 +753,37 @@ bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
         return check_barrier(m);
     }
     const dim3 grd(r.ntiles);
+    if (m->split) {
+        RunK ri, rp;
+        class_runs(m, grp, r, &ri, &rp);
+        for (int n = n1 - 1; n >= n0; --n) {
+            size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
+            if (ri.ntiles) {
+                BH_CUDA(m, launch_pdl(k_adj_stress_c<N, RHO, PM_INTERIOR>, dim3(ri.ntiles), blk,
+                                      m->stream, ri, n, T));
+                ++m->launches;
+            }
+            if (rp.ntiles) {
+                BH_CUDA(m, launch_pdl(k_adj_stress_c<N, RHO, PM_PML>, dim3(rp.ntiles), blk,
+                                      m->stream, rp, n, T));
+                ++m->launches;
+            }
+            prof_end(m, e);
+            e = prof_begin(m, BH_KERNEL_ADJ_VEL, n);
+            if (ri.ntiles) {
+                BH_CUDA(m, launch_pdl(k_adj_vel_c<N, RHO, PM_INTERIOR>, dim3(ri.ntiles), blk,
+                                      m->stream, ri, n, T));
+                ++m->launches;
+            }
+            if (rp.ntiles) {
+                BH_CUDA(m, launch_pdl(k_adj_vel_c<N, RHO, PM_PML>, dim3(rp.ntiles), blk,
+                                      m->stream, rp, n, T));
+                ++m->launches;
+            }
+            prof_end(m, e);
+        }
+        return BH_OK;
+    }
     for (int n = n1 - 1; n >= n0; --n) {
         size_t e = prof_begin(m, BH_KERNEL_ADJ_STRESS, n);
         BH_CUDA(m, launch_pdl(k_adj_stress<N, RHO>, grd, blk, m->stream, r, n, T));
@@ -705,13 +797,21 @@ bh_status run_adjoint_group(bh_model* m, int grp, int n0, int n1, int hist_n0)
     return BH_OK;
 }
 
+// launches per half-step of a group split by tile class
+int class_launches(const bh_model* m, int grp)
+{
+    return (m->group_nint[grp] > 0) + (m->group_ntiles[grp] - m->group_nint[grp] > 0);
+}
+
 // Forward steps n0 .. n1-1 of every shot, group by group.
 bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, long long* runs)
 {
     if (n1 <= n0) return BH_OK;
     const int ngroups = (int)m->group_ntiles.size();
     for (int grp = 0; grp < ngroups; ++grp) {
-        *runs += persistent_for(m, grp, false) ? 1 : 2 * (n1 - n0);
+        *runs += persistent_for(m, grp, false)
+                     ? 1
+                     : 2 * (n1 - n0) * ((m->split && m->tile_code == 1) ? class_launches(m, grp) : 1);
         const bool one = m->G == 1;
         if (m->tile_code == 0) {
             if (one) BH_TRY((run_forward_group<1, 0>(m, grp, n0, n1, hist_n0, record)));
@@ -730,7 +830,9 @@ bh_status run_adjoint(bh_model* m, int n0, int n1, int hist_n0, long long* runs)
     if (n1 <= n0) return BH_OK;
     const int ngroups = (int)m->group_ntiles.size();
     for (int grp = 0; grp < ngroups; ++grp) {
-        *runs += persistent_for(m, grp, true) ? 1 : 2 * (n1 - n0);
+        *runs += persistent_for(m, grp, true)
+                     ? 1
+                     : 2 * (n1 - n0) * (m->split ? class_launches(m, grp) : 1);
         const bool one = m->G == 1;
         if (m->adj_rho) {
             if (one) BH_TRY((run_adjoint_group<1, true>(m, grp, n0, n1, hist_n0)));
@@ -909,8 +1011,9 @@ std::string tune_key(const char* gpu, int nr, int P, int nshots)
     return name + buf;
 }
 
-// the last line of the cache with this key: "<key> <G> <form> <tile code> ..."
-bool tune_lookup(const char* path, const std::string& key, int* G, int* form, int* code)
+// the last line of the cache with this key: "<key> <G> <form> <tile code> <split> ..."
+bool tune_lookup(const char* path, const std::string& key, int* G, int* form, int* code,
+                 int* split)
 {
     std::ifstream f(path);
     if (!f) return false;
@@ -920,12 +1023,15 @@ bool tune_lookup(const char* path, const std::string& key, int* G, int* form, in
         if (line.empty() || line[0] == '#') continue;
         std::istringstream is(line);
         std::string k;
-        int g = 0, p = -1, v = -1;
-        if (!(is >> k >> g >> p >> v)) continue;
-        if (k != key || g < 1 || g > kGroup || p < 0 || p > 2 || v < 0 || v > 1) continue;
+        int g = 0, p = -1, v = -1, sp = -1;
+        if (!(is >> k >> g >> p >> v >> sp)) continue;
+        if (k != key || g < 1 || g > kGroup || p < 0 || p > 2 || v < 0 || v > 1 || sp < 0 ||
+            sp > 1)
+            continue;
         *G = g;
         *form = p;
         *code = v;
+        *split = sp;
         found = true;
     }
     return found;
@@ -1080,7 +1186,15 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
             (const void*)k_adj_stress<1, true>,   (const void*)k_adj_stress<kGroup, true>,
             (const void*)k_adj_stress<1, false>,  (const void*)k_adj_stress<kGroup, false>,
             (const void*)k_adj_vel<1, true>,      (const void*)k_adj_vel<kGroup, true>,
-            (const void*)k_adj_vel<1, false>,     (const void*)k_adj_vel<kGroup, false>};
+            (const void*)k_adj_vel<1, false>,     (const void*)k_adj_vel<kGroup, false>,
+#define BH_CLASS_KERNELS(PM)                                                                    \
+    (const void*)k_adj_stress_c<1, true, PM>, (const void*)k_adj_stress_c<kGroup, true, PM>,    \
+        (const void*)k_adj_stress_c<1, false, PM>,                                              \
+        (const void*)k_adj_stress_c<kGroup, false, PM>, (const void*)k_adj_vel_c<1, true, PM>,  \
+        (const void*)k_adj_vel_c<kGroup, true, PM>, (const void*)k_adj_vel_c<1, false, PM>,     \
+        (const void*)k_adj_vel_c<kGroup, false, PM>
+            BH_CLASS_KERNELS(PM_INTERIOR), BH_CLASS_KERNELS(PM_PML)};
+#undef BH_CLASS_KERNELS
         for (const void* f : big_smem)
             CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     (int)cudaSharedmemCarveoutMaxShared));
@@ -1378,6 +1492,9 @@ bh_status bh_set_option(bh_model* m, const char* key, double value)
                                      std::min(m->fwd_blocks_g, m->adj_blocks_g)) < 1)
             return fail(m, BH_ERR_UNSUPPORTED, "cooperative launch not available");
         m->persistent = (int)value;
+    } else if (k == "split") {
+        if (value != 0.0 && value != 1.0) return fail(m, BH_ERR_INVALID_ARG, "split must be 0 or 1");
+        m->split = (int)value;
     } else if (k == "tile_code") {
         if (value != 0.0 && value != 1.0)
             return fail(m, BH_ERR_INVALID_ARG, "tile_code must be 0 or 1");
@@ -1421,6 +1538,7 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "state_version") *value = (double)m->state_version;
     else if (k == "group") *value = m->G;
     else if (k == "tile_code") *value = m->tile_code;
+    else if (k == "split") *value = m->split;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
                      (kFwdPlanes + kAdjPlanes + 2.0 * m->hist_slots) +
@@ -1457,12 +1575,12 @@ bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
 }
 
 bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr, int window_pitch,
-                         int nshots, int* group, int* form, int* tile_code)
+                         int nshots, int* group, int* form, int* tile_code, int* split)
 {
-    if (!cache_path || !gpu_name || !group || !form || !tile_code)
+    if (!cache_path || !gpu_name || !group || !form || !tile_code || !split)
         return fail(nullptr, BH_ERR_INVALID_ARG, "bh_tune_lookup: NULL argument");
     if (!tune_lookup(cache_path, tune_key(gpu_name, nr, window_pitch, nshots), group, form,
-                     tile_code))
+                     tile_code, split))
         return fail(nullptr, BH_ERR_STATE, "bh_tune_lookup: no entry for this key");
     return BH_OK;
 }
@@ -1477,10 +1595,10 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
     const std::string key = tune_key(prop.name, m->grid.nr, m->P, m->nshots);
     const bool coop = std::min(std::min(m->fwd_blocks, m->adj_blocks),
                                std::min(m->fwd_blocks_g, m->adj_blocks_g)) >= 1;
-    int bestG = m->G, bestForm = m->persistent, bestCode = m->tile_code;
+    int bestG = m->G, bestForm = m->persistent, bestCode = m->tile_code, bestSplit = m->split;
     double best_ms = -1.0;
     std::string how = "cached";
-    if (!(cache_path && tune_lookup(cache_path, key, &bestG, &bestForm, &bestCode))) {
+    if (!(cache_path && tune_lookup(cache_path, key, &bestG, &bestForm, &bestCode, &bestSplit))) {
         const int S = std::min(std::min(steps, m->grid.nt), m->hist_slots - 1);
         if (S < 1) return fail(m, BH_ERR_STATE, "history window too short to time a step");
         // inputs the timed runs read: a zero wavelet and residual
@@ -1521,8 +1639,10 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
                 forms.push_back(1);
                 if (fit > 0 && fit < ng) forms.push_back(2);
             }
-            for (int f : forms) {
+            for (int f : forms)
+            for (int sp = 0; sp <= (f == 0 ? 1 : 0); ++sp) {
                 m->persistent = f;
+                m->split = sp;
                 float ms = 0.f;
                 long long runs = 0;
                 // the best of three runs after a warm-up
@@ -1539,14 +1659,15 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
                 }
                 ms = best_rep;
                 if (st != BH_OK) break;
-                snprintf(line, sizeof line, "%scode=%d G=%d form=%d %.3f ms",
-                         log.empty() ? "" : "; ", code, g, f, ms);
+                snprintf(line, sizeof line, "%scode=%d G=%d form=%d split=%d %.3f ms",
+                         log.empty() ? "" : "; ", code, g, f, sp, ms);
                 log += line;
                 if (best_ms < 0 || ms < best_ms) {
                     best_ms = ms;
                     bestG = g;
                     bestForm = f;
                     bestCode = code;
+                    bestSplit = sp;
                 }
             }
             if (st != BH_OK) break;
@@ -1561,20 +1682,21 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
         how = line + log;
         if (cache_path) {
             std::ofstream f(cache_path, std::ios::app);
-            if (f) f << key << " " << bestG << " " << bestForm << " " << bestCode << " " << best_ms
-                     << " ms/" << S << "-step-pair\n";
+            if (f) f << key << " " << bestG << " " << bestForm << " " << bestCode << " "
+                     << bestSplit << " " << best_ms << " ms/" << S << "-step-pair\n";
         }
     }
     BH_TRY(set_group(m, bestG));
     if (bestForm != 0 && !coop) bestForm = 0;
     m->persistent = bestForm;
     m->tile_code = bestCode;
+    m->split = bestSplit;
     m->have_forward = m->have_gradient = false;
     ++m->state_version;
     if (choice && choice_len > 0) {
         std::string txt = "group " + std::to_string(bestG) + ", form " +
                           std::to_string(bestForm) + ", tile code " + std::to_string(bestCode) +
-                          " (" + how + ")";
+                          ", split " + std::to_string(bestSplit) + " (" + how + ")";
         snprintf(choice, (size_t)choice_len, "%s", txt.c_str());
     }
     return BH_OK;

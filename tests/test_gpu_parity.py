@@ -487,6 +487,16 @@ def test_group_sizes_and_tuner(cuda, tmp_path):
         assert m.info("group") == G
         for a, b in zip(ref, run(m)):
             assert np.array_equal(a, b), G
+    # one launch per tile class: the same per-class code, bit for bit
+    m.set_option("persistent", 0)
+    m.set_option("tile_code", 1)
+    ref1 = run(m)
+    m.set_option("split", 1)
+    for a, b in zip(ref1, run(m)):
+        assert np.array_equal(a, b)
+    m.set_option("split", 0)
+    m.set_option("persistent", 2)
+    m.set_option("tile_code", 0)
     # the other forward tile code agrees to rounding
     m.set_option("tile_code", 1 - m.info("tile_code"))
     for a, b in zip(ref, run(m)):
