@@ -19,13 +19,15 @@ class FwiState:
     J: list = field(default_factory=list)
     alpha: list = field(default_factory=list)
     seconds: list = field(default_factory=list)
+    kappa: float = 0.0     # step factor in force (backtracking halves it); 0: not yet set
+    rejected: int = 0      # trial steps that raised the misfit (backtracking)
 
 
 def save(path, model, state: FwiState, rho):
     vp, vs = model.velocities()
     np.savez(path, vp=vp.cpu().numpy(), vs=vs.cpu().numpy(), rho=rho.cpu().numpy(),
              iteration=state.iteration, J=np.array(state.J), alpha=np.array(state.alpha),
-             seconds=np.array(state.seconds))
+             seconds=np.array(state.seconds), kappa=state.kappa, rejected=state.rejected)
 
 
 def load(path, model, device="cuda"):
@@ -34,37 +36,68 @@ def load(path, model, device="cuda"):
     rho = t(d["rho"])
     model.set_model(t(d["vp"]), t(d["vs"]), rho)
     st = FwiState(int(d["iteration"]), list(d["J"]), [tuple(a) for a in d["alpha"]],
-                  list(d["seconds"]))
+                  list(d["seconds"]), float(d["kappa"]) if "kappa" in d else 0.0,
+                  int(d["rejected"]) if "rejected" in d else 0)
     return st, rho
+
+
+def _step(model, g, param, update_rho, kappa):
+    """One model update along the (preconditioned) gradient g."""
+    if param == "velocity":
+        alpha, _, _, _ = model.update_velocity(g[0], g[1], g[2], update_rho=update_rho,
+                                               kappa=kappa, want_model=False)
+    else:
+        alpha, _, _ = model.update(g[0], g[1], kappa, want_velocities=False)
+    return alpha
 
 
 def run(model, wavelet, seis_obs, iterations, *, kappa=0.02, eps_rel=1e-3, threshold=0.0,
         rel_threshold=0.0, precondition=True, param="lame", update_rho=False,
-        state: FwiState | None = None, checkpoint_path=None, rho=None, log=None):
-    """Run up to `iterations` more inversion steps, stopping once the misfit
-    falls to `threshold` or to `rel_threshold` times the first iteration's
-    (the stop rule of the Method section).  param "lame" steps lambda and mu
-    (Eq. 9, Eq. 10); "velocity" steps Vp, Vs and, with update_rho, rho.
-    Returns the FwiState."""
+        backtrack=False, state: FwiState | None = None, checkpoint_path=None, rho=None,
+        log=None):
+    """Run up to `iterations` more forward modellings, each followed by an
+    inversion step, stopping once the misfit falls to `threshold` or to
+    `rel_threshold` times the first iteration's (the stop rule of the Method
+    section).  param "lame" steps lambda and mu (Eq. 9, Eq. 10); "velocity"
+    steps Vp, Vs and, with update_rho, rho; the step is kappa times the
+    largest model value over the largest gradient (Eq. 11, Eq. 12).
+
+    backtrack: a safeguard the paper does not state.  A step after which the
+    misfit is higher than before is taken back: the model returns to the last
+    accepted one, kappa is halved and the step is retried along the same
+    gradient (one forward modelling per retry, no new gradient).  Without it
+    every step is kept, as in the plain method.  Returns the FwiState."""
     st = state or FwiState()
+    if st.kappa <= 0.0:
+        st.kappa = kappa
     seis = model.empty_seis()
     resid = torch.empty_like(seis)
+    want_rho = param == "velocity" and update_rho
+    last = None  # (model, preconditioned gradient) of the last accepted iteration
     for _ in range(iterations):
         t0 = time.perf_counter()
         model.forward(wavelet, seis)
         _, J = model.residual_misfit(seis, seis_obs, resid)
+        if backtrack and last is not None and J > st.J[-1]:
+            st.rejected += 1
+            st.kappa *= 0.5
+            model.set_model(*last[0])
+            alpha = _step(model, last[1], param, update_rho, st.kappa)
+            st.alpha[-1] = alpha
+            st.seconds[-1] += time.perf_counter() - t0
+            if log:
+                log(f"iteration {st.iteration}: trial J = {J:.6e} rejected, kappa -> {st.kappa:.3g}")
+            continue
         if J <= threshold or (st.J and rel_threshold > 0 and J <= rel_threshold * st.J[0]):
             st.J.append(J)
             break
-        want_rho = param == "velocity" and update_rho
-        g_lam, g_mu, g_rho = model.adjoint_gradient(resid, with_rho=want_rho)
+        g = model.adjoint_gradient(resid, with_rho=want_rho)
         if precondition:
-            model.precondition(g_lam, g_mu, eps_rel)
-        if param == "velocity":
-            alpha, _, _, _ = model.update_velocity(g_lam, g_mu, g_rho, update_rho=update_rho,
-                                                   kappa=kappa, want_model=False)
-        else:
-            alpha, _, _ = model.update(g_lam, g_mu, kappa, want_velocities=False)
+            model.precondition(g[0], g[1], eps_rel)
+        if backtrack:
+            vp, vs = model.velocities()
+            last = ((vp, vs, model.density()), g)
+        alpha = _step(model, g, param, update_rho, st.kappa)
         st.iteration += 1
         st.J.append(J)
         st.alpha.append(alpha)
@@ -114,6 +147,10 @@ def main(argv=None):
                     help="stop once J falls to this fraction of the first iteration's")
     ap.add_argument("--param", default="lame", choices=["lame", "velocity"])
     ap.add_argument("--no-precondition", dest="precondition", action="store_false")
+    ap.add_argument("--backtrack", action="store_true",
+                    help="take back a step that raises the misfit and halve kappa")
+    ap.add_argument("--near-wall", type=float, default=0.4,
+                    help="radial extent (m) beyond the wall of the near-wall model error")
     args = ap.parse_args(argv)
     if not torch.cuda.is_available():
         raise SystemExit("the inversion needs a CUDA device (there is no CPU fallback)")
@@ -143,16 +180,20 @@ def main(argv=None):
     m.set_model(t(w.vp), vs, rho)
     mask = ((w.vs > 0) & (np.arange(w.nr)[:, None] < w.nr - w.npml_r) &
             (np.arange(w.nz)[None, :] >= w.npml_z) & (np.arange(w.nz)[None, :] < w.nz - w.npml_z))
+    # the near-wall zone: formation rows within --near-wall metres of the wall
+    i_wall = int(np.argmax(w.vs[:, w.nz // 2] > 0))
+    near = mask & (np.arange(w.nr)[:, None] < i_wall + int(round(args.near_wall / w.dr)))
 
     def model_error():
         vp_c, vs_c = m.velocities()
         vp_c, vs_c = vp_c.cpu().numpy(), vs_c.cpu().numpy()
-        e = lambda a, b: float(np.linalg.norm((a - b)[mask]) / np.linalg.norm(b[mask]))
-        return {"vp": e(vp_c, w.vp_true), "vs": e(vs_c, w.vs_true)}
+        e = lambda a, b, k: float(np.linalg.norm((a - b)[k]) / np.linalg.norm(b[k]))
+        return {"vp": e(vp_c, w.vp_true, mask), "vs": e(vs_c, w.vs_true, mask),
+                "vp_near_wall": e(vp_c, w.vp_true, near), "vs_near_wall": e(vs_c, w.vs_true, near)}
 
     err0 = model_error()
     st = run(m, wav, obs, args.iterations, kappa=args.kappa, rel_threshold=args.rel_threshold,
-             precondition=args.precondition, param=args.param,
+             precondition=args.precondition, param=args.param, backtrack=args.backtrack,
              log=lambda s: print(s, file=sys.stderr, flush=True))
     err1 = model_error()
     info = {k: m.info(k) for k in ("history_steps", "snapshots", "tail_steps", "recompute_steps",
@@ -162,6 +203,8 @@ def main(argv=None):
         "workload": args.config, "nr": w.nr, "nz": w.nz, "nt": w.nt, "nshots": w.nshots,
         "start": args.start, "param": args.param, "precondition": args.precondition,
         "rel_threshold": args.rel_threshold, "iterations_run": st.iteration,
+        "backtrack": args.backtrack, "rejected_steps": st.rejected, "kappa_start": args.kappa,
+        "kappa_end": st.kappa, "near_wall_m": args.near_wall,
         "model_rel_error_start": err0, "model_rel_error_end": err1,
         "checkpoint": info, "J": [float(x) for x in st.J],
         "seconds_per_iteration": [float(x) for x in st.seconds],
