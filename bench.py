@@ -41,7 +41,7 @@ REF_SAMPLE_STEPS = 100
 L2_BYTES = 129e6
 # checkpoint byte cap per workload when --cap-gb is not given (0: every step
 # of the forward history stored)
-DEFAULT_CAP_GB = {"c0": 0.0, "c1": 0.0, "c2": 240.0, "c3": 4.0, "c4": 60.0, "flushed": 100.0,
+DEFAULT_CAP_GB = {"c0": 0.0, "c1": 0.0, "c2": 240.0, "c3": 4.0, "c4": 240.0, "flushed": 100.0,
                   "tool": 150.0}
 DEFAULT_SNAP = {"c4": "bf16"}
 E2E_STEPS = 3
