@@ -323,8 +323,19 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
  *                     of a shot group; 1: one launch per half-step and tile
  *                     class (interior tiles, C-PML tiles), so that interior
  *                     tiles run more blocks per SM; applies to the adjoint
- *                     and, with "tile_code" 1, to the forward (bit for bit
- *                     the same results).
+ *                     and, with "tile_code" 1, to the forward; 2: as 1,
+ *                     and with "tile_code" 1 the forward's interior tiles
+ *                     run in pipelined kernels (a grid of a few blocks per
+ *                     SM, each block copying its next tile while it
+ *                     computes the current one).  All give bit for bit the
+ *                     same results.  BH_ERR_UNSUPPORTED for 2 when the
+ *                     pipelined kernels do not fit an SM.
+ *   "pipe_grid"       cap on the blocks of a pipelined launch (default 0:
+ *                     as many as fit the SMs); a small cap makes every
+ *                     block walk many tiles (a test knob).
+ *   "tile_order"      order of the tiles within a launch: 0 (default) by
+ *                     global column, then row, then shot; 1 by shot, then
+ *                     row, then column.  The same results bit for bit.
  *   "group"           shots per launch group, 1 .. min(32, nshots) (default
  *                     the largest): one launch, or one cooperative phase,
  *                     covers the tiles of a group's shots; groups run one
@@ -351,12 +362,14 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
  * counterpart).  The candidates are both forward tile codes ("tile_code"),
  * the shot group sizes 1, 2, 4, ... up to min(32, nshots) (and nshots
  * itself) and the launch forms of the "persistent" option that differ for
- * that grouping (and, for one launch per half-step, "split" 0 and 1); each
+ * that grouping (and, for one launch per half-step, "split" 0 and 1, and 2
+ * with tile code 1, and both "tile_order" values); each
  * is timed four times over `steps` forward and `steps` adjoint steps of
  * every shot (CUDA events on the model's stream, the best of the last three
  * kept) and the fastest is applied (options "tile_code", "group",
- * "persistent" and "split").  With cache_path, a line
- * "<key> <group> <form> <tile code> <split> <ms> ..." whose key (GPU name
+ * "persistent", "split" and "tile_order").  With cache_path, a line
+ * "<key> <group> <form> <tile code> <split> <tile order> <ms> ..." whose key
+ * (GPU name
  * with blanks as '_',
  * nr, window pitch, nshots, as bh_tune_lookup forms it) matches is applied
  * without timing; otherwise the timed choice is appended to the file.  The
@@ -374,15 +387,15 @@ bh_status bh_tune(bh_model* model, int steps, const char* cache_path, char* choi
                   int choice_len);
 
 /*
- * The cached launch configuration (group, form, tile code, split) for a key (host
- * only, no GPU): the last
+ * The cached launch configuration (group, form, tile code, split, tile
+ * order) for a key (host only, no GPU): the last
  * line of cache_path whose key is gpu_name (blanks as '_') | nr |
  * window_pitch (the largest window length rounded up to 32) | nshots.
  * Errors: BH_ERR_INVALID_ARG, BH_ERR_STATE (no such line, or no file).
  */
 bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr,
                          int window_pitch, int nshots, int* group, int* form, int* tile_code,
-                         int* split);
+                         int* split, int* tile_order);
 
 /*
  * Read-only facts about a model (the paper has no counterpart):
@@ -393,7 +406,9 @@ bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr,
  * (stepping-kernel launches of the last bh_forward + bh_adjoint_gradient),
  * "history_snapshot_bytes", "device_bytes", "kernel_launches" (kernels the
  * model has launched since it was created, for counting the launches of a
- * timed region), "group" (shots per launch group), "state_version"
+ * timed region), "group" (shots per launch group), "tile_code", "split",
+ * "pipe_grid", "tile_order" (the options' values), "pipe_blocks" (blocks of a pipelined
+ * launch that fit the SMs), "state_version"
  * (changes whenever the stored forward
  * history is replaced or invalidated: bh_forward, bh_set_model, bh_update,
  * bh_update_velocity; a caller that keeps a forward run for a later

@@ -125,7 +125,7 @@ def load_library(path: str | None = None):
     lib.bh_tune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int]
     lib.bh_tune.restype = st
     lib.bh_tune_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
-                                   ctypes.c_int, ip, ip, ip, ip]
+                                   ctypes.c_int, ip, ip, ip, ip, ip]
     lib.bh_tune_lookup.restype = st
     lib.bh_get_info.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.bh_get_info.restype = st
@@ -291,14 +291,14 @@ class Model:
         """bh_tune: pick the shot group size and launch form (cached per GPU
         and workload shape in cache_path, timed on a miss).  Returns the
         library's description of the choice."""
-        buf = ctypes.create_string_buffer(2048)
+        buf = ctypes.create_string_buffer(8192)
         path = cache_path.encode() if cache_path else None
         self._rc(self.lib.bh_tune(self.h, int(steps), path, buf, len(buf)))
         return buf.value.decode()
 
     def set_option(self, key, value):
         """bh_set_option: "persistent", "group", "tile_code", "split",
-        "barrier_timeout_ms", "barrier_extra_arrivals"."""
+        "tile_order", "pipe_grid", "barrier_timeout_ms", "barrier_extra_arrivals"."""
         self._rc(self.lib.bh_set_option(self.h, key.encode(), float(value)))
 
     def info(self, key):
@@ -419,15 +419,15 @@ def starting_model(nr, dr, r_wall, r_far, vp_wall, vs_wall, vp_far, vs_far, vp_f
 
 
 def tune_lookup(cache_path, gpu_name, nr, window_pitch, nshots):
-    """bh_tune_lookup (host only): (group, form, tile code, split) cached
-    for the key, or None."""
+    """bh_tune_lookup (host only): (group, form, tile code, split, tile
+    order) cached for the key, or None."""
     lib = load_library()
-    g, f, v, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    g, f, v, sp, od = (ctypes.c_int() for _ in range(5))
     rc = lib.bh_tune_lookup(cache_path.encode(), gpu_name.encode(), int(nr), int(window_pitch),
                             int(nshots), ctypes.byref(g), ctypes.byref(f), ctypes.byref(v),
-                            ctypes.byref(sp))
+                            ctypes.byref(sp), ctypes.byref(od))
     if rc == 6:
         return None
     if rc != BH_OK:
         raise BhError(rc, lib.bh_last_error(None).decode())
-    return g.value, f.value, v.value, sp.value
+    return g.value, f.value, v.value, sp.value, od.value

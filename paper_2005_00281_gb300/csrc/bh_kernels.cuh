@@ -472,68 +472,31 @@ struct __align__(16) FwdSmem {
     Prof pf;
 };
 
-// Velocity half-step of one tile: Eq. 2 lines 1-2 with the C-PML memories
-// 0..3.  Own-node inputs are loaded before the staging, so the tile pays
-// one round trip to L2.  hist0 (or null): history slot receiving v^{n-1/2}.
+// The arithmetic of the velocity half-step of one tile, from the staged
+// stresses and the own-node inputs (shared by every kernel that runs it, so
+// that they agree bit for bit).
 template <int PM>
-__device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                             float* hist0, int i0, int j0, int flags,
-                                             const BarK* bar, unsigned& epoch, FwdSmem& sm)
+__device__ __forceinline__ void fwd_vel_core(const WinK& g, const StateK& S, float* hist0,
+                                             const Own& o, bool pml, const V4& vr0, const V4& vz0,
+                                             const V4& br, const V4& bz, const V4& q0,
+                                             const V4& q1, const V4& q2, const V4& q3, float ivr,
+                                             float ivh, const Tile& s_rr, const Tile& s_tt,
+                                             const Tile& s_rz, const Tile& s_zz, const Prof* pf,
+                                             const BarK* bar, unsigned& epoch)
 {
-    Tile &s_rr = sm.a, &s_tt = sm.b, &s_rz = sm.c, &s_zz = sm.d;
-    const Own o = own_of(g, i0, j0);
-    const bool pml = tile_pml<PM>(flags);
-    V4 vr0{}, vz0{}, br{}, bz{}, q0{}, q1{}, q2{}, q3{};
-    float ari = 0.f, bri = 0.f, arh = 0.f, brh = 0.f, ivr = 0.f, ivh = 0.f;
+    float ari = 0.f, bri = 0.f, arh = 0.f, brh = 0.f;
     V4 azi{}, bzi{}, azh{}, bzh{};
-    __syncthreads();
-    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
-        const Slot sl = slot_of(it, i0, j0, g);
-        stage_async<EVEN>(s_rr, S.trr, sl);
-        stage_async<EVEN>(s_tt, S.ttt, sl);
-        stage_async<ODD>(s_rz, S.trz, sl);
-        stage_async<EVEN>(s_zz, S.tzz, sl);
-    }
-    if (pml) stage_prof(sm.pf, C, g, i0, j0);
-    // own-node inputs, in flight together with the copies
-    if (o.live) {
-        ivr = __ldg(C.inv_r_int + o.i);
-        ivh = __ldg(C.inv_r_half + o.i);
-        vz0 = ld4cg(S.vz + o.c);
-        bz = ld4g(C.w_bvz + o.cw);
-        if (flags & TILE_LAST) patch4(bz, o.j, g.nz - 1, bvz_at(C, g, o.i, g.nz - 1));
-        if (o.i >= 1) {
-            vr0 = ld4cg(S.vr + o.c);
-            br = ld4g(C.w_bvr + o.cw);
-        }
-        if (pml) {
-            q2 = ld4cg(S.psi[2] + o.c);
-            q3 = ld4cg(S.psi[3] + o.c);
-            if (o.i >= 1) {
-                q0 = ld4cg(S.psi[0] + o.c);
-                q1 = ld4cg(S.psi[1] + o.c);
-            }
-        }
-    }
-    async_wait_all();
-    if (i0 < kH) {
-        for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
-            const Slot sl = slot_of(it, i0, j0, g);
-            if (sl.neg && sl.off_o >= 0) negate_slot(s_rz, sl);
-        }
-    }
-    __syncthreads();
     if (o.live) {
     if (pml) {
-        arh = sm.pf.r[0][o.rr];
-        brh = sm.pf.r[1][o.rr];
-        azh = prof4(sm.pf.z[2], o.cc);
-        bzh = prof4(sm.pf.z[3], o.cc);
+        arh = pf->r[0][o.rr];
+        brh = pf->r[1][o.rr];
+        azh = prof4(pf->z[2], o.cc);
+        bzh = prof4(pf->z[3], o.cc);
         if (o.i >= 1) {
-            ari = sm.pf.r[2][o.rr];
-            bri = sm.pf.r[3][o.rr];
-            azi = prof4(sm.pf.z[0], o.cc);
-            bzi = prof4(sm.pf.z[1], o.cc);
+            ari = pf->r[2][o.rr];
+            bri = pf->r[3][o.rr];
+            azi = prof4(pf->z[0], o.cc);
+            bzi = prof4(pf->z[1], o.cc);
         }
     }
     const int rr = o.rr, cc = o.cc;
@@ -608,46 +571,45 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     }
 }
 
-// Stress half-step of one tile: Eq. 2 lines 3-6 with the C-PML memories
-// 4..7, source injection into the three normal stresses, pressure
-// recording, and the store of v^{n+1/2} for the adjoint.
+// Velocity half-step of one tile: Eq. 2 lines 1-2 with the C-PML memories
+// 0..3.  Own-node inputs are loaded before the staging, so the tile pays
+// one round trip to L2.  hist0 (or null): history slot receiving v^{n-1/2}.
 template <int PM>
-__device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                                const SrcRecK& q, int n, bool record,
-                                                float* hist, int i0, int j0, int flags,
-                                                const BarK* bar, unsigned& epoch, FwdSmem& sm)
+__device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
+                                             float* hist0, int i0, int j0, int flags,
+                                             const BarK* bar, unsigned& epoch, FwdSmem& sm)
 {
-    Tile &s_vr = sm.a, &s_vz = sm.b;
+    Tile &s_rr = sm.a, &s_tt = sm.b, &s_rz = sm.c, &s_zz = sm.d;
     const Own o = own_of(g, i0, j0);
     const bool pml = tile_pml<PM>(flags);
+    V4 vr0{}, vz0{}, br{}, bz{}, q0{}, q1{}, q2{}, q3{};
+    float ivr = 0.f, ivh = 0.f;
     __syncthreads();
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const Slot sl = slot_of(it, i0, j0, g);
-        stage_async<ODD>(s_vr, S.vr, sl);
-        stage_async<EVEN>(s_vz, S.vz, sl);
+        stage_async<EVEN>(s_rr, S.trr, sl);
+        stage_async<EVEN>(s_tt, S.ttt, sl);
+        stage_async<ODD>(s_rz, S.trz, sl);
+        stage_async<EVEN>(s_zz, S.tzz, sl);
     }
     if (pml) stage_prof(sm.pf, C, g, i0, j0);
-    V4 t_rr{}, t_tt{}, t_zz{}, lm{}, mu{}, t_rz{}, mh{};
-    float arh = 0.f, brh = 0.f, ivh = 0.f;
-    V4 azi{}, bzi{}, q4{}, q5{}, q6{}, q7{};
+    // own-node inputs, in flight together with the copies
     if (o.live) {
+        ivr = __ldg(C.inv_r_int + o.i);
         ivh = __ldg(C.inv_r_half + o.i);
-        t_rr = ld4cg(S.trr + o.c);
-        t_tt = ld4cg(S.ttt + o.c);
-        t_zz = ld4cg(S.tzz + o.c);
-        lm = ld4g(C.w_lam + o.cw);
-        mu = ld4g(C.w_mu + o.cw);
+        vz0 = ld4cg(S.vz + o.c);
+        bz = ld4g(C.w_bvz + o.cw);
+        if (flags & TILE_LAST) patch4(bz, o.j, g.nz - 1, bvz_at(C, g, o.i, g.nz - 1));
         if (o.i >= 1) {
-            t_rz = ld4cg(S.trz + o.c);
-            mh = ld4g(C.w_muh + o.cw);
-            if (flags & TILE_LAST) patch4(mh, o.j, g.nz - 1, muh_at(C, g, o.i, g.nz - 1));
+            vr0 = ld4cg(S.vr + o.c);
+            br = ld4g(C.w_bvr + o.cw);
         }
         if (pml) {
-            q4 = ld4cg(S.psi[4] + o.c);
-            q5 = ld4cg(S.psi[5] + o.c);
+            q2 = ld4cg(S.psi[2] + o.c);
+            q3 = ld4cg(S.psi[3] + o.c);
             if (o.i >= 1) {
-                q6 = ld4cg(S.psi[6] + o.c);
-                q7 = ld4cg(S.psi[7] + o.c);
+                q0 = ld4cg(S.psi[0] + o.c);
+                q1 = ld4cg(S.psi[1] + o.c);
             }
         }
     }
@@ -655,17 +617,35 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     if (i0 < kH) {
         for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
             const Slot sl = slot_of(it, i0, j0, g);
-            if (sl.neg && sl.off_o >= 0) negate_slot(s_vr, sl);
+            if (sl.neg && sl.off_o >= 0) negate_slot(s_rz, sl);
         }
     }
     __syncthreads();
+    fwd_vel_core<PM>(g, S, hist0, o, pml, vr0, vz0, br, bz, q0, q1, q2, q3, ivr, ivh, s_rr, s_tt,
+                     s_rz, s_zz, &sm.pf, bar, epoch);
+}
+
+// The arithmetic of the stress half-step of one tile, from the staged
+// velocities and the own-node inputs (shared by every kernel that runs it).
+template <int PM>
+__device__ __forceinline__ void fwd_stress_core(const WinK& g, const StateK& S, const SrcRecK& q,
+                                                int n, bool record, float* hist, const Own& o,
+                                                bool pml, const V4& t_rr, const V4& t_tt,
+                                                const V4& t_zz, const V4& t_rz, const V4& lm,
+                                                const V4& mu, const V4& mh, const V4& q4,
+                                                const V4& q5, const V4& q6, const V4& q7,
+                                                float ivh, const Tile& s_vr, const Tile& s_vz,
+                                                const Prof* pf, const BarK* bar, unsigned& epoch)
+{
     const int rr = o.rr, cc = o.cc;
+    float arh = 0.f, brh = 0.f;
+    V4 azi{}, bzi{};
     if (o.live) {
         if (pml) {
-            arh = sm.pf.r[0][rr];
-            brh = sm.pf.r[1][rr];
-            azi = prof4(sm.pf.z[0], cc);
-            bzi = prof4(sm.pf.z[1], cc);
+            arh = pf->r[0][rr];
+            brh = pf->r[1][rr];
+            azi = prof4(pf->z[0], cc);
+            bzi = prof4(pf->z[1], cc);
         }
         const V12 vr12 = lds12(s_vr, rr, cc - 4), vz12 = lds12(s_vz, rr, cc - 4);
         const V4 vrp1 = lds4(s_vr, rr + 1, cc);
@@ -717,10 +697,10 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         float ari = 0.f, bri = 0.f;
         V4 azh{}, bzh{};
         if (pml) {
-            ari = sm.pf.r[2][rr];
-            bri = sm.pf.r[3][rr];
-            azh = prof4(sm.pf.z[2], cc);
-            bzh = prof4(sm.pf.z[3], cc);
+            ari = pf->r[2][rr];
+            bri = pf->r[3][rr];
+            azh = prof4(pf->z[2], cc);
+            bzh = prof4(pf->z[3], cc);
         }
         const V12 vr12 = lds12(s_vr, rr, cc - 4);
         const V4 vz0 = lds4(s_vz, rr, cc), vzm1 = lds4(s_vz, rr - 1, cc),
@@ -757,6 +737,61 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         st4(hist + o.c, o.j, g.nz, a.v);
         st4(hist + g.nr * g.P + o.c, o.j, g.nz, b.v);
     }
+}
+
+// Stress half-step of one tile: Eq. 2 lines 3-6 with the C-PML memories
+// 4..7, source injection into the three normal stresses, pressure
+// recording, and the store of v^{n+1/2} for the adjoint.
+template <int PM>
+__device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
+                                                const SrcRecK& q, int n, bool record,
+                                                float* hist, int i0, int j0, int flags,
+                                                const BarK* bar, unsigned& epoch, FwdSmem& sm)
+{
+    Tile &s_vr = sm.a, &s_vz = sm.b;
+    const Own o = own_of(g, i0, j0);
+    const bool pml = tile_pml<PM>(flags);
+    __syncthreads();
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_async<ODD>(s_vr, S.vr, sl);
+        stage_async<EVEN>(s_vz, S.vz, sl);
+    }
+    if (pml) stage_prof(sm.pf, C, g, i0, j0);
+    V4 t_rr{}, t_tt{}, t_zz{}, lm{}, mu{}, t_rz{}, mh{};
+    float ivh = 0.f;
+    V4 q4{}, q5{}, q6{}, q7{};
+    if (o.live) {
+        ivh = __ldg(C.inv_r_half + o.i);
+        t_rr = ld4cg(S.trr + o.c);
+        t_tt = ld4cg(S.ttt + o.c);
+        t_zz = ld4cg(S.tzz + o.c);
+        lm = ld4g(C.w_lam + o.cw);
+        mu = ld4g(C.w_mu + o.cw);
+        if (o.i >= 1) {
+            t_rz = ld4cg(S.trz + o.c);
+            mh = ld4g(C.w_muh + o.cw);
+            if (flags & TILE_LAST) patch4(mh, o.j, g.nz - 1, muh_at(C, g, o.i, g.nz - 1));
+        }
+        if (pml) {
+            q4 = ld4cg(S.psi[4] + o.c);
+            q5 = ld4cg(S.psi[5] + o.c);
+            if (o.i >= 1) {
+                q6 = ld4cg(S.psi[6] + o.c);
+                q7 = ld4cg(S.psi[7] + o.c);
+            }
+        }
+    }
+    async_wait_all();
+    if (i0 < kH) {
+        for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+            const Slot sl = slot_of(it, i0, j0, g);
+            if (sl.neg && sl.off_o >= 0) negate_slot(s_vr, sl);
+        }
+    }
+    __syncthreads();
+    fwd_stress_core<PM>(g, S, q, n, record, hist, o, pml, t_rr, t_tt, t_zz, t_rz, lm, mu, mh, q4,
+                        q5, q6, q7, ivh, s_vr, s_vz, &sm.pf, bar, epoch);
 }
 
 // ------------------------------------------ adjoint: transpose of Eq. 2
@@ -1458,9 +1493,9 @@ __device__ __forceinline__ void run_adj_vel(const RunK& r, const ShotTable<N>& T
 }
 
 // One launch per half-step: one block per tile, branching on the tile's
-// class like the persistent kernels (a launch with both classes keeps the
-// block scheduler's overlap of one block's staging with another's compute;
-// separate launches per class measured slower).
+// class like the persistent kernels.  The per-class launches below (option
+// "split") fit more interior blocks per SM; which is faster depends on the
+// workload (the autotuner times both).
 template <int N, int V>
 __global__ void __launch_bounds__(kThreads, 5) k_fwd_vel(RunK r, int n,
                                                       const __grid_constant__ ShotTable<N> T)
@@ -1557,6 +1592,190 @@ __global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
     pdl_wait();
     unsigned epoch = 0;
     run_adj_vel<N, RHO, PM, false>(r, T, n, blockIdx.x, false, false, nullptr, epoch, sm);
+    pdl_launch_dependents();
+}
+
+// ---------------------------------------------- pipelined interior tiles
+//
+// One launch per half-step over the interior tiles of a group, with a grid of
+// a few blocks per SM: a block walks the tiles t, t + grid, t + 2 grid, ...
+// and, while it computes one tile, the copies of its next tile are already
+// in flight into the second of two shared-memory stages (cp.async groups,
+// wait_group 1).  The own-node inputs travel the same way (each thread copies
+// its own float4 groups), so nothing of the next tile waits on a register
+// load.  The arithmetic is the shared core of the one-tile-per-block
+// kernels, so the results agree with theirs bit for bit.
+
+// one 16-byte copy of a thread's own group; zero-filled when !ok (src is
+// then any valid address: nothing is read)
+__device__ __forceinline__ void cp16(void* dst, const float* src, bool ok)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(ok ? 16u : 0u)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// all but the most recent group of this thread's copies have landed
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__device__ __forceinline__ V4 v4_of(const float4& f) { return V4{{f.x, f.y, f.z, f.w}}; }
+
+struct __align__(16) VelStage {
+    Tile a, b, c, d;           // trr, ttt, trz, tzz
+    float4 own[4][kThreads];   // v_r, v_z, buoyancy at v_r and v_z of each thread's group
+};
+
+struct __align__(16) StressStage {
+    Tile a, b;                 // v_r, v_z
+    float4 own[7][kThreads];   // trr, ttt, tzz, trz, lambda, mu, harmonic mu
+};
+
+__device__ __forceinline__ void vel_issue(VelStage& b, const ShotK& sh, int i0, int j0)
+{
+    const WinK& g = sh.g;
+    const StateK& S = sh.Sf;
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_async<EVEN>(b.a, S.trr, sl);
+        stage_async<EVEN>(b.b, S.ttt, sl);
+        stage_async<ODD>(b.c, S.trz, sl);
+        stage_async<EVEN>(b.d, S.tzz, sl);
+    }
+    const Own o = own_of(g, i0, j0);
+    const int tid = tid_of();
+    const bool r1 = o.live && o.i >= 1;
+    cp16(&b.own[0][tid], r1 ? S.vr + o.c : S.vr, r1);
+    cp16(&b.own[1][tid], o.live ? S.vz + o.c : S.vz, o.live);
+    cp16(&b.own[2][tid], r1 ? sh.C.w_bvr + o.cw : sh.C.w_bvr, r1);
+    cp16(&b.own[3][tid], o.live ? sh.C.w_bvz + o.cw : sh.C.w_bvz, o.live);
+}
+
+__device__ __forceinline__ void stress_issue(StressStage& b, const ShotK& sh, int i0, int j0)
+{
+    const WinK& g = sh.g;
+    const StateK& S = sh.Sf;
+    const CoefK& C = sh.C;
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_async<ODD>(b.a, S.vr, sl);
+        stage_async<EVEN>(b.b, S.vz, sl);
+    }
+    const Own o = own_of(g, i0, j0);
+    const int tid = tid_of();
+    const bool r1 = o.live && o.i >= 1;
+    cp16(&b.own[0][tid], o.live ? S.trr + o.c : S.trr, o.live);
+    cp16(&b.own[1][tid], o.live ? S.ttt + o.c : S.ttt, o.live);
+    cp16(&b.own[2][tid], o.live ? S.tzz + o.c : S.tzz, o.live);
+    cp16(&b.own[3][tid], r1 ? S.trz + o.c : S.trz, r1);
+    cp16(&b.own[4][tid], o.live ? C.w_lam + o.cw : C.w_lam, o.live);
+    cp16(&b.own[5][tid], o.live ? C.w_mu + o.cw : C.w_mu, o.live);
+    cp16(&b.own[6][tid], r1 ? C.w_muh + o.cw : C.w_muh, r1);
+}
+
+// negate this thread's staged slots of an odd field that are mirror rows
+__device__ __forceinline__ void negate_mirror(Tile& t, int i0, int j0, const WinK& g)
+{
+    if (i0 < kH) {
+        for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+            const Slot sl = slot_of(it, i0, j0, g);
+            if (sl.neg && sl.off_o >= 0) negate_slot(t, sl);
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_fwd_vel_pipe(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+{
+    __shared__ VelStage st[2];
+    pdl_wait();
+    unsigned epoch = 0;
+    int t = blockIdx.x;
+    if (t < r.ntiles) {
+        const int4 tk = r.tiles[t];
+        vel_issue(st[0], shot_of(T, tk), tk.y, tk.z);
+    }
+    cp_commit();
+    for (int k = 0; t < r.ntiles; ++k, t += gridDim.x) {
+        const int tn = t + (int)gridDim.x;
+        if (tn < r.ntiles) {
+            const int4 tk = r.tiles[tn];
+            vel_issue(st[(k + 1) & 1], shot_of(T, tk), tk.y, tk.z);
+        }
+        cp_commit();
+        cp_wait_prev();
+        VelStage& b = st[k & 1];
+        const int4 tk = r.tiles[t];
+        const ShotK& sh = shot_of(T, tk);
+        const WinK& g = sh.g;
+        negate_mirror(b.c, tk.y, tk.z, g);
+        __syncthreads();
+        const Own o = own_of(g, tk.y, tk.z);
+        const int tid = tid_of();
+        const V4 vr0 = v4_of(b.own[0][tid]), vz0 = v4_of(b.own[1][tid]);
+        const V4 br = v4_of(b.own[2][tid]);
+        V4 bz = v4_of(b.own[3][tid]);
+        float ivr = 0.f, ivh = 0.f;
+        if (o.live) {
+            ivr = __ldg(sh.C.inv_r_int + o.i);
+            ivh = __ldg(sh.C.inv_r_half + o.i);
+            if (tk.w & TILE_LAST) patch4(bz, o.j, g.nz - 1, bvz_at(sh.C, g, o.i, g.nz - 1));
+        }
+        float* h0 = (r.hist_n0 >= 0 && n == r.hist_n0) ? hist_slot(sh, 0) : nullptr;
+        const V4 zero{};
+        fwd_vel_core<PM_INTERIOR>(g, sh.Sf, h0, o, false, vr0, vz0, br, bz, zero, zero, zero,
+                                  zero, ivr, ivh, b.a, b.b, b.c, b.d, nullptr, nullptr, epoch);
+        __syncthreads();  // stage k & 1 is refilled at the next iteration
+    }
+    pdl_launch_dependents();
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_fwd_stress_pipe(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+{
+    __shared__ StressStage st[2];
+    pdl_wait();
+    unsigned epoch = 0;
+    int t = blockIdx.x;
+    if (t < r.ntiles) {
+        const int4 tk = r.tiles[t];
+        stress_issue(st[0], shot_of(T, tk), tk.y, tk.z);
+    }
+    cp_commit();
+    for (int k = 0; t < r.ntiles; ++k, t += gridDim.x) {
+        const int tn = t + (int)gridDim.x;
+        if (tn < r.ntiles) {
+            const int4 tk = r.tiles[tn];
+            stress_issue(st[(k + 1) & 1], shot_of(T, tk), tk.y, tk.z);
+        }
+        cp_commit();
+        cp_wait_prev();
+        StressStage& b = st[k & 1];
+        const int4 tk = r.tiles[t];
+        const ShotK& sh = shot_of(T, tk);
+        const WinK& g = sh.g;
+        negate_mirror(b.a, tk.y, tk.z, g);
+        __syncthreads();
+        const Own o = own_of(g, tk.y, tk.z);
+        const int tid = tid_of();
+        const V4 t_rr = v4_of(b.own[0][tid]), t_tt = v4_of(b.own[1][tid]);
+        const V4 t_zz = v4_of(b.own[2][tid]), t_rz = v4_of(b.own[3][tid]);
+        const V4 lm = v4_of(b.own[4][tid]), mu = v4_of(b.own[5][tid]);
+        V4 mh = v4_of(b.own[6][tid]);
+        float ivh = 0.f;
+        if (o.live) {
+            ivh = __ldg(sh.C.inv_r_half + o.i);
+            if (o.i >= 1 && (tk.w & TILE_LAST))
+                patch4(mh, o.j, g.nz - 1, muh_at(sh.C, g, o.i, g.nz - 1));
+        }
+        float* h = r.hist_n0 >= 0 ? hist_slot(sh, n - r.hist_n0 + 1) : nullptr;
+        const V4 zero{};
+        fwd_stress_core<PM_INTERIOR>(g, sh.Sf, sh.q, n, r.record != 0, h, o, false, t_rr, t_tt,
+                                     t_zz, t_rz, lm, mu, mh, zero, zero, zero, zero, ivh, b.a,
+                                     b.b, nullptr, nullptr, epoch);
+        __syncthreads();
+    }
     pdl_launch_dependents();
 }
 

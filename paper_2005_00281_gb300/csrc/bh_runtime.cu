@@ -95,7 +95,11 @@ struct bh_model {
     int tile_code = 0;          // forward tile code variant (0: one path, 1: per tile class)
     // one launch per half-step and tile class (per-class code only: the
     // adjoint, and the forward with tile code 1)
+    // 2: as 1, with the forward's interior tiles in the pipelined kernels
     int split = 0;
+    int pipe_blocks = 0;                  // grid of the pipelined kernels (0: unavailable)
+    int pipe_grid = 0;                    // option "pipe_grid": cap on that grid (0: none)
+    int tile_order = 0;                   // option "tile_order" (build_tiles)
     int4* d_tiles_cls = nullptr;          // every group's tiles, interior first
     std::vector<int> group_nint;          // interior tiles of each group
     int fwd_blocks = 0, adj_blocks = 0;       // co-resident blocks, 1-shot kernels
@@ -479,9 +483,11 @@ bh_status setup_shots(bh_model* m)
 }
 
 // Tile table of every shot group of G shots, group after group.  Within a
-// group the tiles are ordered by global column, then row, then shot: tiles
-// of several shots at one place of the model run together and share the
-// coefficient copies' lines in L2.
+// group the tiles are ordered (option "tile_order") 0: by global column,
+// then row, then shot: tiles of several shots at one place of the model run
+// together and share the coefficient copies' lines in L2; 1: by shot, then
+// row, then column: the blocks resident at one time cover long runs of
+// each row (DRAM pages read whole).  The order changes no result.
 bh_status build_tiles(bh_model* m)
 {
     const bh_grid_desc& gd = m->grid;
@@ -509,7 +515,7 @@ bh_status build_tiles(bh_model* m)
                                               (last ? TILE_LAST : 0)));
                 m->group_ntiles.back()++;
             }
-        if (s % G == G - 1 || s == m->nshots - 1) {
+        if (m->tile_order == 0 && (s % G == G - 1 || s == m->nshots - 1)) {
             const int g0 = m->group_tile_off.back();
             const int sbase = s - s % G;
             std::stable_sort(tiles.begin() + g0, tiles.end(), [&](const int4& a, const int4& b) {
@@ -691,9 +697,15 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
     if (V == 1 && m->split) {
         RunK ri, rp;
         class_runs(m, grp, r, &ri, &rp);
+        const bool pipe = m->split == 2 && m->pipe_blocks > 0;
+        const int pg = m->pipe_grid > 0 ? std::min(m->pipe_grid, m->pipe_blocks) : m->pipe_blocks;
         for (int n = n0; n < n1; ++n) {
             size_t e = prof_begin(m, BH_KERNEL_FWD_VEL, n);
-            if (ri.ntiles) {
+            if (ri.ntiles && pipe) {
+                BH_CUDA(m, launch_pdl(k_fwd_vel_pipe<N>, dim3(std::min(ri.ntiles, pg)), blk,
+                                      m->stream, ri, n, T));
+                ++m->launches;
+            } else if (ri.ntiles) {
                 BH_CUDA(m, launch_pdl(k_fwd_vel_c<N, PM_INTERIOR>, dim3(ri.ntiles), blk,
                                       m->stream, ri, n, T));
                 ++m->launches;
@@ -705,7 +717,11 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
             }
             prof_end(m, e);
             e = prof_begin(m, BH_KERNEL_FWD_STRESS, n);
-            if (ri.ntiles) {
+            if (ri.ntiles && pipe) {
+                BH_CUDA(m, launch_pdl(k_fwd_stress_pipe<N>,
+                                      dim3(std::min(ri.ntiles, pg)), blk, m->stream, ri, n, T));
+                ++m->launches;
+            } else if (ri.ntiles) {
                 BH_CUDA(m, launch_pdl(k_fwd_stress_c<N, PM_INTERIOR>, dim3(ri.ntiles), blk,
                                       m->stream, ri, n, T));
                 ++m->launches;
@@ -1011,9 +1027,10 @@ std::string tune_key(const char* gpu, int nr, int P, int nshots)
     return name + buf;
 }
 
-// the last line of the cache with this key: "<key> <G> <form> <tile code> <split> ..."
+// the last line of the cache with this key:
+// "<key> <G> <form> <tile code> <split> <tile order> ..."
 bool tune_lookup(const char* path, const std::string& key, int* G, int* form, int* code,
-                 int* split)
+                 int* split, int* order)
 {
     std::ifstream f(path);
     if (!f) return false;
@@ -1023,15 +1040,17 @@ bool tune_lookup(const char* path, const std::string& key, int* G, int* form, in
         if (line.empty() || line[0] == '#') continue;
         std::istringstream is(line);
         std::string k;
-        int g = 0, p = -1, v = -1, sp = -1;
-        if (!(is >> k >> g >> p >> v >> sp)) continue;
+        int g = 0, p = -1, v = -1, sp = -1, od = -1;
+        std::string rest;
+        if (!(is >> k >> g >> p >> v >> sp >> od >> rest)) continue;
         if (k != key || g < 1 || g > kGroup || p < 0 || p > 2 || v < 0 || v > 1 || sp < 0 ||
-            sp > 1)
+            sp > 2 || od < 0 || od > 1)
             continue;
         *G = g;
         *form = p;
         *code = v;
         *split = sp;
+        *order = od;
         found = true;
     }
     return found;
@@ -1175,7 +1194,6 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-        // the adjoint tiles want 5 blocks of ~42 KB shared memory per SM
         // the adjoint kernels want 5 blocks of ~42 KB shared memory per SM;
         // the forward kernels (14 KB per block) keep the default split, which
         // leaves L1 room for their read-only coefficient loads (the maximum
@@ -1198,6 +1216,18 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
         for (const void* f : big_smem)
             CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     (int)cudaSharedmemCarveoutMaxShared));
+        // the pipelined forward kernels hold two ~41 KB stages per block and
+        // read nothing through L1 but the 1/r arrays
+        const void* pipe[] = {(const void*)k_fwd_vel_pipe<1>, (const void*)k_fwd_vel_pipe<kGroup>,
+                              (const void*)k_fwd_stress_pipe<1>,
+                              (const void*)k_fwd_stress_pipe<kGroup>};
+        m->pipe_blocks = 1 << 30;
+        for (const void* f : pipe) {
+            CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, 0));
+            m->pipe_blocks = std::min(m->pipe_blocks, nb * sms);
+        }
         // both forward variants are bounded to 5 blocks of 128 threads; the
         // smaller of their counts serves both
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_persist<1, 0>, kThreads, 0));
@@ -1493,8 +1523,21 @@ bh_status bh_set_option(bh_model* m, const char* key, double value)
             return fail(m, BH_ERR_UNSUPPORTED, "cooperative launch not available");
         m->persistent = (int)value;
     } else if (k == "split") {
-        if (value != 0.0 && value != 1.0) return fail(m, BH_ERR_INVALID_ARG, "split must be 0 or 1");
+        if (value != 0.0 && value != 1.0 && value != 2.0)
+            return fail(m, BH_ERR_INVALID_ARG, "split must be 0, 1 or 2");
+        if (value == 2.0 && m->pipe_blocks < 1)
+            return fail(m, BH_ERR_UNSUPPORTED, "the pipelined kernels do not fit an SM");
         m->split = (int)value;
+    } else if (k == "tile_order") {
+        if (value != 0.0 && value != 1.0)
+            return fail(m, BH_ERR_INVALID_ARG, "tile_order must be 0 or 1");
+        if ((int)value == m->tile_order) return BH_OK;
+        m->tile_order = (int)value;
+        return build_tiles(m);
+    } else if (k == "pipe_grid") {
+        if (value < 0.0 || value > 1e6 || value != std::floor(value))
+            return fail(m, BH_ERR_INVALID_ARG, "pipe_grid must be an integer in [0, 1e6]");
+        m->pipe_grid = (int)value;
     } else if (k == "tile_code") {
         if (value != 0.0 && value != 1.0)
             return fail(m, BH_ERR_INVALID_ARG, "tile_code must be 0 or 1");
@@ -1539,6 +1582,9 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "group") *value = m->G;
     else if (k == "tile_code") *value = m->tile_code;
     else if (k == "split") *value = m->split;
+    else if (k == "pipe_grid") *value = m->pipe_grid;
+    else if (k == "tile_order") *value = m->tile_order;
+    else if (k == "pipe_blocks") *value = m->pipe_blocks;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
                      (kFwdPlanes + kAdjPlanes + 2.0 * m->hist_slots) +
@@ -1575,12 +1621,13 @@ bh_status bh_checkpoint_plan(int nseg, int nsnap, int* actions, int max_actions,
 }
 
 bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr, int window_pitch,
-                         int nshots, int* group, int* form, int* tile_code, int* split)
+                         int nshots, int* group, int* form, int* tile_code, int* split,
+                         int* tile_order)
 {
-    if (!cache_path || !gpu_name || !group || !form || !tile_code || !split)
+    if (!cache_path || !gpu_name || !group || !form || !tile_code || !split || !tile_order)
         return fail(nullptr, BH_ERR_INVALID_ARG, "bh_tune_lookup: NULL argument");
     if (!tune_lookup(cache_path, tune_key(gpu_name, nr, window_pitch, nshots), group, form,
-                     tile_code, split))
+                     tile_code, split, tile_order))
         return fail(nullptr, BH_ERR_STATE, "bh_tune_lookup: no entry for this key");
     return BH_OK;
 }
@@ -1596,9 +1643,11 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
     const bool coop = std::min(std::min(m->fwd_blocks, m->adj_blocks),
                                std::min(m->fwd_blocks_g, m->adj_blocks_g)) >= 1;
     int bestG = m->G, bestForm = m->persistent, bestCode = m->tile_code, bestSplit = m->split;
+    int bestOrder = m->tile_order;
     double best_ms = -1.0;
     std::string how = "cached";
-    if (!(cache_path && tune_lookup(cache_path, key, &bestG, &bestForm, &bestCode, &bestSplit))) {
+    if (!(cache_path &&
+          tune_lookup(cache_path, key, &bestG, &bestForm, &bestCode, &bestSplit, &bestOrder))) {
         const int S = std::min(std::min(steps, m->grid.nt), m->hist_slots - 1);
         if (S < 1) return fail(m, BH_ERR_STATE, "history window too short to time a step");
         // inputs the timed runs read: a zero wavelet and residual
@@ -1640,9 +1689,14 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
                 if (fit > 0 && fit < ng) forms.push_back(2);
             }
             for (int f : forms)
-            for (int sp = 0; sp <= (f == 0 ? 1 : 0); ++sp) {
+            for (int sp = 0; sp <= (f != 0 ? 0 : code == 1 && m->pipe_blocks > 0 ? 2 : 1); ++sp)
+            for (int od = 0; od <= (f != 0 ? 0 : 1) && st == BH_OK; ++od) {
                 m->persistent = f;
                 m->split = sp;
+                if (od != m->tile_order) {
+                    m->tile_order = od;
+                    if ((st = build_tiles(m)) != BH_OK) break;
+                }
                 float ms = 0.f;
                 long long runs = 0;
                 // the best of three runs after a warm-up
@@ -1659,8 +1713,8 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
                 }
                 ms = best_rep;
                 if (st != BH_OK) break;
-                snprintf(line, sizeof line, "%scode=%d G=%d form=%d split=%d %.3f ms",
-                         log.empty() ? "" : "; ", code, g, f, sp, ms);
+                snprintf(line, sizeof line, "%scode=%d G=%d form=%d split=%d order=%d %.3f ms",
+                         log.empty() ? "" : "; ", code, g, f, sp, od, ms);
                 log += line;
                 if (best_ms < 0 || ms < best_ms) {
                     best_ms = ms;
@@ -1668,6 +1722,7 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
                     bestForm = f;
                     bestCode = code;
                     bestSplit = sp;
+                    bestOrder = od;
                 }
             }
             if (st != BH_OK) break;
@@ -1683,20 +1738,26 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
         if (cache_path) {
             std::ofstream f(cache_path, std::ios::app);
             if (f) f << key << " " << bestG << " " << bestForm << " " << bestCode << " "
-                     << bestSplit << " " << best_ms << " ms/" << S << "-step-pair\n";
+                     << bestSplit << " " << bestOrder << " " << best_ms << " ms/" << S
+                     << "-step-pair\n";
         }
     }
     BH_TRY(set_group(m, bestG));
     if (bestForm != 0 && !coop) bestForm = 0;
     m->persistent = bestForm;
     m->tile_code = bestCode;
-    m->split = bestSplit;
+    m->split = (bestSplit == 2 && m->pipe_blocks < 1) ? 1 : bestSplit;
+    if (bestOrder != m->tile_order) {
+        m->tile_order = bestOrder;
+        BH_TRY(build_tiles(m));
+    }
     m->have_forward = m->have_gradient = false;
     ++m->state_version;
     if (choice && choice_len > 0) {
         std::string txt = "group " + std::to_string(bestG) + ", form " +
                           std::to_string(bestForm) + ", tile code " + std::to_string(bestCode) +
-                          ", split " + std::to_string(bestSplit) + " (" + how + ")";
+                          ", split " + std::to_string(bestSplit) + ", tile order " +
+                          std::to_string(bestOrder) + " (" + how + ")";
         snprintf(choice, (size_t)choice_len, "%s", txt.c_str());
     }
     return BH_OK;

@@ -20,17 +20,21 @@ def lookup():
 def test_cache_lookup(lookup, tmp_path):
     p = tmp_path / "cache.txt"
     p.write_text("# comment line\n"
-                 "NVIDIA_GB300|nr240|P2016|shots64 32 0 0 1 12.5 ms/32-step-pair\n"
-                 "NVIDIA_GB300|nr240|P1600|shots1 1 2 1 0 3.1 ms/32-step-pair\n"
+                 "NVIDIA_GB300|nr240|P2016|shots64 32 0 0 1 0 12.5 ms/32-step-pair\n"
+                 "NVIDIA_GB300|nr240|P1600|shots1 1 2 1 0 1 3.1 ms/32-step-pair\n"
                  "garbage line\n"
-                 "NVIDIA_GB300|nr240|P2016|shots64 99 0 0 0 bad group\n"
-                 "NVIDIA_GB300|nr240|P2016|shots64 16 2 5 0 bad tile code\n"
-                 "NVIDIA_GB300|nr240|P2016|shots64 16 2 1 3 bad split\n"
+                 "NVIDIA_GB300|nr240|P2016|shots64 99 0 0 0 0 bad group\n"
+                 "NVIDIA_GB300|nr240|P2016|shots64 16 2 5 0 0 bad tile code\n"
+                 "NVIDIA_GB300|nr240|P2016|shots64 16 2 1 3 0 bad split\n"
+                 "NVIDIA_GB300|nr240|P2016|shots64 16 2 1 1 2 bad order\n"
+                 "NVIDIA_GB300|nr240|P2016|shots64 16 2 1 1 11.0 missing order\n"
                  "NVIDIA_GB300|nr240|P2016|shots64 16 2 1 11.0 missing split\n"
-                 "NVIDIA_GB300|nr240|P2016|shots64 16 0 1 1 11.0 ms/32-step-pair\n")
+                 "NVIDIA_GB300|nr240|P2016|shots64 16 0 1 1 1 11.0 ms/32-step-pair\n"
+                 "NVIDIA_GB300|nr240|P2048|shots16 16 0 1 2 0 5.0 ms/32-step-pair\n")
     # blanks in the GPU name become underscores; the last valid line wins
-    assert lookup(str(p), "NVIDIA GB300", 240, 2016, 64) == (16, 0, 1, 1)
-    assert lookup(str(p), "NVIDIA GB300", 240, 1600, 1) == (1, 2, 1, 0)
+    assert lookup(str(p), "NVIDIA GB300", 240, 2016, 64) == (16, 0, 1, 1, 1)
+    assert lookup(str(p), "NVIDIA GB300", 240, 1600, 1) == (1, 2, 1, 0, 1)
+    assert lookup(str(p), "NVIDIA GB300", 240, 2048, 16) == (16, 0, 1, 2, 0)
     # other shapes, other GPUs, a missing file: no entry
     assert lookup(str(p), "NVIDIA GB300", 240, 2016, 63) is None
     assert lookup(str(p), "NVIDIA B200", 240, 2016, 64) is None
@@ -45,8 +49,8 @@ def test_committed_cache_is_well_formed(lookup):
     for line in open(TUNE_CACHE):
         if not line.strip() or line.startswith("#"):
             continue
-        key, g, f, v, sp = line.split()[:5]
+        key, g, f, v, sp, od = line.split()[:6]
         gpu, nr, P, shots = key.split("|")
         assert 1 <= int(g) <= 32 and int(f) in (0, 1, 2) and int(v) in (0, 1)
-        assert int(sp) in (0, 1)
+        assert int(sp) in (0, 1, 2) and int(od) in (0, 1)
         assert lookup(TUNE_CACHE, gpu, int(nr[2:]), int(P[1:]), int(shots[5:])) is not None
