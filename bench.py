@@ -85,11 +85,15 @@ def all_array_bytes_per_cell(kernel: str, s: float, with_rho: bool, hist: float 
         "adj_stress": 16 + 16 + 12 + 8 + 48 + 24 + 16 * s + (8 + 32 if with_rho else 0),
         # 2 adjoint velocities read, 4 adjoint stresses r+w, 2 buoyancies, 4 memories
         "adj_vel": 8 + 32 + 8 + 16 * s,
+        # a fused forward step: the six fields read and written once, five
+        # coefficients, history write, 8 memories r+w in their strips
+        "fwd_step": 48 + 20 + 8 * hist + 32 * s,
     }[kernel]
 
 
 # persistent kernels run both half-steps of every time step of a shot group
 PERSIST_PARTS = {"fwd_persist": ("fwd_vel", "fwd_stress"), "adj_persist": ("adj_stress", "adj_vel"),
+                 "fwd_step": ("fwd_vel", "fwd_stress"),
                  "fwd_vel": ("fwd_vel",), "fwd_stress": ("fwd_stress",),
                  "adj_stress": ("adj_stress",), "adj_vel": ("adj_vel",)}
 
@@ -451,6 +455,8 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
         hf = hist_frac if k.startswith("fwd") else 1.0
         if model == "survey":
             return sum(survey_bytes_per_cell(p, s, shared, hf) for p in PERSIST_PARTS[k])
+        if k == "fwd_step":
+            return all_array_bytes_per_cell(k, s, with_rho, hf)
         return sum(all_array_bytes_per_cell(p, s, with_rho, hf) for p in PERSIST_PARTS[k])
 
     kernels = {}

@@ -272,7 +272,9 @@ enum {
     BH_KERNEL_ADJ_VEL = 3,     /* transposed velocity step                     */
     BH_KERNEL_FWD_PERSIST = 4, /* cooperative forward: all steps of a run       */
     BH_KERNEL_ADJ_PERSIST = 5, /* cooperative adjoint + correlation of a run    */
-    BH_KERNEL_COUNT = 6
+    BH_KERNEL_FWD_STEP = 6,    /* one whole forward step of a shot group with
+                                  fused interior steps ("split" 3)          */
+    BH_KERNEL_COUNT = 7
 };
 bh_status bh_profile_enable(bh_model* model, int every);
 bh_status bh_profile_read(bh_model* model, int kernel, double* total_ms, long* launches);
@@ -329,7 +331,13 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
  *                     SM, each block copying its next tile while it
  *                     computes the current one).  All give bit for bit the
  *                     same results.  BH_ERR_UNSUPPORTED for 2 when the
- *                     pipelined kernels do not fit an SM.
+ *                     pipelined kernels do not fit an SM.  3: as 1, and
+ *                     with "tile_code" 1 every forward step of the interior
+ *                     tiles is one launch (both half-steps of a tile in one
+ *                     block, velocities recomputed on the stress stencil's
+ *                     halo); the six forward fields then alternate between
+ *                     two buffers (6 planes per shot more device memory).
+ *                     The same results bit for bit.
  *   "pipe_grid"       cap on the blocks of a pipelined launch (default 0:
  *                     as many as fit the SMs); a small cap makes every
  *                     block walk many tiles (a test knob).
@@ -363,7 +371,7 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
  * the shot group sizes 1, 2, 4, ... up to min(32, nshots) (and nshots
  * itself) and the launch forms of the "persistent" option that differ for
  * that grouping (and, for one launch per half-step, "split" 0 and 1, and 2
- * with tile code 1, and both "tile_order" values); each
+ * and 3 with tile code 1, and both "tile_order" values); each
  * is timed four times over `steps` forward and `steps` adjoint steps of
  * every shot (CUDA events on the model's stream, the best of the last three
  * kept) and the fastest is applied (options "tile_code", "group",

@@ -30,7 +30,8 @@ EXPORTS = ("bh_model_create", "bh_model_destroy", "bh_set_model", "bh_forward",
            "bh_tune_lookup")
 TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.txt")
 NOALLOC_MAX_SAMPLES = 33554432
-KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel", "fwd_persist", "adj_persist")
+KERNELS = ("fwd_vel", "fwd_stress", "adj_stress", "adj_vel", "fwd_persist", "adj_persist",
+           "fwd_step")
 
 
 class BhError(RuntimeError):

@@ -476,7 +476,8 @@ struct __align__(16) FwdSmem {
 // stresses and the own-node inputs (shared by every kernel that runs it, so
 // that they agree bit for bit).
 template <int PM>
-__device__ __forceinline__ void fwd_vel_core(const WinK& g, const StateK& S, float* hist0,
+__device__ __forceinline__ void fwd_vel_core(const WinK& g, const StateK& S, ptrdiff_t fout,
+                                             float* hist0,
                                              const Own& o, bool pml, const V4& vr0, const V4& vz0,
                                              const V4& br, const V4& bz, const V4& q0,
                                              const V4& q1, const V4& q2, const V4& q3, float ivr,
@@ -527,7 +528,7 @@ __device__ __forceinline__ void fwd_vel_core(const WinK& g, const StateK& S, flo
             }
             vr[e] = vr0.v[e] + g.dt * br.v[e] * (d_trr + d_trz + hoop);
         }
-        st4(S.vr + o.c, o.j, g.nz, vr);
+        st4(S.vr + fout + o.c, o.j, g.nz, vr);
         if (pml) {
             if (ari != 0.f) st4(S.psi_w[0] + o.c, o.j, g.nz, w0);
             st4(S.psi_w[1] + o.c, o.j, g.nz, w1);
@@ -557,7 +558,7 @@ __device__ __forceinline__ void fwd_vel_core(const WinK& g, const StateK& S, flo
             }
             vz[e] = vz0.v[e] + g.dt * bz.v[e] * (d_trz + d_tzz + hoop);
         }
-        st4(S.vz + o.c, o.j, g.nz, vz);
+        st4(S.vz + fout + o.c, o.j, g.nz, vz);
         if (pml) {
             if (arh != 0.f) st4(S.psi_w[2] + o.c, o.j, g.nz, w2);
             st4(S.psi_w[3] + o.c, o.j, g.nz, w3);
@@ -576,7 +577,8 @@ __device__ __forceinline__ void fwd_vel_core(const WinK& g, const StateK& S, flo
 // one round trip to L2.  hist0 (or null): history slot receiving v^{n-1/2}.
 template <int PM>
 __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                             float* hist0, int i0, int j0, int flags,
+                                             ptrdiff_t fin, ptrdiff_t fout, float* hist0, int i0,
+                                             int j0, int flags,
                                              const BarK* bar, unsigned& epoch, FwdSmem& sm)
 {
     Tile &s_rr = sm.a, &s_tt = sm.b, &s_rz = sm.c, &s_zz = sm.d;
@@ -587,21 +589,21 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
     __syncthreads();
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const Slot sl = slot_of(it, i0, j0, g);
-        stage_async<EVEN>(s_rr, S.trr, sl);
-        stage_async<EVEN>(s_tt, S.ttt, sl);
-        stage_async<ODD>(s_rz, S.trz, sl);
-        stage_async<EVEN>(s_zz, S.tzz, sl);
+        stage_async<EVEN>(s_rr, S.trr + fin, sl);
+        stage_async<EVEN>(s_tt, S.ttt + fin, sl);
+        stage_async<ODD>(s_rz, S.trz + fin, sl);
+        stage_async<EVEN>(s_zz, S.tzz + fin, sl);
     }
     if (pml) stage_prof(sm.pf, C, g, i0, j0);
     // own-node inputs, in flight together with the copies
     if (o.live) {
         ivr = __ldg(C.inv_r_int + o.i);
         ivh = __ldg(C.inv_r_half + o.i);
-        vz0 = ld4cg(S.vz + o.c);
+        vz0 = ld4cg(S.vz + fin + o.c);
         bz = ld4g(C.w_bvz + o.cw);
         if (flags & TILE_LAST) patch4(bz, o.j, g.nz - 1, bvz_at(C, g, o.i, g.nz - 1));
         if (o.i >= 1) {
-            vr0 = ld4cg(S.vr + o.c);
+            vr0 = ld4cg(S.vr + fin + o.c);
             br = ld4g(C.w_bvr + o.cw);
         }
         if (pml) {
@@ -621,14 +623,15 @@ __device__ __forceinline__ void fwd_vel_tile(const WinK& g, const CoefK& C, cons
         }
     }
     __syncthreads();
-    fwd_vel_core<PM>(g, S, hist0, o, pml, vr0, vz0, br, bz, q0, q1, q2, q3, ivr, ivh, s_rr, s_tt,
+    fwd_vel_core<PM>(g, S, fout, hist0, o, pml, vr0, vz0, br, bz, q0, q1, q2, q3, ivr, ivh, s_rr, s_tt,
                      s_rz, s_zz, &sm.pf, bar, epoch);
 }
 
 // The arithmetic of the stress half-step of one tile, from the staged
 // velocities and the own-node inputs (shared by every kernel that runs it).
 template <int PM>
-__device__ __forceinline__ void fwd_stress_core(const WinK& g, const StateK& S, const SrcRecK& q,
+__device__ __forceinline__ void fwd_stress_core(const WinK& g, const StateK& S, ptrdiff_t fout,
+                                                const SrcRecK& q,
                                                 int n, bool record, float* hist, const Own& o,
                                                 bool pml, const V4& t_rr, const V4& t_tt,
                                                 const V4& t_zz, const V4& t_rz, const V4& lm,
@@ -685,9 +688,9 @@ __device__ __forceinline__ void fwd_stress_core(const WinK& g, const StateK& S, 
                 if (k >= 0) q.seis[(size_t)k * q.nt + n] = (trr[e] + ttt[e] + tzz[e]) * (1.f / 3.f);
             }
         }
-        st4(S.trr + o.c, o.j, g.nz, trr);
-        st4(S.ttt + o.c, o.j, g.nz, ttt);
-        st4(S.tzz + o.c, o.j, g.nz, tzz);
+        st4(S.trr + fout + o.c, o.j, g.nz, trr);
+        st4(S.ttt + fout + o.c, o.j, g.nz, ttt);
+        st4(S.tzz + fout + o.c, o.j, g.nz, tzz);
         if (pml) {
             if (arh != 0.f) st4(S.psi_w[4] + o.c, o.j, g.nz, w4);
             st4(S.psi_w[5] + o.c, o.j, g.nz, w5);
@@ -724,7 +727,7 @@ __device__ __forceinline__ void fwd_stress_core(const WinK& g, const StateK& S, 
             }
             trz[e] = t_rz.v[e] + g.dt * mh.v[e] * (d_vrz + d_vzr);
         }
-        st4(S.trz + o.c, o.j, g.nz, trz);
+        st4(S.trz + fout + o.c, o.j, g.nz, trz);
         if (pml) {
             st4(S.psi_w[6] + o.c, o.j, g.nz, w6);
             if (ari != 0.f) st4(S.psi_w[7] + o.c, o.j, g.nz, w7);
@@ -744,7 +747,8 @@ __device__ __forceinline__ void fwd_stress_core(const WinK& g, const StateK& S, 
 // recording, and the store of v^{n+1/2} for the adjoint.
 template <int PM>
 __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, const StateK& S,
-                                                const SrcRecK& q, int n, bool record,
+                                                ptrdiff_t fin, ptrdiff_t fout, const SrcRecK& q,
+                                                int n, bool record,
                                                 float* hist, int i0, int j0, int flags,
                                                 const BarK* bar, unsigned& epoch, FwdSmem& sm)
 {
@@ -754,8 +758,8 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     __syncthreads();
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const Slot sl = slot_of(it, i0, j0, g);
-        stage_async<ODD>(s_vr, S.vr, sl);
-        stage_async<EVEN>(s_vz, S.vz, sl);
+        stage_async<ODD>(s_vr, S.vr + fout, sl);
+        stage_async<EVEN>(s_vz, S.vz + fout, sl);
     }
     if (pml) stage_prof(sm.pf, C, g, i0, j0);
     V4 t_rr{}, t_tt{}, t_zz{}, lm{}, mu{}, t_rz{}, mh{};
@@ -763,13 +767,13 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
     V4 q4{}, q5{}, q6{}, q7{};
     if (o.live) {
         ivh = __ldg(C.inv_r_half + o.i);
-        t_rr = ld4cg(S.trr + o.c);
-        t_tt = ld4cg(S.ttt + o.c);
-        t_zz = ld4cg(S.tzz + o.c);
+        t_rr = ld4cg(S.trr + fin + o.c);
+        t_tt = ld4cg(S.ttt + fin + o.c);
+        t_zz = ld4cg(S.tzz + fin + o.c);
         lm = ld4g(C.w_lam + o.cw);
         mu = ld4g(C.w_mu + o.cw);
         if (o.i >= 1) {
-            t_rz = ld4cg(S.trz + o.c);
+            t_rz = ld4cg(S.trz + fin + o.c);
             mh = ld4g(C.w_muh + o.cw);
             if (flags & TILE_LAST) patch4(mh, o.j, g.nz - 1, muh_at(C, g, o.i, g.nz - 1));
         }
@@ -790,7 +794,7 @@ __device__ __forceinline__ void fwd_stress_tile(const WinK& g, const CoefK& C, c
         }
     }
     __syncthreads();
-    fwd_stress_core<PM>(g, S, q, n, record, hist, o, pml, t_rr, t_tt, t_zz, t_rz, lm, mu, mh, q4,
+    fwd_stress_core<PM>(g, S, fout, q, n, record, hist, o, pml, t_rr, t_tt, t_zz, t_rz, lm, mu, mh, q4,
                         q5, q6, q7, ivh, s_vr, s_vz, &sm.pf, bar, epoch);
 }
 
@@ -1388,6 +1392,9 @@ struct ShotK {
     SrcRecK q;
     AdjK a;
     float* hist;    // history window: slot k = v_r, v_z planes of v^{hist_n0 + k - 1/2}
+    // second forward field buffer (fused steps): field f of buffer 1 is
+    // Sf.f + swap; the C-PML memories exist once
+    long long swap;
 };
 
 // The shots of one launch travel in the kernel's parameter space (constant
@@ -1419,26 +1426,39 @@ __device__ __forceinline__ const ShotK& shot_of(const ShotTable<N>& T, int4 tk)
     return T.s[N == 1 ? 0 : tk.x];
 }
 
+// pp: -1 the fields are updated in place (buffer 0); 0 / 1: read from
+// buffer pp, written to the other (the launches of a fused step)
+__device__ __forceinline__ ptrdiff_t field_in(const ShotK& sh, int pp)
+{
+    return pp == 1 ? (ptrdiff_t)sh.swap : 0;
+}
+__device__ __forceinline__ ptrdiff_t field_out(const ShotK& sh, int pp)
+{
+    return pp == 0 ? (ptrdiff_t)sh.swap : 0;
+}
+
 template <int N, int PM>
 __device__ __forceinline__ void run_fwd_vel(const RunK& r, const ShotTable<N>& T, int n, int t,
-                                            const BarK* bar, unsigned& epoch, FwdSmem& sm)
+                                            const BarK* bar, unsigned& epoch, FwdSmem& sm,
+                                            int pp = -1)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     float* h0 = (r.hist_n0 >= 0 && n == r.hist_n0) ? hist_slot(sh, 0) : nullptr;
-    fwd_vel_tile<PM>(sh.g, sh.C, sh.Sf, h0, tk.y, tk.z, tk.w, bar, epoch, sm);
+    fwd_vel_tile<PM>(sh.g, sh.C, sh.Sf, field_in(sh, pp), field_out(sh, pp), h0, tk.y, tk.z,
+                     tk.w, bar, epoch, sm);
 }
 
 template <int N, int PM>
 __device__ __forceinline__ void run_fwd_stress(const RunK& r, const ShotTable<N>& T, int n,
                                                int t, const BarK* bar, unsigned& epoch,
-                                               FwdSmem& sm)
+                                               FwdSmem& sm, int pp = -1)
 {
     const int4 tk = r.tiles[t];
     const ShotK& sh = shot_of(T, tk);
     float* h = r.hist_n0 >= 0 ? hist_slot(sh, n - r.hist_n0 + 1) : nullptr;
-    fwd_stress_tile<PM>(sh.g, sh.C, sh.Sf, sh.q, n, r.record != 0, h, tk.y, tk.z, tk.w, bar,
-                        epoch, sm);
+    fwd_stress_tile<PM>(sh.g, sh.C, sh.Sf, field_in(sh, pp), field_out(sh, pp), sh.q, n,
+                        r.record != 0, h, tk.y, tk.z, tk.w, bar, epoch, sm);
 }
 
 // forward tiles of either code variant (V 0: one path, 1: per tile class)
@@ -1553,23 +1573,23 @@ __global__ void __launch_bounds__(kThreads) k_adj_vel(RunK r, int n,
 // per-class tile code as the kernels above with the forward tile code 1.
 template <int N, int PM>
 __global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 8 : 5)
-    k_fwd_vel_c(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+    k_fwd_vel_c(RunK r, int n, int pp, const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_fwd_vel<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    run_fwd_vel<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm, pp);
     pdl_launch_dependents();
 }
 
 template <int N, int PM>
 __global__ void __launch_bounds__(kThreads, PM == PM_INTERIOR ? 6 : 5)
-    k_fwd_stress_c(RunK r, int n, const __grid_constant__ ShotTable<N> T)
+    k_fwd_stress_c(RunK r, int n, int pp, const __grid_constant__ ShotTable<N> T)
 {
     __shared__ FwdSmem sm;
     pdl_wait();
     unsigned epoch = 0;
-    run_fwd_stress<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm);
+    run_fwd_stress<N, PM>(r, T, n, blockIdx.x, nullptr, epoch, sm, pp);
     pdl_launch_dependents();
 }
 
@@ -1723,7 +1743,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         }
         float* h0 = (r.hist_n0 >= 0 && n == r.hist_n0) ? hist_slot(sh, 0) : nullptr;
         const V4 zero{};
-        fwd_vel_core<PM_INTERIOR>(g, sh.Sf, h0, o, false, vr0, vz0, br, bz, zero, zero, zero,
+        fwd_vel_core<PM_INTERIOR>(g, sh.Sf, 0, h0, o, false, vr0, vz0, br, bz, zero, zero, zero,
                                   zero, ivr, ivh, b.a, b.b, b.c, b.d, nullptr, nullptr, epoch);
         __syncthreads();  // stage k & 1 is refilled at the next iteration
     }
@@ -1771,11 +1791,230 @@ __global__ void __launch_bounds__(kThreads, 4)
         }
         float* h = r.hist_n0 >= 0 ? hist_slot(sh, n - r.hist_n0 + 1) : nullptr;
         const V4 zero{};
-        fwd_stress_core<PM_INTERIOR>(g, sh.Sf, sh.q, n, r.record != 0, h, o, false, t_rr, t_tt,
+        fwd_stress_core<PM_INTERIOR>(g, sh.Sf, 0, sh.q, n, r.record != 0, h, o, false, t_rr, t_tt,
                                      t_zz, t_rz, lm, mu, mh, zero, zero, zero, zero, ivh, b.a,
                                      b.b, nullptr, nullptr, epoch);
         __syncthreads();
     }
+    pdl_launch_dependents();
+}
+
+// ------------------------------------------------- fused interior steps
+//
+// One launch per time step over the interior tiles (option "split" 3): both
+// half-steps of Eq. 2 for a tile.  The four stresses tau^n are staged with a
+// 4-node halo (rows i0-4 .. i0+19, columns j0-8 .. j0+39), v^{n-1/2} and the
+// buoyancies with the usual 2-node halo.  The block first updates v on the
+// whole 2-node-halo region (the nodes its stress stencils read) and keeps it
+// in shared memory, then runs the stress half-step of its own nodes, so the
+// wavefields cross HBM once per step instead of once per half-step.
+// Neighbouring tiles recompute each other's halo velocities, which is why
+// the fields ping-pong: the launch reads buffer pp and writes buffer 1 - pp,
+// and the C-PML tiles of the same step run the two half-step launches on
+// the same buffers.  An interior tile's 2-node-halo region holds no C-PML
+// node and lies inside the window (the layers are between it and every
+// edge but the axis), so its halo velocities need no layer state and no
+// zero edge; the axis mirror is applied to the updated velocities.  The
+// arithmetic is that of the half-step kernels, node for node.
+
+constexpr int kH4 = 4;
+constexpr int kSR4 = kTR + 2 * kH4;  // 24 staged rows
+constexpr int kSZ4 = kTZ + 16;       // 48 staged columns, j0-8 .. j0+39
+constexpr int kQ4 = kSZ4 / 4;
+typedef float Tile4[kSR4][kSZ4];
+
+__device__ __forceinline__ V4 lds4(const Tile4& s, int rr, int cc)
+{
+    const float4 t = *reinterpret_cast<const float4*>(&s[rr][cc]);
+    return V4{{t.x, t.y, t.z, t.w}};
+}
+
+__device__ __forceinline__ V12 lds12(const Tile4& s, int rr, int cc)
+{
+    V12 r;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 t = *reinterpret_cast<const float4*>(&s[rr][cc + 4 * k]);
+        r.v[4 * k] = t.x;
+        r.v[4 * k + 1] = t.y;
+        r.v[4 * k + 2] = t.z;
+        r.v[4 * k + 3] = t.w;
+    }
+    return r;
+}
+
+// the slot geometry of slot_of for the 4-node-halo staging
+__device__ __forceinline__ Slot slot4_of(int it, int i0, int j0, const WinK& g)
+{
+    Slot s;
+    s.rr = it / kQ4;
+    s.cq = 4 * (it - s.rr * kQ4);
+    const int i = i0 - kH4 + s.rr, j = j0 - 8 + s.cq;
+    const bool zin = j >= 0 && j < g.nz;
+    s.zlim = zin ? min(4, g.nz - j) : 0;
+    const int ie = i < 0 ? -1 - i : i;
+    const int io = i < 0 ? -i : i;
+    s.neg = i < 0;
+    s.off_e = (zin && ie < g.nr) ? ie * g.P + j : -1;
+    s.off_o = (zin && io >= 1 && io < g.nr) ? io * g.P + j : -1;
+    s.offw_e = s.offw_o = -1;
+    return s;
+}
+
+template <int KIND>
+__device__ __forceinline__ void stage4_async(Tile4& t, const float* __restrict__ f, const Slot& s)
+{
+    const int off = KIND == EVEN ? s.off_e : s.off_o;
+    const float* src = f + (off >= 0 ? off : 0);
+    const unsigned bytes = off >= 0 ? 4u * (unsigned)s.zlim : 0u;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(&t[s.rr][s.cq])),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+
+struct __align__(16) StepSmem {
+    Tile4 rr, tt, zz, rz;  // tau^n
+    Tile vr, vz;           // v^{n-1/2}, replaced by v^{n+1/2}
+    Tile br, bz;           // buoyancy at the v_r and v_z nodes
+};
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 6)
+    k_fwd_step(RunK r, int n, int pp, const __grid_constant__ ShotTable<N> T)
+{
+    __shared__ StepSmem sm;
+    pdl_wait();
+    const int4 tk = r.tiles[blockIdx.x];
+    const ShotK& sh = shot_of(T, tk);
+    const WinK& g = sh.g;
+    const CoefK& C = sh.C;
+    const StateK& S = sh.Sf;
+    const ptrdiff_t fin = field_in(sh, pp), fout = field_out(sh, pp);
+    const int i0 = tk.y, j0 = tk.z;
+    const Own o = own_of(g, i0, j0);
+    for (int it = tid_of(); it < kSR4 * kQ4; it += kThreads) {
+        const Slot sl = slot4_of(it, i0, j0, g);
+        stage4_async<EVEN>(sm.rr, S.trr + fin, sl);
+        stage4_async<EVEN>(sm.tt, S.ttt + fin, sl);
+        stage4_async<EVEN>(sm.zz, S.tzz + fin, sl);
+        stage4_async<ODD>(sm.rz, S.trz + fin, sl);
+    }
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_async<ODD>(sm.vr, S.vr + fin, sl);
+        stage_async<EVEN>(sm.vz, S.vz + fin, sl);
+        stage_async<ABS, true>(sm.br, C.w_bvr, sl);
+        stage_async<EVEN, true>(sm.bz, C.w_bvz, sl);
+    }
+    // own-node inputs of the stress half-step, in flight with the copies
+    V4 lm{}, mu{}, mh{};
+    float ivh = 0.f;
+    if (o.live) {
+        ivh = __ldg(C.inv_r_half + o.i);
+        lm = ld4g(C.w_lam + o.cw);
+        mu = ld4g(C.w_mu + o.cw);
+        if (o.i >= 1) mh = ld4g(C.w_muh + o.cw);
+    }
+    async_wait_all();
+    if (i0 < kH4) {
+        for (int it = tid_of(); it < kSR4 * kQ4; it += kThreads) {
+            const Slot sl = slot4_of(it, i0, j0, g);
+            if (sl.neg && sl.off_o >= 0) {
+                float4* q = reinterpret_cast<float4*>(&sm.rz[sl.rr][sl.cq]);
+                float4 v = *q;
+                v.x = -v.x;
+                v.y = -v.y;
+                v.z = -v.z;
+                v.w = -v.w;
+                *q = v;
+            }
+        }
+    }
+    __syncthreads();
+    // v^{n-1/2} of the own nodes (history slot 0 of a segment's first step)
+    const bool h0 = r.hist_n0 >= 0 && n == r.hist_n0;
+    V4 vr_old{}, vz_old{};
+    if (h0) {
+        vr_old = lds4(sm.vr, o.rr, o.cc);
+        vz_old = lds4(sm.vz, o.rr, o.cc);
+    }
+    __syncthreads();
+    // ---- velocity half-step on the 2-node-halo region (rows i >= 0; the
+    // mirror rows follow), in place over this thread's slots
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const int r2 = it / kQ, c2 = 4 * (it - r2 * kQ);
+        const int i = i0 - kH + r2;
+        if (i < 0) continue;
+        const int R = r2 + (kH4 - kH), K = c2 + 4;  // the same node in the Tile4 grid
+        const V12 rz12 = lds12(sm.rz, R, K - 4);
+        const V4 rzp1 = lds4(sm.rz, R + 1, K);
+        if (i >= 1) {
+            const V4 rm2 = lds4(sm.rr, R - 2, K), rm1 = lds4(sm.rr, R - 1, K);
+            const V4 r0 = lds4(sm.rr, R, K), rp1 = lds4(sm.rr, R + 1, K);
+            const V4 tm1 = lds4(sm.tt, R - 1, K), t0 = lds4(sm.tt, R, K);
+            const V4 vr0 = lds4(sm.vr, r2, c2), br = lds4(sm.br, r2, c2);
+            const float inv_r = __ldg(C.inv_r_int + i);
+            float vr[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float d_trr = d4(r0.v[e], rm1.v[e], rp1.v[e], rm2.v[e]) * g.inv_dr;
+                float d_trz = d4(rz12.v[4 + e], rz12.v[3 + e], rz12.v[5 + e], rz12.v[2 + e]) * g.inv_dz;
+                const float hoop = 0.5f * ((rm1.v[e] - tm1.v[e]) + (r0.v[e] - t0.v[e])) * inv_r;
+                vr[e] = vr0.v[e] + g.dt * br.v[e] * (d_trr + d_trz + hoop);
+            }
+            *reinterpret_cast<float4*>(&sm.vr[r2][c2]) = make_float4(vr[0], vr[1], vr[2], vr[3]);
+        }
+        {
+            const V12 zz12 = lds12(sm.zz, R, K - 4);
+            const V4 rzm1 = lds4(sm.rz, R - 1, K), rzp2 = lds4(sm.rz, R + 2, K);
+            const V4 vz0 = lds4(sm.vz, r2, c2), bz = lds4(sm.bz, r2, c2);
+            const float inv_r = __ldg(C.inv_r_half + i);
+            float vz[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float d_trz = d4(rzp1.v[e], rz12.v[4 + e], rzp2.v[e], rzm1.v[e]) * g.inv_dr;
+                float d_tzz = d4(zz12.v[5 + e], zz12.v[4 + e], zz12.v[6 + e], zz12.v[3 + e]) * g.inv_dz;
+                const float hoop = 0.5f * (rz12.v[4 + e] + rzp1.v[e]) * inv_r;
+                vz[e] = vz0.v[e] + g.dt * bz.v[e] * (d_trz + d_tzz + hoop);
+            }
+            *reinterpret_cast<float4*>(&sm.vz[r2][c2]) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+        }
+    }
+    __syncthreads();
+    if (i0 < kH) {
+        // mirror rows of the axis tile: v_r odd (v_r[-k] = -v_r[k]), v_z even
+        // (v_z[-1-k] = v_z[k])
+        const int it = tid_of();
+        if (it < kH * kQ) {
+            const int r2 = it / kQ, c2 = 4 * (it - r2 * kQ);
+            const int i = i0 - kH + r2;  // -2 or -1
+            const float4 a = *reinterpret_cast<const float4*>(&sm.vr[r2 - 2 * i][c2]);
+            const float4 b = *reinterpret_cast<const float4*>(&sm.vz[r2 - 2 * i - 1][c2]);
+            *reinterpret_cast<float4*>(&sm.vr[r2][c2]) = make_float4(-a.x, -a.y, -a.z, -a.w);
+            *reinterpret_cast<float4*>(&sm.vz[r2][c2]) = b;
+        }
+        __syncthreads();
+    }
+    if (o.live) {
+        const V4 a = lds4(sm.vr, o.rr, o.cc), b = lds4(sm.vz, o.rr, o.cc);
+        if (o.i >= 1) st4(S.vr + fout + o.c, o.j, g.nz, a.v);
+        st4(S.vz + fout + o.c, o.j, g.nz, b.v);
+        if (h0) {
+            float* hs = hist_slot(sh, 0);
+            st4(hs + o.c, o.j, g.nz, vr_old.v);
+            st4(hs + g.nr * g.P + o.c, o.j, g.nz, vz_old.v);
+        }
+    }
+    // ---- stress half-step of the own nodes
+    const int R = o.rr + (kH4 - kH), K = o.cc + 4;
+    const V4 t_rr = lds4(sm.rr, R, K), t_tt = lds4(sm.tt, R, K), t_zz = lds4(sm.zz, R, K);
+    const V4 t_rz = lds4(sm.rz, R, K);
+    float* h = r.hist_n0 >= 0 ? hist_slot(sh, n - r.hist_n0 + 1) : nullptr;
+    const V4 zero{};
+    unsigned epoch = 0;
+    fwd_stress_core<PM_INTERIOR>(g, S, fout, sh.q, n, r.record != 0, h, o, false, t_rr, t_tt,
+                                 t_zz, t_rz, lm, mu, mh, zero, zero, zero, zero, ivh, sm.vr,
+                                 sm.vz, nullptr, nullptr, epoch);
     pdl_launch_dependents();
 }
 

@@ -24,6 +24,7 @@ thread_local std::string g_create_error;
 
 // planes (nr x P floats) of one shot's forward and adjoint state
 constexpr int kFwdPlanes = 14;  // v_r v_z trr ttt tzz trz + 8 C-PML memories
+constexpr int kFields = 6;      // v_r v_z trr ttt tzz trz
 constexpr int kAdjPlanes = 35;  // 6 fields + 2 x 8 memories + 5 Kahan pairs + 3 Hessian
 
 struct ShotHost {
@@ -61,6 +62,7 @@ struct bh_model {
     float* d_fwd = nullptr;     // per shot kFwdPlanes planes
     float* d_adj = nullptr;     // per shot kAdjPlanes planes
     float* d_wcoef = nullptr;   // 4 shifted copies x 5 coefficient planes [nr][Pw]
+    float* d_fwd2 = nullptr;    // second buffer of the 6 forward fields per shot (fused steps)
     float* d_hist = nullptr;    // per shot (L + 1) x 2 planes
     void* d_snap = nullptr;     // per slot, all shots' kFwdPlanes planes (fp32 or 16-bit)
     float* d_snap_max = nullptr;  // per slot, max |x| of every plane (16-bit snapshots)
@@ -95,7 +97,8 @@ struct bh_model {
     int tile_code = 0;          // forward tile code variant (0: one path, 1: per tile class)
     // one launch per half-step and tile class (per-class code only: the
     // adjoint, and the forward with tile code 1)
-    // 2: as 1, with the forward's interior tiles in the pipelined kernels
+    // 2: as 1, with the forward's interior tiles in the pipelined kernels;
+    // 3: as 1, with one fused launch per forward step for the interior tiles
     int split = 0;
     int pipe_blocks = 0;                  // grid of the pipelined kernels (0: unavailable)
     int pipe_grid = 0;                    // option "pipe_grid": cap on that grid (0: none)
@@ -171,7 +174,8 @@ void free_model(bh_model* m)
                     m->d_vp,    m->d_vs,
                     m->d_mask,  m->d_colcov, m->d_rprof, m->d_zprof,  m->d_recmap, m->d_fwd,
                     m->d_adj,   m->d_hist,   m->d_snap,  m->d_snap_max, m->d_tiles,  m->d_Hg,
-                    m->d_scal,  m->d_bar,    m->d_wcoef, m->d_part, m->d_tiles_cls};
+                    m->d_scal,  m->d_bar,    m->d_wcoef, m->d_part, m->d_tiles_cls,
+                    m->d_fwd2};
     for (void* b : bufs) cudaFree(b);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     delete m;
@@ -442,6 +446,7 @@ bh_status setup_shots(bh_model* m)
         C.w_bvr = wc + 3 * plw;
         C.w_bvz = wc + 4 * plw;
         float* f = m->d_fwd + (size_t)s * kFwdPlanes * pl;
+        k.swap = (long long)((m->d_fwd2 + (size_t)s * kFields * pl) - f);
         float* a = m->d_adj + (size_t)s * kAdjPlanes * pl;
         StateK* views[3] = {&k.Sf, &k.Sa[0], &k.Sa[1]};
         for (int v = 0; v < 3; ++v) {
@@ -694,6 +699,38 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
         return check_barrier(m);
     }
     const dim3 grd(r.ntiles);
+    if (V == 1 && m->split == 3) {
+        // fused steps: the fields ping-pong between the two buffers and end
+        // in buffer 0 (snapshots and the next run start there)
+        RunK ri, rp;
+        class_runs(m, grp, r, &ri, &rp);
+        for (int n = n0; n < n1; ++n) {
+            const int pp = (n - n0) & 1;
+            size_t e = prof_begin(m, BH_KERNEL_FWD_STEP, n);
+            if (ri.ntiles) {
+                BH_CUDA(m, launch_pdl(k_fwd_step<N>, dim3(ri.ntiles), blk, m->stream, ri, n, pp, T));
+                ++m->launches;
+            }
+            if (rp.ntiles) {
+                BH_CUDA(m, launch_pdl(k_fwd_vel_c<N, PM_PML>, dim3(rp.ntiles), blk, m->stream, rp,
+                                      n, pp, T));
+                BH_CUDA(m, launch_pdl(k_fwd_stress_c<N, PM_PML>, dim3(rp.ntiles), blk, m->stream,
+                                      rp, n, pp, T));
+                m->launches += 2;
+            }
+            prof_end(m, e);
+        }
+        if ((n1 - n0) & 1) {
+            const size_t pl = plane(m);
+            const int s0 = grp * m->G, ns = std::min(m->G, m->nshots - s0);
+            BH_CUDA(m, cudaMemcpy2DAsync(m->d_fwd + (size_t)s0 * kFwdPlanes * pl,
+                                         kFwdPlanes * pl * sizeof(float),
+                                         m->d_fwd2 + (size_t)s0 * kFields * pl,
+                                         kFields * pl * sizeof(float), kFields * pl * sizeof(float),
+                                         ns, cudaMemcpyDeviceToDevice, m->stream));
+        }
+        return BH_OK;
+    }
     if (V == 1 && m->split) {
         RunK ri, rp;
         class_runs(m, grp, r, &ri, &rp);
@@ -707,12 +744,12 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
                 ++m->launches;
             } else if (ri.ntiles) {
                 BH_CUDA(m, launch_pdl(k_fwd_vel_c<N, PM_INTERIOR>, dim3(ri.ntiles), blk,
-                                      m->stream, ri, n, T));
+                                      m->stream, ri, n, -1, T));
                 ++m->launches;
             }
             if (rp.ntiles) {
                 BH_CUDA(m, launch_pdl(k_fwd_vel_c<N, PM_PML>, dim3(rp.ntiles), blk, m->stream,
-                                      rp, n, T));
+                                      rp, n, -1, T));
                 ++m->launches;
             }
             prof_end(m, e);
@@ -723,12 +760,12 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
                 ++m->launches;
             } else if (ri.ntiles) {
                 BH_CUDA(m, launch_pdl(k_fwd_stress_c<N, PM_INTERIOR>, dim3(ri.ntiles), blk,
-                                      m->stream, ri, n, T));
+                                      m->stream, ri, n, -1, T));
                 ++m->launches;
             }
             if (rp.ntiles) {
                 BH_CUDA(m, launch_pdl(k_fwd_stress_c<N, PM_PML>, dim3(rp.ntiles), blk,
-                                      m->stream, rp, n, T));
+                                      m->stream, rp, n, -1, T));
                 ++m->launches;
             }
             prof_end(m, e);
@@ -825,8 +862,10 @@ bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, lon
     if (n1 <= n0) return BH_OK;
     const int ngroups = (int)m->group_ntiles.size();
     for (int grp = 0; grp < ngroups; ++grp) {
-        *runs += persistent_for(m, grp, false)
-                     ? 1
+        const int nint = m->group_nint[grp], npml = m->group_ntiles[grp] - nint;
+        *runs += persistent_for(m, grp, false) ? 1
+                 : (m->split == 3 && m->tile_code == 1)
+                     ? (long long)(n1 - n0) * ((nint > 0) + 2 * (npml > 0))
                      : 2 * (n1 - n0) * ((m->split && m->tile_code == 1) ? class_launches(m, grp) : 1);
         const bool one = m->G == 1;
         if (m->tile_code == 0) {
@@ -1044,7 +1083,7 @@ bool tune_lookup(const char* path, const std::string& key, int* G, int* form, in
         std::string rest;
         if (!(is >> k >> g >> p >> v >> sp >> od >> rest)) continue;
         if (k != key || g < 1 || g > kGroup || p < 0 || p > 2 || v < 0 || v > 1 || sp < 0 ||
-            sp > 2 || od < 0 || od > 1)
+            sp > 3 || od < 0 || od > 1)
             continue;
         *G = g;
         *form = p;
@@ -1179,6 +1218,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_colcov, (size_t)nz_global));
     CK(dalloc(&m->d_rprof, 6 * (size_t)nr));
     CK(dalloc(&m->d_fwd, (size_t)nshots * kFwdPlanes * pl));
+    CK(dalloc(&m->d_fwd2, (size_t)nshots * kFields * pl));
     CK(dalloc(&m->d_adj, (size_t)nshots * kAdjPlanes * pl));
     CK(dalloc(&m->d_wcoef, (size_t)4 * 5 * nr * m->Pw));
     CK(dalloc(&m->d_hist, (size_t)nshots * m->hist_slots * 2 * pl));
@@ -1310,6 +1350,8 @@ bh_status bh_forward(bh_model* m, const float* wavelet, float* seis)
     }
     BH_CUDA(m, cudaMemsetAsync(seis, 0, seis_per_shot * m->nshots * sizeof(float), m->stream));
     BH_CUDA(m, cudaMemsetAsync(m->d_fwd, 0, (size_t)m->nshots * kFwdPlanes * pl * sizeof(float),
+                               m->stream));
+    BH_CUDA(m, cudaMemsetAsync(m->d_fwd2, 0, (size_t)m->nshots * kFields * pl * sizeof(float),
                                m->stream));
     // sweep once, recording: take the schedule's first snapshots on the way
     // through the segments, then store the tail's history as it goes (all of
@@ -1523,8 +1565,8 @@ bh_status bh_set_option(bh_model* m, const char* key, double value)
             return fail(m, BH_ERR_UNSUPPORTED, "cooperative launch not available");
         m->persistent = (int)value;
     } else if (k == "split") {
-        if (value != 0.0 && value != 1.0 && value != 2.0)
-            return fail(m, BH_ERR_INVALID_ARG, "split must be 0, 1 or 2");
+        if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+            return fail(m, BH_ERR_INVALID_ARG, "split must be 0, 1, 2 or 3");
         if (value == 2.0 && m->pipe_blocks < 1)
             return fail(m, BH_ERR_UNSUPPORTED, "the pipelined kernels do not fit an SM");
         m->split = (int)value;
@@ -1689,8 +1731,9 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
                 if (fit > 0 && fit < ng) forms.push_back(2);
             }
             for (int f : forms)
-            for (int sp = 0; sp <= (f != 0 ? 0 : code == 1 && m->pipe_blocks > 0 ? 2 : 1); ++sp)
+            for (int sp = 0; sp <= (f != 0 ? 0 : code == 1 ? 3 : 1); ++sp)
             for (int od = 0; od <= (f != 0 ? 0 : 1) && st == BH_OK; ++od) {
+                if (sp == 2 && m->pipe_blocks < 1) continue;
                 m->persistent = f;
                 m->split = sp;
                 if (od != m->tile_order) {

@@ -575,3 +575,49 @@ def test_pipelined_interior_forward(cuda):
         for a, b in zip(ref, run(m)):
             assert np.array_equal(a, b), sp
     m.close()
+
+
+@pytest.mark.parametrize("cap", [0, 2_000_000])
+def test_fused_interior_steps(cuda, cap):
+    """split 3 (one launch per forward step for the interior tiles, both
+    half-steps in one block, the fields alternating between two buffers)
+    gives the split 1 seismograms and gradients to rounding, and the same
+    bits for every shot grouping: every step stored and an odd step count,
+    and under a checkpoint cap whose segments and re-runs end on odd and
+    even steps; shot groups of 3 and 1."""
+    from paper_2005_00281_gb300.bh import model_from_workload
+    torch = cuda
+    w = tiny_borehole(seed=22, nr=48, nz=420, npml=6, nt=161)
+    w.shots = [dict(z_offset=8 * k, nz=300 + 37 * k, src=(0, 30 + k), rec_iz=[60, 90, 150])
+               for k in range(3)]
+    wav = torch.from_numpy(w.wavelet).cuda()
+
+    def run(m):
+        seis = m.forward(wav)
+        resid, J = m.residual_misfit(seis, torch.zeros_like(seis))
+        g = m.adjoint_gradient(resid)
+        torch.cuda.synchronize()
+        return [seis.cpu().numpy()] + [x.cpu().numpy() for x in g]
+
+    m = model_from_workload(w, checkpoint_cap_bytes=cap)
+    if cap:
+        assert m.info("recompute_steps") > 0
+    m.set_option("persistent", 0)
+    m.set_option("tile_code", 1)
+    m.set_option("split", 1)
+    ref = run(m)
+    assert np.max(np.abs(ref[0])) > 0 and np.max(np.abs(ref[1])) > 0
+    m.set_option("split", 3)
+    got3 = None
+    for G in (3, 1):
+        m.set_option("group", G)
+        got = run(m)
+        # the fused kernel's velocity arithmetic is compiled separately:
+        # the same to rounding, and the same bit for bit across groupings
+        for a, b in zip(ref, got):
+            assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b)), G
+        if got3 is not None:
+            for a, b in zip(got3, got):
+                assert np.array_equal(a, b), G
+        got3 = got
+    m.close()
