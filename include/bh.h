@@ -296,8 +296,8 @@ bh_status bh_profile_reset(bh_model* model);
  *   J        host double; the call synchronises `stream`
  *   stream   cudaStream_t (NULL = legacy default stream)
  * The first call on a device looks up the scratch address on that device
- * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
- * first call before any stream capture.  A device reset (cudaDeviceReset)
+ * (cudaGetSymbolAddress) and keeps it for the life of the process.  A
+ * device reset (cudaDeviceReset)
  * after the first call is not supported: the kept address would be stale.
  * All calls share the one scratch array: calls whose work overlaps on the
  * GPU (unordered streams) race and may return a wrong J.
