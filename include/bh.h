@@ -329,15 +329,19 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
  *                     and with "tile_code" 1 the forward's interior tiles
  *                     run in pipelined kernels (a grid of a few blocks per
  *                     SM, each block copying its next tile while it
- *                     computes the current one).  All give bit for bit the
- *                     same results.  BH_ERR_UNSUPPORTED for 2 when the
- *                     pipelined kernels do not fit an SM.  3: as 1, and
- *                     with "tile_code" 1 every forward step of the interior
- *                     tiles is one launch (both half-steps of a tile in one
- *                     block, velocities recomputed on the stress stencil's
- *                     halo); the six forward fields then alternate between
- *                     two buffers (6 planes per shot more device memory).
- *                     The same results bit for bit.
+ *                     computes the current one).  0, 1 and 2 give bit for
+ *                     bit the same results.  BH_ERR_UNSUPPORTED for 2 when
+ *                     the pipelined kernels do not fit an SM.  3: as 1,
+ *                     and with "tile_code" 1 every forward step of the
+ *                     interior tiles is one launch (both half-steps of a
+ *                     tile in one block, velocities recomputed on the
+ *                     stress stencil's halo); the six forward fields then
+ *                     alternate between two buffers (always allocated: 6
+ *                     planes per shot).  Its velocity arithmetic is the
+ *                     same expressions compiled in another kernel, so
+ *                     results agree with 1 to rounding (multiply-add
+ *                     contraction), and bit for bit across shot
+ *                     groupings.
  *   "pipe_grid"       cap on the blocks of a pipelined launch (default 0:
  *                     as many as fit the SMs); a small cap makes every
  *                     block walk many tiles (a test knob).
