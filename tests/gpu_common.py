@@ -36,11 +36,14 @@ def oracle_observed(w):
     return out
 
 
-def gpu_gradient(w, obs, device="cuda"):
-    """Forward, residual, adjoint through libbh.  Returns a dict of numpy arrays."""
+def gpu_gradient(w, obs, device="cuda", options=None):
+    """Forward, residual, adjoint through libbh (bh_set_option for every item
+    of `options` first).  Returns the model and a dict of numpy arrays."""
     from paper_2005_00281_gb300.bh import model_from_workload
 
     m = model_from_workload(w, device=device)
+    for k, v in (options or {}).items():
+        m.set_option(k, v)
     wav = torch.from_numpy(w.wavelet).to(device)
     seis = m.forward(wav)
     obs_t = torch.from_numpy(obs.astype(np.float32)).to(device)
