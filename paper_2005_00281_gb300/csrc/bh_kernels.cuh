@@ -1802,12 +1802,13 @@ __global__ void __launch_bounds__(kThreads, 4)
 // ------------------------------------------------- fused interior steps
 //
 // One launch per time step over the interior tiles (option "split" 3): both
-// half-steps of Eq. 2 for a tile.  The four stresses tau^n are staged with a
-// 4-node halo (rows i0-4 .. i0+19, columns j0-8 .. j0+39), v^{n-1/2} and the
-// buoyancies with the usual 2-node halo.  The block first updates v on the
-// whole 2-node-halo region (the nodes its stress stencils read) and keeps it
-// in shared memory, then runs the stress half-step of its own nodes, so the
-// wavefields cross HBM once per step instead of once per half-step.
+// half-steps of Eq. 2 for a tile.  The block updates v at the nodes its
+// stress stencils read (v_r rows i0-1 .. i0+17, v_z rows i0-2 .. i0+16,
+// columns j0-4 .. j0+35 in float4 groups) and keeps them in shared memory,
+// then runs the stress half-step of its own nodes, so the wavefields cross
+// HBM once per step instead of once per half-step.  Those velocity updates
+// read tau^n on rows i0-3 .. i0+18 and columns j0-8 .. j0+39 (staged),
+// v^{n-1/2} and the buoyancies on the usual 2-node halo.
 // Neighbouring tiles recompute each other's halo velocities, which is why
 // the fields ping-pong: the launch reads buffer pp and writes buffer 1 - pp,
 // and the C-PML tiles of the same step run the two half-step launches on
@@ -1817,8 +1818,8 @@ __global__ void __launch_bounds__(kThreads, 4)
 // zero edge; the axis mirror is applied to the updated velocities.  The
 // arithmetic is that of the half-step kernels, node for node.
 
-constexpr int kH4 = 4;
-constexpr int kSR4 = kTR + 2 * kH4;  // 24 staged rows
+constexpr int kTop4 = 3;                // staged rows i0-3 .. i0+18
+constexpr int kSR4 = kTR + kTop4 + 3;  // 22
 constexpr int kSZ4 = kTZ + 16;       // 48 staged columns, j0-8 .. j0+39
 constexpr int kQ4 = kSZ4 / 4;
 typedef float Tile4[kSR4][kSZ4];
@@ -1849,7 +1850,7 @@ __device__ __forceinline__ Slot slot4_of(int it, int i0, int j0, const WinK& g)
     Slot s;
     s.rr = it / kQ4;
     s.cq = 4 * (it - s.rr * kQ4);
-    const int i = i0 - kH4 + s.rr, j = j0 - 8 + s.cq;
+    const int i = i0 - kTop4 + s.rr, j = j0 - 8 + s.cq;
     const bool zin = j >= 0 && j < g.nz;
     s.zlim = zin ? min(4, g.nz - j) : 0;
     const int ie = i < 0 ? -1 - i : i;
@@ -1916,7 +1917,7 @@ __global__ void __launch_bounds__(kThreads, 6)
         if (o.i >= 1) mh = ld4g(C.w_muh + o.cw);
     }
     async_wait_all();
-    if (i0 < kH4) {
+    if (i0 < kTop4) {
         for (int it = tid_of(); it < kSR4 * kQ4; it += kThreads) {
             const Slot sl = slot4_of(it, i0, j0, g);
             if (sl.neg && sl.off_o >= 0) {
@@ -1939,16 +1940,16 @@ __global__ void __launch_bounds__(kThreads, 6)
         vz_old = lds4(sm.vz, o.rr, o.cc);
     }
     __syncthreads();
-    // ---- velocity half-step on the 2-node-halo region (rows i >= 0; the
-    // mirror rows follow), in place over this thread's slots
+    // ---- velocity half-step at the nodes the stress stencils read (rows
+    // i >= 0; the mirror rows follow), in place over this thread's slots:
+    // v_r on staged rows 1 .. 19, v_z on rows 0 .. 18
     for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
         const int r2 = it / kQ, c2 = 4 * (it - r2 * kQ);
         const int i = i0 - kH + r2;
         if (i < 0) continue;
-        const int R = r2 + (kH4 - kH), K = c2 + 4;  // the same node in the Tile4 grid
+        const int R = r2 + (kTop4 - kH), K = c2 + 4;  // the same node in the Tile4 grid
         const V12 rz12 = lds12(sm.rz, R, K - 4);
-        const V4 rzp1 = lds4(sm.rz, R + 1, K);
-        if (i >= 1) {
+        if (i >= 1 && r2 >= 1) {
             const V4 rm2 = lds4(sm.rr, R - 2, K), rm1 = lds4(sm.rr, R - 1, K);
             const V4 r0 = lds4(sm.rr, R, K), rp1 = lds4(sm.rr, R + 1, K);
             const V4 tm1 = lds4(sm.tt, R - 1, K), t0 = lds4(sm.tt, R, K);
@@ -1964,8 +1965,9 @@ __global__ void __launch_bounds__(kThreads, 6)
             }
             *reinterpret_cast<float4*>(&sm.vr[r2][c2]) = make_float4(vr[0], vr[1], vr[2], vr[3]);
         }
-        {
+        if (r2 < kSR - 1) {
             const V12 zz12 = lds12(sm.zz, R, K - 4);
+            const V4 rzp1 = lds4(sm.rz, R + 1, K);
             const V4 rzm1 = lds4(sm.rz, R - 1, K), rzp2 = lds4(sm.rz, R + 2, K);
             const V4 vz0 = lds4(sm.vz, r2, c2), bz = lds4(sm.bz, r2, c2);
             const float inv_r = __ldg(C.inv_r_half + i);
@@ -2006,7 +2008,7 @@ __global__ void __launch_bounds__(kThreads, 6)
         }
     }
     // ---- stress half-step of the own nodes
-    const int R = o.rr + (kH4 - kH), K = o.cc + 4;
+    const int R = o.rr + (kTop4 - kH), K = o.cc + 4;
     const V4 t_rr = lds4(sm.rr, R, K), t_tt = lds4(sm.tt, R, K), t_zz = lds4(sm.zz, R, K);
     const V4 t_rz = lds4(sm.rz, R, K);
     float* h = r.hist_n0 >= 0 ? hist_slot(sh, n - r.hist_n0 + 1) : nullptr;

@@ -1629,7 +1629,7 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "pipe_blocks") *value = m->pipe_blocks;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
-                     (kFwdPlanes + kAdjPlanes + 2.0 * m->hist_slots) +
+                     (kFwdPlanes + kFields + kAdjPlanes + 2.0 * m->hist_slots) +
                  20.0 * m->grid.nr * m->Pw * sizeof(float) +
                  (double)pl * (m->snap_prec ? 2 : 4) * m->nshots * m->nsnap * kFwdPlanes +
                  (double)ng * (6 * sizeof(float) + 1 + 2 * sizeof(double));
