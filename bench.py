@@ -59,7 +59,7 @@ SECONDARY_STEPS = 10
 # the three gradient accumulators G_lambda, G_mu,nn, G_mu,rz read and
 # written.  Kahan compensation, the pseudo-Hessian and the density
 # correlation are not counted (implementation extras).
-def survey_bytes_per_cell(kernel: str, s: float, shared_model: bool, hist: float = 1.0) -> float:
+def method_bytes_per_cell(kernel: str, s: float, shared_model: bool, hist: float = 1.0) -> float:
     m = 0.0 if shared_model else 1.0
     return {
         "fwd_vel": 16 + 4 * m + 16 * s,
@@ -453,8 +453,8 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
 
     def per_cell(k, model):
         hf = hist_frac if k.startswith("fwd") else 1.0
-        if model == "survey":
-            return sum(survey_bytes_per_cell(p, s, shared, hf) for p in PERSIST_PARTS[k])
+        if model == "method":
+            return sum(method_bytes_per_cell(p, s, shared, hf) for p in PERSIST_PARTS[k])
         if k == "fwd_step":
             return all_array_bytes_per_cell(k, s, with_rho, hf)
         return sum(all_array_bytes_per_cell(p, s, with_rho, hf) for p in PERSIST_PARTS[k])
@@ -465,8 +465,8 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
         sec = tms / 1e3
         kernels[k] = {"avg_us": 1e3 * tms / nl, "sampled_launches": nl,
                       "cells_per_launch": cells / nl,
-                      "alg_bytes_per_launch": per_cell(k, "survey") * cells / nl,
-                      "alg_GBps": per_cell(k, "survey") * cells / sec / 1e9,
+                      "alg_bytes_per_launch": per_cell(k, "method") * cells / nl,
+                      "alg_GBps": per_cell(k, "method") * cells / sec / 1e9,
                       "all_array_GBps": per_cell(k, "all") * cells / sec / 1e9}
     achieved = kernels[dom]["alg_GBps"]
     dram_per_cell = ncu_traffic(dom, w.name)
@@ -484,13 +484,13 @@ def measure(w, args, dev, world, rank, steps, warmup, cap, prec, with_rho, e2e_s
                 "unit": "GB/s", "frac": achieved / peak if achieved else None,
                 "traffic": (dram_per_cell * kernels[dom]["cells_per_launch"]
                             if dram_per_cell is not None else None),
-                "alg_bytes_per_cell_step": per_cell(dom, "survey"),
+                "alg_bytes_per_cell_step": per_cell(dom, "method"),
                 "frac_all_arrays": kernels[dom]["all_array_GBps"] / peak,
                 "all_array_bytes_per_cell_step": per_cell(dom, "all"),
                 "peak_source": f"{peak_kind} (hbm_gbs)", "note": bound_note}
-    step_bytes = (sum(survey_bytes_per_cell(k, s, shared, hist_frac)
+    step_bytes = (sum(method_bytes_per_cell(k, s, shared, hist_frac)
                       for k in PERSIST_PARTS["fwd_persist"]) * win_cells * fwd_steps +
-                  sum(survey_bytes_per_cell(k, s, shared)
+                  sum(method_bytes_per_cell(k, s, shared)
                       for k in PERSIST_PARTS["adj_persist"]) * win_cells * w.nt)
     out = {"value": value, "ms_per_step": ms / steps, "config": workload_config(w),
            "gradient_evals_per_s": grads_per_s,
