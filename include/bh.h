@@ -341,7 +341,14 @@ bh_status bh_residual_misfit_noalloc(const float* seis_mod, const float* seis_ob
  *                     same expressions compiled in another kernel, so
  *                     results agree with 1 to rounding (multiply-add
  *                     contraction), and bit for bit across shot
- *                     groupings.
+ *                     groupings.  4: as 3, with the fused step's tiles
+ *                     staged by TMA box copies (cp.async.bulk.tensor on
+ *                     tensor maps of the field buffers and coefficient
+ *                     copies, one issuing thread, a bounded mbarrier wait);
+ *                     the same results as 3.  BH_ERR_UNSUPPORTED for 4 when
+ *                     the tensor maps could not be encoded; a copy that
+ *                     does not complete makes bh_forward /
+ *                     bh_adjoint_gradient return BH_ERR_TIMEOUT.
  *   "pipe_grid"       cap on the blocks of a pipelined launch (default 0:
  *                     as many as fit the SMs); a small cap makes every
  *                     block walk many tiles (a test knob).
@@ -375,7 +382,7 @@ bh_status bh_set_option(bh_model* model, const char* key, double value);
  * the shot group sizes 1, 2, 4, ... up to min(32, nshots) (and nshots
  * itself) and the launch forms of the "persistent" option that differ for
  * that grouping (and, for one launch per half-step, "split" 0 and 1, and 2
- * and 3 with tile code 1, and both "tile_order" values); each
+ * to 4 with tile code 1, and both "tile_order" values); each
  * is timed four times over `steps` forward and `steps` adjoint steps of
  * every shot (CUDA events on the model's stream, the best of the last three
  * kept) and the fastest is applied (options "tile_code", "group",
@@ -419,7 +426,8 @@ bh_status bh_tune_lookup(const char* cache_path, const char* gpu_name, int nr,
  * "history_snapshot_bytes", "device_bytes", "kernel_launches" (kernels the
  * model has launched since it was created, for counting the launches of a
  * timed region), "group" (shots per launch group), "tile_code", "split",
- * "pipe_grid", "tile_order" (the options' values), "pipe_blocks" (blocks of a pipelined
+ * "pipe_grid", "tile_order" (the options' values), "tma" (1 when the
+ * tensor maps of "split" 4 exist), "pipe_blocks" (blocks of a pipelined
  * launch that fit the SMs), "state_version"
  * (changes whenever the stored forward
  * history is replaced or invalidated: bh_forward, bh_set_model, bh_update,

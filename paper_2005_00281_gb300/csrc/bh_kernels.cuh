@@ -11,6 +11,7 @@
 // Ghost values: half-r fields mirror evenly about the axis, integer-r fields
 // oddly; everything beyond r >= nr or outside 0 <= z < nz is zero.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -1873,65 +1874,26 @@ __device__ __forceinline__ void stage4_async(Tile4& t, const float* __restrict__
                  : "memory");
 }
 
-struct __align__(16) StepSmem {
+struct __align__(128) StepSmem {
     Tile4 rr, tt, zz, rz;  // tau^n
     Tile vr, vz;           // v^{n-1/2}, replaced by v^{n+1/2}
     Tile br, bz;           // buoyancy at the v_r and v_z nodes
 };
 
+// The part of a fused interior step after the staging: the velocity
+// updates on the halo region, the axis mirror of the result, the own
+// velocities and history, and the stress half-step of the own nodes.
 template <int N>
-__global__ void __launch_bounds__(kThreads, 6)
-    k_fwd_step(RunK r, int n, int pp, const __grid_constant__ ShotTable<N> T)
+__device__ __forceinline__ void fused_step_tail(const RunK& r, int n, const ShotK& sh,
+                                                ptrdiff_t fout, const Own& o, const V4& lm,
+                                                const V4& mu, const V4& mh, float ivh,
+                                                StepSmem& sm)
 {
-    __shared__ StepSmem sm;
-    pdl_wait();
-    const int4 tk = r.tiles[blockIdx.x];
-    const ShotK& sh = shot_of(T, tk);
     const WinK& g = sh.g;
     const CoefK& C = sh.C;
     const StateK& S = sh.Sf;
-    const ptrdiff_t fin = field_in(sh, pp), fout = field_out(sh, pp);
-    const int i0 = tk.y, j0 = tk.z;
-    const Own o = own_of(g, i0, j0);
-    for (int it = tid_of(); it < kSR4 * kQ4; it += kThreads) {
-        const Slot sl = slot4_of(it, i0, j0, g);
-        stage4_async<EVEN>(sm.rr, S.trr + fin, sl);
-        stage4_async<EVEN>(sm.tt, S.ttt + fin, sl);
-        stage4_async<EVEN>(sm.zz, S.tzz + fin, sl);
-        stage4_async<ODD>(sm.rz, S.trz + fin, sl);
-    }
-    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
-        const Slot sl = slot_of(it, i0, j0, g);
-        stage_async<ODD>(sm.vr, S.vr + fin, sl);
-        stage_async<EVEN>(sm.vz, S.vz + fin, sl);
-        stage_async<ABS, true>(sm.br, C.w_bvr, sl);
-        stage_async<EVEN, true>(sm.bz, C.w_bvz, sl);
-    }
-    // own-node inputs of the stress half-step, in flight with the copies
-    V4 lm{}, mu{}, mh{};
-    float ivh = 0.f;
-    if (o.live) {
-        ivh = __ldg(C.inv_r_half + o.i);
-        lm = ld4g(C.w_lam + o.cw);
-        mu = ld4g(C.w_mu + o.cw);
-        if (o.i >= 1) mh = ld4g(C.w_muh + o.cw);
-    }
-    async_wait_all();
-    if (i0 < kTop4) {
-        for (int it = tid_of(); it < kSR4 * kQ4; it += kThreads) {
-            const Slot sl = slot4_of(it, i0, j0, g);
-            if (sl.neg && sl.off_o >= 0) {
-                float4* q = reinterpret_cast<float4*>(&sm.rz[sl.rr][sl.cq]);
-                float4 v = *q;
-                v.x = -v.x;
-                v.y = -v.y;
-                v.z = -v.z;
-                v.w = -v.w;
-                *q = v;
-            }
-        }
-    }
-    __syncthreads();
+    const int4 tk = r.tiles[blockIdx.x];
+    const int i0 = tk.y;
     // v^{n-1/2} of the own nodes (history slot 0 of a segment's first step)
     const bool h0 = r.hist_n0 >= 0 && n == r.hist_n0;
     V4 vr_old{}, vz_old{};
@@ -2017,6 +1979,200 @@ __global__ void __launch_bounds__(kThreads, 6)
     fwd_stress_core<PM_INTERIOR>(g, S, fout, sh.q, n, r.record != 0, h, o, false, t_rr, t_tt,
                                  t_zz, t_rz, lm, mu, mh, zero, zero, zero, zero, ivh, sm.vr,
                                  sm.vz, nullptr, nullptr, epoch);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 6)
+    k_fwd_step(RunK r, int n, int pp, const __grid_constant__ ShotTable<N> T)
+{
+    __shared__ StepSmem sm;
+    pdl_wait();
+    const int4 tk = r.tiles[blockIdx.x];
+    const ShotK& sh = shot_of(T, tk);
+    const WinK& g = sh.g;
+    const CoefK& C = sh.C;
+    const StateK& S = sh.Sf;
+    const ptrdiff_t fin = field_in(sh, pp), fout = field_out(sh, pp);
+    const int i0 = tk.y, j0 = tk.z;
+    const Own o = own_of(g, i0, j0);
+    for (int it = tid_of(); it < kSR4 * kQ4; it += kThreads) {
+        const Slot sl = slot4_of(it, i0, j0, g);
+        stage4_async<EVEN>(sm.rr, S.trr + fin, sl);
+        stage4_async<EVEN>(sm.tt, S.ttt + fin, sl);
+        stage4_async<EVEN>(sm.zz, S.tzz + fin, sl);
+        stage4_async<ODD>(sm.rz, S.trz + fin, sl);
+    }
+    for (int it = tid_of(); it < kSR * kQ; it += kThreads) {
+        const Slot sl = slot_of(it, i0, j0, g);
+        stage_async<ODD>(sm.vr, S.vr + fin, sl);
+        stage_async<EVEN>(sm.vz, S.vz + fin, sl);
+        stage_async<ABS, true>(sm.br, C.w_bvr, sl);
+        stage_async<EVEN, true>(sm.bz, C.w_bvz, sl);
+    }
+    // own-node inputs of the stress half-step, in flight with the copies
+    V4 lm{}, mu{}, mh{};
+    float ivh = 0.f;
+    if (o.live) {
+        ivh = __ldg(C.inv_r_half + o.i);
+        lm = ld4g(C.w_lam + o.cw);
+        mu = ld4g(C.w_mu + o.cw);
+        if (o.i >= 1) mh = ld4g(C.w_muh + o.cw);
+    }
+    async_wait_all();
+    if (i0 < kTop4) {
+        for (int it = tid_of(); it < kSR4 * kQ4; it += kThreads) {
+            const Slot sl = slot4_of(it, i0, j0, g);
+            if (sl.neg && sl.off_o >= 0) {
+                float4* q = reinterpret_cast<float4*>(&sm.rz[sl.rr][sl.cq]);
+                float4 v = *q;
+                v.x = -v.x;
+                v.y = -v.y;
+                v.z = -v.z;
+                v.w = -v.w;
+                *q = v;
+            }
+        }
+    }
+    __syncthreads();
+    fused_step_tail<N>(r, n, sh, fout, o, lm, mu, mh, ivh, sm);
+    pdl_launch_dependents();
+}
+
+// ------------------------------------ fused interior steps, TMA staging
+//
+// The same fused step (option "split" 4) with its eight tiles staged by the
+// tensor memory accelerator: one thread issues a 2-D box copy per field
+// (cp.async.bulk.tensor, 3-D tensor maps over the shots' field planes and
+// over the coefficient copies, no multicast) that completes on a shared
+// mbarrier, instead of 128 threads issuing 16-byte cp.async copies slot by
+// slot.  Interior tiles lie inside their window, so the boxes need no zero
+// edge; rows above the axis come back zero-filled and the axis tile
+// rebuilds the stresses' mirror rows from the copied ones (the velocity
+// and buoyancy mirror rows are never read).  Every box starts at a column
+// that is a multiple of 4 floats (tile columns are multiples of 32, the
+// coefficient copies are shifted for that), every destination tile is
+// 128-byte aligned.  The wait is bounded: a copy that does not complete
+// sets *err, and the block returns.
+
+struct TmaMaps {
+    CUtensorMap t[2];  // stresses of field buffer 0 / 1 (planes shot * 14 + f / shot * 6 + f), box 48 x 22
+    CUtensorMap v[2];  // velocities of field buffer 0 / 1, box 40 x 20
+    CUtensorMap w;     // coefficient copies (planes 5 k + q), box 40 x 20
+};
+
+constexpr unsigned kStepTmaBytes = 4u * kSR4 * kSZ4 * 4u + 4u * kSR * kSZ * 4u;
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for phase `parity` of the mbarrier
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
+{
+    for (int k = 0; k < (1 << 22); ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 6)
+    k_fwd_step_tma(RunK r, int n, int pp, int s0, int* err, const __grid_constant__ TmaMaps M,
+                   const __grid_constant__ ShotTable<N> T)
+{
+    __shared__ StepSmem sm;
+    __shared__ __align__(8) unsigned long long mbar;
+    const unsigned bar = smem_addr(&mbar);
+    const int tid = tid_of();
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    pdl_wait();
+    const int4 tk = r.tiles[blockIdx.x];
+    const ShotK& sh = shot_of(T, tk);
+    const WinK& g = sh.g;
+    const CoefK& C = sh.C;
+    const ptrdiff_t fout = field_out(sh, pp);
+    const int i0 = tk.y, j0 = tk.z;
+    const Own o = own_of(g, i0, j0);
+    if (tid == 0) {
+        mbar_expect_tx(bar, kStepTmaBytes);
+        const int b = pp == 1 ? 1 : 0;  // the buffer this step reads
+        const int shot = s0 + tk.x;
+        const int base = b ? shot * 6 : shot * 14;  // plane of v_r; v_z, trr, ttt, tzz, trz follow
+        const CUtensorMap* mt = &M.t[b];
+        const CUtensorMap* mv = &M.v[b];
+        tma_load_3d(&sm.rr, mt, j0 - 8, i0 - kTop4, base + 2, bar);
+        tma_load_3d(&sm.tt, mt, j0 - 8, i0 - kTop4, base + 3, bar);
+        tma_load_3d(&sm.zz, mt, j0 - 8, i0 - kTop4, base + 4, bar);
+        tma_load_3d(&sm.rz, mt, j0 - 8, i0 - kTop4, base + 5, bar);
+        tma_load_3d(&sm.vr, mv, j0 - 4, i0 - kH, base + 0, bar);
+        tma_load_3d(&sm.vz, mv, j0 - 4, i0 - kH, base + 1, bar);
+        const int kc = (4 - (g.z0 & 3)) & 3;  // the shifted copy of this window
+        tma_load_3d(&sm.br, &M.w, g.z0 + kc + j0 - 4, i0 - kH, 5 * kc + 3, bar);
+        tma_load_3d(&sm.bz, &M.w, g.z0 + kc + j0 - 4, i0 - kH, 5 * kc + 4, bar);
+    }
+    // own-node inputs of the stress half-step, in flight with the copies
+    V4 lm{}, mu{}, mh{};
+    float ivh = 0.f;
+    if (o.live) {
+        ivh = __ldg(C.inv_r_half + o.i);
+        lm = ld4g(C.w_lam + o.cw);
+        mu = ld4g(C.w_mu + o.cw);
+        if (o.i >= 1) mh = ld4g(C.w_muh + o.cw);
+    }
+    if (!mbar_wait_bounded(bar, 0)) {
+        if (tid == 0) atomicExch(err, 1);
+        mbar_wait_bounded(bar, 0);  // the copies still in flight, once more, bounded
+        return;
+    }
+    if (i0 < kTop4) {
+        // the axis tile: stresses at rows i < 0 from their mirror images
+        // (cells even, f[-1-k] = f[k]; trz odd, f[-k] = -f[k])
+        for (int it = tid; it < 4 * kTop4 * kQ4; it += kThreads) {
+            const int f = it / (kTop4 * kQ4), q = it - f * (kTop4 * kQ4);
+            const int rr = q / kQ4, cq = 4 * (q - rr * kQ4);
+            Tile4& t = f == 0 ? sm.rr : f == 1 ? sm.tt : f == 2 ? sm.zz : sm.rz;
+            const int i = rr - kTop4;  // -3 .. -1
+            const float4 src = *reinterpret_cast<const float4*>(
+                &t[(f == 3 ? -i : -1 - i) + kTop4][cq]);
+            *reinterpret_cast<float4*>(&t[rr][cq]) =
+                f == 3 ? make_float4(-src.x, -src.y, -src.z, -src.w) : src;
+        }
+    }
+    __syncthreads();
+    fused_step_tail<N>(r, n, sh, fout, o, lm, mu, mh, ivh, sm);
     pdl_launch_dependents();
 }
 

@@ -6,6 +6,8 @@
 #include "bh_kernels.cuh"
 #include "bh_ops.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -103,6 +105,8 @@ struct bh_model {
     int pipe_blocks = 0;                  // grid of the pipelined kernels (0: unavailable)
     int pipe_grid = 0;                    // option "pipe_grid": cap on that grid (0: none)
     int tile_order = 0;                   // option "tile_order" (build_tiles)
+    TmaMaps maps;                         // tensor maps of the TMA-staged fused step
+    bool tma_ok = false;                  // the maps could be encoded ("split" 4)
     int4* d_tiles_cls = nullptr;          // every group's tiles, interior first
     std::vector<int> group_nint;          // interior tiles of each group
     int fwd_blocks = 0, adj_blocks = 0;       // co-resident blocks, 1-shot kernels
@@ -165,6 +169,41 @@ cudaError_t dalloc(T** p, size_t count)
     *p = nullptr;
     if (count == 0) return cudaSuccess;
     return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+// Tensor maps of the TMA-staged fused step (k_fwd_step_tma): 3-D views
+// (columns, rows, planes) of the two forward field buffers and of the
+// coefficient copies, FP32, zero fill out of bounds, no swizzle.  The
+// encoder comes from the driver through the runtime's entry-point query.
+bool encode_maps(bh_model* m)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    auto one = [&](CUtensorMap* map, void* base, cuuint64_t cols, cuuint64_t rows,
+                   cuuint64_t planes, cuuint32_t bx, cuuint32_t by) {
+        const cuuint64_t dim[3] = {cols, rows, planes};
+        const cuuint64_t stride[2] = {cols * sizeof(float), rows * cols * sizeof(float)};
+        const cuuint32_t box[3] = {bx, by, 1};
+        const cuuint32_t estride[3] = {1, 1, 1};
+        return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dim, stride, box, estride,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    const cuuint64_t nr = m->grid.nr, P = m->P, Pw = m->Pw, ns = m->nshots;
+    return one(&m->maps.t[0], m->d_fwd, P, nr, ns * kFwdPlanes, kSZ4, kSR4) &&
+           one(&m->maps.t[1], m->d_fwd2, P, nr, ns * kFields, kSZ4, kSR4) &&
+           one(&m->maps.v[0], m->d_fwd, P, nr, ns * kFwdPlanes, kSZ, kSR) &&
+           one(&m->maps.v[1], m->d_fwd2, P, nr, ns * kFields, kSZ, kSR) &&
+           one(&m->maps.w, m->d_wcoef, Pw, nr, 20, kSZ, kSR);
 }
 
 void free_model(bh_model* m)
@@ -699,7 +738,7 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
         return check_barrier(m);
     }
     const dim3 grd(r.ntiles);
-    if (V == 1 && m->split == 3) {
+    if (V == 1 && (m->split == 3 || (m->split == 4 && m->tma_ok))) {
         // fused steps: the fields ping-pong between the two buffers and end
         // in buffer 0 (snapshots and the next run start there)
         RunK ri, rp;
@@ -707,7 +746,11 @@ bh_status run_forward_group(bh_model* m, int grp, int n0, int n1, int hist_n0, b
         for (int n = n0; n < n1; ++n) {
             const int pp = (n - n0) & 1;
             size_t e = prof_begin(m, BH_KERNEL_FWD_STEP, n);
-            if (ri.ntiles) {
+            if (ri.ntiles && m->split == 4) {
+                BH_CUDA(m, launch_pdl(k_fwd_step_tma<N>, dim3(ri.ntiles), blk, m->stream, ri, n,
+                                      pp, grp * m->G, (int*)(m->d_bar + 2), m->maps, T));
+                ++m->launches;
+            } else if (ri.ntiles) {
                 BH_CUDA(m, launch_pdl(k_fwd_step<N>, dim3(ri.ntiles), blk, m->stream, ri, n, pp, T));
                 ++m->launches;
             }
@@ -861,10 +904,12 @@ bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, lon
 {
     if (n1 <= n0) return BH_OK;
     const int ngroups = (int)m->group_ntiles.size();
+    const bool tma = m->split == 4 && m->tile_code == 1 && m->tma_ok;
+    if (tma) BH_CUDA(m, cudaMemsetAsync(m->d_bar + 2, 0, sizeof(unsigned), m->stream));
     for (int grp = 0; grp < ngroups; ++grp) {
         const int nint = m->group_nint[grp], npml = m->group_ntiles[grp] - nint;
         *runs += persistent_for(m, grp, false) ? 1
-                 : (m->split == 3 && m->tile_code == 1)
+                 : (m->split >= 3 && m->tile_code == 1)
                      ? (long long)(n1 - n0) * ((nint > 0) + 2 * (npml > 0))
                      : 2 * (n1 - n0) * ((m->split && m->tile_code == 1) ? class_launches(m, grp) : 1);
         const bool one = m->G == 1;
@@ -875,6 +920,17 @@ bh_status run_forward(bh_model* m, int n0, int n1, int hist_n0, bool record, lon
             if (one) BH_TRY((run_forward_group<1, 1>(m, grp, n0, n1, hist_n0, record)));
             else BH_TRY((run_forward_group<kGroup, 1>(m, grp, n0, n1, hist_n0, record)));
         }
+    }
+    if (tma) {
+        // a TMA copy that never completed left its flag (bounded wait)
+        int err = 0;
+        BH_CUDA(m, cudaMemcpyAsync(&err, m->d_bar + 2, sizeof(int), cudaMemcpyDeviceToHost,
+                                   m->stream));
+        BH_CUDA(m, cudaStreamSynchronize(m->stream));
+        if (err)
+            return fail(m, BH_ERR_TIMEOUT,
+                        "a tensor copy of the fused forward step did not complete; results are "
+                        "invalid");
     }
     return BH_OK;
 }
@@ -1083,7 +1139,7 @@ bool tune_lookup(const char* path, const std::string& key, int* G, int* form, in
         std::string rest;
         if (!(is >> k >> g >> p >> v >> sp >> od >> rest)) continue;
         if (k != key || g < 1 || g > kGroup || p < 0 || p > 2 || v < 0 || v > 1 || sp < 0 ||
-            sp > 3 || od < 0 || od > 1)
+            sp > 4 || od < 0 || od > 1)
             continue;
         *G = g;
         *form = p;
@@ -1229,6 +1285,7 @@ bh_status bh_model_create(const bh_grid_desc* grid, int nz_global, const float* 
     CK(dalloc(&m->d_scal, 16));
     CK(dalloc(&m->d_part, 8 * (size_t)kMaxParts));
     CK(dalloc(&m->d_bar, 4));
+    m->tma_ok = encode_maps(m);
     {
         int dev = 0, sms = 0, coop = 0, nb = 0;
         CK(cudaGetDevice(&dev));
@@ -1565,8 +1622,10 @@ bh_status bh_set_option(bh_model* m, const char* key, double value)
             return fail(m, BH_ERR_UNSUPPORTED, "cooperative launch not available");
         m->persistent = (int)value;
     } else if (k == "split") {
-        if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
-            return fail(m, BH_ERR_INVALID_ARG, "split must be 0, 1, 2 or 3");
+        if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0 && value != 4.0)
+            return fail(m, BH_ERR_INVALID_ARG, "split must be 0 .. 4");
+        if (value == 4.0 && !m->tma_ok)
+            return fail(m, BH_ERR_UNSUPPORTED, "tensor maps could not be encoded");
         if (value == 2.0 && m->pipe_blocks < 1)
             return fail(m, BH_ERR_UNSUPPORTED, "the pipelined kernels do not fit an SM");
         m->split = (int)value;
@@ -1626,6 +1685,7 @@ bh_status bh_get_info(bh_model* m, const char* key, double* value)
     else if (k == "split") *value = m->split;
     else if (k == "pipe_grid") *value = m->pipe_grid;
     else if (k == "tile_order") *value = m->tile_order;
+    else if (k == "tma") *value = m->tma_ok ? 1.0 : 0.0;
     else if (k == "pipe_blocks") *value = m->pipe_blocks;
     else if (k == "device_bytes")
         *value = (double)pl * sizeof(float) * m->nshots *
@@ -1731,9 +1791,9 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
                 if (fit > 0 && fit < ng) forms.push_back(2);
             }
             for (int f : forms)
-            for (int sp = 0; sp <= (f != 0 ? 0 : code == 1 ? 3 : 1); ++sp)
+            for (int sp = 0; sp <= (f != 0 ? 0 : code == 1 ? 4 : 1); ++sp)
             for (int od = 0; od <= (f != 0 ? 0 : 1) && st == BH_OK; ++od) {
-                if (sp == 2 && m->pipe_blocks < 1) continue;
+                if ((sp == 2 && m->pipe_blocks < 1) || (sp == 4 && !m->tma_ok)) continue;
                 m->persistent = f;
                 m->split = sp;
                 if (od != m->tile_order) {
@@ -1789,7 +1849,8 @@ bh_status bh_tune(bh_model* m, int steps, const char* cache_path, char* choice, 
     if (bestForm != 0 && !coop) bestForm = 0;
     m->persistent = bestForm;
     m->tile_code = bestCode;
-    m->split = (bestSplit == 2 && m->pipe_blocks < 1) ? 1 : bestSplit;
+    m->split = (bestSplit == 2 && m->pipe_blocks < 1) || (bestSplit == 4 && !m->tma_ok) ? 1
+                                                                                    : bestSplit;
     if (bestOrder != m->tile_order) {
         m->tile_order = bestOrder;
         BH_TRY(build_tiles(m));

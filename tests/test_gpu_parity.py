@@ -584,7 +584,9 @@ def test_fused_interior_steps(cuda, cap):
     gives the split 1 seismograms and gradients to rounding, and the same
     bits for every shot grouping: every step stored and an odd step count,
     and under a checkpoint cap whose segments and re-runs end on odd and
-    even steps; shot groups of 3 and 1."""
+    even steps; shot groups of 3 and 1.  split 4 (the same step staged by
+    TMA box copies, the axis tile's mirror rows rebuilt) gives the split 3
+    bits."""
     from paper_2005_00281_gb300.bh import model_from_workload
     torch = cuda
     w = tiny_borehole(seed=22, nr=48, nz=420, npml=6, nt=161)
@@ -620,4 +622,11 @@ def test_fused_interior_steps(cuda, cap):
             for a, b in zip(got3, got):
                 assert np.array_equal(a, b), G
         got3 = got
+    # the same step with its tiles staged by the tensor memory accelerator
+    if m.info("tma") == 1:
+        m.set_option("split", 4)
+        for G in (3, 1):
+            m.set_option("group", G)
+            for a, b in zip(got3, run(m)):
+                assert np.array_equal(a, b), ("tma", G)
     m.close()
