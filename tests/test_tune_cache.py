@@ -52,5 +52,5 @@ def test_committed_cache_is_well_formed(lookup):
         key, g, f, v, sp, od = line.split()[:6]
         gpu, nr, P, shots = key.split("|")
         assert 1 <= int(g) <= 32 and int(f) in (0, 1, 2) and int(v) in (0, 1)
-        assert int(sp) in (0, 1, 2, 3) and int(od) in (0, 1)
+        assert int(sp) in (0, 1, 2, 3, 4) and int(od) in (0, 1)
         assert lookup(TUNE_CACHE, gpu, int(nr[2:]), int(P[1:]), int(shots[5:])) is not None
